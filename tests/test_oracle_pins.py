@@ -1,0 +1,503 @@
+"""Pins of the FP64 oracle to the paper and to mathematics (CPU only).
+
+Each test checks the oracle against something other than itself: a closed
+form, an invariant, a library routine the definition reduces to, brute force,
+or values printed in the paper.  They are chosen so that a dropped term, a
+wrong sign or index, or a transposed operand in any step fails one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.ndimage as ndi
+
+from oracle import oracle as O
+from paper_1705_09776_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def P():
+    return O.params()
+
+
+# ---------------------------------------------------------------- S1 filters
+
+@pytest.mark.parametrize("tau", [0.8, 1.2262, 1.52, 2.49, 3.161])
+def test_taps_sum_to_one_symmetric_and_variance(tau):
+    g = O.gaussian_taps(tau)
+    r = (g.size - 1) // 2
+    assert r == math.ceil(4 * tau)
+    assert abs(g.sum() - 1.0) < 1e-15
+    assert np.array_equal(g, g[::-1])
+    # second moment of the sampled, 4-sigma-truncated Gaussian is tau^2 up to
+    # the truncated tail (relative loss < 2e-3 at 4 sigma)
+    p = np.arange(-r, r + 1)
+    var = float((p * p * g).sum())
+    assert abs(var / (tau * tau) - 1.0) < 2e-3
+
+
+def test_tau_zero_is_identity():
+    assert np.array_equal(O.gaussian_taps(0.0), np.array([1.0]))
+
+
+def test_separable_equals_bruteforce_2d_and_library():
+    rng = np.random.default_rng(5)
+    img = rng.uniform(0, 255, size=(23, 31))
+    g = O.gaussian_taps(1.953)
+    sep = O.filter_separable(img, g)
+    bf = O.filter_2d(img, g)
+    lib = ndi.correlate(img, np.outer(g, g), mode="nearest")
+    assert np.max(np.abs(sep - bf)) <= 1e-12 * np.max(np.abs(bf))
+    assert np.max(np.abs(sep - lib)) <= 1e-12 * np.max(np.abs(lib))
+
+
+def test_constant_stays_constant_and_impulse_gives_kernel():
+    g = O.gaussian_taps(2.49)
+    c = O.filter_separable(np.full((40, 50), 77.0), g)
+    assert np.max(np.abs(c - 77.0)) < 1e-12
+    imp = np.zeros((41, 41))
+    imp[20, 20] = 1.0
+    out = O.filter_separable(imp, g)
+    r = (g.size - 1) // 2
+    assert np.max(np.abs(out[20 - r:21 + r, 20 - r:21 + r] - np.outer(g, g))) < 1e-16
+    # nothing outside the support
+    mask = np.ones_like(out, bool)
+    mask[20 - r:21 + r, 20 - r:21 + r] = False
+    assert np.all(out[mask] == 0.0)
+    # an off-centre impulse lands at the same offset (no transposition)
+    imp2 = np.zeros((41, 41))
+    imp2[10, 30] = 1.0
+    assert np.unravel_index(np.argmax(O.filter_separable(imp2, g)), (41, 41)) == (10, 30)
+
+
+def test_scale_schedule(P):
+    s = [O.scale(P, k) for k in range(4)]
+    assert s[0] == pytest.approx(1.6) and s[3] == pytest.approx(3.2)
+    assert s[1] / s[0] == pytest.approx(2 ** (1 / 3))
+    # radii of the level filters: octave 0 assumes 0.5 px input blur, later
+    # octaves start from a sigma0-blurred base
+    r0 = [(O.gaussian_taps(O.tau(P, 0, k)).size - 1) // 2 for k in range(4)]
+    r1 = [(O.gaussian_taps(O.tau(P, 1, k)).size - 1) // 2 for k in range(4)]
+    assert r0 == [7, 8, 10, 13]
+    assert r1 == [0, 5, 8, 12]
+
+
+def test_levels_compose_to_the_nominal_blur(P):
+    """Filtering a level further by tau' equals (within sampling/truncation
+    error) filtering the base by sqrt(tau^2 + tau'^2): the levels carry the
+    blurs the schedule claims."""
+    rng = np.random.default_rng(2)
+    img = ndi.gaussian_filter(rng.uniform(0, 255, (64, 64)), 2.0)
+    lv = O.scale_space(img.astype(np.uint8), P)
+    base = img.astype(np.uint8).astype(np.float64)
+    t1, t3 = O.tau(P, 0, 1), O.tau(P, 0, 3)
+    extra = math.sqrt(t3 * t3 - t1 * t1)
+    g_extra = O.gaussian_taps(extra)
+    a = O.filter_separable(lv[0][1], g_extra)
+    b = lv[0][3]
+    inner = (slice(16, 48), slice(16, 48))
+    assert np.max(np.abs(a[inner] - b[inner])) < 1e-2
+    assert np.max(np.abs(O.filter_separable(base, O.gaussian_taps(t3))[inner] - b[inner])) < 1e-12
+
+
+# --------------------------------------------------------------- S2 Laplacian
+
+def test_laplacian_exact_on_quadratic_and_ramp():
+    y, x = np.mgrid[0:20, 0:30].astype(np.float64)
+    q = x * x + y * y
+    L = O.laplacian(q, 2.0)
+    assert np.all(L[1:-1, 1:-1] == 4.0 * 4.0)
+    ramp = 3.0 * x - 2.0 * y + 7.0
+    assert np.all(O.laplacian(ramp, 1.7)[1:-1, 1:-1] == 0.0)
+    # sign: a bright spot has a negative Laplacian
+    spot = np.zeros((9, 9))
+    spot[4, 4] = 1.0
+    assert O.laplacian(spot, 1.0)[4, 4] == -4.0
+
+
+# --------------------------------------------------------------- S3 ALP fit
+
+def test_alp_exact_on_cubic_data(P):
+    rng = np.random.default_rng(3)
+    beta = O.alp_matrix(P)
+    s = np.array([O.scale(P, k) for k in range(4)])
+    for _ in range(50):
+        c = rng.normal(size=4) * np.array([10, 10, 5, 2])
+        Lk = c[0] + c[1] * s + c[2] * s ** 2 + c[3] * s ** 3
+        a = O.alp_fit(beta, Lk)
+        assert np.allclose(a, c, rtol=1e-10, atol=1e-10 * np.abs(c).max())
+
+
+def test_alp_least_squares_for_more_scales():
+    P6 = O.params(scales_per_octave=6)
+    beta = O.alp_matrix(P6)
+    s = np.array([O.scale(P6, k) for k in range(6)])
+    c = np.array([1.0, -2.0, 0.5, 0.25])
+    a = O.alp_fit(beta, c[0] + c[1] * s + c[2] * s ** 2 + c[3] * s ** 3)
+    assert np.allclose(a, c, rtol=1e-10)
+    # the fit of non-cubic data is the least-squares one (library lstsq)
+    Lk = np.sin(s)
+    V = np.vander(s, 4, increasing=True)
+    ref = np.linalg.lstsq(V, Lk, rcond=None)[0]
+    assert np.allclose(O.alp_fit(beta, Lk), ref, rtol=1e-9, atol=1e-12)
+
+
+# ---------------------------------------------------------- S4 extremum logic
+
+def _cubic_from_dp_roots(r1, r2, k, c0):
+    # p'(s) = 3k (s - r1)(s - r2)  =>  p = k s^3 - 1.5k(r1+r2) s^2 + 3k r1 r2 s + c0
+    return np.array([c0, 3 * k * r1 * r2, -1.5 * k * (r1 + r2), k])
+
+
+def test_extremum_is_analytic_root(P):
+    # p' = -3 (s-2)(s-3): minimum at 2, maximum at 3; c0 makes |p(3)| larger
+    a = _cubic_from_dp_roots(2.0, 3.0, -1.0, 20.0)
+    t, s, v = O.alp_extremum(a, P)
+    assert t == +1 and abs(s - 3.0) <= 1e-12 and abs(v - O.cubic(a, 3.0)) < 1e-12
+    # with a strongly negative offset the minimum at 2 has the larger |p|
+    a = _cubic_from_dp_roots(2.0, 3.0, -1.0, -40.0)
+    t, s, v = O.alp_extremum(a, P)
+    assert t == -1 and abs(s - 2.0) <= 1e-12
+    # root outside [s0, s3] -> nothing
+    a = _cubic_from_dp_roots(1.0, 4.0, 1.0, 50.0)
+    assert O.alp_extremum(a, P)[0] == 0
+    # below contrast
+    a = _cubic_from_dp_roots(2.0, 3.0, -1.0, 13.75)   # p(3) = 0.25, p(2) = -0.25
+    assert abs(O.cubic(a, 3.0)) < 4 and abs(O.cubic(a, 2.0)) < 4
+    assert O.alp_extremum(a, P)[0] == 0
+    # quadratic p (a3 = 0): single root of the linear derivative
+    a = np.array([30.0, -12.0, 2.5, 0.0])      # p' = 5 s - 12 -> s = 2.4, minimum
+    t, s, v = O.alp_extremum(a, P)
+    assert t == -1 and abs(s - 2.4) < 1e-15 and v == pytest.approx(30 - 12 * 2.4 + 2.5 * 2.4 ** 2)
+
+
+def test_extremum_matches_dense_grid_search(P):
+    """Brute force: local extrema of p on a dense grid over [s0, s3], with the
+    contrast rule and the larger-|p| choice, agree with the root logic."""
+    rng = np.random.default_rng(11)
+    s0, s3 = O.scale(P, 0), O.scale(P, 3)
+    grid = np.linspace(s0, s3, 10001)
+    h = grid[1] - grid[0]
+    n_checked = {0: 0, 1: 0, -1: 0}
+    for _ in range(3000):
+        a = rng.normal(size=4) * np.array([20, 40, 15, 3])
+        p = a[0] + a[1] * grid + a[2] * grid ** 2 + a[3] * grid ** 3
+        inner = p[1:-1]
+        ismax = (inner > p[:-2]) & (inner > p[2:])
+        ismin = (inner < p[:-2]) & (inner < p[2:])
+        cands = []
+        for i in np.nonzero(ismax | ismin)[0]:
+            if abs(inner[i]) >= 4.0:
+                cands.append((abs(inner[i]), grid[i + 1], +1 if ismax[i] else -1))
+        t, s, v = O.alp_extremum(a, P)
+        # skip draws whose decision sits within grid resolution of a threshold
+        near = any(abs(abs(x[0]) - 4.0) < 1e-3 for x in cands) or \
+            (t and (abs(s - s0) < 2 * h or abs(s3 - s) < 2 * h or abs(abs(v) - 4.0) < 1e-3))
+        if near:
+            continue
+        if not cands:
+            assert t == 0
+        else:
+            best = max(cands, key=lambda x: x[0])
+            if len(cands) == 2 and abs(cands[0][0] - cands[1][0]) < 1e-3:
+                continue
+            assert t == best[2]
+            assert abs(s - best[1]) <= 1.5 * h
+        n_checked[t] += 1
+    assert min(n_checked.values()) > 100
+
+
+# ---------------------------------------------------------------- S5 refine
+
+def test_refine_exact_on_quadratic_bump(P):
+    rng = np.random.default_rng(4)
+    for _ in range(200):
+        x0, y0 = rng.uniform(-0.49, 0.49, 2)
+        a = rng.uniform(10, 50)
+        c = rng.uniform(0.5, 2.0)
+        yy, xx = np.mgrid[-1:2, -1:2].astype(np.float64)
+        q = a - c * (xx - x0) ** 2 - 2 * c * (yy - y0) ** 2
+        ok, out = O.refine(q, P)
+        assert ok
+        assert abs(out[0] - x0) < 1e-12 and abs(out[1] - y0) < 1e-12
+        assert abs(out[2] - a) < 1e-10
+        assert out[3] == pytest.approx((3 * c) ** 2 / (2 * c * c))   # (-2c-4c)^2 / (8c^2)
+        # minimum: negate
+        ok, out = O.refine(-q, P)
+        assert ok and abs(out[0] - x0) < 1e-12 and abs(out[2] + a) < 1e-10
+
+
+def test_refine_rejections(P):
+    yy, xx = np.mgrid[-1:2, -1:2].astype(np.float64)
+    # offset beyond 0.5
+    q = 30 - (xx - 0.6) ** 2 - (yy) ** 2
+    assert not O.refine(q, P)[0]
+    # saddle
+    q = 30 - xx ** 2 + yy ** 2
+    assert not O.refine(q, P)[0]
+    # edge ratio: Hessian diag(-2a, -2b); (a+b)^2/(ab) = 12.1 exactly at a = 10 b
+    b = 0.5
+    q = 30 - 10 * b * xx ** 2 - b * yy ** 2
+    assert not O.refine(q, P)[0]          # ratio == 12.1 -> rejected
+    q = 30 - 9.99 * b * xx ** 2 - b * yy ** 2
+    assert O.refine(q, P)[0]
+    # refined response below T
+    q = 3.9 - 0.1 * xx ** 2 - 0.1 * yy ** 2
+    assert not O.refine(q, P)[0]
+
+
+# ---------------------------------------------- S1-S5 closed-form blob scale
+
+@pytest.mark.parametrize("b,octave", [(3.0, 0), (4.0, 1), (6.0, 1), (10.0, 2)])
+def test_blob_scale_closed_form(P, b, octave):
+    """A centred isotropic Gaussian blob of std b: the scale-normalised LoG at
+    its centre, -2 A b^2 t^2 / (b^2 + t^2)^2, is extremal at t = b.  The
+    detector finds a minimum at the centre pixel with sigma within 5% of b
+    (cubic fit and discretisation), in the octave whose range holds b."""
+    n = 161
+    c = 80
+    yy, xx = np.mgrid[0:n, 0:n].astype(np.float64)
+    img = 60.0 + 150.0 * np.exp(-((xx - c) ** 2 + (yy - c) ** 2) / (2 * b * b))
+    img = np.rint(img).astype(np.uint8)
+    kp, d, nc = O.extract(img, P)
+    assert kp.size >= 1
+    k = kp[np.argmax(np.abs(kp["response"]))]
+    assert k["type"] == -1 and k["response"] < 0
+    assert k["octave"] == octave
+    assert abs(k["x"] - c) < 1e-9 and abs(k["y"] - c) < 1e-9
+    assert abs(k["sigma"] / b - 1.0) < 0.05
+
+
+# ------------------------------------------------------- S6 decimation
+
+def test_decimation_identity_and_coordinates(P):
+    img = synth.blob_image(synth.image_seed(7, 0), 97, 75, n_blobs=20)
+    lv = O.scale_space(img, P)
+    dims = O.octave_dims(97, 75, P)
+    assert dims == [(97, 75), (49, 38), (25, 19), (13, 10)]
+    for o in range(1, len(lv)):
+        assert np.array_equal(lv[o][0], lv[o - 1][3][::2, ::2])
+    c = O.candidates(img, P)
+    for k in c:
+        s = 2.0 ** k["octave"]
+        assert k["x"] == k["xo"] * s and k["y"] == k["yo"] * s and k["sigma"] == k["so"] * s
+
+
+# ------------------------------------------------------- S7 dedupe
+
+def _kp(x, y, sigma, r, o):
+    k = np.zeros(1, O.KP_DTYPE)
+    k["x"], k["y"], k["sigma"], k["response"], k["octave"] = x, y, sigma, r, o
+    k["xo"], k["yo"], k["so"] = x / 2 ** o, y / 2 ** o, sigma / 2 ** o
+    return k
+
+
+def test_dedupe_rules(P):
+    c = np.concatenate([
+        _kp(100, 100, 3.2, -20, 0), _kp(101, 99, 3.3, -25, 1),     # pair: second wins
+        _kp(200, 50, 3.0, 30, 0), _kp(202, 52, 3.0, 30, 1),         # tie at the window edge: finer wins
+        _kp(300, 300, 3.0, 10, 0), _kp(300, 300, 3.0, 50, 0),       # same octave: never duplicates
+        _kp(400, 100, 3.0, 10, 0), _kp(400, 100, 12.0, 50, 2),      # octaves 0 and 2: not adjacent
+        _kp(500, 100, 3.0, 10, 0), _kp(500, 100, 3.0 * 2 ** (1 / 3) * 1.001, 50, 1),  # outside sigma window
+        _kp(600, 100, 6.0, 10, 1), _kp(604, 100, 6.0, 50, 2),       # |dx| = 4 = 2^2 inclusive -> dup
+        _kp(50, 400, 6.0, 10, 1), _kp(54.01, 400, 6.0, 50, 2),      # just outside the box
+    ])
+    keep = O.dedupe(c, P)
+    assert keep.tolist() == [False, True, True, False, True, True, True, True, True, True,
+                             False, True, True, True]
+    # permutation invariance of the decision
+    rng = np.random.default_rng(0)
+    perm = rng.permutation(c.size)
+    keep_p = O.dedupe(c[perm], P)
+    assert np.array_equal(keep_p, keep[perm])
+
+
+def test_dedupe_random_invariants(P):
+    rng = np.random.default_rng(9)
+    n = 400
+    c = np.zeros(n, O.KP_DTYPE)
+    c["octave"] = rng.integers(0, 4, n)
+    c["x"] = rng.uniform(0, 64, n)
+    c["y"] = rng.uniform(0, 64, n)
+    c["sigma"] = 1.6 * 2.0 ** (c["octave"] + rng.uniform(0, 1, n))
+    c["response"] = rng.normal(0, 20, n)
+    keep = O.dedupe(c, P)
+    # every removed point has a kept-or-removed adjacent-octave duplicate with larger |r|;
+    # the point of largest |r| in the set is never removed
+    assert keep[np.argmax(np.abs(c["response"]))]
+    # scaling all coordinates by 2 and shifting octaves by one keeps decisions
+    c2 = c.copy()
+    c2["x"] *= 2
+    c2["y"] *= 2
+    c2["sigma"] *= 2
+    c2["octave"] += 1
+    assert np.array_equal(O.dedupe(c2, P), keep)
+
+
+# ------------------------------------------------------- S8 selection
+
+def test_selection_order_and_cap():
+    P = O.params(max_keypoints=5)
+    c = np.concatenate([_kp(10, 5, 2, 7, 0), _kp(3, 5, 2, -7, 0), _kp(1, 9, 2, 9, 0),
+                        _kp(8, 1, 2, 7, 0), _kp(1, 1, 2, 1, 0), _kp(2, 2, 2, 100, 0),
+                        _kp(5, 5, 2, 0.5, 0)])
+    order = O.dedupe_select(c, P)
+    # |r| desc, then y asc, then x asc
+    assert order.tolist() == [5, 2, 3, 1, 0]
+
+
+# ------------------------------------------------- S9/S10 rotation invariance
+
+@pytest.fixture(scope="module")
+def rot_pair():
+    img = synth.blob_image(synth.image_seed(21, 0), 641, 481, n_blobs=120)
+    return img, np.ascontiguousarray(np.rot90(img))
+
+
+def _match_rot(kpa, kpb, W):
+    # (x, y) in A -> (y, W - 1 - x) in B
+    out = []
+    for i, k in enumerate(kpa):
+        xb, yb = k["y"], W - 1 - k["x"]
+        d = np.abs(kpb["x"] - xb) + np.abs(kpb["y"] - yb) + np.abs(kpb["sigma"] - k["sigma"])
+        j = int(np.argmin(d))
+        out.append((i, j, d[j]))
+    return out
+
+
+def test_rotation_90_oriented(rot_pair):
+    img, rot = rot_pair
+    P = O.params()
+    ka, da, _ = O.extract(img, P)
+    kb, db, _ = O.extract(rot, P)
+    assert ka.size == kb.size and ka.size > 200
+    W = img.shape[1]
+    for i, j, dist in _match_rot(ka, kb, W):
+        assert dist < 1e-9
+        dth = (ka["theta"][i] - math.pi / 2 - kb["theta"][j]) % (2 * math.pi)
+        dth = min(dth, 2 * math.pi - dth)
+        if dth > 1e-9:
+            # same point, another orientation copy
+            continue
+        assert np.max(np.abs(da[i] - db[j])) < 1e-9
+    # every record found its rotated twin with the same theta - pi/2
+    th_a = sorted((round(k["x"], 6), round(k["y"], 6), round((k["theta"] - math.pi / 2) % (2 * math.pi), 6))
+                  for k in ka)
+    th_b = sorted((round(W - 1 - k["y"], 6), round(k["x"], 6), round(k["theta"], 6)) for k in kb)
+    assert th_a == th_b
+
+
+def test_rotation_90_upright_permutes_bins(rot_pair):
+    img, rot = rot_pair
+    P = O.params(upright=1)
+    ka, da, _ = O.extract(img, P)
+    kb, db, _ = O.extract(rot, P)
+    W = img.shape[1]
+    # cell (cx, cy) of A goes to (cy, 3 - cx) of B; orientation bin b -> b - 2 (mod 8)
+    perm = np.zeros(128, int)
+    for cy in range(4):
+        for cx in range(4):
+            for b in range(8):
+                perm[(cy * 4 + cx) * 8 + b] = ((3 - cx) * 4 + cy) * 8 + (b - 2) % 8
+    for i, j, dist in _match_rot(ka, kb, W):
+        assert dist < 1e-9
+        assert np.max(np.abs(db[j][perm] - da[i])) < 1e-9
+        assert np.max(np.abs(da[i] - db[j])) > 1e-3   # really a permutation, not identity
+
+
+# ------------------------------------------------------- S9 orientation
+
+@pytest.mark.parametrize("phi_deg", [5.0, 101.0, 203.0, 333.0])
+def test_orientation_of_a_ramp(P, phi_deg):
+    phi = math.radians(phi_deg)
+    yy, xx = np.mgrid[0:60, 0:60].astype(np.float64)
+    G = 3.0 * (math.cos(phi) * xx + math.sin(phi) * yy)
+    th, hist = O.orientations(G, 30.2, 29.7, 2.0, P)
+    b = int(math.floor(36 * phi / (2 * math.pi))) % 36
+    assert np.count_nonzero(hist) == 1 and hist[b] > 0
+    assert th.size == 1 and abs(th[0] - 2 * math.pi * (b + 0.5) / 36) < 1e-12
+
+
+def test_orientation_peaks_rule(P):
+    """Two ramps in the two halves of a patch: two bins, both returned when the
+    weaker is above 0.8 of the stronger, ordered by value."""
+    yy, xx = np.mgrid[0:61, 0:61].astype(np.float64)
+    G = np.where(yy < 30, 3.0 * xx, 2.7 * yy + 3.0 * 30)   # gradient along x above, along y below
+    th, hist = O.orientations(G, 30, 30, 2.0, P)
+    assert th.size >= 1
+    vals = sorted(hist[hist > 0], reverse=True)
+    for t in th:
+        b = int(t * 36 / (2 * math.pi))
+        assert hist[b] > 0.8 * max(hist)
+
+
+# ------------------------------------------------------- S10 descriptor
+
+def test_descriptor_normalisation(P):
+    img = synth.blob_image(synth.image_seed(1, 0))
+    kp, d, _ = O.extract(img, P)
+    n = np.linalg.norm(d, axis=1)
+    assert np.allclose(n, 1.0, atol=1e-12)
+    assert np.all(d >= 0)
+    # after clamping at 0.2 and renormalising, no element exceeds 0.2 / ||clamped||
+    # and the descriptor of a flat patch is all zeros
+    flat = np.full((50, 50), 9.0)
+    assert np.all(O.descriptor(flat, 25, 25, 2.0, 0.3, P) == 0.0)
+
+
+def test_descriptor_of_a_ramp_uses_only_two_orientation_bins(P):
+    phi = math.radians(40.0)
+    yy, xx = np.mgrid[0:80, 0:80].astype(np.float64)
+    G = 2.0 * (math.cos(phi) * xx + math.sin(phi) * yy)
+    theta = 0.1
+    d = O.descriptor(G, 40, 40, 2.0, theta, P).reshape(16, 8)
+    ob = 8 * ((phi - theta) % (2 * math.pi)) / (2 * math.pi)
+    b0 = int(math.floor(ob))
+    used = np.nonzero(d.sum(axis=0))[0].tolist()
+    assert used == sorted([b0 % 8, (b0 + 1) % 8])
+    # trilinear split between the two bins in the ratio of the distances
+    # (clamping at 0.2 then renormalising keeps the ratio in every cell whose
+    # two values are both below the clamped maximum)
+    f = ob - b0
+    top = d.max()
+    n_cells = 0
+    for cell in d:
+        if cell.max() < top - 1e-12 and cell[b0 % 8] > 0:
+            assert cell[(b0 + 1) % 8] / cell[b0 % 8] == pytest.approx(f / (1 - f), rel=1e-9)
+            n_cells += 1
+    assert n_cells >= 4
+
+
+# ------------------------------------------------------- S11 transform + ternary
+
+def _golden_sets():
+    rows = [list(map(float, l.split())) for l in open(os.path.join(GOLDEN, "transform_sets.txt"))
+            if l.strip() and not l.startswith("#")]
+    M = np.array(rows)
+    return M[:8], M[8:]
+
+
+def test_transform_matches_printed_sets():
+    A, B = _golden_sets()
+    for cell in range(16):
+        cy, cx = divmod(cell, 4)
+        M = A if (cx + cy) % 2 == 0 else B
+        for j in range(8):
+            e = np.zeros(128)
+            e[cell * 8 + j] = 1.0
+            v = O.transform(e)
+            assert np.array_equal(v[cell * 8:cell * 8 + 8], M[:, j])
+            assert np.count_nonzero(v) == np.count_nonzero(M[:, j])
+
+
+def test_ternary_values_and_thresholds():
+    rng = np.random.default_rng(1)
+    v = rng.normal(size=128)
+    lo = np.full(128, -0.3)
+    hi = np.full(128, 0.3)
+    q = O.ternary(v, lo, hi)
+    assert set(np.unique(q)).issubset({-1, 0, 1})
+    assert np.array_equal(q, np.where(v < -0.3, -1, np.where(v > 0.3, 1, 0)))
