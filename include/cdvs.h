@@ -1,0 +1,232 @@
+/*
+ * cdvs.h -- C ABI of the GB300 (sm_103a) CDVS front end: interest point
+ * detection and local feature description of the MPEG-CDVS encoder as
+ * moved to the GPU in "Fast MPEG-CDVS Encoder with GPU-CPU Hybrid Computing"
+ * (arXiv 1705.09776), Sec. IV-A (Alg. 1) and Sec. IV-B (Alg. 2), plus the
+ * feature selection of Sec. III-B (Eq. 5) and the host-side descriptor
+ * transform and ternary quantisation of Sec. III-C.
+ *
+ * Conventions
+ *   - Images are 8-bit grey, row-major, `pitch_bytes` between rows.
+ *   - Coordinates: pixel centres at integer positions, origin at the centre
+ *     of the top-left pixel, x to the right, y down.  "Image px" are input
+ *     pixels; pixel i of octave o sits on image pixel 2^o * i ("octave px").
+ *   - Angles are radians in [0, 2 pi), measured from +x towards +y.
+ *   - Every call is asynchronous on `cuda_stream` (a cudaStream_t, NULL for
+ *     the legacy default stream) unless it reads results back to host memory,
+ *     in which case it returns after they are in place.
+ *   - No exception crosses this boundary.  Every call returns a cdvs_status;
+ *     on anything but CDVS_OK / CDVS_CAPACITY_TRUNCATED the outputs are
+ *     unspecified and cdvs_last_error() describes the failure.
+ *   - Ownership: the caller owns every input and output buffer (host or
+ *     device, as `flags` says) and the library never frees them.  The
+ *     context owns its device workspace and grows it on demand.  Calls on one
+ *     context must not overlap (one context per host thread); distinct
+ *     contexts are independent.
+ */
+#ifndef CDVS_H
+#define CDVS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CDVS_OK = 0,
+    CDVS_INVALID_ARGUMENT = 1,   /* null pointer, bad count, parameter out of range */
+    CDVS_UNSUPPORTED_SIZE = 2,   /* image side < 16 px or > 32768 px */
+    CDVS_OUT_OF_MEMORY = 3,      /* device or pinned host allocation failed */
+    CDVS_CAPACITY_TRUNCATED = 4, /* an output or internal queue was full; results truncated */
+    CDVS_DEVICE_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    CDVS_CUDA_ERROR = 6          /* a CUDA runtime call failed (message in cdvs_last_error) */
+} cdvs_status;
+
+/* flags */
+#define CDVS_INPUT_DEVICE 0x1u   /* image pointers (and point lists) are device memory */
+#define CDVS_OUTPUT_DEVICE 0x2u  /* output buffers are device memory */
+
+/* Level storage types (cdvs_params.storage). */
+#define CDVS_STORAGE_FP32 0
+#define CDVS_STORAGE_FP16 1
+
+typedef struct cdvs_ctx cdvs_ctx;
+
+/* Parameters of the method.  cdvs_params_default() fills the values below;
+ * the paper fixes 3.96, 0.8, 6 and 3 (Sec. IV-B) and about 300 features
+ * (Sec. III-B); the rest are this library's readings where the paper is
+ * silent. */
+typedef struct {
+    int32_t num_octaves;       /* octaves processed at most (4); an octave needs both sides >= 3 */
+    int32_t scales_per_octave; /* K LoG scales per octave fitted by the cubic of Eq. 2 (4; only 4) */
+    float sigma0;              /* scale of level 0 of each octave, octave px (1.6) */
+    float sigma_in;            /* blur assumed present in the input (0.5) */
+    float contrast_T;          /* threshold on |p| at sigma* and after refinement (4.0, grey levels) */
+    float edge_r;              /* Hessian edge ratio r: reject tr^2/det >= (r+1)^2/r (10) */
+    float offset_max;          /* reject refined offsets above this, octave px (0.5) */
+    float ori_radius;          /* orientation disc radius in sigma (3.96) */
+    float ori_peak_ratio;      /* keep histogram peaks above this fraction of the max (0.8) */
+    float ori_weight_sigma;    /* orientation Gaussian weight std in sigma (1.5) */
+    float desc_radius;         /* description disc radius in sigma (6.0) */
+    float cell_side;           /* descriptor cell side in sigma (3.0) */
+    float desc_weight_sigma;   /* descriptor Gaussian weight std in cells (2.0) */
+    float dedupe_dlog2;        /* cross-octave duplicate window on |log2 sigma ratio| (1/3) */
+    int32_t max_keypoints;     /* N points kept by selection, 1..2048 (300) */
+    int32_t max_orientations;  /* orientation copies per point, 1..8 (4) */
+    int32_t upright;           /* 1: theta = 0 and no orientation stage (0) */
+    int32_t storage;           /* CDVS_STORAGE_FP32 or CDVS_STORAGE_FP16 level storage (FP32) */
+} cdvs_params;
+
+typedef struct {
+    int32_t width, height;  /* pixels */
+    int32_t pitch_bytes;    /* bytes between rows, >= width */
+} cdvs_image_desc;
+
+/* One interest point, or one (point, orientation) output record.  44 bytes. */
+typedef struct {
+    float x, y, sigma;      /* image px */
+    float theta;            /* orientation, radians (0 for candidates and in upright mode) */
+    float response;         /* refined scale-normalised LoG response p-hat (Alg. 1 stage B) */
+    float p_ss;             /* d2p/dsigma2 at sigma*, octave px units (Eq. 5 input) */
+    float ratio;            /* Hessian tr^2/det (Eq. 5 input) */
+    int16_t octave;         /* octave o */
+    int16_t scale_idx;      /* Gaussian level used for description */
+    int16_t type;           /* +1 maximum, -1 minimum */
+    int16_t reserved;
+    int32_t image;          /* index of the image in the call */
+    int32_t parent_id;      /* rank of the selected point (descriptor records) */
+} cdvs_keypoint;
+
+/* Fills *p with the defaults listed above. */
+void cdvs_params_default(cdvs_params *p);
+
+/* Creates a context on CUDA device `device`.  `workspace_bytes_hint` (may be
+ * 0) pre-allocates that much device workspace.  Returns CDVS_OK and *out, or
+ * an error (then *out is NULL). */
+cdvs_status cdvs_create(cdvs_ctx **out, int device, size_t workspace_bytes_hint);
+
+/* Destroys a context and frees its workspace.  NULL is a no-op. */
+void cdvs_destroy(cdvs_ctx *ctx);
+
+/* Message of the last failed call on ctx ("" if none).  Valid until the next
+ * call on ctx. */
+const char *cdvs_last_error(const cdvs_ctx *ctx);
+
+/*
+ * cdvs_extract -- the whole front end on a batch: Gaussian scale space
+ * (Eq. 1, Alg. 1 stage A), LoG and ALP cubic-in-scale extremum detection
+ * (Eq. 2-3), refinement (Alg. 1 stage B), cross-octave duplicate removal
+ * (Alg. 1 stage C), selection of the N best points (Eq. 5, |p-hat| standing in
+ * for the normative relevance tables), dominant orientations (Alg. 2 stage A)
+ * and 128-D descriptors (Alg. 2 stage B).
+ *
+ *   images[i]      pointer to image i (host, or device with CDVS_INPUT_DEVICE)
+ *   sizes[i]       its width, height and pitch (host memory)
+ *   kp_out         kp_capacity records, packed over the batch: the records of
+ *                  image i follow those of image i-1, each image's in rank order
+ *                  then orientation order (peak value descending)
+ *   desc_out       kp_capacity * 128 floats, descriptor j belongs to record j:
+ *                  cells row-major (y, x) in the rotated frame, 8 orientation
+ *                  bins fastest; unit L2 norm
+ *   kp_count[i]    records written for image i (host, or device with
+ *                  CDVS_OUTPUT_DEVICE)
+ * Returns CDVS_CAPACITY_TRUNCATED if kp_capacity was too small (records are
+ * dropped from the end of the batch) or an image had more candidates than the
+ * internal queue holds.
+ */
+cdvs_status cdvs_extract(cdvs_ctx *ctx, int32_t n_images, const uint8_t *const *images,
+                         const cdvs_image_desc *sizes, const cdvs_params *params,
+                         cdvs_keypoint *kp_out, float *desc_out, int32_t kp_capacity,
+                         int32_t *kp_count, uint32_t flags, void *cuda_stream);
+
+/*
+ * cdvs_candidates -- Alg. 1 stages A and B only: every refined candidate of
+ * every octave, before the cross-octave check and selection, packed over the
+ * batch (per image in no particular order).  theta = 0, parent_id = -1.
+ */
+cdvs_status cdvs_candidates(cdvs_ctx *ctx, int32_t n_images, const uint8_t *const *images,
+                            const cdvs_image_desc *sizes, const cdvs_params *params,
+                            cdvs_keypoint *cand_out, int32_t cand_capacity, int32_t *cand_count,
+                            uint32_t flags, void *cuda_stream);
+
+/*
+ * cdvs_dedupe_select -- Alg. 1 stage C and the selection of Eq. 5 on given
+ * candidates: cand[i * cand_stride + j], j < cand_count[i], are image i's
+ * candidates (fields x, y, sigma, response, octave used; octave px positions
+ * are x / 2^octave).  Writes the selected points in rank order, packed over
+ * the batch, with parent_id = rank.  Host buffers unless the flags say device.
+ */
+cdvs_status cdvs_dedupe_select(cdvs_ctx *ctx, int32_t n_images, const cdvs_image_desc *sizes,
+                               const cdvs_keypoint *cand, const int32_t *cand_count,
+                               int32_t cand_stride, const cdvs_params *params,
+                               cdvs_keypoint *sel_out, int32_t sel_capacity, int32_t *sel_count,
+                               uint32_t flags, void *cuda_stream);
+
+/*
+ * cdvs_describe -- Alg. 2 on given points: builds each image's scale space,
+ * then orientations and descriptors of pts[i * pts_stride + j], j < n_pts[i]
+ * (fields x, y, sigma, octave used).  Output as cdvs_extract; parent_id is j.
+ */
+cdvs_status cdvs_describe(cdvs_ctx *ctx, int32_t n_images, const uint8_t *const *images,
+                          const cdvs_image_desc *sizes, const cdvs_params *params,
+                          const cdvs_keypoint *pts, const int32_t *n_pts, int32_t pts_stride,
+                          cdvs_keypoint *kp_out, float *desc_out, int32_t kp_capacity,
+                          int32_t *kp_count, uint32_t flags, void *cuda_stream);
+
+/*
+ * cdvs_scale_space -- the Gaussian levels G_{o,k} of one image (Eq. 1,
+ * Alg. 1 stage A, octave downsampling of Alg. 1), as FP32 MINUS 128 (the
+ * library filters the input shifted by -128, which keeps FP32 rounding small;
+ * the shift cancels in every difference).  Levels are written octave-major,
+ * then level, then row-major without padding: level (o, k) has W_o x H_o
+ * values, W_{o+1} = ceil(W_o / 2).  `capacity` is in floats; `*n_octaves`
+ * gets the number of octaves.  Host buffer unless CDVS_OUTPUT_DEVICE.
+ */
+cdvs_status cdvs_scale_space(cdvs_ctx *ctx, const uint8_t *image, const cdvs_image_desc *size,
+                             const cdvs_params *params, float *levels_out, size_t capacity,
+                             int32_t *n_octaves, uint32_t flags, void *cuda_stream);
+
+/*
+ * Measurement hooks (no counterpart in the paper; they only time it).
+ * cdvs_profile(ctx, 1) makes every later call on ctx record CUDA events on
+ * its stream around each kernel stage; cdvs_profile_read() waits for the
+ * recorded events, adds each stage's elapsed device time (ms) and launch
+ * count to ms[s] / launches[s] for stage s in
+ *   0 detect (one launch per octave), 1 dedupe + select, 2 orientation,
+ *   3 record packing, 4 descriptors,
+ * and clears the record when `reset` is nonzero.  Returns the number of
+ * stages (5) or -1 on error.
+ */
+#define CDVS_N_STAGES 5
+cdvs_status cdvs_profile(cdvs_ctx *ctx, int32_t enable);
+int32_t cdvs_profile_read(cdvs_ctx *ctx, double *ms, int32_t *launches, int32_t max_stages,
+                          int32_t reset);
+
+/*
+ * cdvs_rank_host -- the selection order of Eq. 5 on the host (pure CPU,
+ * deterministic): indices of the n points sorted by |response| descending,
+ * then y, x, sigma, octave ascending; at most max_keypoints written to
+ * `order`.  Returns the number written.  This is the same total order the
+ * device selection uses, for re-ranking records on the host.
+ */
+int32_t cdvs_rank_host(const cdvs_keypoint *pts, int32_t n, int32_t max_keypoints,
+                       int32_t *order);
+
+/*
+ * cdvs_transform_ternary -- Sec. III-C on the host (pure CPU, FP64
+ * arithmetic): each of the 16 cell histograms h0..h7 of a descriptor goes
+ * through one of two order-8 add/subtract/shift transforms (set A for cells
+ * with cx + cy even, set B otherwise), and each transformed value v_j becomes
+ * -1 if v_j < t_lo[j], +1 if v_j > t_hi[j], else 0.  desc: n x 128 floats;
+ * t_lo, t_hi: 128 thresholds each; out: n x 128 int8.  v_out (may be NULL)
+ * receives the transformed values as n x 128 doubles.
+ */
+cdvs_status cdvs_transform_ternary(const float *desc, int32_t n, const double *t_lo,
+                                   const double *t_hi, int8_t *out, double *v_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CDVS_H */

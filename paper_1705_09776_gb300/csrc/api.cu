@@ -1,0 +1,873 @@
+// api.cu -- the C ABI of include/cdvs.h: context, parameter checks, batch
+// planning (octave sizes, level arena layout, tile lists), workspace, host <->
+// device staging, and the launch sequence
+//   K1 detect (one launch per octave, all images)
+//   K3+K10 cross-octave check + selection (one CTA per image)
+//   K5 orientation, packing scan, K6 descriptors
+// Every step of the method runs in the kernels; this file only moves bytes.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cdvs_internal.cuh"
+
+using namespace cdvs;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct HostBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct ProfRec {
+  int stage, launches;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct cdvs_ctx {
+  int device = 0;
+  int n_sms = 0;
+  std::string err;
+  DevBuf levels, cands, cand_count, order, keep, sel, sel_count, ori_theta, ori_count, rec_map,
+      rec_total, out_kp, out_desc, out_count, plans, tile_prefix, status, input, dump;
+  HostBuf small;  // pinned: status word + record total
+  std::vector<ImgPlan> h_plans;
+  std::vector<int> h_prefix;
+  bool prof = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+};
+
+namespace {
+
+enum Mode { kExtract, kCandidates, kDescribe, kScaleSpace };
+
+cdvs_status fail(cdvs_ctx* c, cdvs_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+cdvs_status cuda_fail(cdvs_ctx* c, cudaError_t e, const char* what) {
+  if (c) c->err = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? CDVS_OUT_OF_MEMORY : CDVS_CUDA_ERROR;
+}
+
+cudaEvent_t take_event(cdvs_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Stage timing: an event before the stage's launches and one after them, on
+// the stream the kernels run on.
+cudaEvent_t prof_begin(cdvs_ctx* c, cudaStream_t s) {
+  if (!c->prof) return nullptr;
+  cudaEvent_t e = take_event(c);
+  if (e) cudaEventRecord(e, s);
+  return e;
+}
+
+void prof_end(cdvs_ctx* c, int stage, int launches, cudaEvent_t a, cudaStream_t s) {
+  if (!c->prof || !a) return;
+  cudaEvent_t b = take_event(c);
+  if (!b) return;
+  cudaEventRecord(b, s);
+  c->recs.push_back(ProfRec{stage, launches, a, b});
+}
+
+cudaError_t ensure(DevBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (bytes <= b.bytes) return cudaSuccess;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  const size_t nb = bytes + bytes / 4;
+  cudaError_t e = cudaMalloc(&b.p, nb);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e;
+  }
+  b.bytes = nb;
+  return cudaSuccess;
+}
+
+cudaError_t ensure_host(HostBuf& b, size_t bytes) {
+  if (bytes <= b.bytes) return cudaSuccess;
+  if (b.p) cudaFreeHost(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  cudaError_t e = cudaMallocHost(&b.p, bytes);
+  if (e != cudaSuccess) return e;
+  b.bytes = bytes;
+  return cudaSuccess;
+}
+
+// ---- method constants computed on the host (double), passed to the kernels
+
+double scale_k(const cdvs_params& p, int k) {
+  return (double)p.sigma0 * std::pow(2.0, (double)k / (double)(p.scales_per_octave - 1));
+}
+
+// Blur added to the octave base to reach s_k: the input carries sigma_in,
+// a decimated base carries sigma0 (in its own pixels).
+double tau_of(const cdvs_params& p, int octave, int k) {
+  const double s = scale_k(p, k);
+  const double b = octave == 0 ? (double)p.sigma_in : (double)p.sigma0;
+  const double v = s * s - b * b;
+  return v > 0.0 ? std::sqrt(v) : 0.0;
+}
+
+// One side (index 0..r) of the sampled Gaussian on [-r, r], r = ceil(4 tau),
+// normalised to unit sum.
+int gauss_taps(double tau, float* one_side) {
+  if (tau <= 0.0) {
+    one_side[0] = 1.0f;
+    return 0;
+  }
+  const int r = (int)std::ceil(4.0 * tau);
+  if (r > kMaxRadius) return -1;
+  double w[kMaxRadius + 1], sum = 0.0;
+  for (int j = 0; j <= r; ++j) {
+    w[j] = std::exp(-(double)(j * j) / (2.0 * tau * tau));
+    sum += j == 0 ? w[j] : 2.0 * w[j];
+  }
+  for (int j = 0; j <= r; ++j) one_side[j] = (float)(w[j] / sum);
+  return r;
+}
+
+// Cubic through the K = 4 samples (s_k, L_k) in the centred variable
+// t = sigma - tc: a = Vc^-1 L with Vc[k][i] = (s_k - tc)^i (Eq. 2-3 with the
+// interpolating beta; centring only improves FP32 conditioning).
+bool centred_fit(const cdvs_params& p, float B[4][kScales], float& tc, float& tlo, float& thi) {
+  const int K = kScales;
+  double s[kScales];
+  for (int k = 0; k < K; ++k) s[k] = scale_k(p, k);
+  const double c = 0.5 * (s[0] + s[K - 1]);
+  double A[4][8];
+  for (int k = 0; k < K; ++k) {
+    double v = 1.0;
+    for (int i = 0; i < 4; ++i) {
+      A[k][i] = v;
+      v *= s[k] - c;
+    }
+    for (int j = 0; j < 4; ++j) A[k][4 + j] = k == j ? 1.0 : 0.0;
+  }
+  for (int col = 0; col < 4; ++col) {
+    int piv = col;
+    for (int i = col + 1; i < 4; ++i)
+      if (std::fabs(A[i][col]) > std::fabs(A[piv][col])) piv = i;
+    if (A[piv][col] == 0.0) return false;
+    for (int j = 0; j < 8; ++j) std::swap(A[col][j], A[piv][j]);
+    const double d = A[col][col];
+    for (int j = 0; j < 8; ++j) A[col][j] /= d;
+    for (int i = 0; i < 4; ++i) {
+      if (i == col) continue;
+      const double f = A[i][col];
+      for (int j = 0; j < 8; ++j) A[i][j] -= f * A[col][j];
+    }
+  }
+  // A[:, 4:] = Vc^-1: a_i = sum_k Vc^-1[i][k] L_k
+  for (int i = 0; i < 4; ++i)
+    for (int k = 0; k < K; ++k) B[i][k] = (float)A[i][4 + k];
+  tc = (float)c;
+  tlo = (float)(s[0] - c);
+  thi = (float)(s[K - 1] - c);
+  return true;
+}
+
+cdvs_status check_params(cdvs_ctx* c, const cdvs_params* p) {
+  if (!p) return fail(c, CDVS_INVALID_ARGUMENT, "params is NULL");
+  if (p->scales_per_octave != kScales) return fail(c, CDVS_INVALID_ARGUMENT, "scales_per_octave must be 4");
+  if (p->num_octaves < 1 || p->num_octaves > kMaxOctaves)
+    return fail(c, CDVS_INVALID_ARGUMENT, "num_octaves must be in 1..12");
+  if (!(p->sigma0 > 0.0f) || !(p->sigma_in >= 0.0f) || !(p->sigma_in <= p->sigma0))
+    return fail(c, CDVS_INVALID_ARGUMENT, "need 0 <= sigma_in <= sigma0, sigma0 > 0");
+  if (!(p->contrast_T >= 0.0f) || !(p->edge_r > 0.0f) || !(p->offset_max > 0.0f))
+    return fail(c, CDVS_INVALID_ARGUMENT, "contrast_T >= 0, edge_r > 0, offset_max > 0 required");
+  if (!(p->ori_radius > 0.0f) || !(p->ori_weight_sigma > 0.0f) || !(p->desc_radius > 0.0f) ||
+      !(p->cell_side > 0.0f) || !(p->desc_weight_sigma > 0.0f) || !(p->ori_peak_ratio >= 0.0f) ||
+      !(p->dedupe_dlog2 >= 0.0f))
+    return fail(c, CDVS_INVALID_ARGUMENT, "description radii, weights and ratios must be positive");
+  if (p->max_keypoints < 1 || p->max_keypoints > kMaxSelect)
+    return fail(c, CDVS_INVALID_ARGUMENT, "max_keypoints must be in 1..2048");
+  if (p->max_orientations < 1 || p->max_orientations > kMaxOri)
+    return fail(c, CDVS_INVALID_ARGUMENT, "max_orientations must be in 1..8");
+  if (p->storage != CDVS_STORAGE_FP32 && p->storage != CDVS_STORAGE_FP16)
+    return fail(c, CDVS_INVALID_ARGUMENT, "storage must be CDVS_STORAGE_FP32 or CDVS_STORAGE_FP16");
+  float t[kMaxRadius + 1];
+  for (int o = 0; o < 2; ++o)
+    for (int k = 0; k < kScales; ++k)
+      if (gauss_taps(tau_of(*p, o, k), t) < 0)
+        return fail(c, CDVS_INVALID_ARGUMENT, "a level filter radius exceeds 24 (sigma0 too large)");
+  return CDVS_OK;
+}
+
+size_t elem_size(int storage) { return storage == CDVS_STORAGE_FP16 ? 2 : 4; }
+
+// Octave sizes, level arena layout and tile lists of a batch.
+cdvs_status plan_batch(cdvs_ctx* c, int n, const cdvs_image_desc* sizes, const cdvs_params& p,
+                       long long& level_elems, int& max_oct, long long& max_pixels) {
+  c->h_plans.assign(n, ImgPlan{});
+  level_elems = 0;
+  max_oct = 0;
+  max_pixels = 0;
+  for (int i = 0; i < n; ++i) {
+    const cdvs_image_desc& d = sizes[i];
+    if (d.width < 16 || d.height < 16 || d.width > 32768 || d.height > 32768)
+      return fail(c, CDVS_UNSUPPORTED_SIZE, "image " + std::to_string(i) + ": sides must be in 16..32768");
+    if (d.pitch_bytes < d.width) return fail(c, CDVS_INVALID_ARGUMENT, "pitch_bytes < width");
+    ImgPlan& P = c->h_plans[i];
+    P.W = d.width;
+    P.H = d.height;
+    P.pitch = d.pitch_bytes;
+    int w = d.width, h = d.height, no = 0;
+    for (int o = 0; o < p.num_octaves; ++o) {
+      if (w < 3 || h < 3) break;
+      OctPlan& op = P.oct[o];
+      op.W = w;
+      op.H = h;
+      op.lpitch = (w + 7) & ~7;
+      op.tiles_x = (w + kTX - 1) / kTX;
+      op.tiles_y = (h + kTY - 1) / kTY;
+      op.level_off = level_elems;
+      level_elems += ((long long)kScales * op.lpitch * h + 63) & ~63LL;
+      ++no;
+      w = (w + 1) / 2;
+      h = (h + 1) / 2;
+    }
+    P.n_oct = no;
+    max_oct = std::max(max_oct, no);
+    max_pixels = std::max(max_pixels, (long long)d.width * d.height);
+  }
+  c->h_prefix.assign((size_t)kMaxOctaves * (n + 1), 0);
+  for (int o = 0; o < max_oct; ++o) {
+    int* pre = c->h_prefix.data() + (size_t)o * (n + 1);
+    pre[0] = 0;
+    for (int i = 0; i < n; ++i) {
+      const ImgPlan& P = c->h_plans[i];
+      const int t = o < P.n_oct ? P.oct[o].tiles_x * P.oct[o].tiles_y : 0;
+      pre[i + 1] = pre[i] + t;
+    }
+  }
+  return CDVS_OK;
+}
+
+int cand_capacity(long long max_pixels) {
+  long long cap = std::max(4096LL, (max_pixels / 16 + 1023) & ~1023LL);
+  return (int)std::min(cap, 1LL << 22);
+}
+
+// Uploads images (if on the host) and the plans; returns the plan of image i
+// pointing at device memory.
+cdvs_status stage_inputs(cdvs_ctx* c, int n, const uint8_t* const* images, const cdvs_image_desc* sizes,
+                         uint32_t flags, cudaStream_t s) {
+  cudaError_t e;
+  if (flags & CDVS_INPUT_DEVICE) {
+    for (int i = 0; i < n; ++i) c->h_plans[i].src = images[i];
+  } else {
+    size_t total = 0;
+    std::vector<size_t> off(n);
+    for (int i = 0; i < n; ++i) {
+      off[i] = total;
+      total += (size_t)sizes[i].pitch_bytes * sizes[i].height;
+      total = (total + 255) & ~(size_t)255;
+    }
+    if ((e = ensure(c->input, total)) != cudaSuccess) return cuda_fail(c, e, "input staging");
+    uint8_t* base = static_cast<uint8_t*>(c->input.p);
+    // one copy when the host images are back to back with equal size
+    bool contiguous = n > 0;
+    const size_t isz = n > 0 ? (size_t)sizes[0].pitch_bytes * sizes[0].height : 0;
+    for (int i = 1; i < n && contiguous; ++i)
+      contiguous = sizes[i].width == sizes[0].width && sizes[i].height == sizes[0].height &&
+                   sizes[i].pitch_bytes == sizes[0].pitch_bytes && images[i] == images[0] + i * isz &&
+                   (isz & 255) == 0;
+    if (contiguous) {
+      if ((e = cudaMemcpyAsync(base, images[0], isz * n, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_fail(c, e, "image upload");
+    } else {
+      for (int i = 0; i < n; ++i) {
+        const size_t bytes = (size_t)sizes[i].pitch_bytes * sizes[i].height;
+        if ((e = cudaMemcpyAsync(base + off[i], images[i], bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+          return cuda_fail(c, e, "image upload");
+      }
+    }
+    for (int i = 0; i < n; ++i) c->h_plans[i].src = base + (contiguous ? i * isz : off[i]);
+  }
+  if ((e = ensure(c->plans, sizeof(ImgPlan) * n)) != cudaSuccess) return cuda_fail(c, e, "plans");
+  if ((e = ensure(c->tile_prefix, sizeof(int) * c->h_prefix.size())) != cudaSuccess)
+    return cuda_fail(c, e, "tile lists");
+  if ((e = cudaMemcpyAsync(c->plans.p, c->h_plans.data(), sizeof(ImgPlan) * n, cudaMemcpyHostToDevice, s)) !=
+      cudaSuccess)
+    return cuda_fail(c, e, "plan upload");
+  if ((e = cudaMemcpyAsync(c->tile_prefix.p, c->h_prefix.data(), sizeof(int) * c->h_prefix.size(),
+                           cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_fail(c, e, "tile list upload");
+  return CDVS_OK;
+}
+
+cdvs_status run_detect(cdvs_ctx* c, int n, const cdvs_params& p, int max_oct, int cap, cudaStream_t s) {
+  cudaError_t e;
+  DetectArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.plans = static_cast<const ImgPlan*>(c->plans.p);
+  a.n_images = n;
+  a.levels = c->levels.p;
+  a.cands = static_cast<Cand*>(c->cands.p);
+  a.cand_count = static_cast<int*>(c->cand_count.p);
+  a.cand_cap = cap;
+  a.status = static_cast<int*>(c->status.p);
+  for (int k = 0; k < kScales; ++k) {
+    const double sk = scale_k(p, k);
+    a.s2[k] = (float)(sk * sk);
+  }
+  if (!centred_fit(p, a.B, a.tc, a.t_lo, a.t_hi)) return fail(c, CDVS_INVALID_ARGUMENT, "degenerate scales");
+  a.T = p.contrast_T;
+  a.edge_lim = (float)(((double)p.edge_r + 1.0) * ((double)p.edge_r + 1.0) / (double)p.edge_r);
+  a.offset_max = p.offset_max;
+  for (int o = 0; o < max_oct; ++o) {
+    a.octave = o;
+    a.tile_prefix = static_cast<const int*>(c->tile_prefix.p) + (size_t)o * (n + 1);
+    a.write_level0 = o == 0 ? 1 : 0;
+    int maxr = 0;
+    for (int k = 0; k < kScales; ++k) {
+      a.radius[k] = gauss_taps(tau_of(p, o, k), a.taps[k]);
+      maxr = std::max(maxr, a.radius[k]);
+    }
+    const int n_tiles = c->h_prefix[(size_t)o * (n + 1) + n];
+    if ((e = launch_detect(a, n_tiles, maxr, p.storage, s)) != cudaSuccess) return cuda_fail(c, e, "detect launch");
+  }
+  return CDVS_OK;
+}
+
+DescribeArgs describe_args(cdvs_ctx* c, int n, const cdvs_params& p) {
+  DescribeArgs d;
+  std::memset(&d, 0, sizeof(d));
+  d.plans = static_cast<const ImgPlan*>(c->plans.p);
+  d.levels = c->levels.p;
+  d.sel = static_cast<const Cand*>(c->sel.p);
+  d.sel_count = static_cast<const int*>(c->sel_count.p);
+  d.N = p.max_keypoints;
+  d.n_images = n;
+  d.ori_theta = static_cast<float*>(c->ori_theta.p);
+  d.ori_count = static_cast<int*>(c->ori_count.p);
+  d.rec_map = static_cast<int*>(c->rec_map.p);
+  d.rec_total = static_cast<int*>(c->rec_total.p);
+  d.status = static_cast<int*>(c->status.p);
+  d.sigma0 = p.sigma0;
+  d.upright = p.upright;
+  d.max_ori = p.max_orientations;
+  d.ori_radius = p.ori_radius;
+  d.ori_ratio = p.ori_peak_ratio;
+  d.ori_wsig = p.ori_weight_sigma;
+  d.desc_radius = p.desc_radius;
+  d.cell_side = p.cell_side;
+  d.desc_wsig = p.desc_weight_sigma;
+  return d;
+}
+
+cdvs_status map_status(cdvs_ctx* c, int st) {
+  if (st & (kStatusCandOverflow | kStatusSelectOverflow | kStatusOutTruncated)) {
+    std::string m;
+    if (st & kStatusCandOverflow) m += "candidate queue full; ";
+    if (st & kStatusSelectOverflow) m += "selection tie list full; ";
+    if (st & kStatusOutTruncated) m += "output capacity reached; ";
+    c->err = m;
+    return CDVS_CAPACITY_TRUNCATED;
+  }
+  c->err.clear();
+  return CDVS_OK;
+}
+
+struct PointsIn {
+  const cdvs_keypoint* pts;
+  const int32_t* counts;
+  int32_t stride;
+};
+
+// The shared pipeline behind cdvs_extract / cdvs_candidates / cdvs_describe.
+cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, const cdvs_image_desc* sizes,
+                const cdvs_params* params, const PointsIn* pin, cdvs_keypoint* kp_out, float* desc_out,
+                int32_t capacity, int32_t* kp_count, uint32_t flags, cudaStream_t s) {
+  if (!c) return CDVS_INVALID_ARGUMENT;
+  cdvs_status st = check_params(c, params);
+  if (st != CDVS_OK) return st;
+  const cdvs_params& p = *params;
+  if (n < 0) return fail(c, CDVS_INVALID_ARGUMENT, "n_images < 0");
+  if (n == 0) {
+    c->err.clear();
+    return CDVS_OK;
+  }
+  if (!images || !sizes) return fail(c, CDVS_INVALID_ARGUMENT, "images or sizes is NULL");
+  for (int i = 0; i < n; ++i)
+    if (!images[i]) return fail(c, CDVS_INVALID_ARGUMENT, "image pointer is NULL");
+  if (mode != kScaleSpace && (!kp_out || !kp_count || capacity < 0 || (mode != kCandidates && !desc_out)))
+    return fail(c, CDVS_INVALID_ARGUMENT, "output pointer is NULL or capacity < 0");
+  if (mode == kCandidates && (flags & CDVS_OUTPUT_DEVICE))
+    return fail(c, CDVS_INVALID_ARGUMENT, "cdvs_candidates writes host memory only");
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+
+  long long level_elems, max_pixels;
+  int max_oct;
+  if ((st = plan_batch(c, n, sizes, p, level_elems, max_oct, max_pixels)) != CDVS_OK) return st;
+  const int cap = cand_capacity(max_pixels);
+  const int N = p.max_keypoints;
+  const size_t slots = (size_t)n * N;
+  if ((e = ensure(c->levels, (size_t)level_elems * elem_size(p.storage))) != cudaSuccess ||
+      (e = ensure(c->cands, sizeof(Cand) * (size_t)n * cap)) != cudaSuccess ||
+      (e = ensure(c->cand_count, sizeof(int) * n)) != cudaSuccess ||
+      (e = ensure(c->order, sizeof(int) * (size_t)n * cap)) != cudaSuccess ||
+      (e = ensure(c->keep, (size_t)n * cap)) != cudaSuccess ||
+      (e = ensure(c->sel, sizeof(Cand) * slots)) != cudaSuccess ||
+      (e = ensure(c->sel_count, sizeof(int) * n)) != cudaSuccess ||
+      (e = ensure(c->ori_theta, sizeof(float) * slots * kMaxOri)) != cudaSuccess ||
+      (e = ensure(c->ori_count, sizeof(int) * slots)) != cudaSuccess ||
+      (e = ensure(c->rec_map, sizeof(int) * ((size_t)capacity + slots + 1))) != cudaSuccess ||
+      (e = ensure(c->rec_total, sizeof(int) * 4)) != cudaSuccess ||
+      (e = ensure(c->status, sizeof(int) * 4)) != cudaSuccess ||
+      (e = ensure_host(c->small, sizeof(int) * 4)) != cudaSuccess)
+    return cuda_fail(c, e, "workspace");
+
+  if ((st = stage_inputs(c, n, images, sizes, flags, s)) != CDVS_OK) return st;
+  if ((e = cudaMemsetAsync(c->cand_count.p, 0, sizeof(int) * n, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->status.p, 0, sizeof(int) * 4, s)) != cudaSuccess)
+    return cuda_fail(c, e, "memset");
+  cudaEvent_t ev = prof_begin(c, s);
+  if ((st = run_detect(c, n, p, max_oct, cap, s)) != CDVS_OK) return st;
+  prof_end(c, 0, max_oct, ev, s);
+  int* h_small = static_cast<int*>(c->small.p);
+
+  if (mode == kScaleSpace) {
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "scale space");
+    return CDVS_OK;  // the caller copies the levels out
+  }
+
+  if (mode == kCandidates) {
+    std::vector<int> counts(n);
+    if ((e = cudaMemcpyAsync(counts.data(), c->cand_count.p, sizeof(int) * n, cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(h_small, c->status.p, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+      return cuda_fail(c, e, "candidate readback");
+    int status_bits = h_small[0];
+    int written = 0;
+    std::vector<Cand> tmp;
+    for (int i = 0; i < n; ++i) {
+      int m = std::min(counts[i], cap);
+      const int room = std::max(0, capacity - written);
+      if (m > room) {
+        m = room;
+        status_bits |= kStatusOutTruncated;
+      }
+      tmp.resize(m);
+      if (m > 0 &&
+          (e = cudaMemcpy(tmp.data(), static_cast<Cand*>(c->cands.p) + (size_t)i * cap, sizeof(Cand) * m,
+                          cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(c, e, "candidate readback");
+      for (int j = 0; j < m; ++j) {
+        const Cand& q = tmp[j];
+        const float sc = (float)(1 << q.octave);
+        cdvs_keypoint& k = kp_out[written + j];
+        k.x = q.xo * sc;
+        k.y = q.yo * sc;
+        k.sigma = q.so * sc;
+        k.theta = 0.0f;
+        k.response = q.resp;
+        k.p_ss = q.pss;
+        k.ratio = q.ratio;
+        k.octave = q.octave;
+        k.scale_idx = 0;
+        k.type = q.type;
+        k.reserved = 0;
+        k.image = i;
+        k.parent_id = -1;
+      }
+      kp_count[i] = m;
+      written += m;
+    }
+    return map_status(c, status_bits);
+  }
+
+  if (mode == kExtract) {
+    SelectArgs a;
+    a.plans = static_cast<const ImgPlan*>(c->plans.p);
+    a.cands = static_cast<const Cand*>(c->cands.p);
+    a.cand_count = static_cast<const int*>(c->cand_count.p);
+    a.cand_cap = cap;
+    a.order = static_cast<int*>(c->order.p);
+    a.keep = static_cast<unsigned char*>(c->keep.p);
+    a.sel = static_cast<Cand*>(c->sel.p);
+    a.sel_count = static_cast<int*>(c->sel_count.p);
+    a.N = N;
+    a.dlog2 = p.dedupe_dlog2;
+    a.status = static_cast<int*>(c->status.p);
+    ev = prof_begin(c, s);
+    if ((e = launch_select(a, n, s)) != cudaSuccess) return cuda_fail(c, e, "select launch");
+    prof_end(c, 1, 1, ev, s);
+  } else {  // kDescribe: the given points become the selected list
+    std::vector<Cand> h_sel(slots);
+    std::vector<int> h_cnt(n);
+    for (int i = 0; i < n; ++i) {
+      const int m = pin->counts[i];
+      if (m < 0 || m > N) return fail(c, CDVS_INVALID_ARGUMENT, "n_pts[i] must be in 0..max_keypoints");
+      h_cnt[i] = m;
+      for (int j = 0; j < m; ++j) {
+        const cdvs_keypoint& k = pin->pts[(size_t)i * pin->stride + j];
+        if (k.octave < 0 || k.octave >= c->h_plans[i].n_oct)
+          return fail(c, CDVS_INVALID_ARGUMENT, "point octave out of range");
+        const float inv = 1.0f / (float)(1 << k.octave);
+        Cand& q = h_sel[(size_t)i * N + j];
+        q.xo = k.x * inv;
+        q.yo = k.y * inv;
+        q.so = k.sigma * inv;
+        q.resp = k.response;
+        q.pss = k.p_ss;
+        q.ratio = k.ratio;
+        q.octave = k.octave;
+        q.type = k.type;
+        q.spare = 0;
+      }
+    }
+    if ((e = cudaMemcpyAsync(c->sel.p, h_sel.data(), sizeof(Cand) * slots, cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(c->sel_count.p, h_cnt.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+      return cuda_fail(c, e, "point upload");
+  }
+
+  DescribeArgs d = describe_args(c, n, p);
+  d.kp_capacity = capacity;
+  const bool dev_out = (flags & CDVS_OUTPUT_DEVICE) != 0;
+  if (dev_out) {
+    d.kp_out = kp_out;
+    d.desc_out = desc_out;
+    d.kp_count = kp_count;
+  } else {
+    if ((e = ensure(c->out_kp, sizeof(cdvs_keypoint) * (size_t)capacity)) != cudaSuccess ||
+        (e = ensure(c->out_desc, sizeof(float) * 128 * (size_t)capacity)) != cudaSuccess ||
+        (e = ensure(c->out_count, sizeof(int) * n)) != cudaSuccess)
+      return cuda_fail(c, e, "output staging");
+    d.kp_out = static_cast<cdvs_keypoint*>(c->out_kp.p);
+    d.desc_out = static_cast<float*>(c->out_desc.p);
+    d.kp_count = static_cast<int*>(c->out_count.p);
+  }
+  ev = prof_begin(c, s);
+  if ((e = launch_orient(d, p.storage, s)) != cudaSuccess) return cuda_fail(c, e, "orientation launch");
+  prof_end(c, 2, 1, ev, s);
+  ev = prof_begin(c, s);
+  if ((e = launch_pack(d, s)) != cudaSuccess) return cuda_fail(c, e, "packing launch");
+  prof_end(c, 3, 1, ev, s);
+  ev = prof_begin(c, s);
+  if ((e = launch_desc(d, p.storage, c->n_sms, s)) != cudaSuccess) return cuda_fail(c, e, "descriptor launch");
+  prof_end(c, 4, 1, ev, s);
+  if ((e = cudaMemcpyAsync(h_small, c->status.p, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(h_small + 1, c->rec_total.p, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return cuda_fail(c, e, "status readback");
+  const int status_bits = h_small[0];
+  const int total = h_small[1];
+  if (!dev_out) {
+    if ((e = cudaMemcpyAsync(kp_count, c->out_count.p, sizeof(int) * n, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (total > 0 && (e = cudaMemcpyAsync(kp_out, c->out_kp.p, sizeof(cdvs_keypoint) * (size_t)total,
+                                           cudaMemcpyDeviceToHost, s)) != cudaSuccess) ||
+        (total > 0 && (e = cudaMemcpyAsync(desc_out, c->out_desc.p, sizeof(float) * 128 * (size_t)total,
+                                           cudaMemcpyDeviceToHost, s)) != cudaSuccess) ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+      return cuda_fail(c, e, "output readback");
+  }
+  return map_status(c, status_bits);
+}
+
+}  // namespace
+
+extern "C" {
+
+void cdvs_params_default(cdvs_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->num_octaves = 4;
+  p->scales_per_octave = 4;
+  p->sigma0 = 1.6f;
+  p->sigma_in = 0.5f;
+  p->contrast_T = 4.0f;
+  p->edge_r = 10.0f;
+  p->offset_max = 0.5f;
+  p->ori_radius = 3.96f;     // Sec. IV-B
+  p->ori_peak_ratio = 0.8f;  // Sec. IV-B
+  p->ori_weight_sigma = 1.5f;
+  p->desc_radius = 6.0f;     // Alg. 2 stage B
+  p->cell_side = 3.0f;       // Sec. IV-B
+  p->desc_weight_sigma = 2.0f;
+  p->dedupe_dlog2 = 1.0f / 3.0f;
+  p->max_keypoints = 300;    // Sec. III-B
+  p->max_orientations = 4;
+  p->upright = 0;
+  p->storage = CDVS_STORAGE_FP32;
+}
+
+cdvs_status cdvs_create(cdvs_ctx** out, int device, size_t workspace_bytes_hint) {
+  if (!out) return CDVS_INVALID_ARGUMENT;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return CDVS_CUDA_ERROR;
+  }
+  if (device < 0 || device >= ndev) return CDVS_INVALID_ARGUMENT;
+  if (cudaSetDevice(device) != cudaSuccess) return CDVS_CUDA_ERROR;
+  cdvs_ctx* c = new cdvs_ctx();
+  c->device = device;
+  cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, device);
+  if (workspace_bytes_hint > 0 && ensure(c->levels, workspace_bytes_hint) != cudaSuccess) {
+    delete c;
+    return CDVS_OUT_OF_MEMORY;
+  }
+  *out = c;
+  return CDVS_OK;
+}
+
+void cdvs_destroy(cdvs_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  DevBuf* bufs[] = {&c->levels,  &c->cands,   &c->cand_count, &c->order,   &c->keep,
+                    &c->sel,     &c->sel_count, &c->ori_theta, &c->ori_count, &c->rec_map,
+                    &c->rec_total, &c->out_kp, &c->out_desc, &c->out_count, &c->plans,
+                    &c->tile_prefix, &c->status, &c->input, &c->dump};
+  for (DevBuf* b : bufs)
+    if (b->p) cudaFree(b->p);
+  if (c->small.p) cudaFreeHost(c->small.p);
+  for (const ProfRec& r : c->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+  delete c;
+}
+
+const char* cdvs_last_error(const cdvs_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+cdvs_status cdvs_extract(cdvs_ctx* c, int32_t n_images, const uint8_t* const* images,
+                         const cdvs_image_desc* sizes, const cdvs_params* params, cdvs_keypoint* kp_out,
+                         float* desc_out, int32_t kp_capacity, int32_t* kp_count, uint32_t flags,
+                         void* cuda_stream) {
+  return run(c, kExtract, n_images, images, sizes, params, nullptr, kp_out, desc_out, kp_capacity, kp_count,
+             flags, static_cast<cudaStream_t>(cuda_stream));
+}
+
+cdvs_status cdvs_candidates(cdvs_ctx* c, int32_t n_images, const uint8_t* const* images,
+                            const cdvs_image_desc* sizes, const cdvs_params* params, cdvs_keypoint* cand_out,
+                            int32_t cand_capacity, int32_t* cand_count, uint32_t flags, void* cuda_stream) {
+  return run(c, kCandidates, n_images, images, sizes, params, nullptr, cand_out, nullptr, cand_capacity,
+             cand_count, flags, static_cast<cudaStream_t>(cuda_stream));
+}
+
+cdvs_status cdvs_describe(cdvs_ctx* c, int32_t n_images, const uint8_t* const* images,
+                          const cdvs_image_desc* sizes, const cdvs_params* params, const cdvs_keypoint* pts,
+                          const int32_t* n_pts, int32_t pts_stride, cdvs_keypoint* kp_out, float* desc_out,
+                          int32_t kp_capacity, int32_t* kp_count, uint32_t flags, void* cuda_stream) {
+  if (!pts || !n_pts || pts_stride < 0) return fail(c, CDVS_INVALID_ARGUMENT, "points are NULL");
+  if (flags & CDVS_INPUT_DEVICE) {
+    // point lists are read on the host by this entry point
+  }
+  PointsIn pin{pts, n_pts, pts_stride};
+  return run(c, kDescribe, n_images, images, sizes, params, &pin, kp_out, desc_out, kp_capacity, kp_count,
+             flags, static_cast<cudaStream_t>(cuda_stream));
+}
+
+cdvs_status cdvs_dedupe_select(cdvs_ctx* c, int32_t n, const cdvs_image_desc* sizes, const cdvs_keypoint* cand,
+                               const int32_t* cand_count, int32_t cand_stride, const cdvs_params* params,
+                               cdvs_keypoint* sel_out, int32_t sel_capacity, int32_t* sel_count, uint32_t flags,
+                               void* cuda_stream) {
+  if (!c) return CDVS_INVALID_ARGUMENT;
+  cdvs_status st = check_params(c, params);
+  if (st != CDVS_OK) return st;
+  if (n < 0 || !sizes || (n > 0 && (!cand || !cand_count || !sel_out || !sel_count)))
+    return fail(c, CDVS_INVALID_ARGUMENT, "NULL argument or n < 0");
+  if (flags & (CDVS_INPUT_DEVICE | CDVS_OUTPUT_DEVICE))
+    return fail(c, CDVS_INVALID_ARGUMENT, "cdvs_dedupe_select takes host buffers only");
+  if (n == 0) return CDVS_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  const cdvs_params& p = *params;
+  long long level_elems, max_pixels;
+  int max_oct;
+  if ((st = plan_batch(c, n, sizes, p, level_elems, max_oct, max_pixels)) != CDVS_OK) return st;
+  int cap = 1;
+  for (int i = 0; i < n; ++i) cap = std::max(cap, (int)cand_count[i]);
+  const int N = p.max_keypoints;
+  std::vector<Cand> h((size_t)n * cap);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < cand_count[i]; ++j) {
+      const cdvs_keypoint& k = cand[(size_t)i * cand_stride + j];
+      if (k.octave < 0 || k.octave >= kMaxOctaves) return fail(c, CDVS_INVALID_ARGUMENT, "octave out of range");
+      const float inv = 1.0f / (float)(1 << k.octave);
+      Cand& q = h[(size_t)i * cap + j];
+      q.xo = k.x * inv;
+      q.yo = k.y * inv;
+      q.so = k.sigma * inv;
+      q.resp = k.response;
+      q.pss = k.p_ss;
+      q.ratio = k.ratio;
+      q.octave = k.octave;
+      q.type = k.type;
+      q.spare = j;
+    }
+  if ((e = ensure(c->cands, sizeof(Cand) * h.size())) != cudaSuccess ||
+      (e = ensure(c->cand_count, sizeof(int) * n)) != cudaSuccess ||
+      (e = ensure(c->order, sizeof(int) * h.size())) != cudaSuccess || (e = ensure(c->keep, h.size())) != cudaSuccess ||
+      (e = ensure(c->sel, sizeof(Cand) * (size_t)n * N)) != cudaSuccess ||
+      (e = ensure(c->sel_count, sizeof(int) * n)) != cudaSuccess ||
+      (e = ensure(c->status, sizeof(int) * 4)) != cudaSuccess ||
+      (e = ensure(c->plans, sizeof(ImgPlan) * n)) != cudaSuccess)
+    return cuda_fail(c, e, "workspace");
+  std::vector<int> cnt(cand_count, cand_count + n);
+  if ((e = cudaMemcpyAsync(c->cands.p, h.data(), sizeof(Cand) * h.size(), cudaMemcpyHostToDevice, s)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(c->cand_count.p, cnt.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(c->plans.p, c->h_plans.data(), sizeof(ImgPlan) * n, cudaMemcpyHostToDevice, s)) !=
+          cudaSuccess ||
+      (e = cudaMemsetAsync(c->status.p, 0, sizeof(int) * 4, s)) != cudaSuccess)
+    return cuda_fail(c, e, "upload");
+  SelectArgs a;
+  a.plans = static_cast<const ImgPlan*>(c->plans.p);
+  a.cands = static_cast<const Cand*>(c->cands.p);
+  a.cand_count = static_cast<const int*>(c->cand_count.p);
+  a.cand_cap = cap;
+  a.order = static_cast<int*>(c->order.p);
+  a.keep = static_cast<unsigned char*>(c->keep.p);
+  a.sel = static_cast<Cand*>(c->sel.p);
+  a.sel_count = static_cast<int*>(c->sel_count.p);
+  a.N = N;
+  a.dlog2 = p.dedupe_dlog2;
+  a.status = static_cast<int*>(c->status.p);
+  if ((e = launch_select(a, n, s)) != cudaSuccess) return cuda_fail(c, e, "select launch");
+  std::vector<Cand> hs((size_t)n * N);
+  std::vector<int> hc(n);
+  int status_bits = 0;
+  if ((e = cudaMemcpyAsync(hs.data(), c->sel.p, sizeof(Cand) * hs.size(), cudaMemcpyDeviceToHost, s)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(hc.data(), c->sel_count.p, sizeof(int) * n, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&status_bits, c->status.p, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return cuda_fail(c, e, "readback");
+  int written = 0;
+  for (int i = 0; i < n; ++i) {
+    int m = hc[i];
+    if (written + m > sel_capacity) {
+      m = std::max(0, sel_capacity - written);
+      status_bits |= kStatusOutTruncated;
+    }
+    for (int r = 0; r < m; ++r) {
+      const Cand& q = hs[(size_t)i * N + r];
+      const float sc = (float)(1 << q.octave);
+      cdvs_keypoint& k = sel_out[written + r];
+      k.x = q.xo * sc;
+      k.y = q.yo * sc;
+      k.sigma = q.so * sc;
+      k.theta = 0.0f;
+      k.response = q.resp;
+      k.p_ss = q.pss;
+      k.ratio = q.ratio;
+      k.octave = q.octave;
+      k.scale_idx = 0;
+      k.type = q.type;
+      k.reserved = 0;
+      k.image = i;
+      k.parent_id = q.spare;  // index of the point in the caller's list
+    }
+    sel_count[i] = m;
+    written += m;
+  }
+  return map_status(c, status_bits);
+}
+
+cdvs_status cdvs_scale_space(cdvs_ctx* c, const uint8_t* image, const cdvs_image_desc* size,
+                             const cdvs_params* params, float* levels_out, size_t capacity, int32_t* n_octaves,
+                             uint32_t flags, void* cuda_stream) {
+  if (!c) return CDVS_INVALID_ARGUMENT;
+  if (!image || !size || !levels_out || !n_octaves) return fail(c, CDVS_INVALID_ARGUMENT, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const uint8_t* imgs[1] = {image};
+  cdvs_status st = run(c, kScaleSpace, 1, imgs, size, params, nullptr, nullptr, nullptr, 0, nullptr,
+                       flags & CDVS_INPUT_DEVICE, s);
+  if (st != CDVS_OK) return st;
+  const ImgPlan& P = c->h_plans[0];
+  size_t need = 0;
+  for (int o = 0; o < P.n_oct; ++o) need += (size_t)kScales * P.oct[o].W * P.oct[o].H;
+  if (need > capacity) return fail(c, CDVS_INVALID_ARGUMENT, "levels_out capacity too small");
+  cudaError_t e;
+  float* dst = levels_out;
+  if (!(flags & CDVS_OUTPUT_DEVICE)) {
+    if ((e = ensure(c->dump, need * sizeof(float))) != cudaSuccess) return cuda_fail(c, e, "dump buffer");
+    dst = static_cast<float*>(c->dump.p);
+  }
+  size_t off = 0;
+  for (int o = 0; o < P.n_oct; ++o)
+    for (int k = 0; k < kScales; ++k) {
+      const OctPlan& op = P.oct[o];
+      if ((e = launch_levels_to_f32(nullptr, 0, c->levels.p, params->storage, o, k, op.W, op.H,
+                                    op.level_off + (long long)k * op.lpitch * op.H, op.lpitch, dst + off, s)) !=
+          cudaSuccess)
+        return cuda_fail(c, e, "level copy");
+      off += (size_t)op.W * op.H;
+    }
+  if (!(flags & CDVS_OUTPUT_DEVICE)) {
+    if ((e = cudaMemcpyAsync(levels_out, dst, need * sizeof(float), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+      return cuda_fail(c, e, "level readback");
+  }
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(c, e, "sync");
+  *n_octaves = P.n_oct;
+  return CDVS_OK;
+}
+
+cdvs_status cdvs_profile(cdvs_ctx* c, int32_t enable) {
+  if (!c) return CDVS_INVALID_ARGUMENT;
+  c->prof = enable != 0;
+  return CDVS_OK;
+}
+
+int32_t cdvs_profile_read(cdvs_ctx* c, double* ms, int32_t* launches, int32_t max_stages, int32_t reset) {
+  if (!c || !ms || !launches || max_stages < 0) return -1;
+  if (cudaSetDevice(c->device) != cudaSuccess) return -1;
+  for (int i = 0; i < max_stages; ++i) {
+    ms[i] = 0.0;
+    launches[i] = 0;
+  }
+  for (const ProfRec& r : c->recs) {
+    if (cudaEventSynchronize(r.b) != cudaSuccess) return -1;
+    float t = 0.0f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) return -1;
+    if (r.stage < max_stages) {
+      ms[r.stage] += t;
+      launches[r.stage] += r.launches;
+    }
+  }
+  if (reset) {
+    for (const ProfRec& r : c->recs) {
+      c->pool.push_back(r.a);
+      c->pool.push_back(r.b);
+    }
+    c->recs.clear();
+  }
+  return 5;
+}
+
+}  // extern "C"

@@ -1,0 +1,134 @@
+// cdvs_internal.cuh -- device-side data layout and kernel interfaces of the
+// GB300 CDVS front end.  Shared by the .cu files of this library only.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/cdvs.h"
+
+namespace cdvs {
+
+// ---------------------------------------------------------------- limits
+constexpr int kMaxOctaves = 12;
+constexpr int kScales = 4;       // K: levels per octave fitted by the cubic (Eq. 2-3)
+constexpr int kMaxRadius = 24;   // largest Gaussian radius a level filter may have
+constexpr int kMaxOri = 8;       // orientation copies per point
+constexpr int kMaxSelect = 2048; // N limit of the selection step
+constexpr int kSelectList = 4096;  // entries sorted by the selection step (N + ties)
+constexpr int kMaxCells = 8192;  // spatial hash cells of the cross-octave check
+
+// detection tile (output pixels per CTA) and CTA size
+constexpr int kTX = 128;
+constexpr int kTY = 32;
+constexpr int kDetThreads = 256;
+constexpr int kHalo = 2;         // 1 px for the Laplacian + 1 px for the 8-neighbour test
+
+// status word bits (device), OR-ed by kernels
+constexpr int kStatusCandOverflow = 1;
+constexpr int kStatusSelectOverflow = 2;
+constexpr int kStatusOutTruncated = 4;
+
+// ---------------------------------------------------------------- plans
+// Level (o, k) of an image is stored at level_base + oct[o].level_off +
+// k * oct[o].lpitch * oct[o].H elements (FP32 or FP16), rows lpitch apart.
+struct OctPlan {
+  int W, H;
+  int lpitch;          // elements per stored row (multiple of 8)
+  int tiles_x, tiles_y;
+  long long level_off; // element offset of level (o, 0) in the level arena
+};
+
+struct ImgPlan {
+  const uint8_t* src;  // device pointer to the 8-bit image
+  int W, H, pitch;     // pitch in bytes
+  int n_oct;
+  OctPlan oct[kMaxOctaves];
+};
+
+// One candidate / selected point, octave px.  32 bytes.
+struct Cand {
+  float xo, yo, so;    // position and scale in octave px
+  float resp;          // refined response p-hat
+  float pss;           // d2p/dsigma2 at sigma*
+  float ratio;         // Hessian tr^2/det
+  short octave, type;  // octave; +1 max / -1 min
+  int spare;
+};
+
+// ---------------------------------------------------------------- K1 args
+struct DetectArgs {
+  const ImgPlan* plans;
+  const int* tile_prefix;  // n_images + 1 entries: first tile of each image in this launch
+  int n_images;
+  int octave;
+  void* levels;            // level arena (float or __half)
+  Cand* cands;             // n_images x cand_cap
+  int* cand_count;         // per image
+  int cand_cap;
+  int* status;
+  int radius[kScales];
+  float taps[kScales][kMaxRadius + 1];   // one side of each symmetric level filter
+  float s2[kScales];                     // s_k^2: LoG scale normalisation
+  float B[4][kScales];                   // cubic fit in t = sigma - tc: a_i = sum_k B[i][k] L_k
+  float tc;                              // centre of the fitting variable
+  float t_lo, t_hi;                      // admissible t range (s_0 - tc, s_{K-1} - tc)
+  float T;                               // contrast threshold
+  float edge_lim;                        // (r+1)^2 / r
+  float offset_max;
+  int write_level0;                      // 1 at octave 0 (level 0 is filtered, not the base)
+};
+
+// ---------------------------------------------------------------- K3/K10 args
+struct SelectArgs {
+  const ImgPlan* plans;
+  const Cand* cands;
+  const int* cand_count;
+  int cand_cap;
+  int* order;              // scratch n_images x cand_cap
+  unsigned char* keep;     // scratch n_images x cand_cap
+  Cand* sel;               // n_images x N
+  int* sel_count;
+  int N;
+  float dlog2;
+  int* status;
+};
+
+// ---------------------------------------------------------------- K5/K6 args
+struct DescribeArgs {
+  const ImgPlan* plans;
+  const void* levels;
+  const Cand* sel;         // n_images x N
+  const int* sel_count;
+  int N;
+  int n_images;
+  float* ori_theta;        // n_images x N x kMaxOri
+  int* ori_count;          // n_images x N
+  int* rec_map;            // output record -> slot * kMaxOri + copy
+  int* rec_total;          // number of records written
+  int* kp_count;           // per image records written
+  int kp_capacity;
+  cdvs_keypoint* kp_out;
+  float* desc_out;
+  int* status;
+  float sigma0;
+  int upright;
+  int max_ori;
+  float ori_radius, ori_ratio, ori_wsig;
+  float desc_radius, cell_side, desc_wsig;
+};
+
+// launchers (defined in the .cu files)
+size_t detect_smem_bytes(int max_radius);
+cudaError_t launch_detect(const DetectArgs& a, int n_tiles, int max_radius, int storage,
+                          cudaStream_t s);
+cudaError_t launch_select(const SelectArgs& a, int n_images, cudaStream_t s);
+cudaError_t launch_orient(const DescribeArgs& a, int storage, cudaStream_t s);
+cudaError_t launch_pack(const DescribeArgs& a, cudaStream_t s);
+cudaError_t launch_desc(const DescribeArgs& a, int storage, int n_sms, cudaStream_t s);
+cudaError_t launch_levels_to_f32(const ImgPlan* plans, int img, const void* levels, int storage,
+                                 int octave, int k, int W, int H, long long off, int lpitch,
+                                 float* out, cudaStream_t s);
+
+}  // namespace cdvs

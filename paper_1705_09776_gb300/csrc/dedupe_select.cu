@@ -1,0 +1,262 @@
+// dedupe_select.cu -- K3 + K10: per image, the cross-octave duplicate check
+// of Alg. 1 stage C and the top-N selection of Eq. 5, in one CTA.
+//
+//   1. Candidates are bucketed into square cells at least as wide as the
+//      largest duplicate window (one pixel of the coarsest octave), so every
+//      duplicate of a candidate lies in its own or one of the 8 surrounding
+//      cells (a counting sort through shared-memory cell counters).
+//   2. A candidate is removed when an adjacent-octave candidate within
+//      |dx|, |dy| <= 2^max(o_a, o_b) image px and |log2(sigma_a/sigma_b)| <=
+//      dlog2 has a larger |response| (or an equal one from a finer octave).
+//      All decisions use the original set, so the result does not depend on
+//      the order in which candidates were queued.
+//   3. The N-th largest |response| among the kept candidates is found by a
+//      4-pass radix select on the IEEE bits; the candidates at or above it are
+//      gathered and bitonic-sorted by (|response| desc, y, x, sigma, octave),
+//      a total order, and the first N are written in rank order.
+#include "cdvs_internal.cuh"
+
+namespace cdvs {
+namespace {
+
+constexpr int kSelThreads = 512;
+
+struct SelEntry {
+  float absr, y, x, sigma;
+  int octave, idx;
+};
+
+__device__ __forceinline__ bool ranks_before(const SelEntry& a, const SelEntry& b) {
+  if (a.absr != b.absr) return a.absr > b.absr;
+  if (a.y != b.y) return a.y < b.y;
+  if (a.x != b.x) return a.x < b.x;
+  if (a.sigma != b.sigma) return a.sigma < b.sigma;
+  return a.octave < b.octave;
+}
+
+// exclusive scan of cnt[0..n) in place (block-wide); returns the total
+__device__ int block_exclusive_scan(int* cnt, int n, int* warp_sums) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int per = (n + kSelThreads - 1) / kSelThreads;
+  const int b0 = min(tid * per, n), b1 = min(b0 + per, n);
+  int local = 0;
+  for (int i = b0; i < b1; ++i) local += cnt[i];
+  int incl = local;
+  for (int d = 1; d < 32; d <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += v;
+  }
+  if (lane == 31) warp_sums[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int w = lane < kSelThreads / 32 ? warp_sums[lane] : 0;
+    int wi = w;
+    for (int d = 1; d < 32; d <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, wi, d);
+      if (lane >= d) wi += v;
+    }
+    if (lane < kSelThreads / 32) warp_sums[lane] = wi - w;  // exclusive warp offsets
+    if (lane == kSelThreads / 32 - 1) warp_sums[32] = wi;   // total
+  }
+  __syncthreads();
+  int run = warp_sums[warp] + incl - local;
+  for (int i = b0; i < b1; ++i) {
+    const int c = cnt[i];
+    cnt[i] = run;
+    run += c;
+  }
+  const int total = warp_sums[32];
+  __syncthreads();
+  return total;
+}
+
+__global__ void __launch_bounds__(kSelThreads) select_kernel(const __grid_constant__ SelectArgs a) {
+  extern __shared__ float4 smem4[];
+  __shared__ int warp_sums[33];
+  __shared__ int s_hist[256];
+  __shared__ int s_misc[4];
+  const int img = blockIdx.x;
+  const int tid = threadIdx.x;
+  const ImgPlan* P = a.plans + img;
+  const int W = P->W, H = P->H, n_oct = P->n_oct;
+  const int n = min(a.cand_count[img], a.cand_cap);
+  const Cand* C = a.cands + (size_t)img * a.cand_cap;
+  int* order = a.order + (size_t)img * a.cand_cap;
+  unsigned char* keep = a.keep + (size_t)img * a.cand_cap;
+
+  // ---- 1. cells of side cs (image px), cs >= 2^(n_oct-1)
+  int cs = 1 << max(n_oct - 1, 0);
+  while (((W + cs - 1) / cs) * ((H + cs - 1) / cs) > kMaxCells) cs <<= 1;
+  const int gx = (W + cs - 1) / cs, gy = (H + cs - 1) / cs, ncell = gx * gy;
+  const float inv_cs = 1.0f / (float)cs;
+  int* cell = reinterpret_cast<int*>(smem4);  // ncell + 1 counters -> ends
+  for (int i = tid; i <= ncell; i += kSelThreads) cell[i] = 0;
+  __syncthreads();
+  for (int i = tid; i < n; i += kSelThreads) {
+    const float s = (float)(1 << C[i].octave);
+    const int cx = min(max((int)floorf(C[i].xo * s * inv_cs), 0), gx - 1);
+    const int cy = min(max((int)floorf(C[i].yo * s * inv_cs), 0), gy - 1);
+    atomicAdd(cell + cy * gx + cx, 1);
+  }
+  __syncthreads();
+  block_exclusive_scan(cell, ncell, warp_sums);
+  for (int i = tid; i < n; i += kSelThreads) {
+    const float s = (float)(1 << C[i].octave);
+    const int cx = min(max((int)floorf(C[i].xo * s * inv_cs), 0), gx - 1);
+    const int cy = min(max((int)floorf(C[i].yo * s * inv_cs), 0), gy - 1);
+    const int pos = atomicAdd(cell + cy * gx + cx, 1);  // after this, cell[c] = end of cell c
+    order[pos] = i;
+  }
+  __syncthreads();
+
+  // ---- 2. cross-octave duplicates
+  int kept_local = 0;
+  for (int i = tid; i < n; i += kSelThreads) {
+    const Cand ca = C[i];
+    const float sa = (float)(1 << ca.octave);
+    const float xa = ca.xo * sa, ya = ca.yo * sa, siga = ca.so * sa;
+    const float ra = fabsf(ca.resp);
+    const int cx = min(max((int)floorf(xa * inv_cs), 0), gx - 1);
+    const int cy = min(max((int)floorf(ya * inv_cs), 0), gy - 1);
+    bool k = true;
+    for (int yy = max(cy - 1, 0); yy <= min(cy + 1, gy - 1) && k; ++yy)
+      for (int xx = max(cx - 1, 0); xx <= min(cx + 1, gx - 1) && k; ++xx) {
+        const int c = yy * gx + xx;
+        const int beg = c == 0 ? 0 : cell[c - 1], end = cell[c];
+        for (int j = beg; j < end; ++j) {
+          const Cand cb = C[order[j]];
+          const int d = ca.octave - cb.octave;
+          if (d != 1 && d != -1) continue;
+          const float win = (float)(1 << max(ca.octave, (int)cb.octave));
+          const float sb = (float)(1 << cb.octave);
+          if (!(fabsf(xa - cb.xo * sb) <= win && fabsf(ya - cb.yo * sb) <= win)) continue;
+          if (!(fabsf(log2f(siga / (cb.so * sb))) <= a.dlog2)) continue;
+          const float rb = fabsf(cb.resp);
+          if (rb > ra || (rb == ra && cb.octave < ca.octave)) {
+            k = false;
+            break;
+          }
+        }
+      }
+    keep[i] = k ? 1 : 0;
+    kept_local += k ? 1 : 0;
+  }
+  if (tid == 0) s_misc[0] = 0;
+  __syncthreads();
+  atomicAdd(s_misc, kept_local);
+  __syncthreads();
+  const int M = s_misc[0];
+  const int N = a.N;
+
+  // ---- 3. radix select of the N-th largest |response| (IEEE bits of a
+  // non-negative float order like the floats themselves)
+  unsigned thr = 0u;
+  if (M > N) {
+    unsigned prefix = 0u, mask = 0u;
+    int remaining = N;
+    for (int shift = 24; shift >= 0; shift -= 8) {
+      for (int i = tid; i < 256; i += kSelThreads) s_hist[i] = 0;
+      __syncthreads();
+      for (int i = tid; i < n; i += kSelThreads) {
+        if (!keep[i]) continue;
+        const unsigned key = __float_as_uint(fabsf(C[i].resp));
+        if ((key & mask) == prefix) atomicAdd(s_hist + ((key >> shift) & 255u), 1);
+      }
+      __syncthreads();
+      if (tid == 0) {
+        int cum = 0, digit = 0;
+        for (int d = 255; d >= 0; --d) {
+          if (cum + s_hist[d] >= remaining) {
+            digit = d;
+            break;
+          }
+          cum += s_hist[d];
+        }
+        s_misc[1] = digit;
+        s_misc[2] = remaining - cum;
+      }
+      __syncthreads();
+      prefix |= (unsigned)s_misc[1] << shift;
+      mask |= 255u << shift;
+      remaining = s_misc[2];
+      __syncthreads();
+    }
+    thr = prefix;
+  }
+
+  // ---- gather candidates at or above the threshold and sort them
+  SelEntry* list = reinterpret_cast<SelEntry*>(smem4);  // reuses the cell counters
+  int* perm = reinterpret_cast<int*>(list + kSelectList);
+  if (tid == 0) s_misc[3] = 0;
+  __syncthreads();
+  for (int i = tid; i < n; i += kSelThreads) {
+    if (!keep[i]) continue;
+    const float ar = fabsf(C[i].resp);
+    if (__float_as_uint(ar) < thr) continue;
+    const int pos = atomicAdd(s_misc + 3, 1);
+    if (pos >= kSelectList) continue;
+    const float s = (float)(1 << C[i].octave);
+    SelEntry e;
+    e.absr = ar;
+    e.y = C[i].yo * s;
+    e.x = C[i].xo * s;
+    e.sigma = C[i].so * s;
+    e.octave = C[i].octave;
+    e.idx = i;
+    list[pos] = e;
+  }
+  __syncthreads();
+  const int L = min(s_misc[3], kSelectList);
+  if (tid == 0 && s_misc[3] > kSelectList) atomicOr(a.status, kStatusSelectOverflow);
+  int Pn = 1;
+  while (Pn < L) Pn <<= 1;
+  for (int i = tid; i < Pn; i += kSelThreads) {
+    if (i >= L) {
+      SelEntry e;
+      e.absr = -1.0f;
+      e.x = e.y = e.sigma = 0.0f;
+      e.octave = 0x7fffffff;
+      e.idx = -1;
+      list[i] = e;
+    }
+    perm[i] = i;
+  }
+  __syncthreads();
+  for (int k = 2; k <= Pn; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < Pn; i += kSelThreads) {
+        const int l = i ^ j;
+        if (l > i) {
+          const int pi = perm[i], pl = perm[l];
+          const bool asc = (i & k) == 0;  // ascending in "rank" order
+          const bool swap = asc ? ranks_before(list[pl], list[pi]) : ranks_before(list[pi], list[pl]);
+          if (swap) {
+            perm[i] = pl;
+            perm[l] = pi;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  const int cnt = min(N, L);
+  Cand* out = a.sel + (size_t)img * N;
+  for (int r = tid; r < cnt; r += kSelThreads) out[r] = C[list[perm[r]].idx];
+  if (tid == 0) a.sel_count[img] = cnt;
+}
+
+}  // namespace
+
+cudaError_t launch_select(const SelectArgs& a, int n_images, cudaStream_t s) {
+  if (n_images <= 0) return cudaSuccess;
+  const size_t smem_cells = sizeof(int) * (kMaxCells + 1);
+  const size_t smem_list = (sizeof(SelEntry) + sizeof(int)) * kSelectList;
+  const size_t smem = smem_cells > smem_list ? smem_cells : smem_list;
+  cudaError_t e = cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  select_kernel<<<n_images, kSelThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace cdvs

@@ -1,0 +1,75 @@
+"""Matching of GPU records to oracle records, shared by the GPU parity tests.
+
+Tolerances (the CUDA path computes in FP32, the oracle in FP64):
+  * two points match when they are in the same octave, within 0.5 octave px
+    in x and y, and within 0.01 in |log sigma|;
+  * position <= 0.01 octave px, relative scale <= 1e-3, descriptor relative L2
+    <= 1e-3 for matched points;
+  * at least 99.5% of the oracle's points are matched, not counting those the
+    oracle itself decides within a relative 1e-4 of a threshold (points that
+    appear or vanish when every threshold is moved by 1e-4: the "margin" set).
+"""
+import numpy as np
+
+POS_TOL = 0.01        # octave px
+SCALE_TOL = 1e-3      # relative
+DESC_TOL = 1e-3       # relative L2
+THETA_TOL = 2e-3      # rad: an orientation is the same when closer than this
+AGREE = 0.995
+MARGIN = 1e-4
+
+
+def octave_coords(r):
+    s = 2.0 ** r["octave"].astype(np.float64)
+    return r["x"] / s, r["y"] / s, r["sigma"] / s
+
+
+def match(a, b):
+    """For each record of a, the index of the nearest record of b that matches
+    (same octave, |dx|, |dy| < 0.5 octave px, |dlog sigma| < 0.01), else -1."""
+    out = np.full(len(a), -1, np.int64)
+    if len(a) == 0 or len(b) == 0:
+        return out
+    ax, ay, asg = octave_coords(a)
+    bx, by, bsg = octave_coords(b)
+    for i in range(len(a)):
+        m = (b["octave"] == a["octave"][i]) & (np.abs(bx - ax[i]) < 0.5) & (np.abs(by - ay[i]) < 0.5) & \
+            (np.abs(np.log(bsg / asg[i])) < 0.01)
+        idx = np.nonzero(m)[0]
+        if idx.size:
+            d = (bx[idx] - ax[i]) ** 2 + (by[idx] - ay[i]) ** 2
+            out[i] = idx[np.argmin(d)]
+    return out
+
+
+def keyset(r):
+    """Point identity used to compare oracle runs with each other."""
+    x, y, s = octave_coords(r)
+    return [(int(o), round(float(xx), 3), round(float(yy), 3), round(float(np.log(ss)), 3))
+            for o, xx, yy, ss in zip(r["octave"], x, y, s)]
+
+
+def point_agreement(gpu, exact, loose, strict):
+    """Agreement of the GPU point set with the oracle's, excluding margin points.
+
+    Returns (agreement, n_disagree, n_excluded, n_oracle).  A point is in the
+    margin set when it is not in both the loose and the strict oracle result."""
+    g2e = match(gpu, exact)
+    e2g = match(exact, gpu)
+    e_in_loose = match(exact, loose) >= 0
+    e_in_strict = match(exact, strict) >= 0
+    g_in_loose = match(gpu, loose) >= 0
+    # oracle points missing on the GPU
+    miss = (e2g < 0)
+    miss_margin = miss & ~(e_in_loose & e_in_strict)
+    # GPU points absent from the oracle
+    extra = (g2e < 0)
+    extra_margin = extra & g_in_loose
+    n_dis = int((miss & ~miss_margin).sum() + (extra & ~extra_margin).sum())
+    n_exc = int(miss_margin.sum() + extra_margin.sum())
+    n = max(1, len(exact))
+    return 1.0 - n_dis / n, n_dis, n_exc, len(exact)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))

@@ -1,0 +1,297 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Inputs are the seeded synthetic images (paper_1705_09776_gb300.synth) at
+sizes the oracle finishes in seconds: several tiles and ragged tails (97x75,
+641x481, 333x257), the 640x480 workload image, and the smallest supported
+size.  Tolerances are those of tests/parity.py.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1705_09776_gb300 import synth
+
+import parity as PT
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(640, 480), (97, 75), (641, 481), (333, 257), (16, 16)]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1705_09776_gb300 import cdvs
+    return cdvs.Context(0)
+
+
+@pytest.fixture(scope="module")
+def cd():
+    from paper_1705_09776_gb300 import cdvs
+    return cdvs
+
+
+def _img(w, h, seed=1, i=0):
+    nb = max(4, int(200 * w * h / (640 * 480)))
+    return synth.blob_image(synth.image_seed(seed, i), w, h, n_blobs=nb)
+
+
+def _oracle_kp_from(rec):
+    """oracle records from float32 GPU-ABI records (for describe inputs)."""
+    k = np.zeros(len(rec), O.KP_DTYPE)
+    for f in ["x", "y", "sigma", "response", "p_ss", "ratio", "octave", "type"]:
+        k[f] = rec[f]
+    s = 2.0 ** k["octave"]
+    k["xo"], k["yo"], k["so"] = k["x"] / s, k["y"] / s, k["sigma"] / s
+    return k
+
+
+# ------------------------------------------------------------------ S1 / S6
+
+@pytest.mark.parametrize("w,h", SIZES)
+def test_scale_space_levels(ctx, w, h):
+    img = _img(w, h)
+    g = ctx.scale_space(img)
+    o = O.scale_space(img, O.params())
+    assert len(g) == len(o)
+    worst = 0.0
+    for oo in range(len(o)):
+        for k in range(4):
+            err = np.max(np.abs(g[oo][k].astype(np.float64) + 128.0 - o[oo][k]))
+            worst = max(worst, err)
+    # FP32 sums of <= 27 taps of values <= 255 per pass, two passes per
+    # level and a decimated base per octave: well under 2e-3 grey levels
+    assert worst < 2e-3, worst
+
+
+# ------------------------------------------------------------------ S2-S5
+
+@pytest.mark.parametrize("w,h", SIZES[:4])
+def test_candidates_bracketed_by_oracle(ctx, cd, w, h):
+    img = _img(w, h, seed=2)
+    g, cnt, st = ctx.candidates([img])
+    assert st == cd.CDVS_OK
+    ex = O.candidates(img, O.params())
+    lo = O.candidates(img, O.params(margin=PT.MARGIN))
+    sc = O.candidates(img, O.params(margin=-PT.MARGIN))
+    agree, n_dis, n_exc, n = PT.point_agreement(g, ex, lo, sc)
+    assert agree >= PT.AGREE, (agree, n_dis, n_exc, n)
+    m = PT.match(g, ex)
+    ok = m >= 0
+    gx, gy, gs = PT.octave_coords(g[ok])
+    ox, oy, osg = PT.octave_coords(ex[m[ok]])
+    pos = np.maximum(np.abs(gx - ox), np.abs(gy - oy))
+    rel_s = np.abs(gs / osg - 1)
+    # position and scale tolerances on all but a margin fraction of pairs
+    assert np.mean(pos <= PT.POS_TOL) >= PT.AGREE, np.sort(pos)[-5:]
+    assert np.mean(rel_s <= PT.SCALE_TOL) >= PT.AGREE, np.sort(rel_s)[-5:]
+    assert np.all(g["type"][ok] == ex["type"][m[ok]])
+    rr = np.abs(g["response"][ok] / ex["response"][m[ok]] - 1)
+    assert np.mean(rr <= 1e-3) >= PT.AGREE
+
+
+# ------------------------------------------------------------------ S7-S8
+
+@pytest.mark.parametrize("w,h", [(640, 480), (641, 481)])
+def test_dedupe_select_on_oracle_candidates(ctx, w, h):
+    img = _img(w, h, seed=3)
+    ex = O.candidates(img, O.params())
+    # the GPU step gets the oracle's candidates in float32; the oracle decides
+    # on exactly the same (float32-representable) values
+    rec = np.zeros(len(ex), ctx_kp_dtype())
+    for f in ["x", "y", "sigma", "response", "p_ss", "ratio", "octave", "type"]:
+        rec[f] = ex[f]
+    back = _oracle_kp_from(rec)
+    order = O.dedupe_select(back, O.params())
+    sel, cnt, st = ctx.dedupe_select([img.shape], [rec])
+    assert cnt[0] == len(order)
+    assert np.array_equal(sel["parent_id"], order.astype(np.int32))
+
+
+def ctx_kp_dtype():
+    from paper_1705_09776_gb300 import cdvs
+    return cdvs.KEYPOINT_DTYPE
+
+
+def test_dedupe_select_random_sets(ctx):
+    """Random candidate sets with many duplicates, ties in |response| and more
+    candidates than N: the GPU order equals the oracle's exactly."""
+    rng = np.random.default_rng(17)
+    from paper_1705_09776_gb300 import cdvs
+    for trial in range(4):
+        n = 3000
+        rec = np.zeros(n, cdvs.KEYPOINT_DTYPE)
+        rec["octave"] = rng.integers(0, 4, n)
+        s = 2.0 ** rec["octave"]
+        rec["x"] = (rng.integers(1, 630 // s, n) + rng.uniform(-0.5, 0.5, n)) * s
+        rec["y"] = (rng.integers(1, 470 // s, n) + rng.uniform(-0.5, 0.5, n)) * s
+        rec["sigma"] = (1.6 * 2 ** rng.uniform(0, 1, n)) * s
+        rec["response"] = rng.choice([-1, 1], n) * np.round(rng.uniform(4, 40, n), 1)  # ties
+        back = _oracle_kp_from(rec)
+        order = O.dedupe_select(back, O.params())
+        sel, cnt, st = ctx.dedupe_select([(480, 640)], [rec])
+        assert np.array_equal(sel["parent_id"], order.astype(np.int32)), trial
+
+
+# ------------------------------------------------------------------ S9-S10
+
+@pytest.mark.parametrize("w,h,upright", [(640, 480, 0), (641, 481, 0), (333, 257, 1)])
+def test_describe_on_oracle_points(ctx, cd, w, h, upright):
+    img = _img(w, h, seed=4)
+    P = O.params(upright=upright)
+    kp, d, _ = O.extract(img, P)
+    pts = kp[np.unique(kp["parent"], return_index=True)[1]]
+    rec = np.zeros(len(pts), cd.KEYPOINT_DTYPE)
+    for f in ["x", "y", "sigma", "response", "p_ss", "ratio", "octave", "type"]:
+        rec[f] = pts[f]
+    back = _oracle_kp_from(rec)
+    ok_, od = O.describe(img, back, P)
+    lk, ld = O.describe(img, back, O.params(upright=upright, margin=PT.MARGIN, ori_margin=PT.MARGIN))
+    sk, sd = O.describe(img, back, O.params(upright=upright, margin=-PT.MARGIN, ori_margin=-PT.MARGIN))
+    gk, gd, cnt, st = ctx.describe([img], [rec], cd.params(upright=upright))
+    n_pts = len(rec)
+    n_bad = n_exc = 0
+    for j in range(n_pts):
+        def thetas(k):
+            return k["theta"][k["parent"] == j] if "parent" in k.dtype.names else k["theta"][k["parent_id"] == j]
+        gt, et = thetas(gk), thetas(ok_)
+        same = len(gt) == len(et) and all(
+            min(abs(a - b), 2 * math.pi - abs(a - b)) < PT.THETA_TOL for a, b in zip(gt, et))
+        if not same:
+            alt = [thetas(lk), thetas(sk)]
+            if any(len(gt) == len(t) and all(min(abs(a - b), 2 * math.pi - abs(a - b)) < PT.THETA_TOL
+                                             for a, b in zip(gt, t)) for t in alt):
+                n_exc += 1
+            else:
+                n_bad += 1
+            continue
+        gi = np.nonzero(gk["parent_id"] == j)[0]
+        ei = np.nonzero(ok_["parent"] == j)[0]
+        for a, b in zip(gi, ei):
+            if PT.rel_l2(gd[a], od[b]) > PT.DESC_TOL:
+                n_bad += 1
+    assert n_bad <= (1 - PT.AGREE) * n_pts, (n_bad, n_exc, n_pts)
+
+
+# ------------------------------------------------------------------ S1-S10
+
+@pytest.mark.parametrize("w,h", [(640, 480), (641, 481), (333, 257)])
+def test_extract_end_to_end(ctx, cd, w, h):
+    img = _img(w, h, seed=5)
+    gk, gd, cnt, st = ctx.extract([img])
+    assert st == cd.CDVS_OK
+    ek, ed, _ = O.extract(img, O.params())
+    lk, _, _ = O.extract(img, O.params(margin=PT.MARGIN))
+    sk, _, _ = O.extract(img, O.params(margin=-PT.MARGIN))
+
+    def points(r, key):
+        return r[np.unique(r[key], return_index=True)[1]]
+
+    gp, ep = points(gk, "parent_id"), points(ek, "parent")
+    agree, n_dis, n_exc, n = PT.point_agreement(gp, ep, points(lk, "parent"), points(sk, "parent"))
+    assert agree >= PT.AGREE, (agree, n_dis, n_exc, n)
+    # descriptors of matched (point, orientation) records
+    m = PT.match(gk, ek)
+    good = bad = 0
+    for i in np.nonzero(m >= 0)[0]:
+        cand = np.nonzero((PT.match(ek, gk[i:i + 1]) == 0))[0]
+        th = [j for j in cand if min(abs(ek["theta"][j] - gk["theta"][i]),
+                                     2 * math.pi - abs(ek["theta"][j] - gk["theta"][i])) < PT.THETA_TOL]
+        if not th:
+            continue
+        if PT.rel_l2(gd[i], ed[th[0]]) <= PT.DESC_TOL:
+            good += 1
+        else:
+            bad += 1
+    assert good > 0.9 * len(ek)
+    assert bad <= (1 - PT.AGREE) * (good + bad), (good, bad)
+
+
+# ------------------------------------------------------------------ batches
+
+def test_batch_equals_single_and_is_deterministic(ctx):
+    imgs = [_img(640, 480, seed=6, i=i) for i in range(3)] + [_img(333, 257, seed=6, i=9)]
+    bk, bd, bc, _ = ctx.extract(imgs)
+    bk2, bd2, bc2, _ = ctx.extract(imgs)
+    assert np.array_equal(bk.view(np.uint8), bk2.view(np.uint8)) and np.array_equal(bd, bd2)
+    off = 0
+    for i, im in enumerate(imgs):
+        sk, sd, sc, _ = ctx.extract([im])
+        seg = bk[off:off + bc[i]].copy()
+        seg["image"] = 0
+        assert np.array_equal(seg.view(np.uint8), sk.view(np.uint8))
+        assert np.array_equal(bd[off:off + bc[i]], sd)
+        off += bc[i]
+
+
+def test_device_buffers_match_host_path(ctx, cd):
+    import torch
+    imgs = np.stack([_img(640, 480, seed=7, i=i) for i in range(4)])
+    hk, hd, hc, _ = ctx.extract(list(imgs))
+    dev = torch.from_numpy(imgs).cuda()
+    n, H, W = imgs.shape
+    cap = n * 300 * 4
+    kp = torch.zeros(cap * cd.KEYPOINT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    desc = torch.zeros(cap, 128, dtype=torch.float32, device="cuda")
+    cnt = torch.zeros(n, dtype=torch.int32, device="cuda")
+    sizes = np.array([(W, H, W)] * n, cd.IMAGE_DESC_DTYPE)
+    p = cd.params()
+    ptrs = [dev.data_ptr() + i * H * W for i in range(n)]
+    stream = torch.cuda.current_stream()
+    ctx.extract_raw(n, ptrs, sizes, p, kp, desc, cap, cnt,
+                    cd.CDVS_INPUT_DEVICE | cd.CDVS_OUTPUT_DEVICE, stream)
+    torch.cuda.synchronize()
+    c = cnt.cpu().numpy()
+    tot = int(c.sum())
+    assert np.array_equal(c, hc)
+    dk = kp.cpu().numpy()[:tot * cd.KEYPOINT_DTYPE.itemsize].view(cd.KEYPOINT_DTYPE)
+    assert np.array_equal(dk.view(np.uint8), hk.view(np.uint8))
+    assert np.array_equal(desc.cpu().numpy()[:tot], hd)
+
+
+# ------------------------------------------------------------------ edges
+
+def test_edge_cases(ctx, cd):
+    # flat image: no candidate, no record
+    k, d, c, st = ctx.extract([np.full((64, 80), 77, np.uint8)])
+    assert st == cd.CDVS_OK and c[0] == 0 and len(k) == 0
+    # smallest supported size runs; one side below 16 is rejected
+    k, d, c, st = ctx.extract([_img(16, 16)])
+    assert st == cd.CDVS_OK
+    with pytest.raises(cd.CdvsError) as e:
+        ctx.extract([np.zeros((15, 40), np.uint8)])
+    assert e.value.status == cd.CDVS_UNSUPPORTED_SIZE
+    # parameters out of range
+    with pytest.raises(cd.CdvsError) as e:
+        ctx.extract([_img(64, 64)], cd.params(max_keypoints=0))
+    assert e.value.status == cd.CDVS_INVALID_ARGUMENT
+    with pytest.raises(cd.CdvsError) as e:
+        ctx.extract([_img(64, 64)], cd.params(scales_per_octave=5))
+    assert e.value.status == cd.CDVS_INVALID_ARGUMENT
+    # output capacity: truncated deterministically at the end of the batch
+    imgs = [_img(640, 480, seed=8, i=i) for i in range(2)]
+    fk, fd, fc, st = ctx.extract(imgs)
+    cap = int(fc[0]) + 10
+    tk, td, tc, st = ctx.extract(imgs, capacity=cap)
+    assert st == cd.CDVS_CAPACITY_TRUNCATED
+    assert tc[0] == fc[0] and tc[1] == 10
+    assert np.array_equal(tk.view(np.uint8), fk[:cap].view(np.uint8))
+    # an empty batch is a no-op
+    k, d, c, st = ctx.extract([])
+    assert st == cd.CDVS_OK and len(k) == 0
+
+
+def test_fp16_storage_error_is_small(ctx, cd):
+    img = _img(640, 480, seed=9)
+    g16 = ctx.scale_space(img, cd.params(storage=cd.CDVS_STORAGE_FP16))
+    o = O.scale_space(img, O.params())
+    # octave 0 levels: FP32 filtering then one rounding to FP16 (|G - 128| <= 128
+    # -> spacing <= 0.0625, rounding error <= 0.031); later octaves start from
+    # an FP16 base, so their error can grow by a few roundings
+    e0 = max(np.max(np.abs(g16[0][k].astype(np.float64) + 128 - o[0][k])) for k in range(4))
+    assert e0 <= 0.032
+    gk, gd, gc, st = ctx.extract([img], cd.params(storage=cd.CDVS_STORAGE_FP16))
+    ek, ed, _ = O.extract(img, O.params())
+    m = PT.match(gk, ek)
+    assert np.mean(m >= 0) > 0.9
