@@ -187,6 +187,39 @@ def run_reference(args, rank):
     print(json.dumps(out), flush=True)
 
 
+def run_e2e(ctx, imgs, sizes, p, cap, stream, args, barrier, dist, cdvs, torch):
+    """Same call with pinned host inputs and host outputs: the H2D copy of the
+    batch and the D2H copy of every record and descriptor are timed."""
+    n, H, W = imgs.shape
+    h_img = torch.from_numpy(imgs).pin_memory()
+    h_kp = torch.zeros(cap * cdvs.KEYPOINT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    h_desc = torch.zeros(cap, 128, dtype=torch.float32).pin_memory()
+    h_cnt = torch.zeros(n, dtype=torch.int32).pin_memory()
+    hptrs = [h_img.data_ptr() + i * H * W for i in range(n)]
+
+    def step_e2e():
+        return ctx.extract_raw(n, hptrs, sizes, p, h_kp, h_desc, cap, h_cnt, 0, stream)
+
+    for _ in range(3):
+        step_e2e()
+    k_e2e = max(3, args.steps // 2)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        step_e2e()
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / k_e2e
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_records = int(h_cnt.sum().item())
+
+    return e2e_ms, e2e_records
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -195,6 +228,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--images", type=int, default=N_IMAGES, help="images per rank (profiling runs)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank = int(os.environ.get("RANK", "0"))
@@ -203,7 +238,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args, rank)
 
-    imgs = make_batch(N_IMAGES, offset=rank * N_IMAGES)  # before any CUDA call
+    imgs = make_batch(args.images, offset=rank * args.images)  # before any CUDA call
     import torch
     torch.cuda.set_device(local)
     dist = None
@@ -261,34 +296,12 @@ def main():
     value = n * world / (ms * 1e-3)
 
     # ---- end to end through the C ABI: pinned host inputs, host outputs
-    h_img = torch.from_numpy(imgs).pin_memory()
-    h_kp = torch.zeros(cap * cdvs.KEYPOINT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
-    h_desc = torch.zeros(cap, 128, dtype=torch.float32).pin_memory()
-    h_cnt = torch.zeros(n, dtype=torch.int32).pin_memory()
-    hptrs = [h_img.data_ptr() + i * H * W for i in range(n)]
-
-    def step_e2e():
-        return ctx.extract_raw(n, hptrs, sizes, p, h_kp, h_desc, cap, h_cnt, 0, stream)
-
-    for _ in range(3):
-        step_e2e()
-    k_e2e = max(3, args.steps // 2)
-    barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(k_e2e):
-        step_e2e()
-    torch.cuda.synchronize()
-    barrier()
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / k_e2e
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_records = int(h_cnt.sum().item())
+    if args.no_e2e:
+        e2e_ms, e2e_records = float("nan"), 0
+    else:
+        e2e_ms, e2e_records = run_e2e(ctx, imgs, sizes, p, cap, stream, args, barrier, dist, cdvs, torch)
     h2d = n * H * W
     d2h = n * 4 + e2e_records * (cdvs.KEYPOINT_DTYPE.itemsize + 128 * 4) + 8
-
     # ---- roofline of the dominant kernel (K1 detection, all octave launches)
     peaks = load_peaks()
     flops_img, bytes_img = detect_counts(p)
@@ -317,7 +330,8 @@ def main():
                                   f"N=300, 128-D float descriptors", "n_images_per_rank": n,
                       "storage": args.storage, "parallelism": f"replicas x{world} (image-sharded)",
                       "l2": "working set > L2: each step writes 1.7 GB of levels", "records_per_step": records},
-           "e2e": {"value": n * world / (e2e_ms * 1e-3), "unit": "images/s", "ms_per_step": e2e_ms,
+           "e2e": {"value": (n * world / (e2e_ms * 1e-3)) if e2e_ms == e2e_ms else None, "unit": "images/s",
+                   "ms_per_step": e2e_ms if e2e_ms == e2e_ms else None,
                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
            "gpu_launches": launches, "roofline": roofline, "clocks": clocks}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

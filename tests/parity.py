@@ -14,7 +14,8 @@ import numpy as np
 POS_TOL = 0.01        # octave px
 SCALE_TOL = 1e-3      # relative
 DESC_TOL = 1e-3       # relative L2
-THETA_TOL = 2e-3      # rad: an orientation is the same when closer than this
+THETA_TOL = 1e-4      # rad: the same orientation (FP32 histogram sums shift a peak by ~1e-6 rad)
+THETA_ID = 2e-2       # rad: records closer than this are taken as the same orientation copy
 AGREE = 0.995
 MARGIN = 1e-4
 
@@ -69,6 +70,51 @@ def point_agreement(gpu, exact, loose, strict):
     n_exc = int(miss_margin.sum() + extra_margin.sum())
     n = max(1, len(exact))
     return 1.0 - n_dis / n, n_dis, n_exc, len(exact)
+
+
+def ang(a, b):
+    d = abs(a - b) % (2 * np.pi)
+    return min(d, 2 * np.pi - d)
+
+
+def record_agreement(gk, gd, runs):
+    """Orientation and descriptor agreement of GPU records with the oracle.
+
+    runs[0] = (records, descriptors) of the oracle itself; runs[1:] = the
+    oracle with every threshold and every orientation-bin boundary moved by a
+    relative 1e-4 (both ways).  A GPU record is good when the oracle has the
+    same point with theta within THETA_TOL and a descriptor within DESC_TOL;
+    it is a margin case when only a perturbed oracle run has such a theta
+    (a gradient sample sits on a histogram bin boundary, or a peak on the
+    0.8 x max line); otherwise it is bad.  Returns (good, margin, bad)."""
+    good = margin = bad = 0
+    ek, ed = runs[0]
+    m0 = match(gk, ek)
+    alt_m = [match(gk, r[0]) for r in runs[1:]]
+    for i in range(len(gk)):
+        if m0[i] < 0:
+            continue  # point-level disagreement is counted by point_agreement
+        same_pt = np.nonzero(match(ek, gk[i:i + 1]) == 0)[0]
+        dth = [ang(ek["theta"][j], gk["theta"][i]) for j in same_pt]
+        if dth and min(dth) <= THETA_TOL:
+            j = same_pt[int(np.argmin(dth))]
+            if rel_l2(gd[i], ed[j]) <= DESC_TOL:
+                good += 1
+            else:
+                bad += 1
+            continue
+        hit = False
+        for (rk, rd), mm in zip(runs[1:], alt_m):
+            if mm[i] < 0:
+                continue
+            pts = np.nonzero(match(rk, gk[i:i + 1]) == 0)[0]
+            if any(ang(rk["theta"][j], gk["theta"][i]) <= THETA_TOL for j in pts):
+                hit = True
+        if hit:
+            margin += 1
+        else:
+            bad += 1
+    return good, margin, bad
 
 
 def rel_l2(a, b):

@@ -150,28 +150,9 @@ def test_describe_on_oracle_points(ctx, cd, w, h, upright):
     lk, ld = O.describe(img, back, O.params(upright=upright, margin=PT.MARGIN, ori_margin=PT.MARGIN))
     sk, sd = O.describe(img, back, O.params(upright=upright, margin=-PT.MARGIN, ori_margin=-PT.MARGIN))
     gk, gd, cnt, st = ctx.describe([img], [rec], cd.params(upright=upright))
-    n_pts = len(rec)
-    n_bad = n_exc = 0
-    for j in range(n_pts):
-        def thetas(k):
-            return k["theta"][k["parent"] == j] if "parent" in k.dtype.names else k["theta"][k["parent_id"] == j]
-        gt, et = thetas(gk), thetas(ok_)
-        same = len(gt) == len(et) and all(
-            min(abs(a - b), 2 * math.pi - abs(a - b)) < PT.THETA_TOL for a, b in zip(gt, et))
-        if not same:
-            alt = [thetas(lk), thetas(sk)]
-            if any(len(gt) == len(t) and all(min(abs(a - b), 2 * math.pi - abs(a - b)) < PT.THETA_TOL
-                                             for a, b in zip(gt, t)) for t in alt):
-                n_exc += 1
-            else:
-                n_bad += 1
-            continue
-        gi = np.nonzero(gk["parent_id"] == j)[0]
-        ei = np.nonzero(ok_["parent"] == j)[0]
-        for a, b in zip(gi, ei):
-            if PT.rel_l2(gd[a], od[b]) > PT.DESC_TOL:
-                n_bad += 1
-    assert n_bad <= (1 - PT.AGREE) * n_pts, (n_bad, n_exc, n_pts)
+    good, margin, bad = PT.record_agreement(gk, gd, [(ok_, od), (lk, ld), (sk, sd)])
+    assert bad <= (1 - PT.AGREE) * len(ok_), (good, margin, bad, len(ok_))
+    assert good + margin >= PT.AGREE * len(ok_), (good, margin, bad, len(ok_))
 
 
 # ------------------------------------------------------------------ S1-S10
@@ -191,21 +172,14 @@ def test_extract_end_to_end(ctx, cd, w, h):
     gp, ep = points(gk, "parent_id"), points(ek, "parent")
     agree, n_dis, n_exc, n = PT.point_agreement(gp, ep, points(lk, "parent"), points(sk, "parent"))
     assert agree >= PT.AGREE, (agree, n_dis, n_exc, n)
-    # descriptors of matched (point, orientation) records
-    m = PT.match(gk, ek)
-    good = bad = 0
-    for i in np.nonzero(m >= 0)[0]:
-        cand = np.nonzero((PT.match(ek, gk[i:i + 1]) == 0))[0]
-        th = [j for j in cand if min(abs(ek["theta"][j] - gk["theta"][i]),
-                                     2 * math.pi - abs(ek["theta"][j] - gk["theta"][i])) < PT.THETA_TOL]
-        if not th:
-            continue
-        if PT.rel_l2(gd[i], ed[th[0]]) <= PT.DESC_TOL:
-            good += 1
-        else:
-            bad += 1
-    assert good > 0.9 * len(ek)
-    assert bad <= (1 - PT.AGREE) * (good + bad), (good, bad)
+    # orientations and descriptors of matched records: the oracle describes
+    # its own selected points exactly and with every threshold moved by 1e-4
+    sel = ep.copy()
+    od_l = O.describe(img, sel, O.params(margin=PT.MARGIN, ori_margin=PT.MARGIN))
+    od_s = O.describe(img, sel, O.params(margin=-PT.MARGIN, ori_margin=-PT.MARGIN))
+    good, margin, bad = PT.record_agreement(gk, gd, [(ek, ed), od_l, od_s])
+    assert good > 0.9 * len(ek), (good, margin, bad, len(ek))
+    assert bad <= (1 - PT.AGREE) * len(ek), (good, margin, bad, len(ek))
 
 
 # ------------------------------------------------------------------ batches
