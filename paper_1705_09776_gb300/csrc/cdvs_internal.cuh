@@ -22,7 +22,7 @@ constexpr int kMaxCells = 8192;  // spatial hash cells of the cross-octave check
 // detection tile (output pixels per CTA) and CTA size
 constexpr int kTX = 128;
 constexpr int kTY = 32;
-constexpr int kDetThreads = 256;
+constexpr int kDetThreads = 512;
 constexpr int kHalo = 2;         // 1 px for the Laplacian + 1 px for the 8-neighbour test
 
 // status word bits (device), OR-ed by kernels

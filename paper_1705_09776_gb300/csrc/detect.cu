@@ -9,10 +9,19 @@
 //   description) and, on the top level, the decimated base of the next octave
 //   (Alg. 1: Downsampling G_{o,K-1} to G_{o+1,0}).
 //
-// Shared memory per CTA (FP32):
-//   tmp  [36][128 + 4 + 2 R_max]  result of the y pass (rows ty0-2 .. ty0+33)
-//   gs   [36][132]                 G_{o,k} on the tile plus a 2-px halo
-//   Ls   [4][34][130]              L_{o,k} on the tile plus a 1-px halo
+// The filters run on packed FP32 pairs (fma.rn.f32x2: two independent
+// round-to-nearest FMAs per instruction): the y pass on pairs of adjacent
+// columns, the x pass on pairs of adjacent rows.  Intermediate images are kept
+// "row-pair interleaved" -- element (y, x) of a band starting at row y0 sits at
+// [(y - y0) / 2][x][(y - y0) % 2] -- so that every operand pair is one aligned
+// 64-bit shared-memory word.
+//
+// Shared memory per CTA (FP32), Rm = largest level radius of the octave,
+// Cm = 2 + Rm rounded up to a multiple of 4:
+//   in  [36 + 2 Rm][128 + 2 Cm]   octave base with halo, minus 128 at octave 0
+//   tmp [18][128 + 2 Cm][2]       y-pass result, rows ty0-2 .. ty0+33
+//   gs  [18][132][2]              G_{o,k}, rows ty0-2 .. ty0+33, cols tx0-2 ..
+//   Ls  [4][18][130][2]           L_{o,k}, same rows, cols tx0-1 .. tx0+128
 #include <type_traits>
 
 #include "cdvs_internal.cuh"
@@ -21,97 +30,170 @@ namespace cdvs {
 namespace {
 
 constexpr int kRows = kTY + 2 * kHalo;   // 36 rows of G per tile
-constexpr int kGP = kTX + 2 * kHalo;     // 132: row pitch of gs
-constexpr int kLR = kTY + 2;             // 34 rows of L
-constexpr int kLP = kTX + 2;             // 130: row pitch of Ls
-constexpr int kStripV = 12;              // outputs per thread in the y pass
-constexpr int kStripH = 12;              // outputs per thread in the x pass
-static_assert(kRows % kStripV == 0, "y-pass strips must tile the rows");
-static_assert(kGP % kStripH == 0, "x-pass strips must tile the columns");
-static_assert((kTX * kTY) % kDetThreads == 0, "extremum loop must be warp-uniform");
+constexpr int kRP = kRows / 2;           // 18 row pairs
+constexpr int kGC = kTX + 2 * kHalo;     // 132 columns of G
+constexpr int kLC = kTX + 2;             // 130 columns of L
+constexpr int kSV = 6;                   // rows per thread in the y pass
+constexpr int kSH = 6;                   // columns per thread in the x pass
+constexpr int kLG = 3;                   // row-pair groups in the Laplacian pass
+static_assert(kRows % kSV == 0 && kSV % 2 == 0, "y-pass strips must tile the row pairs");
+static_assert(kGC % kSH == 0 && kSH % 2 == 0, "x-pass strips must tile the columns");
+static_assert(kRP % kLG == 0, "Laplacian groups must tile the row pairs");
+static_assert((kTX * kTY / 2) % kDetThreads == 0, "extremum loop must be warp-uniform");
+
+__host__ __device__ constexpr int halo_cols(int rm) { return (2 + rm + 3) & ~3; }
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
 __device__ __forceinline__ float to_f(uint8_t v) { return (float)v - 128.0f; }
 __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
 
-// y pass: tmp[row][c] = sum_d g[|d|] * base[clamp(y + d)][clamp(x)],
-// row <-> y = ty0 - 2 + row, c <-> x = tx0 - 2 - R + c.
-template <int R, typename InT>
-__device__ __forceinline__ void vpass(const InT* __restrict__ src, int spitch, int W, int H,
-                                      int tx0, int ty0, const float (&g)[R + 1], float* tmp,
-                                      int tpitch) {
-  constexpr int kNStrip = kRows / kStripV;
-  const int cols = kTX + 2 * kHalo + 2 * R;
-  const int xbase = tx0 - kHalo - R;
-  const int ybase = ty0 - kHalo - R;
-  for (int item = threadIdx.x; item < cols * kNStrip; item += kDetThreads) {
-    const int s = item / cols;
-    const int c = item - s * cols;
-    const int x = min(max(xbase + c, 0), W - 1);
-    const InT* col = src + x;
-    const int r0 = s * kStripV;
-    float acc[kStripV];
-#pragma unroll
-    for (int o = 0; o < kStripV; ++o) acc[o] = 0.0f;
-#pragma unroll
-    for (int j = 0; j < kStripV + 2 * R; ++j) {
-      const int y = min(max(ybase + r0 + j, 0), H - 1);
-      const float v = to_f(col[(size_t)y * spitch]);
-#pragma unroll
-      for (int o = 0; o < kStripV; ++o) {
-        const int d = j - o - R;
-        if (d >= -R && d <= R) acc[o] = fmaf(g[d < 0 ? -d : d], v, acc[o]);
-      }
-    }
-#pragma unroll
-    for (int o = 0; o < kStripV; ++o) tmp[(r0 + o) * tpitch + c] = acc[o];
-  }
-}
-
-// x pass: gs[row][c] = sum_d g[|d|] * tmp[row][c + R + d], c <-> x = tx0 - 2 + c.
-template <int R>
-__device__ __forceinline__ void hpass(const float* tmp, int tpitch, const float (&g)[R + 1],
-                                      float* gs) {
-  constexpr int kNS = kGP / kStripH;
-  for (int item = threadIdx.x; item < kRows * kNS; item += kDetThreads) {
-    const int row = item / kNS;
-    const int c0 = (item - row * kNS) * kStripH;
-    const float* in = tmp + row * tpitch + c0;
-    float acc[kStripH];
-#pragma unroll
-    for (int o = 0; o < kStripH; ++o) acc[o] = 0.0f;
-#pragma unroll
-    for (int j = 0; j < kStripH + 2 * R; ++j) {
-      const float v = in[j];
-#pragma unroll
-      for (int o = 0; o < kStripH; ++o) {
-        const int d = j - o - R;
-        if (d >= -R && d <= R) acc[o] = fmaf(g[d < 0 ? -d : d], v, acc[o]);
-      }
-    }
-#pragma unroll
-    for (int o = 0; o < kStripH; ++o) gs[row * kGP + c0 + o] = acc[o];
-  }
-}
-
-template <int R, typename InT>
-__device__ __forceinline__ void level_filter(const float* taps, const InT* src, int spitch, int W,
-                                             int H, int tx0, int ty0, float* tmp, int tpitch,
-                                             float* gs) {
-  float g[R + 1];
-#pragma unroll
-  for (int j = 0; j <= R; ++j) g[j] = taps[j];
-  vpass<R, InT>(src, spitch, W, H, tx0, ty0, g, tmp, tpitch);
-  __syncthreads();
-  hpass<R>(tmp, tpitch, g, gs);
-}
-
+// ---- stage the octave base (with clamp-to-edge) into in[IR][IC]
 template <typename InT>
-__device__ void filter_dispatch(int R, const float* taps, const InT* src, int spitch, int W, int H,
-                                int tx0, int ty0, float* tmp, int tpitch, float* gs) {
-#define CDVS_CASE(r) \
-  case r:            \
-    level_filter<r, InT>(taps, src, spitch, W, H, tx0, ty0, tmp, tpitch, gs); \
+__device__ __forceinline__ void stage_input(const InT* __restrict__ src, int spitch, int W, int H,
+                                            int tx0, int ty0, int rm, int cm, float* in) {
+  const int IR = kRows + 2 * rm, IC = kTX + 2 * cm;
+  const int y0 = ty0 - kHalo - rm, x0 = tx0 - cm;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int kWarps = kDetThreads / 32;
+  const bool interior_x = x0 >= 0 && x0 + IC <= W;
+  if constexpr (std::is_same<InT, uint8_t>::value) {
+    // four bytes per load where the row start and pitch allow it
+    const bool vec = interior_x && ((spitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(src) & 3) == 0);
+    if (vec) {
+      const int q = IC / 4;
+      for (int r = warp; r < IR; r += kWarps) {
+        const int y = min(max(y0 + r, 0), H - 1);
+        const uchar4* row = reinterpret_cast<const uchar4*>(src + (size_t)y * spitch + x0);
+        float4* dst = reinterpret_cast<float4*>(in + r * IC);
+        for (int c = lane; c < q; c += 32) {
+          const uchar4 b = __ldg(row + c);
+          dst[c] = make_float4((float)b.x - 128.0f, (float)b.y - 128.0f, (float)b.z - 128.0f,
+                               (float)b.w - 128.0f);
+        }
+      }
+      return;
+    }
+  } else if constexpr (std::is_same<InT, float>::value) {
+    if (interior_x) {  // rows are 16-byte aligned (pitch multiple of 8, x0 multiple of 4)
+      const int q = IC / 4;
+      for (int r = warp; r < IR; r += kWarps) {
+        const int y = min(max(y0 + r, 0), H - 1);
+        const float4* row = reinterpret_cast<const float4*>(src + (size_t)y * spitch + x0);
+        float4* dst = reinterpret_cast<float4*>(in + r * IC);
+        for (int c = lane; c < q; c += 32) dst[c] = __ldg(row + c);
+      }
+      return;
+    }
+  }
+  for (int r = warp; r < IR; r += kWarps) {
+    const int y = min(max(y0 + r, 0), H - 1);
+    const InT* row = src + (size_t)y * spitch;
+    for (int c = lane; c < IC; c += 32) in[r * IC + c] = to_f(row[min(max(x0 + c, 0), W - 1)]);
+  }
+}
+
+// ---- y pass on column pairs: tmp rows ty0-2 .. ty0+33, columns from
+// x = tx0 - C (C = 2 + R rounded up to even) to tx0 + 128 + C.
+template <int R>
+__device__ __forceinline__ void vpass(const float* in, int ic, int rm, int cm, const float2 (&g)[R + 1],
+                                      float* tmp) {
+  constexpr int C = (2 + R + 1) & ~1;
+  constexpr int kPairs = (kTX + 2 * C) / 2;
+  constexpr int kStrips = kRows / kSV;
+  const int col_off = cm - C;  // in-column of tmp column 0
+  for (int item = threadIdx.x; item < kPairs * kStrips; item += kDetThreads) {
+    const int s = item / kPairs;
+    const int p = item - s * kPairs;
+    const int r0 = s * kSV;
+    // output row r reads in-rows r + rm + d, d in [-R, R]
+    const float* src = in + (r0 + rm - R) * ic + col_off + 2 * p;
+    float2 acc[kSV];
+#pragma unroll
+    for (int o = 0; o < kSV; ++o) acc[o] = f2(0.0f, 0.0f);
+#pragma unroll
+    for (int j = 0; j < kSV + 2 * R; ++j) {
+      const float2 v = *reinterpret_cast<const float2*>(src + j * ic);
+#pragma unroll
+      for (int o = 0; o < kSV; ++o) {
+        const int d = j - o - R;
+        if (d >= -R && d <= R) acc[o] = fma2(g[d < 0 ? -d : d], v, acc[o]);
+      }
+    }
+    // rows r0+o, r0+o+1 of columns 2p, 2p+1 -> one 16-byte store
+    float* dst = tmp + ((size_t)(r0 / 2) * ic + 2 * p) * 2;
+#pragma unroll
+    for (int o = 0; o < kSV; o += 2)
+      *reinterpret_cast<float4*>(dst + (size_t)(o / 2) * ic * 2) =
+          make_float4(acc[o].x, acc[o + 1].x, acc[o].y, acc[o + 1].y);
+  }
+}
+
+// ---- x pass on row pairs: gs[yp][c] (c <-> x = tx0 - 2 + c) from tmp
+template <int R>
+__device__ __forceinline__ void hpass(const float* tmp, int ic, const float2 (&g)[R + 1], float* gs) {
+  constexpr int C = (2 + R + 1) & ~1;
+  constexpr int kNS = kGC / kSH;
+  constexpr int kOff = C - 2 - R;  // tmp column of output column 0's first tap (0 or 1)
+  constexpr int kIn = kSH + 2 * R;
+  for (int item = threadIdx.x; item < kRP * kNS; item += kDetThreads) {
+    const int yp = item / kNS;
+    const int c0 = (item - yp * kNS) * kSH;
+    const float2* t = reinterpret_cast<const float2*>(tmp) + (size_t)yp * ic + c0 + kOff;
+    float2 acc[kSH];
+#pragma unroll
+    for (int o = 0; o < kSH; ++o) acc[o] = f2(0.0f, 0.0f);
+    if constexpr (kOff == 0) {
+      // 16-byte loads: two consecutive columns of the row pair
+#pragma unroll
+      for (int j = 0; j < kIn; j += 2) {
+        const float4 v4 = *reinterpret_cast<const float4*>(t + j);
+        const float2 va = f2(v4.x, v4.y), vb = f2(v4.z, v4.w);
+#pragma unroll
+        for (int o = 0; o < kSH; ++o) {
+          const int d = j - o - R;
+          if (d >= -R && d <= R) acc[o] = fma2(g[d < 0 ? -d : d], va, acc[o]);
+          const int d1 = d + 1;
+          if (j + 1 < kIn && d1 >= -R && d1 <= R) acc[o] = fma2(g[d1 < 0 ? -d1 : d1], vb, acc[o]);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < kIn; ++j) {
+        const float2 v = t[j];
+#pragma unroll
+        for (int o = 0; o < kSH; ++o) {
+          const int d = j - o - R;
+          if (d >= -R && d <= R) acc[o] = fma2(g[d < 0 ? -d : d], v, acc[o]);
+        }
+      }
+    }
+    float4* dst = reinterpret_cast<float4*>(gs + ((size_t)yp * kGC + c0) * 2);
+#pragma unroll
+    for (int o = 0; o < kSH; o += 2) dst[o / 2] = make_float4(acc[o].x, acc[o].y, acc[o + 1].x, acc[o + 1].y);
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void level_filter(const float* taps, const float* in, int ic, int rm, int cm,
+                                             float* tmp, float* gs) {
+  float2 g[R + 1];
+#pragma unroll
+  for (int j = 0; j <= R; ++j) g[j] = f2(taps[j], taps[j]);
+  vpass<R>(in, ic, rm, cm, g, tmp);
+  __syncthreads();
+  hpass<R>(tmp, ic, g, gs);
+}
+
+__device__ void filter_dispatch(int R, const float* taps, const float* in, int ic, int rm, int cm, float* tmp,
+                                float* gs) {
+#define CDVS_CASE(r)                                \
+  case r:                                           \
+    level_filter<r>(taps, in, ic, rm, cm, tmp, gs); \
     break;
   switch (R) {
     CDVS_CASE(0) CDVS_CASE(1) CDVS_CASE(2) CDVS_CASE(3) CDVS_CASE(4) CDVS_CASE(5) CDVS_CASE(6)
@@ -119,20 +201,83 @@ __device__ void filter_dispatch(int R, const float* taps, const InT* src, int sp
     CDVS_CASE(13) CDVS_CASE(14) CDVS_CASE(15) CDVS_CASE(16) CDVS_CASE(17) CDVS_CASE(18)
     CDVS_CASE(19) CDVS_CASE(20) CDVS_CASE(21) CDVS_CASE(22) CDVS_CASE(23) CDVS_CASE(24)
     default:
-      break;  // rejected on the host
+      __syncthreads();  // rejected on the host; keep the barrier count uniform
+      break;
   }
 #undef CDVS_CASE
 }
 
-__device__ __forceinline__ void store4(float* d, const float* s) {
-  *reinterpret_cast<float4*>(d) = make_float4(s[0], s[1], s[2], s[3]);
+// gs element (row r, col c) of the row-pair layout
+__device__ __forceinline__ float& gat(float* gs, int r, int c) { return gs[((r >> 1) * kGC + c) * 2 + (r & 1)]; }
+
+// Clamp-to-edge for the Laplacian: columns and rows of the tile that lie
+// outside the image take the value of the nearest image pixel, so the
+// stencil below needs no border cases.
+__device__ __forceinline__ void replicate_borders(float* gs, int W, int H, int tx0, int ty0) {
+  const int xl = -(tx0 - kHalo);            // gs column of x = 0
+  const int xr = (W - 1) - (tx0 - kHalo);   // gs column of x = W - 1
+  const int yt = -(ty0 - kHalo), yb = (H - 1) - (ty0 - kHalo);
+  const bool left = xl > 0, right = xr < kGC - 1, top = yt > 0, bottom = yb < kRows - 1;
+  if (!(left || right || top || bottom)) return;  // uniform over the CTA
+  if (left || right) {
+    for (int i = threadIdx.x; i < kRows * kGC; i += kDetThreads) {
+      const int r = i / kGC, c = i - (i / kGC) * kGC;
+      if (c < xl) gat(gs, r, c) = gat(gs, r, xl);
+      else if (c > xr) gat(gs, r, c) = gat(gs, r, xr);
+    }
+    __syncthreads();
+  }
+  if (top || bottom) {
+    for (int i = threadIdx.x; i < kRows * kGC; i += kDetThreads) {
+      const int r = i / kGC, c = i - (i / kGC) * kGC;
+      if (r < yt) gat(gs, r, c) = gat(gs, yt, c);
+      else if (r > yb) gat(gs, r, c) = gat(gs, yb, c);
+    }
+    __syncthreads();
+  }
 }
-__device__ __forceinline__ void store4(__half* d, const float* s) {
-  __half2 a = __floats2half2_rn(s[0], s[1]);
-  __half2 b = __floats2half2_rn(s[2], s[3]);
+
+// L_{o,k} = s_k^2 * (left + right + up + down - 4 centre) on row pairs; each
+// thread walks one column down kRP / kLG row pairs with a sliding window.
+// (The first and last tile rows of the band get a clamped, unused value.)
+__device__ __forceinline__ void laplacian(const float* gs, float s2k, float* L) {
+  constexpr int kPer = kRP / kLG;
+  const float2 s2 = f2(s2k, s2k), m4 = f2(-4.0f, -4.0f);
+  const float2* g = reinterpret_cast<const float2*>(gs);
+  float2* out = reinterpret_cast<float2*>(L);
+  for (int item = threadIdx.x; item < kLC * kLG; item += kDetThreads) {
+    const int grp = item / kLC;
+    const int c = item - grp * kLC;  // L column c <-> gs column c + 1
+    const int yp0 = grp * kPer;
+    float2 up = g[max(yp0 - 1, 0) * kGC + c + 1];
+    float2 ce = g[yp0 * kGC + c + 1];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int yp = yp0 + k;
+      const float2 dn = g[min(yp + 1, kRP - 1) * kGC + c + 1];
+      const float2 le = g[yp * kGC + c], ri = g[yp * kGC + c + 2];
+      // rows 2yp, 2yp+1: up neighbours (row 2yp-1, row 2yp), down (row 2yp+1, row 2yp+2)
+      const float2 vs = f2(up.y + ce.y, ce.x + dn.x);
+      const float2 t = add2(add2(le, ri), vs);
+      out[yp * kLC + c] = mul2(s2, fma2(m4, ce, t));
+      up = ce;
+      ce = dn;
+    }
+  }
+}
+
+template <typename StoreT>
+__device__ __forceinline__ void store4(StoreT* d, float a, float b, float c, float e);
+template <>
+__device__ __forceinline__ void store4<float>(float* d, float a, float b, float c, float e) {
+  *reinterpret_cast<float4*>(d) = make_float4(a, b, c, e);
+}
+template <>
+__device__ __forceinline__ void store4<__half>(__half* d, float a, float b, float c, float e) {
+  __half2 h0 = __floats2half2_rn(a, b), h1 = __floats2half2_rn(c, e);
   uint2 u;
-  u.x = *reinterpret_cast<unsigned*>(&a);
-  u.y = *reinterpret_cast<unsigned*>(&b);
+  u.x = *reinterpret_cast<unsigned*>(&h0);
+  u.y = *reinterpret_cast<unsigned*>(&h1);
   *reinterpret_cast<uint2*>(d) = u;
 }
 __device__ __forceinline__ void store1(float* d, float v) { *d = v; }
@@ -141,41 +286,165 @@ __device__ __forceinline__ void store1(__half* d, float v) { *d = __float2half_r
 // Tile interior of G_{o,k} -> level storage (4 consecutive x per thread; the
 // row pitch is a multiple of 8 elements, so x + 3 < pitch always holds).
 template <typename StoreT>
-__device__ __forceinline__ void store_level(const float* gs, StoreT* dst, int lpitch, int W, int H,
-                                            int tx0, int ty0) {
+__device__ __forceinline__ void store_level(const float* gs, StoreT* dst, int lpitch, int W, int H, int tx0,
+                                            int ty0) {
   constexpr int kQ = kTX / 4;
   for (int i = threadIdx.x; i < kTY * kQ; i += kDetThreads) {
     const int r = i / kQ;
     const int c = (i - r * kQ) * 4;
     const int y = ty0 + r, x = tx0 + c;
     if (y >= H || x >= W) continue;
-    const float* s = gs + (r + kHalo) * kGP + c + kHalo;
-    float v[4] = {s[0], s[1], s[2], s[3]};
-    store4(dst + (size_t)y * lpitch + x, v);
+    const int gr = r + kHalo, gc = c + kHalo;
+    const float* p = gs + ((gr >> 1) * kGC + gc) * 2 + (gr & 1);
+    store4<StoreT>(dst + (size_t)y * lpitch + x, p[0], p[2], p[4], p[6]);
   }
 }
 
 // Alg. 1: G_{o+1,0}[i][j] = G_{o,K-1}[2i][2j] for the even pixels of this tile.
 template <typename StoreT>
-__device__ __forceinline__ void store_decimated(const float* gs, StoreT* dst, int lpitch1, int W,
-                                                int H, int tx0, int ty0) {
+__device__ __forceinline__ void store_decimated(const float* gs, StoreT* dst, int lpitch1, int W, int H,
+                                                int tx0, int ty0) {
   constexpr int kHX = kTX / 2, kHY = kTY / 2;
   for (int i = threadIdx.x; i < kHX * kHY; i += kDetThreads) {
     const int r = i / kHX;
     const int c = i - r * kHX;
     const int y = ty0 + 2 * r, x = tx0 + 2 * c;
     if (y >= H || x >= W) continue;
-    store1(dst + (size_t)(y >> 1) * lpitch1 + (x >> 1), gs[(2 * r + kHalo) * kGP + 2 * c + kHalo]);
+    // gs row 2r + 2 is the first row of pair r + 1
+    store1(dst + (size_t)(y >> 1) * lpitch1 + (x >> 1), gs[((r + 1) * kGC + 2 * c + kHalo) * 2]);
   }
 }
 
+// L value of tile pixel (ly, lx), ly in -1 .. 32, lx in -1 .. 128, at level k
+__device__ __forceinline__ float Lat(const float* Ls, int k, int ly, int lx) {
+  const int r = ly + kHalo;
+  return Ls[((k * kRP + (r >> 1)) * kLC + lx + 1) * 2 + (r & 1)];
+}
+
+struct Found {
+  float xo, yo, so, resp, pss, ratio;
+  int type;
+};
+
+// S4-S5 for one pixel whose cubic coefficients are `al`; returns true and
+// fills f when the pixel is an interest point.
+__device__ __forceinline__ bool test_pixel(const DetectArgs& a, const float* Ls, const float (&al)[4], int ly,
+                                           int lx, int x, int y, Found& f) {
+  // no t in [t_lo, t_hi] can reach |p| >= T when this bound is below T
+  const float m = fmaxf(-a.t_lo, a.t_hi);
+  const float bound = fabsf(al[0]) + m * (fabsf(al[1]) + m * (fabsf(al[2]) + m * fabsf(al[3])));
+  if (!(bound >= a.T * 0.99999f)) return false;
+  // roots of p'(t) = 3 a3 t^2 + 2 a2 t + a1 in cancellation-free form
+  const float A = 3.0f * al[3], Bq = 2.0f * al[2], C = al[1];
+  float roots[2];
+  int nr = 0;
+  if (A == 0.0f) {
+    if (Bq != 0.0f) roots[nr++] = -C / Bq;
+  } else {
+    const float D = Bq * Bq - 4.0f * A * C;
+    if (!(D > 0.0f)) return false;
+    const float q = -0.5f * (Bq + copysignf(sqrtf(D), Bq));
+    roots[nr++] = q / A;
+    if (q != 0.0f) roots[nr++] = C / q;
+  }
+  int bt = 0;
+  float btv = 0.0f, bv = 0.0f;
+  for (int r = 0; r < nr; ++r) {
+    const float tt = roots[r];
+    if (!(tt >= a.t_lo && tt <= a.t_hi)) continue;
+    const float pdd = 6.0f * al[3] * tt + 2.0f * al[2];
+    if (pdd == 0.0f) continue;
+    const float v = ((al[3] * tt + al[2]) * tt + al[1]) * tt + al[0];
+    if (!(fabsf(v) >= a.T)) continue;
+    if (bt == 0 || fabsf(v) > fabsf(bv) || (fabsf(v) == fabsf(bv) && tt < btv)) {
+      bt = pdd < 0.0f ? 1 : -1;
+      btv = tt;
+      bv = v;
+    }
+  }
+  if (bt == 0) return false;
+  // weights of the K samples in p(t*): w_k = sum_i B[i][k] t*^i
+  float w[kScales];
+#pragma unroll
+  for (int k = 0; k < kScales; ++k)
+    w[k] = fmaf(fmaf(fmaf(a.B[3][k], btv, a.B[2][k]), btv, a.B[1][k]), btv, a.B[0][k]);
+  float q[9];
+#pragma unroll
+  for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx) {
+      float s = 0.0f;
+#pragma unroll
+      for (int k = 0; k < kScales; ++k) s = fmaf(w[k], Lat(Ls, k, ly + dy, lx + dx), s);
+      q[(dy + 1) * 3 + (dx + 1)] = s;
+    }
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    if (j == 4) continue;
+    if (bt > 0 ? !(q[j] < q[4]) : !(q[j] > q[4])) return false;
+  }
+  const float gx = 0.5f * (q[5] - q[3]);
+  const float gy = 0.5f * (q[7] - q[1]);
+  const float hxx = q[5] - 2.0f * q[4] + q[3];
+  const float hyy = q[7] - 2.0f * q[4] + q[1];
+  const float hxy = 0.25f * (q[8] - q[6] - q[2] + q[0]);
+  const float det = hxx * hyy - hxy * hxy;
+  if (!(det > 0.0f)) return false;
+  const float tr = hxx + hyy;
+  const float ratio = tr * tr / det;
+  if (!(ratio < a.edge_lim)) return false;
+  const float ddx = -(hyy * gx - hxy * gy) / det;
+  const float ddy = -(hxx * gy - hxy * gx) / det;
+  if (!(fabsf(ddx) <= a.offset_max && fabsf(ddy) <= a.offset_max)) return false;
+  const float ph = q[4] + 0.5f * (gx * ddx + gy * ddy);
+  if (!(fabsf(ph) >= a.T)) return false;
+  f.xo = (float)x + ddx;
+  f.yo = (float)y + ddy;
+  f.so = a.tc + btv;
+  f.resp = ph;
+  f.pss = 6.0f * al[3] * btv + 2.0f * al[2];
+  f.ratio = ratio;
+  f.type = bt;
+  return true;
+}
+
+// warp-aggregated append to the image's candidate queue (all lanes call it)
+__device__ __forceinline__ void append(const DetectArgs& a, int img, int o, bool found, const Found& f) {
+  const int lane = threadIdx.x & 31;
+  const unsigned m = __ballot_sync(0xffffffffu, found);
+  if (!m) return;
+  const int leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(a.cand_count + img, __popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (!found) return;
+  const int pos = base + __popc(m & ((1u << lane) - 1u));
+  if (pos >= a.cand_cap) {
+    atomicOr(a.status, kStatusCandOverflow);
+    return;
+  }
+  Cand c;
+  c.xo = f.xo;
+  c.yo = f.yo;
+  c.so = f.so;
+  c.resp = f.resp;
+  c.pss = f.pss;
+  c.ratio = f.ratio;
+  c.octave = (short)o;
+  c.type = (short)f.type;
+  c.spare = 0;
+  a.cands[(size_t)img * a.cand_cap + pos] = c;
+}
+
 template <typename InT, typename StoreT>
-__global__ void __launch_bounds__(kDetThreads, 2)
-    detect_kernel(const __grid_constant__ DetectArgs a, int tpitch) {
+__global__ void __launch_bounds__(kDetThreads, 1) detect_kernel(const __grid_constant__ DetectArgs a, int rm) {
   extern __shared__ float4 smem4[];
-  float* tmp = reinterpret_cast<float*>(smem4);
-  float* gs = tmp + kRows * tpitch;
-  float* Ls = gs + kRows * kGP;
+  const int cm = halo_cols(rm);
+  const int ic = kTX + 2 * cm;
+  float* in = reinterpret_cast<float*>(smem4);
+  float* tmp = in + (kRows + 2 * rm) * ic;
+  float* gs = tmp + kRows * ic;
+  float* Ls = gs + kRows * kGC;
 
   // (image, tile) of this CTA: largest i with tile_prefix[i] <= blockIdx.x
   const int b = blockIdx.x;
@@ -196,163 +465,54 @@ __global__ void __launch_bounds__(kDetThreads, 2)
   StoreT* lev = reinterpret_cast<StoreT*>(a.levels) + op.level_off;
   const size_t lstride = (size_t)lpitch * H;
 
-  const InT* src;
-  int spitch;
-  if constexpr (std::is_same<InT, uint8_t>::value) {
-    src = reinterpret_cast<const InT*>(P->src);
-    spitch = P->pitch;
-  } else {
-    src = reinterpret_cast<const InT*>(lev);  // level (o, 0) is the octave base
-    spitch = lpitch;
-  }
+  if constexpr (std::is_same<InT, uint8_t>::value)
+    stage_input<InT>(reinterpret_cast<const InT*>(P->src), P->pitch, W, H, tx0, ty0, rm, cm, in);
+  else
+    stage_input<InT>(reinterpret_cast<const InT*>(lev), lpitch, W, H, tx0, ty0, rm, cm, in);
+  __syncthreads();
 
   for (int k = 0; k < kScales; ++k) {
-    filter_dispatch<InT>(a.radius[k], a.taps[k], src, spitch, W, H, tx0, ty0, tmp, tpitch, gs);
+    filter_dispatch(a.radius[k], a.taps[k], in, ic, rm, cm, tmp, gs);
     __syncthreads();
+    replicate_borders(gs, W, H, tx0, ty0);
     if (k > 0 || a.write_level0) store_level<StoreT>(gs, lev + k * lstride, lpitch, W, H, tx0, ty0);
     if (k == kScales - 1 && o + 1 < P->n_oct) {
       const OctPlan op1 = P->oct[o + 1];
-      store_decimated<StoreT>(gs, reinterpret_cast<StoreT*>(a.levels) + op1.level_off, op1.lpitch,
-                              W, H, tx0, ty0);
+      store_decimated<StoreT>(gs, reinterpret_cast<StoreT*>(a.levels) + op1.level_off, op1.lpitch, W, H, tx0,
+                              ty0);
     }
-    // L_{o,k} = s_k^2 * 5-point Laplacian, clamp-to-edge at the image border
-    const float s2 = a.s2[k];
-    float* Lk = Ls + k * (kLR * kLP);
-    for (int i = threadIdx.x; i < kLR * kLP; i += kDetThreads) {
-      const int ly = i / kLP, lx = i - (i / kLP) * kLP;
-      const int y = ty0 - 1 + ly, x = tx0 - 1 + lx;
-      float L = 0.0f;
-      if (x >= 0 && x < W && y >= 0 && y < H) {
-        const int gr = ly + 1, gc = lx + 1;
-        const int cl = x > 0 ? gc - 1 : gc, cr = x < W - 1 ? gc + 1 : gc;
-        const int ru = y > 0 ? gr - 1 : gr, rd = y < H - 1 ? gr + 1 : gr;
-        const float c = gs[gr * kGP + gc];
-        L = s2 * ((gs[gr * kGP + cl] + gs[gr * kGP + cr]) + (gs[ru * kGP + gc] + gs[rd * kGP + gc]) -
-                  4.0f * c);
-      }
-      Lk[i] = L;
-    }
+    laplacian(gs, a.s2[k], Ls + (size_t)k * kRP * kLC * 2);
     __syncthreads();
   }
 
-  // ---- ALP extremum (Eq. 2-3), 8-neighbour test, refinement (stage B)
-  const int lane = threadIdx.x & 31;
-  Cand* qout = a.cands + (size_t)img * a.cand_cap;
-  for (int it = 0; it < (kTX * kTY) / kDetThreads; ++it) {
+  // ---- per pixel pair (tile rows 2m, 2m+1 are L row pair m + 1): cubic
+  // coefficients of Eq. 3 on packed pairs, then S4-S5 per pixel
+  for (int it = 0; it < (kTX * kTY / 2) / kDetThreads; ++it) {
     const int idx = it * kDetThreads + threadIdx.x;
-    const int ly = idx / kTX, lx = idx - (idx / kTX) * kTX;
-    const int x = tx0 + lx, y = ty0 + ly;
-    bool found = false;
-    Cand c;
-    if (x >= 1 && x < W - 1 && y >= 1 && y < H - 1) {
-      const int li = (ly + 1) * kLP + (lx + 1);
-      float L[kScales];
+    const int m = idx / kTX, lx = idx - (idx / kTX) * kTX;
+    float2 Lk[kScales];
 #pragma unroll
-      for (int k = 0; k < kScales; ++k) L[k] = Ls[k * (kLR * kLP) + li];
-      float al[4];
+    for (int k = 0; k < kScales; ++k) Lk[k] = reinterpret_cast<const float2*>(Ls)[(k * kRP + m + 1) * kLC + lx + 1];
+    float2 al2[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        float s = 0.0f;
+    for (int i = 0; i < 4; ++i) {
+      float2 s = f2(0.0f, 0.0f);
 #pragma unroll
-        for (int k = 0; k < kScales; ++k) s = fmaf(a.B[i][k], L[k], s);
-        al[i] = s;
-      }
-      // roots of p'(t) = 3 a3 t^2 + 2 a2 t + a1 in cancellation-free form
-      const float A = 3.0f * al[3], Bq = 2.0f * al[2], C = al[1];
-      float roots[2];
-      int nr = 0;
-      if (A == 0.0f) {
-        if (Bq != 0.0f) roots[nr++] = -C / Bq;
-      } else {
-        const float D = Bq * Bq - 4.0f * A * C;
-        if (D > 0.0f) {
-          const float q = -0.5f * (Bq + copysignf(sqrtf(D), Bq));
-          roots[nr++] = q / A;
-          if (q != 0.0f) roots[nr++] = C / q;
-        }
-      }
-      int bt = 0;
-      float btv = 0.0f, bv = 0.0f;
-      for (int r = 0; r < nr; ++r) {
-        const float tt = roots[r];
-        if (!(tt >= a.t_lo && tt <= a.t_hi)) continue;
-        const float pdd = 6.0f * al[3] * tt + 2.0f * al[2];
-        if (pdd == 0.0f) continue;
-        const float v = ((al[3] * tt + al[2]) * tt + al[1]) * tt + al[0];
-        if (!(fabsf(v) >= a.T)) continue;
-        if (bt == 0 || fabsf(v) > fabsf(bv) || (fabsf(v) == fabsf(bv) && tt < btv)) {
-          bt = pdd < 0.0f ? 1 : -1;
-          btv = tt;
-          bv = v;
-        }
-      }
-      if (bt != 0) {
-        // weights of the K samples in p(t*): w_k = sum_i B[i][k] t*^i
-        float w[kScales];
-#pragma unroll
-        for (int k = 0; k < kScales; ++k)
-          w[k] = fmaf(fmaf(fmaf(a.B[3][k], btv, a.B[2][k]), btv, a.B[1][k]), btv, a.B[0][k]);
-        float q[9];
-#pragma unroll
-        for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-          for (int dx = -1; dx <= 1; ++dx) {
-            const int lj = li + dy * kLP + dx;
-            float s = 0.0f;
-#pragma unroll
-            for (int k = 0; k < kScales; ++k) s = fmaf(w[k], Ls[k * (kLR * kLP) + lj], s);
-            q[(dy + 1) * 3 + (dx + 1)] = s;
-          }
-        bool ok = true;
-#pragma unroll
-        for (int j = 0; j < 9; ++j) {
-          if (j == 4) continue;
-          if (bt > 0 ? !(q[j] < q[4]) : !(q[j] > q[4])) ok = false;
-        }
-        if (ok) {
-          const float gx = 0.5f * (q[5] - q[3]);
-          const float gy = 0.5f * (q[7] - q[1]);
-          const float hxx = q[5] - 2.0f * q[4] + q[3];
-          const float hyy = q[7] - 2.0f * q[4] + q[1];
-          const float hxy = 0.25f * (q[8] - q[6] - q[2] + q[0]);
-          const float det = hxx * hyy - hxy * hxy;
-          if (det > 0.0f) {
-            const float tr = hxx + hyy;
-            const float ratio = tr * tr / det;
-            if (ratio < a.edge_lim) {
-              const float ddx = -(hyy * gx - hxy * gy) / det;
-              const float ddy = -(hxx * gy - hxy * gx) / det;
-              if (fabsf(ddx) <= a.offset_max && fabsf(ddy) <= a.offset_max) {
-                const float ph = q[4] + 0.5f * (gx * ddx + gy * ddy);
-                if (fabsf(ph) >= a.T) {
-                  c.xo = (float)x + ddx;
-                  c.yo = (float)y + ddy;
-                  c.so = a.tc + btv;
-                  c.resp = ph;
-                  c.pss = 6.0f * al[3] * btv + 2.0f * al[2];
-                  c.ratio = ratio;
-                  c.octave = (short)o;
-                  c.type = (short)bt;
-                  c.spare = 0;
-                  found = true;
-                }
-              }
-            }
-          }
-        }
-      }
+      for (int k = 0; k < kScales; ++k) s = fma2(f2(a.B[i][k], a.B[i][k]), Lk[k], s);
+      al2[i] = s;
     }
-    const unsigned m = __ballot_sync(0xffffffffu, found);
-    if (m) {
-      const int leader = __ffs(m) - 1;
-      int base = 0;
-      if (lane == leader) base = atomicAdd(a.cand_count + img, __popc(m));
-      base = __shfl_sync(0xffffffffu, base, leader);
-      if (found) {
-        const int pos = base + __popc(m & ((1u << lane) - 1u));
-        if (pos < a.cand_cap) qout[pos] = c;
-        else atomicOr(a.status, kStatusCandOverflow);
+    const int x = tx0 + lx;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int ly = 2 * m + h, y = ty0 + ly;
+      Found f;
+      bool found = false;
+      if (x >= 1 && x < W - 1 && y >= 1 && y < H - 1) {
+        const float al[4] = {h ? al2[0].y : al2[0].x, h ? al2[1].y : al2[1].x, h ? al2[2].y : al2[2].x,
+                             h ? al2[3].y : al2[3].x};
+        found = test_pixel(a, Ls, al, ly, lx, x, y, f);
       }
+      append(a, img, o, found, f);
     }
   }
 }
@@ -360,22 +520,21 @@ __global__ void __launch_bounds__(kDetThreads, 2)
 }  // namespace
 
 size_t detect_smem_bytes(int max_radius) {
-  const int tpitch = kTX + 2 * kHalo + 2 * max_radius;
-  return sizeof(float) * ((size_t)kRows * tpitch + (size_t)kRows * kGP + (size_t)kScales * kLR * kLP);
+  const int cm = halo_cols(max_radius);
+  const int ic = kTX + 2 * cm;
+  return sizeof(float) * ((size_t)(kRows + 2 * max_radius) * ic + (size_t)kRows * ic + (size_t)kRows * kGC +
+                          (size_t)kScales * kRows * kLC);
 }
 
-cudaError_t launch_detect(const DetectArgs& a, int n_tiles, int max_radius, int storage,
-                          cudaStream_t s) {
+cudaError_t launch_detect(const DetectArgs& a, int n_tiles, int max_radius, int storage, cudaStream_t s) {
   if (n_tiles <= 0) return cudaSuccess;
-  const int tpitch = kTX + 2 * kHalo + 2 * max_radius;
   const size_t smem = detect_smem_bytes(max_radius);
   cudaError_t e;
-#define CDVS_LAUNCH(IN, ST)                                                                     \
-  do {                                                                                          \
-    e = cudaFuncSetAttribute(detect_kernel<IN, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                             (int)smem);                                                        \
-    if (e != cudaSuccess) return e;                                                             \
-    detect_kernel<IN, ST><<<n_tiles, kDetThreads, smem, s>>>(a, tpitch);                        \
+#define CDVS_LAUNCH(IN, ST)                                                                                   \
+  do {                                                                                                        \
+    e = cudaFuncSetAttribute(detect_kernel<IN, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    if (e != cudaSuccess) return e;                                                                           \
+    detect_kernel<IN, ST><<<n_tiles, kDetThreads, smem, s>>>(a, max_radius);                                  \
   } while (0)
   if (storage == CDVS_STORAGE_FP16) {
     if (a.octave == 0) CDVS_LAUNCH(uint8_t, __half);
