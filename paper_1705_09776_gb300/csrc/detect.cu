@@ -17,11 +17,13 @@
 // 64-bit shared-memory word.
 //
 // Shared memory per CTA (FP32), Rm = largest level radius of the octave,
-// Cm = 2 + Rm rounded up to a multiple of 4:
+// Cm = 16 (Rm <= 14) or 28 (Rm <= 24):
 //   in  [36 + 2 Rm][128 + 2 Cm]   octave base with halo, minus 128 at octave 0
 //   tmp [18][128 + 2 Cm][2]       y-pass result, rows ty0-2 .. ty0+33
 //   gs  [18][132][2]              G_{o,k}, rows ty0-2 .. ty0+33, cols tx0-2 ..
 //   Ls  [4][18][130][2]           L_{o,k}, same rows, cols tx0-1 .. tx0+128
+// After the last level, `in` and `tmp` hold the list of pixels that pass the
+// scale test (phase 1) for the neighbour test and refinement (phase 2).
 #include <type_traits>
 
 #include "cdvs_internal.cuh"
@@ -40,8 +42,6 @@ static_assert(kRows % kSV == 0 && kSV % 2 == 0, "y-pass strips must tile the row
 static_assert(kGC % kSH == 0 && kSH % 2 == 0, "x-pass strips must tile the columns");
 static_assert(kRP % kLG == 0, "Laplacian groups must tile the row pairs");
 static_assert((kTX * kTY / 2) % kDetThreads == 0, "extremum loop must be warp-uniform");
-
-__host__ __device__ constexpr int halo_cols(int rm) { return (2 + rm + 3) & ~3; }
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
@@ -99,9 +99,8 @@ __device__ __forceinline__ void stage_input(const InT* __restrict__ src, int spi
 
 // ---- y pass on column pairs: tmp rows ty0-2 .. ty0+33, columns from
 // x = tx0 - C (C = 2 + R rounded up to even) to tx0 + 128 + C.
-template <int R>
-__device__ __forceinline__ void vpass(const float* in, int ic, int rm, int cm, const float2 (&g)[R + 1],
-                                      float* tmp) {
+template <int R, int ic>
+__device__ __forceinline__ void vpass(const float* in, int rm, int cm, const float2 (&g)[R + 1], float* tmp) {
   constexpr int C = (2 + R + 1) & ~1;
   constexpr int kPairs = (kTX + 2 * C) / 2;
   constexpr int kStrips = kRows / kSV;
@@ -134,8 +133,8 @@ __device__ __forceinline__ void vpass(const float* in, int ic, int rm, int cm, c
 }
 
 // ---- x pass on row pairs: gs[yp][c] (c <-> x = tx0 - 2 + c) from tmp
-template <int R>
-__device__ __forceinline__ void hpass(const float* tmp, int ic, const float2 (&g)[R + 1], float* gs) {
+template <int R, int ic>
+__device__ __forceinline__ void hpass(const float* tmp, const float2 (&g)[R + 1], float* gs) {
   constexpr int C = (2 + R + 1) & ~1;
   constexpr int kNS = kGC / kSH;
   constexpr int kOff = C - 2 - R;  // tmp column of output column 0's first tap (0 or 1)
@@ -162,13 +161,23 @@ __device__ __forceinline__ void hpass(const float* tmp, int ic, const float2 (&g
         }
       }
     } else {
+      // t is 8 bytes past a 16-byte boundary: one 8-byte load, then 16-byte
+      // loads, then one 8-byte load (kIn is even)
+      float2 v[kIn];
+      v[0] = t[0];
+#pragma unroll
+      for (int j = 1; j + 1 < kIn; j += 2) {
+        const float4 v4 = *reinterpret_cast<const float4*>(t + j);
+        v[j] = f2(v4.x, v4.y);
+        v[j + 1] = f2(v4.z, v4.w);
+      }
+      v[kIn - 1] = t[kIn - 1];
 #pragma unroll
       for (int j = 0; j < kIn; ++j) {
-        const float2 v = t[j];
 #pragma unroll
         for (int o = 0; o < kSH; ++o) {
           const int d = j - o - R;
-          if (d >= -R && d <= R) acc[o] = fma2(g[d < 0 ? -d : d], v, acc[o]);
+          if (d >= -R && d <= R) acc[o] = fma2(g[d < 0 ? -d : d], v[j], acc[o]);
         }
       }
     }
@@ -178,22 +187,23 @@ __device__ __forceinline__ void hpass(const float* tmp, int ic, const float2 (&g
   }
 }
 
-template <int R>
-__device__ __forceinline__ void level_filter(const float* taps, const float* in, int ic, int rm, int cm,
-                                             float* tmp, float* gs) {
+template <int R, int ic>
+__device__ __forceinline__ void level_filter(const float* taps, const float* in, int rm, int cm, float* tmp,
+                                             float* gs) {
   float2 g[R + 1];
 #pragma unroll
   for (int j = 0; j <= R; ++j) g[j] = f2(taps[j], taps[j]);
-  vpass<R>(in, ic, rm, cm, g, tmp);
+  vpass<R, ic>(in, rm, cm, g, tmp);
   __syncthreads();
-  hpass<R>(tmp, ic, g, gs);
+  hpass<R, ic>(tmp, g, gs);
 }
 
-__device__ void filter_dispatch(int R, const float* taps, const float* in, int ic, int rm, int cm, float* tmp,
+template <int ic>
+__device__ void filter_dispatch(int R, const float* taps, const float* in, int rm, int cm, float* tmp,
                                 float* gs) {
-#define CDVS_CASE(r)                                \
-  case r:                                           \
-    level_filter<r>(taps, in, ic, rm, cm, tmp, gs); \
+#define CDVS_CASE(r)                                    \
+  case r:                                               \
+    if constexpr (2 + r <= (ic - kTX) / 2) level_filter<r, ic>(taps, in, rm, cm, tmp, gs); \
     break;
   switch (R) {
     CDVS_CASE(0) CDVS_CASE(1) CDVS_CASE(2) CDVS_CASE(3) CDVS_CASE(4) CDVS_CASE(5) CDVS_CASE(6)
@@ -210,28 +220,26 @@ __device__ void filter_dispatch(int R, const float* taps, const float* in, int i
 // gs element (row r, col c) of the row-pair layout
 __device__ __forceinline__ float& gat(float* gs, int r, int c) { return gs[((r >> 1) * kGC + c) * 2 + (r & 1)]; }
 
-// Clamp-to-edge for the Laplacian: columns and rows of the tile that lie
-// outside the image take the value of the nearest image pixel, so the
-// stencil below needs no border cases.
+// Clamp-to-edge for the Laplacian: the column and row just outside the
+// image take the value of the nearest image pixel, so the stencil below
+// needs no border cases (the Laplacian is only used at image pixels).
 __device__ __forceinline__ void replicate_borders(float* gs, int W, int H, int tx0, int ty0) {
-  const int xl = -(tx0 - kHalo);            // gs column of x = 0
-  const int xr = (W - 1) - (tx0 - kHalo);   // gs column of x = W - 1
-  const int yt = -(ty0 - kHalo), yb = (H - 1) - (ty0 - kHalo);
-  const bool left = xl > 0, right = xr < kGC - 1, top = yt > 0, bottom = yb < kRows - 1;
+  const int cl = 1 - tx0;             // gs column of x = -1 (valid when tx0 == 0)
+  const int cr = W - tx0 + kHalo;     // gs column of x = W
+  const int rt = 1 - ty0, rb = H - ty0 + kHalo;
+  const bool left = tx0 == 0, right = cr < kGC, top = ty0 == 0, bottom = rb < kRows;
   if (!(left || right || top || bottom)) return;  // uniform over the CTA
   if (left || right) {
-    for (int i = threadIdx.x; i < kRows * kGC; i += kDetThreads) {
-      const int r = i / kGC, c = i - (i / kGC) * kGC;
-      if (c < xl) gat(gs, r, c) = gat(gs, r, xl);
-      else if (c > xr) gat(gs, r, c) = gat(gs, r, xr);
+    for (int r = threadIdx.x; r < kRows; r += kDetThreads) {
+      if (left) gat(gs, r, cl) = gat(gs, r, cl + 1);
+      if (right) gat(gs, r, cr) = gat(gs, r, cr - 1);
     }
     __syncthreads();
   }
   if (top || bottom) {
-    for (int i = threadIdx.x; i < kRows * kGC; i += kDetThreads) {
-      const int r = i / kGC, c = i - (i / kGC) * kGC;
-      if (r < yt) gat(gs, r, c) = gat(gs, yt, c);
-      else if (r > yb) gat(gs, r, c) = gat(gs, yb, c);
+    for (int c = threadIdx.x; c < kGC; c += kDetThreads) {
+      if (top) gat(gs, rt, c) = gat(gs, rt + 1, c);
+      if (bottom) gat(gs, rb, c) = gat(gs, rb - 1, c);
     }
     __syncthreads();
   }
@@ -266,37 +274,28 @@ __device__ __forceinline__ void laplacian(const float* gs, float s2k, float* L) 
   }
 }
 
-template <typename StoreT>
-__device__ __forceinline__ void store4(StoreT* d, float a, float b, float c, float e);
-template <>
-__device__ __forceinline__ void store4<float>(float* d, float a, float b, float c, float e) {
-  *reinterpret_cast<float4*>(d) = make_float4(a, b, c, e);
-}
-template <>
-__device__ __forceinline__ void store4<__half>(__half* d, float a, float b, float c, float e) {
-  __half2 h0 = __floats2half2_rn(a, b), h1 = __floats2half2_rn(c, e);
-  uint2 u;
-  u.x = *reinterpret_cast<unsigned*>(&h0);
-  u.y = *reinterpret_cast<unsigned*>(&h1);
-  *reinterpret_cast<uint2*>(d) = u;
+__device__ __forceinline__ void store2(float* d, float a, float b) { *reinterpret_cast<float2*>(d) = f2(a, b); }
+__device__ __forceinline__ void store2(__half* d, float a, float b) {
+  *reinterpret_cast<__half2*>(d) = __floats2half2_rn(a, b);
 }
 __device__ __forceinline__ void store1(float* d, float v) { *d = v; }
 __device__ __forceinline__ void store1(__half* d, float v) { *d = __float2half_rn(v); }
 
-// Tile interior of G_{o,k} -> level storage (4 consecutive x per thread; the
-// row pitch is a multiple of 8 elements, so x + 3 < pitch always holds).
+// Tile interior of G_{o,k} -> level storage.  Each thread takes 2 columns of a
+// row pair (one 16-byte shared load) and writes 2 x 2 values; the row pitch is
+// a multiple of 8 elements, so x + 1 < pitch always holds.
 template <typename StoreT>
 __device__ __forceinline__ void store_level(const float* gs, StoreT* dst, int lpitch, int W, int H, int tx0,
                                             int ty0) {
-  constexpr int kQ = kTX / 4;
-  for (int i = threadIdx.x; i < kTY * kQ; i += kDetThreads) {
-    const int r = i / kQ;
-    const int c = (i - r * kQ) * 4;
-    const int y = ty0 + r, x = tx0 + c;
-    if (y >= H || x >= W) continue;
-    const int gr = r + kHalo, gc = c + kHalo;
-    const float* p = gs + ((gr >> 1) * kGC + gc) * 2 + (gr & 1);
-    store4<StoreT>(dst + (size_t)y * lpitch + x, p[0], p[2], p[4], p[6]);
+  constexpr int kQ = kTX / 2;
+  for (int i = threadIdx.x; i < (kTY / 2) * kQ; i += kDetThreads) {
+    const int m = i / kQ;                 // tile rows 2m, 2m+1 = gs row pair m + 1
+    const int c = (i - m * kQ) * 2;       // tile columns c, c+1 = gs columns c+2, c+3
+    const int x = tx0 + c, y = ty0 + 2 * m;
+    if (x >= W || y >= H) continue;
+    const float4 v = *reinterpret_cast<const float4*>(gs + ((m + 1) * kGC + c + kHalo) * 2);
+    store2(dst + (size_t)y * lpitch + x, v.x, v.z);
+    if (y + 1 < H) store2(dst + (size_t)(y + 1) * lpitch + x, v.y, v.w);
   }
 }
 
@@ -310,8 +309,9 @@ __device__ __forceinline__ void store_decimated(const float* gs, StoreT* dst, in
     const int c = i - r * kHX;
     const int y = ty0 + 2 * r, x = tx0 + 2 * c;
     if (y >= H || x >= W) continue;
-    // gs row 2r + 2 is the first row of pair r + 1
-    store1(dst + (size_t)(y >> 1) * lpitch1 + (x >> 1), gs[((r + 1) * kGC + 2 * c + kHalo) * 2]);
+    // tile row 2r is the first row of gs pair r + 1; 16-byte load of columns 2c+2, 2c+3
+    const float4 v = *reinterpret_cast<const float4*>(gs + ((r + 1) * kGC + 2 * c + kHalo) * 2);
+    store1(dst + (size_t)(y >> 1) * lpitch1 + (x >> 1), v.x);
   }
 }
 
@@ -326,31 +326,37 @@ struct Found {
   int type;
 };
 
-// S4-S5 for one pixel whose cubic coefficients are `al`; returns true and
-// fills f when the pixel is an interest point.
-__device__ __forceinline__ bool test_pixel(const DetectArgs& a, const float* Ls, const float (&al)[4], int ly,
-                                           int lx, int x, int y, Found& f) {
+// S4 on one pixel (phase 1): the admissible extremum of the cubic
+// p(t) = a0 + a1 t + a2 t^2 + a3 t^3 with |p| >= T; returns +1 (maximum),
+// -1 (minimum) or 0, and its t.
+__device__ __forceinline__ int cubic_extremum(const DetectArgs& a, const float (&al)[4], float& t_best) {
   // no t in [t_lo, t_hi] can reach |p| >= T when this bound is below T
   const float m = fmaxf(-a.t_lo, a.t_hi);
   const float bound = fabsf(al[0]) + m * (fabsf(al[1]) + m * (fabsf(al[2]) + m * fabsf(al[3])));
-  if (!(bound >= a.T * 0.99999f)) return false;
+  if (!(bound >= a.T * 0.99999f)) return 0;
   // roots of p'(t) = 3 a3 t^2 + 2 a2 t + a1 in cancellation-free form
   const float A = 3.0f * al[3], Bq = 2.0f * al[2], C = al[1];
-  float roots[2];
-  int nr = 0;
+  float r0, r1;
+  int nr;
   if (A == 0.0f) {
-    if (Bq != 0.0f) roots[nr++] = -C / Bq;
+    if (Bq == 0.0f) return 0;
+    r0 = -C / Bq;
+    r1 = r0;
+    nr = 1;
   } else {
     const float D = Bq * Bq - 4.0f * A * C;
-    if (!(D > 0.0f)) return false;
+    if (!(D > 0.0f)) return 0;
     const float q = -0.5f * (Bq + copysignf(sqrtf(D), Bq));
-    roots[nr++] = q / A;
-    if (q != 0.0f) roots[nr++] = C / q;
+    r0 = q / A;
+    r1 = q != 0.0f ? C / q : r0;
+    nr = q != 0.0f ? 2 : 1;
   }
   int bt = 0;
   float btv = 0.0f, bv = 0.0f;
-  for (int r = 0; r < nr; ++r) {
-    const float tt = roots[r];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    if (r >= nr) break;
+    const float tt = r == 0 ? r0 : r1;
     if (!(tt >= a.t_lo && tt <= a.t_hi)) continue;
     const float pdd = 6.0f * al[3] * tt + 2.0f * al[2];
     if (pdd == 0.0f) continue;
@@ -362,7 +368,14 @@ __device__ __forceinline__ bool test_pixel(const DetectArgs& a, const float* Ls,
       bv = v;
     }
   }
-  if (bt == 0) return false;
+  t_best = btv;
+  return bt;
+}
+
+// 8-neighbour test at the centre's t* and refinement (Alg. 1 stage B) for
+// a pixel that passed phase 1 (phase 2).
+__device__ __forceinline__ bool refine_pixel(const DetectArgs& a, const float* Ls, int ly, int lx, int bt,
+                                             float btv, int x, int y, Found& f) {
   // weights of the K samples in p(t*): w_k = sum_i B[i][k] t*^i
   float w[kScales];
 #pragma unroll
@@ -398,11 +411,19 @@ __device__ __forceinline__ bool test_pixel(const DetectArgs& a, const float* Ls,
   if (!(fabsf(ddx) <= a.offset_max && fabsf(ddy) <= a.offset_max)) return false;
   const float ph = q[4] + 0.5f * (gx * ddx + gy * ddy);
   if (!(fabsf(ph) >= a.T)) return false;
+  // p''(t*) = 6 a3 t* + 2 a2 from the centre's samples
+  float a2 = 0.0f, a3 = 0.0f;
+#pragma unroll
+  for (int k = 0; k < kScales; ++k) {
+    const float L = Lat(Ls, k, ly, lx);
+    a2 = fmaf(a.B[2][k], L, a2);
+    a3 = fmaf(a.B[3][k], L, a3);
+  }
   f.xo = (float)x + ddx;
   f.yo = (float)y + ddy;
   f.so = a.tc + btv;
   f.resp = ph;
-  f.pss = 6.0f * al[3] * btv + 2.0f * al[2];
+  f.pss = 6.0f * a3 * btv + 2.0f * a2;
   f.ratio = ratio;
   f.type = bt;
   return true;
@@ -436,11 +457,17 @@ __device__ __forceinline__ void append(const DetectArgs& a, int img, int o, bool
   a.cands[(size_t)img * a.cand_cap + pos] = c;
 }
 
-template <typename InT, typename StoreT>
+// Phase-1 survivors of a tile: packed (ly, lx, type) and t*.
+struct Pending {
+  int code;  // ly << 16 | lx << 1 | (type > 0)
+  float t;
+};
+
+template <typename InT, typename StoreT, int ic>
 __global__ void __launch_bounds__(kDetThreads, 1) detect_kernel(const __grid_constant__ DetectArgs a, int rm) {
   extern __shared__ float4 smem4[];
-  const int cm = halo_cols(rm);
-  const int ic = kTX + 2 * cm;
+  __shared__ int n_pending;
+  const int cm = (ic - kTX) / 2;
   float* in = reinterpret_cast<float*>(smem4);
   float* tmp = in + (kRows + 2 * rm) * ic;
   float* gs = tmp + kRows * ic;
@@ -469,10 +496,11 @@ __global__ void __launch_bounds__(kDetThreads, 1) detect_kernel(const __grid_con
     stage_input<InT>(reinterpret_cast<const InT*>(P->src), P->pitch, W, H, tx0, ty0, rm, cm, in);
   else
     stage_input<InT>(reinterpret_cast<const InT*>(lev), lpitch, W, H, tx0, ty0, rm, cm, in);
+  if (threadIdx.x == 0) n_pending = 0;
   __syncthreads();
 
   for (int k = 0; k < kScales; ++k) {
-    filter_dispatch(a.radius[k], a.taps[k], in, ic, rm, cm, tmp, gs);
+    filter_dispatch<ic>(a.radius[k], a.taps[k], in, rm, cm, tmp, gs);
     __syncthreads();
     replicate_borders(gs, W, H, tx0, ty0);
     if (k > 0 || a.write_level0) store_level<StoreT>(gs, lev + k * lstride, lpitch, W, H, tx0, ty0);
@@ -485,8 +513,11 @@ __global__ void __launch_bounds__(kDetThreads, 1) detect_kernel(const __grid_con
     __syncthreads();
   }
 
-  // ---- per pixel pair (tile rows 2m, 2m+1 are L row pair m + 1): cubic
-  // coefficients of Eq. 3 on packed pairs, then S4-S5 per pixel
+  // ---- phase 1, per pixel pair (tile rows 2m, 2m+1 are L row pair m + 1):
+  // cubic coefficients of Eq. 3 on packed pairs, then the admissible
+  // extremum in scale; survivors are compacted into `in` (no longer needed)
+  Pending* pend = reinterpret_cast<Pending*>(in);
+  const int lane = threadIdx.x & 31;
   for (int it = 0; it < (kTX * kTY / 2) / kDetThreads; ++it) {
     const int idx = it * kDetThreads + threadIdx.x;
     const int m = idx / kTX, lx = idx - (idx / kTX) * kTX;
@@ -505,44 +536,81 @@ __global__ void __launch_bounds__(kDetThreads, 1) detect_kernel(const __grid_con
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int ly = 2 * m + h, y = ty0 + ly;
-      Found f;
-      bool found = false;
+      int bt = 0;
+      float tb = 0.0f;
       if (x >= 1 && x < W - 1 && y >= 1 && y < H - 1) {
         const float al[4] = {h ? al2[0].y : al2[0].x, h ? al2[1].y : al2[1].x, h ? al2[2].y : al2[2].x,
                              h ? al2[3].y : al2[3].x};
-        found = test_pixel(a, Ls, al, ly, lx, x, y, f);
+        bt = cubic_extremum(a, al, tb);
       }
-      append(a, img, o, found, f);
+      const unsigned msk = __ballot_sync(0xffffffffu, bt != 0);
+      if (msk) {
+        const int leader = __ffs(msk) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(&n_pending, __popc(msk));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (bt != 0) {
+          Pending e;
+          e.code = (ly << 16) | (lx << 1) | (bt > 0 ? 1 : 0);
+          e.t = tb;
+          pend[base + __popc(msk & ((1u << lane) - 1u))] = e;
+        }
+      }
     }
+  }
+  __syncthreads();
+
+  // ---- phase 2: neighbour test and refinement of the survivors, densely
+  const int np = n_pending;
+  const int rounds = (np + kDetThreads - 1) / kDetThreads;
+  for (int r = 0; r < rounds; ++r) {
+    const int i = r * kDetThreads + threadIdx.x;
+    Found f;
+    bool found = false;
+    if (i < np) {
+      const Pending e = pend[i];
+      const int ly = e.code >> 16, lx = (e.code >> 1) & 0x7fff;
+      found = refine_pixel(a, Ls, ly, lx, (e.code & 1) ? 1 : -1, e.t, tx0 + lx, ty0 + ly, f);
+    }
+    append(a, img, o, found, f);
   }
 }
 
 }  // namespace
 
+// The input tile pitch: 128 + 2 Cm columns for radii up to 14 and up to 24.
+static int tile_pitch(int max_radius) { return max_radius <= 14 ? 160 : 184; }
+
 size_t detect_smem_bytes(int max_radius) {
-  const int cm = halo_cols(max_radius);
-  const int ic = kTX + 2 * cm;
+  const int ic = tile_pitch(max_radius);
   return sizeof(float) * ((size_t)(kRows + 2 * max_radius) * ic + (size_t)kRows * ic + (size_t)kRows * kGC +
                           (size_t)kScales * kRows * kLC);
 }
 
 cudaError_t launch_detect(const DetectArgs& a, int n_tiles, int max_radius, int storage, cudaStream_t s) {
   if (n_tiles <= 0) return cudaSuccess;
+  if (max_radius > kMaxRadius) return cudaErrorInvalidValue;
   const size_t smem = detect_smem_bytes(max_radius);
   cudaError_t e;
-#define CDVS_LAUNCH(IN, ST)                                                                                   \
-  do {                                                                                                        \
-    e = cudaFuncSetAttribute(detect_kernel<IN, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-    if (e != cudaSuccess) return e;                                                                           \
-    detect_kernel<IN, ST><<<n_tiles, kDetThreads, smem, s>>>(a, max_radius);                                  \
+#define CDVS_LAUNCH(IN, ST, IC)                                                                                   \
+  do {                                                                                                            \
+    e = cudaFuncSetAttribute(detect_kernel<IN, ST, IC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    if (e != cudaSuccess) return e;                                                                               \
+    detect_kernel<IN, ST, IC><<<n_tiles, kDetThreads, smem, s>>>(a, max_radius);                                  \
+  } while (0)
+#define CDVS_LAUNCH_IC(IN, ST)                                  \
+  do {                                                          \
+    if (tile_pitch(max_radius) == 160) CDVS_LAUNCH(IN, ST, 160); \
+    else CDVS_LAUNCH(IN, ST, 184);                              \
   } while (0)
   if (storage == CDVS_STORAGE_FP16) {
-    if (a.octave == 0) CDVS_LAUNCH(uint8_t, __half);
-    else CDVS_LAUNCH(__half, __half);
+    if (a.octave == 0) CDVS_LAUNCH_IC(uint8_t, __half);
+    else CDVS_LAUNCH_IC(__half, __half);
   } else {
-    if (a.octave == 0) CDVS_LAUNCH(uint8_t, float);
-    else CDVS_LAUNCH(float, float);
+    if (a.octave == 0) CDVS_LAUNCH_IC(uint8_t, float);
+    else CDVS_LAUNCH_IC(float, float);
   }
+#undef CDVS_LAUNCH_IC
 #undef CDVS_LAUNCH
   return cudaGetLastError();
 }
