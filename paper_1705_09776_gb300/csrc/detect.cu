@@ -61,19 +61,36 @@ __device__ __forceinline__ void stage_input(const InT* __restrict__ src, int spi
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int kWarps = kDetThreads / 32;
   const bool interior_x = x0 >= 0 && x0 + IC <= W;
+  constexpr int kMaxQ = 2;              // 16-byte row chunks per lane: IC / 4 <= 64
+  constexpr int kMaxRows = (kRows + 2 * kMaxRadius + kWarps - 1) / kWarps;
   if constexpr (std::is_same<InT, uint8_t>::value) {
-    // four bytes per load where the row start and pitch allow it
+    // four bytes per load where the row start and pitch allow it; every load
+    // of the thread is issued before the first conversion
     const bool vec = interior_x && ((spitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(src) & 3) == 0);
     if (vec) {
       const int q = IC / 4;
-      for (int r = warp; r < IR; r += kWarps) {
+      uchar4 b[kMaxRows][kMaxQ];
+#pragma unroll
+      for (int i = 0; i < kMaxRows; ++i) {
+        const int r = warp + i * kWarps;
         const int y = min(max(y0 + r, 0), H - 1);
         const uchar4* row = reinterpret_cast<const uchar4*>(src + (size_t)y * spitch + x0);
-        float4* dst = reinterpret_cast<float4*>(in + r * IC);
-        for (int c = lane; c < q; c += 32) {
-          const uchar4 b = __ldg(row + c);
-          dst[c] = make_float4((float)b.x - 128.0f, (float)b.y - 128.0f, (float)b.z - 128.0f,
-                               (float)b.w - 128.0f);
+#pragma unroll
+        for (int j = 0; j < kMaxQ; ++j) {
+          const int c = lane + 32 * j;
+          if (r < IR && c < q) b[i][j] = __ldg(row + c);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < kMaxRows; ++i) {
+        const int r = warp + i * kWarps;
+#pragma unroll
+        for (int j = 0; j < kMaxQ; ++j) {
+          const int c = lane + 32 * j;
+          if (r < IR && c < q)
+            reinterpret_cast<float4*>(in + r * IC)[c] =
+                make_float4((float)b[i][j].x - 128.0f, (float)b[i][j].y - 128.0f, (float)b[i][j].z - 128.0f,
+                            (float)b[i][j].w - 128.0f);
         }
       }
       return;
@@ -81,11 +98,26 @@ __device__ __forceinline__ void stage_input(const InT* __restrict__ src, int spi
   } else if constexpr (std::is_same<InT, float>::value) {
     if (interior_x) {  // rows are 16-byte aligned (pitch multiple of 8, x0 multiple of 4)
       const int q = IC / 4;
-      for (int r = warp; r < IR; r += kWarps) {
+      float4 b[kMaxRows][kMaxQ];
+#pragma unroll
+      for (int i = 0; i < kMaxRows; ++i) {
+        const int r = warp + i * kWarps;
         const int y = min(max(y0 + r, 0), H - 1);
         const float4* row = reinterpret_cast<const float4*>(src + (size_t)y * spitch + x0);
-        float4* dst = reinterpret_cast<float4*>(in + r * IC);
-        for (int c = lane; c < q; c += 32) dst[c] = __ldg(row + c);
+#pragma unroll
+        for (int j = 0; j < kMaxQ; ++j) {
+          const int c = lane + 32 * j;
+          if (r < IR && c < q) b[i][j] = __ldg(row + c);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < kMaxRows; ++i) {
+        const int r = warp + i * kWarps;
+#pragma unroll
+        for (int j = 0; j < kMaxQ; ++j) {
+          const int c = lane + 32 * j;
+          if (r < IR && c < q) reinterpret_cast<float4*>(in + r * IC)[c] = b[i][j];
+        }
       }
       return;
     }
@@ -315,61 +347,85 @@ __device__ __forceinline__ void store_decimated(const float* gs, StoreT* dst, in
   }
 }
 
-// L value of tile pixel (ly, lx), ly in -1 .. 32, lx in -1 .. 128, at level k
-__device__ __forceinline__ float Lat(const float* Ls, int k, int ly, int lx) {
-  const int r = ly + kHalo;
-  return Ls[((k * kRP + (r >> 1)) * kLC + lx + 1) * 2 + (r & 1)];
-}
-
 struct Found {
   float xo, yo, so, resp, pss, ratio;
   int type;
 };
 
-// S4 on one pixel (phase 1): the admissible extremum of the cubic
-// p(t) = a0 + a1 t + a2 t^2 + a3 t^3 with |p| >= T; returns +1 (maximum),
-// -1 (minimum) or 0, and its t.
-__device__ __forceinline__ int cubic_extremum(const DetectArgs& a, const float (&al)[4], float& t_best) {
+__device__ __forceinline__ float2 abs2(float2 v) { return f2(fabsf(v.x), fabsf(v.y)); }
+__device__ __forceinline__ float2 rcp2(float2 v) { return f2(__frcp_rn(v.x), __frcp_rn(v.y)); }
+
+// S4 on a pair of pixels (phase 1): for each pixel, the admissible extremum
+// of the cubic p(t) = a0 + a1 t + a2 t^2 + a3 t^3 with |p| >= T.  The roots of
+// p'(t) = 3 a3 t^2 + 2 a2 t + a1 come from the cancellation-free form
+// q = -(B + sign(B) sqrt(D)) / 2, t = q / A and C / q; when both are admissible
+// the larger |p| wins (ties: the smaller t).  bt = +1 maximum, -1 minimum, 0.
+__device__ __forceinline__ void cubic_extremum2(const DetectArgs& a, const float2 (&al)[4], bool live0,
+                                                bool live1, int (&bt)[2], float (&tb)[2]) {
+  bt[0] = bt[1] = 0;
+  tb[0] = tb[1] = 0.0f;
   // no t in [t_lo, t_hi] can reach |p| >= T when this bound is below T
-  const float m = fmaxf(-a.t_lo, a.t_hi);
-  const float bound = fabsf(al[0]) + m * (fabsf(al[1]) + m * (fabsf(al[2]) + m * fabsf(al[3])));
-  if (!(bound >= a.T * 0.99999f)) return 0;
-  // roots of p'(t) = 3 a3 t^2 + 2 a2 t + a1 in cancellation-free form
-  const float A = 3.0f * al[3], Bq = 2.0f * al[2], C = al[1];
-  float r0, r1;
-  int nr;
-  if (A == 0.0f) {
-    if (Bq == 0.0f) return 0;
-    r0 = -C / Bq;
-    r1 = r0;
-    nr = 1;
-  } else {
-    const float D = Bq * Bq - 4.0f * A * C;
-    if (!(D > 0.0f)) return 0;
-    const float q = -0.5f * (Bq + copysignf(sqrtf(D), Bq));
-    r0 = q / A;
-    r1 = q != 0.0f ? C / q : r0;
-    nr = q != 0.0f ? 2 : 1;
-  }
-  int bt = 0;
-  float btv = 0.0f, bv = 0.0f;
+  const float mm = fmaxf(-a.t_lo, a.t_hi);
+  const float2 m2 = f2(mm, mm);
+  const float2 bound = add2(abs2(al[0]), mul2(m2, add2(abs2(al[1]), mul2(m2, fma2(m2, abs2(al[3]), abs2(al[2]))))));
+  const float Tb = a.T * 0.99999f;
+  const bool go0 = live0 && bound.x >= Tb, go1 = live1 && bound.y >= Tb;
+  if (!(go0 || go1)) return;
+  const float2 A = mul2(f2(3.0f, 3.0f), al[3]), Bq = mul2(f2(2.0f, 2.0f), al[2]), C = al[1];
+  const float2 D = fma2(mul2(f2(-4.0f, -4.0f), A), C, mul2(Bq, Bq));
+  const float2 sq = f2(sqrtf(fmaxf(D.x, 0.0f)), sqrtf(fmaxf(D.y, 0.0f)));
+  const float2 q = mul2(f2(-0.5f, -0.5f), add2(Bq, f2(copysignf(sq.x, Bq.x), copysignf(sq.y, Bq.y))));
+  const float2 r0 = mul2(q, rcp2(A));
+  const float2 r1 = mul2(C, rcp2(q));
+  const float2 six_a3 = mul2(f2(6.0f, 6.0f), al[3]);
+  const float2 two_a2 = mul2(f2(2.0f, 2.0f), al[2]);
+  // p'' and p at both roots, both pixels
+  const float2 pdd0 = fma2(six_a3, r0, two_a2), pdd1 = fma2(six_a3, r1, two_a2);
+  const float2 v0 = fma2(fma2(fma2(al[3], r0, al[2]), r0, al[1]), r0, al[0]);
+  const float2 v1 = fma2(fma2(fma2(al[3], r1, al[2]), r1, al[1]), r1, al[0]);
 #pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    if (r >= nr) break;
-    const float tt = r == 0 ? r0 : r1;
-    if (!(tt >= a.t_lo && tt <= a.t_hi)) continue;
-    const float pdd = 6.0f * al[3] * tt + 2.0f * al[2];
-    if (pdd == 0.0f) continue;
-    const float v = ((al[3] * tt + al[2]) * tt + al[1]) * tt + al[0];
-    if (!(fabsf(v) >= a.T)) continue;
-    if (bt == 0 || fabsf(v) > fabsf(bv) || (fabsf(v) == fabsf(bv) && tt < btv)) {
-      bt = pdd < 0.0f ? 1 : -1;
-      btv = tt;
-      bv = v;
+  for (int h = 0; h < 2; ++h) {
+    if (!(h ? go1 : go0)) continue;
+    const float Ah = h ? A.y : A.x, Bh = h ? Bq.y : Bq.x, Ch = h ? C.y : C.x;
+    const float Dh = h ? D.y : D.x, qh = h ? q.y : q.x;
+    float t0, t1, p0, p1, s0, s1;
+    int nr;
+    if (Ah == 0.0f) {  // quadratic p: the single root of the linear derivative
+      if (Bh == 0.0f) continue;
+      t0 = -Ch / Bh;
+      s0 = h ? two_a2.y : two_a2.x;
+      p0 = h ? fmaf(fmaf(fmaf(al[3].y, t0, al[2].y), t0, al[1].y), t0, al[0].y)
+             : fmaf(fmaf(fmaf(al[3].x, t0, al[2].x), t0, al[1].x), t0, al[0].x);
+      t1 = p1 = s1 = 0.0f;
+      nr = 1;
+    } else {
+      if (!(Dh > 0.0f)) continue;
+      t0 = h ? r0.y : r0.x;
+      p0 = h ? v0.y : v0.x;
+      s0 = h ? pdd0.y : pdd0.x;
+      t1 = h ? r1.y : r1.x;
+      p1 = h ? v1.y : v1.x;
+      s1 = h ? pdd1.y : pdd1.x;
+      nr = qh != 0.0f ? 2 : 1;
     }
+    int best = 0;
+    float bt_t = 0.0f, bv = 0.0f;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      if (r >= nr) break;
+      const float tt = r ? t1 : t0, v = r ? p1 : p0, pdd = r ? s1 : s0;
+      if (!(tt >= a.t_lo && tt <= a.t_hi)) continue;
+      if (pdd == 0.0f) continue;
+      if (!(fabsf(v) >= a.T)) continue;
+      if (best == 0 || fabsf(v) > fabsf(bv) || (fabsf(v) == fabsf(bv) && tt < bt_t)) {
+        best = pdd < 0.0f ? 1 : -1;
+        bt_t = tt;
+        bv = v;
+      }
+    }
+    bt[h] = best;
+    tb[h] = bt_t;
   }
-  t_best = btv;
-  return bt;
 }
 
 // 8-neighbour test at the centre's t* and refinement (Alg. 1 stage B) for
@@ -381,16 +437,25 @@ __device__ __forceinline__ bool refine_pixel(const DetectArgs& a, const float* L
 #pragma unroll
   for (int k = 0; k < kScales; ++k)
     w[k] = fmaf(fmaf(fmaf(a.B[3][k], btv, a.B[2][k]), btv, a.B[1][k]), btv, a.B[0][k]);
-  float q[9];
+  // one address per neighbour row; level and column offsets are constants
+  constexpr int kLevel = kRP * kLC * 2;
+  float q[9], Lc[kScales];
 #pragma unroll
-  for (int dy = -1; dy <= 1; ++dy)
+  for (int dy = -1; dy <= 1; ++dy) {
+    const int r = ly + kHalo + dy;
+    const float* row = Ls + ((r >> 1) * kLC + lx + 1) * 2 + (r & 1);
 #pragma unroll
     for (int dx = -1; dx <= 1; ++dx) {
       float s = 0.0f;
 #pragma unroll
-      for (int k = 0; k < kScales; ++k) s = fmaf(w[k], Lat(Ls, k, ly + dy, lx + dx), s);
+      for (int k = 0; k < kScales; ++k) {
+        const float L = row[k * kLevel + 2 * dx];
+        if (dx == 0 && dy == 0) Lc[k] = L;
+        s = fmaf(w[k], L, s);
+      }
       q[(dy + 1) * 3 + (dx + 1)] = s;
     }
+  }
 #pragma unroll
   for (int j = 0; j < 9; ++j) {
     if (j == 4) continue;
@@ -415,9 +480,8 @@ __device__ __forceinline__ bool refine_pixel(const DetectArgs& a, const float* L
   float a2 = 0.0f, a3 = 0.0f;
 #pragma unroll
   for (int k = 0; k < kScales; ++k) {
-    const float L = Lat(Ls, k, ly, lx);
-    a2 = fmaf(a.B[2][k], L, a2);
-    a3 = fmaf(a.B[3][k], L, a3);
+    a2 = fmaf(a.B[2][k], Lc[k], a2);
+    a3 = fmaf(a.B[3][k], Lc[k], a3);
   }
   f.xo = (float)x + ddx;
   f.yo = (float)y + ddy;
@@ -532,27 +596,23 @@ __global__ void __launch_bounds__(kDetThreads, 1) detect_kernel(const __grid_con
       for (int k = 0; k < kScales; ++k) s = fma2(f2(a.B[i][k], a.B[i][k]), Lk[k], s);
       al2[i] = s;
     }
-    const int x = tx0 + lx;
+    const int x = tx0 + lx, y0 = ty0 + 2 * m;
+    const bool inx = x >= 1 && x < W - 1;
+    int bt[2];
+    float tb[2];
+    cubic_extremum2(a, al2, inx && y0 >= 1 && y0 < H - 1, inx && y0 + 1 >= 1 && y0 + 1 < H - 1, bt, tb);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int ly = 2 * m + h, y = ty0 + ly;
-      int bt = 0;
-      float tb = 0.0f;
-      if (x >= 1 && x < W - 1 && y >= 1 && y < H - 1) {
-        const float al[4] = {h ? al2[0].y : al2[0].x, h ? al2[1].y : al2[1].x, h ? al2[2].y : al2[2].x,
-                             h ? al2[3].y : al2[3].x};
-        bt = cubic_extremum(a, al, tb);
-      }
-      const unsigned msk = __ballot_sync(0xffffffffu, bt != 0);
+      const unsigned msk = __ballot_sync(0xffffffffu, bt[h] != 0);
       if (msk) {
         const int leader = __ffs(msk) - 1;
         int base = 0;
         if (lane == leader) base = atomicAdd(&n_pending, __popc(msk));
         base = __shfl_sync(0xffffffffu, base, leader);
-        if (bt != 0) {
+        if (bt[h] != 0) {
           Pending e;
-          e.code = (ly << 16) | (lx << 1) | (bt > 0 ? 1 : 0);
-          e.t = tb;
+          e.code = ((2 * m + h) << 16) | (lx << 1) | (bt[h] > 0 ? 1 : 0);
+          e.t = tb[h];
           pend[base + __popc(msk & ((1u << lane) - 1u))] = e;
         }
       }
