@@ -349,7 +349,7 @@ cdvs_status run_detect(cdvs_ctx* c, int n, const cdvs_params& p, int max_oct, in
       maxr = std::max(maxr, a.radius[k]);
     }
     const int n_tiles = c->h_prefix[(size_t)o * (n + 1) + n];
-    if ((e = launch_detect(a, n_tiles, maxr, p.storage, s)) != cudaSuccess) return cuda_fail(c, e, "detect launch");
+    if ((e = launch_detect(a, n_tiles, maxr, p.storage, c->n_sms, s)) != cudaSuccess) return cuda_fail(c, e, "detect launch");
   }
   return CDVS_OK;
 }
@@ -381,6 +381,10 @@ DescribeArgs describe_args(cdvs_ctx* c, int n, const cdvs_params& p) {
 }
 
 cdvs_status map_status(cdvs_ctx* c, int st) {
+  if (st & kStatusTimeout) {
+    c->err = "a bounded device-side wait gave up (asynchronous copy did not complete)";
+    return CDVS_DEVICE_TIMEOUT;
+  }
   if (st & (kStatusCandOverflow | kStatusSelectOverflow | kStatusOutTruncated)) {
     std::string m;
     if (st & kStatusCandOverflow) m += "candidate queue full; ";

@@ -29,6 +29,7 @@ constexpr int kHalo = 2;         // 1 px for the Laplacian + 1 px for the 8-neig
 constexpr int kStatusCandOverflow = 1;
 constexpr int kStatusSelectOverflow = 2;
 constexpr int kStatusOutTruncated = 4;
+constexpr int kStatusTimeout = 8;        // a bounded device-side wait gave up
 
 // ---------------------------------------------------------------- plans
 // Level (o, k) of an image is stored at level_base + oct[o].level_off +
@@ -121,7 +122,7 @@ struct DescribeArgs {
 
 // launchers (defined in the .cu files)
 size_t detect_smem_bytes(int max_radius);
-cudaError_t launch_detect(const DetectArgs& a, int n_tiles, int max_radius, int storage,
+cudaError_t launch_detect(const DetectArgs& a, int n_tiles, int max_radius, int storage, int n_sms,
                           cudaStream_t s);
 cudaError_t launch_select(const SelectArgs& a, int n_images, cudaStream_t s);
 cudaError_t launch_orient(const DescribeArgs& a, int storage, cudaStream_t s);

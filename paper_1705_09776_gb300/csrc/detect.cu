@@ -1,27 +1,34 @@
 // detect.cu -- K1: one octave of interest point detection for a batch of
-// images, fused in one CTA per 128x32 output tile:
+// images.  A persistent CTA per SM walks over 128x32 output tiles; for each
+// tile it computes, fused in shared memory:
 //   Gaussian levels G_{o,k} (Eq. 1, Alg. 1 stage A: a pass along y then a
 //   pass along x, every level filtered directly from the octave base),
 //   scale-normalised 5-point LoG L_{o,k}, the per-pixel cubic in sigma of
 //   Eq. 2-3, its extremum scale, the 8-neighbour test, the sub-pixel
-//   refinement of Alg. 1 stage B, and warp-aggregated appends to the image's
-//   candidate queue.  The same CTA stores its tile of every level (for
-//   description) and, on the top level, the decimated base of the next octave
-//   (Alg. 1: Downsampling G_{o,K-1} to G_{o+1,0}).
+//   refinement of Alg. 1 stage B, and appends to the image's candidate queue.
+// The same CTA stores its tile of every level (for description) and, on the
+// top level, the decimated base of the next octave (Alg. 1: Downsampling
+// G_{o,K-1} to G_{o+1,0}).
+//
+// While a tile is processed, the rows of the next tile's input are already
+// on their way into shared memory through bulk asynchronous copies
+// (cp.async.bulk, completion on an mbarrier), so global-memory latency
+// overlaps the arithmetic.
 //
 // The filters run on packed FP32 pairs (fma.rn.f32x2: two independent
 // round-to-nearest FMAs per instruction): the y pass on pairs of adjacent
 // columns, the x pass on pairs of adjacent rows.  Intermediate images are kept
 // "row-pair interleaved" -- element (y, x) of a band starting at row y0 sits at
-// [(y - y0) / 2][x][(y - y0) % 2] -- so that every operand pair is one aligned
+// [(y - y0) / 2][x][(y - y0) % 2] -- so every operand pair is one aligned
 // 64-bit shared-memory word.
 //
-// Shared memory per CTA (FP32), Rm = largest level radius of the octave,
-// Cm = 16 (Rm <= 14) or 28 (Rm <= 24):
-//   in  [36 + 2 Rm][128 + 2 Cm]   octave base with halo, minus 128 at octave 0
-//   tmp [18][128 + 2 Cm][2]       y-pass result, rows ty0-2 .. ty0+33
-//   gs  [18][132][2]              G_{o,k}, rows ty0-2 .. ty0+33, cols tx0-2 ..
-//   Ls  [4][18][130][2]           L_{o,k}, same rows, cols tx0-1 .. tx0+128
+// Shared memory per CTA, Rm = largest level radius of the octave (<= 14 or
+// <= 24), IC = 160 or 184 columns, IR = 36 + 2 Rm rows:
+//   raw [IR][IC]            next tile's input as stored (u8 or FP32 / FP16)
+//   in  [IR][IC]            this tile's input in FP32 (minus 128 at octave 0)
+//   tmp [18][IC][2]         y-pass result, rows ty0-2 .. ty0+33
+//   gs  [18][132][2]        G_{o,k}, rows ty0-2 .. ty0+33, cols tx0-2 ..
+//   Ls  [4][18][130][2]     L_{o,k}, same rows, cols tx0-1 .. tx0+128
 // After the last level, `in` and `tmp` hold the list of pixels that pass the
 // scale test (phase 1) for the neighbour test and refinement (phase 2).
 #include <type_traits>
@@ -38,6 +45,8 @@ constexpr int kLC = kTX + 2;             // 130 columns of L
 constexpr int kSV = 6;                   // rows per thread in the y pass
 constexpr int kSH = 6;                   // columns per thread in the x pass
 constexpr int kLG = 3;                   // row-pair groups in the Laplacian pass
+constexpr int kWarps = kDetThreads / 32;
+constexpr long long kWaitLimit = 1ll << 22;  // polls of an mbarrier before giving up
 static_assert(kRows % kSV == 0 && kSV % 2 == 0, "y-pass strips must tile the row pairs");
 static_assert(kGC % kSH == 0 && kSH % 2 == 0, "x-pass strips must tile the columns");
 static_assert(kRP % kLG == 0, "Laplacian groups must tile the row pairs");
@@ -52,91 +61,183 @@ __device__ __forceinline__ float to_f(uint8_t v) { return (float)v - 128.0f; }
 __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
 
-// ---- stage the octave base (with clamp-to-edge) into in[IR][IC]
-template <typename InT>
-__device__ __forceinline__ void stage_input(const InT* __restrict__ src, int spitch, int W, int H,
-                                            int tx0, int ty0, int rm, int cm, float* in) {
-  const int IR = kRows + 2 * rm, IC = kTX + 2 * cm;
-  const int y0 = ty0 - kHalo - rm, x0 = tx0 - cm;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int kWarps = kDetThreads / 32;
-  const bool interior_x = x0 >= 0 && x0 + IC <= W;
-  constexpr int kMaxQ = 2;              // 16-byte row chunks per lane: IC / 4 <= 64
-  constexpr int kMaxRows = (kRows + 2 * kMaxRadius + kWarps - 1) / kWarps;
-  if constexpr (std::is_same<InT, uint8_t>::value) {
-    // four bytes per load where the row start and pitch allow it; every load
-    // of the thread is issued before the first conversion
-    const bool vec = interior_x && ((spitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(src) & 3) == 0);
-    if (vec) {
-      const int q = IC / 4;
-      uchar4 b[kMaxRows][kMaxQ];
-#pragma unroll
-      for (int i = 0; i < kMaxRows; ++i) {
-        const int r = warp + i * kWarps;
-        const int y = min(max(y0 + r, 0), H - 1);
-        const uchar4* row = reinterpret_cast<const uchar4*>(src + (size_t)y * spitch + x0);
-#pragma unroll
-        for (int j = 0; j < kMaxQ; ++j) {
-          const int c = lane + 32 * j;
-          if (r < IR && c < q) b[i][j] = __ldg(row + c);
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < kMaxRows; ++i) {
-        const int r = warp + i * kWarps;
-#pragma unroll
-        for (int j = 0; j < kMaxQ; ++j) {
-          const int c = lane + 32 * j;
-          if (r < IR && c < q)
-            reinterpret_cast<float4*>(in + r * IC)[c] =
-                make_float4((float)b[i][j].x - 128.0f, (float)b[i][j].y - 128.0f, (float)b[i][j].z - 128.0f,
-                            (float)b[i][j].w - 128.0f);
-        }
-      }
-      return;
-    }
-  } else if constexpr (std::is_same<InT, float>::value) {
-    if (interior_x) {  // rows are 16-byte aligned (pitch multiple of 8, x0 multiple of 4)
-      const int q = IC / 4;
-      float4 b[kMaxRows][kMaxQ];
-#pragma unroll
-      for (int i = 0; i < kMaxRows; ++i) {
-        const int r = warp + i * kWarps;
-        const int y = min(max(y0 + r, 0), H - 1);
-        const float4* row = reinterpret_cast<const float4*>(src + (size_t)y * spitch + x0);
-#pragma unroll
-        for (int j = 0; j < kMaxQ; ++j) {
-          const int c = lane + 32 * j;
-          if (r < IR && c < q) b[i][j] = __ldg(row + c);
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < kMaxRows; ++i) {
-        const int r = warp + i * kWarps;
-#pragma unroll
-        for (int j = 0; j < kMaxQ; ++j) {
-          const int c = lane + 32 * j;
-          if (r < IR && c < q) reinterpret_cast<float4*>(in + r * IC)[c] = b[i][j];
-        }
-      }
-      return;
-    }
+// ------------------------------------------------ bulk copies and mbarrier
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for the given phase parity; false when the limit ran out
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  for (long long i = 0; i < kWaitLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes,
+                                              unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// ------------------------------------------------ tile geometry
+struct Tile {
+  int img, tx0, ty0;
+  int W, H, lpitch;
+  const ImgPlan* P;
+  long long level_off;
+};
+
+__device__ __forceinline__ Tile locate(const DetectArgs& a, int b) {
+  // largest i with tile_prefix[i] <= b
+  int lo = 0, hi = a.n_images;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (a.tile_prefix[mid] <= b) lo = mid;
+    else hi = mid;
   }
-  for (int r = warp; r < IR; r += kWarps) {
-    const int y = min(max(y0 + r, 0), H - 1);
-    const InT* row = src + (size_t)y * spitch;
-    for (int c = lane; c < IC; c += 32) in[r * IC + c] = to_f(row[min(max(x0 + c, 0), W - 1)]);
+  Tile t;
+  t.img = lo;
+  t.P = a.plans + lo;
+  const OctPlan& op = t.P->oct[a.octave];
+  const int k = b - a.tile_prefix[lo];
+  t.tx0 = (k % op.tiles_x) * kTX;
+  t.ty0 = (k / op.tiles_x) * kTY;
+  t.W = op.W;
+  t.H = op.H;
+  t.lpitch = op.lpitch;
+  t.level_off = op.level_off;
+  return t;
+}
+
+// Where the tile's input comes from: element pointer, pitch (elements), the
+// copied columns, and whether its rows can be fetched by bulk copies (16-byte
+// aligned starts and lengths) -- otherwise it is loaded element by element.
+template <typename InT>
+struct InputRef {
+  const InT* base;
+  int pitch;   // elements
+  int cs, ce;  // copied columns [cs, ce) (image x)
+  bool bulk;
+};
+
+template <typename InT>
+__device__ __forceinline__ InputRef<InT> input_ref(const DetectArgs& a, const Tile& t, int ic) {
+  InputRef<InT> r;
+  if constexpr (std::is_same<InT, uint8_t>::value) {
+    r.base = reinterpret_cast<const InT*>(t.P->src);
+    r.pitch = t.P->pitch;
+  } else {
+    r.base = reinterpret_cast<const InT*>(a.levels) + t.level_off;  // level (o, 0) is the base
+    r.pitch = t.lpitch;
+  }
+  const int cm = (ic - kTX) / 2;
+  const int x0 = t.tx0 - cm;
+  r.cs = max(x0, 0);
+  r.ce = min(x0 + ic, t.W);
+  constexpr int es = sizeof(InT);
+  // 16-byte aligned source rows, lengths, and destination rows in raw
+  r.bulk = ((reinterpret_cast<uintptr_t>(r.base) & 15) == 0) && (((size_t)r.pitch * es) % 16 == 0) &&
+           ((r.cs * es) % 16 == 0) && (((r.ce - r.cs) * es) % 16 == 0) && r.ce > r.cs &&
+           ((ic * es) % 16 == 0) && (((r.cs - x0) * es) % 16 == 0);
+  return r;
+}
+
+// One thread issues the bulk copies of every input row of tile t into raw
+// (column c of a raw row is image x = tx0 - cm + c; rows clamp to the image).
+template <typename InT>
+__device__ __forceinline__ void issue_tile_copy(const Tile& t, const InputRef<InT>& r, int ic, int rm, InT* raw,
+                                                unsigned long long* bar) {
+  const int cm = (ic - kTX) / 2;
+  const int IR = kRows + 2 * rm;
+  const int y0 = t.ty0 - kHalo - rm;
+  const int x0 = t.tx0 - cm;
+  const unsigned row_bytes = (unsigned)((r.ce - r.cs) * sizeof(InT));
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  mbar_expect_tx(bar, row_bytes * IR);
+  for (int i = 0; i < IR; ++i) {
+    const int y = min(max(y0 + i, 0), t.H - 1);
+    bulk_copy_g2s(raw + (size_t)i * ic + (r.cs - x0), r.base + (size_t)y * r.pitch + r.cs, row_bytes, bar);
   }
 }
 
-// ---- y pass on column pairs: tmp rows ty0-2 .. ty0+33, columns from
+// raw (copied columns only) -> in (FP32), replicating the edge columns.
+template <typename InT>
+__device__ __forceinline__ void convert_raw(const InT* raw, const Tile& t, const InputRef<InT>& r, int ic, int rm,
+                                            float* in) {
+  const int cm = (ic - kTX) / 2;
+  const int IR = kRows + 2 * rm;
+  const int x0 = t.tx0 - cm;
+  const int clo = r.cs - x0, chi = r.ce - 1 - x0;  // first / last copied column
+  const int n4 = ic / 4;
+  for (int i = threadIdx.x; i < IR * n4; i += kDetThreads) {
+    const int row = i / n4;
+    const int c = (i - row * n4) * 4;
+    const InT* src = raw + (size_t)row * ic;
+    float4 v;
+    if (c >= clo && c + 3 <= chi) {
+      if constexpr (std::is_same<InT, uint8_t>::value) {
+        const uchar4 b = *reinterpret_cast<const uchar4*>(src + c);
+        v = make_float4((float)b.x - 128.0f, (float)b.y - 128.0f, (float)b.z - 128.0f, (float)b.w - 128.0f);
+      } else if constexpr (std::is_same<InT, float>::value) {
+        v = *reinterpret_cast<const float4*>(src + c);
+      } else {
+        v = make_float4(to_f(src[c]), to_f(src[c + 1]), to_f(src[c + 2]), to_f(src[c + 3]));
+      }
+    } else {
+      v = make_float4(to_f(src[min(max(c, clo), chi)]), to_f(src[min(max(c + 1, clo), chi)]),
+                      to_f(src[min(max(c + 2, clo), chi)]), to_f(src[min(max(c + 3, clo), chi)]));
+    }
+    reinterpret_cast<float4*>(in + (size_t)row * ic)[c / 4] = v;
+  }
+}
+
+// Element-by-element input load with clamp-to-edge (tiles whose rows cannot
+// be bulk-copied).
+template <typename InT>
+__device__ __forceinline__ void load_tile_direct(const Tile& t, const InputRef<InT>& r, int ic, int rm, float* in) {
+  const int cm = (ic - kTX) / 2;
+  const int IR = kRows + 2 * rm;
+  const int y0 = t.ty0 - kHalo - rm, x0 = t.tx0 - cm;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int row = warp; row < IR; row += kWarps) {
+    const int y = min(max(y0 + row, 0), t.H - 1);
+    const InT* src = r.base + (size_t)y * r.pitch;
+    for (int c = lane; c < ic; c += 32) in[row * ic + c] = to_f(src[min(max(x0 + c, 0), t.W - 1)]);
+  }
+}
+
+// ------------------------------------------------ separable filters
+// y pass on column pairs: tmp rows ty0-2 .. ty0+33, columns from
 // x = tx0 - C (C = 2 + R rounded up to even) to tx0 + 128 + C.
 template <int R, int ic>
-__device__ __forceinline__ void vpass(const float* in, int rm, int cm, const float2 (&g)[R + 1], float* tmp) {
+__device__ __forceinline__ void vpass(const float* taps, const float* in, int rm, float* tmp) {
   constexpr int C = (2 + R + 1) & ~1;
   constexpr int kPairs = (kTX + 2 * C) / 2;
   constexpr int kStrips = kRows / kSV;
-  const int col_off = cm - C;  // in-column of tmp column 0
+  constexpr int cm = (ic - kTX) / 2;
+  constexpr int col_off = cm - C;  // in-column of tmp column 0
+  float2 g[R + 1];
+#pragma unroll
+  for (int j = 0; j <= R; ++j) g[j] = f2(taps[j], taps[j]);
   for (int item = threadIdx.x; item < kPairs * kStrips; item += kDetThreads) {
     const int s = item / kPairs;
     const int p = item - s * kPairs;
@@ -164,13 +265,16 @@ __device__ __forceinline__ void vpass(const float* in, int rm, int cm, const flo
   }
 }
 
-// ---- x pass on row pairs: gs[yp][c] (c <-> x = tx0 - 2 + c) from tmp
+// x pass on row pairs: gs[yp][c] (c <-> x = tx0 - 2 + c) from tmp
 template <int R, int ic>
-__device__ __forceinline__ void hpass(const float* tmp, const float2 (&g)[R + 1], float* gs) {
+__device__ __forceinline__ void hpass(const float* taps, const float* tmp, float* gs) {
   constexpr int C = (2 + R + 1) & ~1;
   constexpr int kNS = kGC / kSH;
-  constexpr int kOff = C - 2 - R;  // tmp column of output column 0's first tap (0 or 1)
-  constexpr int kIn = kSH + 2 * R;
+  constexpr int kOff = C - 2 - R;   // tmp column of output column 0's first tap (0 or 1)
+  constexpr int kIn = kSH + 2 * R;  // even
+  float2 g[R + 1];
+#pragma unroll
+  for (int j = 0; j <= R; ++j) g[j] = f2(taps[j], taps[j]);
   for (int item = threadIdx.x; item < kRP * kNS; item += kDetThreads) {
     const int yp = item / kNS;
     const int c0 = (item - yp * kNS) * kSH;
@@ -178,39 +282,35 @@ __device__ __forceinline__ void hpass(const float* tmp, const float2 (&g)[R + 1]
     float2 acc[kSH];
 #pragma unroll
     for (int o = 0; o < kSH; ++o) acc[o] = f2(0.0f, 0.0f);
-    if constexpr (kOff == 0) {
-      // 16-byte loads: two consecutive columns of the row pair
+    // 16-byte loads (two consecutive columns of the row pair); with kOff = 1
+    // the first and the last column come from 8-byte loads
 #pragma unroll
-      for (int j = 0; j < kIn; j += 2) {
+    for (int j = 0; j < kIn; j += 2) {
+      float2 va, vb;
+      if constexpr (kOff == 0) {
         const float4 v4 = *reinterpret_cast<const float4*>(t + j);
-        const float2 va = f2(v4.x, v4.y), vb = f2(v4.z, v4.w);
-#pragma unroll
-        for (int o = 0; o < kSH; ++o) {
-          const int d = j - o - R;
-          if (d >= -R && d <= R) acc[o] = fma2(g[d < 0 ? -d : d], va, acc[o]);
-          const int d1 = d + 1;
-          if (j + 1 < kIn && d1 >= -R && d1 <= R) acc[o] = fma2(g[d1 < 0 ? -d1 : d1], vb, acc[o]);
+        va = f2(v4.x, v4.y);
+        vb = f2(v4.z, v4.w);
+      } else {
+        if (j == 0) {
+          va = t[0];
+        } else {
+          const float4 v4 = *reinterpret_cast<const float4*>(t + j - 1);
+          va = f2(v4.z, v4.w);
+        }
+        if (j + 1 == kIn - 1) {
+          vb = t[j + 1];
+        } else {
+          const float4 v4 = *reinterpret_cast<const float4*>(t + j + 1);
+          vb = f2(v4.x, v4.y);
         }
       }
-    } else {
-      // t is 8 bytes past a 16-byte boundary: one 8-byte load, then 16-byte
-      // loads, then one 8-byte load (kIn is even)
-      float2 v[kIn];
-      v[0] = t[0];
 #pragma unroll
-      for (int j = 1; j + 1 < kIn; j += 2) {
-        const float4 v4 = *reinterpret_cast<const float4*>(t + j);
-        v[j] = f2(v4.x, v4.y);
-        v[j + 1] = f2(v4.z, v4.w);
-      }
-      v[kIn - 1] = t[kIn - 1];
-#pragma unroll
-      for (int j = 0; j < kIn; ++j) {
-#pragma unroll
-        for (int o = 0; o < kSH; ++o) {
-          const int d = j - o - R;
-          if (d >= -R && d <= R) acc[o] = fma2(g[d < 0 ? -d : d], v[j], acc[o]);
-        }
+      for (int o = 0; o < kSH; ++o) {
+        const int d = j - o - R;
+        if (d >= -R && d <= R) acc[o] = fma2(g[d < 0 ? -d : d], va, acc[o]);
+        const int d1 = d + 1;
+        if (d1 >= -R && d1 <= R) acc[o] = fma2(g[d1 < 0 ? -d1 : d1], vb, acc[o]);
       }
     }
     float4* dst = reinterpret_cast<float4*>(gs + ((size_t)yp * kGC + c0) * 2);
@@ -219,34 +319,31 @@ __device__ __forceinline__ void hpass(const float* tmp, const float2 (&g)[R + 1]
   }
 }
 
-template <int R, int ic>
-__device__ __forceinline__ void level_filter(const float* taps, const float* in, int rm, int cm, float* tmp,
-                                             float* gs) {
-  float2 g[R + 1];
-#pragma unroll
-  for (int j = 0; j <= R; ++j) g[j] = f2(taps[j], taps[j]);
-  vpass<R, ic>(in, rm, cm, g, tmp);
-  __syncthreads();
-  hpass<R, ic>(tmp, g, gs);
-}
+#define CDVS_RC(N, ...) \
+  case N: {             \
+    constexpr int r = N; \
+    __VA_ARGS__;        \
+  } break;
+#define CDVS_RADIUS_SWITCH(R, ...)                                                                       \
+  switch (R) {                                                                                           \
+    CDVS_RC(0, __VA_ARGS__) CDVS_RC(1, __VA_ARGS__) CDVS_RC(2, __VA_ARGS__) CDVS_RC(3, __VA_ARGS__)      \
+    CDVS_RC(4, __VA_ARGS__) CDVS_RC(5, __VA_ARGS__) CDVS_RC(6, __VA_ARGS__) CDVS_RC(7, __VA_ARGS__)      \
+    CDVS_RC(8, __VA_ARGS__) CDVS_RC(9, __VA_ARGS__) CDVS_RC(10, __VA_ARGS__) CDVS_RC(11, __VA_ARGS__)    \
+    CDVS_RC(12, __VA_ARGS__) CDVS_RC(13, __VA_ARGS__) CDVS_RC(14, __VA_ARGS__) CDVS_RC(15, __VA_ARGS__)  \
+    CDVS_RC(16, __VA_ARGS__) CDVS_RC(17, __VA_ARGS__) CDVS_RC(18, __VA_ARGS__) CDVS_RC(19, __VA_ARGS__)  \
+    CDVS_RC(20, __VA_ARGS__) CDVS_RC(21, __VA_ARGS__) CDVS_RC(22, __VA_ARGS__) CDVS_RC(23, __VA_ARGS__)  \
+    CDVS_RC(24, __VA_ARGS__)                                                                             \
+    default:                                                                                             \
+      break;                                                                                             \
+  }
 
 template <int ic>
-__device__ void filter_dispatch(int R, const float* taps, const float* in, int rm, int cm, float* tmp,
-                                float* gs) {
-#define CDVS_CASE(r)                                    \
-  case r:                                               \
-    if constexpr (2 + r <= (ic - kTX) / 2) level_filter<r, ic>(taps, in, rm, cm, tmp, gs); \
-    break;
-  switch (R) {
-    CDVS_CASE(0) CDVS_CASE(1) CDVS_CASE(2) CDVS_CASE(3) CDVS_CASE(4) CDVS_CASE(5) CDVS_CASE(6)
-    CDVS_CASE(7) CDVS_CASE(8) CDVS_CASE(9) CDVS_CASE(10) CDVS_CASE(11) CDVS_CASE(12)
-    CDVS_CASE(13) CDVS_CASE(14) CDVS_CASE(15) CDVS_CASE(16) CDVS_CASE(17) CDVS_CASE(18)
-    CDVS_CASE(19) CDVS_CASE(20) CDVS_CASE(21) CDVS_CASE(22) CDVS_CASE(23) CDVS_CASE(24)
-    default:
-      __syncthreads();  // rejected on the host; keep the barrier count uniform
-      break;
-  }
-#undef CDVS_CASE
+__device__ void vpass_dispatch(int R, const float* taps, const float* in, int rm, float* tmp) {
+  CDVS_RADIUS_SWITCH(R, if constexpr (2 + r <= (ic - kTX) / 2) vpass<r, ic>(taps, in, rm, tmp))
+}
+template <int ic>
+__device__ void hpass_dispatch(int R, const float* taps, const float* tmp, float* gs) {
+  CDVS_RADIUS_SWITCH(R, if constexpr (2 + r <= (ic - kTX) / 2) hpass<r, ic>(taps, tmp, gs))
 }
 
 // gs element (row r, col c) of the row-pair layout
@@ -256,8 +353,8 @@ __device__ __forceinline__ float& gat(float* gs, int r, int c) { return gs[((r >
 // image take the value of the nearest image pixel, so the stencil below
 // needs no border cases (the Laplacian is only used at image pixels).
 __device__ __forceinline__ void replicate_borders(float* gs, int W, int H, int tx0, int ty0) {
-  const int cl = 1 - tx0;             // gs column of x = -1 (valid when tx0 == 0)
-  const int cr = W - tx0 + kHalo;     // gs column of x = W
+  const int cl = 1 - tx0;          // gs column of x = -1 (valid when tx0 == 0)
+  const int cr = W - tx0 + kHalo;  // gs column of x = W
   const int rt = 1 - ty0, rb = H - ty0 + kHalo;
   const bool left = tx0 == 0, right = cr < kGC, top = ty0 == 0, bottom = rb < kRows;
   if (!(left || right || top || bottom)) return;  // uniform over the CTA
@@ -321,8 +418,8 @@ __device__ __forceinline__ void store_level(const float* gs, StoreT* dst, int lp
                                             int ty0) {
   constexpr int kQ = kTX / 2;
   for (int i = threadIdx.x; i < (kTY / 2) * kQ; i += kDetThreads) {
-    const int m = i / kQ;                 // tile rows 2m, 2m+1 = gs row pair m + 1
-    const int c = (i - m * kQ) * 2;       // tile columns c, c+1 = gs columns c+2, c+3
+    const int m = i / kQ;            // tile rows 2m, 2m+1 = gs row pair m + 1
+    const int c = (i - m * kQ) * 2;  // tile columns c, c+1 = gs columns c+2, c+3
     const int x = tx0 + c, y = ty0 + 2 * m;
     if (x >= W || y >= H) continue;
     const float4 v = *reinterpret_cast<const float4*>(gs + ((m + 1) * kGC + c + kHalo) * 2);
@@ -347,13 +444,23 @@ __device__ __forceinline__ void store_decimated(const float* gs, StoreT* dst, in
   }
 }
 
+// ------------------------------------------------ extremum in scale and space
 struct Found {
   float xo, yo, so, resp, pss, ratio;
   int type;
 };
 
 __device__ __forceinline__ float2 abs2(float2 v) { return f2(fabsf(v.x), fabsf(v.y)); }
-__device__ __forceinline__ float2 rcp2(float2 v) { return f2(__frcp_rn(v.x), __frcp_rn(v.y)); }
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 // S4 on a pair of pixels (phase 1): for each pixel, the admissible extremum
 // of the cubic p(t) = a0 + a1 t + a2 t^2 + a3 t^3 with |p| >= T.  The roots of
@@ -373,10 +480,10 @@ __device__ __forceinline__ void cubic_extremum2(const DetectArgs& a, const float
   if (!(go0 || go1)) return;
   const float2 A = mul2(f2(3.0f, 3.0f), al[3]), Bq = mul2(f2(2.0f, 2.0f), al[2]), C = al[1];
   const float2 D = fma2(mul2(f2(-4.0f, -4.0f), A), C, mul2(Bq, Bq));
-  const float2 sq = f2(sqrtf(fmaxf(D.x, 0.0f)), sqrtf(fmaxf(D.y, 0.0f)));
+  const float2 sq = f2(sqrt_approx(fmaxf(D.x, 0.0f)), sqrt_approx(fmaxf(D.y, 0.0f)));
   const float2 q = mul2(f2(-0.5f, -0.5f), add2(Bq, f2(copysignf(sq.x, Bq.x), copysignf(sq.y, Bq.y))));
-  const float2 r0 = mul2(q, rcp2(A));
-  const float2 r1 = mul2(C, rcp2(q));
+  const float2 r0 = mul2(q, f2(rcp_approx(A.x), rcp_approx(A.y)));
+  const float2 r1 = mul2(C, f2(rcp_approx(q.x), rcp_approx(q.y)));
   const float2 six_a3 = mul2(f2(6.0f, 6.0f), al[3]);
   const float2 two_a2 = mul2(f2(2.0f, 2.0f), al[2]);
   // p'' and p at both roots, both pixels
@@ -387,7 +494,7 @@ __device__ __forceinline__ void cubic_extremum2(const DetectArgs& a, const float
   for (int h = 0; h < 2; ++h) {
     if (!(h ? go1 : go0)) continue;
     const float Ah = h ? A.y : A.x, Bh = h ? Bq.y : Bq.x, Ch = h ? C.y : C.x;
-    const float Dh = h ? D.y : D.x, qh = h ? q.y : q.x;
+    const float Dh = h ? D.y : D.x;
     float t0, t1, p0, p1, s0, s1;
     int nr;
     if (Ah == 0.0f) {  // quadratic p: the single root of the linear derivative
@@ -406,7 +513,7 @@ __device__ __forceinline__ void cubic_extremum2(const DetectArgs& a, const float
       t1 = h ? r1.y : r1.x;
       p1 = h ? v1.y : v1.x;
       s1 = h ? pdd1.y : pdd1.x;
-      nr = qh != 0.0f ? 2 : 1;
+      nr = 2;  // D > 0 makes q nonzero
     }
     int best = 0;
     float bt_t = 0.0f, bv = 0.0f;
@@ -493,147 +600,205 @@ __device__ __forceinline__ bool refine_pixel(const DetectArgs& a, const float* L
   return true;
 }
 
-// warp-aggregated append to the image's candidate queue (all lanes call it)
-__device__ __forceinline__ void append(const DetectArgs& a, int img, int o, bool found, const Found& f) {
-  const int lane = threadIdx.x & 31;
-  const unsigned m = __ballot_sync(0xffffffffu, found);
-  if (!m) return;
-  const int leader = __ffs(m) - 1;
-  int base = 0;
-  if (lane == leader) base = atomicAdd(a.cand_count + img, __popc(m));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  if (!found) return;
-  const int pos = base + __popc(m & ((1u << lane) - 1u));
-  if (pos >= a.cand_cap) {
-    atomicOr(a.status, kStatusCandOverflow);
-    return;
-  }
-  Cand c;
-  c.xo = f.xo;
-  c.yo = f.yo;
-  c.so = f.so;
-  c.resp = f.resp;
-  c.pss = f.pss;
-  c.ratio = f.ratio;
-  c.octave = (short)o;
-  c.type = (short)f.type;
-  c.spare = 0;
-  a.cands[(size_t)img * a.cand_cap + pos] = c;
-}
-
 // Phase-1 survivors of a tile: packed (ly, lx, type) and t*.
 struct Pending {
   int code;  // ly << 16 | lx << 1 | (type > 0)
   float t;
 };
 
+struct TileShared {
+  unsigned long long bar;  // completion of the bulk copies into raw
+  int n_pending;
+  int out_base;  // first queue slot of this round's survivors
+  int warp_count[kWarps];
+  int timeout;
+};
+
 template <typename InT, typename StoreT, int ic>
-__global__ void __launch_bounds__(kDetThreads, 1) detect_kernel(const __grid_constant__ DetectArgs a, int rm) {
+__global__ void __launch_bounds__(kDetThreads, 1)
+    detect_kernel(const __grid_constant__ DetectArgs a, int rm, int n_tiles) {
   extern __shared__ float4 smem4[];
-  __shared__ int n_pending;
-  const int cm = (ic - kTX) / 2;
-  float* in = reinterpret_cast<float*>(smem4);
-  float* tmp = in + (kRows + 2 * rm) * ic;
+  __shared__ TileShared sh;
+  const int IR = kRows + 2 * rm;
+  const size_t raw_floats = ((size_t)IR * ic * sizeof(InT) + 15) / 16 * 4;
+  InT* raw = reinterpret_cast<InT*>(smem4);
+  float* in = reinterpret_cast<float*>(smem4) + raw_floats;
+  float* tmp = in + (size_t)IR * ic;
   float* gs = tmp + kRows * ic;
   float* Ls = gs + kRows * kGC;
-
-  // (image, tile) of this CTA: largest i with tile_prefix[i] <= blockIdx.x
-  const int b = blockIdx.x;
-  int lo = 0, hi = a.n_images;
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (a.tile_prefix[mid] <= b) lo = mid;
-    else hi = mid;
-  }
-  const int img = lo;
-  const ImgPlan* P = a.plans + img;
   const int o = a.octave;
-  const OctPlan op = P->oct[o];
-  const int W = op.W, H = op.H, lpitch = op.lpitch;
-  const int t = b - a.tile_prefix[img];
-  const int tx0 = (t % op.tiles_x) * kTX;
-  const int ty0 = (t / op.tiles_x) * kTY;
-  StoreT* lev = reinterpret_cast<StoreT*>(a.levels) + op.level_off;
-  const size_t lstride = (size_t)lpitch * H;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-  if constexpr (std::is_same<InT, uint8_t>::value)
-    stage_input<InT>(reinterpret_cast<const InT*>(P->src), P->pitch, W, H, tx0, ty0, rm, cm, in);
-  else
-    stage_input<InT>(reinterpret_cast<const InT*>(lev), lpitch, W, H, tx0, ty0, rm, cm, in);
-  if (threadIdx.x == 0) n_pending = 0;
-  __syncthreads();
-
-  for (int k = 0; k < kScales; ++k) {
-    filter_dispatch<ic>(a.radius[k], a.taps[k], in, rm, cm, tmp, gs);
-    __syncthreads();
-    replicate_borders(gs, W, H, tx0, ty0);
-    if (k > 0 || a.write_level0) store_level<StoreT>(gs, lev + k * lstride, lpitch, W, H, tx0, ty0);
-    if (k == kScales - 1 && o + 1 < P->n_oct) {
-      const OctPlan op1 = P->oct[o + 1];
-      store_decimated<StoreT>(gs, reinterpret_cast<StoreT*>(a.levels) + op1.level_off, op1.lpitch, W, H, tx0,
-                              ty0);
-    }
-    laplacian(gs, a.s2[k], Ls + (size_t)k * kRP * kLC * 2);
-    __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_init(&sh.bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    sh.timeout = 0;
   }
+  __syncthreads();
+  unsigned parity = 0;
 
-  // ---- phase 1, per pixel pair (tile rows 2m, 2m+1 are L row pair m + 1):
-  // cubic coefficients of Eq. 3 on packed pairs, then the admissible
-  // extremum in scale; survivors are compacted into `in` (no longer needed)
-  Pending* pend = reinterpret_cast<Pending*>(in);
-  const int lane = threadIdx.x & 31;
-  for (int it = 0; it < (kTX * kTY / 2) / kDetThreads; ++it) {
-    const int idx = it * kDetThreads + threadIdx.x;
-    const int m = idx / kTX, lx = idx - (idx / kTX) * kTX;
-    float2 Lk[kScales];
-#pragma unroll
-    for (int k = 0; k < kScales; ++k) Lk[k] = reinterpret_cast<const float2*>(Ls)[(k * kRP + m + 1) * kLC + lx + 1];
-    float2 al2[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      float2 s = f2(0.0f, 0.0f);
-#pragma unroll
-      for (int k = 0; k < kScales; ++k) s = fma2(f2(a.B[i][k], a.B[i][k]), Lk[k], s);
-      al2[i] = s;
+  int b = blockIdx.x;
+  if (b >= n_tiles) return;
+  Tile cur = locate(a, b);
+  InputRef<InT> cref = input_ref<InT>(a, cur, ic);
+  if (threadIdx.x == 0 && cref.bulk) issue_tile_copy<InT>(cur, cref, ic, rm, raw, &sh.bar);
+  bool pending_copy = cref.bulk;
+
+  for (; b < n_tiles; b += gridDim.x) {
+    // ---- this tile's input into `in`
+    if (cref.bulk) {
+      if (mbar_wait(&sh.bar, parity)) {
+        parity ^= 1u;
+        pending_copy = false;
+      } else {
+        sh.timeout = 1;
+      }
+      convert_raw<InT>(raw, cur, cref, ic, rm, in);
+    } else {
+      load_tile_direct<InT>(cur, cref, ic, rm, in);
     }
-    const int x = tx0 + lx, y0 = ty0 + 2 * m;
-    const bool inx = x >= 1 && x < W - 1;
-    int bt[2];
-    float tb[2];
-    cubic_extremum2(a, al2, inx && y0 >= 1 && y0 < H - 1, inx && y0 + 1 >= 1 && y0 + 1 < H - 1, bt, tb);
+    if (threadIdx.x == 0) sh.n_pending = 0;
+    __syncthreads();
+    if (sh.timeout) break;  // uniform: a copy never completed
+    // ---- next tile's input on its way while this one is processed
+    const int nb = b + gridDim.x;
+    Tile nxt = cur;
+    InputRef<InT> nref = cref;
+    nref.bulk = false;
+    if (nb < n_tiles) {
+      nxt = locate(a, nb);
+      nref = input_ref<InT>(a, nxt, ic);
+      if (threadIdx.x == 0 && nref.bulk) issue_tile_copy<InT>(nxt, nref, ic, rm, raw, &sh.bar);
+      pending_copy = nref.bulk;
+    }
+
+    const int W = cur.W, H = cur.H, lpitch = cur.lpitch, tx0 = cur.tx0, ty0 = cur.ty0;
+    StoreT* lev = reinterpret_cast<StoreT*>(a.levels) + cur.level_off;
+    const size_t lstride = (size_t)lpitch * H;
+
+    // ---- levels: the y pass of level k+1 shares a phase with the stores and
+    // the Laplacian of level k
+    vpass_dispatch<ic>(a.radius[0], a.taps[0], in, rm, tmp);
+    __syncthreads();
+    hpass_dispatch<ic>(a.radius[0], a.taps[0], tmp, gs);
+    __syncthreads();
+    for (int k = 0; k < kScales; ++k) {
+      replicate_borders(gs, W, H, tx0, ty0);
+      if (k > 0 || a.write_level0) store_level<StoreT>(gs, lev + k * lstride, lpitch, W, H, tx0, ty0);
+      if (k == kScales - 1 && o + 1 < cur.P->n_oct) {
+        const OctPlan& op1 = cur.P->oct[o + 1];
+        store_decimated<StoreT>(gs, reinterpret_cast<StoreT*>(a.levels) + op1.level_off, op1.lpitch, W, H, tx0,
+                                ty0);
+      }
+      laplacian(gs, a.s2[k], Ls + (size_t)k * kRP * kLC * 2);
+      if (k + 1 < kScales) vpass_dispatch<ic>(a.radius[k + 1], a.taps[k + 1], in, rm, tmp);
+      __syncthreads();
+      if (k + 1 < kScales) {
+        hpass_dispatch<ic>(a.radius[k + 1], a.taps[k + 1], tmp, gs);
+        __syncthreads();
+      }
+    }
+
+    // ---- phase 1, per pixel pair (tile rows 2m, 2m+1 are L row pair m + 1):
+    // cubic coefficients of Eq. 3 on packed pairs, then the admissible
+    // extremum in scale; survivors are compacted into `in` and `tmp`
+    Pending* pend = reinterpret_cast<Pending*>(in);
+    for (int it = 0; it < (kTX * kTY / 2) / kDetThreads; ++it) {
+      const int idx = it * kDetThreads + threadIdx.x;
+      const int m = idx / kTX, lx = idx - (idx / kTX) * kTX;
+      float2 Lk[kScales];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const unsigned msk = __ballot_sync(0xffffffffu, bt[h] != 0);
-      if (msk) {
-        const int leader = __ffs(msk) - 1;
+      for (int k = 0; k < kScales; ++k)
+        Lk[k] = reinterpret_cast<const float2*>(Ls)[(k * kRP + m + 1) * kLC + lx + 1];
+      float2 al2[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        float2 s = f2(0.0f, 0.0f);
+#pragma unroll
+        for (int k = 0; k < kScales; ++k) s = fma2(f2(a.B[i][k], a.B[i][k]), Lk[k], s);
+        al2[i] = s;
+      }
+      const int x = tx0 + lx, y0 = ty0 + 2 * m;
+      const bool inx = x >= 1 && x < W - 1;
+      int bt[2];
+      float tb[2];
+      cubic_extremum2(a, al2, inx && y0 >= 1 && y0 < H - 1, inx && y0 + 1 < H - 1, bt, tb);
+      const unsigned m0 = __ballot_sync(0xffffffffu, bt[0] != 0);
+      const unsigned m1 = __ballot_sync(0xffffffffu, bt[1] != 0);
+      if (m0 | m1) {
         int base = 0;
-        if (lane == leader) base = atomicAdd(&n_pending, __popc(msk));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (bt[h] != 0) {
+        if (lane == 0) base = atomicAdd(&sh.n_pending, __popc(m0) + __popc(m1));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        const unsigned below = (1u << lane) - 1u;
+        if (bt[0] != 0) {
           Pending e;
-          e.code = ((2 * m + h) << 16) | (lx << 1) | (bt[h] > 0 ? 1 : 0);
-          e.t = tb[h];
-          pend[base + __popc(msk & ((1u << lane) - 1u))] = e;
+          e.code = ((2 * m) << 16) | (lx << 1) | (bt[0] > 0 ? 1 : 0);
+          e.t = tb[0];
+          pend[base + __popc(m0 & below)] = e;
+        }
+        if (bt[1] != 0) {
+          Pending e;
+          e.code = ((2 * m + 1) << 16) | (lx << 1) | (bt[1] > 0 ? 1 : 0);
+          e.t = tb[1];
+          pend[base + __popc(m0) + __popc(m1 & below)] = e;
         }
       }
     }
-  }
-  __syncthreads();
+    __syncthreads();
 
-  // ---- phase 2: neighbour test and refinement of the survivors, densely
-  const int np = n_pending;
-  const int rounds = (np + kDetThreads - 1) / kDetThreads;
-  for (int r = 0; r < rounds; ++r) {
-    const int i = r * kDetThreads + threadIdx.x;
-    Found f;
-    bool found = false;
-    if (i < np) {
-      const Pending e = pend[i];
-      const int ly = e.code >> 16, lx = (e.code >> 1) & 0x7fff;
-      found = refine_pixel(a, Ls, ly, lx, (e.code & 1) ? 1 : -1, e.t, tx0 + lx, ty0 + ly, f);
+    // ---- phase 2: neighbour test and refinement of the survivors, densely;
+    // one queue reservation per round for the whole CTA
+    const int np = sh.n_pending;
+    for (int r0 = 0; r0 < np; r0 += kDetThreads) {
+      const int i = r0 + threadIdx.x;
+      Found f;
+      bool found = false;
+      if (i < np) {
+        const Pending e = pend[i];
+        const int ly = e.code >> 16, lx = (e.code >> 1) & 0x7fff;
+        found = refine_pixel(a, Ls, ly, lx, (e.code & 1) ? 1 : -1, e.t, tx0 + lx, ty0 + ly, f);
+      }
+      const unsigned msk = __ballot_sync(0xffffffffu, found);
+      if (lane == 0) sh.warp_count[warp] = __popc(msk);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < kWarps; ++w) {
+          const int c = sh.warp_count[w];
+          sh.warp_count[w] = tot;
+          tot += c;
+        }
+        sh.out_base = tot > 0 ? atomicAdd(a.cand_count + cur.img, tot) : 0;
+      }
+      __syncthreads();
+      if (found) {
+        const int pos = sh.out_base + sh.warp_count[warp] + __popc(msk & ((1u << lane) - 1u));
+        if (pos < a.cand_cap) {
+          Cand c;
+          c.xo = f.xo;
+          c.yo = f.yo;
+          c.so = f.so;
+          c.resp = f.resp;
+          c.pss = f.pss;
+          c.ratio = f.ratio;
+          c.octave = (short)o;
+          c.type = (short)f.type;
+          c.spare = 0;
+          a.cands[(size_t)cur.img * a.cand_cap + pos] = c;
+        } else {
+          atomicOr(a.status, kStatusCandOverflow);
+        }
+      }
+      __syncthreads();  // warp_count / out_base are reused by the next round
     }
-    append(a, img, o, found, f);
+    cur = nxt;
+    cref = nref;
+    __syncthreads();  // the pending list lives in `in`, rewritten by the next tile
   }
+  if (sh.timeout && threadIdx.x == 0) atomicOr(a.status, kStatusTimeout);
+  // a copy still in flight must land before the CTA's shared memory goes
+  // (bounded: after a timeout the kernel returns regardless)
+  if (pending_copy) mbar_wait(&sh.bar, parity);
 }
 
 }  // namespace
@@ -641,27 +806,33 @@ __global__ void __launch_bounds__(kDetThreads, 1) detect_kernel(const __grid_con
 // The input tile pitch: 128 + 2 Cm columns for radii up to 14 and up to 24.
 static int tile_pitch(int max_radius) { return max_radius <= 14 ? 160 : 184; }
 
-size_t detect_smem_bytes(int max_radius) {
+static size_t detect_smem(int max_radius, int in_size) {
   const int ic = tile_pitch(max_radius);
-  return sizeof(float) * ((size_t)(kRows + 2 * max_radius) * ic + (size_t)kRows * ic + (size_t)kRows * kGC +
-                          (size_t)kScales * kRows * kLC);
+  const size_t rows = (size_t)(kRows + 2 * max_radius);
+  const size_t raw = (rows * ic * in_size + 15) / 16 * 16;
+  return raw + sizeof(float) * (rows * ic + (size_t)kRows * ic + (size_t)kRows * kGC +
+                                (size_t)kScales * kRows * kLC);
 }
 
-cudaError_t launch_detect(const DetectArgs& a, int n_tiles, int max_radius, int storage, cudaStream_t s) {
+size_t detect_smem_bytes(int max_radius) { return detect_smem(max_radius, 4); }
+
+cudaError_t launch_detect(const DetectArgs& a, int n_tiles, int max_radius, int storage, int n_sms,
+                          cudaStream_t s) {
   if (n_tiles <= 0) return cudaSuccess;
   if (max_radius > kMaxRadius) return cudaErrorInvalidValue;
-  const size_t smem = detect_smem_bytes(max_radius);
+  const int grid = n_tiles < n_sms ? n_tiles : n_sms;
   cudaError_t e;
 #define CDVS_LAUNCH(IN, ST, IC)                                                                                   \
   do {                                                                                                            \
+    const size_t smem = detect_smem(max_radius, sizeof(IN));                                                     \
     e = cudaFuncSetAttribute(detect_kernel<IN, ST, IC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
     if (e != cudaSuccess) return e;                                                                               \
-    detect_kernel<IN, ST, IC><<<n_tiles, kDetThreads, smem, s>>>(a, max_radius);                                  \
+    detect_kernel<IN, ST, IC><<<grid, kDetThreads, smem, s>>>(a, max_radius, n_tiles);                           \
   } while (0)
-#define CDVS_LAUNCH_IC(IN, ST)                                  \
-  do {                                                          \
+#define CDVS_LAUNCH_IC(IN, ST)                                   \
+  do {                                                           \
     if (tile_pitch(max_radius) == 160) CDVS_LAUNCH(IN, ST, 160); \
-    else CDVS_LAUNCH(IN, ST, 184);                              \
+    else CDVS_LAUNCH(IN, ST, 184);                               \
   } while (0)
   if (storage == CDVS_STORAGE_FP16) {
     if (a.octave == 0) CDVS_LAUNCH_IC(uint8_t, __half);
