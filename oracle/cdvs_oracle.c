@@ -504,7 +504,9 @@ int oracle_orientations(const double *G, int W, int H, double xo, double yo, dou
     const double m = p->margin;
     double h[36];
     memset(h, 0, sizeof(h));
-    const double R = p->ori_radius * so, R2 = R * R;
+    /* the disc membership (distance < ori_radius * sigma) is a threshold
+     * decision too: the bracketing runs move the radius by the margin */
+    const double R = p->ori_radius * so * (1.0 + m), R2 = R * R;
     const double sw = p->ori_weight_sigma * so;
     for (int v = (int)ceil(yo - R); v <= (int)floor(yo + R); ++v) {
         if (v < 0 || v >= H) continue;
@@ -566,7 +568,9 @@ int oracle_orientations(const double *G, int W, int H, double xo, double yo, dou
 void oracle_descriptor(const double *G, int W, int H, double xo, double yo, double so,
                        double theta, const oracle_params *p, double *d) {
     memset(d, 0, sizeof(double) * 128);
-    const double R = p->desc_radius * so, R2 = R * R;
+    /* disc membership (distance < desc_radius * sigma), bracketed like every
+     * other threshold decision */
+    const double R = p->desc_radius * so * (1.0 + p->margin), R2 = R * R;
     const double cs = p->cell_side * so;
     const double ct = cos(theta), st = sin(theta);
     const double ws2 = 2.0 * p->desc_weight_sigma * p->desc_weight_sigma;

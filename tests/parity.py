@@ -81,12 +81,13 @@ def record_agreement(gk, gd, runs):
     """Orientation and descriptor agreement of GPU records with the oracle.
 
     runs[0] = (records, descriptors) of the oracle itself; runs[1:] = the
-    oracle with every threshold and every orientation-bin boundary moved by a
-    relative 1e-4 (both ways).  A GPU record is good when the oracle has the
-    same point with theta within THETA_TOL and a descriptor within DESC_TOL;
-    it is a margin case when only a perturbed oracle run has such a theta
-    (a gradient sample sits on a histogram bin boundary, or a peak on the
-    0.8 x max line); otherwise it is bad.  Returns (good, margin, bad)."""
+    oracle with every threshold, every orientation-bin boundary and the
+    sampling-disc radii moved by a relative 1e-4 (both ways).  A GPU record is
+    good when the oracle has the same point with theta within THETA_TOL and a
+    descriptor within DESC_TOL; it is a margin case when only a perturbed
+    oracle run has such a record (a gradient sample on a histogram bin
+    boundary, a peak on the 0.8 x max line, a pixel on the edge of the
+    sampling disc); otherwise it is bad.  Returns (good, margin, bad)."""
     good = margin = bad = 0
     ek, ed = runs[0]
     m0 = match(gk, ek)
@@ -100,15 +101,16 @@ def record_agreement(gk, gd, runs):
             j = same_pt[int(np.argmin(dth))]
             if rel_l2(gd[i], ed[j]) <= DESC_TOL:
                 good += 1
-            else:
-                bad += 1
-            continue
+                continue
+        # not explained by the oracle itself: a margin case when a perturbed
+        # oracle run has the same orientation and descriptor
         hit = False
         for (rk, rd), mm in zip(runs[1:], alt_m):
             if mm[i] < 0:
                 continue
             pts = np.nonzero(match(rk, gk[i:i + 1]) == 0)[0]
-            if any(ang(rk["theta"][j], gk["theta"][i]) <= THETA_TOL for j in pts):
+            if any(ang(rk["theta"][j], gk["theta"][i]) <= THETA_TOL and rel_l2(gd[i], rd[j]) <= DESC_TOL
+                   for j in pts):
                 hit = True
         if hit:
             margin += 1
