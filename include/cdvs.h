@@ -127,7 +127,8 @@ const char *cdvs_last_error(const cdvs_ctx *ctx);
  *   kp_out         kp_capacity records, packed over the batch: the records of
  *                  image i follow those of image i-1, each image's in rank order
  *                  then orientation order (peak value descending)
- *   desc_out       kp_capacity * 128 floats, descriptor j belongs to record j:
+ *   desc_out       kp_capacity * 128 floats (16-byte aligned when on the
+ *                  device), descriptor j belongs to record j:
  *                  cells row-major (y, x) in the rotated frame, 8 orientation
  *                  bins fastest; unit L2 norm
  *   kp_count[i]    records written for image i (host, or device with
@@ -194,8 +195,8 @@ cdvs_status cdvs_scale_space(cdvs_ctx *ctx, const uint8_t *image, const cdvs_ima
  * its stream around each kernel stage; cdvs_profile_read() waits for the
  * recorded events, adds each stage's elapsed device time (ms) and launch
  * count to ms[s] / launches[s] for stage s in
- *   0 detect (one launch per octave), 1 dedupe + select, 2 orientation,
- *   3 record packing, 4 descriptors,
+ *   0 detect (one launch per octave), 1 dedupe + select, 2 orientation and
+ *   descriptors, 3 record offsets, 4 record packing,
  * and clears the record when `reset` is nonzero.  Returns the number of
  * stages (5) or -1 on error.
  */

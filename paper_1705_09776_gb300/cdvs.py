@@ -48,7 +48,7 @@ assert PARAMS_DTYPE.itemsize == 72 and KEYPOINT_DTYPE.itemsize == 44
 EXPORTED = ["cdvs_params_default", "cdvs_create", "cdvs_destroy", "cdvs_last_error", "cdvs_extract",
             "cdvs_candidates", "cdvs_dedupe_select", "cdvs_describe", "cdvs_scale_space",
             "cdvs_rank_host", "cdvs_transform_ternary", "cdvs_profile", "cdvs_profile_read"]
-STAGES = ["detect", "select", "orient", "pack", "describe"]
+STAGES = ["detect", "select", "describe", "offsets", "pack"]
 
 
 class CdvsError(RuntimeError):

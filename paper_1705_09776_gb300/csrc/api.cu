@@ -39,7 +39,7 @@ struct cdvs_ctx {
   int n_sms = 0;
   std::string err;
   DevBuf levels, cands, cand_count, order, keep, sel, sel_count, ori_theta, ori_count, rec_map,
-      rec_total, out_kp, out_desc, out_count, plans, tile_prefix, status, input, dump;
+      rec_total, out_kp, out_desc, out_count, plans, tile_prefix, status, input, dump, stage_kp, stage_desc;
   HostBuf small;  // pinned: status word + record total
   std::vector<ImgPlan> h_plans;
   std::vector<int> h_prefix;
@@ -377,6 +377,13 @@ DescribeArgs describe_args(cdvs_ctx* c, int n, const cdvs_params& p) {
   d.desc_radius = p.desc_radius;
   d.cell_side = p.cell_side;
   d.desc_wsig = p.desc_weight_sigma;
+  // the largest sampling disc of a detected point (sigma <= 2 sigma0 in
+  // octave px) plus the gradient margin; larger discs read global memory
+  const double smax = 2.0 * (double)p.sigma0 * (1.0 + 1e-3);
+  const double rmax = std::max((double)p.desc_radius, p.upright ? 0.0 : (double)p.ori_radius) * smax;
+  d.patch_side = std::min(2 * (int)std::ceil(rmax) + 3, 55);
+  d.stage_kp = static_cast<cdvs_keypoint*>(c->stage_kp.p);
+  d.stage_desc = static_cast<float*>(c->stage_desc.p);
   return d;
 }
 
@@ -444,6 +451,8 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
       (e = ensure(c->rec_map, sizeof(int) * ((size_t)capacity + slots + 1))) != cudaSuccess ||
       (e = ensure(c->rec_total, sizeof(int) * 4)) != cudaSuccess ||
       (e = ensure(c->status, sizeof(int) * 4)) != cudaSuccess ||
+      (e = ensure(c->stage_kp, sizeof(cdvs_keypoint) * slots * p.max_orientations)) != cudaSuccess ||
+      (e = ensure(c->stage_desc, sizeof(float) * 128 * slots * p.max_orientations)) != cudaSuccess ||
       (e = ensure_host(c->small, sizeof(int) * 4)) != cudaSuccess)
     return cuda_fail(c, e, "workspace");
 
@@ -558,6 +567,8 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
   DescribeArgs d = describe_args(c, n, p);
   d.kp_capacity = capacity;
   const bool dev_out = (flags & CDVS_OUTPUT_DEVICE) != 0;
+  if (dev_out && (reinterpret_cast<uintptr_t>(desc_out) & 15) != 0)
+    return fail(c, CDVS_INVALID_ARGUMENT, "device desc_out must be 16-byte aligned");
   if (dev_out) {
     d.kp_out = kp_out;
     d.desc_out = desc_out;
@@ -572,13 +583,13 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
     d.kp_count = static_cast<int*>(c->out_count.p);
   }
   ev = prof_begin(c, s);
-  if ((e = launch_orient(d, p.storage, s)) != cudaSuccess) return cuda_fail(c, e, "orientation launch");
+  if ((e = launch_describe(d, p.storage, s)) != cudaSuccess) return cuda_fail(c, e, "describe launch");
   prof_end(c, 2, 1, ev, s);
   ev = prof_begin(c, s);
   if ((e = launch_pack(d, s)) != cudaSuccess) return cuda_fail(c, e, "packing launch");
   prof_end(c, 3, 1, ev, s);
   ev = prof_begin(c, s);
-  if ((e = launch_desc(d, p.storage, c->n_sms, s)) != cudaSuccess) return cuda_fail(c, e, "descriptor launch");
+  if ((e = launch_copy(d, c->n_sms, s)) != cudaSuccess) return cuda_fail(c, e, "copy launch");
   prof_end(c, 4, 1, ev, s);
   if ((e = cudaMemcpyAsync(h_small, c->status.p, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(h_small + 1, c->rec_total.p, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
@@ -652,7 +663,7 @@ void cdvs_destroy(cdvs_ctx* c) {
   DevBuf* bufs[] = {&c->levels,  &c->cands,   &c->cand_count, &c->order,   &c->keep,
                     &c->sel,     &c->sel_count, &c->ori_theta, &c->ori_count, &c->rec_map,
                     &c->rec_total, &c->out_kp, &c->out_desc, &c->out_count, &c->plans,
-                    &c->tile_prefix, &c->status, &c->input, &c->dump};
+                    &c->tile_prefix, &c->status, &c->input, &c->dump, &c->stage_kp, &c->stage_desc};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (c->small.p) cudaFreeHost(c->small.p);

@@ -118,6 +118,9 @@ struct DescribeArgs {
   int max_ori;
   float ori_radius, ori_ratio, ori_wsig;
   float desc_radius, cell_side, desc_wsig;
+  int patch_side;               // staged patch side (pixels) per point
+  cdvs_keypoint* stage_kp;      // n_images x N x max_ori staging slots
+  float* stage_desc;            // n_images x N x max_ori x 128
 };
 
 // launchers (defined in the .cu files)
@@ -125,9 +128,10 @@ size_t detect_smem_bytes(int max_radius);
 cudaError_t launch_detect(const DetectArgs& a, int n_tiles, int max_radius, int storage, int n_sms,
                           cudaStream_t s);
 cudaError_t launch_select(const SelectArgs& a, int n_images, cudaStream_t s);
-cudaError_t launch_orient(const DescribeArgs& a, int storage, cudaStream_t s);
+size_t describe_smem_bytes(int patch_side);
+cudaError_t launch_describe(const DescribeArgs& a, int storage, cudaStream_t s);
 cudaError_t launch_pack(const DescribeArgs& a, cudaStream_t s);
-cudaError_t launch_desc(const DescribeArgs& a, int storage, int n_sms, cudaStream_t s);
+cudaError_t launch_copy(const DescribeArgs& a, int n_sms, cudaStream_t s);
 cudaError_t launch_levels_to_f32(const ImgPlan* plans, int img, const void* levels, int storage,
                                  int octave, int k, int W, int H, long long off, int lpitch,
                                  float* out, cudaStream_t s);

@@ -1,20 +1,20 @@
-// describe.cu -- Alg. 2 on the GPU: K5 dominant orientations (stage A),
-// a scan that packs the (point, orientation) records of the whole batch, and
-// K6 128-D descriptors (stage B).
+// describe.cu -- Alg. 2 on the GPU: dominant orientations (stage A) and
+// 128-D descriptors (stage B), then the packing of the (point, orientation)
+// records of the whole batch.
 //
-// One warp per point (K5) and one warp per record (K6): the lanes stride
-// over the pixels of the sampling disc and vote into lane-private histograms
-// in shared memory laid out [bin][lane] (bank = lane, no conflicts, no
-// atomics); the lane copies are summed in a fixed order, so the result does
-// not depend on scheduling.
+// One warp per selected point: the warp stages the point's patch of its
+// Gaussian level in shared memory (coalesced row loads), builds the 36-bin
+// orientation histogram from it, finds the orientations, and for each one
+// builds the 4x4x8 descriptor histogram.  The lanes stride over the pixels of
+// the sampling disc and add their votes to a per-warp histogram with 64-bit
+// integer atomics on a 2^-24 fixed-point scale: integer addition is
+// associative, so the sums do not depend on the order in which lanes land.
 #include "cdvs_internal.cuh"
 
 namespace cdvs {
 namespace {
 
 constexpr float kTwoPi = 6.283185307179586f;
-constexpr int kOriWarps = 8;
-constexpr int kDescWarps = 4;
 constexpr int kScanThreads = 1024;
 
 __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
@@ -57,67 +57,119 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-// ---- K5: 36-bin orientation histogram over the disc of radius
-// ori_radius * sigma, weight |g| exp(-d^2 / (2 (ori_wsig sigma)^2)); peaks
-// strictly above both circular neighbours and above ori_ratio * max, each
-// refined by a parabola through three bins.
+// votes of one histogram bin, fixed point with 24 fractional bits
+constexpr float kFixScale = 16777216.0f;
+constexpr float kFixInv = 1.0f / 16777216.0f;
+constexpr int kFWarps = 8;
+
+__device__ __forceinline__ void vote(unsigned long long* h, float w) {
+  atomicAdd(h, __float2ull_rn(w * kFixScale));
+}
+
+// Walks the bw x bh box starting at (u0, v0): calls f(u, v) for the box
+// pixels of this lane (index lane, lane + 32, ...) without a division per step.
+template <typename F>
+__device__ __forceinline__ void for_box(int u0, int v0, int bw, int bh, int lane, F&& f) {
+  if (bw <= 0 || bh <= 0) return;
+  const int dq = 32 / bw, dr = 32 - dq * bw;
+  int vv = lane / bw, uu = lane - vv * bw;
+  for (int i = lane; i < bw * bh; i += 32) {
+    f(u0 + uu, v0 + vv);
+    uu += dr;
+    vv += dq;
+    if (uu >= bw) {
+      uu -= bw;
+      ++vv;
+    }
+  }
+}
+
+// ---- Alg. 2, fused per point.  Stage A: 36-bin histogram of atan2(gy, gx)
+// over the disc of radius ori_radius * sigma, weight
+// |g| exp(-d^2 / (2 (ori_wsig sigma)^2)); orientations at bins strictly above
+// both circular neighbours and above ori_ratio * max, refined by a parabola
+// through three bins, in order of bin value.  Stage B, per orientation: 4x4
+// cells of side cell_side * sigma in the frame rotated by -theta, 8 bins of
+// the gradient angle relative to theta, trilinear votes weighted by
+// |g| exp(-(u^2+v^2) / (2 desc_wsig^2)) ((u, v) in cells) over the disc of
+// radius desc_radius * sigma; L2-normalise, clamp at 0.2, renormalise.
+// Records and descriptors go to per-point staging slots (max_ori each).
 template <typename StoreT>
-__global__ void __launch_bounds__(kOriWarps * 32) orient_kernel(const __grid_constant__ DescribeArgs a) {
-  __shared__ float hist[kOriWarps][36][32];
-  __shared__ float h36[kOriWarps][36];
+__global__ void __launch_bounds__(kFWarps * 32) describe_kernel(const __grid_constant__ DescribeArgs a) {
+  extern __shared__ float4 smem4[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int slot = blockIdx.x * kOriWarps + warp;
+  const int P = a.patch_side;
+  float* patch = reinterpret_cast<float*>(smem4) + (size_t)warp * P * P;
+  unsigned long long* hist =
+      reinterpret_cast<unsigned long long*>(reinterpret_cast<float*>(smem4) + (size_t)kFWarps * P * P) +
+      warp * (36 + 128);
+  unsigned long long* ho = hist;        // 36 orientation bins
+  unsigned long long* hd = hist + 36;   // 128 descriptor bins
+  const int slot = blockIdx.x * kFWarps + warp;
   if (slot >= a.n_images * a.N) return;
   const int img = slot / a.N, rank = slot - img * a.N;
   if (rank >= a.sel_count[img]) return;
   const Cand c = a.sel[slot];
-  float* th = a.ori_theta + (size_t)slot * kMaxOri;
-  if (a.upright) {
-    if (lane == 0) {
-      th[0] = 0.0f;
-      a.ori_count[slot] = 1;
-    }
-    return;
-  }
   const int k = desc_level(c.so, a.sigma0);
   const LevelView<StoreT> G = level_of<StoreT>(a, img, c.octave, k);
-  float(*hw)[32] = hist[warp];
-  for (int b = 0; b < 36; ++b) hw[b][lane] = 0.0f;
-  const float R = a.ori_radius * c.so, R2 = R * R;
-  const float sw = a.ori_wsig * c.so;
-  const float inv2 = 1.0f / (2.0f * sw * sw);
+  const float Rd = a.desc_radius * c.so, Ro = a.ori_radius * c.so;
+  const float R = fmaxf(Rd, a.upright ? 0.0f : Ro);
   const int u0 = max((int)ceilf(c.xo - R), 0), u1 = min((int)floorf(c.xo + R), G.W - 1);
   const int v0 = max((int)ceilf(c.yo - R), 0), v1 = min((int)floorf(c.yo + R), G.H - 1);
-  const int bw = u1 - u0 + 1, bh = v1 - v0 + 1;
-  if (bw > 0 && bh > 0) {
-    for (int i = lane; i < bw * bh; i += 32) {
-      const int vv = i / bw;
-      const int v = v0 + vv, u = u0 + (i - vv * bw);
+  // the patch: the sampling box plus the pixels its gradients read
+  const int pu0 = max(u0 - 1, 0), pu1 = min(u1 + 1, G.W - 1);
+  const int pv0 = max(v0 - 1, 0), pv1 = min(v1 + 1, G.H - 1);
+  const int pw = pu1 - pu0 + 1, ph = pv1 - pv0 + 1;
+  const bool staged = pw > 0 && ph > 0 && pw <= P && ph <= P;
+  if (staged) {
+    for (int r = 0; r < ph; ++r) {
+      const StoreT* row = G.base + (size_t)(pv0 + r) * G.pitch + pu0;
+      for (int cc = lane; cc < pw; cc += 32) patch[r * P + cc] = ld(row + cc);
+    }
+  }
+  __syncwarp();
+  auto at = [&](int u, int v) -> float { return staged ? patch[(v - pv0) * P + (u - pu0)] : G.at(u, v); };
+  // central differences, clamp-to-edge
+  auto grad = [&](int u, int v, float& gx, float& gy) {
+    gx = at(min(u + 1, G.W - 1), v) - at(max(u - 1, 0), v);
+    gy = at(u, min(v + 1, G.H - 1)) - at(u, max(v - 1, 0));
+  };
+
+  // ---- stage A
+  float thetas[kMaxOri];
+  int n_ori = 1;
+  thetas[0] = 0.0f;
+  if (!a.upright) {
+    for (int b = lane; b < 36; b += 32) ho[b] = 0ull;
+    __syncwarp();
+    const float R2 = Ro * Ro;
+    const float sw = a.ori_wsig * c.so;
+    const float inv2 = 1.0f / (2.0f * sw * sw);
+    const int ou0 = max((int)ceilf(c.xo - Ro), 0), ou1 = min((int)floorf(c.xo + Ro), G.W - 1);
+    const int ov0 = max((int)ceilf(c.yo - Ro), 0), ov1 = min((int)floorf(c.yo + Ro), G.H - 1);
+    for_box(ou0, ov0, ou1 - ou0 + 1, ov1 - ov0 + 1, lane, [&](int u, int v) {
       const float du = (float)u - c.xo, dv = (float)v - c.yo;
       const float d2 = du * du + dv * dv;
-      if (!(d2 < R2)) continue;
+      if (!(d2 < R2)) return;
       float gx, gy;
-      G.grad(u, v, gx, gy);
+      grad(u, v, gx, gy);
       const float w = sqrtf(gx * gx + gy * gy) * expf(-d2 * inv2);
       const float f = atan2f(gy, gx) * (36.0f / kTwoPi);
       int b = (int)floorf(f);
       b = ((b % 36) + 36) % 36;
-      hw[b][lane] += w;
-    }
-  }
-  __syncwarp();
-  for (int b = lane; b < 36; b += 32) {
-    float s = 0.0f;
-    for (int l = 0; l < 32; ++l) s += hw[b][l];
-    h36[warp][b] = s;
-  }
-  __syncwarp();
-  const float* h = h36[warp];
-  float mx = fmaxf(h[lane], lane < 4 ? h[32 + lane] : 0.0f);
-  mx = warp_max(mx);
-  if (lane == 0) {
-    float pv[36], pt[36];
-    int pb[36], np = 0;
+      vote(ho + b, w);
+    });
+    __syncwarp();
+    // every lane reads the 36 sums; the peak search is uniform over the warp
+    float h[36];
+#pragma unroll
+    for (int b = 0; b < 36; ++b) h[b] = (float)ho[b] * kFixInv;
+    float mx = 0.0f;
+#pragma unroll
+    for (int b = 0; b < 36; ++b) mx = fmaxf(mx, h[b]);
+    float pv[kMaxOri];
+    n_ori = 0;
+#pragma unroll
     for (int b = 0; b < 36; ++b) {
       const float l = h[(b + 35) % 36], cc = h[b], r = h[(b + 1) % 36];
       if (!(cc > l && cc > r)) continue;
@@ -126,21 +178,107 @@ __global__ void __launch_bounds__(kOriWarps * 32) orient_kernel(const __grid_con
       float t = kTwoPi * ((float)b + 0.5f + off) / 36.0f;
       if (t >= kTwoPi) t -= kTwoPi;
       if (t < 0.0f) t += kTwoPi;
-      // insertion by (value desc, bin asc)
-      int j = np++;
-      while (j > 0 && (cc > pv[j - 1])) {
-        pv[j] = pv[j - 1];
-        pt[j] = pt[j - 1];
-        pb[j] = pb[j - 1];
+      // keep the max_ori largest, by (value desc, bin asc)
+      int j = n_ori < a.max_ori ? n_ori++ : a.max_ori;
+      while (j > 0 && cc > pv[j - 1]) {
+        if (j < a.max_ori) {
+          pv[j] = pv[j - 1];
+          thetas[j] = thetas[j - 1];
+        }
         --j;
       }
-      pv[j] = cc;
-      pt[j] = t;
-      pb[j] = b;
+      if (j < a.max_ori) {
+        pv[j] = cc;
+        thetas[j] = t;
+      }
     }
-    const int n = min(np, a.max_ori);
-    for (int j = 0; j < n; ++j) th[j] = pt[j];
-    a.ori_count[slot] = n;
+  }
+  if (lane == 0) a.ori_count[slot] = n_ori;
+
+  // ---- stage B, per orientation
+  const float Rd2 = Rd * Rd;
+  const float inv_cs = 1.0f / (a.cell_side * c.so);
+  const float inv2w = 1.0f / (2.0f * a.desc_wsig * a.desc_wsig);
+  const int du0 = max((int)ceilf(c.xo - Rd), 0), du1 = min((int)floorf(c.xo + Rd), G.W - 1);
+  const int dv0 = max((int)ceilf(c.yo - Rd), 0), dv1 = min((int)floorf(c.yo + Rd), G.H - 1);
+  const size_t out0 = (size_t)slot * a.max_ori;
+  for (int j = 0; j < n_ori; ++j) {
+    const float theta = thetas[j];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) hd[lane + 32 * q] = 0ull;
+    __syncwarp();
+    float st, ct;
+    sincosf(theta, &st, &ct);
+    for_box(du0, dv0, du1 - du0 + 1, dv1 - dv0 + 1, lane, [&](int u, int v) {
+      const float du = (float)u - c.xo, dv = (float)v - c.yo;
+      if (!(du * du + dv * dv < Rd2)) return;
+      const float xr = (ct * du + st * dv) * inv_cs;
+      const float yr = (-st * du + ct * dv) * inv_cs;
+      float gx, gy;
+      grad(u, v, gx, gy);
+      const float mag = sqrtf(gx * gx + gy * gy);
+      float ang = atan2f(gy, gx) - theta;
+      while (ang < 0.0f) ang += kTwoPi;
+      while (ang >= kTwoPi) ang -= kTwoPi;
+      float ob = ang * (8.0f / kTwoPi);
+      if (ob >= 8.0f) ob -= 8.0f;
+      const float w = mag * expf(-(xr * xr + yr * yr) * inv2w);
+      const float cx = xr + 1.5f, cy = yr + 1.5f;
+      const float fx0 = floorf(cx), fy0 = floorf(cy), fo0 = floorf(ob);
+      const float fx = cx - fx0, fy = cy - fy0, fo = ob - fo0;
+      const int x0 = (int)fx0, y0 = (int)fy0, o0 = (int)fo0;
+#pragma unroll
+      for (int iy = 0; iy < 2; ++iy) {
+        const int yy = y0 + iy;
+        if (yy < 0 || yy > 3) continue;
+        const float wy = w * (iy ? fy : 1.0f - fy);
+#pragma unroll
+        for (int ix = 0; ix < 2; ++ix) {
+          const int xx = x0 + ix;
+          if (xx < 0 || xx > 3) continue;
+          const float wxy = wy * (ix ? fx : 1.0f - fx);
+          const int cb = (yy * 4 + xx) * 8;
+          vote(hd + cb + (o0 & 7), wxy * (1.0f - fo));
+          vote(hd + cb + ((o0 + 1) & 7), wxy * fo);
+        }
+      }
+    });
+    __syncwarp();
+    float v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = (float)hd[lane + 32 * q] * kFixInv;
+    float n2 = warp_sum(v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
+    if (n2 > 0.0f) {
+      const float inv = 1.0f / sqrtf(n2);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] = fminf(v[q] * inv, 0.2f);
+      n2 = warp_sum(v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
+      const float inv2 = 1.0f / sqrtf(n2);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] *= inv2;
+    }
+    float* d = a.stage_desc + (out0 + j) * 128;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) d[lane + 32 * q] = v[q];
+    if (lane == 0) {
+      const float s = (float)(1 << c.octave);
+      cdvs_keypoint kp;
+      kp.x = c.xo * s;
+      kp.y = c.yo * s;
+      kp.sigma = c.so * s;
+      kp.theta = theta;
+      kp.response = c.resp;
+      kp.p_ss = c.pss;
+      kp.ratio = c.ratio;
+      kp.octave = c.octave;
+      kp.scale_idx = (int16_t)k;
+      kp.type = c.type;
+      kp.reserved = 0;
+      kp.image = img;
+      kp.parent_id = rank;
+      a.stage_kp[out0 + j] = kp;
+    }
+    __syncwarp();
   }
 }
 
@@ -198,112 +336,16 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(const __grid_constan
   }
 }
 
-// ---- K6: 4x4 cells of side cell_side * sigma in the frame rotated by -theta,
-// 8 orientation bins, trilinear votes weighted by |g| exp(-(u^2+v^2) /
-// (2 desc_wsig^2)) with (u, v) in cells, over the disc of radius desc_radius *
-// sigma; L2-normalise, clamp at 0.2, renormalise.
-template <typename StoreT>
-__global__ void __launch_bounds__(kDescWarps * 32) desc_kernel(const __grid_constant__ DescribeArgs a) {
-  extern __shared__ float4 smem4[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float(*hw)[32] = reinterpret_cast<float(*)[32]>(reinterpret_cast<float*>(smem4) + warp * 128 * 32);
+// ---- packed output: record r of the batch comes from staging slot rec_map[r]
+__global__ void __launch_bounds__(256) copy_kernel(const __grid_constant__ DescribeArgs a) {
+  const int lane = threadIdx.x & 31;
   const int total = *a.rec_total;
-  for (int r = blockIdx.x * kDescWarps + warp; r < total; r += gridDim.x * kDescWarps) {
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < total; r += (gridDim.x * blockDim.x) >> 5) {
     const int m = a.rec_map[r];
-    const int slot = m / kMaxOri;
-    const int img = slot / a.N, rank = slot - img * a.N;
-    const Cand c = a.sel[slot];
-    const float theta = a.ori_theta[m];
-    const int k = desc_level(c.so, a.sigma0);
-    const LevelView<StoreT> G = level_of<StoreT>(a, img, c.octave, k);
-    for (int b = 0; b < 128; ++b) hw[b][lane] = 0.0f;
-    const float R = a.desc_radius * c.so, R2 = R * R;
-    const float inv_cs = 1.0f / (a.cell_side * c.so);
-    float st, ct;
-    sincosf(theta, &st, &ct);
-    const float inv2w = 1.0f / (2.0f * a.desc_wsig * a.desc_wsig);
-    const int u0 = max((int)ceilf(c.xo - R), 0), u1 = min((int)floorf(c.xo + R), G.W - 1);
-    const int v0 = max((int)ceilf(c.yo - R), 0), v1 = min((int)floorf(c.yo + R), G.H - 1);
-    const int bw = u1 - u0 + 1, bh = v1 - v0 + 1;
-    if (bw > 0 && bh > 0) {
-      for (int i = lane; i < bw * bh; i += 32) {
-        const int vv = i / bw;
-        const int v = v0 + vv, u = u0 + (i - vv * bw);
-        const float du = (float)u - c.xo, dv = (float)v - c.yo;
-        if (!(du * du + dv * dv < R2)) continue;
-        const float xr = (ct * du + st * dv) * inv_cs;
-        const float yr = (-st * du + ct * dv) * inv_cs;
-        float gx, gy;
-        G.grad(u, v, gx, gy);
-        const float mag = sqrtf(gx * gx + gy * gy);
-        float ang = atan2f(gy, gx) - theta;
-        while (ang < 0.0f) ang += kTwoPi;
-        while (ang >= kTwoPi) ang -= kTwoPi;
-        float ob = ang * (8.0f / kTwoPi);
-        if (ob >= 8.0f) ob -= 8.0f;
-        const float w = mag * expf(-(xr * xr + yr * yr) * inv2w);
-        const float cx = xr + 1.5f, cy = yr + 1.5f;
-        const float fx0 = floorf(cx), fy0 = floorf(cy), fo0 = floorf(ob);
-        const float fx = cx - fx0, fy = cy - fy0, fo = ob - fo0;
-        const int x0 = (int)fx0, y0 = (int)fy0, o0 = (int)fo0;
-#pragma unroll
-        for (int iy = 0; iy < 2; ++iy) {
-          const int yy = y0 + iy;
-          if (yy < 0 || yy > 3) continue;
-          const float wy = w * (iy ? fy : 1.0f - fy);
-#pragma unroll
-          for (int ix = 0; ix < 2; ++ix) {
-            const int xx = x0 + ix;
-            if (xx < 0 || xx > 3) continue;
-            const float wxy = wy * (ix ? fx : 1.0f - fx);
-            const int cb = (yy * 4 + xx) * 8;
-            hw[cb + (o0 & 7)][lane] += wxy * (1.0f - fo);
-            hw[cb + ((o0 + 1) & 7)][lane] += wxy * fo;
-          }
-        }
-      }
-    }
-    __syncwarp();
-    float v[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int b = lane + 32 * j;
-      float s = 0.0f;
-      for (int l = 0; l < 32; ++l) s += hw[b][l];
-      v[j] = s;
-    }
-    float n2 = warp_sum(v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
-    if (n2 > 0.0f) {
-      const float inv = 1.0f / sqrtf(n2);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) v[j] = fminf(v[j] * inv, 0.2f);
-      n2 = warp_sum(v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
-      const float inv2 = 1.0f / sqrtf(n2);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) v[j] *= inv2;
-    }
-    float* d = a.desc_out + (size_t)r * 128;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) d[lane + 32 * j] = v[j];
-    if (lane == 0) {
-      const float s = (float)(1 << c.octave);
-      cdvs_keypoint kp;
-      kp.x = c.xo * s;
-      kp.y = c.yo * s;
-      kp.sigma = c.so * s;
-      kp.theta = theta;
-      kp.response = c.resp;
-      kp.p_ss = c.pss;
-      kp.ratio = c.ratio;
-      kp.octave = c.octave;
-      kp.scale_idx = (int16_t)k;
-      kp.type = c.type;
-      kp.reserved = 0;
-      kp.image = img;
-      kp.parent_id = rank;
-      a.kp_out[r] = kp;
-    }
-    __syncwarp();
+    const size_t src = (size_t)(m / kMaxOri) * a.max_ori + (m % kMaxOri);
+    reinterpret_cast<float4*>(a.desc_out + (size_t)r * 128)[lane] =
+        reinterpret_cast<const float4*>(a.stage_desc + src * 128)[lane];
+    if (lane == 0) a.kp_out[r] = a.stage_kp[src];
   }
 }
 
@@ -316,12 +358,25 @@ __global__ void levels_to_f32_kernel(const StoreT* src, int W, int H, int lpitch
 
 }  // namespace
 
-cudaError_t launch_orient(const DescribeArgs& a, int storage, cudaStream_t s) {
+size_t describe_smem_bytes(int patch_side) {
+  return (size_t)kFWarps * ((size_t)patch_side * patch_side * sizeof(float) + (36 + 128) * sizeof(unsigned long long));
+}
+
+cudaError_t launch_describe(const DescribeArgs& a, int storage, cudaStream_t s) {
   const int slots = a.n_images * a.N;
   if (slots <= 0) return cudaSuccess;
-  const int ob = (slots + kOriWarps - 1) / kOriWarps;
-  if (storage == CDVS_STORAGE_FP16) orient_kernel<__half><<<ob, kOriWarps * 32, 0, s>>>(a);
-  else orient_kernel<float><<<ob, kOriWarps * 32, 0, s>>>(a);
+  const int grid = (slots + kFWarps - 1) / kFWarps;
+  const size_t smem = describe_smem_bytes(a.patch_side);
+  cudaError_t e;
+  if (storage == CDVS_STORAGE_FP16) {
+    e = cudaFuncSetAttribute(describe_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    describe_kernel<__half><<<grid, kFWarps * 32, smem, s>>>(a);
+  } else {
+    e = cudaFuncSetAttribute(describe_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    describe_kernel<float><<<grid, kFWarps * 32, smem, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -333,20 +388,9 @@ cudaError_t launch_pack(const DescribeArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_desc(const DescribeArgs& a, int storage, int n_sms, cudaStream_t s) {
+cudaError_t launch_copy(const DescribeArgs& a, int n_sms, cudaStream_t s) {
   if (a.n_images * a.N <= 0) return cudaSuccess;
-  const size_t dsmem = sizeof(float) * 128 * 32 * kDescWarps;
-  const int db = n_sms * 4;
-  cudaError_t e;
-  if (storage == CDVS_STORAGE_FP16) {
-    e = cudaFuncSetAttribute(desc_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem);
-    if (e != cudaSuccess) return e;
-    desc_kernel<__half><<<db, kDescWarps * 32, dsmem, s>>>(a);
-  } else {
-    e = cudaFuncSetAttribute(desc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem);
-    if (e != cudaSuccess) return e;
-    desc_kernel<float><<<db, kDescWarps * 32, dsmem, s>>>(a);
-  }
+  copy_kernel<<<n_sms * 8, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -161,19 +161,22 @@ __device__ __forceinline__ InputRef<InT> input_ref(const DetectArgs& a, const Ti
   return r;
 }
 
-// One thread issues the bulk copies of every input row of tile t into raw
-// (column c of a raw row is image x = tx0 - cm + c; rows clamp to the image).
+// The 32 lanes of warp 0 issue the bulk copies of every input row of tile t
+// into raw (column c of a raw row is image x = tx0 - cm + c; rows clamp to the
+// image); lane 0 first announces the byte count on the mbarrier.
 template <typename InT>
 __device__ __forceinline__ void issue_tile_copy(const Tile& t, const InputRef<InT>& r, int ic, int rm, InT* raw,
                                                 unsigned long long* bar) {
+  const int lane = threadIdx.x & 31;
   const int cm = (ic - kTX) / 2;
   const int IR = kRows + 2 * rm;
   const int y0 = t.ty0 - kHalo - rm;
   const int x0 = t.tx0 - cm;
   const unsigned row_bytes = (unsigned)((r.ce - r.cs) * sizeof(InT));
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  mbar_expect_tx(bar, row_bytes * IR);
-  for (int i = 0; i < IR; ++i) {
+  if (lane == 0) mbar_expect_tx(bar, row_bytes * IR);
+  __syncwarp();
+  for (int i = lane; i < IR; i += 32) {
     const int y = min(max(y0 + i, 0), t.H - 1);
     bulk_copy_g2s(raw + (size_t)i * ic + (r.cs - x0), r.base + (size_t)y * r.pitch + r.cs, row_bytes, bar);
   }
@@ -641,7 +644,7 @@ __global__ void __launch_bounds__(kDetThreads, 1)
   if (b >= n_tiles) return;
   Tile cur = locate(a, b);
   InputRef<InT> cref = input_ref<InT>(a, cur, ic);
-  if (threadIdx.x == 0 && cref.bulk) issue_tile_copy<InT>(cur, cref, ic, rm, raw, &sh.bar);
+  if (warp == 0 && cref.bulk) issue_tile_copy<InT>(cur, cref, ic, rm, raw, &sh.bar);
   bool pending_copy = cref.bulk;
 
   for (; b < n_tiles; b += gridDim.x) {
@@ -668,7 +671,7 @@ __global__ void __launch_bounds__(kDetThreads, 1)
     if (nb < n_tiles) {
       nxt = locate(a, nb);
       nref = input_ref<InT>(a, nxt, ic);
-      if (threadIdx.x == 0 && nref.bulk) issue_tile_copy<InT>(nxt, nref, ic, rm, raw, &sh.bar);
+      if (warp == 0 && nref.bulk) issue_tile_copy<InT>(nxt, nref, ic, rm, raw, &sh.bar);
       pending_copy = nref.bulk;
     }
 
@@ -703,7 +706,13 @@ __global__ void __launch_bounds__(kDetThreads, 1)
     // cubic coefficients of Eq. 3 on packed pairs, then the admissible
     // extremum in scale; survivors are compacted into `in` and `tmp`
     Pending* pend = reinterpret_cast<Pending*>(in);
-    for (int it = 0; it < (kTX * kTY / 2) / kDetThreads; ++it) {
+    constexpr int kIt = (kTX * kTY / 2) / kDetThreads;
+    int bt[kIt][2];
+    float tb[kIt][2];
+    // all pixel pairs of the thread first (independent work in flight), then
+    // the compaction
+#pragma unroll
+    for (int it = 0; it < kIt; ++it) {
       const int idx = it * kDetThreads + threadIdx.x;
       const int m = idx / kTX, lx = idx - (idx / kTX) * kTX;
       float2 Lk[kScales];
@@ -720,26 +729,29 @@ __global__ void __launch_bounds__(kDetThreads, 1)
       }
       const int x = tx0 + lx, y0 = ty0 + 2 * m;
       const bool inx = x >= 1 && x < W - 1;
-      int bt[2];
-      float tb[2];
-      cubic_extremum2(a, al2, inx && y0 >= 1 && y0 < H - 1, inx && y0 + 1 < H - 1, bt, tb);
-      const unsigned m0 = __ballot_sync(0xffffffffu, bt[0] != 0);
-      const unsigned m1 = __ballot_sync(0xffffffffu, bt[1] != 0);
+      cubic_extremum2(a, al2, inx && y0 >= 1 && y0 < H - 1, inx && y0 + 1 < H - 1, bt[it], tb[it]);
+    }
+#pragma unroll
+    for (int it = 0; it < kIt; ++it) {
+      const int idx = it * kDetThreads + threadIdx.x;
+      const int m = idx / kTX, lx = idx - (idx / kTX) * kTX;
+      const unsigned m0 = __ballot_sync(0xffffffffu, bt[it][0] != 0);
+      const unsigned m1 = __ballot_sync(0xffffffffu, bt[it][1] != 0);
       if (m0 | m1) {
         int base = 0;
         if (lane == 0) base = atomicAdd(&sh.n_pending, __popc(m0) + __popc(m1));
         base = __shfl_sync(0xffffffffu, base, 0);
         const unsigned below = (1u << lane) - 1u;
-        if (bt[0] != 0) {
+        if (bt[it][0] != 0) {
           Pending e;
-          e.code = ((2 * m) << 16) | (lx << 1) | (bt[0] > 0 ? 1 : 0);
-          e.t = tb[0];
+          e.code = ((2 * m) << 16) | (lx << 1) | (bt[it][0] > 0 ? 1 : 0);
+          e.t = tb[it][0];
           pend[base + __popc(m0 & below)] = e;
         }
-        if (bt[1] != 0) {
+        if (bt[it][1] != 0) {
           Pending e;
-          e.code = ((2 * m + 1) << 16) | (lx << 1) | (bt[1] > 0 ? 1 : 0);
-          e.t = tb[1];
+          e.code = ((2 * m + 1) << 16) | (lx << 1) | (bt[it][1] > 0 ? 1 : 0);
+          e.t = tb[it][1];
           pend[base + __popc(m0) + __popc(m1 & below)] = e;
         }
       }
