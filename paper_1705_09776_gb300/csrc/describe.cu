@@ -6,8 +6,8 @@
 // Gaussian level in shared memory (coalesced row loads), builds the 36-bin
 // orientation histogram from it, finds the orientations, and for each one
 // builds the 4x4x8 descriptor histogram.  The lanes stride over the pixels of
-// the sampling disc and add their votes to a per-warp histogram with 64-bit
-// integer atomics on a 2^-24 fixed-point scale: integer addition is
+// the sampling disc and add their votes to a per-warp histogram with 32-bit
+// integer atomics on a 2^-13 fixed-point scale: integer addition is
 // associative, so the sums do not depend on the order in which lanes land.
 #include "cdvs_internal.cuh"
 
@@ -57,13 +57,23 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-// votes of one histogram bin, fixed point with 24 fractional bits
-constexpr float kFixScale = 16777216.0f;
-constexpr float kFixInv = 1.0f / 16777216.0f;
+// Votes are summed as unsigned 32-bit fixed point.  A vote is |g| times
+// weights <= 1 with |g| <= 255 * sqrt(2) < 512, so n votes stay below
+// 512 n; the scale is the largest power of two <= 2^13 that keeps 512 n
+// below 2^32 for the n pixels of the sampling box.  The scaled vote is rounded
+// by adding 1.5 * 2^23 in FP32 (exact for values below 2^22) and reading the
+// mantissa.
 constexpr int kFWarps = 8;
 
-__device__ __forceinline__ void vote(unsigned long long* h, float w) {
-  atomicAdd(h, __float2ull_rn(w * kFixScale));
+__device__ __forceinline__ float vote_scale(int n_pixels) {
+  int sh = 13;
+  while (sh > 0 && (512.0 * (double)(n_pixels + 1)) * (double)(1 << sh) >= 4294967296.0) --sh;
+  return (float)(1 << sh);
+}
+
+__device__ __forceinline__ void vote(unsigned* h, float w, float scale) {
+  const unsigned q = (unsigned)(__float_as_int(fmaf(w, scale, 12582912.0f)) - 0x4B400000);
+  atomicAdd(h, q);
 }
 
 // Walks the bw x bh box starting at (u0, v0): calls f(u, v) for the box
@@ -100,11 +110,10 @@ __global__ void __launch_bounds__(kFWarps * 32) describe_kernel(const __grid_con
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int P = a.patch_side;
   float* patch = reinterpret_cast<float*>(smem4) + (size_t)warp * P * P;
-  unsigned long long* hist =
-      reinterpret_cast<unsigned long long*>(reinterpret_cast<float*>(smem4) + (size_t)kFWarps * P * P) +
-      warp * (36 + 128);
-  unsigned long long* ho = hist;        // 36 orientation bins
-  unsigned long long* hd = hist + 36;   // 128 descriptor bins
+  unsigned* hist = reinterpret_cast<unsigned*>(reinterpret_cast<float*>(smem4) + (size_t)kFWarps * P * P) +
+                   warp * (36 + 128);
+  unsigned* ho = hist;        // 36 orientation bins
+  unsigned* hd = hist + 36;   // 128 descriptor bins
   const int slot = blockIdx.x * kFWarps + warp;
   if (slot >= a.n_images * a.N) return;
   const int img = slot / a.N, rank = slot - img * a.N;
@@ -140,13 +149,14 @@ __global__ void __launch_bounds__(kFWarps * 32) describe_kernel(const __grid_con
   int n_ori = 1;
   thetas[0] = 0.0f;
   if (!a.upright) {
-    for (int b = lane; b < 36; b += 32) ho[b] = 0ull;
+    for (int b = lane; b < 36; b += 32) ho[b] = 0u;
     __syncwarp();
     const float R2 = Ro * Ro;
     const float sw = a.ori_wsig * c.so;
     const float inv2 = 1.0f / (2.0f * sw * sw);
     const int ou0 = max((int)ceilf(c.xo - Ro), 0), ou1 = min((int)floorf(c.xo + Ro), G.W - 1);
     const int ov0 = max((int)ceilf(c.yo - Ro), 0), ov1 = min((int)floorf(c.yo + Ro), G.H - 1);
+    const float osc = vote_scale(max(ou1 - ou0 + 1, 0) * max(ov1 - ov0 + 1, 0));
     for_box(ou0, ov0, ou1 - ou0 + 1, ov1 - ov0 + 1, lane, [&](int u, int v) {
       const float du = (float)u - c.xo, dv = (float)v - c.yo;
       const float d2 = du * du + dv * dv;
@@ -157,13 +167,13 @@ __global__ void __launch_bounds__(kFWarps * 32) describe_kernel(const __grid_con
       const float f = atan2f(gy, gx) * (36.0f / kTwoPi);
       int b = (int)floorf(f);
       b = ((b % 36) + 36) % 36;
-      vote(ho + b, w);
+      vote(ho + b, w, osc);
     });
     __syncwarp();
     // every lane reads the 36 sums; the peak search is uniform over the warp
     float h[36];
 #pragma unroll
-    for (int b = 0; b < 36; ++b) h[b] = (float)ho[b] * kFixInv;
+    for (int b = 0; b < 36; ++b) h[b] = (float)ho[b] / osc;
     float mx = 0.0f;
 #pragma unroll
     for (int b = 0; b < 36; ++b) mx = fmaxf(mx, h[b]);
@@ -201,11 +211,12 @@ __global__ void __launch_bounds__(kFWarps * 32) describe_kernel(const __grid_con
   const float inv2w = 1.0f / (2.0f * a.desc_wsig * a.desc_wsig);
   const int du0 = max((int)ceilf(c.xo - Rd), 0), du1 = min((int)floorf(c.xo + Rd), G.W - 1);
   const int dv0 = max((int)ceilf(c.yo - Rd), 0), dv1 = min((int)floorf(c.yo + Rd), G.H - 1);
+  const float dsc = vote_scale(max(du1 - du0 + 1, 0) * max(dv1 - dv0 + 1, 0));
   const size_t out0 = (size_t)slot * a.max_ori;
   for (int j = 0; j < n_ori; ++j) {
     const float theta = thetas[j];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) hd[lane + 32 * q] = 0ull;
+    for (int q = 0; q < 4; ++q) hd[lane + 32 * q] = 0u;
     __syncwarp();
     float st, ct;
     sincosf(theta, &st, &ct);
@@ -238,15 +249,15 @@ __global__ void __launch_bounds__(kFWarps * 32) describe_kernel(const __grid_con
           if (xx < 0 || xx > 3) continue;
           const float wxy = wy * (ix ? fx : 1.0f - fx);
           const int cb = (yy * 4 + xx) * 8;
-          vote(hd + cb + (o0 & 7), wxy * (1.0f - fo));
-          vote(hd + cb + ((o0 + 1) & 7), wxy * fo);
+          vote(hd + cb + (o0 & 7), wxy * (1.0f - fo), dsc);
+          vote(hd + cb + ((o0 + 1) & 7), wxy * fo, dsc);
         }
       }
     });
     __syncwarp();
     float v[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = (float)hd[lane + 32 * q] * kFixInv;
+    for (int q = 0; q < 4; ++q) v[q] = (float)hd[lane + 32 * q] / dsc;
     float n2 = warp_sum(v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
     if (n2 > 0.0f) {
       const float inv = 1.0f / sqrtf(n2);
@@ -359,7 +370,7 @@ __global__ void levels_to_f32_kernel(const StoreT* src, int W, int H, int lpitch
 }  // namespace
 
 size_t describe_smem_bytes(int patch_side) {
-  return (size_t)kFWarps * ((size_t)patch_side * patch_side * sizeof(float) + (36 + 128) * sizeof(unsigned long long));
+  return (size_t)kFWarps * ((size_t)patch_side * patch_side * sizeof(float) + (36 + 128) * sizeof(unsigned));
 }
 
 cudaError_t launch_describe(const DescribeArgs& a, int storage, cudaStream_t s) {
