@@ -227,6 +227,42 @@ int32_t cdvs_rank_host(const cdvs_keypoint *pts, int32_t n, int32_t max_keypoint
 cdvs_status cdvs_transform_ternary(const float *desc, int32_t n, const double *t_lo,
                                    const double *t_hi, int8_t *out, double *v_out);
 
+/*
+ * cdvs_dedupe_select_noalloc -- the cross-octave check and selection of
+ * cdvs_dedupe_select for ONE image, without allocating any memory.  The
+ * paper has no counterpart: this entry point exists for callers that cannot
+ * call cudaMalloc, for example code that runs with a fixed device-memory
+ * budget reserved at start-up, or code that must not add allocations while
+ * other threads capture CUDA graphs (an allocation there can break or
+ * serialise the capture).
+ *
+ * Its scratch (converted candidates, cell order, check flags, selected
+ * points; about 660 KB) is a fixed array inside the library, so every GPU
+ * that loads the library keeps that much device memory until the process
+ * exits.  The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents: calls
+ * whose GPU work overlaps (other streams, other host threads) race and give
+ * wrong results -- serialise them.
+ *
+ *   cand       n_cand candidate records in DEVICE memory (fields x, y, sigma,
+ *              response, p_ss, ratio, octave, type used), octave in 0..11
+ *   n_cand     0 .. CDVS_NOALLOC_MAX_CANDIDATES; more -> CDVS_UNSUPPORTED_SIZE
+ *              (nothing is launched)
+ *   width, height  image size (16..32768) the candidates come from
+ *   sel_out    DEVICE memory for params->max_keypoints records, written in
+ *              rank order with image = 0 and parent_id = index in cand
+ *   sel_count  DEVICE int, receives the number of selected points
+ * Runs asynchronously on cuda_stream on the current device.  No status word
+ * is read back (that would need a synchronisation): the call returns
+ * CDVS_OK once the work is queued, or an argument / launch error.
+ */
+#define CDVS_NOALLOC_MAX_CANDIDATES 16384
+cdvs_status cdvs_dedupe_select_noalloc(const cdvs_keypoint *cand, int32_t n_cand, int32_t width,
+                                       int32_t height, const cdvs_params *params,
+                                       cdvs_keypoint *sel_out, int32_t *sel_count,
+                                       void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

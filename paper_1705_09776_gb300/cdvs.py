@@ -47,7 +47,8 @@ assert PARAMS_DTYPE.itemsize == 72 and KEYPOINT_DTYPE.itemsize == 44
 
 EXPORTED = ["cdvs_params_default", "cdvs_create", "cdvs_destroy", "cdvs_last_error", "cdvs_extract",
             "cdvs_candidates", "cdvs_dedupe_select", "cdvs_describe", "cdvs_scale_space",
-            "cdvs_rank_host", "cdvs_transform_ternary", "cdvs_profile", "cdvs_profile_read"]
+            "cdvs_rank_host", "cdvs_transform_ternary", "cdvs_profile", "cdvs_profile_read",
+            "cdvs_dedupe_select_noalloc"]
 STAGES = ["detect", "select", "describe", "offsets", "pack"]
 
 
@@ -85,6 +86,7 @@ def load(build_if_missing: bool = True):
         "cdvs_transform_ternary": (i32, [P, i32, P, P, P, P]),
         "cdvs_profile": (i32, [P, i32]),
         "cdvs_profile_read": (i32, [P, P, P, i32, i32]),
+        "cdvs_dedupe_select_noalloc": (i32, [P, i32, i32, i32, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -275,6 +277,19 @@ class Context:
             levels.append(lv)
             w, h = (w + 1) // 2, (h + 1) // 2
         return levels
+
+
+NOALLOC_MAX_CANDIDATES = 16384
+
+
+def dedupe_select_noalloc(cand_dev, n_cand, width, height, p, sel_out_dev, sel_count_dev, stream=None) -> int:
+    """cdvs_dedupe_select_noalloc on device buffers (torch tensors or device
+    addresses as ints): no memory is allocated by the library.  Returns the
+    status code (asynchronous: outputs are ready once `stream` is)."""
+    def addr(x):
+        return x if isinstance(x, int) or x is None else x.data_ptr()
+    return load().cdvs_dedupe_select_noalloc(addr(cand_dev), n_cand, width, height, p.ctypes.data,
+                                             addr(sel_out_dev), addr(sel_count_dev), _stream_handle(stream))
 
 
 def rank_host(pts: np.ndarray, max_keypoints: int) -> np.ndarray:
