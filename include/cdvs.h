@@ -122,6 +122,7 @@ const char *cdvs_last_error(const cdvs_ctx *ctx);
  * for the normative relevance tables), dominant orientations (Alg. 2 stage A)
  * and 128-D descriptors (Alg. 2 stage B).
  *
+ *   n_images       0 .. 4096 images in one call
  *   images[i]      pointer to image i (host, or device with CDVS_INPUT_DEVICE)
  *   sizes[i]       its width, height and pitch (host memory)
  *   kp_out         kp_capacity records, packed over the batch: the records of

@@ -419,6 +419,7 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
   if (st != CDVS_OK) return st;
   const cdvs_params& p = *params;
   if (n < 0) return fail(c, CDVS_INVALID_ARGUMENT, "n_images < 0");
+  if (n > kMaxBatch) return fail(c, CDVS_INVALID_ARGUMENT, "at most 4096 images per call");
   if (n == 0) {
     c->err.clear();
     return CDVS_OK;

@@ -18,6 +18,7 @@ constexpr int kMaxOri = 8;       // orientation copies per point
 constexpr int kMaxSelect = 2048; // N limit of the selection step
 constexpr int kSelectList = 4096;  // entries sorted by the selection step (N + ties)
 constexpr int kMaxCells = 8192;  // spatial hash cells of the cross-octave check
+constexpr int kMaxBatch = 4096;  // images per call (the detection tile list lives in shared memory)
 
 // detection tile (output pixels per CTA) and CTA size
 constexpr int kTX = 128;

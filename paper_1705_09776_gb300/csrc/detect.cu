@@ -106,19 +106,20 @@ struct Tile {
   long long level_off;
 };
 
-__device__ __forceinline__ Tile locate(const DetectArgs& a, int b) {
-  // largest i with tile_prefix[i] <= b
+// prefix: the launch's tile_prefix (n_images + 1 entries) in shared memory
+__device__ __forceinline__ Tile locate(const DetectArgs& a, const int* prefix, int b) {
+  // largest i with prefix[i] <= b
   int lo = 0, hi = a.n_images;
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
-    if (a.tile_prefix[mid] <= b) lo = mid;
+    if (prefix[mid] <= b) lo = mid;
     else hi = mid;
   }
   Tile t;
   t.img = lo;
   t.P = a.plans + lo;
   const OctPlan& op = t.P->oct[a.octave];
-  const int k = b - a.tile_prefix[lo];
+  const int k = b - prefix[lo];
   t.tx0 = (k % op.tiles_x) * kTX;
   t.ty0 = (k / op.tiles_x) * kTY;
   t.W = op.W;
@@ -629,9 +630,11 @@ __global__ void __launch_bounds__(kDetThreads, 1)
   float* tmp = in + (size_t)IR * ic;
   float* gs = tmp + kRows * ic;
   float* Ls = gs + kRows * kGC;
+  int* prefix = reinterpret_cast<int*>(Ls + kScales * kRows * kLC);
   const int o = a.octave;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
+  for (int i = threadIdx.x; i <= a.n_images; i += kDetThreads) prefix[i] = a.tile_prefix[i];
   if (threadIdx.x == 0) {
     mbar_init(&sh.bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -642,7 +645,7 @@ __global__ void __launch_bounds__(kDetThreads, 1)
 
   int b = blockIdx.x;
   if (b >= n_tiles) return;
-  Tile cur = locate(a, b);
+  Tile cur = locate(a, prefix, b);
   InputRef<InT> cref = input_ref<InT>(a, cur, ic);
   if (warp == 0 && cref.bulk) issue_tile_copy<InT>(cur, cref, ic, rm, raw, &sh.bar);
   bool pending_copy = cref.bulk;
@@ -669,7 +672,7 @@ __global__ void __launch_bounds__(kDetThreads, 1)
     InputRef<InT> nref = cref;
     nref.bulk = false;
     if (nb < n_tiles) {
-      nxt = locate(a, nb);
+      nxt = locate(a, prefix, nb);
       nref = input_ref<InT>(a, nxt, ic);
       if (warp == 0 && nref.bulk) issue_tile_copy<InT>(nxt, nref, ic, rm, raw, &sh.bar);
       pending_copy = nref.bulk;
@@ -818,15 +821,16 @@ __global__ void __launch_bounds__(kDetThreads, 1)
 // The input tile pitch: 128 + 2 Cm columns for radii up to 14 and up to 24.
 static int tile_pitch(int max_radius) { return max_radius <= 14 ? 160 : 184; }
 
-static size_t detect_smem(int max_radius, int in_size) {
+static size_t detect_smem(int max_radius, int in_size, int n_images) {
   const int ic = tile_pitch(max_radius);
   const size_t rows = (size_t)(kRows + 2 * max_radius);
   const size_t raw = (rows * ic * in_size + 15) / 16 * 16;
   return raw + sizeof(float) * (rows * ic + (size_t)kRows * ic + (size_t)kRows * kGC +
-                                (size_t)kScales * kRows * kLC);
+                                (size_t)kScales * kRows * kLC) +
+         sizeof(int) * (size_t)(n_images + 1);
 }
 
-size_t detect_smem_bytes(int max_radius) { return detect_smem(max_radius, 4); }
+size_t detect_smem_bytes(int max_radius) { return detect_smem(max_radius, 4, 0); }
 
 cudaError_t launch_detect(const DetectArgs& a, int n_tiles, int max_radius, int storage, int n_sms,
                           cudaStream_t s) {
@@ -836,7 +840,7 @@ cudaError_t launch_detect(const DetectArgs& a, int n_tiles, int max_radius, int 
   cudaError_t e;
 #define CDVS_LAUNCH(IN, ST, IC)                                                                                   \
   do {                                                                                                            \
-    const size_t smem = detect_smem(max_radius, sizeof(IN));                                                     \
+    const size_t smem = detect_smem(max_radius, sizeof(IN), a.n_images);                                                     \
     e = cudaFuncSetAttribute(detect_kernel<IN, ST, IC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
     if (e != cudaSuccess) return e;                                                                               \
     detect_kernel<IN, ST, IC><<<grid, kDetThreads, smem, s>>>(a, max_radius, n_tiles);                           \
