@@ -49,7 +49,7 @@ EXPORTED = ["cdvs_params_default", "cdvs_create", "cdvs_destroy", "cdvs_last_err
             "cdvs_candidates", "cdvs_dedupe_select", "cdvs_describe", "cdvs_scale_space",
             "cdvs_rank_host", "cdvs_transform_ternary", "cdvs_profile", "cdvs_profile_read",
             "cdvs_dedupe_select_noalloc"]
-STAGES = ["detect", "select", "describe", "offsets", "pack"]
+STAGES = ["detect", "select", "describe", "offsets", "pack", "detect_octave0"]
 
 
 class CdvsError(RuntimeError):

@@ -349,7 +349,9 @@ cdvs_status run_detect(cdvs_ctx* c, int n, const cdvs_params& p, int max_oct, in
       maxr = std::max(maxr, a.radius[k]);
     }
     const int n_tiles = c->h_prefix[(size_t)o * (n + 1) + n];
+    cudaEvent_t ev0 = o == 0 ? prof_begin(c, s) : nullptr;
     if ((e = launch_detect(a, n_tiles, maxr, p.storage, c->n_sms, s)) != cudaSuccess) return cuda_fail(c, e, "detect launch");
+    if (o == 0) prof_end(c, 5, 1, ev0, s);
   }
   return CDVS_OK;
 }
@@ -883,7 +885,7 @@ int32_t cdvs_profile_read(cdvs_ctx* c, double* ms, int32_t* launches, int32_t ma
     }
     c->recs.clear();
   }
-  return 5;
+  return CDVS_N_STAGES;
 }
 
 }  // extern "C"
