@@ -99,98 +99,105 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsign
 }
 
 // ------------------------------------------------ tile geometry
-struct Tile {
+// Everything the CTA needs to know about one tile, computed ahead of time by a
+// single thread and kept in shared memory.
+struct TileInfo {
+  long long level_off;  // element offset of level (o, 0) of the tile's image
+  long long dec_off;    // level (o + 1, 0), or -1 when o is the image's last octave
+  const void* base;     // first input row (u8 image or level (o, 0))
   int img, tx0, ty0;
-  int W, H, lpitch;
-  const ImgPlan* P;
-  long long level_off;
+  int W, H, lpitch;     // octave size and stored row pitch (elements)
+  int dec_pitch;        // row pitch of level (o + 1, 0)
+  int pitch;            // input row pitch (elements)
+  int cs, ce;           // copied input columns [cs, ce) (image x)
+  int bulk;             // rows can be fetched by bulk copies
+  int valid;            // 0 past the launch's last tile
 };
 
-// prefix: the launch's tile_prefix (n_images + 1 entries) in shared memory
-__device__ __forceinline__ Tile locate(const DetectArgs& a, const int* prefix, int b) {
-  // largest i with prefix[i] <= b
+// Tile b of the launch (prefix: the launch's tile_prefix, n_images + 1 entries,
+// in shared memory): its image is the largest i with prefix[i] <= b.  The
+// rows can be bulk-copied when source rows, lengths and destination rows in
+// raw all start on 16-byte boundaries; otherwise they are loaded element by
+// element.
+template <typename InT>
+__device__ __noinline__ void tile_info(const DetectArgs& a, const int* prefix, int b, int n_tiles, int ic, TileInfo* out) {
+  TileInfo t;
+  t.valid = b < n_tiles;
+  if (!t.valid) {
+    t.bulk = 0;
+    *out = t;
+    return;
+  }
   int lo = 0, hi = a.n_images;
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
     if (prefix[mid] <= b) lo = mid;
     else hi = mid;
   }
-  Tile t;
-  t.img = lo;
-  t.P = a.plans + lo;
-  const OctPlan& op = t.P->oct[a.octave];
+  const ImgPlan* P = a.plans + lo;
+  const OctPlan& op = P->oct[a.octave];
   const int k = b - prefix[lo];
+  t.img = lo;
   t.tx0 = (k % op.tiles_x) * kTX;
   t.ty0 = (k / op.tiles_x) * kTY;
   t.W = op.W;
   t.H = op.H;
   t.lpitch = op.lpitch;
   t.level_off = op.level_off;
-  return t;
-}
-
-// Where the tile's input comes from: element pointer, pitch (elements), the
-// copied columns, and whether its rows can be fetched by bulk copies (16-byte
-// aligned starts and lengths) -- otherwise it is loaded element by element.
-template <typename InT>
-struct InputRef {
-  const InT* base;
-  int pitch;   // elements
-  int cs, ce;  // copied columns [cs, ce) (image x)
-  bool bulk;
-};
-
-template <typename InT>
-__device__ __forceinline__ InputRef<InT> input_ref(const DetectArgs& a, const Tile& t, int ic) {
-  InputRef<InT> r;
-  if constexpr (std::is_same<InT, uint8_t>::value) {
-    r.base = reinterpret_cast<const InT*>(t.P->src);
-    r.pitch = t.P->pitch;
+  if (a.octave + 1 < P->n_oct) {
+    t.dec_off = P->oct[a.octave + 1].level_off;
+    t.dec_pitch = P->oct[a.octave + 1].lpitch;
   } else {
-    r.base = reinterpret_cast<const InT*>(a.levels) + t.level_off;  // level (o, 0) is the base
-    r.pitch = t.lpitch;
+    t.dec_off = -1;
+    t.dec_pitch = 0;
+  }
+  if constexpr (std::is_same<InT, uint8_t>::value) {
+    t.base = P->src;
+    t.pitch = P->pitch;
+  } else {
+    t.base = reinterpret_cast<const InT*>(a.levels) + t.level_off;
+    t.pitch = t.lpitch;
   }
   const int cm = (ic - kTX) / 2;
   const int x0 = t.tx0 - cm;
-  r.cs = max(x0, 0);
-  r.ce = min(x0 + ic, t.W);
+  t.cs = max(x0, 0);
+  t.ce = min(x0 + ic, t.W);
   constexpr int es = sizeof(InT);
-  // 16-byte aligned source rows, lengths, and destination rows in raw
-  r.bulk = ((reinterpret_cast<uintptr_t>(r.base) & 15) == 0) && (((size_t)r.pitch * es) % 16 == 0) &&
-           ((r.cs * es) % 16 == 0) && (((r.ce - r.cs) * es) % 16 == 0) && r.ce > r.cs &&
-           ((ic * es) % 16 == 0) && (((r.cs - x0) * es) % 16 == 0);
-  return r;
+  t.bulk = ((reinterpret_cast<uintptr_t>(t.base) & 15) == 0) && (((size_t)t.pitch * es) % 16 == 0) &&
+           ((t.cs * es) % 16 == 0) && (((t.ce - t.cs) * es) % 16 == 0) && t.ce > t.cs &&
+           ((ic * es) % 16 == 0) && (((t.cs - x0) * es) % 16 == 0);
+  *out = t;
 }
 
 // The 32 lanes of warp 0 issue the bulk copies of every input row of tile t
 // into raw (column c of a raw row is image x = tx0 - cm + c; rows clamp to the
 // image); lane 0 first announces the byte count on the mbarrier.
 template <typename InT>
-__device__ __forceinline__ void issue_tile_copy(const Tile& t, const InputRef<InT>& r, int ic, int rm, InT* raw,
+__device__ __forceinline__ void issue_tile_copy(const TileInfo& t, int ic, int rm, InT* raw,
                                                 unsigned long long* bar) {
   const int lane = threadIdx.x & 31;
   const int cm = (ic - kTX) / 2;
   const int IR = kRows + 2 * rm;
   const int y0 = t.ty0 - kHalo - rm;
   const int x0 = t.tx0 - cm;
-  const unsigned row_bytes = (unsigned)((r.ce - r.cs) * sizeof(InT));
+  const unsigned row_bytes = (unsigned)((t.ce - t.cs) * sizeof(InT));
+  const InT* base = static_cast<const InT*>(t.base);
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   if (lane == 0) mbar_expect_tx(bar, row_bytes * IR);
   __syncwarp();
   for (int i = lane; i < IR; i += 32) {
     const int y = min(max(y0 + i, 0), t.H - 1);
-    bulk_copy_g2s(raw + (size_t)i * ic + (r.cs - x0), r.base + (size_t)y * r.pitch + r.cs, row_bytes, bar);
+    bulk_copy_g2s(raw + (size_t)i * ic + (t.cs - x0), base + (size_t)y * t.pitch + t.cs, row_bytes, bar);
   }
 }
 
 // raw (copied columns only) -> in (FP32), replicating the edge columns.
 template <typename InT>
-__device__ __forceinline__ void convert_raw(const InT* raw, const Tile& t, const InputRef<InT>& r, int ic, int rm,
-                                            float* in) {
+__device__ __forceinline__ void convert_raw(const InT* raw, const TileInfo& t, int ic, int rm, float* in) {
   const int cm = (ic - kTX) / 2;
   const int IR = kRows + 2 * rm;
   const int x0 = t.tx0 - cm;
-  const int clo = r.cs - x0, chi = r.ce - 1 - x0;  // first / last copied column
+  const int clo = t.cs - x0, chi = t.ce - 1 - x0;  // first / last copied column
   const int n4 = ic / 4;
   for (int i = threadIdx.x; i < IR * n4; i += kDetThreads) {
     const int row = i / n4;
@@ -217,14 +224,14 @@ __device__ __forceinline__ void convert_raw(const InT* raw, const Tile& t, const
 // Element-by-element input load with clamp-to-edge (tiles whose rows cannot
 // be bulk-copied).
 template <typename InT>
-__device__ __forceinline__ void load_tile_direct(const Tile& t, const InputRef<InT>& r, int ic, int rm, float* in) {
+__device__ __forceinline__ void load_tile_direct(const TileInfo& t, int ic, int rm, float* in) {
   const int cm = (ic - kTX) / 2;
   const int IR = kRows + 2 * rm;
   const int y0 = t.ty0 - kHalo - rm, x0 = t.tx0 - cm;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int row = warp; row < IR; row += kWarps) {
     const int y = min(max(y0 + row, 0), t.H - 1);
-    const InT* src = r.base + (size_t)y * r.pitch;
+    const InT* src = static_cast<const InT*>(t.base) + (size_t)y * t.pitch;
     for (int c = lane; c < ic; c += 32) in[row * ic + c] = to_f(src[min(max(x0 + c, 0), t.W - 1)]);
   }
 }
@@ -610,12 +617,15 @@ struct Pending {
   float t;
 };
 
+// Tile j of a CTA is described by info[j % 3]: while tile j is processed,
+// info[(j + 1) % 3] drives the copy of its successor and the last warp fills
+// info[(j + 2) % 3] during phase 2, so no thread waits on the plan's global
+// loads.
 struct TileShared {
   unsigned long long bar;  // completion of the bulk copies into raw
   int n_pending;
-  int out_base;  // first queue slot of this round's survivors
-  int warp_count[kWarps];
   int timeout;
+  TileInfo info[3];
 };
 
 template <typename InT, typename StoreT, int ic>
@@ -645,40 +655,42 @@ __global__ void __launch_bounds__(kDetThreads, 1)
 
   int b = blockIdx.x;
   if (b >= n_tiles) return;
-  Tile cur = locate(a, prefix, b);
-  InputRef<InT> cref = input_ref<InT>(a, cur, ic);
-  if (warp == 0 && cref.bulk) issue_tile_copy<InT>(cur, cref, ic, rm, raw, &sh.bar);
-  bool pending_copy = cref.bulk;
+  if (threadIdx.x == 0) {
+    tile_info<InT>(a, prefix, b, n_tiles, ic, &sh.info[0]);
+    tile_info<InT>(a, prefix, b + gridDim.x, n_tiles, ic, &sh.info[1]);
+  }
+  __syncthreads();
+  if (warp == 0 && sh.info[0].bulk) issue_tile_copy<InT>(sh.info[0], ic, rm, raw, &sh.bar);
+  bool pending_copy = sh.info[0].bulk;
 
-  for (; b < n_tiles; b += gridDim.x) {
+  for (int slot = 0; b < n_tiles; b += gridDim.x, slot = slot == 2 ? 0 : slot + 1) {
+    const TileInfo& cur = sh.info[slot];
+    const TileInfo& nxt = sh.info[slot == 2 ? 0 : slot + 1];
+    TileInfo* after = &sh.info[slot == 0 ? 2 : slot - 1];
     // ---- this tile's input into `in`
-    if (cref.bulk) {
+    if (cur.bulk) {
       if (mbar_wait(&sh.bar, parity)) {
         parity ^= 1u;
         pending_copy = false;
       } else {
         sh.timeout = 1;
       }
-      convert_raw<InT>(raw, cur, cref, ic, rm, in);
+      convert_raw<InT>(raw, cur, ic, rm, in);
     } else {
-      load_tile_direct<InT>(cur, cref, ic, rm, in);
+      load_tile_direct<InT>(cur, ic, rm, in);
     }
     if (threadIdx.x == 0) sh.n_pending = 0;
     __syncthreads();
     if (sh.timeout) break;  // uniform: a copy never completed
     // ---- next tile's input on its way while this one is processed
-    const int nb = b + gridDim.x;
-    Tile nxt = cur;
-    InputRef<InT> nref = cref;
-    nref.bulk = false;
-    if (nb < n_tiles) {
-      nxt = locate(a, prefix, nb);
-      nref = input_ref<InT>(a, nxt, ic);
-      if (warp == 0 && nref.bulk) issue_tile_copy<InT>(nxt, nref, ic, rm, raw, &sh.bar);
-      pending_copy = nref.bulk;
+    if (nxt.bulk) {
+      if (warp == 0) issue_tile_copy<InT>(nxt, ic, rm, raw, &sh.bar);
+      pending_copy = true;
     }
 
-    const int W = cur.W, H = cur.H, lpitch = cur.lpitch, tx0 = cur.tx0, ty0 = cur.ty0;
+    const int W = cur.W, H = cur.H, lpitch = cur.lpitch, tx0 = cur.tx0, ty0 = cur.ty0, img = cur.img;
+    const long long dec_off = cur.dec_off;
+    const int dec_pitch = cur.dec_pitch;
     StoreT* lev = reinterpret_cast<StoreT*>(a.levels) + cur.level_off;
     const size_t lstride = (size_t)lpitch * H;
 
@@ -691,11 +703,8 @@ __global__ void __launch_bounds__(kDetThreads, 1)
     for (int k = 0; k < kScales; ++k) {
       replicate_borders(gs, W, H, tx0, ty0);
       if (k > 0 || a.write_level0) store_level<StoreT>(gs, lev + k * lstride, lpitch, W, H, tx0, ty0);
-      if (k == kScales - 1 && o + 1 < cur.P->n_oct) {
-        const OctPlan& op1 = cur.P->oct[o + 1];
-        store_decimated<StoreT>(gs, reinterpret_cast<StoreT*>(a.levels) + op1.level_off, op1.lpitch, W, H, tx0,
-                                ty0);
-      }
+      if (k == kScales - 1 && dec_off >= 0)
+        store_decimated<StoreT>(gs, reinterpret_cast<StoreT*>(a.levels) + dec_off, dec_pitch, W, H, tx0, ty0);
       laplacian(gs, a.s2[k], Ls + (size_t)k * kRP * kLC * 2);
       if (k + 1 < kScales) vpass_dispatch<ic>(a.radius[k + 1], a.taps[k + 1], in, rm, tmp);
       __syncthreads();
@@ -762,10 +771,13 @@ __global__ void __launch_bounds__(kDetThreads, 1)
     __syncthreads();
 
     // ---- phase 2: neighbour test and refinement of the survivors, densely;
-    // one queue reservation per round for the whole CTA
+    // one queue reservation per warp and round.  The queue order does not
+    // matter: the selection orders candidates by a total order of their own.
+    // Meanwhile the last warp's lane 0 looks up the tile after next.
     const int np = sh.n_pending;
-    for (int r0 = 0; r0 < np; r0 += kDetThreads) {
-      const int i = r0 + threadIdx.x;
+    if (warp == kWarps - 1 && lane == 0) tile_info<InT>(a, prefix, b + 2 * gridDim.x, n_tiles, ic, after);
+    for (int i0 = warp * 32; i0 < np; i0 += kDetThreads) {
+      const int i = i0 + lane;
       Found f;
       bool found = false;
       if (i < np) {
@@ -774,20 +786,12 @@ __global__ void __launch_bounds__(kDetThreads, 1)
         found = refine_pixel(a, Ls, ly, lx, (e.code & 1) ? 1 : -1, e.t, tx0 + lx, ty0 + ly, f);
       }
       const unsigned msk = __ballot_sync(0xffffffffu, found);
-      if (lane == 0) sh.warp_count[warp] = __popc(msk);
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        int tot = 0;
-        for (int w = 0; w < kWarps; ++w) {
-          const int c = sh.warp_count[w];
-          sh.warp_count[w] = tot;
-          tot += c;
-        }
-        sh.out_base = tot > 0 ? atomicAdd(a.cand_count + cur.img, tot) : 0;
-      }
-      __syncthreads();
+      if (msk == 0) continue;
+      int base = 0;
+      if (lane == 0) base = atomicAdd(a.cand_count + img, __popc(msk));
+      base = __shfl_sync(0xffffffffu, base, 0);
       if (found) {
-        const int pos = sh.out_base + sh.warp_count[warp] + __popc(msk & ((1u << lane) - 1u));
+        const int pos = base + __popc(msk & ((1u << lane) - 1u));
         if (pos < a.cand_cap) {
           Cand c;
           c.xo = f.xo;
@@ -799,16 +803,15 @@ __global__ void __launch_bounds__(kDetThreads, 1)
           c.octave = (short)o;
           c.type = (short)f.type;
           c.spare = 0;
-          a.cands[(size_t)cur.img * a.cand_cap + pos] = c;
+          a.cands[(size_t)img * a.cand_cap + pos] = c;
         } else {
           atomicOr(a.status, kStatusCandOverflow);
         }
       }
-      __syncthreads();  // warp_count / out_base are reused by the next round
     }
-    cur = nxt;
-    cref = nref;
-    __syncthreads();  // the pending list lives in `in`, rewritten by the next tile
+    // the pending list lives in `in`, rewritten by the next tile; the tile
+    // after next is described in `after`
+    __syncthreads();
   }
   if (sh.timeout && threadIdx.x == 0) atomicOr(a.status, kStatusTimeout);
   // a copy still in flight must land before the CTA's shared memory goes
