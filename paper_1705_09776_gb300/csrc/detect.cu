@@ -461,7 +461,6 @@ struct Found {
   int type;
 };
 
-__device__ __forceinline__ float2 abs2(float2 v) { return f2(fabsf(v.x), fabsf(v.y)); }
 __device__ __forceinline__ float rcp_approx(float x) {
   float y;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -473,22 +472,30 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   return y;
 }
 
+// The admissible one of a pixel's two stationary points t0, t1 (values v,
+// second derivatives s): inside [t_lo, t_hi], p'' != 0 and |p| >= T; when both
+// are, the larger |p| wins, ties going to the smaller t.
+__device__ __forceinline__ void pick_root(const DetectArgs& a, bool live, float t0, float t1, float v0, float v1,
+                                          float s0, float s1, int& bt, float& tb) {
+  const bool ok0 = live && t0 >= a.t_lo && t0 <= a.t_hi && s0 != 0.0f && fabsf(v0) >= a.T;
+  const bool ok1 = live && t1 >= a.t_lo && t1 <= a.t_hi && s1 != 0.0f && fabsf(v1) >= a.T;
+  const bool take1 = ok1 && (!ok0 || fabsf(v1) > fabsf(v0) || (fabsf(v1) == fabsf(v0) && t1 < t0));
+  const float s = take1 ? s1 : s0;
+  bt = (ok0 || ok1) ? (s < 0.0f ? 1 : -1) : 0;
+  tb = (ok0 || ok1) ? (take1 ? t1 : t0) : 0.0f;
+}
+
 // S4 on a pair of pixels (phase 1): for each pixel, the admissible extremum
 // of the cubic p(t) = a0 + a1 t + a2 t^2 + a3 t^3 with |p| >= T.  The roots of
-// p'(t) = 3 a3 t^2 + 2 a2 t + a1 come from the cancellation-free form
-// q = -(B + sign(B) sqrt(D)) / 2, t = q / A and C / q; when both are admissible
-// the larger |p| wins (ties: the smaller t).  bt = +1 maximum, -1 minimum, 0.
+// p'(t) = A t^2 + B t + C (A = 3 a3, B = 2 a2, C = a1) come from the
+// cancellation-free form q = -(B + sign(B) sqrt(D)) / 2, t = q / A and C / q;
+// they exist when D = B^2 - 4AC > 0.  With A = 0 the same formulas give q = -B
+// and t = C / q = -C / B, the root of the linear derivative, while q / A is
+// infinite and never admissible.  No branches: every pixel pair takes the same
+// instruction stream, so the caller's unrolled pairs interleave.
+// bt = +1 maximum, -1 minimum, 0 none.
 __device__ __forceinline__ void cubic_extremum2(const DetectArgs& a, const float2 (&al)[4], bool live0,
                                                 bool live1, int (&bt)[2], float (&tb)[2]) {
-  bt[0] = bt[1] = 0;
-  tb[0] = tb[1] = 0.0f;
-  // no t in [t_lo, t_hi] can reach |p| >= T when this bound is below T
-  const float mm = fmaxf(-a.t_lo, a.t_hi);
-  const float2 m2 = f2(mm, mm);
-  const float2 bound = add2(abs2(al[0]), mul2(m2, add2(abs2(al[1]), mul2(m2, fma2(m2, abs2(al[3]), abs2(al[2]))))));
-  const float Tb = a.T * 0.99999f;
-  const bool go0 = live0 && bound.x >= Tb, go1 = live1 && bound.y >= Tb;
-  if (!(go0 || go1)) return;
   const float2 A = mul2(f2(3.0f, 3.0f), al[3]), Bq = mul2(f2(2.0f, 2.0f), al[2]), C = al[1];
   const float2 D = fma2(mul2(f2(-4.0f, -4.0f), A), C, mul2(Bq, Bq));
   const float2 sq = f2(sqrt_approx(fmaxf(D.x, 0.0f)), sqrt_approx(fmaxf(D.y, 0.0f)));
@@ -496,54 +503,12 @@ __device__ __forceinline__ void cubic_extremum2(const DetectArgs& a, const float
   const float2 r0 = mul2(q, f2(rcp_approx(A.x), rcp_approx(A.y)));
   const float2 r1 = mul2(C, f2(rcp_approx(q.x), rcp_approx(q.y)));
   const float2 six_a3 = mul2(f2(6.0f, 6.0f), al[3]);
-  const float2 two_a2 = mul2(f2(2.0f, 2.0f), al[2]);
   // p'' and p at both roots, both pixels
-  const float2 pdd0 = fma2(six_a3, r0, two_a2), pdd1 = fma2(six_a3, r1, two_a2);
+  const float2 pdd0 = fma2(six_a3, r0, Bq), pdd1 = fma2(six_a3, r1, Bq);
   const float2 v0 = fma2(fma2(fma2(al[3], r0, al[2]), r0, al[1]), r0, al[0]);
   const float2 v1 = fma2(fma2(fma2(al[3], r1, al[2]), r1, al[1]), r1, al[0]);
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    if (!(h ? go1 : go0)) continue;
-    const float Ah = h ? A.y : A.x, Bh = h ? Bq.y : Bq.x, Ch = h ? C.y : C.x;
-    const float Dh = h ? D.y : D.x;
-    float t0, t1, p0, p1, s0, s1;
-    int nr;
-    if (Ah == 0.0f) {  // quadratic p: the single root of the linear derivative
-      if (Bh == 0.0f) continue;
-      t0 = -Ch / Bh;
-      s0 = h ? two_a2.y : two_a2.x;
-      p0 = h ? fmaf(fmaf(fmaf(al[3].y, t0, al[2].y), t0, al[1].y), t0, al[0].y)
-             : fmaf(fmaf(fmaf(al[3].x, t0, al[2].x), t0, al[1].x), t0, al[0].x);
-      t1 = p1 = s1 = 0.0f;
-      nr = 1;
-    } else {
-      if (!(Dh > 0.0f)) continue;
-      t0 = h ? r0.y : r0.x;
-      p0 = h ? v0.y : v0.x;
-      s0 = h ? pdd0.y : pdd0.x;
-      t1 = h ? r1.y : r1.x;
-      p1 = h ? v1.y : v1.x;
-      s1 = h ? pdd1.y : pdd1.x;
-      nr = 2;  // D > 0 makes q nonzero
-    }
-    int best = 0;
-    float bt_t = 0.0f, bv = 0.0f;
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      if (r >= nr) break;
-      const float tt = r ? t1 : t0, v = r ? p1 : p0, pdd = r ? s1 : s0;
-      if (!(tt >= a.t_lo && tt <= a.t_hi)) continue;
-      if (pdd == 0.0f) continue;
-      if (!(fabsf(v) >= a.T)) continue;
-      if (best == 0 || fabsf(v) > fabsf(bv) || (fabsf(v) == fabsf(bv) && tt < bt_t)) {
-        best = pdd < 0.0f ? 1 : -1;
-        bt_t = tt;
-        bv = v;
-      }
-    }
-    bt[h] = best;
-    tb[h] = bt_t;
-  }
+  pick_root(a, live0 && D.x > 0.0f, r0.x, r1.x, v0.x, v1.x, pdd0.x, pdd1.x, bt[0], tb[0]);
+  pick_root(a, live1 && D.y > 0.0f, r0.y, r1.y, v0.y, v1.y, pdd0.y, pdd1.y, bt[1], tb[1]);
 }
 
 // 8-neighbour test at the centre's t* and refinement (Alg. 1 stage B) for
