@@ -11,9 +11,9 @@
 // G_{o,K-1} to G_{o+1,0}).
 //
 // While a tile is processed, the rows of the next tile's input are already
-// on their way into shared memory through bulk asynchronous copies
-// (cp.async.bulk, completion on an mbarrier), so global-memory latency
-// overlaps the arithmetic.
+// on their way into shared memory through asynchronous 16-byte copies
+// (cp.async), issued by all threads at once, so global-memory latency overlaps
+// the arithmetic.
 //
 // The filters run on packed FP32 pairs (fma.rn.f32x2: two independent
 // round-to-nearest FMAs per instruction): the y pass on pairs of adjacent
@@ -46,7 +46,6 @@ constexpr int kSV = 6;                   // rows per thread in the y pass
 constexpr int kSH = 6;                   // columns per thread in the x pass
 constexpr int kLG = 3;                   // row-pair groups in the Laplacian pass
 constexpr int kWarps = kDetThreads / 32;
-constexpr long long kWaitLimit = 1ll << 22;  // polls of an mbarrier before giving up
 static_assert(kRows % kSV == 0 && kSV % 2 == 0, "y-pass strips must tile the row pairs");
 static_assert(kGC % kSH == 0 && kSH % 2 == 0, "x-pass strips must tile the columns");
 static_assert(kRP % kLG == 0, "Laplacian groups must tile the row pairs");
@@ -61,42 +60,17 @@ __device__ __forceinline__ float to_f(uint8_t v) { return (float)v - 128.0f; }
 __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
 
-// ------------------------------------------------ bulk copies and mbarrier
+// ------------------------------------------------ asynchronous copies
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+// 16 bytes global -> shared, cached in L2 only; both addresses 16-byte aligned
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait for the given phase parity; false when the limit ran out
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-  for (long long i = 0; i < kWaitLimit; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes,
-                                              unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// this thread's copies have landed (a wait on its own loads, like any load)
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // ------------------------------------------------ tile geometry
 // Everything the CTA needs to know about one tile, computed ahead of time by a
@@ -110,15 +84,15 @@ struct TileInfo {
   int dec_pitch;        // row pitch of level (o + 1, 0)
   int pitch;            // input row pitch (elements)
   int cs, ce;           // copied input columns [cs, ce) (image x)
-  int bulk;             // rows can be fetched by bulk copies
+  int bulk;             // rows can be fetched by 16-byte asynchronous copies
   int valid;            // 0 past the launch's last tile
 };
 
 // Tile b of the launch (prefix: the launch's tile_prefix, n_images + 1 entries,
 // in shared memory): its image is the largest i with prefix[i] <= b.  The
-// rows can be bulk-copied when source rows, lengths and destination rows in
-// raw all start on 16-byte boundaries; otherwise they are loaded element by
-// element.
+// rows can be copied in 16-byte pieces when source rows, lengths and
+// destination rows in raw all start on 16-byte boundaries; otherwise they are
+// loaded element by element.
 template <typename InT>
 __device__ __noinline__ void tile_info(const DetectArgs& a, const int* prefix, int b, int n_tiles, int ic, TileInfo* out) {
   TileInfo t;
@@ -169,26 +143,25 @@ __device__ __noinline__ void tile_info(const DetectArgs& a, const int* prefix, i
   *out = t;
 }
 
-// The 32 lanes of warp 0 issue the bulk copies of every input row of tile t
-// into raw (column c of a raw row is image x = tx0 - cm + c; rows clamp to the
-// image); lane 0 first announces the byte count on the mbarrier.
+// All threads of the CTA issue the 16-byte copies of every input row of tile
+// t into raw (column c of a raw row is image x = tx0 - cm + c; rows clamp to
+// the image) and commit them as one group.
 template <typename InT>
-__device__ __forceinline__ void issue_tile_copy(const TileInfo& t, int ic, int rm, InT* raw,
-                                                unsigned long long* bar) {
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void issue_tile_copy(const TileInfo& t, int ic, int rm, InT* raw) {
+  constexpr int per = 16 / sizeof(InT);  // elements per piece
   const int cm = (ic - kTX) / 2;
   const int IR = kRows + 2 * rm;
   const int y0 = t.ty0 - kHalo - rm;
   const int x0 = t.tx0 - cm;
-  const unsigned row_bytes = (unsigned)((t.ce - t.cs) * sizeof(InT));
-  const InT* base = static_cast<const InT*>(t.base);
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  if (lane == 0) mbar_expect_tx(bar, row_bytes * IR);
-  __syncwarp();
-  for (int i = lane; i < IR; i += 32) {
-    const int y = min(max(y0 + i, 0), t.H - 1);
-    bulk_copy_g2s(raw + (size_t)i * ic + (t.cs - x0), base + (size_t)y * t.pitch + t.cs, row_bytes, bar);
+  const int nc = (t.ce - t.cs) / per;  // pieces per row
+  const InT* src = static_cast<const InT*>(t.base) + t.cs;
+  InT* dst = raw + (t.cs - x0);
+  for (int i = threadIdx.x; i < IR * nc; i += kDetThreads) {
+    const int row = i / nc, c = i - row * nc;
+    const int y = min(max(y0 + row, 0), t.H - 1);
+    cp_async16(dst + (size_t)row * ic + c * per, src + (size_t)y * t.pitch + c * per);
   }
+  cp_async_commit();
 }
 
 // raw (copied columns only) -> in (FP32), replicating the edge columns.
@@ -222,7 +195,7 @@ __device__ __forceinline__ void convert_raw(const InT* raw, const TileInfo& t, i
 }
 
 // Element-by-element input load with clamp-to-edge (tiles whose rows cannot
-// be bulk-copied).
+// be copied in 16-byte pieces).
 template <typename InT>
 __device__ __forceinline__ void load_tile_direct(const TileInfo& t, int ic, int rm, float* in) {
   const int cm = (ic - kTX) / 2;
@@ -587,9 +560,7 @@ struct Pending {
 // info[(j + 2) % 3] during phase 2, so no thread waits on the plan's global
 // loads.
 struct TileShared {
-  unsigned long long bar;  // completion of the bulk copies into raw
   int n_pending;
-  int timeout;
   TileInfo info[3];
 };
 
@@ -610,13 +581,7 @@ __global__ void __launch_bounds__(kDetThreads, 1)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
   for (int i = threadIdx.x; i <= a.n_images; i += kDetThreads) prefix[i] = a.tile_prefix[i];
-  if (threadIdx.x == 0) {
-    mbar_init(&sh.bar, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    sh.timeout = 0;
-  }
   __syncthreads();
-  unsigned parity = 0;
 
   int b = blockIdx.x;
   if (b >= n_tiles) return;
@@ -625,33 +590,25 @@ __global__ void __launch_bounds__(kDetThreads, 1)
     tile_info<InT>(a, prefix, b + gridDim.x, n_tiles, ic, &sh.info[1]);
   }
   __syncthreads();
-  if (warp == 0 && sh.info[0].bulk) issue_tile_copy<InT>(sh.info[0], ic, rm, raw, &sh.bar);
-  bool pending_copy = sh.info[0].bulk;
+  if (sh.info[0].bulk) issue_tile_copy<InT>(sh.info[0], ic, rm, raw);
 
   for (int slot = 0; b < n_tiles; b += gridDim.x, slot = slot == 2 ? 0 : slot + 1) {
     const TileInfo& cur = sh.info[slot];
     const TileInfo& nxt = sh.info[slot == 2 ? 0 : slot + 1];
     TileInfo* after = &sh.info[slot == 0 ? 2 : slot - 1];
     // ---- this tile's input into `in`
-    if (cur.bulk) {
-      if (mbar_wait(&sh.bar, parity)) {
-        parity ^= 1u;
-        pending_copy = false;
-      } else {
-        sh.timeout = 1;
-      }
+    if (cur.bulk) {  // uniform
+      cp_async_wait_all();
+      __syncthreads();
       convert_raw<InT>(raw, cur, ic, rm, in);
     } else {
       load_tile_direct<InT>(cur, ic, rm, in);
     }
     if (threadIdx.x == 0) sh.n_pending = 0;
     __syncthreads();
-    if (sh.timeout) break;  // uniform: a copy never completed
-    // ---- next tile's input on its way while this one is processed
-    if (nxt.bulk) {
-      if (warp == 0) issue_tile_copy<InT>(nxt, ic, rm, raw, &sh.bar);
-      pending_copy = true;
-    }
+    // ---- next tile's input on its way while this one is processed (raw is
+    // free: every thread is past convert_raw)
+    if (nxt.bulk) issue_tile_copy<InT>(nxt, ic, rm, raw);
 
     const int W = cur.W, H = cur.H, lpitch = cur.lpitch, tx0 = cur.tx0, ty0 = cur.ty0, img = cur.img;
     const long long dec_off = cur.dec_off;
@@ -778,10 +735,7 @@ __global__ void __launch_bounds__(kDetThreads, 1)
     // after next is described in `after`
     __syncthreads();
   }
-  if (sh.timeout && threadIdx.x == 0) atomicOr(a.status, kStatusTimeout);
-  // a copy still in flight must land before the CTA's shared memory goes
-  // (bounded: after a timeout the kernel returns regardless)
-  if (pending_copy) mbar_wait(&sh.bar, parity);
+  cp_async_wait_all();  // nothing may still be landing in shared memory at exit
 }
 
 }  // namespace
