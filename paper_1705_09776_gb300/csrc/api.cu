@@ -586,7 +586,7 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
     d.kp_count = static_cast<int*>(c->out_count.p);
   }
   ev = prof_begin(c, s);
-  if ((e = launch_describe(d, p.storage, s)) != cudaSuccess) return cuda_fail(c, e, "describe launch");
+  if ((e = launch_describe(d, p.storage, c->n_sms, s)) != cudaSuccess) return cuda_fail(c, e, "describe launch");
   prof_end(c, 2, 1, ev, s);
   ev = prof_begin(c, s);
   if ((e = launch_pack(d, s)) != cudaSuccess) return cuda_fail(c, e, "packing launch");

@@ -130,7 +130,7 @@ cudaError_t launch_detect(const DetectArgs& a, int n_tiles, int max_radius, int 
                           cudaStream_t s);
 cudaError_t launch_select(const SelectArgs& a, int n_images, cudaStream_t s);
 size_t describe_smem_bytes(int patch_side);
-cudaError_t launch_describe(const DescribeArgs& a, int storage, cudaStream_t s);
+cudaError_t launch_describe(const DescribeArgs& a, int storage, int n_sms, cudaStream_t s);
 cudaError_t launch_pack(const DescribeArgs& a, cudaStream_t s);
 cudaError_t launch_copy(const DescribeArgs& a, int n_sms, cudaStream_t s);
 cudaError_t launch_levels_to_f32(const ImgPlan* plans, int img, const void* levels, int storage,

@@ -2,19 +2,23 @@
 // 128-D descriptors (stage B), then the packing of the (point, orientation)
 // records of the whole batch.
 //
-// One warp per selected point: the warp stages the point's patch of its
-// Gaussian level in shared memory (coalesced row loads), builds the 36-bin
+// One warp per selected point, persistent warps: the warp stages the point's
+// patch of its Gaussian level in shared memory (4-byte asynchronous copies,
+// all in flight at once, the image border replicated), builds the 36-bin
 // orientation histogram from it, finds the orientations, and for each one
-// builds the 4x4x8 descriptor histogram.  The lanes stride over the pixels of
-// the sampling disc and add their votes to a per-warp histogram with 32-bit
-// integer atomics on a 2^-13 fixed-point scale: integer addition is
-// associative, so the sums do not depend on the order in which lanes land.
+// builds the 4x4x8 descriptor histogram.  Each lane walks a contiguous run of
+// the sampling disc's pixels (rows clipped to the disc, so no lane idles on
+// the box corners, and the 32 runs are spread over the disc, so concurrent
+// votes rarely hit the same bin).  Votes go to a per-warp histogram with
+// 32-bit integer atomics on a power-of-two fixed-point scale: integer addition
+// is associative, so the sums do not depend on the order in which lanes land.
+#include <algorithm>
+
 #include "cdvs_internal.cuh"
 
 namespace cdvs {
 namespace {
 
-constexpr float kTwoPi = 6.283185307179586f;
 constexpr int kScanThreads = 1024;
 
 __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
@@ -48,22 +52,21 @@ __device__ __forceinline__ LevelView<StoreT> level_of(const DescribeArgs& a, int
   return v;
 }
 
-__device__ __forceinline__ float warp_max(float v) {
-  for (int d = 16; d > 0; d >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, d));
-  return v;
-}
 __device__ __forceinline__ float warp_sum(float v) {
   for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
   return v;
 }
 
 // Votes are summed as unsigned 32-bit fixed point.  A vote is |g| times
-// weights <= 1 with |g| <= 255 * sqrt(2) < 512, so n votes stay below
-// 512 n; the scale is the largest power of two <= 2^13 that keeps 512 n
-// below 2^32 for the n pixels of the sampling box.  The scaled vote is rounded
-// by adding 1.5 * 2^23 in FP32 (exact for values below 2^22) and reading the
-// mantissa.
+// weights <= 1 with |g| <= 255 * sqrt(2) < 512, and a bin takes at most one
+// vote per pixel, so n pixels keep a bin below 512 n; the scale is the
+// largest power of two <= 2^13 that keeps 512 (n + 1) below 2^32.  The scaled
+// vote is rounded by adding 1.5 * 2^23 in FP32 (exact for values below 2^22)
+// and reading the mantissa.
 constexpr int kFWarps = 8;
+constexpr float kPi = 3.14159265358979f;
+constexpr float kHalfPi = 1.57079632679490f;
+constexpr float kLog2e = 1.44269504088896f;
 
 __device__ __forceinline__ float vote_scale(int n_pixels) {
   int sh = 13;
@@ -76,97 +79,200 @@ __device__ __forceinline__ void vote(unsigned* h, float w, float scale) {
   atomicAdd(h, q);
 }
 
-// Walks the bw x bh box starting at (u0, v0): calls f(u, v) for the box
-// pixels of this lane (index lane, lane + 32, ...) without a division per step.
+// The approximate hardware instructions (PTX ex2.approx, sqrt.approx,
+// rcp.approx; relative errors of a few FP32 ulps): the weights they feed are
+// smooth in their inputs, so these errors stay far below the parity tolerance.
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// atan2(y, x) in [-pi, pi]: t = min(|x|, |y|) / max(|x|, |y|) in [0, 1],
+// atan(t) = t P(t^2) with the degree-15 near-minimax odd polynomial printed by
+// fit_atan.py (|error| < 1.2e-7 rad in FP32), then the octant: pi/2 - r when
+// |y| > |x|, pi - r when x < 0, and the sign of y.  Gradients below 1e-30 in
+// both components give 0 or pi; their votes weigh nothing.
+__device__ __forceinline__ float atan2_poly(float y, float x) {
+  const float ax = fabsf(x), ay = fabsf(y);
+  const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+  const float t = mx >= 1e-30f ? mn * rcp_approx(mx) : 0.0f;
+  const float z = t * t;
+  float p = -4.054549150e-03f;
+  p = fmaf(p, z, 2.186289616e-02f);
+  p = fmaf(p, z, -5.591224134e-02f);
+  p = fmaf(p, z, 9.642191231e-02f);
+  p = fmaf(p, z, -1.390862763e-01f);
+  p = fmaf(p, z, 1.994656473e-01f);
+  p = fmaf(p, z, -3.332985938e-01f);
+  p = fmaf(p, z, 9.999993443e-01f);
+  float r = p * t;
+  r = ay > ax ? kHalfPi - r : r;
+  r = x < 0.0f ? kPi - r : r;
+  return copysignf(r, y);
+}
+
+// ---- sampling discs
+// The pixels (u, v) with (u - xo)^2 + (v - yo)^2 < R^2, clipped to the box
+// [bx0, bx1] x [by0, by1], are walked in bands of at most P rows (P = the
+// warp's row-table length; one band whenever the patch is staged).  For a
+// band, the warp's shared row tables hold per row r (v = v0 + r) the first
+// column ru[r], the count rn[r] and the exclusive prefix rp[r] of the counts.
+// The row spans come from h = sqrt(R^2 - dv^2) (pixels strictly inside); a
+// pixel within FP32 rounding of the circle may fall on either side.
+struct Disc {
+  int v0, nr, total;
+};
+
+__device__ __forceinline__ void disc_rows(float yo, float R, int by0, int by1, int& v0, int& n) {
+  v0 = max((int)ceilf(yo - R), by0);
+  n = max(min((int)floorf(yo + R), by1) - v0 + 1, 0);
+}
+
+__device__ __forceinline__ Disc build_band(float xo, float yo, float R2, int bx0, int bx1, int v0, int nr,
+                                           int* ru, int* rn, int* rp, int lane) {
+  Disc d;
+  d.v0 = v0;
+  d.nr = nr;
+  int carry = 0;
+  for (int r0 = 0; r0 < nr; r0 += 32) {
+    const int r = r0 + lane;
+    int n = 0;
+    if (r < nr) {
+      const float dv = (float)(v0 + r) - yo;
+      const float h2 = R2 - dv * dv;
+      int lo = 0;
+      if (h2 > 0.0f) {
+        const float h = sqrtf(h2);
+        lo = max((int)floorf(xo - h) + 1, bx0);
+        const int hi = min((int)ceilf(xo + h) - 1, bx1);
+        n = max(hi - lo + 1, 0);
+      }
+      ru[r] = lo;
+      rn[r] = n;
+    }
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (r < nr) rp[r] = carry + incl - n;
+    carry += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  d.total = carry;
+  __syncwarp();
+  return d;
+}
+
+// Lane l visits the disc pixels [l T / 32, (l + 1) T / 32) in row order and
+// calls f(u, v) for each.
 template <typename F>
-__device__ __forceinline__ void for_box(int u0, int v0, int bw, int bh, int lane, F&& f) {
-  if (bw <= 0 || bh <= 0) return;
-  const int dq = 32 / bw, dr = 32 - dq * bw;
-  int vv = lane / bw, uu = lane - vv * bw;
-  for (int i = lane; i < bw * bh; i += 32) {
-    f(u0 + uu, v0 + vv);
-    uu += dr;
-    vv += dq;
-    if (uu >= bw) {
-      uu -= bw;
-      ++vv;
+__device__ __forceinline__ void for_disc(const Disc& d, const int* ru, const int* rn, const int* rp, int lane,
+                                         F&& f) {
+  const int i0 = (d.total * lane) >> 5, i1 = (d.total * (lane + 1)) >> 5;
+  if (i0 >= i1) return;
+  // the row holding pixel i0: the last row r with rp[r] <= i0 (an empty row
+  // shares its prefix with the next one, which then wins)
+  int lo = 0, hi = d.nr;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (rp[mid] <= i0) lo = mid;
+    else hi = mid;
+  }
+  int r = lo;
+  int u = ru[r] + (i0 - rp[r]);
+  int rem = rn[r] - (i0 - rp[r]);
+  for (int i = i0; i < i1; ++i) {
+    f(u, d.v0 + r);
+    ++u;
+    if (--rem == 0 && i + 1 < i1) {
+      // pixels remain, so a non-empty row follows within the table
+      do {
+        ++r;
+      } while (r + 1 < d.nr && rn[r] == 0);
+      u = ru[r];
+      rem = rn[r];
     }
   }
 }
 
-// ---- Alg. 2, fused per point.  Stage A: 36-bin histogram of atan2(gy, gx)
+// Every pixel of the disc of radius R, band by band: f(u, v) on each.
+template <typename F>
+__device__ __forceinline__ void for_each_disc_pixel(float xo, float yo, float R, int bx0, int bx1, int by0,
+                                                    int by1, int P, int* ru, int* rn, int* rp, int lane, F&& f) {
+  int v0, n;
+  disc_rows(yo, R, by0, by1, v0, n);
+  for (int b0 = 0; b0 < n; b0 += P) {
+    const Disc d = build_band(xo, yo, R * R, bx0, bx1, v0 + b0, min(P, n - b0), ru, rn, rp, lane);
+    for_disc(d, ru, rn, rp, lane, f);
+    __syncwarp();  // the row tables are rebuilt for the next band
+  }
+}
+
+// Central-difference gradients, clamp-to-edge.  PatchSrc reads the staged
+// patch, whose one-pixel ring around the sampling box already holds the
+// replicated edge, so it needs no clamps; LevelSrc reads the level itself.
+struct PatchSrc {
+  const float* p;  // patch element (pu0, pv0)
+  int P, pu0, pv0;
+  __device__ __forceinline__ void grad(int u, int v, float& gx, float& gy) const {
+    const float* q = p + (v - pv0) * P + (u - pu0);
+    gx = q[1] - q[-1];
+    gy = q[P] - q[-P];
+  }
+};
+
+template <typename StoreT>
+struct LevelSrc {
+  LevelView<StoreT> G;
+  __device__ __forceinline__ void grad(int u, int v, float& gx, float& gy) const { G.grad(u, v, gx, gy); }
+};
+
+// ---- Alg. 2 for one point.  Stage A: 36-bin histogram of atan2(gy, gx)
 // over the disc of radius ori_radius * sigma, weight
 // |g| exp(-d^2 / (2 (ori_wsig sigma)^2)); orientations at bins strictly above
 // both circular neighbours and above ori_ratio * max, refined by a parabola
 // through three bins, in order of bin value.  Stage B, per orientation: 4x4
 // cells of side cell_side * sigma in the frame rotated by -theta, 8 bins of
 // the gradient angle relative to theta, trilinear votes weighted by
-// |g| exp(-(u^2+v^2) / (2 desc_wsig^2)) ((u, v) in cells) over the disc of
-// radius desc_radius * sigma; L2-normalise, clamp at 0.2, renormalise.
-// Records and descriptors go to per-point staging slots (max_ori each).
-template <typename StoreT>
-__global__ void __launch_bounds__(kFWarps * 32) describe_kernel(const __grid_constant__ DescribeArgs a) {
-  extern __shared__ float4 smem4[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int P = a.patch_side;
-  float* patch = reinterpret_cast<float*>(smem4) + (size_t)warp * P * P;
-  unsigned* hist = reinterpret_cast<unsigned*>(reinterpret_cast<float*>(smem4) + (size_t)kFWarps * P * P) +
-                   warp * (36 + 128);
-  unsigned* ho = hist;        // 36 orientation bins
-  unsigned* hd = hist + 36;   // 128 descriptor bins
-  const int slot = blockIdx.x * kFWarps + warp;
-  if (slot >= a.n_images * a.N) return;
-  const int img = slot / a.N, rank = slot - img * a.N;
-  if (rank >= a.sel_count[img]) return;
-  const Cand c = a.sel[slot];
-  const int k = desc_level(c.so, a.sigma0);
-  const LevelView<StoreT> G = level_of<StoreT>(a, img, c.octave, k);
-  const float Rd = a.desc_radius * c.so, Ro = a.ori_radius * c.so;
-  const float R = fmaxf(Rd, a.upright ? 0.0f : Ro);
-  const int u0 = max((int)ceilf(c.xo - R), 0), u1 = min((int)floorf(c.xo + R), G.W - 1);
-  const int v0 = max((int)ceilf(c.yo - R), 0), v1 = min((int)floorf(c.yo + R), G.H - 1);
-  // the patch: the sampling box plus the pixels its gradients read
-  const int pu0 = max(u0 - 1, 0), pu1 = min(u1 + 1, G.W - 1);
-  const int pv0 = max(v0 - 1, 0), pv1 = min(v1 + 1, G.H - 1);
-  const int pw = pu1 - pu0 + 1, ph = pv1 - pv0 + 1;
-  const bool staged = pw > 0 && ph > 0 && pw <= P && ph <= P;
-  if (staged) {
-    for (int r = 0; r < ph; ++r) {
-      const StoreT* row = G.base + (size_t)(pv0 + r) * G.pitch + pu0;
-      for (int cc = lane; cc < pw; cc += 32) patch[r * P + cc] = ld(row + cc);
-    }
-  }
-  __syncwarp();
-  auto at = [&](int u, int v) -> float { return staged ? patch[(v - pv0) * P + (u - pu0)] : G.at(u, v); };
-  // central differences, clamp-to-edge
-  auto grad = [&](int u, int v, float& gx, float& gy) {
-    gx = at(min(u + 1, G.W - 1), v) - at(max(u - 1, 0), v);
-    gy = at(u, min(v + 1, G.H - 1)) - at(u, max(v - 1, 0));
-  };
-
-  // ---- stage A
+// |g| exp(-(u^2+v^2) / (2 desc_wsig^2)) ((u, v) in cells; the rotation keeps
+// u^2 + v^2 = d^2 / cell^2) over the disc of radius desc_radius * sigma;
+// L2-normalise, clamp at 0.2, renormalise.  Records and descriptors go to the
+// point's staging slots (max_ori each).
+template <typename Src>
+__device__ __forceinline__ void describe_point(const DescribeArgs& a, const Cand& c, int slot, int img, int rank,
+                                               int k, const Src& src, int bx0, int bx1, int by0, int by1, int P,
+                                               unsigned* ho, unsigned* hd, int* ru, int* rn, int* rp, int lane) {
+  // vote scales from the box area, which bounds the pixel count of any disc
+  const float osc = vote_scale((bx1 - bx0 + 1) * (by1 - by0 + 1)), dsc = osc;
   float thetas[kMaxOri];
   int n_ori = 1;
   thetas[0] = 0.0f;
   if (!a.upright) {
     for (int b = lane; b < 36; b += 32) ho[b] = 0u;
     __syncwarp();
-    const float R2 = Ro * Ro;
     const float sw = a.ori_wsig * c.so;
-    const float inv2 = 1.0f / (2.0f * sw * sw);
-    const int ou0 = max((int)ceilf(c.xo - Ro), 0), ou1 = min((int)floorf(c.xo + Ro), G.W - 1);
-    const int ov0 = max((int)ceilf(c.yo - Ro), 0), ov1 = min((int)floorf(c.yo + Ro), G.H - 1);
-    const float osc = vote_scale(max(ou1 - ou0 + 1, 0) * max(ov1 - ov0 + 1, 0));
-    for_box(ou0, ov0, ou1 - ou0 + 1, ov1 - ov0 + 1, lane, [&](int u, int v) {
+    const float kA = -kLog2e / (2.0f * sw * sw);
+    for_each_disc_pixel(c.xo, c.yo, a.ori_radius * c.so, bx0, bx1, by0, by1, P, ru, rn, rp, lane,
+                        [&](int u, int v) {
       const float du = (float)u - c.xo, dv = (float)v - c.yo;
-      const float d2 = du * du + dv * dv;
-      if (!(d2 < R2)) return;
       float gx, gy;
-      grad(u, v, gx, gy);
-      const float w = sqrtf(gx * gx + gy * gy) * expf(-d2 * inv2);
-      const float f = atan2f(gy, gx) * (36.0f / kTwoPi);
-      int b = (int)floorf(f);
-      b = ((b % 36) + 36) % 36;
+      src.grad(u, v, gx, gy);
+      const float w = sqrt_approx(gx * gx + gy * gy) * ex2_approx((du * du + dv * dv) * kA);
+      int b = (int)floorf(atan2_poly(gy, gx) * (36.0f / (2.0f * kPi)));
+      b += b < 0 ? 36 : 0;
+      b -= b >= 36 ? 36 : 0;
       vote(ho + b, w, osc);
     });
     __syncwarp();
@@ -185,9 +291,9 @@ __global__ void __launch_bounds__(kFWarps * 32) describe_kernel(const __grid_con
       if (!(cc > l && cc > r)) continue;
       if (!(cc > a.ori_ratio * mx)) continue;
       const float off = 0.5f * (l - r) / (l - 2.0f * cc + r);
-      float t = kTwoPi * ((float)b + 0.5f + off) / 36.0f;
-      if (t >= kTwoPi) t -= kTwoPi;
-      if (t < 0.0f) t += kTwoPi;
+      float t = 2.0f * kPi * ((float)b + 0.5f + off) / 36.0f;
+      if (t >= 2.0f * kPi) t -= 2.0f * kPi;
+      if (t < 0.0f) t += 2.0f * kPi;
       // keep the max_ori largest, by (value desc, bin asc)
       int j = n_ori < a.max_ori ? n_ori++ : a.max_ori;
       while (j > 0 && cc > pv[j - 1]) {
@@ -206,12 +312,8 @@ __global__ void __launch_bounds__(kFWarps * 32) describe_kernel(const __grid_con
   if (lane == 0) a.ori_count[slot] = n_ori;
 
   // ---- stage B, per orientation
-  const float Rd2 = Rd * Rd;
   const float inv_cs = 1.0f / (a.cell_side * c.so);
-  const float inv2w = 1.0f / (2.0f * a.desc_wsig * a.desc_wsig);
-  const int du0 = max((int)ceilf(c.xo - Rd), 0), du1 = min((int)floorf(c.xo + Rd), G.W - 1);
-  const int dv0 = max((int)ceilf(c.yo - Rd), 0), dv1 = min((int)floorf(c.yo + Rd), G.H - 1);
-  const float dsc = vote_scale(max(du1 - du0 + 1, 0) * max(dv1 - dv0 + 1, 0));
+  const float kB = -kLog2e * inv_cs * inv_cs / (2.0f * a.desc_wsig * a.desc_wsig);
   const size_t out0 = (size_t)slot * a.max_ori;
   for (int j = 0; j < n_ori; ++j) {
     const float theta = thetas[j];
@@ -220,20 +322,19 @@ __global__ void __launch_bounds__(kFWarps * 32) describe_kernel(const __grid_con
     __syncwarp();
     float st, ct;
     sincosf(theta, &st, &ct);
-    for_box(du0, dv0, du1 - du0 + 1, dv1 - dv0 + 1, lane, [&](int u, int v) {
+    const float cc_ = ct * inv_cs, sc_ = st * inv_cs;
+    for_each_disc_pixel(c.xo, c.yo, a.desc_radius * c.so, bx0, bx1, by0, by1, P, ru, rn, rp, lane,
+                        [&](int u, int v) {
       const float du = (float)u - c.xo, dv = (float)v - c.yo;
-      if (!(du * du + dv * dv < Rd2)) return;
-      const float xr = (ct * du + st * dv) * inv_cs;
-      const float yr = (-st * du + ct * dv) * inv_cs;
+      const float xr = fmaf(cc_, du, sc_ * dv);
+      const float yr = fmaf(cc_, dv, -sc_ * du);
       float gx, gy;
-      grad(u, v, gx, gy);
-      const float mag = sqrtf(gx * gx + gy * gy);
-      float ang = atan2f(gy, gx) - theta;
-      while (ang < 0.0f) ang += kTwoPi;
-      while (ang >= kTwoPi) ang -= kTwoPi;
-      float ob = ang * (8.0f / kTwoPi);
-      if (ob >= 8.0f) ob -= 8.0f;
-      const float w = mag * expf(-(xr * xr + yr * yr) * inv2w);
+      src.grad(u, v, gx, gy);
+      const float w = sqrt_approx(gx * gx + gy * gy) * ex2_approx((du * du + dv * dv) * kB);
+      float ob = (atan2_poly(gy, gx) - theta) * (8.0f / (2.0f * kPi));
+      ob += ob < 0.0f ? 8.0f : 0.0f;
+      ob += ob < 0.0f ? 8.0f : 0.0f;
+      ob -= ob >= 8.0f ? 8.0f : 0.0f;
       const float cx = xr + 1.5f, cy = yr + 1.5f;
       const float fx0 = floorf(cx), fy0 = floorf(cy), fo0 = floorf(ob);
       const float fx = cx - fx0, fy = cy - fy0, fo = ob - fo0;
@@ -268,9 +369,9 @@ __global__ void __launch_bounds__(kFWarps * 32) describe_kernel(const __grid_con
 #pragma unroll
       for (int q = 0; q < 4; ++q) v[q] *= inv2;
     }
-    float* d = a.stage_desc + (out0 + j) * 128;
+    float* dd = a.stage_desc + (out0 + j) * 128;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) d[lane + 32 * q] = v[q];
+    for (int q = 0; q < 4; ++q) dd[lane + 32 * q] = v[q];
     if (lane == 0) {
       const float s = (float)(1 << c.octave);
       cdvs_keypoint kp;
@@ -290,6 +391,72 @@ __global__ void __launch_bounds__(kFWarps * 32) describe_kernel(const __grid_con
       a.stage_kp[out0 + j] = kp;
     }
     __syncwarp();
+  }
+}
+
+// 4 bytes global -> shared without passing through registers
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(static_cast<unsigned>(__cvta_generic_to_shared(dst))),
+               "l"(src)
+               : "memory");
+}
+
+// Patch rows pv0 .. pv0 + ph - 1, columns pu0 .. pu0 + pw - 1 of the level,
+// clamped to the image, into patch[r * P + c].
+__device__ __forceinline__ void stage_patch(const LevelView<float>& G, int pu0, int pv0, int pw, int ph, int P,
+                                            float* patch, int lane) {
+  for (int r = 0; r < ph; ++r) {
+    const float* row = G.base + (size_t)min(max(pv0 + r, 0), G.H - 1) * G.pitch;
+    for (int cc = lane; cc < pw; cc += 32) cp_async4(patch + r * P + cc, row + min(max(pu0 + cc, 0), G.W - 1));
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+__device__ __forceinline__ void stage_patch(const LevelView<__half>& G, int pu0, int pv0, int pw, int ph, int P,
+                                            float* patch, int lane) {
+  for (int r = 0; r < ph; ++r) {
+    const __half* row = G.base + (size_t)min(max(pv0 + r, 0), G.H - 1) * G.pitch;
+    for (int cc = lane; cc < pw; cc += 32) patch[r * P + cc] = ld(row + min(max(pu0 + cc, 0), G.W - 1));
+  }
+}
+
+// Persistent warps: warp w of the grid takes the slots w, w + (all warps), ...
+template <typename StoreT>
+__global__ void __launch_bounds__(kFWarps * 32) describe_kernel(const __grid_constant__ DescribeArgs a) {
+  extern __shared__ float4 smem4[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int P = a.patch_side;
+  float* patch = reinterpret_cast<float*>(smem4) + (size_t)warp * P * P;
+  unsigned* hist = reinterpret_cast<unsigned*>(reinterpret_cast<float*>(smem4) + (size_t)kFWarps * P * P) +
+                   warp * (36 + 128 + 3 * P);
+  unsigned* ho = hist;        // 36 orientation bins
+  unsigned* hd = hist + 36;   // 128 descriptor bins
+  int* ru = reinterpret_cast<int*>(hist + 36 + 128);  // disc row tables, P rows each
+  int* rn = ru + P;
+  int* rp = rn + P;
+  const int S = a.n_images * a.N;
+  for (int slot = blockIdx.x * kFWarps + warp; slot < S; slot += gridDim.x * kFWarps) {
+    const int img = slot / a.N, rank = slot - img * a.N;
+    if (rank >= a.sel_count[img]) continue;
+    const Cand c = a.sel[slot];
+    const int k = desc_level(c.so, a.sigma0);
+    const LevelView<StoreT> G = level_of<StoreT>(a, img, c.octave, k);
+    // the sampling box of both discs, clipped to the image
+    const float R = fmaxf(a.desc_radius * c.so, a.upright ? 0.0f : a.ori_radius * c.so);
+    const int bx0 = max((int)ceilf(c.xo - R), 0), bx1 = min((int)floorf(c.xo + R), G.W - 1);
+    const int by0 = max((int)ceilf(c.yo - R), 0), by1 = min((int)floorf(c.yo + R), G.H - 1);
+    // the patch: the box and a one-pixel ring (edge replicated)
+    const int pu0 = bx0 - 1, pv0 = by0 - 1;
+    const int pw = bx1 - bx0 + 3, ph = by1 - by0 + 3;
+    if (pw <= P && ph <= P) {
+      stage_patch(G, pu0, pv0, pw, ph, P, patch, lane);
+      __syncwarp();
+      PatchSrc src{patch, P, pu0, pv0};
+      describe_point(a, c, slot, img, rank, k, src, bx0, bx1, by0, by1, P, ho, hd, ru, rn, rp, lane);
+    } else {
+      LevelSrc<StoreT> src{G};
+      describe_point(a, c, slot, img, rank, k, src, bx0, bx1, by0, by1, P, ho, hd, ru, rn, rp, lane);
+    }
+    __syncwarp();  // the patch and tables are rewritten for the next point
   }
 }
 
@@ -370,25 +537,28 @@ __global__ void levels_to_f32_kernel(const StoreT* src, int W, int H, int lpitch
 }  // namespace
 
 size_t describe_smem_bytes(int patch_side) {
-  return (size_t)kFWarps * ((size_t)patch_side * patch_side * sizeof(float) + (36 + 128) * sizeof(unsigned));
+  return (size_t)kFWarps * ((size_t)patch_side * patch_side * sizeof(float) +
+                            (36 + 128 + 3 * (size_t)patch_side) * sizeof(unsigned));
 }
 
-cudaError_t launch_describe(const DescribeArgs& a, int storage, cudaStream_t s) {
+// Persistent grid: as many CTAs as fit on the SMs at once (never more than
+// there are slots for).
+cudaError_t launch_describe(const DescribeArgs& a, int storage, int n_sms, cudaStream_t s) {
   const int slots = a.n_images * a.N;
   if (slots <= 0) return cudaSuccess;
-  const int grid = (slots + kFWarps - 1) / kFWarps;
   const size_t smem = describe_smem_bytes(a.patch_side);
-  cudaError_t e;
-  if (storage == CDVS_STORAGE_FP16) {
-    e = cudaFuncSetAttribute(describe_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto go = [&](auto kernel) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    describe_kernel<__half><<<grid, kFWarps * 32, smem, s>>>(a);
-  } else {
-    e = cudaFuncSetAttribute(describe_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kFWarps * 32, smem);
     if (e != cudaSuccess) return e;
-    describe_kernel<float><<<grid, kFWarps * 32, smem, s>>>(a);
-  }
-  return cudaGetLastError();
+    const int need = (slots + kFWarps - 1) / kFWarps;
+    const int grid = std::max(1, std::min(need, std::max(per_sm, 1) * n_sms));
+    kernel<<<grid, kFWarps * 32, smem, s>>>(a);
+    return cudaGetLastError();
+  };
+  return storage == CDVS_STORAGE_FP16 ? go(describe_kernel<__half>) : go(describe_kernel<float>);
 }
 
 // The slot offsets live right after the record map's kp_capacity entries
