@@ -38,7 +38,7 @@ struct cdvs_ctx {
   int device = 0;
   int n_sms = 0;
   std::string err;
-  DevBuf levels, cands, cand_count, order, keep, sel, sel_count, ori_theta, ori_count, rec_map,
+  DevBuf levels, cands, cand_count, order, keep, sel, sel_count, ori_theta, ori_count, rec_off,
       rec_total, out_kp, out_desc, out_count, plans, tile_prefix, status, input, dump, stage_kp, stage_desc;
   HostBuf small;  // pinned: status word + record total
   std::vector<ImgPlan> h_plans;
@@ -367,7 +367,7 @@ DescribeArgs describe_args(cdvs_ctx* c, int n, const cdvs_params& p) {
   d.n_images = n;
   d.ori_theta = static_cast<float*>(c->ori_theta.p);
   d.ori_count = static_cast<int*>(c->ori_count.p);
-  d.rec_map = static_cast<int*>(c->rec_map.p);
+  d.rec_off = static_cast<int*>(c->rec_off.p);
   d.rec_total = static_cast<int*>(c->rec_total.p);
   d.status = static_cast<int*>(c->status.p);
   d.sigma0 = p.sigma0;
@@ -451,7 +451,7 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
       (e = ensure(c->sel_count, sizeof(int) * n)) != cudaSuccess ||
       (e = ensure(c->ori_theta, sizeof(float) * slots * kMaxOri)) != cudaSuccess ||
       (e = ensure(c->ori_count, sizeof(int) * slots)) != cudaSuccess ||
-      (e = ensure(c->rec_map, sizeof(int) * ((size_t)capacity + slots + 1))) != cudaSuccess ||
+      (e = ensure(c->rec_off, sizeof(int) * (slots + 2 * (size_t)n + 1))) != cudaSuccess ||
       (e = ensure(c->rec_total, sizeof(int) * 4)) != cudaSuccess ||
       (e = ensure(c->status, sizeof(int) * 4)) != cudaSuccess ||
       (e = ensure(c->stage_kp, sizeof(cdvs_keypoint) * slots * p.max_orientations)) != cudaSuccess ||
@@ -664,7 +664,7 @@ void cdvs_destroy(cdvs_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   DevBuf* bufs[] = {&c->levels,  &c->cands,   &c->cand_count, &c->order,   &c->keep,
-                    &c->sel,     &c->sel_count, &c->ori_theta, &c->ori_count, &c->rec_map,
+                    &c->sel,     &c->sel_count, &c->ori_theta, &c->ori_count, &c->rec_off,
                     &c->rec_total, &c->out_kp, &c->out_desc, &c->out_count, &c->plans,
                     &c->tile_prefix, &c->status, &c->input, &c->dump, &c->stage_kp, &c->stage_desc};
   for (DevBuf* b : bufs)

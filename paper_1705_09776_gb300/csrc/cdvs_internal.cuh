@@ -107,7 +107,7 @@ struct DescribeArgs {
   int n_images;
   float* ori_theta;        // n_images x N x kMaxOri
   int* ori_count;          // n_images x N
-  int* rec_map;            // output record -> slot * kMaxOri + copy
+  int* rec_off;            // packing scratch: per-slot and per-image record offsets
   int* rec_total;          // number of records written
   int* kp_count;           // per image records written
   int kp_capacity;

@@ -19,7 +19,6 @@
 namespace cdvs {
 namespace {
 
-constexpr int kScanThreads = 1024;
 
 __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float ld(const __half* p) { return __half2float(*p); }
@@ -52,6 +51,10 @@ __device__ __forceinline__ LevelView<StoreT> level_of(const DescribeArgs& a, int
   return v;
 }
 
+__device__ __forceinline__ float warp_max(float v) {
+  for (int d = 16; d > 0; d >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, d));
+  return v;
+}
 __device__ __forceinline__ float warp_sum(float v) {
   for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
   return v;
@@ -253,12 +256,12 @@ struct LevelSrc {
 template <typename Src>
 __device__ __forceinline__ void describe_point(const DescribeArgs& a, const Cand& c, int slot, int img, int rank,
                                                int k, const Src& src, int bx0, int bx1, int by0, int by1, int P,
-                                               unsigned* ho, unsigned* hd, int* ru, int* rn, int* rp, int lane) {
+                                               unsigned* ho, unsigned* hd, float* thetas, int* ru, int* rn, int* rp,
+                                               int lane) {
   // vote scales from the box area, which bounds the pixel count of any disc
   const float osc = vote_scale((bx1 - bx0 + 1) * (by1 - by0 + 1)), dsc = osc;
-  float thetas[kMaxOri];
   int n_ori = 1;
-  thetas[0] = 0.0f;
+  if (lane == 0) thetas[0] = 0.0f;
   if (!a.upright) {
     for (int b = lane; b < 36; b += 32) ho[b] = 0u;
     __syncwarp();
@@ -276,38 +279,52 @@ __device__ __forceinline__ void describe_point(const DescribeArgs& a, const Cand
       vote(ho + b, w, osc);
     });
     __syncwarp();
-    // every lane reads the 36 sums; the peak search is uniform over the warp
-    float h[36];
+    // peaks: lane b (and b + 32) takes bin b; a peak's place among the
+    // orientations is its rank by (value desc, bin asc)
+    const float inv_osc = 1.0f / osc;
+    float hv[2], mx = 0.0f;
 #pragma unroll
-    for (int b = 0; b < 36; ++b) h[b] = (float)ho[b] / osc;
-    float mx = 0.0f;
-#pragma unroll
-    for (int b = 0; b < 36; ++b) mx = fmaxf(mx, h[b]);
-    float pv[kMaxOri];
-    n_ori = 0;
-#pragma unroll
-    for (int b = 0; b < 36; ++b) {
-      const float l = h[(b + 35) % 36], cc = h[b], r = h[(b + 1) % 36];
-      if (!(cc > l && cc > r)) continue;
-      if (!(cc > a.ori_ratio * mx)) continue;
-      const float off = 0.5f * (l - r) / (l - 2.0f * cc + r);
-      float t = 2.0f * kPi * ((float)b + 0.5f + off) / 36.0f;
-      if (t >= 2.0f * kPi) t -= 2.0f * kPi;
-      if (t < 0.0f) t += 2.0f * kPi;
-      // keep the max_ori largest, by (value desc, bin asc)
-      int j = n_ori < a.max_ori ? n_ori++ : a.max_ori;
-      while (j > 0 && cc > pv[j - 1]) {
-        if (j < a.max_ori) {
-          pv[j] = pv[j - 1];
-          thetas[j] = thetas[j - 1];
-        }
-        --j;
-      }
-      if (j < a.max_ori) {
-        pv[j] = cc;
-        thetas[j] = t;
-      }
+    for (int q = 0; q < 2; ++q) {
+      const int b = lane + 32 * q;
+      hv[q] = b < 36 ? (float)ho[b] * inv_osc : 0.0f;
+      mx = fmaxf(mx, hv[q]);
     }
+    mx = warp_max(mx);
+    bool pk[2];
+    float th[2];
+    unsigned peaks[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int b = lane + 32 * q;
+      pk[q] = false;
+      th[q] = 0.0f;
+      if (b < 36) {
+        const float l = (float)ho[b == 0 ? 35 : b - 1] * inv_osc, cc = hv[q];
+        const float r = (float)ho[b == 35 ? 0 : b + 1] * inv_osc;
+        pk[q] = cc > l && cc > r && cc > a.ori_ratio * mx;
+        const float off = 0.5f * (l - r) / (l - 2.0f * cc + r);
+        float t = 2.0f * kPi * ((float)b + 0.5f + off) / 36.0f;
+        if (t >= 2.0f * kPi) t -= 2.0f * kPi;
+        if (t < 0.0f) t += 2.0f * kPi;
+        th[q] = t;
+      }
+      peaks[q] = __ballot_sync(0xffffffffu, pk[q]);
+    }
+    n_ori = min(__popc(peaks[0]) + __popc(peaks[1]), a.max_ori);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      if (!pk[q]) continue;
+      const int b = lane + 32 * q;
+      int rank = 0;
+      for (int m = 0; m < 2; ++m)
+        for (unsigned bits = peaks[m]; bits; bits &= bits - 1) {
+          const int b2 = __ffs(bits) - 1 + 32 * m;
+          const float v2 = (float)ho[b2] * inv_osc;
+          rank += v2 > hv[q] || (v2 == hv[q] && b2 < b);
+        }
+      if (rank < a.max_ori) thetas[rank] = th[q];
+    }
+    __syncwarp();
   }
   if (lane == 0) a.ori_count[slot] = n_ori;
 
@@ -315,6 +332,7 @@ __device__ __forceinline__ void describe_point(const DescribeArgs& a, const Cand
   const float inv_cs = 1.0f / (a.cell_side * c.so);
   const float kB = -kLog2e * inv_cs * inv_cs / (2.0f * a.desc_wsig * a.desc_wsig);
   const size_t out0 = (size_t)slot * a.max_ori;
+  __syncwarp();
   for (int j = 0; j < n_ori; ++j) {
     const float theta = thetas[j];
 #pragma unroll
@@ -394,6 +412,17 @@ __device__ __forceinline__ void describe_point(const DescribeArgs& a, const Cand
   }
 }
 
+// Points whose box does not fit the patch read the level directly; kept out
+// of line so the kernel's hot code stays small.
+template <typename StoreT>
+__device__ __noinline__ void describe_point_unstaged(const DescribeArgs& a, const Cand& c, int slot, int img,
+                                                     int rank, int k, const LevelView<StoreT>& G, int bx0, int bx1,
+                                                     int by0, int by1, int P, unsigned* ho, unsigned* hd,
+                                                     float* thetas, int* ru, int* rn, int* rp, int lane) {
+  LevelSrc<StoreT> src{G};
+  describe_point(a, c, slot, img, rank, k, src, bx0, bx1, by0, by1, P, ho, hd, thetas, ru, rn, rp, lane);
+}
+
 // 4 bytes global -> shared without passing through registers
 __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(static_cast<unsigned>(__cvta_generic_to_shared(dst))),
@@ -421,16 +450,17 @@ __device__ __forceinline__ void stage_patch(const LevelView<__half>& G, int pu0,
 
 // Persistent warps: warp w of the grid takes the slots w, w + (all warps), ...
 template <typename StoreT>
-__global__ void __launch_bounds__(kFWarps * 32) describe_kernel(const __grid_constant__ DescribeArgs a) {
+__global__ void __launch_bounds__(kFWarps * 32, 3) describe_kernel(const __grid_constant__ DescribeArgs a) {
   extern __shared__ float4 smem4[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int P = a.patch_side;
   float* patch = reinterpret_cast<float*>(smem4) + (size_t)warp * P * P;
   unsigned* hist = reinterpret_cast<unsigned*>(reinterpret_cast<float*>(smem4) + (size_t)kFWarps * P * P) +
-                   warp * (36 + 128 + 3 * P);
+                   warp * (36 + 128 + kMaxOri + 3 * P);
   unsigned* ho = hist;        // 36 orientation bins
   unsigned* hd = hist + 36;   // 128 descriptor bins
-  int* ru = reinterpret_cast<int*>(hist + 36 + 128);  // disc row tables, P rows each
+  float* thetas = reinterpret_cast<float*>(hist + 36 + 128);  // the point's orientations
+  int* ru = reinterpret_cast<int*>(hist + 36 + 128 + kMaxOri);  // disc row tables, P rows each
   int* rn = ru + P;
   int* rp = rn + P;
   const int S = a.n_images * a.N;
@@ -451,79 +481,114 @@ __global__ void __launch_bounds__(kFWarps * 32) describe_kernel(const __grid_con
       stage_patch(G, pu0, pv0, pw, ph, P, patch, lane);
       __syncwarp();
       PatchSrc src{patch, P, pu0, pv0};
-      describe_point(a, c, slot, img, rank, k, src, bx0, bx1, by0, by1, P, ho, hd, ru, rn, rp, lane);
+      describe_point(a, c, slot, img, rank, k, src, bx0, bx1, by0, by1, P, ho, hd, thetas, ru, rn, rp, lane);
     } else {
-      LevelSrc<StoreT> src{G};
-      describe_point(a, c, slot, img, rank, k, src, bx0, bx1, by0, by1, P, ho, hd, ru, rn, rp, lane);
+      describe_point_unstaged<StoreT>(a, c, slot, img, rank, k, G, bx0, bx1, by0, by1, P, ho, hd, thetas, ru, rn,
+                                      rp, lane);
     }
     __syncwarp();  // the patch and tables are rewritten for the next point
   }
 }
 
-// ---- packing: record offsets of every (image, rank, copy) in batch order
-__global__ void __launch_bounds__(kScanThreads) scan_kernel(const __grid_constant__ DescribeArgs a,
-                                                            int* slot_off) {
-  __shared__ int warp_sums[33];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int S = a.n_images * a.N;
-  const int per = (S + kScanThreads - 1) / kScanThreads;
-  const int b0 = min(tid * per, S), b1 = min(b0 + per, S);
-  auto count_of = [&](int slot) {
-    const int img = slot / a.N, rank = slot - img * a.N;
-    return rank < a.sel_count[img] ? a.ori_count[slot] : 0;
-  };
+// ---- packing.  Records go out in batch order: image, then rank, then copy.
+// scan_kernel: one warp per image writes, per slot, the offset of its first
+// record within the image (local_off) and the image's record count
+// (img_tot); the CTA that finishes last (a counter in status[1], zeroed with
+// the status word before every call) scans the image counts into img_off,
+// the per-image counts clipped to the capacity, and the batch total.
+constexpr int kPackWarps = 8;
+
+__global__ void __launch_bounds__(kPackWarps * 32) scan_kernel(const __grid_constant__ DescribeArgs a,
+                                                               int* local_off, int* img_tot, int* img_off) {
+  __shared__ int is_last;
+  __shared__ int warp_sums[kPackWarps * 32 / 32 + 1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int img = blockIdx.x * kPackWarps + warp;
+  if (img < a.n_images) {
+    const int cnt = a.sel_count[img];
+    const int per = (a.N + 31) / 32;
+    const int r0 = min(lane * per, a.N), r1 = min(r0 + per, a.N);
+    const int* oc = a.ori_count + (size_t)img * a.N;
+    int local = 0;
+    for (int r = r0; r < r1; ++r) local += r < cnt ? oc[r] : 0;
+    int incl = local;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += v;
+    }
+    int run = incl - local;
+    int* lo = local_off + (size_t)img * a.N;
+    for (int r = r0; r < r1; ++r) {
+      lo[r] = run;
+      run += r < cnt ? oc[r] : 0;
+    }
+    if (lane == 31) img_tot[img] = incl;
+  }
+  // the last CTA to arrive sees every image count
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(reinterpret_cast<unsigned*>(a.status + 1), 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  const int n = a.n_images;
+  const int per = (n + blockDim.x - 1) / blockDim.x;
+  const int i0 = min((int)threadIdx.x * per, n), i1 = min(i0 + per, n);
   int local = 0;
-  for (int s = b0; s < b1; ++s) local += count_of(s);
+  for (int i = i0; i < i1; ++i) local += __ldcg(img_tot + i);
   int incl = local;
+#pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
     const int v = __shfl_up_sync(0xffffffffu, incl, d);
     if (lane >= d) incl += v;
   }
   if (lane == 31) warp_sums[warp] = incl;
   __syncthreads();
-  if (warp == 0) {
-    const int w = warp_sums[lane];
-    int wi = w;
-    for (int d = 1; d < 32; d <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, wi, d);
-      if (lane >= d) wi += v;
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < kPackWarps; ++w) {
+      const int v = warp_sums[w];
+      warp_sums[w] = t;
+      t += v;
     }
-    warp_sums[lane] = wi - w;
-    if (lane == 31) warp_sums[32] = wi;
+    warp_sums[kPackWarps] = t;
   }
   __syncthreads();
-  int run = warp_sums[warp] + incl - local;
-  const int total = warp_sums[32];
   const int cap = a.kp_capacity;
-  for (int s = b0; s < b1; ++s) {
-    const int c = count_of(s);
-    slot_off[s] = run;
-    for (int j = 0; j < c; ++j)
-      if (run + j < cap) a.rec_map[run + j] = s * kMaxOri + j;
+  int run = warp_sums[warp] + incl - local;
+  for (int i = i0; i < i1; ++i) {
+    const int c = __ldcg(img_tot + i);
+    img_off[i] = run;
+    a.kp_count[i] = min(run + c, cap) - min(run, cap);
     run += c;
   }
-  if (tid == 0) slot_off[S] = total;
-  __syncthreads();
-  for (int i = tid; i < a.n_images; i += kScanThreads) {
-    const int beg = min(slot_off[i * a.N], cap), end = min(slot_off[(i + 1) * a.N], cap);
-    a.kp_count[i] = end - beg;
-  }
-  if (tid == 0) {
+  if (threadIdx.x == 0) {
+    const int total = warp_sums[kPackWarps];
+    img_off[n] = total;
     *a.rec_total = min(total, cap);
     if (total > cap) atomicOr(a.status, kStatusOutTruncated);
   }
 }
 
-// ---- packed output: record r of the batch comes from staging slot rec_map[r]
-__global__ void __launch_bounds__(256) copy_kernel(const __grid_constant__ DescribeArgs a) {
+// ---- packed output: one warp per slot copies its records from the staging
+// slots to their batch positions (records past the capacity are dropped)
+__global__ void __launch_bounds__(256) copy_kernel(const __grid_constant__ DescribeArgs a, const int* local_off,
+                                                   const int* img_off) {
   const int lane = threadIdx.x & 31;
-  const int total = *a.rec_total;
-  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < total; r += (gridDim.x * blockDim.x) >> 5) {
-    const int m = a.rec_map[r];
-    const size_t src = (size_t)(m / kMaxOri) * a.max_ori + (m % kMaxOri);
-    reinterpret_cast<float4*>(a.desc_out + (size_t)r * 128)[lane] =
-        reinterpret_cast<const float4*>(a.stage_desc + src * 128)[lane];
-    if (lane == 0) a.kp_out[r] = a.stage_kp[src];
+  const int S = a.n_images * a.N;
+  const int cap = a.kp_capacity;
+  for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < S; s += (gridDim.x * blockDim.x) >> 5) {
+    const int img = s / a.N, rank = s - img * a.N;
+    if (rank >= a.sel_count[img]) continue;
+    const int n = a.ori_count[s];
+    const int base = img_off[img] + local_off[s];
+    for (int j = 0; j < n && base + j < cap; ++j) {
+      const size_t src = (size_t)s * a.max_ori + j, dst = (size_t)(base + j);
+      reinterpret_cast<float4*>(a.desc_out + dst * 128)[lane] =
+          reinterpret_cast<const float4*>(a.stage_desc + src * 128)[lane];
+      if (lane == 0) a.kp_out[dst] = a.stage_kp[src];
+    }
   }
 }
 
@@ -538,7 +603,7 @@ __global__ void levels_to_f32_kernel(const StoreT* src, int W, int H, int lpitch
 
 size_t describe_smem_bytes(int patch_side) {
   return (size_t)kFWarps * ((size_t)patch_side * patch_side * sizeof(float) +
-                            (36 + 128 + 3 * (size_t)patch_side) * sizeof(unsigned));
+                            (36 + 128 + kMaxOri + 3 * (size_t)patch_side) * sizeof(unsigned));
 }
 
 // Persistent grid: as many CTAs as fit on the SMs at once (never more than
@@ -561,17 +626,25 @@ cudaError_t launch_describe(const DescribeArgs& a, int storage, int n_sms, cudaS
   return storage == CDVS_STORAGE_FP16 ? go(describe_kernel<__half>) : go(describe_kernel<float>);
 }
 
-// The slot offsets live right after the record map's kp_capacity entries
-// (the caller allocates kp_capacity + n_images * N + 1 ints).
+// The packing scratch (rec_off) holds local_off (n_images * N ints), then
+// img_tot (n_images), then img_off (n_images + 1).
 cudaError_t launch_pack(const DescribeArgs& a, cudaStream_t s) {
-  if (a.n_images * a.N <= 0) return cudaSuccess;
-  scan_kernel<<<1, kScanThreads, 0, s>>>(a, a.rec_map + a.kp_capacity);
+  if (a.n_images <= 0 || a.N <= 0) return cudaSuccess;
+  int* local_off = a.rec_off;
+  int* img_tot = local_off + (size_t)a.n_images * a.N;
+  int* img_off = img_tot + a.n_images;
+  scan_kernel<<<(a.n_images + kPackWarps - 1) / kPackWarps, kPackWarps * 32, 0, s>>>(a, local_off, img_tot,
+                                                                                     img_off);
   return cudaGetLastError();
 }
 
 cudaError_t launch_copy(const DescribeArgs& a, int n_sms, cudaStream_t s) {
-  if (a.n_images * a.N <= 0) return cudaSuccess;
-  copy_kernel<<<n_sms * 8, 256, 0, s>>>(a);
+  if (a.n_images <= 0 || a.N <= 0) return cudaSuccess;
+  const int* local_off = a.rec_off;
+  const int* img_off = local_off + (size_t)a.n_images * a.N + a.n_images;
+  const int slots = a.n_images * a.N;
+  const int grid = std::min((slots + 7) / 8, n_sms * 8);
+  copy_kernel<<<grid, 256, 0, s>>>(a, local_off, img_off);
   return cudaGetLastError();
 }
 
