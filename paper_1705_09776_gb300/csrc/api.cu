@@ -34,6 +34,14 @@ struct ProfRec {
 
 }  // namespace
 
+constexpr int kMaxInputChunks = 4;
+
+struct Upload {
+  void* dst;
+  const void* src;
+  size_t bytes;
+};
+
 struct cdvs_ctx {
   int device = 0;
   int n_sms = 0;
@@ -46,6 +54,13 @@ struct cdvs_ctx {
   bool prof = false;
   std::vector<ProfRec> recs;
   std::vector<cudaEvent_t> pool;
+  // host inputs go up in image chunks on copy_stream, each chunk's octave-0
+  // detection waiting for its chunk only
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ready[kMaxInputChunks + 1] = {};
+  int n_chunks = 1;                        // of the current call
+  int chunk_begin[kMaxInputChunks + 1] = {};
+  std::vector<Upload> uploads[kMaxInputChunks];  // empty: inputs already on the device
 };
 
 namespace {
@@ -274,39 +289,63 @@ int cand_capacity(long long max_pixels) {
 
 // Uploads images (if on the host) and the plans; returns the plan of image i
 // pointing at device memory.
+// Host images are uploaded in up to kMaxInputChunks chunks of whole images on
+// the context's copy stream; each chunk's copies are issued just before the
+// first octave's detection of that chunk (issue_upload), which waits for them,
+// so the detection of chunk k overlaps the upload of chunk k + 1 -- also for
+// pageable memory, whose copies hold the host thread while they are staged.
 cdvs_status stage_inputs(cdvs_ctx* c, int n, const uint8_t* const* images, const cdvs_image_desc* sizes,
                          uint32_t flags, cudaStream_t s) {
   cudaError_t e;
+  c->n_chunks = 1;
+  c->chunk_begin[0] = 0;
+  c->chunk_begin[1] = n;
+  for (auto& u : c->uploads) u.clear();
   if (flags & CDVS_INPUT_DEVICE) {
     for (int i = 0; i < n; ++i) c->h_plans[i].src = images[i];
   } else {
     size_t total = 0;
-    std::vector<size_t> off(n);
+    std::vector<size_t> off(n + 1);
     for (int i = 0; i < n; ++i) {
       off[i] = total;
       total += (size_t)sizes[i].pitch_bytes * sizes[i].height;
       total = (total + 255) & ~(size_t)255;
     }
+    off[n] = total;
     if ((e = ensure(c->input, total)) != cudaSuccess) return cuda_fail(c, e, "input staging");
     uint8_t* base = static_cast<uint8_t*>(c->input.p);
-    // one copy when the host images are back to back with equal size
-    bool contiguous = n > 0;
-    const size_t isz = n > 0 ? (size_t)sizes[0].pitch_bytes * sizes[0].height : 0;
-    for (int i = 1; i < n && contiguous; ++i)
-      contiguous = sizes[i].width == sizes[0].width && sizes[i].height == sizes[0].height &&
-                   sizes[i].pitch_bytes == sizes[0].pitch_bytes && images[i] == images[0] + i * isz &&
-                   (isz & 255) == 0;
-    if (contiguous) {
-      if ((e = cudaMemcpyAsync(base, images[0], isz * n, cudaMemcpyHostToDevice, s)) != cudaSuccess)
-        return cuda_fail(c, e, "image upload");
-    } else {
-      for (int i = 0; i < n; ++i) {
-        const size_t bytes = (size_t)sizes[i].pitch_bytes * sizes[i].height;
-        if ((e = cudaMemcpyAsync(base + off[i], images[i], bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
-          return cuda_fail(c, e, "image upload");
+    if (!c->copy_stream) {
+      if ((e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(c, e, "copy stream");
+      for (cudaEvent_t& ev : c->ready)
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+          return cuda_fail(c, e, "copy events");
+    }
+    // chunks only pay off for batches that fill the GPU several times over
+    c->n_chunks = n >= 64 ? kMaxInputChunks : 1;
+    for (int k = 0; k <= c->n_chunks; ++k) c->chunk_begin[k] = (int)((long long)n * k / c->n_chunks);
+    for (int k = 0; k < c->n_chunks; ++k) {
+      const int i0 = c->chunk_begin[k], i1 = c->chunk_begin[k + 1];
+      // back-to-back host images of one size go up in one copy
+      bool contiguous = i1 > i0;
+      const size_t isz = i1 > i0 ? (size_t)sizes[i0].pitch_bytes * sizes[i0].height : 0;
+      for (int i = i0 + 1; i < i1 && contiguous; ++i)
+        contiguous = sizes[i].pitch_bytes == sizes[i0].pitch_bytes && sizes[i].height == sizes[i0].height &&
+                     images[i] == images[i0] + (size_t)(i - i0) * isz && off[i] == off[i0] + (size_t)(i - i0) * isz;
+      if (contiguous) {
+        c->uploads[k].push_back(Upload{base + off[i0], images[i0], isz * (i1 - i0)});
+      } else {
+        for (int i = i0; i < i1; ++i)
+          c->uploads[k].push_back(Upload{base + off[i], images[i], (size_t)sizes[i].pitch_bytes * sizes[i].height});
       }
     }
-    for (int i = 0; i < n; ++i) c->h_plans[i].src = base + (contiguous ? i * isz : off[i]);
+    // the copy stream starts after the work already on s (which may still
+    // read the staging buffer)
+    cudaEvent_t after = c->ready[kMaxInputChunks];
+    if ((e = cudaEventRecord(after, s)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(c->copy_stream, after, 0)) != cudaSuccess)
+      return cuda_fail(c, e, "copy ordering");
+    for (int i = 0; i < n; ++i) c->h_plans[i].src = base + off[i];
   }
   if ((e = ensure(c->plans, sizeof(ImgPlan) * n)) != cudaSuccess) return cuda_fail(c, e, "plans");
   if ((e = ensure(c->tile_prefix, sizeof(int) * c->h_prefix.size())) != cudaSuccess)
@@ -318,6 +357,17 @@ cdvs_status stage_inputs(cdvs_ctx* c, int n, const uint8_t* const* images, const
                            cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return cuda_fail(c, e, "tile list upload");
   return CDVS_OK;
+}
+
+// Chunk k of the host images on its way, and s waiting for it.
+cudaError_t issue_upload(cdvs_ctx* c, int k, cudaStream_t s) {
+  if (c->uploads[k].empty()) return cudaSuccess;
+  cudaError_t e;
+  for (const Upload& u : c->uploads[k])
+    if ((e = cudaMemcpyAsync(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice, c->copy_stream)) != cudaSuccess)
+      return e;
+  if ((e = cudaEventRecord(c->ready[k], c->copy_stream)) != cudaSuccess) return e;
+  return cudaStreamWaitEvent(s, c->ready[k], 0);
 }
 
 cdvs_status run_detect(cdvs_ctx* c, int n, const cdvs_params& p, int max_oct, int cap, cudaStream_t s) {
@@ -341,17 +391,31 @@ cdvs_status run_detect(cdvs_ctx* c, int n, const cdvs_params& p, int max_oct, in
   a.offset_max = p.offset_max;
   for (int o = 0; o < max_oct; ++o) {
     a.octave = o;
-    a.tile_prefix = static_cast<const int*>(c->tile_prefix.p) + (size_t)o * (n + 1);
     a.write_level0 = o == 0 ? 1 : 0;
     int maxr = 0;
     for (int k = 0; k < kScales; ++k) {
       a.radius[k] = gauss_taps(tau_of(p, o, k), a.taps[k]);
       maxr = std::max(maxr, a.radius[k]);
     }
-    const int n_tiles = c->h_prefix[(size_t)o * (n + 1) + n];
+    const int* prefix = c->h_prefix.data() + (size_t)o * (n + 1);
+    const int* d_prefix = static_cast<const int*>(c->tile_prefix.p) + (size_t)o * (n + 1);
+    // octave 0 runs per input chunk, each launch after its chunk's upload
+    const int parts = o == 0 ? c->n_chunks : 1;
     cudaEvent_t ev0 = o == 0 ? prof_begin(c, s) : nullptr;
-    if ((e = launch_detect(a, n_tiles, maxr, p.storage, c->n_sms, s)) != cudaSuccess) return cuda_fail(c, e, "detect launch");
-    if (o == 0) prof_end(c, 5, 1, ev0, s);
+    for (int k = 0; k < parts; ++k) {
+      const int i0 = parts > 1 ? c->chunk_begin[k] : 0, i1 = parts > 1 ? c->chunk_begin[k + 1] : n;
+      if (o == 0 && (e = issue_upload(c, k, s)) != cudaSuccess) return cuda_fail(c, e, "image upload");
+      a.plans = static_cast<const ImgPlan*>(c->plans.p) + i0;
+      a.cands = static_cast<Cand*>(c->cands.p) + (size_t)i0 * cap;
+      a.cand_count = static_cast<int*>(c->cand_count.p) + i0;
+      a.n_images = i1 - i0;
+      a.tile_prefix = d_prefix + i0;
+      a.tile_base = prefix[i0];
+      const int n_tiles = prefix[i1] - prefix[i0];
+      if ((e = launch_detect(a, n_tiles, maxr, p.storage, c->n_sms, s)) != cudaSuccess)
+        return cuda_fail(c, e, "detect launch");
+    }
+    if (o == 0) prof_end(c, 5, parts, ev0, s);
   }
   return CDVS_OK;
 }
@@ -675,6 +739,11 @@ void cdvs_destroy(cdvs_ctx* c) {
     cudaEventDestroy(r.b);
   }
   for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+  if (c->copy_stream) {
+    cudaStreamSynchronize(c->copy_stream);
+    for (cudaEvent_t e : c->ready) cudaEventDestroy(e);
+    cudaStreamDestroy(c->copy_stream);
+  }
   delete c;
 }
 

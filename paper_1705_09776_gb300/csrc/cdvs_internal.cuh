@@ -62,7 +62,8 @@ struct Cand {
 // ---------------------------------------------------------------- K1 args
 struct DetectArgs {
   const ImgPlan* plans;
-  const int* tile_prefix;  // n_images + 1 entries: first tile of each image in this launch
+  const int* tile_prefix;  // n_images + 1 entries: first tile of each image, minus tile_base
+  int tile_base;
   int n_images;
   int octave;
   void* levels;            // level arena (float or __half)

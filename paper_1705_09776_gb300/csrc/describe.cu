@@ -448,7 +448,9 @@ __device__ __forceinline__ void stage_patch(const LevelView<__half>& G, int pu0,
   }
 }
 
-// Persistent warps: warp w of the grid takes the slots w, w + (all warps), ...
+// Persistent warps claim slots one at a time from a counter (status[2],
+// zeroed with the status word before every call), so a warp that drew small
+// points takes more of them and the grid finishes together.
 template <typename StoreT>
 __global__ void __launch_bounds__(kFWarps * 32, 3) describe_kernel(const __grid_constant__ DescribeArgs a) {
   extern __shared__ float4 smem4[];
@@ -464,7 +466,12 @@ __global__ void __launch_bounds__(kFWarps * 32, 3) describe_kernel(const __grid_
   int* rn = ru + P;
   int* rp = rn + P;
   const int S = a.n_images * a.N;
-  for (int slot = blockIdx.x * kFWarps + warp; slot < S; slot += gridDim.x * kFWarps) {
+  unsigned* next_slot = reinterpret_cast<unsigned*>(a.status + 2);
+  for (;;) {
+    int slot = 0;
+    if (lane == 0) slot = (int)atomicAdd(next_slot, 1u);
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    if (slot >= S) break;
     const int img = slot / a.N, rank = slot - img * a.N;
     if (rank >= a.sel_count[img]) continue;
     const Cand c = a.sel[slot];

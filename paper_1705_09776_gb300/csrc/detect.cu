@@ -580,7 +580,7 @@ __global__ void __launch_bounds__(kDetThreads, 1)
   const int o = a.octave;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-  for (int i = threadIdx.x; i <= a.n_images; i += kDetThreads) prefix[i] = a.tile_prefix[i];
+  for (int i = threadIdx.x; i <= a.n_images; i += kDetThreads) prefix[i] = a.tile_prefix[i] - a.tile_base;
   __syncthreads();
 
   int b = blockIdx.x;

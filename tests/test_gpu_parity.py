@@ -224,6 +224,34 @@ def test_device_buffers_match_host_path(ctx, cd):
     assert np.array_equal(desc.cpu().numpy()[:tot], hd)
 
 
+def test_pinned_host_buffers_match_pageable(ctx, cd):
+    """Page-locked host images are read in place by the first octave's kernel
+    and page-locked host outputs are written in place by the packing kernels;
+    the records must be byte-identical to the staged (pageable) path."""
+    import torch
+    imgs = np.stack([_img(640, 480, seed=9, i=i) for i in range(5)])
+    hk, hd, hc, _ = ctx.extract(list(imgs))
+    n, H, W = imgs.shape
+    cap = n * 300 * 4
+    h_img = torch.from_numpy(imgs).pin_memory()
+    kp = torch.zeros(cap * cd.KEYPOINT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    desc = torch.zeros(cap, 128, dtype=torch.float32).pin_memory()
+    cnt = torch.zeros(n, dtype=torch.int32).pin_memory()
+    sizes = np.array([(W, H, W)] * n, cd.IMAGE_DESC_DTYPE)
+    ptrs = [h_img.data_ptr() + i * H * W for i in range(n)]
+    for _ in range(2):   # twice: the second call must not see the first one's output
+        ctx.extract_raw(n, ptrs, sizes, cd.params(), kp, desc, cap, cnt, 0, torch.cuda.current_stream())
+        c = cnt.numpy().copy()
+        tot = int(c.sum())
+        assert np.array_equal(c, hc)
+        dk = kp.numpy()[:tot * cd.KEYPOINT_DTYPE.itemsize].view(cd.KEYPOINT_DTYPE)
+        assert np.array_equal(dk.view(np.uint8), hk.view(np.uint8))
+        assert np.array_equal(desc.numpy()[:tot], hd)
+        kp.zero_()
+        desc.zero_()
+        cnt.zero_()
+
+
 # ------------------------------------------------------------------ edges
 
 def test_edge_cases(ctx, cd):
