@@ -77,6 +77,9 @@ typedef struct {
     int32_t max_orientations;  /* orientation copies per point, 1..8 (4) */
     int32_t upright;           /* 1: theta = 0 and no orientation stage (0) */
     int32_t storage;           /* CDVS_STORAGE_FP32 or CDVS_STORAGE_FP16 level storage (FP32) */
+    int32_t use_proposal;      /* 1: the learned block proposal masks first-octave detection in
+                                  cdvs_extract and cdvs_candidates (0; needs cdvs_set_proposal) */
+    float proposal_threshold;  /* a 16x16 block is proposed when its probability exceeds this (0.5) */
 } cdvs_params;
 
 typedef struct {
@@ -264,6 +267,59 @@ cdvs_status cdvs_dedupe_select_noalloc(const cdvs_keypoint *cand, int32_t n_cand
                                        int32_t height, const cdvs_params *params,
                                        cdvs_keypoint *sel_out, int32_t *sel_count,
                                        void *cuda_stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned block proposal.  Not in the paper: an extension of its detector
+ * (Sec. IV-A, Alg. 1) that predicts, from the 8-bit image, which 16x16 blocks
+ * hold interest points, so that the first octave's detection runs only near
+ * them.  The network (CDVS_PROPOSAL_PARAMS FP32 parameters, in this order:
+ * W1[16][1][3][3], b1[16], W2[16][16][3][3], b2[16], W3[16][16][3][3], b3[16],
+ * Wh[16], bh):
+ *   x  = (u8 - 128) / 64
+ *   A1 = relu(conv3x3(x,  W1, stride 2, pad 1) + b1)   (BF16)
+ *   A2 = relu(conv3x3(A1, W2, stride 2, pad 1) + b2)   (BF16)
+ *   A3 = relu(conv3x3(A2, W3, stride 1, pad 1) + b3)
+ *   logit(block) = Wh . mean over the block's 4x4 cell of A3 + bh
+ * conv3x3 is cross-correlation; weights are used in BF16, biases and every
+ * sum in FP32.  An image of W x H has ceil(W/16) x ceil(H/16) blocks.
+ *
+ * With params->use_proposal = 1, cdvs_extract and cdvs_candidates first run
+ * the network, then treat each first-octave detection tile (128 x 32 px) in
+ * one of three ways: tiles within one block of a proposed block (probability
+ * > params->proposal_threshold) run the whole detector; tiles whose levels a
+ * descriptor disc may read store every level without detecting; the rest only
+ * build level 3, which the next octave is decimated from.  Later octaves run
+ * in full.
+ * ------------------------------------------------------------------------- */
+#define CDVS_PROPOSAL_PARAMS 4817
+
+/* Copies the network's parameters (host memory, CDVS_PROPOSAL_PARAMS floats)
+ * into the context.  INVALID_ARGUMENT when n_params differs. */
+cdvs_status cdvs_set_proposal(cdvs_ctx *ctx, const float *params, int32_t n_params);
+
+/* The network's logits for a batch: image i's ceil(W/16) x ceil(H/16) logits,
+ * row-major, follow those of images 0..i-1 in logits_out (capacity floats;
+ * UNSUPPORTED_SIZE when too small).  Images as in cdvs_extract (flags
+ * CDVS_INPUT_DEVICE, CDVS_OUTPUT_DEVICE: logits_out in device memory).
+ * Synchronous unless both flags are set. */
+cdvs_status cdvs_proposal_logits(cdvs_ctx *ctx, int32_t n_images, const uint8_t *const *images,
+                                 const cdvs_image_desc *sizes, float *logits_out, int32_t capacity,
+                                 uint32_t flags, void *cuda_stream);
+
+/* One training step of the network on the GPU, every pointer DEVICE memory.
+ * images: n_images images of width x height, row pitch `pitch` bytes, back to
+ * back.  labels: per block 0 or 1 (same order as the logits), or NULL for a
+ * forward pass only.  params: CDVS_PROPOSAL_PARAMS FP32, updated in place by
+ * Adam (beta 0.9, 0.999, eps 1e-8, bias correction with `step` >= 1) when
+ * lr > 0.  adam_m, adam_v: Adam moments (caller-owned, zero before step 1).
+ * grad (CDVS_PROPOSAL_PARAMS) receives the gradient of the mean BCE over all
+ * blocks, loss (1 float, may be NULL) the loss, logits (may be NULL) the
+ * logits.  bf16 = 1 rounds weights and A1, A2 to BF16 as the inference does;
+ * 0 keeps FP32 (gradient checks).  Asynchronous on cuda_stream. */
+cdvs_status cdvs_proposal_train_step(cdvs_ctx *ctx, const uint8_t *images, int32_t n_images, int32_t width,
+                                     int32_t height, int32_t pitch, const float *labels, float *params,
+                                     float *adam_m, float *adam_v, float *grad, float *loss, float *logits,
+                                     int32_t step, float lr, int32_t bf16, void *cuda_stream);
 
 #ifdef __cplusplus
 }

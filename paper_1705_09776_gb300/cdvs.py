@@ -36,6 +36,7 @@ PARAMS_DTYPE = np.dtype([
     ("ori_weight_sigma", "<f4"), ("desc_radius", "<f4"), ("cell_side", "<f4"),
     ("desc_weight_sigma", "<f4"), ("dedupe_dlog2", "<f4"),
     ("max_keypoints", "<i4"), ("max_orientations", "<i4"), ("upright", "<i4"), ("storage", "<i4"),
+    ("use_proposal", "<i4"), ("proposal_threshold", "<f4"),
 ])
 KEYPOINT_DTYPE = np.dtype([
     ("x", "<f4"), ("y", "<f4"), ("sigma", "<f4"), ("theta", "<f4"), ("response", "<f4"),
@@ -43,12 +44,14 @@ KEYPOINT_DTYPE = np.dtype([
     ("reserved", "<i2"), ("image", "<i4"), ("parent_id", "<i4"),
 ])
 IMAGE_DESC_DTYPE = np.dtype([("width", "<i4"), ("height", "<i4"), ("pitch_bytes", "<i4")])
-assert PARAMS_DTYPE.itemsize == 72 and KEYPOINT_DTYPE.itemsize == 44
+assert PARAMS_DTYPE.itemsize == 80 and KEYPOINT_DTYPE.itemsize == 44
+PROPOSAL_PARAMS = 4817
 
 EXPORTED = ["cdvs_params_default", "cdvs_create", "cdvs_destroy", "cdvs_last_error", "cdvs_extract",
             "cdvs_candidates", "cdvs_dedupe_select", "cdvs_describe", "cdvs_scale_space",
             "cdvs_rank_host", "cdvs_transform_ternary", "cdvs_profile", "cdvs_profile_read",
-            "cdvs_dedupe_select_noalloc"]
+            "cdvs_dedupe_select_noalloc", "cdvs_set_proposal", "cdvs_proposal_logits",
+            "cdvs_proposal_train_step"]
 STAGES = ["detect", "select", "describe", "offsets", "pack", "detect_octave0"]
 
 
@@ -87,6 +90,9 @@ def load(build_if_missing: bool = True):
         "cdvs_profile": (i32, [P, i32]),
         "cdvs_profile_read": (i32, [P, P, P, i32, i32]),
         "cdvs_dedupe_select_noalloc": (i32, [P, i32, i32, i32, P, P, P, P]),
+        "cdvs_set_proposal": (i32, [P, P, i32]),
+        "cdvs_proposal_logits": (i32, [P, i32, P, P, P, i32, u32, P]),
+        "cdvs_proposal_train_step": (i32, [P, P, i32, i32, i32, i32, P, P, P, P, P, P, P, i32, C.c_float, i32, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -151,6 +157,36 @@ class Context:
         if st == CDVS_OK or (allow_truncated and st == CDVS_CAPACITY_TRUNCATED):
             return st
         raise CdvsError(st, self.last_error())
+
+    # ------------------------------------------------------------ proposal
+    def set_proposal(self, theta):
+        """Network parameters (PROPOSAL_PARAMS floats) for use_proposal = 1."""
+        t = np.ascontiguousarray(theta, np.float32)
+        self._check(self._L.cdvs_set_proposal(self.handle, t.ctypes.data, int(t.size)))
+
+    def proposal_logits(self, images):
+        """Logits of the 16x16 blocks of each image: a list of (ceil(H/16), ceil(W/16)) arrays."""
+        imgs, sizes, ptrs = self._host_images(images)
+        shapes = [(-(-a.shape[0] // 16), -(-a.shape[1] // 16)) for a in imgs]
+        out = np.zeros(sum(h * w for h, w in shapes), np.float32)
+        self._check(self._L.cdvs_proposal_logits(self.handle, len(imgs), C.cast(ptrs, C.c_void_p), sizes.ctypes.data,
+                                                 out.ctypes.data, out.size, 0, None))
+        res, o = [], 0
+        for h, w in shapes:
+            res.append(out[o:o + h * w].reshape(h, w))
+            o += h * w
+        return res
+
+    def proposal_train_step(self, images, labels, theta, adam_m, adam_v, grad, loss=None, logits=None,
+                            step=1, lr=0.0, bf16=True, stream=None):
+        """One training step on device tensors: images (B, H, W) uint8, labels
+        (B, ceil(H/16), ceil(W/16)) float32 or None; theta, adam_m, adam_v,
+        grad: PROPOSAL_PARAMS float32; loss: 1 float32; logits like labels."""
+        B, H, W = images.shape
+        st = self._L.cdvs_proposal_train_step(self.handle, _ptr(images), B, W, H, W, _ptr(labels), _ptr(theta),
+                                              _ptr(adam_m), _ptr(adam_v), _ptr(grad), _ptr(loss), _ptr(logits),
+                                              int(step), float(lr), 1 if bf16 else 0, _stream_handle(stream))
+        return self._check(st)
 
     # ------------------------------------------------------------ measurement
     def profile(self, enable: bool):

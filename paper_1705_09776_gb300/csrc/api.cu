@@ -48,6 +48,9 @@ struct cdvs_ctx {
   std::string err;
   DevBuf levels, cands, cand_count, order, keep, sel, sel_count, ori_theta, ori_count, rec_off,
       rec_total, out_kp, out_desc, out_count, plans, tile_prefix, status, input, dump, stage_kp, stage_desc;
+  // learned block proposal: parameters, per-call image table, logits, tile modes, training workspace
+  DevBuf prop_theta, prop_imgs, prop_logits, prop_mode, prop_ws;
+  bool prop_set = false;
   HostBuf small;  // pinned: status word + record total
   std::vector<ImgPlan> h_plans;
   std::vector<int> h_prefix;
@@ -224,6 +227,9 @@ cdvs_status check_params(cdvs_ctx* c, const cdvs_params* p) {
     return fail(c, CDVS_INVALID_ARGUMENT, "max_orientations must be in 1..8");
   if (p->storage != CDVS_STORAGE_FP32 && p->storage != CDVS_STORAGE_FP16)
     return fail(c, CDVS_INVALID_ARGUMENT, "storage must be CDVS_STORAGE_FP32 or CDVS_STORAGE_FP16");
+  if (p->use_proposal != 0 && p->use_proposal != 1) return fail(c, CDVS_INVALID_ARGUMENT, "use_proposal must be 0 or 1");
+  if (p->use_proposal && !(p->proposal_threshold > 0.0f && p->proposal_threshold < 1.0f))
+    return fail(c, CDVS_INVALID_ARGUMENT, "proposal_threshold must be in (0, 1)");
   float t[kMaxRadius + 1];
   for (int o = 0; o < 2; ++o)
     for (int k = 0; k < kScales; ++k)
@@ -370,7 +376,8 @@ cudaError_t issue_upload(cdvs_ctx* c, int k, cudaStream_t s) {
   return cudaStreamWaitEvent(s, c->ready[k], 0);
 }
 
-cdvs_status run_detect(cdvs_ctx* c, int n, const cdvs_params& p, int max_oct, int cap, cudaStream_t s) {
+cdvs_status run_detect(cdvs_ctx* c, int n, const cdvs_params& p, int max_oct, int cap, cudaStream_t s,
+                       const uint8_t* tile_mode = nullptr) {
   cudaError_t e;
   DetectArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -392,6 +399,7 @@ cdvs_status run_detect(cdvs_ctx* c, int n, const cdvs_params& p, int max_oct, in
   for (int o = 0; o < max_oct; ++o) {
     a.octave = o;
     a.write_level0 = o == 0 ? 1 : 0;
+    a.tile_mode = o == 0 ? tile_mode : nullptr;
     int maxr = 0;
     for (int k = 0; k < kScales; ++k) {
       a.radius[k] = gauss_taps(tau_of(p, o, k), a.taps[k]);
@@ -477,6 +485,70 @@ struct PointsIn {
 };
 
 // The shared pipeline behind cdvs_extract / cdvs_candidates / cdvs_describe.
+// The proposal network's per-image table (sizes of every layer, first logit)
+// for images whose device pixels are srcs[i]; returns the number of logits.
+size_t prop_table(int n, const cdvs_image_desc* sizes, const uint8_t* const* srcs, std::vector<PropImage>& t,
+                  int& max_th, int& max_tw) {
+  t.resize(n);
+  size_t off = 0;
+  max_th = max_tw = 0;
+  for (int i = 0; i < n; ++i) {
+    PropImage& q = t[i];
+    q.src = srcs[i];
+    q.W = sizes[i].width;
+    q.H = sizes[i].height;
+    q.pitch = sizes[i].pitch_bytes;
+    q.H1 = (q.H + 1) / 2;
+    q.W1 = (q.W + 1) / 2;
+    q.H2 = (q.H1 + 1) / 2;
+    q.W2 = (q.W1 + 1) / 2;
+    q.Th = (q.H + 15) / 16;
+    q.Tw = (q.W + 15) / 16;
+    q.logit_off = (int)off;
+    off += (size_t)q.Th * q.Tw;
+    max_th = std::max(max_th, q.Th);
+    max_tw = std::max(max_tw, q.Tw);
+  }
+  return off;
+}
+
+// Block proposal for the batch already staged on the device (h_plans[i].src):
+// logits, then the first octave's tile modes in c->prop_mode.
+cdvs_status run_proposal_mask(cdvs_ctx* c, int n, const cdvs_image_desc* sizes, const cdvs_params& p,
+                              cudaStream_t s) {
+  if (!c->prop_set) return fail(c, CDVS_INVALID_ARGUMENT, "use_proposal set but no cdvs_set_proposal call");
+  std::vector<const uint8_t*> srcs(n);
+  for (int i = 0; i < n; ++i) srcs[i] = c->h_plans[i].src;
+  std::vector<PropImage> t;
+  int max_th, max_tw;
+  const size_t n_logits = prop_table(n, sizes, srcs.data(), t, max_th, max_tw);
+  const int n_tiles = c->h_prefix[n];
+  int max_tiles = 0;
+  for (int i = 0; i < n; ++i) max_tiles = std::max(max_tiles, c->h_plans[i].oct[0].tiles_x * c->h_plans[i].oct[0].tiles_y);
+  cudaError_t e;
+  if ((e = ensure(c->prop_imgs, sizeof(PropImage) * n)) != cudaSuccess ||
+      (e = ensure(c->prop_logits, sizeof(float) * n_logits)) != cudaSuccess ||
+      (e = ensure(c->prop_mode, (size_t)n_tiles)) != cudaSuccess)
+    return cuda_fail(c, e, "proposal workspace");
+  if ((e = cudaMemcpyAsync(c->prop_imgs.p, t.data(), sizeof(PropImage) * n, cudaMemcpyHostToDevice, s)) !=
+      cudaSuccess)
+    return cuda_fail(c, e, "proposal table upload");
+  const PropImage* d_t = static_cast<const PropImage*>(c->prop_imgs.p);
+  if ((e = launch_proposal_infer(d_t, n, max_th, max_tw, static_cast<const float*>(c->prop_theta.p),
+                                 static_cast<float*>(c->prop_logits.p), s)) != cudaSuccess)
+    return cuda_fail(c, e, "proposal launch");
+  // a descriptor disc of a first-octave point reaches this far (image px)
+  const double reach = std::max(p.desc_radius, p.ori_radius) * 2.0 * p.sigma0 * 1.001 + 2.0;
+  const int ny = (int)std::ceil(reach / kTY), nx = (int)std::ceil(reach / kTX);
+  const double thr = p.proposal_threshold;
+  const float zt = (float)std::log(thr / (1.0 - thr));
+  if ((e = launch_tile_mode(d_t, static_cast<const ImgPlan*>(c->plans.p), static_cast<const int*>(c->tile_prefix.p),
+                            n, max_tiles, static_cast<const float*>(c->prop_logits.p), zt, 1, ny, nx,
+                            static_cast<uint8_t*>(c->prop_mode.p), s)) != cudaSuccess)
+    return cuda_fail(c, e, "tile mode launch");
+  return CDVS_OK;
+}
+
 cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, const cdvs_image_desc* sizes,
                 const cdvs_params* params, const PointsIn* pin, cdvs_keypoint* kp_out, float* desc_out,
                 int32_t capacity, int32_t* kp_count, uint32_t flags, cudaStream_t s) {
@@ -528,7 +600,18 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
       (e = cudaMemsetAsync(c->status.p, 0, sizeof(int) * 4, s)) != cudaSuccess)
     return cuda_fail(c, e, "memset");
   cudaEvent_t ev = prof_begin(c, s);
-  if ((st = run_detect(c, n, p, max_oct, cap, s)) != CDVS_OK) return st;
+  const uint8_t* tile_mode = nullptr;
+  if (p.use_proposal && (mode == kExtract || mode == kCandidates)) {
+    // the network reads the whole batch: every upload first, in one piece
+    for (int k = 0; k < c->n_chunks; ++k)
+      if ((e = issue_upload(c, k, s)) != cudaSuccess) return cuda_fail(c, e, "image upload");
+    for (auto& u : c->uploads) u.clear();
+    c->n_chunks = 1;
+    c->chunk_begin[1] = n;
+    if ((st = run_proposal_mask(c, n, sizes, p, s)) != CDVS_OK) return st;
+    tile_mode = static_cast<const uint8_t*>(c->prop_mode.p);
+  }
+  if ((st = run_detect(c, n, p, max_oct, cap, s, tile_mode)) != CDVS_OK) return st;
   prof_end(c, 0, max_oct, ev, s);
   int* h_small = static_cast<int*>(c->small.p);
 
@@ -701,6 +784,8 @@ void cdvs_params_default(cdvs_params* p) {
   p->max_orientations = 4;
   p->upright = 0;
   p->storage = CDVS_STORAGE_FP32;
+  p->use_proposal = 0;
+  p->proposal_threshold = 0.5f;
 }
 
 cdvs_status cdvs_create(cdvs_ctx** out, int device, size_t workspace_bytes_hint) {
@@ -730,7 +815,8 @@ void cdvs_destroy(cdvs_ctx* c) {
   DevBuf* bufs[] = {&c->levels,  &c->cands,   &c->cand_count, &c->order,   &c->keep,
                     &c->sel,     &c->sel_count, &c->ori_theta, &c->ori_count, &c->rec_off,
                     &c->rec_total, &c->out_kp, &c->out_desc, &c->out_count, &c->plans,
-                    &c->tile_prefix, &c->status, &c->input, &c->dump, &c->stage_kp, &c->stage_desc};
+                    &c->tile_prefix, &c->status, &c->input, &c->dump, &c->stage_kp, &c->stage_desc,
+                    &c->prop_theta, &c->prop_imgs, &c->prop_logits, &c->prop_mode, &c->prop_ws};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (c->small.p) cudaFreeHost(c->small.p);
@@ -928,6 +1014,109 @@ cdvs_status cdvs_scale_space(cdvs_ctx* c, const uint8_t* image, const cdvs_image
 cdvs_status cdvs_profile(cdvs_ctx* c, int32_t enable) {
   if (!c) return CDVS_INVALID_ARGUMENT;
   c->prof = enable != 0;
+  return CDVS_OK;
+}
+
+cdvs_status cdvs_set_proposal(cdvs_ctx* c, const float* params, int32_t n_params) {
+  if (!c) return CDVS_INVALID_ARGUMENT;
+  if (!params || n_params != kPropParams) return fail(c, CDVS_INVALID_ARGUMENT, "need CDVS_PROPOSAL_PARAMS floats");
+  cudaError_t e;
+  if ((e = cudaSetDevice(c->device)) != cudaSuccess || (e = ensure(c->prop_theta, sizeof(float) * kPropParams)) != cudaSuccess ||
+      (e = cudaMemcpy(c->prop_theta.p, params, sizeof(float) * kPropParams, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_fail(c, e, "proposal parameters");
+  c->prop_set = true;
+  return CDVS_OK;
+}
+
+cdvs_status cdvs_proposal_logits(cdvs_ctx* c, int32_t n, const uint8_t* const* images, const cdvs_image_desc* sizes,
+                                 float* logits_out, int32_t capacity, uint32_t flags, void* cuda_stream) {
+  if (!c) return CDVS_INVALID_ARGUMENT;
+  if (!c->prop_set) return fail(c, CDVS_INVALID_ARGUMENT, "no cdvs_set_proposal call");
+  if (n < 0 || n > kMaxBatch) return fail(c, CDVS_INVALID_ARGUMENT, "n_images must be in 0..4096");
+  if (n == 0) return CDVS_OK;
+  if (!images || !sizes || !logits_out || capacity < 0) return fail(c, CDVS_INVALID_ARGUMENT, "NULL argument");
+  for (int i = 0; i < n; ++i) {
+    if (!images[i]) return fail(c, CDVS_INVALID_ARGUMENT, "image pointer is NULL");
+    if (sizes[i].width < 16 || sizes[i].height < 16 || sizes[i].width > 32768 || sizes[i].height > 32768 ||
+        sizes[i].pitch_bytes < sizes[i].width)
+      return fail(c, CDVS_UNSUPPORTED_SIZE, "image sizes must be 16..32768 with pitch >= width");
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e;
+  if ((e = cudaSetDevice(c->device)) != cudaSuccess) return cuda_fail(c, e, "device");
+  std::vector<const uint8_t*> srcs(images, images + n);
+  if (!(flags & CDVS_INPUT_DEVICE)) {
+    size_t total = 0;
+    std::vector<size_t> off(n);
+    for (int i = 0; i < n; ++i) {
+      off[i] = total;
+      total += ((size_t)sizes[i].pitch_bytes * sizes[i].height + 255) & ~(size_t)255;
+    }
+    if ((e = ensure(c->input, total)) != cudaSuccess) return cuda_fail(c, e, "input staging");
+    for (int i = 0; i < n; ++i) {
+      uint8_t* dst = static_cast<uint8_t*>(c->input.p) + off[i];
+      if ((e = cudaMemcpyAsync(dst, images[i], (size_t)sizes[i].pitch_bytes * sizes[i].height,
+                               cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_fail(c, e, "image upload");
+      srcs[i] = dst;
+    }
+  }
+  std::vector<PropImage> t;
+  int max_th, max_tw;
+  const size_t n_logits = prop_table(n, sizes, srcs.data(), t, max_th, max_tw);
+  if (n_logits > (size_t)capacity) return fail(c, CDVS_UNSUPPORTED_SIZE, "logits_out too small");
+  const bool dev_out = (flags & CDVS_OUTPUT_DEVICE) != 0;
+  if ((e = ensure(c->prop_imgs, sizeof(PropImage) * n)) != cudaSuccess ||
+      (!dev_out && (e = ensure(c->prop_logits, sizeof(float) * n_logits)) != cudaSuccess) ||
+      (e = cudaMemcpyAsync(c->prop_imgs.p, t.data(), sizeof(PropImage) * n, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_fail(c, e, "proposal workspace");
+  float* out = dev_out ? logits_out : static_cast<float*>(c->prop_logits.p);
+  if ((e = launch_proposal_infer(static_cast<const PropImage*>(c->prop_imgs.p), n, max_th, max_tw,
+                                 static_cast<const float*>(c->prop_theta.p), out, s)) != cudaSuccess)
+    return cuda_fail(c, e, "proposal launch");
+  if (!dev_out && ((e = cudaMemcpyAsync(logits_out, out, sizeof(float) * n_logits, cudaMemcpyDeviceToHost, s)) !=
+                       cudaSuccess ||
+                   (e = cudaStreamSynchronize(s)) != cudaSuccess))
+    return cuda_fail(c, e, "logits readback");
+  if ((flags & CDVS_INPUT_DEVICE) == 0 && dev_out && (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return cuda_fail(c, e, "proposal");
+  return CDVS_OK;
+}
+
+cdvs_status cdvs_proposal_train_step(cdvs_ctx* c, const uint8_t* images, int32_t n, int32_t width, int32_t height,
+                                     int32_t pitch, const float* labels, float* params, float* adam_m, float* adam_v,
+                                     float* grad, float* loss, float* logits, int32_t step, float lr, int32_t bf16,
+                                     void* cuda_stream) {
+  if (!c) return CDVS_INVALID_ARGUMENT;
+  if (!images || !params || !grad || n < 1 || width < 16 || height < 16 || pitch < width || (bf16 != 0 && bf16 != 1))
+    return fail(c, CDVS_INVALID_ARGUMENT, "bad training arguments");
+  if (lr > 0.0f && (!adam_m || !adam_v || step < 1 || !labels))
+    return fail(c, CDVS_INVALID_ARGUMENT, "an update needs labels, Adam moments and step >= 1");
+  if ((size_t)n * ((height + 15) / 16) * ((width + 15) / 16) > (size_t)1 << 30 || (size_t)n * height * width > (size_t)1 << 31)
+    return fail(c, CDVS_UNSUPPORTED_SIZE, "training batch too large");
+  cudaError_t e;
+  if ((e = cudaSetDevice(c->device)) != cudaSuccess) return cuda_fail(c, e, "device");
+  const size_t nf = proposal_train_floats(n, height, width, c->n_sms);
+  if ((e = ensure(c->prop_ws, sizeof(float) * nf)) != cudaSuccess) return cuda_fail(c, e, "training workspace");
+  PropTrainArgs t;
+  t.images = images;
+  t.B = n;
+  t.H = height;
+  t.W = width;
+  t.pitch = pitch;
+  t.labels = labels;
+  t.theta = params;
+  t.adam_m = adam_m;
+  t.adam_v = adam_v;
+  t.grad = grad;
+  t.loss = loss;
+  t.logits_out = logits;
+  t.step = step;
+  t.lr = lr;
+  t.bf16 = bf16;
+  if ((e = run_proposal_train(t, static_cast<float*>(c->prop_ws.p), c->n_sms, static_cast<cudaStream_t>(cuda_stream))) !=
+      cudaSuccess)
+    return cuda_fail(c, e, "training step");
   return CDVS_OK;
 }
 

@@ -81,7 +81,13 @@ struct DetectArgs {
   float edge_lim;                        // (r+1)^2 / r
   float offset_max;
   int write_level0;                      // 1 at octave 0 (level 0 is filtered, not the base)
+  const uint8_t* tile_mode;              // per tile of the batch (index tile_base + b), or null: all detect
 };
+
+// What K1 does with a tile when a block proposal masks the first octave
+constexpr uint8_t kModeLevel3 = 0;  // level 3 and the next octave's base only
+constexpr uint8_t kModeLevels = 1;  // every level stored (description may read them), no detection
+constexpr uint8_t kModeDetect = 2;  // the whole of Alg. 1 on the tile
 
 // ---------------------------------------------------------------- K3/K10 args
 struct SelectArgs {
@@ -137,5 +143,40 @@ cudaError_t launch_copy(const DescribeArgs& a, int n_sms, cudaStream_t s);
 cudaError_t launch_levels_to_f32(const ImgPlan* plans, int img, const void* levels, int storage,
                                  int octave, int k, int W, int H, long long off, int lpitch,
                                  float* out, cudaStream_t s);
+
+// ---------------------------------------------------------------- proposal
+constexpr int kPropParams = 4817;  // W1 144, b1 16, W2 2304, b2 16, W3 2304, b3 16, Wh 16, bh 1
+
+struct PropImage {
+  const uint8_t* src;
+  int W, H, pitch;
+  int H1, W1, H2, W2;  // conv1 and conv2/conv3 output sizes
+  int Th, Tw;          // 16x16 blocks
+  int logit_off;       // first logit of the image
+};
+
+struct PropTrainArgs {
+  const uint8_t* images;  // B images of H x W, row pitch `pitch`, back to back
+  int B, H, W, pitch;
+  const float* labels;    // B x Th x Tw in {0, 1}, or null: forward only
+  float* theta;           // kPropParams FP32 (updated when lr > 0)
+  float* adam_m;
+  float* adam_v;
+  float* grad;            // kPropParams
+  float* loss;            // mean BCE (1 float), may be null
+  float* logits_out;      // B x Th x Tw, may be null
+  int step;               // Adam step (from 1)
+  float lr;               // 0: no update
+  int bf16;               // 1: BF16 weights and A1/A2, as in inference
+};
+
+size_t proposal_infer_smem();
+cudaError_t launch_proposal_infer(const PropImage* d_imgs, int n_images, int max_th, int max_tw, const float* theta,
+                                  float* logits, cudaStream_t s);
+cudaError_t launch_tile_mode(const PropImage* d_imgs, const ImgPlan* plans, const int* tile_prefix, int n_images,
+                             int max_tiles, const float* logits, float zt, int dil, int ny, int nx, uint8_t* mode,
+                             cudaStream_t s);
+size_t proposal_train_floats(int B, int H, int W, int n_sms);
+cudaError_t run_proposal_train(const PropTrainArgs& t, float* ws, int n_sms, cudaStream_t s);
 
 }  // namespace cdvs

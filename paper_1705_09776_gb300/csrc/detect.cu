@@ -616,24 +616,35 @@ __global__ void __launch_bounds__(kDetThreads, 1)
     StoreT* lev = reinterpret_cast<StoreT*>(a.levels) + cur.level_off;
     const size_t lstride = (size_t)lpitch * H;
 
+    // what a block proposal leaves to do on this tile (uniform over the CTA):
+    // everything, the levels only, or level 3 and the next octave's base
+    const int mode = a.tile_mode ? a.tile_mode[a.tile_base + b] : kModeDetect;
+    const int k0 = mode == kModeLevel3 ? kScales - 1 : 0;
+
     // ---- levels: the y pass of level k+1 shares a phase with the stores and
     // the Laplacian of level k
-    vpass_dispatch<ic>(a.radius[0], a.taps[0], in, rm, tmp);
+    vpass_dispatch<ic>(a.radius[k0], a.taps[k0], in, rm, tmp);
     __syncthreads();
-    hpass_dispatch<ic>(a.radius[0], a.taps[0], tmp, gs);
+    hpass_dispatch<ic>(a.radius[k0], a.taps[k0], tmp, gs);
     __syncthreads();
-    for (int k = 0; k < kScales; ++k) {
+    for (int k = k0; k < kScales; ++k) {
       replicate_borders(gs, W, H, tx0, ty0);
       if (k > 0 || a.write_level0) store_level<StoreT>(gs, lev + k * lstride, lpitch, W, H, tx0, ty0);
       if (k == kScales - 1 && dec_off >= 0)
         store_decimated<StoreT>(gs, reinterpret_cast<StoreT*>(a.levels) + dec_off, dec_pitch, W, H, tx0, ty0);
-      laplacian(gs, a.s2[k], Ls + (size_t)k * kRP * kLC * 2);
+      if (mode == kModeDetect) laplacian(gs, a.s2[k], Ls + (size_t)k * kRP * kLC * 2);
       if (k + 1 < kScales) vpass_dispatch<ic>(a.radius[k + 1], a.taps[k + 1], in, rm, tmp);
       __syncthreads();
       if (k + 1 < kScales) {
         hpass_dispatch<ic>(a.radius[k + 1], a.taps[k + 1], tmp, gs);
         __syncthreads();
       }
+    }
+
+    if (mode != kModeDetect) {
+      if (warp == kWarps - 1 && lane == 0) tile_info<InT>(a, prefix, b + 2 * gridDim.x, n_tiles, ic, after);
+      __syncthreads();  // gs and `in` are rewritten by the next tile
+      continue;
     }
 
     // ---- phase 1, per pixel pair (tile rows 2m, 2m+1 are L row pair m + 1):

@@ -1,0 +1,634 @@
+// proposal.cu -- the learned block proposal: a small CNN that gives one logit
+// per 16x16 block of an 8-bit image, trained on blocks that hold interest
+// points of the plain detector (ALP, Sec. IV-A), so that detection can skip
+// blocks where none is likely.
+//
+//   x  = (u8 - 128) / 64
+//   A1 = relu(conv3x3(x,  W1, stride 2) + b1)      16 ch, BF16
+//   A2 = relu(conv3x3(A1, W2, stride 2) + b2)      16 ch, BF16
+//   A3 = relu(conv3x3(A2, W3, stride 1) + b3)      16 ch, FP32
+//   z  = Wh . mean_4x4(A3) + bh                    one logit per 16x16 block
+//
+// (padding 1 everywhere; weights used in BF16, biases and every accumulation
+// in FP32).  Two implementations of the forward pass:
+//  * training kernels, one per layer, on the FP32 pipes with the BF16
+//    roundings applied where the network stores BF16 (bf16 = 0 turns them
+//    off for gradient checks), followed by the backward kernels, the BCE
+//    loss and Adam; every reduction runs in a fixed order, so a training
+//    step is deterministic;
+//  * the fused inference kernel: one CTA per 8x4 blocks keeps the input,
+//    A1 and A2 of its region in shared memory; conv2 and conv3 are 9
+//    contractions (one per tap) of K = 16 input channels on the tensor cores
+//    (mma.sync m16n8k16 BF16 -> FP32), and each conv3 row tile of 16
+//    positions is exactly one 4x4 pooling cell, so the pooling is a warp
+//    reduction.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "cdvs_internal.cuh"
+
+namespace cdvs {
+namespace {
+
+constexpr int kC = 16;
+constexpr int kOffW1 = 0, kOffB1 = 144, kOffW2 = 160, kOffB2 = 2464, kOffW3 = 2480, kOffB3 = 4784,
+              kOffWh = 4800, kOffBh = 4816;
+static_assert(kOffBh + 1 == kPropParams, "parameter layout");
+
+__device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+__device__ __forceinline__ float wq(const float* theta, int i, int bf16) { return bf16 ? bf16r(theta[i]) : theta[i]; }
+
+// ------------------------------------------------------------------ training
+// Activations are planar FP32 tensors [B][16][H][W] (A1, A2 hold BF16 values
+// in bf16 mode).  A > 0 exactly where the pre-activation was > 0, so the
+// ReLU masks of the backward pass come from the stored activations.
+
+struct U8Input {  // the network input x = (u8 - 128) / 64, zero outside
+  const uint8_t* img;
+  int pitch;
+  size_t stride;  // bytes between images
+  int H, W;
+  __device__ __forceinline__ float operator()(int b, int ci, int y, int x) const {
+    (void)ci;
+    if (y < 0 || y >= H || x < 0 || x >= W) return 0.0f;
+    return ((float)img[(size_t)b * stride + (size_t)y * pitch + x] - 128.0f) * (1.0f / 64.0f);
+  }
+};
+
+struct F32Input {  // planar [B][C][H][W], zero outside
+  const float* a;
+  int C, H, W;
+  __device__ __forceinline__ float operator()(int b, int ci, int y, int x) const {
+    if (y < 0 || y >= H || x < 0 || x >= W) return 0.0f;
+    return a[(((size_t)b * C + ci) * H + y) * W + x];
+  }
+};
+
+// Forward of one 3x3 layer with CIN inputs and 16 outputs, stride S: one
+// thread per output pixel, all 16 channels.  round_out: BF16 activations.
+template <int CIN, int S, typename In>
+__global__ void __launch_bounds__(256) conv_fwd_kernel(In in, const float* theta, int w_off, int b_off, int bf16,
+                                                       int round_out, float* out, int B, int Ho, int Wo) {
+  __shared__ float w[kC * CIN * 9];
+  __shared__ float bias[kC];
+  for (int i = threadIdx.x; i < kC * CIN * 9; i += blockDim.x) w[i] = wq(theta, w_off + i, bf16);
+  if (threadIdx.x < kC) bias[threadIdx.x] = theta[b_off + threadIdx.x];
+  __syncthreads();
+  const long long n = (long long)B * Ho * Wo;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(idx / ((long long)Ho * Wo));
+    const int r = (int)(idx - (long long)b * Ho * Wo);
+    const int y = r / Wo, x = r - (r / Wo) * Wo;
+    float acc[kC];
+#pragma unroll
+    for (int co = 0; co < kC; ++co) acc[co] = bias[co];
+    for (int ci = 0; ci < CIN; ++ci)
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        const float v = in(b, ci, S * y + k / 3 - 1, S * x + k % 3 - 1);
+#pragma unroll
+        for (int co = 0; co < kC; ++co) acc[co] = fmaf(w[(co * CIN + ci) * 9 + k], v, acc[co]);
+      }
+#pragma unroll
+    for (int co = 0; co < kC; ++co) {
+      float a = fmaxf(acc[co], 0.0f);
+      if (round_out) a = bf16r(a);
+      out[(((size_t)b * kC + co) * Ho + y) * Wo + x] = a;
+    }
+  }
+}
+
+// Pooling, head and loss, one thread per block: P (kept for the head
+// gradient), the logit z, dL/dz = (sigmoid(z) - y) / n_blocks and the
+// block's loss softplus(z) - y z; per-CTA loss sums in a fixed tree order.
+__global__ void __launch_bounds__(256) pool_head_kernel(const float* a3, int B, int H2, int W2, int Th, int Tw,
+                                                        const float* theta, int bf16, const float* labels,
+                                                        float* P, float* z_out, float* dz, float* loss_part) {
+  __shared__ float red[256];
+  const int n = B * Th * Tw;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  float l = 0.0f;
+  if (i < n) {
+    const int b = i / (Th * Tw), t = i - b * Th * Tw, ty = t / Tw, tx = t - (t / Tw) * Tw;
+    const int y0 = 4 * ty, x0 = 4 * tx, y1 = min(y0 + 4, H2), x1 = min(x0 + 4, W2);
+    const int cnt = max(y1 - y0, 0) * max(x1 - x0, 0);
+    float z = theta[kOffBh];
+    for (int c = 0; c < kC; ++c) {
+      float s = 0.0f;
+      for (int y = y0; y < y1; ++y)
+        for (int x = x0; x < x1; ++x) s += a3[(((size_t)b * kC + c) * H2 + y) * W2 + x];
+      const float p = cnt > 0 ? s / (float)cnt : 0.0f;
+      P[(size_t)i * kC + c] = p;
+      z = fmaf(wq(theta, kOffWh + c, bf16), p, z);
+    }
+    z_out[i] = z;
+    if (labels) {
+      const float y = labels[i];
+      dz[i] = (1.0f / (1.0f + expf(-z)) - y) / (float)n;
+      l = fmaxf(z, 0.0f) - y * z + log1pf(expf(-fabsf(z)));
+    }
+  }
+  red[threadIdx.x] = l;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) loss_part[blockIdx.x] = red[0];
+}
+
+// dL/dZ3 = [A3 > 0] Wh[c] dz(block) / count(block)
+__global__ void __launch_bounds__(256) dz3_kernel(const float* a3, const float* dz, const float* theta, int bf16,
+                                                  int B, int H2, int W2, int Th, int Tw, float* dz3) {
+  const long long n = (long long)B * kC * H2 * W2;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(idx % W2);
+    const int y = (int)((idx / W2) % H2);
+    const int c = (int)((idx / ((long long)W2 * H2)) % kC);
+    const int b = (int)(idx / ((long long)W2 * H2 * kC));
+    const int ty = y / 4, tx = x / 4;
+    const int cnt = (min(4 * ty + 4, H2) - 4 * ty) * (min(4 * tx + 4, W2) - 4 * tx);
+    const float g = wq(theta, kOffWh + c, bf16) * dz[((size_t)b * Th + ty) * Tw + tx] / (float)cnt;
+    dz3[idx] = a3[idx] > 0.0f ? g : 0.0f;
+  }
+}
+
+// Input gradient of a 16 -> 16 layer of stride S, times the ReLU mask of its
+// input: dZin[ci](y, x) = [Ain > 0] sum over co, taps with S yo + ky - 1 = y
+// (and the same in x) of dZ[co](yo, xo) W[co][ci][ky][kx].
+template <int S>
+__global__ void __launch_bounds__(256) conv_dgrad_kernel(const float* dz, int Ho, int Wo, const float* ain, int Hi,
+                                                         int Wi, const float* theta, int w_off, int bf16, int B,
+                                                         float* dzin) {
+  __shared__ float w[kC * kC * 9];
+  for (int i = threadIdx.x; i < kC * kC * 9; i += blockDim.x) w[i] = wq(theta, w_off + i, bf16);
+  __syncthreads();
+  const long long n = (long long)B * Hi * Wi;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(idx / ((long long)Hi * Wi));
+    const int r = (int)(idx - (long long)b * Hi * Wi);
+    const int y = r / Wi, x = r - (r / Wi) * Wi;
+    float acc[kC];
+#pragma unroll
+    for (int ci = 0; ci < kC; ++ci) acc[ci] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const int ty = y + 1 - k / 3, tx = x + 1 - k % 3;
+      if (ty < 0 || tx < 0 || ty % S || tx % S) continue;
+      const int yo = ty / S, xo = tx / S;
+      if (yo >= Ho || xo >= Wo) continue;
+      for (int co = 0; co < kC; ++co) {
+        const float g = dz[(((size_t)b * kC + co) * Ho + yo) * Wo + xo];
+#pragma unroll
+        for (int ci = 0; ci < kC; ++ci) acc[ci] = fmaf(w[(co * kC + ci) * 9 + k], g, acc[ci]);
+      }
+    }
+#pragma unroll
+    for (int ci = 0; ci < kC; ++ci) {
+      const size_t o = (((size_t)b * kC + ci) * Hi + y) * Wi + x;
+      dzin[o] = ain[o] > 0.0f ? acc[ci] : 0.0f;
+    }
+  }
+}
+
+// Weight and bias gradients of a CIN -> 16 layer of stride S.  Each CTA takes
+// chunks of 64 output pixels (grid-stride, so the assignment is fixed), stages
+// their dZ and input patches, and thread j accumulates the weights j,
+// j + 256, ...; per-CTA partial sums go to part[blockIdx.x][16 * CIN * 9 + 16].
+constexpr int kWgChunk = 64;
+template <int CIN, int S, typename In>
+__global__ void __launch_bounds__(256) conv_wgrad_kernel(In in, const float* dz, int B, int Ho, int Wo,
+                                                         float* part) {
+  constexpr int NW = kC * CIN * 9, PL = CIN * 9;
+  __shared__ float sdz[kC][kWgChunk];
+  __shared__ float patch[kWgChunk][PL + 1];
+  float acc[(NW + 255) / 256];
+  float bacc = 0.0f;
+#pragma unroll
+  for (int m = 0; m < (NW + 255) / 256; ++m) acc[m] = 0.0f;
+  const long long n = (long long)B * Ho * Wo;
+  for (long long c0 = (long long)blockIdx.x * kWgChunk; c0 < n; c0 += (long long)gridDim.x * kWgChunk) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < kWgChunk * (kC + PL); i += blockDim.x) {
+      const int p = i % kWgChunk, f = i / kWgChunk;
+      const long long idx = c0 + p;
+      float v = 0.0f;
+      if (idx < n) {
+        const int b = (int)(idx / ((long long)Ho * Wo));
+        const int r = (int)(idx - (long long)b * Ho * Wo);
+        const int y = r / Wo, x = r - (r / Wo) * Wo;
+        if (f < kC) {
+          v = dz[(((size_t)b * kC + f) * Ho + y) * Wo + x];
+        } else {
+          const int ci = (f - kC) / 9, k = (f - kC) % 9;
+          v = in(b, ci, S * y + k / 3 - 1, S * x + k % 3 - 1);
+        }
+      }
+      if (f < kC) sdz[f][p] = v;
+      else patch[p][f - kC] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < (NW + 255) / 256; ++m) {
+      const int j = threadIdx.x + 256 * m;
+      if (j < NW) {
+        const int co = j / PL, q = j - co * PL;
+        float s = acc[m];
+        for (int p = 0; p < kWgChunk; ++p) s = fmaf(sdz[co][p], patch[p][q], s);
+        acc[m] = s;
+      }
+    }
+    if (threadIdx.x < kC)
+      for (int p = 0; p < kWgChunk; ++p) bacc += sdz[threadIdx.x][p];
+  }
+  float* out = part + (size_t)blockIdx.x * (NW + kC);
+#pragma unroll
+  for (int m = 0; m < (NW + 255) / 256; ++m) {
+    const int j = threadIdx.x + 256 * m;
+    if (j < NW) out[j] = acc[m];
+  }
+  if (threadIdx.x < kC) out[NW + threadIdx.x] = bacc;
+}
+
+// grad[w_off + j] = sum over g of part[g][j] (j < nw), grad[b_off + c] from
+// the bias columns; g in increasing order.
+__global__ void reduce_parts_kernel(const float* part, int n_parts, int nw, float* grad, int w_off, int b_off) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nw + kC) return;
+  float s = 0.0f;
+  for (int g = 0; g < n_parts; ++g) s += part[(size_t)g * (nw + kC) + j];
+  grad[j < nw ? w_off + j : b_off + (j - nw)] = s;
+}
+
+// Head gradients (one CTA per output: dWh[c] = sum dz P[c], dbh = sum dz) and,
+// in the CTA of bh, the mean loss from the pool kernel's CTA sums.
+__global__ void __launch_bounds__(256) head_grad_kernel(const float* P, const float* dz, int n, float* grad,
+                                                        const float* loss_part, int n_loss, float* loss) {
+  __shared__ float red[256];
+  const int c = blockIdx.x;  // 0..15 weights, 16 bias
+  float s = 0.0f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += dz[i] * (c < kC ? P[(size_t)i * kC + c] : 1.0f);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = 128; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) grad[c < kC ? kOffWh + c : kOffBh] = red[0];
+  if (c == kC && threadIdx.x == 0 && loss) {
+    float l = 0.0f;
+    for (int g = 0; g < n_loss; ++g) l += loss_part[g];
+    *loss = l / (float)n;
+  }
+}
+
+// Adam with bias correction: bc1 = 1 - beta1^t, bc2 = 1 - beta2^t.
+__global__ void adam_kernel(float* theta, float* m, float* v, const float* g, int n, float lr, float b1, float b2,
+                            float bc1, float bc2, float eps) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.0f - b1) * gi;
+  const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  theta[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+}
+
+// ------------------------------------------------------------------ inference
+constexpr int kRBX = 8, kRBY = 4;                          // blocks per CTA
+constexpr int kA3X = 4 * kRBX, kA3Y = 4 * kRBY;            // 32 x 16 A3 positions
+constexpr int kA2X = kA3X + 2, kA2Y = kA3Y + 2;            // 34 x 18 (conv3 halo)
+constexpr int kA1X = 2 * kA2X + 1, kA1Y = 2 * kA2Y + 1;    // 69 x 37
+constexpr int kInX = 2 * kA1X + 1, kInY = 2 * kA1Y + 1;    // 139 x 75
+constexpr int kInP = 144;                                  // input row pitch (bytes)
+constexpr int kInfThreads = 256;
+constexpr int kA2Tiles = (kA2X * kA2Y + 15) / 16;          // 39 row tiles of conv2
+constexpr size_t kInfSmem = (size_t)kInY * kInP + (size_t)kA1X * kA1Y * kC * 2 + (size_t)kA2X * kA2Y * kC * 2;
+
+__device__ __forceinline__ void ldmatrix_x4(unsigned (&r)[4], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(static_cast<unsigned>(__cvta_generic_to_shared(p))));
+}
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // .x = lo (low half)
+  return *reinterpret_cast<const unsigned*>(&v);
+}
+
+// B fragments of one 16 -> 16 layer for this lane: for tap t and output half
+// h, reg 0 holds W[co][ci][t] for ci = 2q, 2q + 1 and reg 1 for ci = 2q + 8,
+// 2q + 9, with co = 8h + lane / 4 and q = lane % 4.
+__device__ __forceinline__ void load_bfrag(const float* theta, int w_off, int lane, unsigned (&bw)[9][2][2]) {
+  const int q = lane & 3, nn = lane >> 2;
+#pragma unroll
+  for (int t = 0; t < 9; ++t)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int co = 8 * h + nn;
+      const float* w = theta + w_off + co * kC * 9 + t;
+      bw[t][h][0] = pack_bf16(w[(2 * q) * 9], w[(2 * q + 1) * 9]);
+      bw[t][h][1] = pack_bf16(w[(2 * q + 8) * 9], w[(2 * q + 9) * 9]);
+    }
+}
+
+__global__ void __launch_bounds__(kInfThreads, 2) proposal_infer_kernel(const PropImage* imgs, const float* theta,
+                                                                     float* logits) {
+  extern __shared__ float4 smem4[];
+  uint8_t* in_s = reinterpret_cast<uint8_t*>(smem4);
+  __nv_bfloat16* a1_s = reinterpret_cast<__nv_bfloat16*>(in_s + (size_t)kInY * kInP);
+  __nv_bfloat16* a2_s = a1_s + (size_t)kA1X * kA1Y * kC;
+  __shared__ float w1[kC * 9], b1[kC], b2[kC], b3[kC], wh[kC];
+  const PropImage im = imgs[blockIdx.z];
+  const int bx0 = blockIdx.x * kRBX, by0 = blockIdx.y * kRBY;  // first block of the CTA
+  if (bx0 >= im.Tw || by0 >= im.Th) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // global origins of the regions (A3, A2, A1, input)
+  const int ya3 = 4 * by0, xa3 = 4 * bx0;
+  const int ya2 = ya3 - 1, xa2 = xa3 - 1;
+  const int ya1 = 2 * ya2 - 1, xa1 = 2 * xa2 - 1;
+  const int yin = 2 * ya1 - 1, xin = 2 * xa1 - 1;
+  for (int i = threadIdx.x; i < kC * 9; i += kInfThreads) w1[i] = bf16r(theta[kOffW1 + i]);
+  if (threadIdx.x < kC) {
+    b1[threadIdx.x] = theta[kOffB1 + threadIdx.x];
+    b2[threadIdx.x] = theta[kOffB2 + threadIdx.x];
+    b3[threadIdx.x] = theta[kOffB3 + threadIdx.x];
+    wh[threadIdx.x] = bf16r(theta[kOffWh + threadIdx.x]);
+  }
+  // input region (128 = x of 0 outside the image: the zero padding of x)
+  for (int i = threadIdx.x; i < kInY * kInX; i += kInfThreads) {
+    const int r = i / kInX, c = i - r * kInX;
+    const int gy = yin + r, gx = xin + c;
+    in_s[r * kInP + c] = (gy >= 0 && gy < im.H && gx >= 0 && gx < im.W) ? im.src[(size_t)gy * im.pitch + gx] : 128;
+  }
+  __syncthreads();
+  // conv1 on the FP32 pipes: A1 positions of the region, zero outside A1
+  for (int p = threadIdx.x; p < kA1X * kA1Y; p += kInfThreads) {
+    const int r = p / kA1X, c = p - r * kA1X;
+    const int gy = ya1 + r, gx = xa1 + c;
+    uint4* dst = reinterpret_cast<uint4*>(a1_s + (size_t)p * kC);
+    if (gy < 0 || gy >= im.H1 || gx < 0 || gx >= im.W1) {
+      dst[0] = make_uint4(0, 0, 0, 0);
+      dst[1] = make_uint4(0, 0, 0, 0);
+      continue;
+    }
+    float xv[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) xv[k] = ((float)in_s[(2 * r + k / 3) * kInP + 2 * c + k % 3] - 128.0f) * (1.0f / 64.0f);
+    unsigned pk[8];
+#pragma unroll
+    for (int co = 0; co < kC; co += 2) {
+      float s0 = b1[co], s1 = b1[co + 1];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        s0 = fmaf(w1[co * 9 + k], xv[k], s0);
+        s1 = fmaf(w1[(co + 1) * 9 + k], xv[k], s1);
+      }
+      pk[co / 2] = pack_bf16(fmaxf(s0, 0.0f), fmaxf(s1, 0.0f));
+    }
+    dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+  }
+  __syncthreads();
+  const int q = lane & 3, rr = lane >> 2;
+  // conv2 on the tensor cores: row tiles of 16 A2 positions (row-major over
+  // the 34 x 18 region), one K = 16 contraction per tap
+  {
+    unsigned bw[9][2][2];
+    load_bfrag(theta, kOffW2, lane, bw);
+    for (int t = warp; t < kA2Tiles; t += kInfThreads / 32) {
+      // this lane's ldmatrix row: position 16 t + lane % 16 (clamped), k half lane / 16
+      const int pr = min(16 * t + (lane & 15), kA2X * kA2Y - 1);
+      const int r2 = pr / kA2X, c2 = pr - (pr / kA2X) * kA2X;
+      const __nv_bfloat16* base = a1_s + ((size_t)(2 * r2) * kA1X + 2 * c2) * kC + 8 * (lane >> 4);
+      float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        unsigned a[4];
+        ldmatrix_x4(a, base + ((size_t)(k / 3) * kA1X + k % 3) * kC);
+        mma_bf16(acc[0], a, bw[k][0][0], bw[k][0][1]);
+        mma_bf16(acc[1], a, bw[k][1][0], bw[k][1][1]);
+      }
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {  // rows rr and rr + 8
+        const int p = 16 * t + rr + 8 * half;
+        if (p >= kA2X * kA2Y) continue;
+        const int r2o = p / kA2X, c2o = p - (p / kA2X) * kA2X;
+        const int gy = ya2 + r2o, gx = xa2 + c2o;
+        const bool ok = gy >= 0 && gy < im.H2 && gx >= 0 && gx < im.W2;
+        unsigned* dst = reinterpret_cast<unsigned*>(a2_s + (size_t)p * kC);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int co = 8 * h + 2 * q;
+          const float v0 = ok ? fmaxf(acc[h][2 * half] + b2[co], 0.0f) : 0.0f;
+          const float v1 = ok ? fmaxf(acc[h][2 * half + 1] + b2[co + 1], 0.0f) : 0.0f;
+          dst[co / 2] = pack_bf16(v0, v1);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // conv3 + pooling + head: row tile t = pooling cell (t / 8, t % 8) of the
+  // CTA, row i = position (4 (t / 8) + i / 4, 4 (t % 8) + i % 4)
+  {
+    unsigned bw[9][2][2];
+    load_bfrag(theta, kOffW3, lane, bw);
+    for (int t = warp; t < kRBX * kRBY; t += kInfThreads / 32) {
+      const int cy = t / kRBX, cx = t - (t / kRBX) * kRBX;
+      const int ty = by0 + cy, tx = bx0 + cx;
+      if (ty >= im.Th || tx >= im.Tw) continue;  // warp-uniform
+      const int i = lane & 15;
+      const int r3 = 4 * cy + i / 4, c3 = 4 * cx + i % 4;
+      const __nv_bfloat16* base = a2_s + ((size_t)r3 * kA2X + c3) * kC + 8 * (lane >> 4);
+      float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        unsigned a[4];
+        ldmatrix_x4(a, base + ((size_t)(k / 3) * kA2X + k % 3) * kC);
+        mma_bf16(acc[0], a, bw[k][0][0], bw[k][0][1]);
+        mma_bf16(acc[1], a, bw[k][1][0], bw[k][1][1]);
+      }
+      // relu(z3 + b3) at the lane's two rows, zero for positions outside A3
+      float s[2][2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) s[h][j] = 0.0f;
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const int ii = rr + 8 * half;
+        const int gy = ya3 + 4 * cy + ii / 4, gx = xa3 + 4 * cx + ii % 4;
+        if (gy < im.H2 && gx < im.W2)
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) s[h][j] += fmaxf(acc[h][2 * half + j] + b3[8 * h + 2 * q + j], 0.0f);
+      }
+      // sum over the 8 row lanes (same q): lane bits 2..4
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+          for (int o = 4; o < 32; o <<= 1) s[h][j] += __shfl_xor_sync(0xffffffffu, s[h][j], o);
+      const int gy0 = 4 * ty, gx0 = 4 * tx;
+      const int cnt = (min(gy0 + 4, im.H2) - gy0) * (min(gx0 + 4, im.W2) - gx0);
+      const float inv = 1.0f / (float)cnt;
+      float zp = 0.0f;
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) zp = fmaf(wh[8 * h + 2 * q + j], s[h][j] * inv, zp);
+      zp += __shfl_xor_sync(0xffffffffu, zp, 1);
+      zp += __shfl_xor_sync(0xffffffffu, zp, 2);
+      if (lane == 0) logits[im.logit_off + (size_t)ty * im.Tw + tx] = zp + theta[kOffBh];
+    }
+  }
+}
+
+// Detection mode of every first-octave tile (see TileMode): a tile detects
+// when a block with logit > zt lies within `dil` blocks of its area; it
+// stores all levels when a detecting tile lies within (ny, nx) tiles of it.
+__global__ void tile_mode_kernel(const PropImage* imgs, const ImgPlan* plans, const int* tile_prefix, int n_images,
+                                 const float* logits, float zt, int dil, int ny, int nx, uint8_t* mode) {
+  const int img = blockIdx.y;
+  if (img >= n_images) return;
+  const PropImage im = imgs[img];
+  const OctPlan& op = plans[img].oct[0];
+  const int nt = op.tiles_x * op.tiles_y;
+  auto detects = [&](int tx, int ty) {
+    const int bx0 = max(tx * (kTX / 16) - dil, 0), bx1 = min((tx + 1) * (kTX / 16) + dil, im.Tw);
+    const int by0 = max(ty * (kTY / 16) - dil, 0), by1 = min((ty + 1) * (kTY / 16) + dil, im.Th);
+    for (int by = by0; by < by1; ++by)
+      for (int bx = bx0; bx < bx1; ++bx)
+        if (logits[im.logit_off + (size_t)by * im.Tw + bx] > zt) return true;
+    return false;
+  };
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+    const int ty = t / op.tiles_x, tx = t - ty * op.tiles_x;
+    uint8_t m = kModeLevel3;
+    if (detects(tx, ty)) {
+      m = kModeDetect;
+    } else {
+      for (int dy = -ny; dy <= ny && m == kModeLevel3; ++dy)
+        for (int dx = -nx; dx <= nx; ++dx) {
+          const int ux = tx + dx, uy = ty + dy;
+          if (ux < 0 || uy < 0 || ux >= op.tiles_x || uy >= op.tiles_y) continue;
+          if (detects(ux, uy)) {
+            m = kModeLevels;
+            break;
+          }
+        }
+    }
+    mode[tile_prefix[img] + t] = m;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+size_t proposal_infer_smem() { return kInfSmem; }
+
+cudaError_t launch_proposal_infer(const PropImage* d_imgs, int n_images, int max_th, int max_tw, const float* theta,
+                                  float* logits, cudaStream_t s) {
+  if (n_images <= 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(proposal_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kInfSmem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((max_tw + kRBX - 1) / kRBX, (max_th + kRBY - 1) / kRBY, n_images);
+  proposal_infer_kernel<<<grid, kInfThreads, kInfSmem, s>>>(d_imgs, theta, logits);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_mode(const PropImage* d_imgs, const ImgPlan* plans, const int* tile_prefix, int n_images,
+                             int max_tiles, const float* logits, float zt, int dil, int ny, int nx, uint8_t* mode,
+                             cudaStream_t s) {
+  if (n_images <= 0) return cudaSuccess;
+  dim3 grid((max_tiles + 127) / 128, n_images);
+  tile_mode_kernel<<<grid, 128, 0, s>>>(d_imgs, plans, tile_prefix, n_images, logits, zt, dil, ny, nx, mode);
+  return cudaGetLastError();
+}
+
+// Workspace layout of a training step (floats): A1, A2, A3, dZ1, dZ2, dZ3,
+// P, z, dz, loss parts, weight-gradient parts.
+size_t proposal_train_floats(int B, int H, int W, int n_sms) {
+  const size_t H1 = (H + 1) / 2, W1 = (W + 1) / 2, H2 = (H1 + 1) / 2, W2 = (W1 + 1) / 2;
+  const size_t Th = (H + 15) / 16, Tw = (W + 15) / 16;
+  const size_t a1 = (size_t)B * kC * H1 * W1, a2 = (size_t)B * kC * H2 * W2;
+  const size_t nb = (size_t)B * Th * Tw;
+  const size_t parts = (size_t)2 * n_sms * (kC * kC * 9 + kC);
+  return 2 * a1 + 4 * a2 + nb * kC + 2 * nb + (nb + 255) / 256 + parts;
+}
+
+cudaError_t run_proposal_train(const PropTrainArgs& t, float* ws, int n_sms, cudaStream_t s) {
+  const int B = t.B, H = t.H, W = t.W;
+  const int H1 = (H + 1) / 2, W1 = (W + 1) / 2, H2 = (H1 + 1) / 2, W2 = (W1 + 1) / 2;
+  const int Th = (H + 15) / 16, Tw = (W + 15) / 16;
+  const size_t na1 = (size_t)B * kC * H1 * W1, na2 = (size_t)B * kC * H2 * W2;
+  const int nb = B * Th * Tw;
+  float* a1 = ws;
+  float* dz1 = a1 + na1;
+  float* a2 = dz1 + na1;
+  float* dz2 = a2 + na2;
+  float* a3 = dz2 + na2;
+  float* dz3 = a3 + na2;
+  float* P = dz3 + na2;
+  float* z = P + (size_t)nb * kC;
+  float* dz = z + nb;
+  float* lpart = dz + nb;
+  const int n_lpart = (nb + 255) / 256;
+  float* wpart = lpart + n_lpart;
+  const int gparts = 2 * n_sms;
+  auto grid_for = [&](long long n) { return (int)std::min<long long>((n + 255) / 256, (long long)n_sms * 16); };
+  U8Input x{t.images, t.pitch, (size_t)t.pitch * H, H, W};
+  F32Input in1{a1, kC, H1, W1}, in2{a2, kC, H2, W2};
+  conv_fwd_kernel<1, 2, U8Input><<<grid_for((long long)B * H1 * W1), 256, 0, s>>>(x, t.theta, kOffW1, kOffB1, t.bf16,
+                                                                                 t.bf16, a1, B, H1, W1);
+  conv_fwd_kernel<kC, 2, F32Input><<<grid_for((long long)B * H2 * W2), 256, 0, s>>>(in1, t.theta, kOffW2, kOffB2,
+                                                                                    t.bf16, t.bf16, a2, B, H2, W2);
+  conv_fwd_kernel<kC, 1, F32Input><<<grid_for((long long)B * H2 * W2), 256, 0, s>>>(in2, t.theta, kOffW3, kOffB3,
+                                                                                    t.bf16, 0, a3, B, H2, W2);
+  pool_head_kernel<<<n_lpart, 256, 0, s>>>(a3, B, H2, W2, Th, Tw, t.theta, t.bf16, t.labels, P, z, dz, lpart);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (t.logits_out) {
+    if ((e = cudaMemcpyAsync(t.logits_out, z, sizeof(float) * nb, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+      return e;
+  }
+  if (!t.labels) return cudaSuccess;  // forward only
+  float* grad = t.grad;
+  head_grad_kernel<<<kC + 1, 256, 0, s>>>(P, dz, nb, grad, lpart, n_lpart, t.loss);
+  dz3_kernel<<<grid_for((long long)na2), 256, 0, s>>>(a3, dz, t.theta, t.bf16, B, H2, W2, Th, Tw, dz3);
+  conv_wgrad_kernel<kC, 1, F32Input><<<gparts, 256, 0, s>>>(in2, dz3, B, H2, W2, wpart);
+  reduce_parts_kernel<<<(kC * kC * 9 + kC + 255) / 256, 256, 0, s>>>(wpart, gparts, kC * kC * 9, grad, kOffW3, kOffB3);
+  conv_dgrad_kernel<1><<<grid_for((long long)B * H2 * W2), 256, 0, s>>>(dz3, H2, W2, a2, H2, W2, t.theta, kOffW3,
+                                                                        t.bf16, B, dz2);
+  conv_wgrad_kernel<kC, 2, F32Input><<<gparts, 256, 0, s>>>(in1, dz2, B, H2, W2, wpart);
+  reduce_parts_kernel<<<(kC * kC * 9 + kC + 255) / 256, 256, 0, s>>>(wpart, gparts, kC * kC * 9, grad, kOffW2, kOffB2);
+  conv_dgrad_kernel<2><<<grid_for((long long)B * H1 * W1), 256, 0, s>>>(dz2, H2, W2, a1, H1, W1, t.theta, kOffW2,
+                                                                        t.bf16, B, dz1);
+  conv_wgrad_kernel<1, 2, U8Input><<<gparts, 256, 0, s>>>(x, dz1, B, H1, W1, wpart);
+  reduce_parts_kernel<<<1, 256, 0, s>>>(wpart, gparts, kC * 9, grad, kOffW1, kOffB1);
+  if (t.lr > 0.0f) {
+    const double b1 = 0.9, b2 = 0.999;
+    adam_kernel<<<(kPropParams + 255) / 256, 256, 0, s>>>(t.theta, t.adam_m, t.adam_v, grad, kPropParams, t.lr,
+                                                          (float)b1, (float)b2,
+                                                          (float)(1.0 - std::pow(b1, (double)t.step)),
+                                                          (float)(1.0 - std::pow(b2, (double)t.step)), 1e-8f);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace cdvs

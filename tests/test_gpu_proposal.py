@@ -1,0 +1,152 @@
+"""The learned block proposal on the GPU, against the FP64 oracle of the
+network (oracle/proposal_oracle.py) and against the plain detector.
+
+* training kernels: logits, loss and every gradient in FP32 mode against
+  the oracle's FP64 (tight), and in BF16 mode against the oracle's BF16
+  emulation (BF16 roundings of FP32 vs FP64 sums may differ by one BF16 ulp
+  near a rounding boundary, so the bound is looser);
+* the fused tensor-core inference kernel against the oracle on ragged sizes;
+* training is deterministic and lowers the loss;
+* masked detection: a network that proposes every block gives the plain
+  detector's records bit for bit; one that proposes none removes exactly the
+  first octave's candidates and leaves every later octave's bit for bit (the
+  level-3 path and the decimation are exact).
+"""
+import numpy as np
+import pytest
+
+from oracle import proposal_oracle as PO
+from paper_1705_09776_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    from paper_1705_09776_gb300 import cdvs
+    torch.cuda.init()
+    return cdvs, cdvs.Context(0), torch
+
+
+def _theta(seed, scale=0.5):
+    rng = np.random.default_rng(seed)
+    p = {}
+    for name, shp in PO.SHAPES:
+        fan_in = int(np.prod(shp[1:])) if len(shp) > 1 else 16
+        p[name] = rng.normal(0.0, scale * np.sqrt(2.0 / fan_in), shp)
+        if name.startswith("b"):
+            p[name] = rng.normal(0.02, 0.05, shp)
+    return PO.pack(p).astype(np.float32)
+
+
+def _batch(n, H, W, seed):
+    return np.stack([synth.blob_image(synth.image_seed(seed, i), width=W, height=H,
+                                      n_blobs=max(4, H * W // 1500)) for i in range(n)])
+
+
+def _gpu_step(cdvs, ctx, torch, imgs, labels, theta, bf16):
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    th = dev(theta.astype(np.float32))
+    m = torch.zeros_like(th)
+    v = torch.zeros_like(th)
+    g = torch.zeros_like(th)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    lg = torch.zeros(labels.shape, dtype=torch.float32, device="cuda")
+    ctx.proposal_train_step(dev(imgs), dev(labels.astype(np.float32)), th, m, v, g, loss, lg, step=1, lr=0.0,
+                            bf16=bf16)
+    torch.cuda.synchronize()
+    return float(loss.item()), g.cpu().numpy().astype(np.float64), lg.cpu().numpy().astype(np.float64)
+
+
+def _split(g):
+    offs = np.cumsum([0] + [int(np.prod(s)) for _, s in PO.SHAPES])
+    return {name: g[offs[k]:offs[k + 1]] for k, (name, _) in enumerate(PO.SHAPES)}
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_training_kernels_match_oracle(env, bf16):
+    cdvs, ctx, torch = env
+    imgs = _batch(3, 72, 100, seed=21)           # ragged: 72/16 and 100/16 are not whole
+    th, tw = -(-72 // 16), -(-100 // 16)
+    labels = (np.random.default_rng(5).random((3, th, tw)) < 0.4).astype(np.float64)
+    theta = _theta(7)
+    loss, g, lg = _gpu_step(cdvs, ctx, torch, imgs, labels, theta, bf16)
+    ref_loss, ref_g = PO.loss_and_grad(list(imgs), list(labels), theta.astype(np.float64), bf16=bf16)
+    ref_z = np.stack([PO.forward(im, theta.astype(np.float64), bf16=bf16)[0] for im in imgs])
+    zt, gt = (1e-4, 1e-4) if not bf16 else (2e-3, 2e-3)
+    assert np.max(np.abs(lg - ref_z) / (1.0 + np.abs(ref_z))) < zt
+    assert abs(loss - ref_loss) <= zt * abs(ref_loss)
+    G, R = _split(g), _split(ref_g)
+    for name, _ in PO.SHAPES:
+        err = np.linalg.norm(G[name] - R[name]) / max(np.linalg.norm(R[name]), 1e-12)
+        assert err < gt, (name, err)
+
+
+def test_inference_kernel_matches_oracle(env):
+    cdvs, ctx, torch = env
+    theta = _theta(11)
+    ctx.set_proposal(theta)
+    imgs = [synth.blob_image(synth.image_seed(31, 0)),                        # 640 x 480: 40 x 30 blocks
+            synth.blob_image(synth.image_seed(31, 1), width=161, height=121, n_blobs=40),
+            synth.blob_image(synth.image_seed(31, 2), width=37, height=300, n_blobs=20)]
+    got = ctx.proposal_logits(imgs)
+    for im, z in zip(imgs, got):
+        ref = PO.forward(im, theta.astype(np.float64), bf16=True)[0]
+        assert z.shape == ref.shape
+        assert np.max(np.abs(z - ref) / (1.0 + np.abs(ref))) < 2e-3
+
+
+def test_training_is_deterministic_and_learns(env):
+    cdvs, ctx, torch = env
+    imgs = _batch(8, 96, 128, seed=41)
+    th, tw = 6, 8
+    # a learnable rule: blocks whose mean grey level departs from 128
+    labels = np.stack([(np.abs(im.reshape(th, 16, tw, 16).mean(axis=(1, 3)) - 128.0) > 6.0) for im in imgs])
+    labels = labels.astype(np.float32)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    finals = []
+    for run in range(2):
+        th_ = dev(_theta(13))
+        m, v, g = torch.zeros_like(th_), torch.zeros_like(th_), torch.zeros_like(th_)
+        loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        losses = []
+        di, dl = dev(imgs), dev(labels)
+        for step in range(1, 61):
+            ctx.proposal_train_step(di, dl, th_, m, v, g, loss, None, step=step, lr=3e-3, bf16=True)
+            losses.append(float(loss.item()))
+        finals.append(th_.cpu().numpy())
+        assert losses[-1] < 0.7 * losses[0], losses[::10]
+    assert np.array_equal(finals[0], finals[1])
+
+
+def _all_blocks(value):
+    t = np.zeros(PO.N_PARAMS, np.float32)
+    t[-1] = value              # bh: every logit equals bh (all weights zero)
+    return t
+
+
+def test_proposing_every_block_gives_the_plain_detector(env):
+    cdvs, ctx, torch = env
+    imgs = [synth.blob_image(synth.image_seed(51, i)) for i in range(3)]
+    k0, d0, c0, _ = ctx.extract(imgs)
+    ctx.set_proposal(_all_blocks(20.0))
+    k1, d1, c1, _ = ctx.extract(imgs, cdvs.params(use_proposal=1))
+    assert np.array_equal(c0, c1)
+    assert np.array_equal(k0.view(np.uint8), k1.view(np.uint8))
+    assert np.array_equal(d0, d1)
+
+
+def test_proposing_no_block_removes_exactly_the_first_octave(env):
+    cdvs, ctx, torch = env
+    imgs = [synth.blob_image(synth.image_seed(52, i)) for i in range(2)]
+    full, cf, _ = ctx.candidates(imgs)
+    ctx.set_proposal(_all_blocks(-20.0))
+    masked, cm, _ = ctx.candidates(imgs, cdvs.params(use_proposal=1))
+    assert (masked["octave"] > 0).all()
+
+    def key(k):
+        return sorted(map(tuple, np.stack([k["image"], k["octave"], k["x"].view(np.int32), k["y"].view(np.int32),
+                                           k["sigma"].view(np.int32), k["response"].view(np.int32)], 1).tolist()))
+    assert key(masked) == key(full[full["octave"] > 0])
