@@ -221,6 +221,74 @@ def run_e2e(ctx, imgs, sizes, p, cap, stream, args, barrier, dist, cdvs, torch):
     return e2e_ms, e2e_records
 
 
+def record_keys(kp):
+    k = np.stack([kp["image"], kp["octave"], kp["x"].view(np.int32), kp["y"].view(np.int32),
+                  kp["sigma"].view(np.int32), kp["theta"].view(np.int32)], 1)
+    return set(map(tuple, k.tolist()))
+
+
+def tile_modes(logits, zt, H, W, reach):
+    """Counts of first-octave tiles (128 x 32 px) per mode, by the library's
+    rule: detect when a block with logit > zt lies within one block of the
+    tile; store levels when a detecting tile lies within the descriptor reach."""
+    tx_n, ty_n = -(-W // 128), -(-H // 32)
+    ny, nx = int(np.ceil(reach / 32)), int(np.ceil(reach / 128))
+    counts = np.zeros(3, np.int64)
+    for z in logits:
+        th, tw = z.shape
+        det = np.zeros((ty_n, tx_n), bool)
+        for ty in range(ty_n):
+            for tx in range(tx_n):
+                win = z[max(2 * ty - 1, 0):min(2 * ty + 3, th), max(8 * tx - 1, 0):min(8 * tx + 9, tw)]
+                det[ty, tx] = (win > zt).any()
+        for ty in range(ty_n):
+            for tx in range(tx_n):
+                if det[ty, tx]:
+                    counts[2] += 1
+                elif det[max(ty - ny, 0):ty + ny + 1, max(tx - nx, 0):tx + nx + 1].any():
+                    counts[1] += 1
+                else:
+                    counts[0] += 1
+    return counts
+
+
+def run_learned(ctx, imgs, step_with, p_plain, args, cdvs, torch, plain_kp):
+    """The same batch with the learned block proposal masking first-octave
+    detection: throughput, keypoint recall against the plain detector (exact
+    record identity), and how the first-octave tiles were treated."""
+    theta, thr = cdvs.load_proposal_weights()
+    ctx.set_proposal(theta)
+    p = cdvs.params(storage=int(p_plain["storage"][0]), use_proposal=1, proposal_threshold=thr)
+    for _ in range(args.warmup):
+        step_with(p)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    ctx.profile_read(reset=True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        kp, cnt = step_with(p)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    prof = ctx.profile_read(reset=True)
+    ctx.profile(False)
+    learned_kp = kp()
+    plain = record_keys(plain_kp)
+    recall = len(plain & record_keys(learned_kp)) / max(len(plain), 1)
+    zt = float(np.log(thr / (1 - thr)))
+    reach = max(float(p["desc_radius"][0]), float(p["ori_radius"][0])) * 2 * float(p["sigma0"][0]) * 1.001 + 2
+    counts = tile_modes(ctx.proposal_logits(list(imgs)), zt, imgs.shape[1], imgs.shape[2], reach)
+    n = len(imgs)
+    return {"value": n / (ms * 1e-3), "unit": "images/s", "ms_per_step": ms, "threshold": thr,
+            "recall_vs_plain": recall, "records_per_step": int(len(learned_kp)),
+            "first_octave_tiles": {"detect": int(counts[2]), "levels_only": int(counts[1]),
+                                   "level3_only": int(counts[0])},
+            "stage_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+            "weights": "paper_1705_09776_gb300/proposal_weights.npz (train_proposal.py; images of seeds 1e6+i)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -231,6 +299,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--images", type=int, default=N_IMAGES, help="images per rank (profiling runs)")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal leg")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank = int(os.environ.get("RANK", "0"))
@@ -296,6 +365,18 @@ def main():
     records = int(d_cnt.sum().item())
     value = n * world / (ms * 1e-3)
 
+    def read_kp():
+        tot = int(d_cnt.sum().item())
+        return d_kp[:tot * cdvs.KEYPOINT_DTYPE.itemsize].cpu().numpy().view(cdvs.KEYPOINT_DTYPE).copy()
+
+    plain_kp = read_kp()
+    learned = None
+    if not args.no_learned and os.path.exists(cdvs.PROPOSAL_WEIGHTS):
+        def step_with(pp):
+            ctx.extract_raw(n, dptrs, sizes, pp, d_kp, d_desc, cap, d_cnt, dev_flags, stream)
+            return read_kp, d_cnt
+        learned = run_learned(ctx, imgs, step_with, p, args, cdvs, torch, plain_kp)
+
     # ---- end to end through the C ABI: pinned host inputs, host outputs
     if args.no_e2e:
         e2e_ms, e2e_records = float("nan"), 0
@@ -338,6 +419,8 @@ def main():
                    "ms_per_step": e2e_ms if e2e_ms == e2e_ms else None,
                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
            "gpu_launches": launches, "roofline": roofline, "clocks": clocks}
+    if learned is not None:
+        out["learned"] = learned
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(imgs)
     if rank == 0:

@@ -201,11 +201,12 @@ cdvs_status cdvs_scale_space(cdvs_ctx *ctx, const uint8_t *image, const cdvs_ima
  * count to ms[s] / launches[s] for stage s in
  *   0 detect (one launch per octave), 1 dedupe + select, 2 orientation and
  *   descriptors, 3 record offsets, 4 record packing, 5 the octave-0 detect
- *   launch alone (part of stage 0),
+ *   launch alone (part of stage 0), 6 the block proposal network and the
+ *   tile modes (params->use_proposal = 1 only),
  * and clears the record when `reset` is nonzero.  Returns the number of
- * stages (6) or -1 on error.
+ * stages (7) or -1 on error.
  */
-#define CDVS_N_STAGES 6
+#define CDVS_N_STAGES 7
 cdvs_status cdvs_profile(cdvs_ctx *ctx, int32_t enable);
 int32_t cdvs_profile_read(cdvs_ctx *ctx, double *ms, int32_t *launches, int32_t max_stages,
                           int32_t reset);

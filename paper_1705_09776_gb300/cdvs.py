@@ -46,13 +46,20 @@ KEYPOINT_DTYPE = np.dtype([
 IMAGE_DESC_DTYPE = np.dtype([("width", "<i4"), ("height", "<i4"), ("pitch_bytes", "<i4")])
 assert PARAMS_DTYPE.itemsize == 80 and KEYPOINT_DTYPE.itemsize == 44
 PROPOSAL_PARAMS = 4817
+PROPOSAL_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "proposal_weights.npz")
+
+
+def load_proposal_weights(path=None):
+    """(theta, threshold) of a trained block proposal (train_proposal.py)."""
+    d = np.load(path or PROPOSAL_WEIGHTS)
+    return d["theta"].astype(np.float32), float(d["threshold"])
 
 EXPORTED = ["cdvs_params_default", "cdvs_create", "cdvs_destroy", "cdvs_last_error", "cdvs_extract",
             "cdvs_candidates", "cdvs_dedupe_select", "cdvs_describe", "cdvs_scale_space",
             "cdvs_rank_host", "cdvs_transform_ternary", "cdvs_profile", "cdvs_profile_read",
             "cdvs_dedupe_select_noalloc", "cdvs_set_proposal", "cdvs_proposal_logits",
             "cdvs_proposal_train_step"]
-STAGES = ["detect", "select", "describe", "offsets", "pack", "detect_octave0"]
+STAGES = ["detect", "select", "describe", "offsets", "pack", "detect_octave0", "proposal"]
 
 
 class CdvsError(RuntimeError):

@@ -608,7 +608,9 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
     for (auto& u : c->uploads) u.clear();
     c->n_chunks = 1;
     c->chunk_begin[1] = n;
+    cudaEvent_t evp = prof_begin(c, s);
     if ((st = run_proposal_mask(c, n, sizes, p, s)) != CDVS_OK) return st;
+    prof_end(c, 6, 2, evp, s);
     tile_mode = static_cast<const uint8_t*>(c->prop_mode.p);
   }
   if ((st = run_detect(c, n, p, max_oct, cap, s, tile_mode)) != CDVS_OK) return st;

@@ -1,0 +1,160 @@
+"""Trains the learned block proposal on the GPU and writes its parameters.
+
+    python -m paper_1705_09776_gb300.train_proposal [--train 16384] [--out PATH]
+
+Labels come from the plain detector: a 16x16 block is positive when a
+first-octave record of cdvs_extract (after the cross-octave check and the
+selection, Sec. III-B) lies in it.  The images are the seeded synthetic
+blob images (seeds 1000000 + i for training, 3000000 + i for choosing the
+threshold).  Training runs the library's own forward, backward and Adam
+kernels (cdvs_proposal_train_step, BF16 as in inference).  The threshold is
+the largest of a fixed list whose masked extraction keeps at least
+`--keep` of the plain detector's records on the validation images.  The
+output .npz holds `theta` (FP32), `threshold` and the training record.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import time
+
+import numpy as np
+
+from . import synth
+
+TRAIN_BASE, VAL_BASE = 1_000_000, 3_000_000
+HERE = os.path.dirname(os.path.abspath(__file__))
+DEFAULT_OUT = os.path.join(HERE, "proposal_weights.npz")
+THRESHOLDS = (0.5, 0.4, 0.3, 0.2, 0.15, 0.1, 0.07, 0.05, 0.03, 0.02, 0.01)
+
+
+def _gen(args):
+    base, i = args
+    return synth.blob_image(synth.image_seed(base, i))
+
+
+def make_images(base: int, n: int, procs: int) -> np.ndarray:
+    """Seeded images, generated in a spawn pool (call before CUDA starts)."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return np.stack(pool.map(_gen, [(base, i) for i in range(n)], chunksize=16))
+
+
+def block_labels(records, n_images: int, height: int, width: int) -> np.ndarray:
+    """(n, ceil(H/16), ceil(W/16)) float32: 1 where a first-octave record lies."""
+    th, tw = -(-height // 16), -(-width // 16)
+    y = np.zeros((n_images, th, tw), np.float32)
+    r = records[records["octave"] == 0]
+    bx = np.clip(np.floor(r["x"] + 0.5).astype(np.int64) // 16, 0, tw - 1)
+    by = np.clip(np.floor(r["y"] + 0.5).astype(np.int64) // 16, 0, th - 1)
+    y[r["image"], by, bx] = 1.0
+    return y
+
+
+def record_keys(records) -> set:
+    """Exact identity of records: image, octave and the bits of x, y, sigma, theta."""
+    k = np.stack([records["image"], records["octave"], records["x"].view(np.int32), records["y"].view(np.int32),
+                  records["sigma"].view(np.int32), records["theta"].view(np.int32)], 1)
+    return set(map(tuple, k.tolist()))
+
+
+def extract_batches(ctx, cdvs, images, p, batch=256):
+    recs, counts = [], []
+    for b0 in range(0, len(images), batch):
+        k, _, c, _ = ctx.extract(list(images[b0:b0 + batch]), p)
+        k = k.copy()
+        k["image"] += b0
+        recs.append(k)
+        counts.append(c)
+    return np.concatenate(recs), np.concatenate(counts)
+
+
+def recall(plain_keys: set, masked) -> float:
+    return len(plain_keys & record_keys(masked)) / max(len(plain_keys), 1)
+
+
+def init_theta(seed: int = 0) -> np.ndarray:
+    """He-normal weights, zero biases except a negative head bias (positives are rare)."""
+    rng = np.random.default_rng(seed)
+    parts = [rng.normal(0, np.sqrt(2 / 9), 144), np.zeros(16), rng.normal(0, np.sqrt(2 / 144), 2304), np.zeros(16),
+             rng.normal(0, np.sqrt(2 / 144), 2304), np.zeros(16), rng.normal(0, np.sqrt(1 / 16), 16), [-2.0]]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=16384)
+    ap.add_argument("--val", type=int, default=512)
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--epochs", type=int, default=3)
+    ap.add_argument("--lr", type=float, default=3e-3)
+    ap.add_argument("--keep", type=float, default=0.995)
+    ap.add_argument("--procs", type=int, default=os.cpu_count() or 1)
+    ap.add_argument("--out", default=DEFAULT_OUT)
+    a = ap.parse_args(argv)
+    t0 = time.time()
+    train = make_images(TRAIN_BASE, a.train, a.procs)
+    val = make_images(VAL_BASE, a.val, a.procs)
+    t_gen = time.time() - t0
+
+    import torch
+
+    from . import cdvs
+    ctx = cdvs.Context(0)
+    H, W = train.shape[1:]
+    plain = cdvs.params()
+    rec, _ = extract_batches(ctx, cdvs, train, plain)
+    labels = block_labels(rec, len(train), H, W)
+    print(f"labels: {labels.mean():.4f} of blocks positive, {len(rec) / len(train):.1f} records/img", flush=True)
+
+    dev_img = torch.from_numpy(train).cuda()
+    dev_lab = torch.from_numpy(labels).cuda()
+    theta = torch.from_numpy(init_theta()).cuda()
+    m, v, g = torch.zeros_like(theta), torch.zeros_like(theta), torch.zeros_like(theta)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    steps_per_epoch = len(train) // a.batch
+    total = steps_per_epoch * a.epochs
+    order = np.random.default_rng(1).permutation(len(train))
+    hist = []
+    t1 = time.time()
+    step = 0
+    for ep in range(a.epochs):
+        perm = np.roll(order, ep * 7919)
+        for s in range(steps_per_epoch):
+            step += 1
+            lr = a.lr * 0.5 * (1 + np.cos(np.pi * (step - 1) / total))   # cosine decay
+            idx = torch.from_numpy(np.sort(perm[s * a.batch:(s + 1) * a.batch])).cuda()
+            bi = dev_img.index_select(0, idx).contiguous()
+            bl = dev_lab.index_select(0, idx).contiguous()
+            ctx.proposal_train_step(bi, bl, theta, m, v, g, loss, None, step=step, lr=lr, bf16=True)
+            if step % 50 == 0 or step == total:
+                hist.append((step, float(loss.item())))
+                print(f"step {step}/{total} loss {hist[-1][1]:.4f}", flush=True)
+    torch.cuda.synchronize()
+    t_train = time.time() - t1
+    th = theta.cpu().numpy()
+
+    # threshold: the largest whose masked extraction keeps `keep` of the records
+    ctx.set_proposal(th)
+    vrec, _ = extract_batches(ctx, cdvs, val, plain)
+    vkeys = record_keys(vrec)
+    chosen, table = None, []
+    for t in THRESHOLDS:
+        mrec, _ = extract_batches(ctx, cdvs, val, cdvs.params(use_proposal=1, proposal_threshold=t))
+        r = recall(vkeys, mrec)
+        table.append((t, r))
+        print(f"threshold {t}: recall {r:.5f}", flush=True)
+        if r >= a.keep:
+            chosen = t
+            break
+    if chosen is None:
+        chosen = THRESHOLDS[-1]
+    np.savez(a.out, theta=th, threshold=np.float32(chosen), loss_history=np.array(hist, np.float64),
+             recall_table=np.array(table, np.float64),
+             config=np.array([a.train, a.val, a.batch, a.epochs, a.lr, a.keep], np.float64),
+             seconds=np.array([t_gen, t_train], np.float64))
+    print(f"wrote {a.out}: threshold {chosen}, gen {t_gen:.1f} s, train {t_train:.1f} s", flush=True)
+
+
+if __name__ == "__main__":
+    main()
