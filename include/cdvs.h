@@ -287,10 +287,11 @@ cdvs_status cdvs_dedupe_select_noalloc(const cdvs_keypoint *cand, int32_t n_cand
  * With params->use_proposal = 1, cdvs_extract and cdvs_candidates first run
  * the network, then treat each first-octave detection tile (128 x 32 px) in
  * one of three ways: tiles within one block of a proposed block (probability
- * > params->proposal_threshold) run the whole detector; tiles whose levels a
- * descriptor disc may read store every level without detecting; the rest only
- * build level 3, which the next octave is decimated from.  Later octaves run
- * in full.
+ * > params->proposal_threshold) run the whole detector, keeping candidates
+ * only in their blocks within one block of a proposed block; tiles whose
+ * levels a descriptor disc may read store every level without detecting; the
+ * rest only build level 3, which the next octave is decimated from.  Later
+ * octaves run in full.
  * ------------------------------------------------------------------------- */
 #define CDVS_PROPOSAL_PARAMS 4817
 

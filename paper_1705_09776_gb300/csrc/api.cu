@@ -377,7 +377,7 @@ cudaError_t issue_upload(cdvs_ctx* c, int k, cudaStream_t s) {
 }
 
 cdvs_status run_detect(cdvs_ctx* c, int n, const cdvs_params& p, int max_oct, int cap, cudaStream_t s,
-                       const uint8_t* tile_mode = nullptr) {
+                       const uint8_t* tile_mode = nullptr, const uint16_t* block_mask = nullptr) {
   cudaError_t e;
   DetectArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -400,6 +400,7 @@ cdvs_status run_detect(cdvs_ctx* c, int n, const cdvs_params& p, int max_oct, in
     a.octave = o;
     a.write_level0 = o == 0 ? 1 : 0;
     a.tile_mode = o == 0 ? tile_mode : nullptr;
+    a.block_mask = o == 0 ? block_mask : nullptr;
     int maxr = 0;
     for (int k = 0; k < kScales; ++k) {
       a.radius[k] = gauss_taps(tau_of(p, o, k), a.taps[k]);
@@ -528,7 +529,7 @@ cdvs_status run_proposal_mask(cdvs_ctx* c, int n, const cdvs_image_desc* sizes, 
   cudaError_t e;
   if ((e = ensure(c->prop_imgs, sizeof(PropImage) * n)) != cudaSuccess ||
       (e = ensure(c->prop_logits, sizeof(float) * n_logits)) != cudaSuccess ||
-      (e = ensure(c->prop_mode, (size_t)n_tiles)) != cudaSuccess)
+      (e = ensure(c->prop_mode, (size_t)n_tiles * 4 + n_logits)) != cudaSuccess)
     return cuda_fail(c, e, "proposal workspace");
   if ((e = cudaMemcpyAsync(c->prop_imgs.p, t.data(), sizeof(PropImage) * n, cudaMemcpyHostToDevice, s)) !=
       cudaSuccess)
@@ -542,9 +543,13 @@ cdvs_status run_proposal_mask(cdvs_ctx* c, int n, const cdvs_image_desc* sizes, 
   const int ny = (int)std::ceil(reach / kTY), nx = (int)std::ceil(reach / kTX);
   const double thr = p.proposal_threshold;
   const float zt = (float)std::log(thr / (1.0 - thr));
+  // prop_mode: modes (n_tiles) | spare (n_tiles) | block masks (2 n_tiles) ...
+  // the spare bytes hold the per-tile detect flags, then near flags per block
+  uint8_t* mb = static_cast<uint8_t*>(c->prop_mode.p);
   if ((e = launch_tile_mode(d_t, static_cast<const ImgPlan*>(c->plans.p), static_cast<const int*>(c->tile_prefix.p),
-                            n, max_tiles, static_cast<const float*>(c->prop_logits.p), zt, 1, ny, nx,
-                            static_cast<uint8_t*>(c->prop_mode.p), s)) != cudaSuccess)
+                            n, max_th * max_tw, max_tiles, static_cast<const float*>(c->prop_logits.p), zt, 1, ny,
+                            nx, mb, reinterpret_cast<uint16_t*>(mb + 2 * (size_t)n_tiles), mb + 4 * (size_t)n_tiles,
+                            mb + (size_t)n_tiles, s)) != cudaSuccess)
     return cuda_fail(c, e, "tile mode launch");
   return CDVS_OK;
 }
@@ -601,6 +606,7 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
     return cuda_fail(c, e, "memset");
   cudaEvent_t ev = prof_begin(c, s);
   const uint8_t* tile_mode = nullptr;
+  const uint16_t* block_mask = nullptr;
   if (p.use_proposal && (mode == kExtract || mode == kCandidates)) {
     // the network reads the whole batch: every upload first, in one piece
     for (int k = 0; k < c->n_chunks; ++k)
@@ -612,8 +618,9 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
     if ((st = run_proposal_mask(c, n, sizes, p, s)) != CDVS_OK) return st;
     prof_end(c, 6, 2, evp, s);
     tile_mode = static_cast<const uint8_t*>(c->prop_mode.p);
+    block_mask = reinterpret_cast<const uint16_t*>(tile_mode + 2 * (size_t)c->h_prefix[n]);
   }
-  if ((st = run_detect(c, n, p, max_oct, cap, s, tile_mode)) != CDVS_OK) return st;
+  if ((st = run_detect(c, n, p, max_oct, cap, s, tile_mode, block_mask)) != CDVS_OK) return st;
   prof_end(c, 0, max_oct, ev, s);
   int* h_small = static_cast<int*>(c->small.p);
 

@@ -82,6 +82,8 @@ struct DetectArgs {
   float offset_max;
   int write_level0;                      // 1 at octave 0 (level 0 is filtered, not the base)
   const uint8_t* tile_mode;              // per tile of the batch (index tile_base + b), or null: all detect
+  const uint16_t* block_mask;            // per tile: its 8 x 2 blocks of 16 x 16 px (bit 8 row + col) where
+                                         // detection keeps survivors, or null: all
 };
 
 // What K1 does with a tile when a block proposal masks the first octave
@@ -174,8 +176,8 @@ size_t proposal_infer_smem();
 cudaError_t launch_proposal_infer(const PropImage* d_imgs, int n_images, int max_th, int max_tw, const float* theta,
                                   float* logits, cudaStream_t s);
 cudaError_t launch_tile_mode(const PropImage* d_imgs, const ImgPlan* plans, const int* tile_prefix, int n_images,
-                             int max_tiles, const float* logits, float zt, int dil, int ny, int nx, uint8_t* mode,
-                             cudaStream_t s);
+                             int max_blocks, int max_tiles, const float* logits, float zt, int dil, int ny, int nx,
+                             uint8_t* mode, uint16_t* block_mask, uint8_t* near, uint8_t* det, cudaStream_t s);
 size_t proposal_train_floats(int B, int H, int W, int n_sms);
 cudaError_t run_proposal_train(const PropTrainArgs& t, float* ws, int n_sms, cudaStream_t s);
 

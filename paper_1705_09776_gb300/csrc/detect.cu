@@ -619,6 +619,7 @@ __global__ void __launch_bounds__(kDetThreads, 1)
     // what a block proposal leaves to do on this tile (uniform over the CTA):
     // everything, the levels only, or level 3 and the next octave's base
     const int mode = a.tile_mode ? a.tile_mode[a.tile_base + b] : kModeDetect;
+    const unsigned bmask = a.block_mask ? a.block_mask[a.tile_base + b] : 0xFFFFu;
     const int k0 = mode == kModeLevel3 ? kScales - 1 : 0;
 
     // ---- levels: the y pass of level k+1 shares a phase with the stores and
@@ -673,7 +674,8 @@ __global__ void __launch_bounds__(kDetThreads, 1)
         al2[i] = s;
       }
       const int x = tx0 + lx, y0 = ty0 + 2 * m;
-      const bool inx = x >= 1 && x < W - 1;
+      // rows 2m, 2m + 1 lie in block row m / 8; a proposal may rule the block out
+      const bool inx = x >= 1 && x < W - 1 && ((bmask >> ((m >> 3) * (kTX / 16) + (lx >> 4))) & 1u);
       cubic_extremum2(a, al2, inx && y0 >= 1 && y0 < H - 1, inx && y0 + 1 < H - 1, bt[it], tb[it]);
     }
 #pragma unroll

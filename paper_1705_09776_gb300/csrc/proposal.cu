@@ -306,8 +306,9 @@ constexpr int kA3X = 4 * kRBX, kA3Y = 4 * kRBY;            // 32 x 16 A3 positio
 constexpr int kA2X = kA3X + 2, kA2Y = kA3Y + 2;            // 34 x 18 (conv3 halo)
 constexpr int kA1X = 2 * kA2X + 1, kA1Y = 2 * kA2Y + 1;    // 69 x 37
 constexpr int kInX = 2 * kA1X + 1, kInY = 2 * kA1Y + 1;    // 139 x 75
-constexpr int kInP = 144;                                  // input row pitch (bytes)
+constexpr int kInP = 160;                                  // input row pitch (bytes): 139 + 15 alignment slack
 constexpr int kInfThreads = 256;
+static_assert(kInX + 15 <= kInP, "input rows hold the region after 16-byte alignment");
 constexpr int kA2Tiles = (kA2X * kA2Y + 15) / 16;          // 39 row tiles of conv2
 constexpr size_t kInfSmem = (size_t)kInY * kInP + (size_t)kA1X * kA1Y * kC * 2 + (size_t)kA2X * kA2Y * kC * 2;
 
@@ -367,12 +368,30 @@ __global__ void __launch_bounds__(kInfThreads, 2) proposal_infer_kernel(const Pr
     b3[threadIdx.x] = theta[kOffB3 + threadIdx.x];
     wh[threadIdx.x] = bf16r(theta[kOffWh + threadIdx.x]);
   }
-  // input region (128 = x of 0 outside the image: the zero padding of x)
-  for (int i = threadIdx.x; i < kInY * kInX; i += kInfThreads) {
-    const int r = i / kInX, c = i - r * kInX;
-    const int gy = yin + r, gx = xin + c;
-    in_s[r * kInP + c] = (gy >= 0 && gy < im.H && gx >= 0 && gx < im.W) ? im.src[(size_t)gy * im.pitch + gx] : 128;
+  // input region, from image column xal = xin rounded down to 16 bytes (so
+  // in_s column c + sh is image x = xin + c): 16-byte asynchronous copies of
+  // the aligned pieces inside the image, bytes elsewhere (128 = x of 0
+  // outside the image: the zero padding of x)
+  const int xal = xin & ~15, sh = xin - xal;
+  const bool vec = ((reinterpret_cast<uintptr_t>(im.src) | (uintptr_t)im.pitch) & 15) == 0;
+  for (int i = threadIdx.x; i < kInY * (kInP / 16); i += kInfThreads) {
+    const int r = i / (kInP / 16), c16 = i - r * (kInP / 16);
+    const int gy = yin + r, gx = xal + 16 * c16;
+    uint8_t* dst = in_s + r * kInP + 16 * c16;
+    if (vec && gy >= 0 && gy < im.H && gx >= 0 && gx + 16 <= im.W) {
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                       static_cast<unsigned>(__cvta_generic_to_shared(dst))),
+                   "l"(im.src + (size_t)gy * im.pitch + gx)
+                   : "memory");
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int x = gx + j;
+        dst[j] = (gy >= 0 && gy < im.H && x >= 0 && x < im.W) ? im.src[(size_t)gy * im.pitch + x] : 128;
+      }
+    }
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
   // conv1 on the FP32 pipes: A1 positions of the region, zero outside A1
   for (int p = threadIdx.x; p < kA1X * kA1Y; p += kInfThreads) {
@@ -386,7 +405,8 @@ __global__ void __launch_bounds__(kInfThreads, 2) proposal_infer_kernel(const Pr
     }
     float xv[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) xv[k] = ((float)in_s[(2 * r + k / 3) * kInP + 2 * c + k % 3] - 128.0f) * (1.0f / 64.0f);
+    for (int k = 0; k < 9; ++k)
+      xv[k] = ((float)in_s[(2 * r + k / 3) * kInP + sh + 2 * c + k % 3] - 128.0f) * (1.0f / 64.0f);
     unsigned pk[8];
 #pragma unroll
     for (int co = 0; co < kC; co += 2) {
@@ -498,39 +518,64 @@ __global__ void __launch_bounds__(kInfThreads, 2) proposal_infer_kernel(const Pr
   }
 }
 
-// Detection mode of every first-octave tile (see TileMode): a tile detects
-// when a block with logit > zt lies within `dil` blocks of its area; it
-// stores all levels when a detecting tile lies within (ny, nx) tiles of it.
-__global__ void tile_mode_kernel(const PropImage* imgs, const ImgPlan* plans, const int* tile_prefix, int n_images,
-                                 const float* logits, float zt, int dil, int ny, int nx, uint8_t* mode) {
+// Tile modes of the first octave, in three passes over the batch.
+// near[block]: a block with logit > zt lies within `dil` blocks.
+__global__ void near_kernel(const PropImage* imgs, int n_images, const float* logits, float zt, int dil,
+                            uint8_t* near) {
+  const int img = blockIdx.y;
+  if (img >= n_images) return;
+  const PropImage im = imgs[img];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < im.Th * im.Tw; i += gridDim.x * blockDim.x) {
+    const int by = i / im.Tw, bx = i - (i / im.Tw) * im.Tw;
+    bool hit = false;
+    for (int yy = max(by - dil, 0); yy <= min(by + dil, im.Th - 1); ++yy)
+      for (int xx = max(bx - dil, 0); xx <= min(bx + dil, im.Tw - 1); ++xx)
+        hit |= logits[im.logit_off + (size_t)yy * im.Tw + xx] > zt;
+    near[im.logit_off + i] = hit;
+  }
+}
+
+// Per first-octave tile (128 x 32 px = 8 x 2 blocks): block_mask = its near
+// blocks (bit 8 row + col), det = any of them.
+__global__ void tile_det_kernel(const PropImage* imgs, const ImgPlan* plans, const int* tile_prefix, int n_images,
+                                const uint8_t* near, uint16_t* block_mask, uint8_t* det) {
   const int img = blockIdx.y;
   if (img >= n_images) return;
   const PropImage im = imgs[img];
   const OctPlan& op = plans[img].oct[0];
-  const int nt = op.tiles_x * op.tiles_y;
-  auto detects = [&](int tx, int ty) {
-    const int bx0 = max(tx * (kTX / 16) - dil, 0), bx1 = min((tx + 1) * (kTX / 16) + dil, im.Tw);
-    const int by0 = max(ty * (kTY / 16) - dil, 0), by1 = min((ty + 1) * (kTY / 16) + dil, im.Th);
-    for (int by = by0; by < by1; ++by)
-      for (int bx = bx0; bx < bx1; ++bx)
-        if (logits[im.logit_off + (size_t)by * im.Tw + bx] > zt) return true;
-    return false;
-  };
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+  constexpr int bw = kTX / 16, bh = kTY / 16;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < op.tiles_x * op.tiles_y; t += gridDim.x * blockDim.x) {
+    const int ty = t / op.tiles_x, tx = t - ty * op.tiles_x;
+    unsigned bits = 0;
+#pragma unroll
+    for (int j = 0; j < bw * bh; ++j) {
+      const int by = ty * bh + j / bw, bx = tx * bw + j % bw;
+      if (by < im.Th && bx < im.Tw && near[im.logit_off + (size_t)by * im.Tw + bx]) bits |= 1u << j;
+    }
+    block_mask[tile_prefix[img] + t] = (uint16_t)bits;
+    det[tile_prefix[img] + t] = bits != 0;
+  }
+}
+
+// mode: kModeDetect for detecting tiles, kModeLevels when a detecting tile
+// lies within (ny, nx) tiles (a descriptor disc of its points may read this
+// tile's levels), else kModeLevel3.
+__global__ void tile_mode_kernel(const ImgPlan* plans, const int* tile_prefix, int n_images, const uint8_t* det,
+                                 int ny, int nx, uint8_t* mode) {
+  const int img = blockIdx.y;
+  if (img >= n_images) return;
+  const OctPlan& op = plans[img].oct[0];
+  const uint8_t* d = det + tile_prefix[img];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < op.tiles_x * op.tiles_y; t += gridDim.x * blockDim.x) {
     const int ty = t / op.tiles_x, tx = t - ty * op.tiles_x;
     uint8_t m = kModeLevel3;
-    if (detects(tx, ty)) {
+    if (d[t]) {
       m = kModeDetect;
     } else {
-      for (int dy = -ny; dy <= ny && m == kModeLevel3; ++dy)
-        for (int dx = -nx; dx <= nx; ++dx) {
-          const int ux = tx + dx, uy = ty + dy;
-          if (ux < 0 || uy < 0 || ux >= op.tiles_x || uy >= op.tiles_y) continue;
-          if (detects(ux, uy)) {
-            m = kModeLevels;
-            break;
-          }
-        }
+      bool any = false;
+      for (int uy = max(ty - ny, 0); uy <= min(ty + ny, op.tiles_y - 1); ++uy)
+        for (int ux = max(tx - nx, 0); ux <= min(tx + nx, op.tiles_x - 1); ++ux) any |= d[uy * op.tiles_x + ux] != 0;
+      if (any) m = kModeLevels;
     }
     mode[tile_prefix[img] + t] = m;
   }
@@ -552,12 +597,16 @@ cudaError_t launch_proposal_infer(const PropImage* d_imgs, int n_images, int max
   return cudaGetLastError();
 }
 
+// scratch: max(n_logits, 1) + n_tiles bytes
 cudaError_t launch_tile_mode(const PropImage* d_imgs, const ImgPlan* plans, const int* tile_prefix, int n_images,
-                             int max_tiles, const float* logits, float zt, int dil, int ny, int nx, uint8_t* mode,
-                             cudaStream_t s) {
+                             int max_blocks, int max_tiles, const float* logits, float zt, int dil, int ny, int nx,
+                             uint8_t* mode, uint16_t* block_mask, uint8_t* near, uint8_t* det, cudaStream_t s) {
   if (n_images <= 0) return cudaSuccess;
-  dim3 grid((max_tiles + 127) / 128, n_images);
-  tile_mode_kernel<<<grid, 128, 0, s>>>(d_imgs, plans, tile_prefix, n_images, logits, zt, dil, ny, nx, mode);
+  near_kernel<<<dim3((max_blocks + 255) / 256, n_images), 256, 0, s>>>(d_imgs, n_images, logits, zt, dil, near);
+  tile_det_kernel<<<dim3((max_tiles + 127) / 128, n_images), 128, 0, s>>>(d_imgs, plans, tile_prefix, n_images, near,
+                                                                        block_mask, det);
+  tile_mode_kernel<<<dim3((max_tiles + 127) / 128, n_images), 128, 0, s>>>(plans, tile_prefix, n_images, det, ny, nx,
+                                                                         mode);
   return cudaGetLastError();
 }
 
