@@ -31,6 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_IMAGES, WIDTH, HEIGHT, BASE_SEED = 256, 640, 480, 1
+UNEVEN_SEED = 3
 METRIC = "images/s CDVS keypoints+descriptors @640px (batched/learned vs plain), HBM GB/s"
 SM_COUNT, FP32_LANES_PER_SM, MAX_SM_MHZ = 152, 128, 2070.0
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k1_detect_traffic.json")
@@ -289,6 +290,87 @@ def run_learned(ctx, imgs, step_with, p_plain, args, cdvs, torch, plain_kp):
             "weights": "paper_1705_09776_gb300/proposal_weights.npz (train_proposal.py; images of seeds 1e6+i)"}
 
 
+def _gen_uneven(args):
+    from paper_1705_09776_gb300 import synth
+    i, w, h = args
+    return synth.blob_image(synth.image_seed(UNEVEN_SEED, i), width=w, height=h,
+                            n_blobs=max(8, int(round(200 * w * h / (WIDTH * HEIGHT)))))
+
+
+def run_uneven(args, rank, world, local):
+    """Uneven batch: 1024 images with sides in 240..1280 and aspect 0.5..2
+    (blob count scaled by area), resized on the GPU to larger side 640 (S0)
+    and extracted in one call per step; device-resident inputs and outputs,
+    the call's work replayed as one CUDA graph.  FP32 and FP16 level storage,
+    and the same without the graph."""
+    import multiprocessing as mp
+
+    from paper_1705_09776_gb300 import synth
+    sizes = synth.uneven_sizes(args.images, base_seed=UNEVEN_SEED + rank)
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        imgs = pool.map(_gen_uneven, [(i, w, h) for i, (w, h) in enumerate(sizes)], chunksize=8)
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1705_09776_gb300 import cdvs
+    n = len(imgs)
+    flat = np.concatenate([im.ravel() for im in imgs])
+    offs = np.cumsum([0] + [im.size for im in imgs])
+    d_img = torch.from_numpy(flat).cuda()
+    ptrs = [d_img.data_ptr() + int(o) for o in offs[:-1]]
+    desc_sizes = np.array([(im.shape[1], im.shape[0], im.shape[1]) for im in imgs], cdvs.IMAGE_DESC_DTYPE)
+    cap = n * 300 * 4
+    ctx = cdvs.Context(local)
+    stream = torch.cuda.current_stream()
+    d_kp = torch.zeros(cap * cdvs.KEYPOINT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    d_desc = torch.zeros(cap, 128, dtype=torch.float32, device="cuda")
+    d_cnt = torch.zeros(n, dtype=torch.int32, device="cuda")
+    flags = cdvs.CDVS_INPUT_DEVICE | cdvs.CDVS_OUTPUT_DEVICE
+
+    def timed(p, graph):
+        ctx.set_graph(graph)
+        for _ in range(args.warmup):
+            ctx.extract_raw(n, ptrs, desc_sizes, p, d_kp, d_desc, cap, d_cnt, flags, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            ctx.extract_raw(n, ptrs, desc_sizes, p, d_kp, d_desc, cap, d_cnt, flags, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ctx.set_graph(False)
+        return e0.elapsed_time(e1) / args.steps, int(d_cnt.sum().item())
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    p32 = cdvs.params(max_side=640)
+    p16 = cdvs.params(max_side=640, storage=cdvs.CDVS_STORAGE_FP16)
+    ms32, rec32 = timed(p32, True)
+    ms16, rec16 = timed(p16, True)
+    ms_direct, _ = timed(p32, False)
+    clocks = sampler.stop()
+    # stage times from one profiled (direct) call
+    ctx.profile(True)
+    ctx.profile_read(reset=True)
+    ctx.extract_raw(n, ptrs, desc_sizes, p32, d_kp, d_desc, cap, d_cnt, flags, stream)
+    torch.cuda.synchronize()
+    prof = ctx.profile_read(reset=True)
+    ctx.profile(False)
+    area = float(sum(w * h for w, h in sizes))
+    out = {"metric": METRIC, "value": n / (ms32 * 1e-3), "unit": "images/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"{n}x uneven u8 seeded blob images (sides 240-1280, aspect 0.5-2, blobs by area), "
+                                  "S0 area resize to larger side 640, 4 octaves x 4 LoG scales, N=300",
+                      "mean_input_megapixels": area / n / 1e6, "storage": "fp32", "graph": True,
+                      "l2": "working set > L2", "records_per_step": rec32},
+           "fp16": {"value": n / (ms16 * 1e-3), "ms_per_step": ms16, "records_per_step": rec16},
+           "direct_launches": {"value": n / (ms_direct * 1e-3), "ms_per_step": ms_direct},
+           "stage_ms_per_call": {k: v[0] for k, v in prof.items()}, "clocks": clocks}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -300,6 +382,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--images", type=int, default=N_IMAGES, help="images per rank (profiling runs)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal leg")
+    ap.add_argument("--workload", default="batch", choices=["batch", "uneven"],
+                    help="batch: 256 x 640x480 (default); uneven: 1024 uneven images resized to 640")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank = int(os.environ.get("RANK", "0"))
@@ -307,6 +391,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank)
+    if args.workload == "uneven":
+        if args.images == N_IMAGES:
+            args.images = 1024
+        return run_uneven(args, rank, world, local)
 
     imgs = make_batch(args.images, offset=rank * args.images)  # before any CUDA call
     import torch

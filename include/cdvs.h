@@ -80,6 +80,9 @@ typedef struct {
     int32_t use_proposal;      /* 1: the learned block proposal masks first-octave detection in
                                   cdvs_extract and cdvs_candidates (0; needs cdvs_set_proposal) */
     float proposal_threshold;  /* a 16x16 block is proposed when its probability exceeds this (0.5) */
+    int32_t max_side;          /* S0: an image whose larger side exceeds this is first resized by area
+                                  averaging to that side (0 = never; 640 for uneven batches); its
+                                  records are then in the resized image's pixels */
 } cdvs_params;
 
 typedef struct {
@@ -268,6 +271,25 @@ cdvs_status cdvs_dedupe_select_noalloc(const cdvs_keypoint *cand, int32_t n_cand
                                        int32_t height, const cdvs_params *params,
                                        cdvs_keypoint *sel_out, int32_t *sel_count,
                                        void *cuda_stream);
+
+/* enable = 1: calls of cdvs_extract with both CDVS_INPUT_DEVICE and
+ * CDVS_OUTPUT_DEVICE (and profiling off) capture their device work -- input
+ * tables, every kernel of the batch, the status read -- into a CUDA graph,
+ * update the context's executable graph with it in place (instantiating it
+ * again when the work changed shape) and launch that.  Results are
+ * unchanged.  0 turns it off and frees the graph. */
+cdvs_status cdvs_set_graph(cdvs_ctx *ctx, int32_t enable);
+
+/* S0 alone: each image whose larger side exceeds max_side is resized by area
+ * averaging (see cdvs_params.max_side), the others are copied.  Output image
+ * i is written to out (row pitch = its width) after images 0..i-1, and its
+ * size to out_sizes[i]; capacity is the size of out in bytes
+ * (UNSUPPORTED_SIZE when too small).  flags: CDVS_INPUT_DEVICE,
+ * CDVS_OUTPUT_DEVICE (out in device memory; out_sizes is always host
+ * memory).  Synchronous unless both flags are set. */
+cdvs_status cdvs_resize(cdvs_ctx *ctx, int32_t n_images, const uint8_t *const *images,
+                        const cdvs_image_desc *sizes, int32_t max_side, uint8_t *out, size_t capacity,
+                        cdvs_image_desc *out_sizes, uint32_t flags, void *cuda_stream);
 
 /* ---------------------------------------------------------------------------
  * Learned block proposal.  Not in the paper: an extension of its detector

@@ -36,7 +36,7 @@ PARAMS_DTYPE = np.dtype([
     ("ori_weight_sigma", "<f4"), ("desc_radius", "<f4"), ("cell_side", "<f4"),
     ("desc_weight_sigma", "<f4"), ("dedupe_dlog2", "<f4"),
     ("max_keypoints", "<i4"), ("max_orientations", "<i4"), ("upright", "<i4"), ("storage", "<i4"),
-    ("use_proposal", "<i4"), ("proposal_threshold", "<f4"),
+    ("use_proposal", "<i4"), ("proposal_threshold", "<f4"), ("max_side", "<i4"),
 ])
 KEYPOINT_DTYPE = np.dtype([
     ("x", "<f4"), ("y", "<f4"), ("sigma", "<f4"), ("theta", "<f4"), ("response", "<f4"),
@@ -44,7 +44,7 @@ KEYPOINT_DTYPE = np.dtype([
     ("reserved", "<i2"), ("image", "<i4"), ("parent_id", "<i4"),
 ])
 IMAGE_DESC_DTYPE = np.dtype([("width", "<i4"), ("height", "<i4"), ("pitch_bytes", "<i4")])
-assert PARAMS_DTYPE.itemsize == 80 and KEYPOINT_DTYPE.itemsize == 44
+assert PARAMS_DTYPE.itemsize == 84 and KEYPOINT_DTYPE.itemsize == 44
 PROPOSAL_PARAMS = 4817
 PROPOSAL_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "proposal_weights.npz")
 
@@ -58,7 +58,7 @@ EXPORTED = ["cdvs_params_default", "cdvs_create", "cdvs_destroy", "cdvs_last_err
             "cdvs_candidates", "cdvs_dedupe_select", "cdvs_describe", "cdvs_scale_space",
             "cdvs_rank_host", "cdvs_transform_ternary", "cdvs_profile", "cdvs_profile_read",
             "cdvs_dedupe_select_noalloc", "cdvs_set_proposal", "cdvs_proposal_logits",
-            "cdvs_proposal_train_step"]
+            "cdvs_proposal_train_step", "cdvs_resize", "cdvs_set_graph"]
 STAGES = ["detect", "select", "describe", "offsets", "pack", "detect_octave0", "proposal"]
 
 
@@ -98,6 +98,8 @@ def load(build_if_missing: bool = True):
         "cdvs_profile_read": (i32, [P, P, P, i32, i32]),
         "cdvs_dedupe_select_noalloc": (i32, [P, i32, i32, i32, P, P, P, P]),
         "cdvs_set_proposal": (i32, [P, P, i32]),
+        "cdvs_resize": (i32, [P, i32, P, P, i32, P, sz, P, u32, P]),
+        "cdvs_set_graph": (i32, [P, i32]),
         "cdvs_proposal_logits": (i32, [P, i32, P, P, P, i32, u32, P]),
         "cdvs_proposal_train_step": (i32, [P, P, i32, i32, i32, i32, P, P, P, P, P, P, P, i32, C.c_float, i32, P]),
     }
@@ -164,6 +166,26 @@ class Context:
         if st == CDVS_OK or (allow_truncated and st == CDVS_CAPACITY_TRUNCATED):
             return st
         raise CdvsError(st, self.last_error())
+
+    def set_graph(self, enable: bool):
+        """Device-resident extractions through one CUDA graph (cdvs_set_graph)."""
+        self._check(self._L.cdvs_set_graph(self.handle, 1 if enable else 0))
+
+    # ------------------------------------------------------------ S0
+    def resize(self, images, max_side):
+        """cdvs_resize on host images: the list of resized uint8 arrays."""
+        imgs, sizes, ptrs = self._host_images(images)
+        out_sizes = np.zeros(len(imgs), IMAGE_DESC_DTYPE)
+        cap = sum(a.size for a in imgs) + 16
+        out = np.zeros(cap, np.uint8)
+        self._check(self._L.cdvs_resize(self.handle, len(imgs), C.cast(ptrs, C.c_void_p), sizes.ctypes.data,
+                                        int(max_side), out.ctypes.data, cap, out_sizes.ctypes.data, 0, None))
+        res, o = [], 0
+        for d in out_sizes:
+            w, h = int(d["width"]), int(d["height"])
+            res.append(out[o:o + w * h].reshape(h, w).copy())
+            o += w * h
+        return res
 
     # ------------------------------------------------------------ proposal
     def set_proposal(self, theta):

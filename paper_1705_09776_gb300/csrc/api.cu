@@ -50,6 +50,15 @@ struct cdvs_ctx {
       rec_total, out_kp, out_desc, out_count, plans, tile_prefix, status, input, dump, stage_kp, stage_desc;
   // learned block proposal: parameters, per-call image table, logits, tile modes, training workspace
   DevBuf prop_theta, prop_imgs, prop_logits, prop_mode, prop_ws;
+  DevBuf resized, resize_jobs;  // S0: resized images and their job table
+  // page-locked staging of the small per-call tables (one buffer per upload
+  // site, so no upload overwrites another one still in flight), and the CUDA
+  // graph that device-resident extractions are replayed through
+  HostBuf pin_plans, pin_prefix, pin_prop, pin_jobs, pin_plans2;
+  bool graph = false;
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t gstream = nullptr;  // capture stream when the caller passes the legacy default stream
+  cudaEvent_t gev = nullptr;
   bool prop_set = false;
   HostBuf small;  // pinned: status word + record total
   std::vector<ImgPlan> h_plans;
@@ -122,6 +131,17 @@ cudaError_t ensure(DevBuf& b, size_t bytes) {
   }
   b.bytes = nb;
   return cudaSuccess;
+}
+
+cudaError_t ensure_host(HostBuf& b, size_t bytes);
+
+// Host table -> device through a page-locked copy (capturable in a graph).
+cudaError_t upload(HostBuf& stage, void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) return cudaSuccess;
+  cudaError_t e = ensure_host(stage, bytes);
+  if (e != cudaSuccess) return e;
+  std::memcpy(stage.p, src, bytes);
+  return cudaMemcpyAsync(dst, stage.p, bytes, cudaMemcpyHostToDevice, s);
 }
 
 cudaError_t ensure_host(HostBuf& b, size_t bytes) {
@@ -228,6 +248,8 @@ cdvs_status check_params(cdvs_ctx* c, const cdvs_params* p) {
   if (p->storage != CDVS_STORAGE_FP32 && p->storage != CDVS_STORAGE_FP16)
     return fail(c, CDVS_INVALID_ARGUMENT, "storage must be CDVS_STORAGE_FP32 or CDVS_STORAGE_FP16");
   if (p->use_proposal != 0 && p->use_proposal != 1) return fail(c, CDVS_INVALID_ARGUMENT, "use_proposal must be 0 or 1");
+  if (p->max_side != 0 && (p->max_side < 16 || p->max_side > 32768))
+    return fail(c, CDVS_INVALID_ARGUMENT, "max_side must be 0 or 16..32768");
   if (p->use_proposal && !(p->proposal_threshold > 0.0f && p->proposal_threshold < 1.0f))
     return fail(c, CDVS_INVALID_ARGUMENT, "proposal_threshold must be in (0, 1)");
   float t[kMaxRadius + 1];
@@ -356,11 +378,10 @@ cdvs_status stage_inputs(cdvs_ctx* c, int n, const uint8_t* const* images, const
   if ((e = ensure(c->plans, sizeof(ImgPlan) * n)) != cudaSuccess) return cuda_fail(c, e, "plans");
   if ((e = ensure(c->tile_prefix, sizeof(int) * c->h_prefix.size())) != cudaSuccess)
     return cuda_fail(c, e, "tile lists");
-  if ((e = cudaMemcpyAsync(c->plans.p, c->h_plans.data(), sizeof(ImgPlan) * n, cudaMemcpyHostToDevice, s)) !=
-      cudaSuccess)
+  if ((e = upload(c->pin_plans, c->plans.p, c->h_plans.data(), sizeof(ImgPlan) * n, s)) != cudaSuccess)
     return cuda_fail(c, e, "plan upload");
-  if ((e = cudaMemcpyAsync(c->tile_prefix.p, c->h_prefix.data(), sizeof(int) * c->h_prefix.size(),
-                           cudaMemcpyHostToDevice, s)) != cudaSuccess)
+  if ((e = upload(c->pin_prefix, c->tile_prefix.p, c->h_prefix.data(), sizeof(int) * c->h_prefix.size(), s)) !=
+      cudaSuccess)
     return cuda_fail(c, e, "tile list upload");
   return CDVS_OK;
 }
@@ -486,6 +507,11 @@ struct PointsIn {
 };
 
 // The shared pipeline behind cdvs_extract / cdvs_candidates / cdvs_describe.
+const uint32_t* prop_frag(cdvs_ctx* c) {
+  const size_t pbytes = (sizeof(float) * kPropParams + 255) & ~(size_t)255;
+  return reinterpret_cast<const uint32_t*>(static_cast<const uint8_t*>(c->prop_theta.p) + pbytes);
+}
+
 // The proposal network's per-image table (sizes of every layer, first logit)
 // for images whose device pixels are srcs[i]; returns the number of logits.
 size_t prop_table(int n, const cdvs_image_desc* sizes, const uint8_t* const* srcs, std::vector<PropImage>& t,
@@ -531,11 +557,10 @@ cdvs_status run_proposal_mask(cdvs_ctx* c, int n, const cdvs_image_desc* sizes, 
       (e = ensure(c->prop_logits, sizeof(float) * n_logits)) != cudaSuccess ||
       (e = ensure(c->prop_mode, (size_t)n_tiles * 4 + n_logits)) != cudaSuccess)
     return cuda_fail(c, e, "proposal workspace");
-  if ((e = cudaMemcpyAsync(c->prop_imgs.p, t.data(), sizeof(PropImage) * n, cudaMemcpyHostToDevice, s)) !=
-      cudaSuccess)
+  if ((e = upload(c->pin_prop, c->prop_imgs.p, t.data(), sizeof(PropImage) * n, s)) != cudaSuccess)
     return cuda_fail(c, e, "proposal table upload");
   const PropImage* d_t = static_cast<const PropImage*>(c->prop_imgs.p);
-  if ((e = launch_proposal_infer(d_t, n, max_th, max_tw, static_cast<const float*>(c->prop_theta.p),
+  if ((e = launch_proposal_infer(d_t, n, max_th, max_tw, static_cast<const float*>(c->prop_theta.p), prop_frag(c),
                                  static_cast<float*>(c->prop_logits.p), s)) != cudaSuccess)
     return cuda_fail(c, e, "proposal launch");
   // a descriptor disc of a first-octave point reaches this far (image px)
@@ -551,6 +576,66 @@ cdvs_status run_proposal_mask(cdvs_ctx* c, int n, const cdvs_image_desc* sizes, 
                             nx, mb, reinterpret_cast<uint16_t*>(mb + 2 * (size_t)n_tiles), mb + 4 * (size_t)n_tiles,
                             mb + (size_t)n_tiles, s)) != cudaSuccess)
     return cuda_fail(c, e, "tile mode launch");
+  return CDVS_OK;
+}
+
+// S0 target size: the larger side becomes max_side, the other side is scaled
+// and rounded to the nearest integer, ties to even (at least 1).
+void resize_target(int W, int H, int max_side, int& W2, int& H2) {
+  W2 = W;
+  H2 = H;
+  if (max_side <= 0 || std::max(W, H) <= max_side) return;
+  auto rhe = [](long long num, long long den) {
+    long long q = num / den, r = num - q * den;
+    if (2 * r > den || (2 * r == den && (q & 1))) ++q;
+    return q;
+  };
+  if (W >= H) {
+    W2 = max_side;
+    H2 = (int)std::max(1LL, rhe((long long)H * max_side, W));
+  } else {
+    H2 = max_side;
+    W2 = (int)std::max(1LL, rhe((long long)W * max_side, H));
+  }
+}
+
+// S0 on the device: every resized image into c->resized (row pitch a
+// multiple of 16), and the plans pointed at them.
+cdvs_status run_resize(cdvs_ctx* c, int n, const cdvs_image_desc* sizes, const std::vector<cdvs_image_desc>& eff,
+                       cudaStream_t s) {
+  std::vector<ResizeJob> jobs;
+  size_t total = 0;
+  std::vector<size_t> off(n, 0);
+  for (int i = 0; i < n; ++i)
+    if (eff[i].width != sizes[i].width || eff[i].height != sizes[i].height) {
+      off[i] = total;
+      total += ((size_t)eff[i].pitch_bytes * eff[i].height + 255) & ~(size_t)255;
+    }
+  cudaError_t e;
+  if ((e = ensure(c->resized, total)) != cudaSuccess) return cuda_fail(c, e, "resize buffer");
+  int max_pixels = 0;
+  for (int i = 0; i < n; ++i)
+    if (eff[i].width != sizes[i].width || eff[i].height != sizes[i].height) {
+      ResizeJob j;
+      j.src = c->h_plans[i].src;
+      j.W = sizes[i].width;
+      j.H = sizes[i].height;
+      j.pitch = sizes[i].pitch_bytes;
+      j.dst = static_cast<uint8_t*>(c->resized.p) + off[i];
+      j.W2 = eff[i].width;
+      j.H2 = eff[i].height;
+      j.pitch2 = eff[i].pitch_bytes;
+      jobs.push_back(j);
+      c->h_plans[i].src = j.dst;
+      max_pixels = std::max(max_pixels, j.W2 * j.H2);
+    }
+  if (jobs.empty()) return CDVS_OK;
+  if ((e = ensure(c->resize_jobs, sizeof(ResizeJob) * jobs.size())) != cudaSuccess ||
+      (e = upload(c->pin_jobs, c->resize_jobs.p, jobs.data(), sizeof(ResizeJob) * jobs.size(), s)) != cudaSuccess ||
+      (e = launch_resize(static_cast<const ResizeJob*>(c->resize_jobs.p), (int)jobs.size(), max_pixels, s)) !=
+          cudaSuccess ||
+      (e = upload(c->pin_plans2, c->plans.p, c->h_plans.data(), sizeof(ImgPlan) * n, s)) != cudaSuccess)
+    return cuda_fail(c, e, "resize");
   return CDVS_OK;
 }
 
@@ -577,9 +662,23 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
   cudaError_t e = cudaSetDevice(c->device);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
 
+  // S0: the sizes the method sees
+  std::vector<cdvs_image_desc> eff(sizes, sizes + n);
+  bool any_resize = false;
+  for (int i = 0; i < n; ++i) {
+    int W2, H2;
+    resize_target(sizes[i].width, sizes[i].height, p.max_side, W2, H2);
+    if (W2 != sizes[i].width || H2 != sizes[i].height) {
+      if (sizes[i].pitch_bytes < sizes[i].width) return fail(c, CDVS_INVALID_ARGUMENT, "pitch_bytes < width");
+      eff[i].width = W2;
+      eff[i].height = H2;
+      eff[i].pitch_bytes = (W2 + 15) & ~15;
+      any_resize = true;
+    }
+  }
   long long level_elems, max_pixels;
   int max_oct;
-  if ((st = plan_batch(c, n, sizes, p, level_elems, max_oct, max_pixels)) != CDVS_OK) return st;
+  if ((st = plan_batch(c, n, eff.data(), p, level_elems, max_oct, max_pixels)) != CDVS_OK) return st;
   const int cap = cand_capacity(max_pixels);
   const int N = p.max_keypoints;
   const size_t slots = (size_t)n * N;
@@ -600,6 +699,36 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
       (e = ensure_host(c->small, sizeof(int) * 4)) != cudaSuccess)
     return cuda_fail(c, e, "workspace");
 
+  // Device-resident extraction can run as one CUDA graph: the stream work
+  // below is captured, the cached executable graph is updated in place (or
+  // instantiated again when the work changed shape) and launched.
+  const bool graph = c->graph && mode == kExtract && (flags & CDVS_INPUT_DEVICE) && (flags & CDVS_OUTPUT_DEVICE) &&
+                     !c->prof;
+  struct CaptureGuard {  // ends an abandoned capture on early returns
+    cudaStream_t s;
+    bool on = false;
+    ~CaptureGuard() {
+      if (!on) return;
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(s, &g);
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+    }
+  } capture{s};
+  if (graph) {
+    if (!s) {  // the legacy default stream cannot be captured: work on our own stream after it
+      if (!c->gstream && ((e = cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking)) != cudaSuccess ||
+                          (e = cudaEventCreateWithFlags(&c->gev, cudaEventDisableTiming)) != cudaSuccess))
+        return cuda_fail(c, e, "graph stream");
+      if ((e = cudaEventRecord(c->gev, s)) != cudaSuccess || (e = cudaStreamWaitEvent(c->gstream, c->gev, 0)) != cudaSuccess)
+        return cuda_fail(c, e, "graph stream");
+      s = c->gstream;
+      capture.s = s;
+    }
+    if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+      return cuda_fail(c, e, "graph capture");
+    capture.on = true;
+  }
   if ((st = stage_inputs(c, n, images, sizes, flags, s)) != CDVS_OK) return st;
   if ((e = cudaMemsetAsync(c->cand_count.p, 0, sizeof(int) * n, s)) != cudaSuccess ||
       (e = cudaMemsetAsync(c->status.p, 0, sizeof(int) * 4, s)) != cudaSuccess)
@@ -607,15 +736,19 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
   cudaEvent_t ev = prof_begin(c, s);
   const uint8_t* tile_mode = nullptr;
   const uint16_t* block_mask = nullptr;
-  if (p.use_proposal && (mode == kExtract || mode == kCandidates)) {
-    // the network reads the whole batch: every upload first, in one piece
+  const bool proposal = p.use_proposal && (mode == kExtract || mode == kCandidates);
+  if (proposal || any_resize) {
+    // the resize and the network read the whole batch: every upload first
     for (int k = 0; k < c->n_chunks; ++k)
       if ((e = issue_upload(c, k, s)) != cudaSuccess) return cuda_fail(c, e, "image upload");
     for (auto& u : c->uploads) u.clear();
     c->n_chunks = 1;
     c->chunk_begin[1] = n;
+  }
+  if (any_resize && (st = run_resize(c, n, sizes, eff, s)) != CDVS_OK) return st;
+  if (proposal) {
     cudaEvent_t evp = prof_begin(c, s);
-    if ((st = run_proposal_mask(c, n, sizes, p, s)) != CDVS_OK) return st;
+    if ((st = run_proposal_mask(c, n, eff.data(), p, s)) != CDVS_OK) return st;
     prof_end(c, 6, 2, evp, s);
     tile_mode = static_cast<const uint8_t*>(c->prop_mode.p);
     block_mask = reinterpret_cast<const uint16_t*>(tile_mode + 2 * (size_t)c->h_prefix[n]);
@@ -751,9 +884,28 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
   if ((e = launch_copy(d, c->n_sms, s)) != cudaSuccess) return cuda_fail(c, e, "copy launch");
   prof_end(c, 4, 1, ev, s);
   if ((e = cudaMemcpyAsync(h_small, c->status.p, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(h_small + 1, c->rec_total.p, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+      (e = cudaMemcpyAsync(h_small + 1, c->rec_total.p, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return cuda_fail(c, e, "status readback");
+  if (graph) {
+    cudaGraph_t g = nullptr;
+    capture.on = false;
+    if ((e = cudaStreamEndCapture(s, &g)) != cudaSuccess) return cuda_fail(c, e, "graph capture");
+    if (c->gexec) {
+      cudaGraphExecUpdateResultInfo info;
+      if (cudaGraphExecUpdate(c->gexec, g, &info) != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+      }
+    }
+    if (!c->gexec && (e = cudaGraphInstantiate(&c->gexec, g, 0)) != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return cuda_fail(c, e, "graph instantiation");
+    }
+    cudaGraphDestroy(g);
+    if ((e = cudaGraphLaunch(c->gexec, s)) != cudaSuccess) return cuda_fail(c, e, "graph launch");
+  }
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(c, e, "status readback");
   const int status_bits = h_small[0];
   const int total = h_small[1];
   if (!dev_out) {
@@ -795,6 +947,7 @@ void cdvs_params_default(cdvs_params* p) {
   p->storage = CDVS_STORAGE_FP32;
   p->use_proposal = 0;
   p->proposal_threshold = 0.5f;
+  p->max_side = 0;
 }
 
 cdvs_status cdvs_create(cdvs_ctx** out, int device, size_t workspace_bytes_hint) {
@@ -825,10 +978,16 @@ void cdvs_destroy(cdvs_ctx* c) {
                     &c->sel,     &c->sel_count, &c->ori_theta, &c->ori_count, &c->rec_off,
                     &c->rec_total, &c->out_kp, &c->out_desc, &c->out_count, &c->plans,
                     &c->tile_prefix, &c->status, &c->input, &c->dump, &c->stage_kp, &c->stage_desc,
-                    &c->prop_theta, &c->prop_imgs, &c->prop_logits, &c->prop_mode, &c->prop_ws};
+                    &c->prop_theta, &c->prop_imgs, &c->prop_logits, &c->prop_mode, &c->prop_ws,
+                    &c->resized, &c->resize_jobs};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (c->small.p) cudaFreeHost(c->small.p);
+  for (HostBuf* h : {&c->pin_plans, &c->pin_prefix, &c->pin_prop, &c->pin_jobs, &c->pin_plans2})
+    if (h->p) cudaFreeHost(h->p);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->gstream) cudaStreamDestroy(c->gstream);
+  if (c->gev) cudaEventDestroy(c->gev);
   for (const ProfRec& r : c->recs) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -1026,12 +1185,104 @@ cdvs_status cdvs_profile(cdvs_ctx* c, int32_t enable) {
   return CDVS_OK;
 }
 
+cdvs_status cdvs_set_graph(cdvs_ctx* c, int32_t enable) {
+  if (!c || (enable != 0 && enable != 1)) return CDVS_INVALID_ARGUMENT;
+  c->graph = enable != 0;
+  if (!c->graph && c->gexec) {
+    cudaSetDevice(c->device);
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  return CDVS_OK;
+}
+
+cdvs_status cdvs_resize(cdvs_ctx* c, int32_t n, const uint8_t* const* images, const cdvs_image_desc* sizes,
+                        int32_t max_side, uint8_t* out, size_t capacity, cdvs_image_desc* out_sizes, uint32_t flags,
+                        void* cuda_stream) {
+  if (!c) return CDVS_INVALID_ARGUMENT;
+  if (n < 0 || n > kMaxBatch) return fail(c, CDVS_INVALID_ARGUMENT, "n_images must be in 0..4096");
+  if (n == 0) return CDVS_OK;
+  if (!images || !sizes || !out || !out_sizes) return fail(c, CDVS_INVALID_ARGUMENT, "NULL argument");
+  if (max_side < 0 || max_side > 32768) return fail(c, CDVS_INVALID_ARGUMENT, "max_side must be 0..32768");
+  size_t need = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!images[i]) return fail(c, CDVS_INVALID_ARGUMENT, "image pointer is NULL");
+    if (sizes[i].width < 1 || sizes[i].height < 1 || sizes[i].width > 32768 || sizes[i].height > 32768 ||
+        sizes[i].pitch_bytes < sizes[i].width)
+      return fail(c, CDVS_UNSUPPORTED_SIZE, "image sizes must be 1..32768 with pitch >= width");
+    int W2, H2;
+    resize_target(sizes[i].width, sizes[i].height, max_side, W2, H2);
+    out_sizes[i].width = W2;
+    out_sizes[i].height = H2;
+    out_sizes[i].pitch_bytes = W2;
+    need += (size_t)W2 * H2;
+  }
+  if (need > capacity) return fail(c, CDVS_UNSUPPORTED_SIZE, "out too small");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e;
+  if ((e = cudaSetDevice(c->device)) != cudaSuccess) return cuda_fail(c, e, "device");
+  // inputs on the device (staged when on the host)
+  std::vector<const uint8_t*> src(images, images + n);
+  if (!(flags & CDVS_INPUT_DEVICE)) {
+    size_t total = 0;
+    std::vector<size_t> off(n);
+    for (int i = 0; i < n; ++i) {
+      off[i] = total;
+      total += ((size_t)sizes[i].pitch_bytes * sizes[i].height + 255) & ~(size_t)255;
+    }
+    if ((e = ensure(c->input, total)) != cudaSuccess) return cuda_fail(c, e, "input staging");
+    for (int i = 0; i < n; ++i) {
+      src[i] = static_cast<uint8_t*>(c->input.p) + off[i];
+      if ((e = cudaMemcpyAsync(const_cast<uint8_t*>(src[i]), images[i], (size_t)sizes[i].pitch_bytes * sizes[i].height,
+                               cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_fail(c, e, "image upload");
+    }
+  }
+  const bool dev_out = (flags & CDVS_OUTPUT_DEVICE) != 0;
+  if (!dev_out && (e = ensure(c->resized, need)) != cudaSuccess) return cuda_fail(c, e, "output staging");
+  uint8_t* dst = dev_out ? out : static_cast<uint8_t*>(c->resized.p);
+  std::vector<ResizeJob> jobs;
+  size_t o = 0;
+  int max_pixels = 0;
+  for (int i = 0; i < n; ++i) {
+    const int W2 = out_sizes[i].width, H2 = out_sizes[i].height;
+    if (W2 == sizes[i].width && H2 == sizes[i].height) {
+      if ((e = cudaMemcpy2DAsync(dst + o, W2, src[i], sizes[i].pitch_bytes, W2, H2, cudaMemcpyDeviceToDevice, s)) !=
+          cudaSuccess)
+        return cuda_fail(c, e, "copy");
+    } else {
+      jobs.push_back(ResizeJob{src[i], sizes[i].width, sizes[i].height, sizes[i].pitch_bytes, dst + o, W2, H2, W2});
+      max_pixels = std::max(max_pixels, W2 * H2);
+    }
+    o += (size_t)W2 * H2;
+  }
+  if (!jobs.empty() &&
+      ((e = ensure(c->resize_jobs, sizeof(ResizeJob) * jobs.size())) != cudaSuccess ||
+       (e = cudaMemcpyAsync(c->resize_jobs.p, jobs.data(), sizeof(ResizeJob) * jobs.size(), cudaMemcpyHostToDevice,
+                            s)) != cudaSuccess ||
+       (e = launch_resize(static_cast<const ResizeJob*>(c->resize_jobs.p), (int)jobs.size(), max_pixels, s)) !=
+           cudaSuccess))
+    return cuda_fail(c, e, "resize");
+  if (!dev_out && (e = cudaMemcpyAsync(out, dst, need, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(c, e, "readback");
+  if ((!dev_out || !(flags & CDVS_INPUT_DEVICE)) && (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return cuda_fail(c, e, "resize");
+  return CDVS_OK;
+}
+
 cdvs_status cdvs_set_proposal(cdvs_ctx* c, const float* params, int32_t n_params) {
   if (!c) return CDVS_INVALID_ARGUMENT;
   if (!params || n_params != kPropParams) return fail(c, CDVS_INVALID_ARGUMENT, "need CDVS_PROPOSAL_PARAMS floats");
   cudaError_t e;
-  if ((e = cudaSetDevice(c->device)) != cudaSuccess || (e = ensure(c->prop_theta, sizeof(float) * kPropParams)) != cudaSuccess ||
-      (e = cudaMemcpy(c->prop_theta.p, params, sizeof(float) * kPropParams, cudaMemcpyHostToDevice)) != cudaSuccess)
+  // the parameters, then the tensor-core B fragments of conv2 and conv3
+  std::vector<uint32_t> frag(kPropFragWords);
+  pack_proposal_fragments(params, frag.data());
+  const size_t pbytes = (sizeof(float) * kPropParams + 255) & ~(size_t)255;
+  if ((e = cudaSetDevice(c->device)) != cudaSuccess ||
+      (e = ensure(c->prop_theta, pbytes + sizeof(uint32_t) * kPropFragWords)) != cudaSuccess ||
+      (e = cudaMemcpy(c->prop_theta.p, params, sizeof(float) * kPropParams, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(static_cast<uint8_t*>(c->prop_theta.p) + pbytes, frag.data(), sizeof(uint32_t) * kPropFragWords,
+                      cudaMemcpyHostToDevice)) != cudaSuccess)
     return cuda_fail(c, e, "proposal parameters");
   c->prop_set = true;
   return CDVS_OK;
@@ -1081,7 +1332,7 @@ cdvs_status cdvs_proposal_logits(cdvs_ctx* c, int32_t n, const uint8_t* const* i
     return cuda_fail(c, e, "proposal workspace");
   float* out = dev_out ? logits_out : static_cast<float*>(c->prop_logits.p);
   if ((e = launch_proposal_infer(static_cast<const PropImage*>(c->prop_imgs.p), n, max_th, max_tw,
-                                 static_cast<const float*>(c->prop_theta.p), out, s)) != cudaSuccess)
+                                 static_cast<const float*>(c->prop_theta.p), prop_frag(c), out, s)) != cudaSuccess)
     return cuda_fail(c, e, "proposal launch");
   if (!dev_out && ((e = cudaMemcpyAsync(logits_out, out, sizeof(float) * n_logits, cudaMemcpyDeviceToHost, s)) !=
                        cudaSuccess ||

@@ -173,12 +173,23 @@ struct PropTrainArgs {
 };
 
 size_t proposal_infer_smem();
+constexpr int kPropFragWords = 2 * 9 * 2 * 32 * 2;  // conv2/conv3 B fragments (uint32)
+void pack_proposal_fragments(const float* theta, uint32_t* frag);
 cudaError_t launch_proposal_infer(const PropImage* d_imgs, int n_images, int max_th, int max_tw, const float* theta,
-                                  float* logits, cudaStream_t s);
+                                  const uint32_t* frag, float* logits, cudaStream_t s);
 cudaError_t launch_tile_mode(const PropImage* d_imgs, const ImgPlan* plans, const int* tile_prefix, int n_images,
                              int max_blocks, int max_tiles, const float* logits, float zt, int dil, int ny, int nx,
                              uint8_t* mode, uint16_t* block_mask, uint8_t* near, uint8_t* det, cudaStream_t s);
 size_t proposal_train_floats(int B, int H, int W, int n_sms);
 cudaError_t run_proposal_train(const PropTrainArgs& t, float* ws, int n_sms, cudaStream_t s);
+
+// ---------------------------------------------------------------- S0 resize
+struct ResizeJob {
+  const uint8_t* src;
+  int W, H, pitch;
+  uint8_t* dst;
+  int W2, H2, pitch2;
+};
+cudaError_t launch_resize(const ResizeJob* d_jobs, int n_jobs, int max_pixels, cudaStream_t s);
 
 }  // namespace cdvs

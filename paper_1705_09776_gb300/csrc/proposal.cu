@@ -26,6 +26,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "cdvs_internal.cuh"
 
@@ -329,24 +330,21 @@ __device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
   return *reinterpret_cast<const unsigned*>(&v);
 }
 
-// B fragments of one 16 -> 16 layer for this lane: for tap t and output half
-// h, reg 0 holds W[co][ci][t] for ci = 2q, 2q + 1 and reg 1 for ci = 2q + 8,
-// 2q + 9, with co = 8h + lane / 4 and q = lane % 4.
-__device__ __forceinline__ void load_bfrag(const float* theta, int w_off, int lane, unsigned (&bw)[9][2][2]) {
-  const int q = lane & 3, nn = lane >> 2;
+// B fragments of one 16 -> 16 layer for this lane, prepacked by the host
+// (pack_proposal_fragments): one coalesced 8-byte load per tap and half.
+__device__ __forceinline__ void load_bfrag(const uint2* frag, int layer, int lane, unsigned (&bw)[9][2][2]) {
 #pragma unroll
   for (int t = 0; t < 9; ++t)
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int co = 8 * h + nn;
-      const float* w = theta + w_off + co * kC * 9 + t;
-      bw[t][h][0] = pack_bf16(w[(2 * q) * 9], w[(2 * q + 1) * 9]);
-      bw[t][h][1] = pack_bf16(w[(2 * q + 8) * 9], w[(2 * q + 9) * 9]);
+      const uint2 v = frag[((layer * 9 + t) * 2 + h) * 32 + lane];
+      bw[t][h][0] = v.x;
+      bw[t][h][1] = v.y;
     }
 }
 
 __global__ void __launch_bounds__(kInfThreads, 2) proposal_infer_kernel(const PropImage* imgs, const float* theta,
-                                                                     float* logits) {
+                                                                        const uint2* frag, float* logits) {
   extern __shared__ float4 smem4[];
   uint8_t* in_s = reinterpret_cast<uint8_t*>(smem4);
   __nv_bfloat16* a1_s = reinterpret_cast<__nv_bfloat16*>(in_s + (size_t)kInY * kInP);
@@ -427,7 +425,7 @@ __global__ void __launch_bounds__(kInfThreads, 2) proposal_infer_kernel(const Pr
   // the 34 x 18 region), one K = 16 contraction per tap
   {
     unsigned bw[9][2][2];
-    load_bfrag(theta, kOffW2, lane, bw);
+    load_bfrag(frag, 0, lane, bw);
     for (int t = warp; t < kA2Tiles; t += kInfThreads / 32) {
       // this lane's ldmatrix row: position 16 t + lane % 16 (clamped), k half lane / 16
       const int pr = min(16 * t + (lane & 15), kA2X * kA2Y - 1);
@@ -464,7 +462,7 @@ __global__ void __launch_bounds__(kInfThreads, 2) proposal_infer_kernel(const Pr
   // CTA, row i = position (4 (t / 8) + i / 4, 4 (t % 8) + i % 4)
   {
     unsigned bw[9][2][2];
-    load_bfrag(theta, kOffW3, lane, bw);
+    load_bfrag(frag, 1, lane, bw);
     for (int t = warp; t < kRBX * kRBY; t += kInfThreads / 32) {
       const int cy = t / kRBX, cx = t - (t / kRBX) * kRBX;
       const int ty = by0 + cy, tx = bx0 + cx;
@@ -586,14 +584,38 @@ __global__ void tile_mode_kernel(const ImgPlan* plans, const int* tile_prefix, i
 // ---------------------------------------------------------------- launchers
 size_t proposal_infer_smem() { return kInfSmem; }
 
+// The B fragments of conv2 (layer 0) and conv3 (layer 1) for every lane:
+// frag[((layer 9 + t) 2 + h) 32 + lane] = {W[co][2q, 2q + 1][t], W[co][2q + 8, 2q + 9][t]} in BF16 (round to
+// nearest even, low half = lower ci), co = 8h + lane / 4, q = lane % 4: the register layout of the B operand of
+// mma.m16n8k16 (.col).  n = kPropFragWords uint32 words.
+void pack_proposal_fragments(const float* theta, uint32_t* frag) {
+  auto bits = [](float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    return (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;  // BF16, round to nearest even
+  };
+  const int w_off[2] = {kOffW2, kOffW3};
+  for (int layer = 0; layer < 2; ++layer)
+    for (int t = 0; t < 9; ++t)
+      for (int h = 0; h < 2; ++h)
+        for (int lane = 0; lane < 32; ++lane) {
+          const int q = lane & 3, co = 8 * h + (lane >> 2);
+          const float* w = theta + w_off[layer] + co * kC * 9 + t;
+          uint32_t* o = frag + 2 * (((layer * 9 + t) * 2 + h) * 32 + lane);
+          o[0] = bits(w[(2 * q) * 9]) | (bits(w[(2 * q + 1) * 9]) << 16);
+          o[1] = bits(w[(2 * q + 8) * 9]) | (bits(w[(2 * q + 9) * 9]) << 16);
+        }
+}
+
 cudaError_t launch_proposal_infer(const PropImage* d_imgs, int n_images, int max_th, int max_tw, const float* theta,
-                                  float* logits, cudaStream_t s) {
+                                  const uint32_t* frag, float* logits, cudaStream_t s) {
   if (n_images <= 0) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(proposal_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kInfSmem);
   if (e != cudaSuccess) return e;
   dim3 grid((max_tw + kRBX - 1) / kRBX, (max_th + kRBY - 1) / kRBY, n_images);
-  proposal_infer_kernel<<<grid, kInfThreads, kInfSmem, s>>>(d_imgs, theta, logits);
+  proposal_infer_kernel<<<grid, kInfThreads, kInfSmem, s>>>(d_imgs, theta, reinterpret_cast<const uint2*>(frag),
+                                                            logits);
   return cudaGetLastError();
 }
 
