@@ -52,15 +52,15 @@ def make_batch(n, offset=0):
     return np.stack(imgs)
 
 
-def detect_counts(p):
-    """Algorithmic FLOPs and bytes of the detection stage (K1) per 640x480 image
+def detect_counts(p, width=None, height=None):
+    """Algorithmic FLOPs and bytes of the detection stage (K1) per image (640x480 by default)
     and per octave, FP32 levels: S1 filters (2 passes x 2 flops per tap,
     identity levels free), S2 Laplacian (7 flops per level), S3 cubic fit (32),
     S4 roots (25); bytes = octave base read + every level written once (level 0
     of octaves >= 1 is written by the previous octave as its decimated base)."""
     s = [float(p["sigma0"][0]) * 2 ** (k / 3) for k in range(4)]
     flops, byts = [], []
-    w, h = WIDTH, HEIGHT
+    w, h = width or WIDTH, height or HEIGHT
     for o in range(int(p["num_octaves"][0])):
         base = float(p["sigma_in"][0]) if o == 0 else float(p["sigma0"][0])
         per_px = 0.0
@@ -371,6 +371,96 @@ def run_uneven(args, rank, world, local):
     ctx.close()
 
 
+HIGHRES_W, HIGHRES_H, HIGHRES_SEED = 2048, 1536, 5
+
+
+def _gen_highres(i):
+    from paper_1705_09776_gb300 import synth
+    k = HIGHRES_W * HIGHRES_H / (WIDTH * HEIGHT)
+    return synth.blob_image(synth.image_seed(HIGHRES_SEED, i), HIGHRES_W, HIGHRES_H, n_blobs=int(round(200 * k)),
+                            sigma_range=(1.5 * 3.2, 20.0 * 3.2))
+
+
+def run_highres(args, rank, world, local):
+    """High-resolution stress: 2048 x 1536 images (blob count by area, blob
+    sizes x3.2), 6 octaves, up to 2000 points each; plain FP32 against FP16
+    level storage with the learned block proposal, device-resident."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        imgs = np.stack(pool.map(_gen_highres, range(rank * args.images, (rank + 1) * args.images)))
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1705_09776_gb300 import cdvs
+    n, H, W = imgs.shape
+    d_img = torch.from_numpy(imgs).cuda()
+    ptrs = [d_img.data_ptr() + i * H * W for i in range(n)]
+    sizes = np.array([(W, H, W)] * n, cdvs.IMAGE_DESC_DTYPE)
+    N = 2000
+    cap = n * N * 4
+    ctx = cdvs.Context(local)
+    stream = torch.cuda.current_stream()
+    d_kp = torch.zeros(cap * cdvs.KEYPOINT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    d_desc = torch.zeros(cap, 128, dtype=torch.float32, device="cuda")
+    d_cnt = torch.zeros(n, dtype=torch.int32, device="cuda")
+    flags = cdvs.CDVS_INPUT_DEVICE | cdvs.CDVS_OUTPUT_DEVICE
+
+    def call(p):
+        ctx.extract_raw(n, ptrs, sizes, p, d_kp, d_desc, cap, d_cnt, flags, stream)
+
+    def timed(p):
+        for _ in range(args.warmup):
+            call(p)
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        ctx.profile_read(reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            call(p)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = ctx.profile_read(reset=True)
+        ctx.profile(False)
+        tot = int(d_cnt.sum().item())
+        kp = d_kp[:tot * cdvs.KEYPOINT_DTYPE.itemsize].cpu().numpy().view(cdvs.KEYPOINT_DTYPE).copy()
+        return e0.elapsed_time(e1) / args.steps, kp, {k: v[0] / args.steps for k, v in prof.items()}
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    p32 = cdvs.params(num_octaves=6, max_keypoints=N)
+    ms32, kp32, st32 = timed(p32)
+    p16 = cdvs.params(num_octaves=6, max_keypoints=N, storage=cdvs.CDVS_STORAGE_FP16)
+    ms16, kp16, st16 = timed(p16)
+    learned = None
+    if os.path.exists(cdvs.PROPOSAL_WEIGHTS):
+        theta, thr = cdvs.load_proposal_weights()
+        ctx.set_proposal(theta)
+        pl = cdvs.params(num_octaves=6, max_keypoints=N, storage=cdvs.CDVS_STORAGE_FP16, use_proposal=1,
+                         proposal_threshold=thr)
+        msl, kpl, stl = timed(pl)
+        base = record_keys(kp16)
+        learned = {"value": n / (msl * 1e-3), "ms_per_step": msl, "threshold": thr,
+                   "recall_vs_fp16_plain": len(base & record_keys(kpl)) / max(len(base), 1),
+                   "stage_ms_per_step": stl,
+                   "note": "network trained on 640x480 images only"}
+    clocks = sampler.stop()
+    flops_o, bytes_o = detect_counts(p32, W, H)
+    out = {"metric": METRIC, "value": n / (ms32 * 1e-3), "unit": "images/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"{n}x {W}x{H} u8 seeded blob images (blobs x3.2, count by area), 6 octaves x 4 "
+                                  "LoG scales, N=2000, 128-D float descriptors", "storage": "fp32",
+                      "l2": "working set > L2", "records_per_step": int(len(kp32))},
+           "stage_ms_per_step": st32,
+           "octave0_tflops": flops_o[0] * n / (st32["detect_octave0"] * 1e-3) / 1e12,
+           "fp16": {"value": n / (ms16 * 1e-3), "ms_per_step": ms16, "records_per_step": int(len(kp16)),
+                    "stage_ms_per_step": st16},
+           "fp16_learned": learned, "clocks": clocks}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -382,8 +472,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--images", type=int, default=N_IMAGES, help="images per rank (profiling runs)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal leg")
-    ap.add_argument("--workload", default="batch", choices=["batch", "uneven"],
-                    help="batch: 256 x 640x480 (default); uneven: 1024 uneven images resized to 640")
+    ap.add_argument("--workload", default="batch", choices=["batch", "uneven", "highres"],
+                    help="batch: 256 x 640x480 (default); uneven: 1024 uneven images resized to 640; "
+                         "highres: 512 x 2048x1536, 6 octaves, N=2000")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank = int(os.environ.get("RANK", "0"))
@@ -395,6 +486,10 @@ def main():
         if args.images == N_IMAGES:
             args.images = 1024
         return run_uneven(args, rank, world, local)
+    if args.workload == "highres":
+        if args.images == N_IMAGES:
+            args.images = 512
+        return run_highres(args, rank, world, local)
 
     imgs = make_batch(args.images, offset=rank * args.images)  # before any CUDA call
     import torch

@@ -627,7 +627,7 @@ cdvs_status run_resize(cdvs_ctx* c, int n, const cdvs_image_desc* sizes, const s
       j.pitch2 = eff[i].pitch_bytes;
       jobs.push_back(j);
       c->h_plans[i].src = j.dst;
-      max_pixels = std::max(max_pixels, j.W2 * j.H2);
+      max_pixels = std::max(max_pixels, j.H2);  // rows
     }
   if (jobs.empty()) return CDVS_OK;
   if ((e = ensure(c->resize_jobs, sizeof(ResizeJob) * jobs.size())) != cudaSuccess ||
@@ -1252,7 +1252,7 @@ cdvs_status cdvs_resize(cdvs_ctx* c, int32_t n, const uint8_t* const* images, co
         return cuda_fail(c, e, "copy");
     } else {
       jobs.push_back(ResizeJob{src[i], sizes[i].width, sizes[i].height, sizes[i].pitch_bytes, dst + o, W2, H2, W2});
-      max_pixels = std::max(max_pixels, W2 * H2);
+      max_pixels = std::max(max_pixels, H2);  // rows
     }
     o += (size_t)W2 * H2;
   }

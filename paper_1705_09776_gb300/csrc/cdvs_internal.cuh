@@ -190,6 +190,6 @@ struct ResizeJob {
   uint8_t* dst;
   int W2, H2, pitch2;
 };
-cudaError_t launch_resize(const ResizeJob* d_jobs, int n_jobs, int max_pixels, cudaStream_t s);
+cudaError_t launch_resize(const ResizeJob* d_jobs, int n_jobs, int max_rows, cudaStream_t s);
 
 }  // namespace cdvs

@@ -14,42 +14,60 @@
 namespace cdvs {
 namespace {
 
-__device__ __forceinline__ long long overlap(int o, int i, int n_in, int n_out) {
-  const long long lo = max((long long)o * n_in, (long long)i * n_out);
-  const long long hi = min((long long)(o + 1) * n_in, (long long)(i + 1) * n_out);
+// Overlap of input i with output o in units of 1 / (n_in n_out) of a pixel;
+// every product is at most 32768^2 = 2^30, so 32-bit integers hold it.
+__device__ __forceinline__ int overlap(int o, int i, int n_in, int n_out) {
+  const int lo = max(o * n_in, i * n_out), hi = min((o + 1) * n_in, (i + 1) * n_out);
   return hi > lo ? hi - lo : 0;
+}
+
+// Round-to-nearest-even quotient of non-negative integers.
+template <typename U>
+__device__ __forceinline__ U div_rhe(U num, U den) {
+  U q = num / den;
+  const U r = num - q * den;
+  if (2 * r > den || (2 * r == den && (q & 1))) ++q;
+  return q;
+}
+
+// One CTA per kRowsPerCta output rows of one image; the row's input rows and
+// their weights are shared by its pixels.  Sums and the division run in 32
+// bits when 255 W H fits (every image up to 16.8 Mpx), else in 64 bits.
+constexpr int kRowsPerCta = 4;
+
+template <typename U>
+__device__ __forceinline__ void resize_row(const ResizeJob& j, int y2) {
+  const int y0 = (y2 * j.H) / j.H2;
+  const int y1 = min(((y2 + 1) * j.H + j.H2 - 1) / j.H2, j.H);
+  const U den = (U)j.W * (U)j.H;
+  for (int x2 = threadIdx.x; x2 < j.W2; x2 += blockDim.x) {
+    const int x0 = (x2 * j.W) / j.W2;
+    const int x1 = min(((x2 + 1) * j.W + j.W2 - 1) / j.W2, j.W);
+    U s = 0;
+    for (int y = y0; y < y1; ++y) {
+      const uint8_t* row = j.src + (size_t)y * j.pitch;
+      U sr = 0;
+      for (int x = x0; x < x1; ++x) sr += (U)row[x] * (U)overlap(x2, x, j.W, j.W2);
+      s += sr * (U)overlap(y2, y, j.H, j.H2);
+    }
+    j.dst[(size_t)y2 * j.pitch2 + x2] = (uint8_t)div_rhe<U>(s, den);
+  }
 }
 
 __global__ void __launch_bounds__(256) resize_kernel(const ResizeJob* jobs) {
   const ResizeJob j = jobs[blockIdx.y];
-  const unsigned long long den = (unsigned long long)j.W * j.H;
-  const int n = j.W2 * j.H2;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int y2 = i / j.W2, x2 = i - (i / j.W2) * j.W2;
-    const int y0 = (int)(((long long)y2 * j.H) / j.H2);
-    const int y1 = min((int)(((long long)(y2 + 1) * j.H + j.H2 - 1) / j.H2), j.H);
-    const int x0 = (int)(((long long)x2 * j.W) / j.W2);
-    const int x1 = min((int)(((long long)(x2 + 1) * j.W + j.W2 - 1) / j.W2), j.W);
-    unsigned long long s = 0;
-    for (int y = y0; y < y1; ++y) {
-      const unsigned long long wy = (unsigned long long)overlap(y2, y, j.H, j.H2);
-      const uint8_t* row = j.src + (size_t)y * j.pitch;
-      unsigned long long sr = 0;
-      for (int x = x0; x < x1; ++x) sr += (unsigned long long)row[x] * (unsigned long long)overlap(x2, x, j.W, j.W2);
-      s += sr * wy;
-    }
-    unsigned long long q = s / den;
-    const unsigned long long r = s - q * den;
-    if (2 * r > den || (2 * r == den && (q & 1ull))) ++q;
-    j.dst[(size_t)y2 * j.pitch2 + x2] = (uint8_t)q;
+  const bool narrow = 255ull * (unsigned long long)j.W * (unsigned long long)j.H < (1ull << 32);
+  for (int y2 = blockIdx.x * kRowsPerCta; y2 < min((int)(blockIdx.x + 1) * kRowsPerCta, j.H2); ++y2) {
+    if (narrow) resize_row<unsigned>(j, y2);
+    else resize_row<unsigned long long>(j, y2);
   }
 }
 
 }  // namespace
 
-cudaError_t launch_resize(const ResizeJob* d_jobs, int n_jobs, int max_pixels, cudaStream_t s) {
+cudaError_t launch_resize(const ResizeJob* d_jobs, int n_jobs, int max_rows, cudaStream_t s) {
   if (n_jobs <= 0) return cudaSuccess;
-  dim3 grid((max_pixels + 255) / 256, n_jobs);
+  dim3 grid((max_rows + kRowsPerCta - 1) / kRowsPerCta, n_jobs);
   resize_kernel<<<grid, 256, 0, s>>>(d_jobs);
   return cudaGetLastError();
 }

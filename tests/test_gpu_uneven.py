@@ -124,3 +124,41 @@ def test_graph_mode_matches_direct_launches(env):
                 assert np.array_equal(got[2], r[2])
     finally:
         ctx.set_graph(False)
+
+
+def _highres(w, h, seed, i=0):
+    k = w * h / (640 * 480)
+    return synth.blob_image(synth.image_seed(seed, i), w, h, n_blobs=int(round(200 * k)), sigma_range=(4.8, 64.0))
+
+
+def test_highres_six_octaves_2000_points_vs_oracle(env):
+    """The high-resolution configuration (6 octaves, N = 2000, blobs x3.2) on a
+    1024 x 768 image against the oracle, with the parity bracketing."""
+    cdvs, ctx = env
+    img = _highres(1024, 768, seed=5)
+    p = cdvs.params(num_octaves=6, max_keypoints=2000)
+    gk, gd, cnt, st = ctx.extract([img], p)
+    assert st == cdvs.CDVS_OK and 300 < cnt[0]
+    op = dict(num_octaves=6, max_keypoints=2000)
+    ek, ed, _ = O.extract(img, O.params(**op), cap=16384)
+    lk, _, _ = O.extract(img, O.params(margin=PT.MARGIN, **op), cap=16384)
+    sk, _, _ = O.extract(img, O.params(margin=-PT.MARGIN, **op), cap=16384)
+
+    def points(r, key):
+        return r[np.unique(r[key], return_index=True)[1]]
+
+    gp, ep = points(gk, "parent_id"), points(ek, "parent")
+    assert (gp["octave"] >= 4).any()                  # the added octaves contribute
+    agree, n_dis, n_exc, n = PT.point_agreement(gp, ep, points(lk, "parent"), points(sk, "parent"))
+    assert agree >= PT.AGREE, (agree, n_dis, n_exc, n)
+
+
+def test_highres_full_size_runs_and_is_deterministic(env):
+    cdvs, ctx = env
+    imgs = [_highres(2048, 1536, seed=5, i=i) for i in range(2)]
+    p = cdvs.params(num_octaves=6, max_keypoints=2000)
+    a = ctx.extract(imgs, p)
+    b = ctx.extract(imgs, p)
+    assert (a[2] <= 2000 * p["max_orientations"][0]).all() and (a[2] > 1000).all()
+    assert np.array_equal(a[0].view(np.uint8), b[0].view(np.uint8)) and np.array_equal(a[1], b[1])
+    assert len(np.unique(a[0][a[0]["image"] == 0]["parent_id"])) <= 2000
