@@ -461,6 +461,39 @@ def run_highres(args, rank, world, local):
     ctx.close()
 
 
+def run_scfv(ctx, cdvs, torch, d_desc, counts, args):
+    """SCFV aggregation (Sec. III-D) of the batch's descriptors, device-resident,
+    with the oracle-derived stand-in PCA/GMM model; ms per batch."""
+    path = os.path.join(ROOT, "tests", "golden", "scfv_model.npz")
+    if not os.path.exists(path):
+        return None
+    ctx.set_scfv_model(dict(np.load(path)))
+    n = len(counts)
+    cnt = np.ascontiguousarray(counts, np.int32)
+    outs = [torch.zeros(n, 512, 32, device="cuda"), torch.zeros(n, 512, 32, device="cuda"),
+            torch.zeros(n, 512, device="cuda"), torch.zeros(n, 512, dtype=torch.int32, device="cuda"),
+            torch.zeros(n, 64, dtype=torch.int32, device="cuda")]
+    stream = torch.cuda.current_stream()
+    flags = cdvs.CDVS_INPUT_DEVICE | cdvs.CDVS_OUTPUT_DEVICE
+
+    def call():
+        st = ctx._L.cdvs_scfv(ctx.handle, n, d_desc.data_ptr(), cnt.ctypes.data, 64, *[o.data_ptr() for o in outs],
+                              flags, stream.cuda_stream)
+        ctx._check(st)
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        call()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    return {"ms_per_batch": ms, "images_per_s": n / (ms * 1e-3), "records": int(cnt.sum()), "components": 512,
+            "n_select": 64, "model": "tests/golden/scfv_model.npz (stand-in PCA/GMM from oracle descriptors)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -553,6 +586,7 @@ def main():
         return d_kp[:tot * cdvs.KEYPOINT_DTYPE.itemsize].cpu().numpy().view(cdvs.KEYPOINT_DTYPE).copy()
 
     plain_kp = read_kp()
+    scfv = run_scfv(ctx, cdvs, torch, d_desc, d_cnt.cpu().numpy(), args)
     learned = None
     if not args.no_learned and os.path.exists(cdvs.PROPOSAL_WEIGHTS):
         def step_with(pp):
@@ -604,6 +638,8 @@ def main():
            "gpu_launches": launches, "roofline": roofline, "clocks": clocks}
     if learned is not None:
         out["learned"] = learned
+    if scfv is not None:
+        out["scfv"] = scfv
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(imgs)
     if rank == 0:

@@ -345,6 +345,44 @@ cdvs_status cdvs_proposal_train_step(cdvs_ctx *ctx, const uint8_t *images, int32
                                      float *adam_m, float *adam_v, float *grad, float *loss, float *logits,
                                      int32_t step, float lr, int32_t bf16, void *cuda_stream);
 
+/* ---------------------------------------------------------------------------
+ * SCFV aggregation (Sec. III-D, Eq. 6-8; the matrix form of Sec. IV-C,
+ * Eq. 9-14): for the K descriptors x_t of each image,
+ *   y_t = P (x_t - m)                                  (PCA 128 -> 32)
+ *   gamma_t(i) = w_i N(y_t; mu_i, diag v_i) / sum_j w_j N(y_t; mu_j, diag v_j)
+ *   g_mu(i)    = 1/(K sqrt(w_i))   sum_t gamma_t(i) (y_t - mu_i) / sqrt(v_i)
+ *   g_sigma(i) = 1/(K sqrt(2 w_i)) sum_t gamma_t(i) ((y_t - mu_i)^2 / v_i - 1)
+ *   delta(i)   = population standard deviation of the 32 entries of g_mu(i)
+ * for the 512 components, the components ranked by delta (descending, ties to
+ * the lower index), and bit k of the word of each of the first n_select
+ * ranked components set when g_mu(i)_k > 0.  An image with no descriptor
+ * gives zero gradients.  All arithmetic is FP32.
+ * ------------------------------------------------------------------------- */
+#define CDVS_SCFV_COMPONENTS 512
+#define CDVS_SCFV_DIM 32
+
+typedef struct {
+    const float *pca_mean;   /* 128 */
+    const float *pca;        /* 32 x 128, row-major (row j = output dimension j) */
+    const float *weights;    /* 512, positive */
+    const float *means;      /* 512 x 32 */
+    const float *variances;  /* 512 x 32, positive (diagonal) */
+} cdvs_scfv_model;
+
+/* Copies a model (host memory) into the context. */
+cdvs_status cdvs_set_scfv_model(cdvs_ctx *ctx, const cdvs_scfv_model *model);
+
+/* SCFV of a batch.  desc: the records' descriptors packed over the batch as
+ * cdvs_extract writes them (counts[i] rows of 128 floats for image i, in
+ * image order; 16-byte aligned in device memory); counts: host memory.
+ * Outputs per image (any may be NULL): g_mu and g_sigma [512][32], delta
+ * [512], order [512] (component of each rank), bits [n_select] (0 <= n_select
+ * <= 512).  flags: CDVS_INPUT_DEVICE (desc on the device), CDVS_OUTPUT_DEVICE
+ * (outputs on the device).  Synchronous unless both flags are set. */
+cdvs_status cdvs_scfv(cdvs_ctx *ctx, int32_t n_images, const float *desc, const int32_t *counts,
+                      int32_t n_select, float *g_mu, float *g_sigma, float *delta, int32_t *order,
+                      uint32_t *bits, uint32_t flags, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -58,7 +58,7 @@ EXPORTED = ["cdvs_params_default", "cdvs_create", "cdvs_destroy", "cdvs_last_err
             "cdvs_candidates", "cdvs_dedupe_select", "cdvs_describe", "cdvs_scale_space",
             "cdvs_rank_host", "cdvs_transform_ternary", "cdvs_profile", "cdvs_profile_read",
             "cdvs_dedupe_select_noalloc", "cdvs_set_proposal", "cdvs_proposal_logits",
-            "cdvs_proposal_train_step", "cdvs_resize", "cdvs_set_graph"]
+            "cdvs_proposal_train_step", "cdvs_resize", "cdvs_set_graph", "cdvs_set_scfv_model", "cdvs_scfv"]
 STAGES = ["detect", "select", "describe", "offsets", "pack", "detect_octave0", "proposal"]
 
 
@@ -100,6 +100,8 @@ def load(build_if_missing: bool = True):
         "cdvs_set_proposal": (i32, [P, P, i32]),
         "cdvs_resize": (i32, [P, i32, P, P, i32, P, sz, P, u32, P]),
         "cdvs_set_graph": (i32, [P, i32]),
+        "cdvs_set_scfv_model": (i32, [P, P]),
+        "cdvs_scfv": (i32, [P, i32, P, P, i32, P, P, P, P, P, u32, P]),
         "cdvs_proposal_logits": (i32, [P, i32, P, P, P, i32, u32, P]),
         "cdvs_proposal_train_step": (i32, [P, P, i32, i32, i32, i32, P, P, P, P, P, P, P, i32, C.c_float, i32, P]),
     }
@@ -170,6 +172,32 @@ class Context:
     def set_graph(self, enable: bool):
         """Device-resident extractions through one CUDA graph (cdvs_set_graph)."""
         self._check(self._L.cdvs_set_graph(self.handle, 1 if enable else 0))
+
+    # ------------------------------------------------------------ SCFV
+    def set_scfv_model(self, model):
+        """model: mapping with pca_mean (128), pca (32 x 128), weights (512),
+        means (512 x 32), variances (512 x 32)."""
+        arrs = [np.ascontiguousarray(model[k], np.float32) for k in
+                ("pca_mean", "pca", "weights", "means", "variances")]
+        st = (C.c_void_p * 5)(*[a.ctypes.data for a in arrs])
+        self._check(self._L.cdvs_set_scfv_model(self.handle, C.cast(st, C.c_void_p)))
+
+    def scfv(self, desc, counts, n_select=64):
+        """Host SCFV of a batch: desc (sum(counts) x 128 float32, image order),
+        counts per image.  Returns g_mu, g_sigma (n x 512 x 32), delta (n x
+        512), order (n x 512) and bits (n x n_select uint32)."""
+        d = np.ascontiguousarray(desc, np.float32)
+        cnt = np.ascontiguousarray(counts, np.int32)
+        n = len(cnt)
+        g_mu = np.zeros((n, 512, 32), np.float32)
+        g_sig = np.zeros((n, 512, 32), np.float32)
+        delta = np.zeros((n, 512), np.float32)
+        order = np.zeros((n, 512), np.int32)
+        bits = np.zeros((n, max(n_select, 1)), np.uint32)
+        self._check(self._L.cdvs_scfv(self.handle, n, d.ctypes.data, cnt.ctypes.data, int(n_select),
+                                      g_mu.ctypes.data, g_sig.ctypes.data, delta.ctypes.data, order.ctypes.data,
+                                      bits.ctypes.data, 0, None))
+        return g_mu, g_sig, delta, order, bits[:, :n_select]
 
     # ------------------------------------------------------------ S0
     def resize(self, images, max_side):

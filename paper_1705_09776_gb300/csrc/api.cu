@@ -51,6 +51,8 @@ struct cdvs_ctx {
   // learned block proposal: parameters, per-call image table, logits, tile modes, training workspace
   DevBuf prop_theta, prop_imgs, prop_logits, prop_mode, prop_ws;
   DevBuf resized, resize_jobs;  // S0: resized images and their job table
+  DevBuf scfv_model, scfv_desc, scfv_y, scfv_q, scfv_out, scfv_off;  // SCFV model and scratch
+  bool scfv_set = false;
   // page-locked staging of the small per-call tables (one buffer per upload
   // site, so no upload overwrites another one still in flight), and the CUDA
   // graph that device-resident extractions are replayed through
@@ -979,7 +981,8 @@ void cdvs_destroy(cdvs_ctx* c) {
                     &c->rec_total, &c->out_kp, &c->out_desc, &c->out_count, &c->plans,
                     &c->tile_prefix, &c->status, &c->input, &c->dump, &c->stage_kp, &c->stage_desc,
                     &c->prop_theta, &c->prop_imgs, &c->prop_logits, &c->prop_mode, &c->prop_ws,
-                    &c->resized, &c->resize_jobs};
+                    &c->resized, &c->resize_jobs, &c->scfv_model, &c->scfv_desc, &c->scfv_y, &c->scfv_q,
+                    &c->scfv_out, &c->scfv_off};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (c->small.p) cudaFreeHost(c->small.p);
@@ -1182,6 +1185,110 @@ cdvs_status cdvs_scale_space(cdvs_ctx* c, const uint8_t* image, const cdvs_image
 cdvs_status cdvs_profile(cdvs_ctx* c, int32_t enable) {
   if (!c) return CDVS_INVALID_ARGUMENT;
   c->prof = enable != 0;
+  return CDVS_OK;
+}
+
+cdvs_status cdvs_set_scfv_model(cdvs_ctx* c, const cdvs_scfv_model* m) {
+  if (!c) return CDVS_INVALID_ARGUMENT;
+  if (!m || !m->pca_mean || !m->pca || !m->weights || !m->means || !m->variances)
+    return fail(c, CDVS_INVALID_ARGUMENT, "NULL model array");
+  std::vector<float> d(kScfvModelFloats);
+  for (int k = 0; k < 128; ++k) {
+    d[kScfvOffMean + k] = m->pca_mean[k];
+    for (int j = 0; j < kScfvDim; ++j) d[kScfvOffPcaT + k * kScfvDim + j] = m->pca[j * 128 + k];
+  }
+  for (int i = 0; i < kScfvComp; ++i) {
+    const double w = m->weights[i];
+    if (!(w > 0.0)) return fail(c, CDVS_INVALID_ARGUMENT, "GMM weights must be positive");
+    double logdet = 0.0;
+    for (int k = 0; k < kScfvDim; ++k) {
+      const double v = m->variances[i * kScfvDim + k];
+      if (!(v > 0.0)) return fail(c, CDVS_INVALID_ARGUMENT, "GMM variances must be positive");
+      d[kScfvOffMu + i * kScfvDim + k] = m->means[i * kScfvDim + k];
+      d[kScfvOffIsd + i * kScfvDim + k] = (float)(1.0 / std::sqrt(v));
+      logdet += std::log(2.0 * 3.14159265358979323846 * v);
+    }
+    d[kScfvOffLw + i] = (float)(std::log(w) - 0.5 * logdet);
+    d[kScfvOffNmu + i] = (float)(1.0 / std::sqrt(w));
+    d[kScfvOffNsig + i] = (float)(1.0 / std::sqrt(2.0 * w));
+  }
+  cudaError_t e;
+  if ((e = cudaSetDevice(c->device)) != cudaSuccess || (e = ensure(c->scfv_model, sizeof(float) * d.size())) != cudaSuccess ||
+      (e = cudaMemcpy(c->scfv_model.p, d.data(), sizeof(float) * d.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_fail(c, e, "SCFV model");
+  c->scfv_set = true;
+  return CDVS_OK;
+}
+
+cdvs_status cdvs_scfv(cdvs_ctx* c, int32_t n, const float* desc, const int32_t* counts, int32_t n_select,
+                      float* g_mu, float* g_sigma, float* delta, int32_t* order, uint32_t* bits, uint32_t flags,
+                      void* cuda_stream) {
+  if (!c) return CDVS_INVALID_ARGUMENT;
+  if (!c->scfv_set) return fail(c, CDVS_INVALID_ARGUMENT, "no cdvs_set_scfv_model call");
+  if (n < 0 || n > kMaxBatch || n_select < 0 || n_select > kScfvComp)
+    return fail(c, CDVS_INVALID_ARGUMENT, "n_images in 0..4096 and n_select in 0..512 required");
+  if (n == 0) return CDVS_OK;
+  if (!counts || (n_select > 0 && !bits)) return fail(c, CDVS_INVALID_ARGUMENT, "NULL counts or bits");
+  std::vector<int> off(n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    if (counts[i] < 0) return fail(c, CDVS_INVALID_ARGUMENT, "negative count");
+    off[i + 1] = off[i] + counts[i];
+  }
+  const int n_rec = off[n];
+  if (n_rec > 0 && !desc) return fail(c, CDVS_INVALID_ARGUMENT, "NULL desc");
+  const bool dev_in = (flags & CDVS_INPUT_DEVICE) != 0, dev_out = (flags & CDVS_OUTPUT_DEVICE) != 0;
+  if (dev_in && (reinterpret_cast<uintptr_t>(desc) & 15) != 0)
+    return fail(c, CDVS_INVALID_ARGUMENT, "device desc must be 16-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e;
+  if ((e = cudaSetDevice(c->device)) != cudaSuccess) return cuda_fail(c, e, "device");
+  const size_t per = (size_t)kScfvComp * kScfvDim;
+  // scratch: projected descriptors, posteriors, and the outputs the caller
+  // does not take (or takes on the host)
+  const size_t out_floats = (size_t)n * (2 * per + kScfvComp) + (size_t)n * kScfvComp + (size_t)n * kScfvComp;
+  if ((e = ensure(c->scfv_y, sizeof(float) * std::max<size_t>(n_rec, 1) * kScfvDim)) != cudaSuccess ||
+      (e = ensure(c->scfv_q, sizeof(float) * std::max<size_t>(n_rec, 1) * kScfvComp)) != cudaSuccess ||
+      (e = ensure(c->scfv_out, sizeof(float) * out_floats)) != cudaSuccess ||
+      (e = ensure(c->scfv_off, sizeof(int) * (n + 1))) != cudaSuccess ||
+      (!dev_in && n_rec > 0 && (e = ensure(c->scfv_desc, sizeof(float) * 128 * (size_t)n_rec)) != cudaSuccess))
+    return cuda_fail(c, e, "SCFV workspace");
+  float* sc = static_cast<float*>(c->scfv_out.p);
+  float* s_mu = sc;
+  float* s_sig = s_mu + (size_t)n * per;
+  float* s_delta = s_sig + (size_t)n * per;
+  int* s_order = reinterpret_cast<int*>(s_delta + (size_t)n * kScfvComp);
+  uint32_t* s_bits = reinterpret_cast<uint32_t*>(s_order + (size_t)n * kScfvComp);
+  float* o_mu = dev_out && g_mu ? g_mu : s_mu;
+  float* o_sig = dev_out && g_sigma ? g_sigma : s_sig;
+  float* o_delta = dev_out && delta ? delta : s_delta;
+  int* o_order = dev_out && order ? order : s_order;
+  uint32_t* o_bits = dev_out && bits ? bits : s_bits;
+  const float* d_desc = desc;
+  if (!dev_in && n_rec > 0) {
+    if ((e = cudaMemcpyAsync(c->scfv_desc.p, desc, sizeof(float) * 128 * (size_t)n_rec, cudaMemcpyHostToDevice, s)) !=
+        cudaSuccess)
+      return cuda_fail(c, e, "descriptor upload");
+    d_desc = static_cast<const float*>(c->scfv_desc.p);
+  }
+  if ((e = cudaMemcpyAsync(c->scfv_off.p, off.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = launch_scfv(d_desc, n_rec, static_cast<const int*>(c->scfv_off.p), n,
+                       static_cast<const float*>(c->scfv_model.p), n_select, static_cast<float*>(c->scfv_y.p),
+                       static_cast<float*>(c->scfv_q.p), o_mu, o_sig, o_delta, o_order, o_bits, c->n_sms, s)) !=
+          cudaSuccess)
+    return cuda_fail(c, e, "SCFV launch");
+  if (!dev_out) {
+    struct Out {
+      void* h;
+      const void* d;
+      size_t bytes;
+    } outs[] = {{g_mu, o_mu, sizeof(float) * n * per}, {g_sigma, o_sig, sizeof(float) * n * per},
+                {delta, o_delta, sizeof(float) * n * kScfvComp}, {order, o_order, sizeof(int) * n * kScfvComp},
+                {bits, o_bits, sizeof(uint32_t) * (size_t)n * n_select}};
+    for (const Out& o : outs)
+      if (o.h && o.bytes && (e = cudaMemcpyAsync(o.h, o.d, o.bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail(c, e, "SCFV readback");
+  }
+  if ((!dev_in || !dev_out) && (e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(c, e, "SCFV");
   return CDVS_OK;
 }
 

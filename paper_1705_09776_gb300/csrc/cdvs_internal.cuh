@@ -192,4 +192,15 @@ struct ResizeJob {
 };
 cudaError_t launch_resize(const ResizeJob* d_jobs, int n_jobs, int max_rows, cudaStream_t s);
 
+// ---------------------------------------------------------------- SCFV
+constexpr int kScfvComp = 512, kScfvDim = 32;
+// the device model, derived on the host: P transposed [128][32], the PCA
+// mean, mu [512][32], 1/s [512][32], log w_i - 1/2 sum_k log(2 pi v_ik),
+// 1/sqrt(w_i), 1/sqrt(2 w_i)
+constexpr int kScfvOffPcaT = 0, kScfvOffMean = 4096, kScfvOffMu = 4224, kScfvOffIsd = 20608, kScfvOffLw = 36992,
+              kScfvOffNmu = 37504, kScfvOffNsig = 38016, kScfvModelFloats = 38528;
+cudaError_t launch_scfv(const float* desc, int n_rec, const int* rec_off, int n_images, const float* model,
+                        int n_select, float* Y, float* Q, float* g_mu, float* g_sig, float* delta, int* order,
+                        uint32_t* bits, int n_sms, cudaStream_t s);
+
 }  // namespace cdvs

@@ -1,0 +1,85 @@
+"""SCFV aggregation on the GPU against the FP64 oracle (oracle/scfv_oracle.py)
+with the oracle-derived stand-in model (tests/golden/scfv_model.npz).
+
+Inputs are the GPU's own descriptors of seeded images (the aggregation is
+compared, not the descriptors), plus an empty image.  Tolerances: g_mu and
+g_sigma relative L2 per image <= 1e-4, delta <= 1e-4 relative; ranks and
+sign bits are compared where the FP64 values decide them with a margin
+(adjacent deltas apart by more than 1e-4 relative, |g| above 1e-4 of the
+component's largest entry) and must be valid elsewhere."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import scfv_oracle as S
+from paper_1705_09776_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def env():
+    from paper_1705_09776_gb300 import cdvs
+    ctx = cdvs.Context(0)
+    model = dict(np.load(os.path.join(GOLDEN, "scfv_model.npz")))
+    ctx.set_scfv_model(model)
+    return cdvs, ctx, model
+
+
+def test_scfv_matches_oracle(env):
+    cdvs, ctx, model = env
+    imgs = [synth.blob_image(synth.image_seed(81, i)) for i in range(3)]
+    kp, desc, cnt, _ = ctx.extract(imgs)
+    counts = np.concatenate([cnt, [0]])                    # a fourth image with no descriptor
+    n_sel = 64
+    g_mu, g_sig, delta, order, bits = ctx.scfv(desc, counts, n_sel)
+    off = np.concatenate([[0], np.cumsum(counts)])
+    for b in range(4):
+        X = desc[off[b]:off[b + 1]].astype(np.float64)
+        rm, rs, rd = S.fisher(X, model)
+        if len(X) == 0:
+            assert not g_mu[b].any() and not g_sig[b].any() and not delta[b].any()
+            np.testing.assert_array_equal(order[b], np.arange(512))
+            continue
+        for got, ref in ((g_mu[b], rm), (g_sig[b], rs)):
+            assert np.linalg.norm(got - ref) <= 1e-4 * np.linalg.norm(ref)
+        np.testing.assert_allclose(delta[b], rd, rtol=1e-4, atol=1e-7 * rd.max())
+        # ranking: a valid permutation, equal to the oracle's wherever the
+        # deltas of neighbouring ranks are apart by more than the tolerance
+        assert sorted(order[b].tolist()) == list(range(512))
+        ro = S.ranking(rd)
+        gap = np.abs(np.diff(rd[ro])) > 1e-4 * rd.max()
+        for r in range(512):
+            if (r == 0 or gap[r - 1]) and (r == 511 or gap[r]):
+                assert order[b][r] == ro[r]
+        # bits of the selected components, decided ones only
+        for r in range(n_sel):
+            i = order[b][r]
+            ref = rm[i]
+            decided = np.abs(ref) > 1e-4 * np.abs(ref).max()
+            want = ref > 0
+            have = np.array([(int(bits[b][r]) >> k) & 1 for k in range(32)], bool)
+            assert np.array_equal(have[decided], want[decided])
+
+
+def test_scfv_device_buffers_equal_host(env):
+    import torch
+    cdvs, ctx, model = env
+    imgs = [synth.blob_image(synth.image_seed(82, i)) for i in range(2)]
+    kp, desc, cnt, _ = ctx.extract(imgs)
+    h = ctx.scfv(desc, cnt, 32)
+    n = len(cnt)
+    dd = torch.from_numpy(np.ascontiguousarray(desc)).cuda()
+    outs = [torch.zeros(n, 512, 32, device="cuda"), torch.zeros(n, 512, 32, device="cuda"),
+            torch.zeros(n, 512, device="cuda"), torch.zeros(n, 512, dtype=torch.int32, device="cuda"),
+            torch.zeros(n, 32, dtype=torch.int32, device="cuda")]
+    st = ctx._L.cdvs_scfv(ctx.handle, n, dd.data_ptr(), np.ascontiguousarray(cnt, np.int32).ctypes.data, 32,
+                          *[o.data_ptr() for o in outs], cdvs.CDVS_INPUT_DEVICE | cdvs.CDVS_OUTPUT_DEVICE,
+                          torch.cuda.current_stream().cuda_stream)
+    assert st == cdvs.CDVS_OK
+    torch.cuda.synchronize()
+    for a, b in zip(h[:4], outs[:4]):
+        assert np.array_equal(a, b.cpu().numpy())
+    assert np.array_equal(h[4], outs[4].cpu().numpy().view(np.uint32))
