@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(256) scfv_pca_kernel(const float* desc, int n_
 constexpr int kPostRec = 32;
 __global__ void __launch_bounds__(kComp, 1) scfv_post_kernel(const float* Y, int n_rec, const float* model,
                                                              float* Q) {
-  __shared__ float ys[kPostRec][kDim];
+  __shared__ __align__(16) float ys[kPostRec][kDim];
   __shared__ float red[kComp / 32][kPostRec];
   __shared__ float tot[kPostRec];
   const int i = threadIdx.x, lane = i & 31, warp = i >> 5;
@@ -72,9 +72,14 @@ __global__ void __launch_bounds__(kComp, 1) scfv_post_kernel(const float* Y, int
     for (int r = 0; r < kPostRec; ++r) {
       float d2 = 0.0f;
 #pragma unroll
-      for (int k = 0; k < kDim; ++k) {
-        const float d = (ys[r][k] - mu[k]) * isd[k];
-        d2 = fmaf(d, d, d2);
+      for (int k = 0; k < kDim; k += 4) {
+        const float4 y = *reinterpret_cast<const float4*>(&ys[r][k]);
+        const float d0 = (y.x - mu[k]) * isd[k], d1 = (y.y - mu[k + 1]) * isd[k + 1];
+        const float d2_ = (y.z - mu[k + 2]) * isd[k + 2], d3 = (y.w - mu[k + 3]) * isd[k + 3];
+        d2 = fmaf(d0, d0, d2);
+        d2 = fmaf(d1, d1, d2);
+        d2 = fmaf(d2_, d2_, d2);
+        d2 = fmaf(d3, d3, d2);
       }
       l[r] = fmaf(-0.5f, d2, lw);
     }
@@ -112,27 +117,51 @@ __global__ void __launch_bounds__(kComp, 1) scfv_post_kernel(const float* Y, int
   }
 }
 
-// K_c: Fisher gradients; warp = one component of one image, lane = dimension.
-constexpr int kGradWarps = 16;
-__global__ void __launch_bounds__(kGradWarps * 32) scfv_grad_kernel(const float* Y, const float* Q,
-                                                                    const int* rec_off, const float* model,
-                                                                    float* g_mu, float* g_sig) {
-  const int b = blockIdx.y, lane = threadIdx.x & 31;
-  const int i = blockIdx.x * kGradWarps + (threadIdx.x >> 5);
-  const float mu = model[kScfvOffMu + i * kDim + lane], isd = model[kScfvOffIsd + i * kDim + lane];
+// K_c: Fisher gradients.  CTA = 32 components of one image; thread = one
+// component and two dimensions.  Chunks of kGradRec records' posteriors (of
+// those components) and projections are staged in shared memory with
+// coalesced loads; every thread then sums its terms in record order.
+constexpr int kGradComp = 32, kGradRec = 64, kGradThreads = 512;
+__global__ void __launch_bounds__(kGradThreads) scfv_grad_kernel(const float* Y, const float* Q,
+                                                                 const int* rec_off, const float* model,
+                                                                 float* g_mu, float* g_sig) {
+  __shared__ float qs[kGradRec][kGradComp];
+  __shared__ float2 ys[kGradRec][kDim / 2];
+  const int b = blockIdx.y, i0 = blockIdx.x * kGradComp;
+  const int il = threadIdx.x >> 4, kp = threadIdx.x & 15;  // component i0 + il, dimensions 2 kp, 2 kp + 1
+  const int i = i0 + il;
+  const float2 mu = make_float2(model[kScfvOffMu + i * kDim + 2 * kp], model[kScfvOffMu + i * kDim + 2 * kp + 1]);
+  const float2 isd = make_float2(model[kScfvOffIsd + i * kDim + 2 * kp], model[kScfvOffIsd + i * kDim + 2 * kp + 1]);
   const int t0 = rec_off[b], t1 = rec_off[b + 1];
-  float a1 = 0.0f, a2 = 0.0f;
-  for (int t = t0; t < t1; ++t) {
-    const float g = Q[(size_t)t * kComp + i];
-    const float d = (Y[(size_t)t * kDim + lane] - mu) * isd;
-    a1 = fmaf(g, d, a1);
-    a2 = fmaf(g, fmaf(d, d, -1.0f), a2);
+  float a1x = 0.0f, a1y = 0.0f, a2x = 0.0f, a2y = 0.0f;
+  for (int c0 = t0; c0 < t1; c0 += kGradRec) {
+    const int nr = min(kGradRec, t1 - c0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kGradRec * kGradComp; e += kGradThreads) {
+      const int r = e / kGradComp, c = e - r * kGradComp;
+      qs[r][c] = r < nr ? Q[(size_t)(c0 + r) * kComp + i0 + c] : 0.0f;
+    }
+    for (int e = threadIdx.x; e < kGradRec * (kDim / 2); e += kGradThreads) {
+      const int r = e / (kDim / 2), c = e - r * (kDim / 2);
+      ys[r][c] = r < nr ? reinterpret_cast<const float2*>(Y + (size_t)(c0 + r) * kDim)[c] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int r = 0; r < nr; ++r) {
+      const float g = qs[r][il];
+      const float2 y = ys[r][kp];
+      const float dx = (y.x - mu.x) * isd.x, dy = (y.y - mu.y) * isd.y;
+      a1x = fmaf(g, dx, a1x);
+      a1y = fmaf(g, dy, a1y);
+      a2x = fmaf(g, fmaf(dx, dx, -1.0f), a2x);
+      a2y = fmaf(g, fmaf(dy, dy, -1.0f), a2y);
+    }
   }
   const int K = t1 - t0;
   const float inv = K > 0 ? 1.0f / (float)K : 0.0f;
-  const size_t o = ((size_t)b * kComp + i) * kDim + lane;
-  g_mu[o] = a1 * inv * model[kScfvOffNmu + i];
-  g_sig[o] = a2 * inv * model[kScfvOffNsig + i];
+  const float nm = inv * model[kScfvOffNmu + i], ns = inv * model[kScfvOffNsig + i];
+  const size_t o = ((size_t)b * kComp + i) * kDim + 2 * kp;
+  reinterpret_cast<float2*>(g_mu + o)[0] = make_float2(a1x * nm, a1y * nm);
+  reinterpret_cast<float2*>(g_sig + o)[0] = make_float2(a2x * ns, a2y * ns);
 }
 
 // K_d: delta, ranks and sign bits; one CTA per image, thread i = component i.
@@ -183,7 +212,7 @@ cudaError_t launch_scfv(const float* desc, int n_rec, const int* rec_off, int n_
     scfv_post_kernel<<<std::max(1, std::min((n_rec + kPostRec - 1) / kPostRec, n_sms)), kComp, 0, s>>>(Y, n_rec,
                                                                                                    model, Q);
   }
-  scfv_grad_kernel<<<dim3(kComp / kGradWarps, n_images), kGradWarps * 32, 0, s>>>(Y, Q, rec_off, model, g_mu, g_sig);
+  scfv_grad_kernel<<<dim3(kComp / kGradComp, n_images), kGradThreads, 0, s>>>(Y, Q, rec_off, model, g_mu, g_sig);
   scfv_rank_kernel<<<n_images, kComp, 0, s>>>(g_mu, n_select, delta, order, bits);
   return cudaGetLastError();
 }
