@@ -52,6 +52,7 @@ struct cdvs_ctx {
   DevBuf prop_theta, prop_imgs, prop_logits, prop_mode, prop_ws;
   DevBuf resized, resize_jobs;  // S0: resized images and their job table
   DevBuf scfv_model, scfv_desc, scfv_y, scfv_q, scfv_out, scfv_off;  // SCFV model and scratch
+  DevBuf out_counters;  // per output group: slot claims, scan CTAs done, first record (+1)
   bool scfv_set = false;
   // page-locked staging of the small per-call tables (one buffer per upload
   // site, so no upload overwrites another one still in flight), and the CUDA
@@ -698,7 +699,7 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
       (e = ensure(c->status, sizeof(int) * 4)) != cudaSuccess ||
       (e = ensure(c->stage_kp, sizeof(cdvs_keypoint) * slots * p.max_orientations)) != cudaSuccess ||
       (e = ensure(c->stage_desc, sizeof(float) * 128 * slots * p.max_orientations)) != cudaSuccess ||
-      (e = ensure_host(c->small, sizeof(int) * 4)) != cudaSuccess)
+      (e = ensure_host(c->small, sizeof(int) * (4 + kMaxOutGroups + 1))) != cudaSuccess)
     return cuda_fail(c, e, "workspace");
 
   // Device-resident extraction can run as one CUDA graph: the stream work
@@ -876,15 +877,33 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
     d.desc_out = static_cast<float*>(c->out_desc.p);
     d.kp_count = static_cast<int*>(c->out_count.p);
   }
-  ev = prof_begin(c, s);
-  if ((e = launch_describe(d, p.storage, c->n_sms, s)) != cudaSuccess) return cuda_fail(c, e, "describe launch");
-  prof_end(c, 2, 1, ev, s);
-  ev = prof_begin(c, s);
-  if ((e = launch_pack(d, s)) != cudaSuccess) return cuda_fail(c, e, "packing launch");
-  prof_end(c, 3, 1, ev, s);
-  ev = prof_begin(c, s);
-  if ((e = launch_copy(d, c->n_sms, s)) != cudaSuccess) return cuda_fail(c, e, "copy launch");
-  prof_end(c, 4, 1, ev, s);
+  // Description and packing over the whole batch as one image group (the
+  // kernels take a group's image range; returning host records per group
+  // while later groups were described measured slower than one readback).
+  const int groups = 1;
+  if ((e = ensure(c->out_counters, sizeof(int) * (3 * kMaxOutGroups + 1))) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->out_counters.p, 0, sizeof(int) * (3 * kMaxOutGroups + 1), s)) != cudaSuccess)
+    return cuda_fail(c, e, "output counters");
+  unsigned* ctr = static_cast<unsigned*>(c->out_counters.p);
+  int* bases = reinterpret_cast<int*>(ctr + 2 * kMaxOutGroups);
+  for (int g = 0; g < groups; ++g) {
+    d.img_begin = (int)((long long)n * g / groups);
+    d.img_end = (int)((long long)n * (g + 1) / groups);
+    d.claim = ctr + g;
+    d.scan_done = ctr + kMaxOutGroups + g;
+    d.base_in = bases + g;
+    d.base_out = bases + g + 1;
+    d.last_group = g == groups - 1;
+    ev = prof_begin(c, s);
+    if ((e = launch_describe(d, p.storage, c->n_sms, s)) != cudaSuccess) return cuda_fail(c, e, "describe launch");
+    prof_end(c, 2, 1, ev, s);
+    ev = prof_begin(c, s);
+    if ((e = launch_pack(d, s)) != cudaSuccess) return cuda_fail(c, e, "packing launch");
+    prof_end(c, 3, 1, ev, s);
+    ev = prof_begin(c, s);
+    if ((e = launch_copy(d, c->n_sms, s)) != cudaSuccess) return cuda_fail(c, e, "copy launch");
+    prof_end(c, 4, 1, ev, s);
+  }
   if ((e = cudaMemcpyAsync(h_small, c->status.p, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(h_small + 1, c->rec_total.p, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return cuda_fail(c, e, "status readback");
@@ -982,7 +1001,7 @@ void cdvs_destroy(cdvs_ctx* c) {
                     &c->tile_prefix, &c->status, &c->input, &c->dump, &c->stage_kp, &c->stage_desc,
                     &c->prop_theta, &c->prop_imgs, &c->prop_logits, &c->prop_mode, &c->prop_ws,
                     &c->resized, &c->resize_jobs, &c->scfv_model, &c->scfv_desc, &c->scfv_y, &c->scfv_q,
-                    &c->scfv_out, &c->scfv_off};
+                    &c->scfv_out, &c->scfv_off, &c->out_counters};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (c->small.p) cudaFreeHost(c->small.p);

@@ -131,15 +131,27 @@ struct DescribeArgs {
   int patch_side;               // staged patch side (pixels) per point
   cdvs_keypoint* stage_kp;      // n_images x N x max_ori staging slots
   float* stage_desc;            // n_images x N x max_ori x 128
+  // the launch's image group [img_begin, img_end); its counters (zeroed
+  // before the call): slot claims of the description, CTAs done in the
+  // scan; the group's first record (base_in) and the next group's (base_out)
+  int img_begin, img_end;
+  unsigned* claim;
+  unsigned* scan_done;
+  const int* base_in;
+  int* base_out;
+  int last_group;               // 1: the scan also writes the batch total and the truncation bit
 };
 
 // launchers (defined in the .cu files)
 size_t detect_smem_bytes(int max_radius);
 cudaError_t launch_detect(const DetectArgs& a, int n_tiles, int max_radius, int storage, int n_sms,
                           cudaStream_t s);
+cudaError_t launch_detect_masked(const DetectArgs& a, int n_tiles, int max_radius, int storage, int grid,
+                                 cudaStream_t s);
 cudaError_t launch_select(const SelectArgs& a, int n_images, cudaStream_t s);
 size_t describe_smem_bytes(int patch_side);
 cudaError_t launch_describe(const DescribeArgs& a, int storage, int n_sms, cudaStream_t s);
+constexpr int kMaxOutGroups = 4;  // image groups the description and packing kernels can be launched on
 cudaError_t launch_pack(const DescribeArgs& a, cudaStream_t s);
 cudaError_t launch_copy(const DescribeArgs& a, int n_sms, cudaStream_t s);
 cudaError_t launch_levels_to_f32(const ImgPlan* plans, int img, const void* levels, int storage,

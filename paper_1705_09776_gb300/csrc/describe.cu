@@ -448,9 +448,9 @@ __device__ __forceinline__ void stage_patch(const LevelView<__half>& G, int pu0,
   }
 }
 
-// Persistent warps claim slots one at a time from a counter (status[2],
-// zeroed with the status word before every call), so a warp that drew small
-// points takes more of them and the grid finishes together.
+// Persistent warps claim the group's slots one at a time from its counter
+// (zeroed before every call), so a warp that drew small points takes more of
+// them and the grid finishes together.
 template <typename StoreT>
 __global__ void __launch_bounds__(kFWarps * 32, 3) describe_kernel(const __grid_constant__ DescribeArgs a) {
   extern __shared__ float4 smem4[];
@@ -465,13 +465,12 @@ __global__ void __launch_bounds__(kFWarps * 32, 3) describe_kernel(const __grid_
   int* ru = reinterpret_cast<int*>(hist + 36 + 128 + kMaxOri);  // disc row tables, P rows each
   int* rn = ru + P;
   int* rp = rn + P;
-  const int S = a.n_images * a.N;
-  unsigned* next_slot = reinterpret_cast<unsigned*>(a.status + 2);
+  const int S0 = a.img_begin * a.N, S1 = a.img_end * a.N;
   for (;;) {
     int slot = 0;
-    if (lane == 0) slot = (int)atomicAdd(next_slot, 1u);
+    if (lane == 0) slot = S0 + (int)atomicAdd(a.claim, 1u);
     slot = __shfl_sync(0xffffffffu, slot, 0);
-    if (slot >= S) break;
+    if (slot >= S1) break;
     const int img = slot / a.N, rank = slot - img * a.N;
     if (rank >= a.sel_count[img]) continue;
     const Cand c = a.sel[slot];
@@ -498,11 +497,13 @@ __global__ void __launch_bounds__(kFWarps * 32, 3) describe_kernel(const __grid_
 }
 
 // ---- packing.  Records go out in batch order: image, then rank, then copy.
-// scan_kernel: one warp per image writes, per slot, the offset of its first
-// record within the image (local_off) and the image's record count
-// (img_tot); the CTA that finishes last (a counter in status[1], zeroed with
-// the status word before every call) scans the image counts into img_off,
-// the per-image counts clipped to the capacity, and the batch total.
+// scan_kernel, per image group: one warp per image writes, per slot, the
+// offset of its first record within the image (local_off) and the image's
+// record count (img_tot); the CTA that finishes last (the group's counter,
+// zeroed before every call) scans the group's image counts from the group's
+// first record (base_in) into img_off and the per-image counts clipped to the
+// capacity, and writes the next group's first record (base_out); the last
+// group also writes the batch total.
 constexpr int kPackWarps = 8;
 
 __global__ void __launch_bounds__(kPackWarps * 32) scan_kernel(const __grid_constant__ DescribeArgs a,
@@ -510,8 +511,8 @@ __global__ void __launch_bounds__(kPackWarps * 32) scan_kernel(const __grid_cons
   __shared__ int is_last;
   __shared__ int warp_sums[kPackWarps * 32 / 32 + 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int img = blockIdx.x * kPackWarps + warp;
-  if (img < a.n_images) {
+  const int img = a.img_begin + blockIdx.x * kPackWarps + warp;
+  if (img < a.img_end) {
     const int cnt = a.sel_count[img];
     const int per = (a.N + 31) / 32;
     const int r0 = min(lane * per, a.N), r1 = min(r0 + per, a.N);
@@ -535,13 +536,13 @@ __global__ void __launch_bounds__(kPackWarps * 32) scan_kernel(const __grid_cons
   // the last CTA to arrive sees every image count
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) is_last = atomicAdd(reinterpret_cast<unsigned*>(a.status + 1), 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) is_last = atomicAdd(a.scan_done, 1u) == gridDim.x - 1;
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  const int n = a.n_images;
+  const int n = a.img_end - a.img_begin;
   const int per = (n + blockDim.x - 1) / blockDim.x;
-  const int i0 = min((int)threadIdx.x * per, n), i1 = min(i0 + per, n);
+  const int i0 = a.img_begin + min((int)threadIdx.x * per, n), i1 = min(i0 + per, a.img_end);
   int local = 0;
   for (int i = i0; i < i1; ++i) local += __ldcg(img_tot + i);
   int incl = local;
@@ -563,7 +564,8 @@ __global__ void __launch_bounds__(kPackWarps * 32) scan_kernel(const __grid_cons
   }
   __syncthreads();
   const int cap = a.kp_capacity;
-  int run = warp_sums[warp] + incl - local;
+  const int base = __ldcg(a.base_in);
+  int run = base + warp_sums[warp] + incl - local;
   for (int i = i0; i < i1; ++i) {
     const int c = __ldcg(img_tot + i);
     img_off[i] = run;
@@ -571,10 +573,13 @@ __global__ void __launch_bounds__(kPackWarps * 32) scan_kernel(const __grid_cons
     run += c;
   }
   if (threadIdx.x == 0) {
-    const int total = warp_sums[kPackWarps];
-    img_off[n] = total;
-    *a.rec_total = min(total, cap);
-    if (total > cap) atomicOr(a.status, kStatusOutTruncated);
+    const int total = base + warp_sums[kPackWarps];
+    img_off[a.img_end] = total;
+    *a.base_out = total;
+    if (a.last_group) {
+      *a.rec_total = min(total, cap);
+      if (total > cap) atomicOr(a.status, kStatusOutTruncated);
+    }
   }
 }
 
@@ -583,9 +588,9 @@ __global__ void __launch_bounds__(kPackWarps * 32) scan_kernel(const __grid_cons
 __global__ void __launch_bounds__(256) copy_kernel(const __grid_constant__ DescribeArgs a, const int* local_off,
                                                    const int* img_off) {
   const int lane = threadIdx.x & 31;
-  const int S = a.n_images * a.N;
+  const int S0 = a.img_begin * a.N, S1 = a.img_end * a.N;
   const int cap = a.kp_capacity;
-  for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < S; s += (gridDim.x * blockDim.x) >> 5) {
+  for (int s = S0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); s < S1; s += (gridDim.x * blockDim.x) >> 5) {
     const int img = s / a.N, rank = s - img * a.N;
     if (rank >= a.sel_count[img]) continue;
     const int n = a.ori_count[s];
@@ -616,7 +621,7 @@ size_t describe_smem_bytes(int patch_side) {
 // Persistent grid: as many CTAs as fit on the SMs at once (never more than
 // there are slots for).
 cudaError_t launch_describe(const DescribeArgs& a, int storage, int n_sms, cudaStream_t s) {
-  const int slots = a.n_images * a.N;
+  const int slots = (a.img_end - a.img_begin) * a.N;
   if (slots <= 0) return cudaSuccess;
   const size_t smem = describe_smem_bytes(a.patch_side);
   auto go = [&](auto kernel) -> cudaError_t {
@@ -636,20 +641,20 @@ cudaError_t launch_describe(const DescribeArgs& a, int storage, int n_sms, cudaS
 // The packing scratch (rec_off) holds local_off (n_images * N ints), then
 // img_tot (n_images), then img_off (n_images + 1).
 cudaError_t launch_pack(const DescribeArgs& a, cudaStream_t s) {
-  if (a.n_images <= 0 || a.N <= 0) return cudaSuccess;
+  if (a.img_end <= a.img_begin || a.N <= 0) return cudaSuccess;
   int* local_off = a.rec_off;
   int* img_tot = local_off + (size_t)a.n_images * a.N;
   int* img_off = img_tot + a.n_images;
-  scan_kernel<<<(a.n_images + kPackWarps - 1) / kPackWarps, kPackWarps * 32, 0, s>>>(a, local_off, img_tot,
+  scan_kernel<<<(a.img_end - a.img_begin + kPackWarps - 1) / kPackWarps, kPackWarps * 32, 0, s>>>(a, local_off, img_tot,
                                                                                      img_off);
   return cudaGetLastError();
 }
 
 cudaError_t launch_copy(const DescribeArgs& a, int n_sms, cudaStream_t s) {
-  if (a.n_images <= 0 || a.N <= 0) return cudaSuccess;
+  if (a.img_end <= a.img_begin || a.N <= 0) return cudaSuccess;
   const int* local_off = a.rec_off;
   const int* img_off = local_off + (size_t)a.n_images * a.N + a.n_images;
-  const int slots = a.n_images * a.N;
+  const int slots = (a.img_end - a.img_begin) * a.N;
   const int grid = std::min((slots + 7) / 8, n_sms * 8);
   copy_kernel<<<grid, 256, 0, s>>>(a, local_off, img_off);
   return cudaGetLastError();

@@ -252,6 +252,31 @@ def test_pinned_host_buffers_match_pageable(ctx, cd):
         cnt.zero_()
 
 
+def test_host_output_equals_device_output_large_batch(ctx, cd):
+    """A 66-image batch with host outputs equals the device-output call byte
+    for byte, with a roomy and with a truncating capacity."""
+    import torch
+    imgs = np.stack([_img(160, 120, seed=17, i=i) for i in range(66)])
+    n, H, W = imgs.shape
+    sizes = np.array([(W, H, W)] * n, cd.IMAGE_DESC_DTYPE)
+    dev = torch.from_numpy(imgs).cuda()
+    for cap in (n * 300 * 4, 2000):
+        kp = torch.zeros(cap * cd.KEYPOINT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        desc = torch.zeros(cap, 128, dtype=torch.float32, device="cuda")
+        cnt = torch.zeros(n, dtype=torch.int32, device="cuda")
+        st_d = ctx.extract_raw(n, [dev.data_ptr() + i * H * W for i in range(n)], sizes, cd.params(), kp, desc, cap,
+                               cnt, cd.CDVS_INPUT_DEVICE | cd.CDVS_OUTPUT_DEVICE, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        hk, hd, hc, st_h = ctx.extract(list(imgs), capacity=cap)
+        assert st_d == st_h
+        c = cnt.cpu().numpy()
+        assert np.array_equal(c, hc)
+        tot = int(c.sum())
+        assert tot <= cap
+        assert np.array_equal(kp.cpu().numpy()[:tot * cd.KEYPOINT_DTYPE.itemsize], hk.view(np.uint8))
+        assert np.array_equal(desc.cpu().numpy()[:tot], hd)
+
+
 # ------------------------------------------------------------------ edges
 
 def test_edge_cases(ctx, cd):
