@@ -132,14 +132,20 @@ def load_peaks():
         return {}
 
 
+def kernel_sha():
+    """sha256 of K1's sources (the kernel header and its launcher)."""
+    h = hashlib.sha256()
+    for f in ("detect_kernel.cuh", "detect.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1705_09776_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def load_traffic():
     """DRAM bytes per detection step from the committed ncu summary, when it was
     taken on the current kernel source."""
     try:
         t = json.load(open(TRAFFIC_FILE))
-        sha = hashlib.sha256(open(os.path.join(ROOT, "paper_1705_09776_gb300", "csrc", "detect.cu"), "rb")
-                             .read()).hexdigest()
-        if t.get("detect_cu_sha256") == sha:
+        if t.get("kernel_sha256") == kernel_sha():
             return t
     except Exception:
         pass
