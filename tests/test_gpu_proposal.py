@@ -181,3 +181,42 @@ def test_trained_proposal_recall_and_skipped_work(env):
                 detect += bool(hit[max(2 * ty - 1, 0):2 * ty + 3, max(8 * tx - 1, 0):8 * tx + 9].any())
     assert detect < total
     print(f"recall {recall:.4f}; first-octave tiles detecting {detect}/{total}")
+
+
+def test_all_pass_proposal_with_fp16_levels_and_uneven_batch(env):
+    """The masked first-octave variants with FP16 level storage, and the
+    proposal together with the S0 resize of an uneven batch: a network that
+    proposes every block must reproduce the plain calls bit for bit."""
+    cdvs, ctx, torch = env
+    imgs = [synth.blob_image(synth.image_seed(53, i)) for i in range(2)]
+    p16 = cdvs.params(storage=cdvs.CDVS_STORAGE_FP16)
+    k0, d0, c0, _ = ctx.extract(imgs, p16)
+    ctx.set_proposal(_all_blocks(20.0))
+    k1, d1, c1, _ = ctx.extract(imgs, cdvs.params(storage=cdvs.CDVS_STORAGE_FP16, use_proposal=1))
+    assert np.array_equal(c0, c1) and np.array_equal(k0.view(np.uint8), k1.view(np.uint8)) and np.array_equal(d0, d1)
+    uneven = [synth.blob_image(synth.image_seed(54, i), width=w, height=h, n_blobs=300)
+              for i, (w, h) in enumerate([(900, 700), (500, 820), (640, 480)])]
+    k0, d0, c0, _ = ctx.extract(uneven, cdvs.params(max_side=640))
+    k1, d1, c1, _ = ctx.extract(uneven, cdvs.params(max_side=640, use_proposal=1))
+    assert np.array_equal(c0, c1) and np.array_equal(k0.view(np.uint8), k1.view(np.uint8)) and np.array_equal(d0, d1)
+
+
+def test_entry_point_argument_errors(env):
+    cdvs, _, torch = env
+    ctx = cdvs.Context(0)                      # fresh: no proposal, no SCFV model
+    img = [synth.blob_image(synth.image_seed(55, 0), width=64, height=48, n_blobs=5)]
+    for call in (lambda: ctx.extract(img, cdvs.params(use_proposal=1)),
+                 lambda: ctx.proposal_logits(img),
+                 lambda: ctx.scfv(np.zeros((3, 128), np.float32), [3], 8),
+                 lambda: ctx.set_proposal(np.zeros(100, np.float32)),
+                 lambda: ctx.extract(img, cdvs.params(max_side=8)),
+                 lambda: ctx.extract(img, cdvs.params(use_proposal=2)),
+                 lambda: ctx.resize(img, -1)):
+        with pytest.raises(cdvs.CdvsError) as e:
+            call()
+        assert e.value.status == cdvs.CDVS_INVALID_ARGUMENT
+    ctx.set_proposal(_all_blocks(1.0))
+    with pytest.raises(cdvs.CdvsError) as e:
+        ctx.extract(img, cdvs.params(use_proposal=1, proposal_threshold=1.5))
+    assert e.value.status == cdvs.CDVS_INVALID_ARGUMENT
+    ctx.close()
