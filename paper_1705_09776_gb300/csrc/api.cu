@@ -285,13 +285,17 @@ cdvs_status plan_batch(cdvs_ctx* c, int n, const cdvs_image_desc* sizes, const c
     for (int o = 0; o < p.num_octaves; ++o) {
       if (w < 3 || h < 3) break;
       OctPlan& op = P.oct[o];
-      op.W = w;
-      op.H = h;
-      op.lpitch = (w + 7) & ~7;
-      op.tiles_x = (w + kTX - 1) / kTX;
-      op.tiles_y = (h + kTY - 1) / kTY;
+      // past the first octave (whose input is the caller's image), store the
+      // octave transposed when that takes fewer 128 x 32 tiles
+      auto tiles = [](int tw, int th) { return ((tw + kTX - 1) / kTX) * ((th + kTY - 1) / kTY); };
+      op.tr = o > 0 && tiles(h, w) < tiles(w, h);
+      op.W = op.tr ? h : w;
+      op.H = op.tr ? w : h;
+      op.lpitch = (op.W + 7) & ~7;
+      op.tiles_x = (op.W + kTX - 1) / kTX;
+      op.tiles_y = (op.H + kTY - 1) / kTY;
       op.level_off = level_elems;
-      level_elems += ((long long)kScales * op.lpitch * h + 63) & ~63LL;
+      level_elems += ((long long)kScales * op.lpitch * op.H + 63) & ~63LL;
       ++no;
       w = (w + 1) / 2;
       h = (h + 1) / 2;
@@ -1186,7 +1190,7 @@ cdvs_status cdvs_scale_space(cdvs_ctx* c, const uint8_t* image, const cdvs_image
   for (int o = 0; o < P.n_oct; ++o)
     for (int k = 0; k < kScales; ++k) {
       const OctPlan& op = P.oct[o];
-      if ((e = launch_levels_to_f32(nullptr, 0, c->levels.p, params->storage, o, k, op.W, op.H,
+      if ((e = launch_levels_to_f32(c->levels.p, params->storage, op.W, op.H, op.tr,
                                     op.level_off + (long long)k * op.lpitch * op.H, op.lpitch, dst + off, s)) !=
           cudaSuccess)
         return cuda_fail(c, e, "level copy");

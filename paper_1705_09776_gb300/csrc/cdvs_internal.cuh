@@ -35,10 +35,15 @@ constexpr int kStatusTimeout = 8;        // a bounded device-side wait gave up
 // ---------------------------------------------------------------- plans
 // Level (o, k) of an image is stored at level_base + oct[o].level_off +
 // k * oct[o].lpitch * oct[o].H elements (FP32 or FP16), rows lpitch apart.
+// An octave's levels are stored either in the image's orientation or
+// transposed (a stored row is an image column), whichever covers the octave
+// with fewer detection tiles; W, H, lpitch and the tiles are those of the
+// stored frame.
 struct OctPlan {
   int W, H;
   int lpitch;          // elements per stored row (multiple of 8)
   int tiles_x, tiles_y;
+  int tr;              // 1: stored transposed
   long long level_off; // element offset of level (o, 0) in the level arena
 };
 
@@ -154,8 +159,9 @@ cudaError_t launch_describe(const DescribeArgs& a, int storage, int n_sms, cudaS
 constexpr int kMaxOutGroups = 4;  // image groups the description and packing kernels can be launched on
 cudaError_t launch_pack(const DescribeArgs& a, cudaStream_t s);
 cudaError_t launch_copy(const DescribeArgs& a, int n_sms, cudaStream_t s);
-cudaError_t launch_levels_to_f32(const ImgPlan* plans, int img, const void* levels, int storage,
-                                 int octave, int k, int W, int H, long long off, int lpitch,
+// One stored level (W x H in the stored frame, transposed when tr) -> FP32
+// in the image's orientation, rows of the image width.
+cudaError_t launch_levels_to_f32(const void* levels, int storage, int W, int H, int tr, long long off, int lpitch,
                                  float* out, cudaStream_t s);
 
 // ---------------------------------------------------------------- proposal

@@ -23,11 +23,13 @@ namespace {
 __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float ld(const __half* p) { return __half2float(*p); }
 
+// A level in the image's frame: W x H, pixel (x, y) at base[y * sy + x * sx]
+// -- (sx, sy) = (1, pitch), or (pitch, 1) for an octave stored transposed.
 template <typename StoreT>
 struct LevelView {
   const StoreT* base;
-  int W, H, pitch;
-  __device__ __forceinline__ float at(int x, int y) const { return ld(base + (size_t)y * pitch + x); }
+  int W, H, sx, sy;
+  __device__ __forceinline__ float at(int x, int y) const { return ld(base + (size_t)y * sy + (size_t)x * sx); }
   // central differences, clamp-to-edge
   __device__ __forceinline__ void grad(int u, int v, float& gx, float& gy) const {
     gx = at(min(u + 1, W - 1), v) - at(max(u - 1, 0), v);
@@ -45,9 +47,10 @@ __device__ __forceinline__ LevelView<StoreT> level_of(const DescribeArgs& a, int
   const OctPlan op = a.plans[img].oct[o];
   LevelView<StoreT> v;
   v.base = reinterpret_cast<const StoreT*>(a.levels) + op.level_off + (size_t)k * op.lpitch * op.H;
-  v.W = op.W;
-  v.H = op.H;
-  v.pitch = op.lpitch;
+  v.W = op.tr ? op.H : op.W;
+  v.H = op.tr ? op.W : op.H;
+  v.sx = op.tr ? op.lpitch : 1;
+  v.sy = op.tr ? 1 : op.lpitch;
   return v;
 }
 
@@ -430,21 +433,36 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
                : "memory");
 }
 
-// Patch rows pv0 .. pv0 + ph - 1, columns pu0 .. pu0 + pw - 1 of the level,
-// clamped to the image, into patch[r * P + c].
+// Patch rows pv0 .. pv0 + ph - 1, columns pu0 .. pu0 + pw - 1 of the level
+// (image frame), clamped to the image, into patch[r * P + c].  The lanes walk
+// along the stored rows: image rows, or image columns of a transposed octave.
 __device__ __forceinline__ void stage_patch(const LevelView<float>& G, int pu0, int pv0, int pw, int ph, int P,
                                             float* patch, int lane) {
-  for (int r = 0; r < ph; ++r) {
-    const float* row = G.base + (size_t)min(max(pv0 + r, 0), G.H - 1) * G.pitch;
-    for (int cc = lane; cc < pw; cc += 32) cp_async4(patch + r * P + cc, row + min(max(pu0 + cc, 0), G.W - 1));
+  if (G.sx == 1) {
+    for (int r = 0; r < ph; ++r) {
+      const float* row = G.base + (size_t)min(max(pv0 + r, 0), G.H - 1) * G.sy;
+      for (int cc = lane; cc < pw; cc += 32) cp_async4(patch + r * P + cc, row + min(max(pu0 + cc, 0), G.W - 1));
+    }
+  } else {
+    for (int cc = 0; cc < pw; ++cc) {
+      const float* col = G.base + (size_t)min(max(pu0 + cc, 0), G.W - 1) * G.sx;
+      for (int r = lane; r < ph; r += 32) cp_async4(patch + r * P + cc, col + min(max(pv0 + r, 0), G.H - 1));
+    }
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
 __device__ __forceinline__ void stage_patch(const LevelView<__half>& G, int pu0, int pv0, int pw, int ph, int P,
                                             float* patch, int lane) {
-  for (int r = 0; r < ph; ++r) {
-    const __half* row = G.base + (size_t)min(max(pv0 + r, 0), G.H - 1) * G.pitch;
-    for (int cc = lane; cc < pw; cc += 32) patch[r * P + cc] = ld(row + min(max(pu0 + cc, 0), G.W - 1));
+  if (G.sx == 1) {
+    for (int r = 0; r < ph; ++r) {
+      const __half* row = G.base + (size_t)min(max(pv0 + r, 0), G.H - 1) * G.sy;
+      for (int cc = lane; cc < pw; cc += 32) patch[r * P + cc] = ld(row + min(max(pu0 + cc, 0), G.W - 1));
+    }
+  } else {
+    for (int cc = 0; cc < pw; ++cc) {
+      const __half* col = G.base + (size_t)min(max(pu0 + cc, 0), G.W - 1) * G.sx;
+      for (int r = lane; r < ph; r += 32) patch[r * P + cc] = ld(col + min(max(pv0 + r, 0), G.H - 1));
+    }
   }
 }
 
@@ -605,10 +623,10 @@ __global__ void __launch_bounds__(256) copy_kernel(const __grid_constant__ Descr
 }
 
 template <typename StoreT>
-__global__ void levels_to_f32_kernel(const StoreT* src, int W, int H, int lpitch, float* out) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void levels_to_f32_kernel(const StoreT* src, int Wi, int Hi, int tr, int lpitch, float* out) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;  // image frame
   const int y = blockIdx.y;
-  if (x < W && y < H) out[(size_t)y * W + x] = ld(src + (size_t)y * lpitch + x);
+  if (x < Wi && y < Hi) out[(size_t)y * Wi + x] = ld(tr ? src + (size_t)x * lpitch + y : src + (size_t)y * lpitch + x);
 }
 
 }  // namespace
@@ -660,19 +678,15 @@ cudaError_t launch_copy(const DescribeArgs& a, int n_sms, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_levels_to_f32(const ImgPlan* plans, int img, const void* levels, int storage,
-                                 int octave, int k, int W, int H, long long off, int lpitch,
+cudaError_t launch_levels_to_f32(const void* levels, int storage, int W, int H, int tr, long long off, int lpitch,
                                  float* out, cudaStream_t s) {
-  (void)plans;
-  (void)img;
-  (void)octave;
-  (void)k;
-  dim3 grid((W + 255) / 256, H);
+  const int Wi = tr ? H : W, Hi = tr ? W : H;
+  dim3 grid((Wi + 255) / 256, Hi);
   if (storage == CDVS_STORAGE_FP16)
-    levels_to_f32_kernel<__half><<<grid, 256, 0, s>>>(reinterpret_cast<const __half*>(levels) + off, W, H,
+    levels_to_f32_kernel<__half><<<grid, 256, 0, s>>>(reinterpret_cast<const __half*>(levels) + off, Wi, Hi, tr,
                                                       lpitch, out);
   else
-    levels_to_f32_kernel<float><<<grid, 256, 0, s>>>(reinterpret_cast<const float*>(levels) + off, W, H,
+    levels_to_f32_kernel<float><<<grid, 256, 0, s>>>(reinterpret_cast<const float*>(levels) + off, Wi, Hi, tr,
                                                      lpitch, out);
   return cudaGetLastError();
 }

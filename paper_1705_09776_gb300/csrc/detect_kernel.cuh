@@ -11,6 +11,12 @@
 // top level, the decimated base of the next octave (Alg. 1: Downsampling
 // G_{o,K-1} to G_{o+1,0}).
 //
+// An octave past the first may be stored transposed, when its transposed
+// frame takes fewer tiles (a 320 x 240 octave: 20 tiles instead of 24).  The
+// filters are separable and the detector symmetric in x and y, so the kernel
+// works in the stored frame unchanged, swaps x and y of the candidates it
+// emits, and writes the next octave's base in that octave's orientation.
+//
 // While a tile is processed, the rows of the next tile's input are already
 // on their way into shared memory through asynchronous 16-byte copies
 // (cp.async), issued by all threads at once, so global-memory latency overlaps
@@ -82,7 +88,9 @@ struct TileInfo {
   long long dec_off;    // level (o + 1, 0), or -1 when o is the image's last octave
   const void* base;     // first input row (u8 image or level (o, 0))
   int img, tx0, ty0;
-  int W, H, lpitch;     // octave size and stored row pitch (elements)
+  int W, H, lpitch;     // octave size and row pitch (elements), stored frame
+  int tr;               // the octave is stored transposed (x and y of the frame swapped)
+  int dec_tr;           // level (o + 1, 0) is stored in the other orientation
   int dec_pitch;        // row pitch of level (o + 1, 0)
   int pitch;            // input row pitch (elements)
   int cs, ce;           // copied input columns [cs, ce) (image x)
@@ -119,13 +127,16 @@ __device__ __noinline__ void tile_info(const DetectArgs& a, const int* prefix, i
   t.W = op.W;
   t.H = op.H;
   t.lpitch = op.lpitch;
+  t.tr = op.tr;
   t.level_off = op.level_off;
   if (a.octave + 1 < P->n_oct) {
     t.dec_off = P->oct[a.octave + 1].level_off;
     t.dec_pitch = P->oct[a.octave + 1].lpitch;
+    t.dec_tr = P->oct[a.octave + 1].tr != op.tr;
   } else {
     t.dec_off = -1;
     t.dec_pitch = 0;
+    t.dec_tr = 0;
   }
   if constexpr (std::is_same<InT, uint8_t>::value) {
     t.base = P->src;
@@ -414,19 +425,22 @@ __device__ __forceinline__ void store_level(const float* gs, StoreT* dst, int lp
   }
 }
 
-// Alg. 1: G_{o+1,0}[i][j] = G_{o,K-1}[2i][2j] for the even pixels of this tile.
+// Alg. 1: G_{o+1,0}[i][j] = G_{o,K-1}[2i][2j] for the even pixels of this
+// tile, written transposed (to [j][i]) when the next octave is stored in the
+// other orientation.  Consecutive threads write consecutive elements of a
+// stored row either way (16 of a transposed row: 64 bytes).
 template <typename StoreT>
 __device__ __forceinline__ void store_decimated(const float* gs, StoreT* dst, int lpitch1, int W, int H,
-                                                int tx0, int ty0) {
+                                                int tx0, int ty0, int dtr) {
   constexpr int kHX = kTX / 2, kHY = kTY / 2;
   for (int i = threadIdx.x; i < kHX * kHY; i += kDetThreads) {
-    const int r = i / kHX;
-    const int c = i - r * kHX;
+    const int r = dtr ? i % kHY : i / kHX;
+    const int c = dtr ? i / kHY : i % kHX;
     const int y = ty0 + 2 * r, x = tx0 + 2 * c;
     if (y >= H || x >= W) continue;
-    // tile row 2r is the first row of gs pair r + 1; 16-byte load of columns 2c+2, 2c+3
-    const float4 v = *reinterpret_cast<const float4*>(gs + ((r + 1) * kGC + 2 * c + kHalo) * 2);
-    store1(dst + (size_t)(y >> 1) * lpitch1 + (x >> 1), v.x);
+    // tile row 2r is the first row of gs pair r + 1
+    const float v = gs[((r + 1) * kGC + 2 * c + kHalo) * 2];
+    store1(dst + (dtr ? (size_t)(x >> 1) * lpitch1 + (y >> 1) : (size_t)(y >> 1) * lpitch1 + (x >> 1)), v);
   }
 }
 
@@ -636,7 +650,8 @@ __global__ void __launch_bounds__(kDetThreads, 1)
       replicate_borders(gs, W, H, tx0, ty0);
       if (k > 0 || a.write_level0) store_level<StoreT>(gs, lev + k * lstride, lpitch, W, H, tx0, ty0);
       if (k == kScales - 1 && dec_off >= 0)
-        store_decimated<StoreT>(gs, reinterpret_cast<StoreT*>(a.levels) + dec_off, dec_pitch, W, H, tx0, ty0);
+        store_decimated<StoreT>(gs, reinterpret_cast<StoreT*>(a.levels) + dec_off, dec_pitch, W, H, tx0, ty0,
+                                cur.dec_tr);
       if (!Masked || mode == kModeDetect) laplacian(gs, a.s2[k], Ls + (size_t)k * kRP * kLC * 2);
       if (k + 1 < kScales) vpass_dispatch<ic>(a.radius[k + 1], a.taps[k + 1], in, rm, tmp);
       __syncthreads();
@@ -733,8 +748,9 @@ __global__ void __launch_bounds__(kDetThreads, 1)
         const int pos = base + __popc(msk & ((1u << lane) - 1u));
         if (pos < a.cand_cap) {
           Cand c;
-          c.xo = f.xo;
-          c.yo = f.yo;
+          const bool tr = cur.tr;  // image frame
+          c.xo = tr ? f.yo : f.xo;
+          c.yo = tr ? f.xo : f.yo;
           c.so = f.so;
           c.resp = f.resp;
           c.pss = f.pss;

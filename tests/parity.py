@@ -77,7 +77,7 @@ def ang(a, b):
     return min(d, 2 * np.pi - d)
 
 
-def record_agreement(gk, gd, runs):
+def record_agreement(gk, gd, runs, at_point=None):
     """Orientation and descriptor agreement of GPU records with the oracle.
 
     runs[0] = (records, descriptors) of the oracle itself; runs[1:] = the
@@ -87,7 +87,14 @@ def record_agreement(gk, gd, runs):
     descriptor within DESC_TOL; it is a margin case when only a perturbed
     oracle run has such a record (a gradient sample on a histogram bin
     boundary, a peak on the 0.8 x max line, a pixel on the edge of the
-    sampling disc); otherwise it is bad.  Returns (good, margin, bad)."""
+    sampling disc); otherwise it is bad.
+
+    at_point(i), when given, returns the oracle's (records, descriptors) for
+    the point of GPU record i as the GPU found it.  Alg. 2 is discontinuous in
+    the point (a pixel enters or leaves the sampling disc), so where the
+    end-to-end points differ by FP32 rounding (far inside POS_TOL) a record
+    that the oracle reproduces at the GPU's own point is a margin case too.
+    Returns (good, margin, bad)."""
     good = margin = bad = 0
     ek, ed = runs[0]
     m0 = match(gk, ek)
@@ -112,6 +119,10 @@ def record_agreement(gk, gd, runs):
             if any(ang(rk["theta"][j], gk["theta"][i]) <= THETA_TOL and rel_l2(gd[i], rd[j]) <= DESC_TOL
                    for j in pts):
                 hit = True
+        if not hit and at_point is not None:
+            rk, rd = at_point(i)
+            hit = any(ang(rk["theta"][j], gk["theta"][i]) <= THETA_TOL and rel_l2(gd[i], rd[j]) <= DESC_TOL
+                      for j in range(len(rk)))
         if hit:
             margin += 1
         else:
