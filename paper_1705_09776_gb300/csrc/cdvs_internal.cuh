@@ -16,7 +16,7 @@ constexpr int kScales = 4;       // K: levels per octave fitted by the cubic (Eq
 constexpr int kMaxRadius = 24;   // largest Gaussian radius a level filter may have
 constexpr int kMaxOri = 8;       // orientation copies per point
 constexpr int kMaxSelect = 2048; // N limit of the selection step
-constexpr int kSelectList = 4096;  // entries sorted by the selection step (N + ties)
+constexpr int kSelectList = 4096;  // most entries sorted by the selection step (N + ties)
 constexpr int kMaxCells = 8192;  // spatial hash cells of the cross-octave check
 constexpr int kMaxBatch = 4096;  // images per call (the detection tile list lives in shared memory)
 
@@ -109,6 +109,7 @@ struct SelectArgs {
   int N;
   float dlog2;
   int* status;
+  int list_cap;            // entries of the tie list sorted per image (set by launch_select)
 };
 
 // ---------------------------------------------------------------- K5/K6 args

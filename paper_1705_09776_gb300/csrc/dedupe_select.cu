@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(const __grid_consta
 
   // ---- gather candidates at or above the threshold and sort them
   SelEntry* list = reinterpret_cast<SelEntry*>(smem4);  // reuses the cell counters
-  int* perm = reinterpret_cast<int*>(list + kSelectList);
+  int* perm = reinterpret_cast<int*>(list + a.list_cap);
   if (tid == 0) s_misc[3] = 0;
   __syncthreads();
   for (int i = tid; i < n; i += kSelThreads) {
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(const __grid_consta
     const float ar = fabsf(C[i].resp);
     if (__float_as_uint(ar) < thr) continue;
     const int pos = atomicAdd(s_misc + 3, 1);
-    if (pos >= kSelectList) continue;
+    if (pos >= a.list_cap) continue;
     const float s = (float)(1 << C[i].octave);
     SelEntry e;
     e.absr = ar;
@@ -206,8 +206,8 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(const __grid_consta
     list[pos] = e;
   }
   __syncthreads();
-  const int L = min(s_misc[3], kSelectList);
-  if (tid == 0 && s_misc[3] > kSelectList) atomicOr(a.status, kStatusSelectOverflow);
+  const int L = min(s_misc[3], a.list_cap);
+  if (tid == 0 && s_misc[3] > a.list_cap) atomicOr(a.status, kStatusSelectOverflow);
   int Pn = 1;
   while (Pn < L) Pn <<= 1;
   for (int i = tid; i < Pn; i += kSelThreads) {
@@ -247,10 +247,18 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(const __grid_consta
 
 }  // namespace
 
-cudaError_t launch_select(const SelectArgs& a, int n_images, cudaStream_t s) {
+// The tie list holds the N selected candidates and any that tie with the
+// N-th: 2N entries (at least 1024, at most kSelectList).  Sized by N, the
+// shared memory of N = 300 (32 KB, the cell counters) lets four CTAs share an
+// SM, so a 256-image batch selects in one wave; a fixed 4096-entry list
+// (115 KB) had allowed one CTA per SM and two waves.
+cudaError_t launch_select(const SelectArgs& args, int n_images, cudaStream_t s) {
   if (n_images <= 0) return cudaSuccess;
+  SelectArgs a = args;
+  a.list_cap = 1024;
+  while (a.list_cap < 2 * a.N && a.list_cap < kSelectList) a.list_cap <<= 1;
   const size_t smem_cells = sizeof(int) * (kMaxCells + 1);
-  const size_t smem_list = (sizeof(SelEntry) + sizeof(int)) * kSelectList;
+  const size_t smem_list = (sizeof(SelEntry) + sizeof(int)) * (size_t)a.list_cap;
   const size_t smem = smem_cells > smem_list ? smem_cells : smem_list;
   cudaError_t e = cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
