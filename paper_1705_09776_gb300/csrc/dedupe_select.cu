@@ -163,17 +163,41 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(const __grid_consta
         if ((key & mask) == prefix) atomicAdd(s_hist + ((key >> shift) & 255u), 1);
       }
       __syncthreads();
-      if (tid == 0) {
-        int cum = 0, digit = 0;
-        for (int d = 255; d >= 0; --d) {
-          if (cum + s_hist[d] >= remaining) {
-            digit = d;
-            break;
-          }
-          cum += s_hist[d];
+      // the digit d where the count of keys with digits d and above first
+      // reaches `remaining`, scanning down from 255: lane l of warp 0 sums
+      // digits 255 - 8l .. 248 - 8l, a warp scan gives the counts above each
+      // lane's group, and the lane whose group crosses walks its 8 digits
+      if (tid < 32) {
+        const int lane = tid;
+        int c[8], sum = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          c[q] = s_hist[255 - 8 * lane - q];
+          sum += c[q];
         }
-        s_misc[1] = digit;
-        s_misc[2] = remaining - cum;
+        int incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += t;
+        }
+        const int excl = incl - sum;
+        if (lane == 31 && incl < remaining) {  // fewer keys than remaining: as a full scan would end
+          s_misc[1] = 0;
+          s_misc[2] = remaining - incl;
+        }
+        if (excl < remaining && remaining <= incl) {
+          int cum = excl;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            if (cum + c[q] >= remaining) {
+              s_misc[1] = 255 - 8 * lane - q;
+              s_misc[2] = remaining - cum;
+              break;
+            }
+            cum += c[q];
+          }
+        }
       }
       __syncthreads();
       prefix |= (unsigned)s_misc[1] << shift;
