@@ -360,19 +360,24 @@ __device__ __forceinline__ void describe_point(const DescribeArgs& a, const Cand
       const float fx0 = floorf(cx), fy0 = floorf(cy), fo0 = floorf(ob);
       const float fx = cx - fx0, fy = cy - fy0, fo = ob - fo0;
       const int x0 = (int)fx0, y0 = (int)fy0, o0 = (int)fo0;
+      // the scaled orientation shares, then one multiply-add per vote
+      const float ws = w * dsc;
+      const float a0 = ws * (1.0f - fo), a1 = ws * fo;
+      unsigned* h0 = hd + (o0 & 7);
+      unsigned* h1 = hd + ((o0 + 1) & 7);
 #pragma unroll
       for (int iy = 0; iy < 2; ++iy) {
         const int yy = y0 + iy;
         if (yy < 0 || yy > 3) continue;
-        const float wy = w * (iy ? fy : 1.0f - fy);
+        const float wy = iy ? fy : 1.0f - fy;
 #pragma unroll
         for (int ix = 0; ix < 2; ++ix) {
           const int xx = x0 + ix;
           if (xx < 0 || xx > 3) continue;
           const float wxy = wy * (ix ? fx : 1.0f - fx);
           const int cb = (yy * 4 + xx) * 8;
-          vote(hd + cb + (o0 & 7), wxy * (1.0f - fo), dsc);
-          vote(hd + cb + ((o0 + 1) & 7), wxy * fo, dsc);
+          vote(h0 + cb, wxy, a0);  // the vote wxy * a, a already scaled
+          vote(h1 + cb, wxy, a1);
         }
       }
     });
