@@ -553,7 +553,9 @@ def main():
     dev_flags = cdvs.CDVS_INPUT_DEVICE | cdvs.CDVS_OUTPUT_DEVICE
 
     def step():
-        return ctx.extract_raw(n, dptrs, sizes, p, d_kp, d_desc, cap, d_cnt, dev_flags, stream)
+        # enqueued without host synchronisation: the host prepares the next
+        # batch while the GPU runs this one (cdvs_wait after the loop)
+        return ctx.extract_raw(n, dptrs, sizes, p, d_kp, d_desc, cap, d_cnt, dev_flags | cdvs.CDVS_ASYNC, stream)
 
     def barrier():
         if dist is not None:
@@ -561,6 +563,7 @@ def main():
 
     for _ in range(args.warmup):
         step()
+    ctx.wait(stream)
     torch.cuda.synchronize()
     sampler = ClockSampler(local)
     sampler.start()
@@ -574,6 +577,7 @@ def main():
     for _ in range(args.steps):
         step()
     e1.record(stream)
+    ctx.wait(stream)
     torch.cuda.synchronize()
     barrier()
     ms = e0.elapsed_time(e1) / args.steps

@@ -47,6 +47,7 @@ typedef enum {
 /* flags */
 #define CDVS_INPUT_DEVICE 0x1u   /* image pointers (and point lists) are device memory */
 #define CDVS_OUTPUT_DEVICE 0x2u  /* output buffers are device memory */
+#define CDVS_ASYNC 0x4u          /* cdvs_extract only, with both flags above: see cdvs_wait */
 
 /* Level storage types (cdvs_params.storage). */
 #define CDVS_STORAGE_FP32 0
@@ -148,6 +149,22 @@ cdvs_status cdvs_extract(cdvs_ctx *ctx, int32_t n_images, const uint8_t *const *
                          const cdvs_image_desc *sizes, const cdvs_params *params,
                          cdvs_keypoint *kp_out, float *desc_out, int32_t kp_capacity,
                          int32_t *kp_count, uint32_t flags, void *cuda_stream);
+
+/*
+ * cdvs_wait -- completes asynchronous extractions.  A cdvs_extract call with
+ * CDVS_ASYNC (and CDVS_INPUT_DEVICE | CDVS_OUTPUT_DEVICE) returns as soon as
+ * its work is enqueued on the stream, with CDVS_OK or an
+ * argument error; its outputs are valid once the stream reaches that point,
+ * and the host may meanwhile enqueue the next batch (no host synchronisation
+ * between batches).  cdvs_wait synchronises `cuda_stream` (the stream of
+ * those calls) and returns what the calls since the previous cdvs_wait
+ * reported together: CDVS_CAPACITY_TRUNCATED if any of them truncated, else
+ * CDVS_OK.  Asynchronous calls on one context must use one stream, and no
+ * other call on the context is accepted until cdvs_wait (INVALID_ARGUMENT).
+ * The context alternates two page-locked staging sets, so enqueueing a call
+ * waits at most for the call two before it to finish.
+ */
+cdvs_status cdvs_wait(cdvs_ctx *ctx, void *cuda_stream);
 
 /*
  * cdvs_candidates -- Alg. 1 stages A and B only: every refined candidate of

@@ -26,6 +26,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARGUMENT", 2: "UNSUPPORTED_SIZE", 3: "OUT_O
 
 CDVS_INPUT_DEVICE = 0x1
 CDVS_OUTPUT_DEVICE = 0x2
+CDVS_ASYNC = 0x4
 CDVS_STORAGE_FP32 = 0
 CDVS_STORAGE_FP16 = 1
 
@@ -56,7 +57,7 @@ def load_proposal_weights(path=None):
 
 EXPORTED = ["cdvs_params_default", "cdvs_create", "cdvs_destroy", "cdvs_last_error", "cdvs_extract",
             "cdvs_candidates", "cdvs_dedupe_select", "cdvs_describe", "cdvs_scale_space",
-            "cdvs_rank_host", "cdvs_transform_ternary", "cdvs_profile", "cdvs_profile_read",
+            "cdvs_rank_host", "cdvs_transform_ternary", "cdvs_profile", "cdvs_profile_read", "cdvs_wait",
             "cdvs_dedupe_select_noalloc", "cdvs_set_proposal", "cdvs_proposal_logits",
             "cdvs_proposal_train_step", "cdvs_resize", "cdvs_set_graph", "cdvs_set_scfv_model", "cdvs_scfv"]
 STAGES = ["detect", "select", "describe", "offsets", "pack", "detect_octave0", "proposal"]
@@ -95,6 +96,7 @@ def load(build_if_missing: bool = True):
         "cdvs_rank_host": (i32, [P, i32, i32, P]),
         "cdvs_transform_ternary": (i32, [P, i32, P, P, P, P]),
         "cdvs_profile": (i32, [P, i32]),
+        "cdvs_wait": (i32, [P, P]),
         "cdvs_profile_read": (i32, [P, P, P, i32, i32]),
         "cdvs_dedupe_select_noalloc": (i32, [P, i32, i32, i32, P, P, P, P]),
         "cdvs_set_proposal": (i32, [P, P, i32]),
@@ -168,6 +170,11 @@ class Context:
         if st == CDVS_OK or (allow_truncated and st == CDVS_CAPACITY_TRUNCATED):
             return st
         raise CdvsError(st, self.last_error())
+
+    def wait(self, stream=None):
+        """cdvs_wait: synchronises the stream of CDVS_ASYNC extractions and
+        returns their combined status (raises on errors other than truncation)."""
+        return self._check(self._L.cdvs_wait(self.handle, _stream_handle(stream)))
 
     def set_graph(self, enable: bool):
         """Device-resident extractions through one CUDA graph (cdvs_set_graph)."""

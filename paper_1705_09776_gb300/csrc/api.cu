@@ -27,6 +27,17 @@ struct HostBuf {
   size_t bytes = 0;
 };
 
+// Page-locked staging of the small per-call tables, one buffer per upload
+// site (no upload overwrites another one still in flight).  Calls alternate
+// between two sets; a set is reused only after the call two back that used it
+// has finished (its `done` event), so an asynchronous call can stage its
+// tables while the previous call is still running.
+struct HostSet {
+  HostBuf plans, prefix, prop, jobs, plans2;
+  HostBuf small;  // status word + record total
+  cudaEvent_t done = nullptr;
+};
+
 struct ProfRec {
   int stage, launches;
   cudaEvent_t a, b;
@@ -54,16 +65,17 @@ struct cdvs_ctx {
   DevBuf scfv_model, scfv_desc, scfv_y, scfv_q, scfv_out, scfv_off;  // SCFV model and scratch
   DevBuf out_counters;  // per output group: slot claims, scan CTAs done, first record (+1)
   bool scfv_set = false;
-  // page-locked staging of the small per-call tables (one buffer per upload
-  // site, so no upload overwrites another one still in flight), and the CUDA
-  // graph that device-resident extractions are replayed through
-  HostBuf pin_plans, pin_prefix, pin_prop, pin_jobs, pin_plans2;
+  // the host staging sets (HostSet) and the CUDA graph that device-resident
+  // extractions are replayed through
+  HostSet hset[2];
+  int cur_set = 0;
+  bool async_open = false;  // CDVS_ASYNC extractions since the last cdvs_wait
+  HostSet& hs() { return hset[cur_set]; }
   bool graph = false;
   cudaGraphExec_t gexec = nullptr;
   cudaStream_t gstream = nullptr;  // capture stream when the caller passes the legacy default stream
   cudaEvent_t gev = nullptr;
   bool prop_set = false;
-  HostBuf small;  // pinned: status word + record total
   std::vector<ImgPlan> h_plans;
   std::vector<int> h_prefix;
   bool prof = false;
@@ -385,9 +397,9 @@ cdvs_status stage_inputs(cdvs_ctx* c, int n, const uint8_t* const* images, const
   if ((e = ensure(c->plans, sizeof(ImgPlan) * n)) != cudaSuccess) return cuda_fail(c, e, "plans");
   if ((e = ensure(c->tile_prefix, sizeof(int) * c->h_prefix.size())) != cudaSuccess)
     return cuda_fail(c, e, "tile lists");
-  if ((e = upload(c->pin_plans, c->plans.p, c->h_plans.data(), sizeof(ImgPlan) * n, s)) != cudaSuccess)
+  if ((e = upload(c->hs().plans, c->plans.p, c->h_plans.data(), sizeof(ImgPlan) * n, s)) != cudaSuccess)
     return cuda_fail(c, e, "plan upload");
-  if ((e = upload(c->pin_prefix, c->tile_prefix.p, c->h_prefix.data(), sizeof(int) * c->h_prefix.size(), s)) !=
+  if ((e = upload(c->hs().prefix, c->tile_prefix.p, c->h_prefix.data(), sizeof(int) * c->h_prefix.size(), s)) !=
       cudaSuccess)
     return cuda_fail(c, e, "tile list upload");
   return CDVS_OK;
@@ -564,7 +576,7 @@ cdvs_status run_proposal_mask(cdvs_ctx* c, int n, const cdvs_image_desc* sizes, 
       (e = ensure(c->prop_logits, sizeof(float) * n_logits)) != cudaSuccess ||
       (e = ensure(c->prop_mode, (size_t)n_tiles * 4 + n_logits)) != cudaSuccess)
     return cuda_fail(c, e, "proposal workspace");
-  if ((e = upload(c->pin_prop, c->prop_imgs.p, t.data(), sizeof(PropImage) * n, s)) != cudaSuccess)
+  if ((e = upload(c->hs().prop, c->prop_imgs.p, t.data(), sizeof(PropImage) * n, s)) != cudaSuccess)
     return cuda_fail(c, e, "proposal table upload");
   const PropImage* d_t = static_cast<const PropImage*>(c->prop_imgs.p);
   if ((e = launch_proposal_infer(d_t, n, max_th, max_tw, static_cast<const float*>(c->prop_theta.p), prop_frag(c),
@@ -638,10 +650,10 @@ cdvs_status run_resize(cdvs_ctx* c, int n, const cdvs_image_desc* sizes, const s
     }
   if (jobs.empty()) return CDVS_OK;
   if ((e = ensure(c->resize_jobs, sizeof(ResizeJob) * jobs.size())) != cudaSuccess ||
-      (e = upload(c->pin_jobs, c->resize_jobs.p, jobs.data(), sizeof(ResizeJob) * jobs.size(), s)) != cudaSuccess ||
+      (e = upload(c->hs().jobs, c->resize_jobs.p, jobs.data(), sizeof(ResizeJob) * jobs.size(), s)) != cudaSuccess ||
       (e = launch_resize(static_cast<const ResizeJob*>(c->resize_jobs.p), (int)jobs.size(), max_pixels, s)) !=
           cudaSuccess ||
-      (e = upload(c->pin_plans2, c->plans.p, c->h_plans.data(), sizeof(ImgPlan) * n, s)) != cudaSuccess)
+      (e = upload(c->hs().plans2, c->plans.p, c->h_plans.data(), sizeof(ImgPlan) * n, s)) != cudaSuccess)
     return cuda_fail(c, e, "resize");
   return CDVS_OK;
 }
@@ -666,8 +678,26 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
     return fail(c, CDVS_INVALID_ARGUMENT, "output pointer is NULL or capacity < 0");
   if (mode == kCandidates && (flags & CDVS_OUTPUT_DEVICE))
     return fail(c, CDVS_INVALID_ARGUMENT, "cdvs_candidates writes host memory only");
+  const bool async = (flags & CDVS_ASYNC) != 0;
+  if (async && !(mode == kExtract && (flags & CDVS_INPUT_DEVICE) && (flags & CDVS_OUTPUT_DEVICE)))
+    return fail(c, CDVS_INVALID_ARGUMENT, "CDVS_ASYNC needs device inputs and outputs");
+  if (!async && c->async_open)
+    return fail(c, CDVS_INVALID_ARGUMENT, "asynchronous extractions are pending: call cdvs_wait first");
   cudaError_t e = cudaSetDevice(c->device);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  // the host staging set of this call, free once the call two back is done;
+  // the guard marks it in use up to this call's last enqueued work, on every
+  // return path
+  c->cur_set ^= 1;
+  HostSet& hset = c->hs();
+  if (hset.done && (e = cudaEventSynchronize(hset.done)) != cudaSuccess) return cuda_fail(c, e, "staging set");
+  if (!hset.done && (e = cudaEventCreateWithFlags(&hset.done, cudaEventDisableTiming)) != cudaSuccess)
+    return cuda_fail(c, e, "staging set");
+  struct SetGuard {
+    cudaEvent_t ev;
+    cudaStream_t& s;
+    ~SetGuard() { cudaEventRecord(ev, s); }
+  } set_guard{hset.done, s};
 
   // S0: the sizes the method sees
   std::vector<cdvs_image_desc> eff(sizes, sizes + n);
@@ -703,7 +733,7 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
       (e = ensure(c->status, sizeof(int) * 4)) != cudaSuccess ||
       (e = ensure(c->stage_kp, sizeof(cdvs_keypoint) * slots * p.max_orientations)) != cudaSuccess ||
       (e = ensure(c->stage_desc, sizeof(float) * 128 * slots * p.max_orientations)) != cudaSuccess ||
-      (e = ensure_host(c->small, sizeof(int) * (4 + kMaxOutGroups + 1))) != cudaSuccess)
+      (e = ensure_host(c->hs().small, sizeof(int) * (4 + kMaxOutGroups + 1))) != cudaSuccess)
     return cuda_fail(c, e, "workspace");
 
   // Device-resident extraction can run as one CUDA graph: the stream work
@@ -722,6 +752,7 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
       cudaGetLastError();
     }
   } capture{s};
+  const cudaStream_t caller_s = s;
   if (graph) {
     if (!s) {  // the legacy default stream cannot be captured: work on our own stream after it
       if (!c->gstream && ((e = cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking)) != cudaSuccess ||
@@ -737,8 +768,9 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
     capture.on = true;
   }
   if ((st = stage_inputs(c, n, images, sizes, flags, s)) != CDVS_OK) return st;
+  // the status bits of asynchronous calls accumulate until cdvs_wait
   if ((e = cudaMemsetAsync(c->cand_count.p, 0, sizeof(int) * n, s)) != cudaSuccess ||
-      (e = cudaMemsetAsync(c->status.p, 0, sizeof(int) * 4, s)) != cudaSuccess)
+      (!c->async_open && (e = cudaMemsetAsync(c->status.p, 0, sizeof(int) * 4, s)) != cudaSuccess))
     return cuda_fail(c, e, "memset");
   cudaEvent_t ev = prof_begin(c, s);
   const uint8_t* tile_mode = nullptr;
@@ -762,7 +794,7 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
   }
   if ((st = run_detect(c, n, p, max_oct, cap, s, tile_mode, block_mask)) != CDVS_OK) return st;
   prof_end(c, 0, max_oct, ev, s);
-  int* h_small = static_cast<int*>(c->small.p);
+  int* h_small = static_cast<int*>(c->hs().small.p);
 
   if (mode == kScaleSpace) {
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "scale space");
@@ -908,8 +940,9 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
     if ((e = launch_copy(d, c->n_sms, s)) != cudaSuccess) return cuda_fail(c, e, "copy launch");
     prof_end(c, 4, 1, ev, s);
   }
-  if ((e = cudaMemcpyAsync(h_small, c->status.p, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(h_small + 1, c->rec_total.p, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+  if (!async && ((e = cudaMemcpyAsync(h_small, c->status.p, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+                 (e = cudaMemcpyAsync(h_small + 1, c->rec_total.p, sizeof(int), cudaMemcpyDeviceToHost, s)) !=
+                     cudaSuccess))
     return cuda_fail(c, e, "status readback");
   if (graph) {
     cudaGraph_t g = nullptr;
@@ -929,6 +962,15 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
     }
     cudaGraphDestroy(g);
     if ((e = cudaGraphLaunch(c->gexec, s)) != cudaSuccess) return cuda_fail(c, e, "graph launch");
+    if (s != caller_s) {  // the caller's stream continues after the graph
+      if ((e = cudaEventRecord(c->gev, s)) != cudaSuccess || (e = cudaStreamWaitEvent(caller_s, c->gev, 0)) != cudaSuccess)
+        return cuda_fail(c, e, "graph stream");
+    }
+  }
+  if (async) {  // the caller synchronizes; cdvs_wait reports the status bits
+    c->async_open = true;
+    c->err.clear();
+    return CDVS_OK;
   }
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(c, e, "status readback");
   const int status_bits = h_small[0];
@@ -1008,9 +1050,11 @@ void cdvs_destroy(cdvs_ctx* c) {
                     &c->scfv_out, &c->scfv_off, &c->out_counters};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
-  if (c->small.p) cudaFreeHost(c->small.p);
-  for (HostBuf* h : {&c->pin_plans, &c->pin_prefix, &c->pin_prop, &c->pin_jobs, &c->pin_plans2})
-    if (h->p) cudaFreeHost(h->p);
+  for (HostSet& hs : c->hset) {
+    for (HostBuf* h : {&hs.plans, &hs.prefix, &hs.prop, &hs.jobs, &hs.plans2, &hs.small})
+      if (h->p) cudaFreeHost(h->p);
+    if (hs.done) cudaEventDestroy(hs.done);
+  }
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->gstream) cudaStreamDestroy(c->gstream);
   if (c->gev) cudaEventDestroy(c->gev);
@@ -1064,6 +1108,7 @@ cdvs_status cdvs_dedupe_select(cdvs_ctx* c, int32_t n, const cdvs_image_desc* si
   if (!c) return CDVS_INVALID_ARGUMENT;
   cdvs_status st = check_params(c, params);
   if (st != CDVS_OK) return st;
+  if (c->async_open) return fail(c, CDVS_INVALID_ARGUMENT, "asynchronous extractions are pending: call cdvs_wait first");
   if (n < 0 || !sizes || (n > 0 && (!cand || !cand_count || !sel_out || !sel_count)))
     return fail(c, CDVS_INVALID_ARGUMENT, "NULL argument or n < 0");
   if (flags & (CDVS_INPUT_DEVICE | CDVS_OUTPUT_DEVICE))
@@ -1203,6 +1248,24 @@ cdvs_status cdvs_scale_space(cdvs_ctx* c, const uint8_t* image, const cdvs_image
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(c, e, "sync");
   *n_octaves = P.n_oct;
   return CDVS_OK;
+}
+
+cdvs_status cdvs_wait(cdvs_ctx* c, void* cuda_stream) {
+  if (!c) return CDVS_INVALID_ARGUMENT;
+  if (!c->async_open) {
+    c->err.clear();
+    return CDVS_OK;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  HostBuf& h = c->hs().small;
+  if ((e = ensure_host(h, sizeof(int) * (4 + kMaxOutGroups + 1))) != cudaSuccess ||
+      (e = cudaMemcpyAsync(h.p, c->status.p, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return cuda_fail(c, e, "status readback");
+  c->async_open = false;
+  return map_status(c, static_cast<int*>(h.p)[0]);
 }
 
 cdvs_status cdvs_profile(cdvs_ctx* c, int32_t enable) {
