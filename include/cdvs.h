@@ -152,17 +152,26 @@ cdvs_status cdvs_extract(cdvs_ctx *ctx, int32_t n_images, const uint8_t *const *
 
 /*
  * cdvs_wait -- completes asynchronous extractions.  A cdvs_extract call with
- * CDVS_ASYNC (and CDVS_INPUT_DEVICE | CDVS_OUTPUT_DEVICE) returns as soon as
- * its work is enqueued on the stream, with CDVS_OK or an
- * argument error; its outputs are valid once the stream reaches that point,
- * and the host may meanwhile enqueue the next batch (no host synchronisation
- * between batches).  cdvs_wait synchronises `cuda_stream` (the stream of
- * those calls) and returns what the calls since the previous cdvs_wait
- * reported together: CDVS_CAPACITY_TRUNCATED if any of them truncated, else
- * CDVS_OK.  Asynchronous calls on one context must use one stream, and no
- * other call on the context is accepted until cdvs_wait (INVALID_ARGUMENT).
- * The context alternates two page-locked staging sets, so enqueueing a call
- * waits at most for the call two before it to finish.
+ * CDVS_ASYNC returns as soon as its batch is enqueued, with CDVS_OK or an
+ * argument error, so the host prepares and enqueues the next batch while the
+ * GPU works on this one.
+ *   Device outputs are complete when `cuda_stream` reaches the call.
+ *   Host outputs (kp_out, desc_out, kp_count) are copied out once the call's
+ *   record total is known: the copies are enqueued by the next asynchronous
+ *   call (which first waits until this call's records are packed) or by
+ *   cdvs_wait, on a copy stream of the context, so they overlap the next
+ *   batch.  Host images are copied in by the call itself.  Host buffers of
+ *   both directions must stay valid and unchanged until cdvs_wait returns;
+ *   page-locked memory keeps the copies asynchronous.
+ * cdvs_wait enqueues what is pending, synchronises `cuda_stream` (the stream
+ * of those calls) and the copies, and returns what the calls since the
+ * previous cdvs_wait reported together: CDVS_CAPACITY_TRUNCATED if any of
+ * them truncated, else CDVS_OK.  Asynchronous calls on one context must use
+ * one stream, and no other call that uses the context's workspace is
+ * accepted until cdvs_wait (INVALID_ARGUMENT).  The context alternates two
+ * staging sets (page-locked tables, device copies of host images and of
+ * host-bound records), so enqueueing a call waits at most for the call two
+ * before it.
  */
 cdvs_status cdvs_wait(cdvs_ctx *ctx, void *cuda_stream);
 

@@ -27,15 +27,30 @@ struct HostBuf {
   size_t bytes = 0;
 };
 
-// Page-locked staging of the small per-call tables, one buffer per upload
-// site (no upload overwrites another one still in flight).  Calls alternate
-// between two sets; a set is reused only after the call two back that used it
-// has finished (its `done` event), so an asynchronous call can stage its
-// tables while the previous call is still running.
-struct HostSet {
+// What one call stages: page-locked copies of the small per-call tables (one
+// buffer per upload site, so no upload overwrites another one still in
+// flight), the device copy of host images, and the device copy of records
+// bound for host memory.  Calls alternate between two sets.  The host tables
+// of a set are rewritten only after the call two back that used it has
+// finished (`done`), its input copy only after that call's detection
+// (`in_free`), its output copy only after that call's records reached the
+// host (`out_free`); so an asynchronous call stages and enqueues its batch
+// while the previous one is still running.
+struct StageSet {
   HostBuf plans, prefix, prop, jobs, plans2;
   HostBuf small;  // status word + record total
-  cudaEvent_t done = nullptr;
+  DevBuf input, out_kp, out_desc, out_count;
+  cudaEvent_t done = nullptr, in_free = nullptr, out_free = nullptr, packed = nullptr;
+};
+
+// An asynchronous call with host outputs whose records still have to be
+// copied out (the copies are enqueued once its record total is known).
+struct PendingReadback {
+  bool on = false;
+  int set = 0, n = 0;
+  cdvs_keypoint* kp = nullptr;
+  float* desc = nullptr;
+  int32_t* count = nullptr;
 };
 
 struct ProfRec {
@@ -58,19 +73,21 @@ struct cdvs_ctx {
   int n_sms = 0;
   std::string err;
   DevBuf levels, cands, cand_count, order, keep, sel, sel_count, ori_theta, ori_count, rec_off,
-      rec_total, out_kp, out_desc, out_count, plans, tile_prefix, status, input, dump, stage_kp, stage_desc;
+      rec_total, plans, tile_prefix, status, input, dump, stage_kp, stage_desc;
   // learned block proposal: parameters, per-call image table, logits, tile modes, training workspace
   DevBuf prop_theta, prop_imgs, prop_logits, prop_mode, prop_ws;
   DevBuf resized, resize_jobs;  // S0: resized images and their job table
   DevBuf scfv_model, scfv_desc, scfv_y, scfv_q, scfv_out, scfv_off;  // SCFV model and scratch
   DevBuf out_counters;  // per output group: slot claims, scan CTAs done, first record (+1)
   bool scfv_set = false;
-  // the host staging sets (HostSet) and the CUDA graph that device-resident
-  // extractions are replayed through
-  HostSet hset[2];
+  // the per-call staging sets (StageSet) and the CUDA graph that
+  // device-resident extractions are replayed through
+  StageSet hset[2];
   int cur_set = 0;
   bool async_open = false;  // CDVS_ASYNC extractions since the last cdvs_wait
-  HostSet& hs() { return hset[cur_set]; }
+  PendingReadback pend;
+  cudaStream_t d2h_stream = nullptr;  // record copies of asynchronous calls
+  StageSet& hs() { return hset[cur_set]; }
   bool graph = false;
   cudaGraphExec_t gexec = nullptr;
   cudaStream_t gstream = nullptr;  // capture stream when the caller passes the legacy default stream
@@ -359,8 +376,9 @@ cdvs_status stage_inputs(cdvs_ctx* c, int n, const uint8_t* const* images, const
       total = (total + 255) & ~(size_t)255;
     }
     off[n] = total;
-    if ((e = ensure(c->input, total)) != cudaSuccess) return cuda_fail(c, e, "input staging");
-    uint8_t* base = static_cast<uint8_t*>(c->input.p);
+    DevBuf& input = c->hs().input;
+    if ((e = ensure(input, total)) != cudaSuccess) return cuda_fail(c, e, "input staging");
+    uint8_t* base = static_cast<uint8_t*>(input.p);
     if (!c->copy_stream) {
       if ((e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
         return cuda_fail(c, e, "copy stream");
@@ -386,11 +404,9 @@ cdvs_status stage_inputs(cdvs_ctx* c, int n, const uint8_t* const* images, const
           c->uploads[k].push_back(Upload{base + off[i], images[i], (size_t)sizes[i].pitch_bytes * sizes[i].height});
       }
     }
-    // the copy stream starts after the work already on s (which may still
-    // read the staging buffer)
-    cudaEvent_t after = c->ready[kMaxInputChunks];
-    if ((e = cudaEventRecord(after, s)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(c->copy_stream, after, 0)) != cudaSuccess)
+    // the copies start once the last detection that read this staging buffer
+    // (two calls back) is done
+    if ((e = cudaStreamWaitEvent(c->copy_stream, c->hs().in_free, 0)) != cudaSuccess)
       return cuda_fail(c, e, "copy ordering");
     for (int i = 0; i < n; ++i) c->h_plans[i].src = base + off[i];
   }
@@ -658,6 +674,32 @@ cdvs_status run_resize(cdvs_ctx* c, int n, const cdvs_image_desc* sizes, const s
   return CDVS_OK;
 }
 
+// The pending readback of an asynchronous call with host outputs: waits
+// until the call's records are packed (its record total is then in the set's
+// page-locked word), copies them out on the readback stream, and marks the
+// set's output copy free again after the copies.
+cdvs_status flush_readback(cdvs_ctx* c) {
+  PendingReadback& r = c->pend;
+  if (!r.on) return CDVS_OK;
+  r.on = false;
+  StageSet& set = c->hset[r.set];
+  cudaError_t e;
+  if (!c->d2h_stream && (e = cudaStreamCreateWithFlags(&c->d2h_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(c, e, "readback stream");
+  if ((e = cudaEventSynchronize(set.packed)) != cudaSuccess) return cuda_fail(c, e, "readback");
+  const int total = static_cast<const int*>(set.small.p)[1];
+  cudaStream_t q = c->d2h_stream;
+  if ((e = cudaStreamWaitEvent(q, set.packed, 0)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(r.count, set.out_count.p, sizeof(int) * r.n, cudaMemcpyDeviceToHost, q)) != cudaSuccess ||
+      (total > 0 && (e = cudaMemcpyAsync(r.kp, set.out_kp.p, sizeof(cdvs_keypoint) * (size_t)total,
+                                         cudaMemcpyDeviceToHost, q)) != cudaSuccess) ||
+      (total > 0 && (e = cudaMemcpyAsync(r.desc, set.out_desc.p, sizeof(float) * 128 * (size_t)total,
+                                         cudaMemcpyDeviceToHost, q)) != cudaSuccess) ||
+      (e = cudaEventRecord(set.out_free, q)) != cudaSuccess)
+    return cuda_fail(c, e, "readback");
+  return CDVS_OK;
+}
+
 cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, const cdvs_image_desc* sizes,
                 const cdvs_params* params, const PointsIn* pin, cdvs_keypoint* kp_out, float* desc_out,
                 int32_t capacity, int32_t* kp_count, uint32_t flags, cudaStream_t s) {
@@ -679,8 +721,7 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
   if (mode == kCandidates && (flags & CDVS_OUTPUT_DEVICE))
     return fail(c, CDVS_INVALID_ARGUMENT, "cdvs_candidates writes host memory only");
   const bool async = (flags & CDVS_ASYNC) != 0;
-  if (async && !(mode == kExtract && (flags & CDVS_INPUT_DEVICE) && (flags & CDVS_OUTPUT_DEVICE)))
-    return fail(c, CDVS_INVALID_ARGUMENT, "CDVS_ASYNC needs device inputs and outputs");
+  if (async && mode != kExtract) return fail(c, CDVS_INVALID_ARGUMENT, "CDVS_ASYNC is for cdvs_extract only");
   if (!async && c->async_open)
     return fail(c, CDVS_INVALID_ARGUMENT, "asynchronous extractions are pending: call cdvs_wait first");
   cudaError_t e = cudaSetDevice(c->device);
@@ -689,10 +730,11 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
   // the guard marks it in use up to this call's last enqueued work, on every
   // return path
   c->cur_set ^= 1;
-  HostSet& hset = c->hs();
+  StageSet& hset = c->hs();
   if (hset.done && (e = cudaEventSynchronize(hset.done)) != cudaSuccess) return cuda_fail(c, e, "staging set");
-  if (!hset.done && (e = cudaEventCreateWithFlags(&hset.done, cudaEventDisableTiming)) != cudaSuccess)
-    return cuda_fail(c, e, "staging set");
+  for (cudaEvent_t* ev : {&hset.done, &hset.in_free, &hset.out_free, &hset.packed})
+    if (!*ev && (e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(c, e, "staging set");
   struct SetGuard {
     cudaEvent_t ev;
     cudaStream_t& s;
@@ -794,6 +836,9 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
   }
   if ((st = run_detect(c, n, p, max_oct, cap, s, tile_mode, block_mask)) != CDVS_OK) return st;
   prof_end(c, 0, max_oct, ev, s);
+  // the staged host images are read no more
+  if (!(flags & CDVS_INPUT_DEVICE) && (e = cudaEventRecord(hset.in_free, s)) != cudaSuccess)
+    return cuda_fail(c, e, "staging set");
   int* h_small = static_cast<int*>(c->hs().small.p);
 
   if (mode == kScaleSpace) {
@@ -905,13 +950,15 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
     d.desc_out = desc_out;
     d.kp_count = kp_count;
   } else {
-    if ((e = ensure(c->out_kp, sizeof(cdvs_keypoint) * (size_t)capacity)) != cudaSuccess ||
-        (e = ensure(c->out_desc, sizeof(float) * 128 * (size_t)capacity)) != cudaSuccess ||
-        (e = ensure(c->out_count, sizeof(int) * n)) != cudaSuccess)
+    // the set's output copy, once the records it held two calls back are out
+    if ((e = ensure(hset.out_kp, sizeof(cdvs_keypoint) * (size_t)capacity)) != cudaSuccess ||
+        (e = ensure(hset.out_desc, sizeof(float) * 128 * (size_t)capacity)) != cudaSuccess ||
+        (e = ensure(hset.out_count, sizeof(int) * n)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(s, hset.out_free, 0)) != cudaSuccess)
       return cuda_fail(c, e, "output staging");
-    d.kp_out = static_cast<cdvs_keypoint*>(c->out_kp.p);
-    d.desc_out = static_cast<float*>(c->out_desc.p);
-    d.kp_count = static_cast<int*>(c->out_count.p);
+    d.kp_out = static_cast<cdvs_keypoint*>(hset.out_kp.p);
+    d.desc_out = static_cast<float*>(hset.out_desc.p);
+    d.kp_count = static_cast<int*>(hset.out_count.p);
   }
   // Description and packing over the whole batch as one image group (the
   // kernels take a group's image range; returning host records per group
@@ -940,9 +987,10 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
     if ((e = launch_copy(d, c->n_sms, s)) != cudaSuccess) return cuda_fail(c, e, "copy launch");
     prof_end(c, 4, 1, ev, s);
   }
-  if (!async && ((e = cudaMemcpyAsync(h_small, c->status.p, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-                 (e = cudaMemcpyAsync(h_small + 1, c->rec_total.p, sizeof(int), cudaMemcpyDeviceToHost, s)) !=
-                     cudaSuccess))
+  if ((!async || !dev_out) &&
+      ((e = cudaMemcpyAsync(h_small, c->status.p, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+       (e = cudaMemcpyAsync(h_small + 1, c->rec_total.p, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+       (!dev_out && (e = cudaEventRecord(hset.packed, s)) != cudaSuccess)))
     return cuda_fail(c, e, "status readback");
   if (graph) {
     cudaGraph_t g = nullptr;
@@ -969,6 +1017,12 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
   }
   if (async) {  // the caller synchronizes; cdvs_wait reports the status bits
     c->async_open = true;
+    if (!dev_out) {
+      // the previous call's records go out now (this call's work is already
+      // queued behind it); this call's go out at the next call or cdvs_wait
+      if ((st = flush_readback(c)) != CDVS_OK) return st;
+      c->pend = PendingReadback{true, c->cur_set, n, kp_out, desc_out, kp_count};
+    }
     c->err.clear();
     return CDVS_OK;
   }
@@ -976,10 +1030,10 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
   const int status_bits = h_small[0];
   const int total = h_small[1];
   if (!dev_out) {
-    if ((e = cudaMemcpyAsync(kp_count, c->out_count.p, sizeof(int) * n, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-        (total > 0 && (e = cudaMemcpyAsync(kp_out, c->out_kp.p, sizeof(cdvs_keypoint) * (size_t)total,
+    if ((e = cudaMemcpyAsync(kp_count, hset.out_count.p, sizeof(int) * n, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (total > 0 && (e = cudaMemcpyAsync(kp_out, hset.out_kp.p, sizeof(cdvs_keypoint) * (size_t)total,
                                            cudaMemcpyDeviceToHost, s)) != cudaSuccess) ||
-        (total > 0 && (e = cudaMemcpyAsync(desc_out, c->out_desc.p, sizeof(float) * 128 * (size_t)total,
+        (total > 0 && (e = cudaMemcpyAsync(desc_out, hset.out_desc.p, sizeof(float) * 128 * (size_t)total,
                                            cudaMemcpyDeviceToHost, s)) != cudaSuccess) ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
       return cuda_fail(c, e, "output readback");
@@ -1043,17 +1097,24 @@ void cdvs_destroy(cdvs_ctx* c) {
   cudaSetDevice(c->device);
   DevBuf* bufs[] = {&c->levels,  &c->cands,   &c->cand_count, &c->order,   &c->keep,
                     &c->sel,     &c->sel_count, &c->ori_theta, &c->ori_count, &c->rec_off,
-                    &c->rec_total, &c->out_kp, &c->out_desc, &c->out_count, &c->plans,
+                    &c->rec_total, &c->plans,
                     &c->tile_prefix, &c->status, &c->input, &c->dump, &c->stage_kp, &c->stage_desc,
                     &c->prop_theta, &c->prop_imgs, &c->prop_logits, &c->prop_mode, &c->prop_ws,
                     &c->resized, &c->resize_jobs, &c->scfv_model, &c->scfv_desc, &c->scfv_y, &c->scfv_q,
                     &c->scfv_out, &c->scfv_off, &c->out_counters};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
-  for (HostSet& hs : c->hset) {
+  if (c->d2h_stream) {
+    cudaStreamSynchronize(c->d2h_stream);
+    cudaStreamDestroy(c->d2h_stream);
+  }
+  for (StageSet& hs : c->hset) {
     for (HostBuf* h : {&hs.plans, &hs.prefix, &hs.prop, &hs.jobs, &hs.plans2, &hs.small})
       if (h->p) cudaFreeHost(h->p);
-    if (hs.done) cudaEventDestroy(hs.done);
+    for (DevBuf* b : {&hs.input, &hs.out_kp, &hs.out_desc, &hs.out_count})
+      if (b->p) cudaFree(b->p);
+    for (cudaEvent_t ev : {hs.done, hs.in_free, hs.out_free, hs.packed})
+      if (ev) cudaEventDestroy(ev);
   }
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->gstream) cudaStreamDestroy(c->gstream);
@@ -1259,6 +1320,9 @@ cdvs_status cdvs_wait(cdvs_ctx* c, void* cuda_stream) {
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   cudaError_t e = cudaSetDevice(c->device);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  cdvs_status st = flush_readback(c);
+  if (st != CDVS_OK) return st;
+  if (c->d2h_stream && (e = cudaStreamSynchronize(c->d2h_stream)) != cudaSuccess) return cuda_fail(c, e, "readback");
   HostBuf& h = c->hs().small;
   if ((e = ensure_host(h, sizeof(int) * (4 + kMaxOutGroups + 1))) != cudaSuccess ||
       (e = cudaMemcpyAsync(h.p, c->status.p, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
@@ -1380,6 +1444,7 @@ cdvs_status cdvs_scfv(cdvs_ctx* c, int32_t n, const float* desc, const int32_t* 
 
 cdvs_status cdvs_set_graph(cdvs_ctx* c, int32_t enable) {
   if (!c || (enable != 0 && enable != 1)) return CDVS_INVALID_ARGUMENT;
+  if (c->async_open) return fail(c, CDVS_INVALID_ARGUMENT, "asynchronous extractions are pending: call cdvs_wait first");
   c->graph = enable != 0;
   if (!c->graph && c->gexec) {
     cudaSetDevice(c->device);
@@ -1393,6 +1458,7 @@ cdvs_status cdvs_resize(cdvs_ctx* c, int32_t n, const uint8_t* const* images, co
                         int32_t max_side, uint8_t* out, size_t capacity, cdvs_image_desc* out_sizes, uint32_t flags,
                         void* cuda_stream) {
   if (!c) return CDVS_INVALID_ARGUMENT;
+  if (c->async_open) return fail(c, CDVS_INVALID_ARGUMENT, "asynchronous extractions are pending: call cdvs_wait first");
   if (n < 0 || n > kMaxBatch) return fail(c, CDVS_INVALID_ARGUMENT, "n_images must be in 0..4096");
   if (n == 0) return CDVS_OK;
   if (!images || !sizes || !out || !out_sizes) return fail(c, CDVS_INVALID_ARGUMENT, "NULL argument");
@@ -1465,6 +1531,7 @@ cdvs_status cdvs_resize(cdvs_ctx* c, int32_t n, const uint8_t* const* images, co
 
 cdvs_status cdvs_set_proposal(cdvs_ctx* c, const float* params, int32_t n_params) {
   if (!c) return CDVS_INVALID_ARGUMENT;
+  if (c->async_open) return fail(c, CDVS_INVALID_ARGUMENT, "asynchronous extractions are pending: call cdvs_wait first");
   if (!params || n_params != kPropParams) return fail(c, CDVS_INVALID_ARGUMENT, "need CDVS_PROPOSAL_PARAMS floats");
   cudaError_t e;
   // the parameters, then the tensor-core B fragments of conv2 and conv3
@@ -1484,6 +1551,7 @@ cdvs_status cdvs_set_proposal(cdvs_ctx* c, const float* params, int32_t n_params
 cdvs_status cdvs_proposal_logits(cdvs_ctx* c, int32_t n, const uint8_t* const* images, const cdvs_image_desc* sizes,
                                  float* logits_out, int32_t capacity, uint32_t flags, void* cuda_stream) {
   if (!c) return CDVS_INVALID_ARGUMENT;
+  if (c->async_open) return fail(c, CDVS_INVALID_ARGUMENT, "asynchronous extractions are pending: call cdvs_wait first");
   if (!c->prop_set) return fail(c, CDVS_INVALID_ARGUMENT, "no cdvs_set_proposal call");
   if (n < 0 || n > kMaxBatch) return fail(c, CDVS_INVALID_ARGUMENT, "n_images must be in 0..4096");
   if (n == 0) return CDVS_OK;
@@ -1541,6 +1609,7 @@ cdvs_status cdvs_proposal_train_step(cdvs_ctx* c, const uint8_t* images, int32_t
                                      float* grad, float* loss, float* logits, int32_t step, float lr, int32_t bf16,
                                      void* cuda_stream) {
   if (!c) return CDVS_INVALID_ARGUMENT;
+  if (c->async_open) return fail(c, CDVS_INVALID_ARGUMENT, "asynchronous extractions are pending: call cdvs_wait first");
   if (!images || !params || !grad || n < 1 || width < 16 || height < 16 || pitch < width || (bf16 != 0 && bf16 != 1))
     return fail(c, CDVS_INVALID_ARGUMENT, "bad training arguments");
   if (lr > 0.0f && (!adam_m || !adam_v || step < 1 || !labels))

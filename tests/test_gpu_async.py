@@ -2,12 +2,15 @@
 
 * batches enqueued back to back without host synchronisation -- more calls
   than the context has staging sets, different shapes, direct launches and
-  the CUDA graph -- give exactly the records of synchronous calls;
+  the CUDA graph, device buffers or host buffers (page-locked or not) --
+  give exactly the records of synchronous calls;
 * the truncation of any call since the last cdvs_wait is reported by it, and
   only once;
-* the flag's preconditions: device inputs and outputs, and no other call on
-  the context while asynchronous calls are pending.
+* the flag's preconditions: cdvs_extract only, and no other call on the
+  context while asynchronous calls are pending.
 """
+import ctypes as C
+
 import numpy as np
 import pytest
 
@@ -114,10 +117,15 @@ def test_async_preconditions(env):
     dev = cdvs.CDVS_INPUT_DEVICE | cdvs.CDVS_OUTPUT_DEVICE
     b = _Dev(cdvs, _batch(91, 2))
     p = cdvs.params()
-    # host outputs cannot be asynchronous
-    with pytest.raises(cdvs.CdvsError) as ei:
-        b.run(cdvs, ctx, p, cdvs.CDVS_INPUT_DEVICE | cdvs.CDVS_ASYNC, stream)
-    assert ei.value.status == cdvs.CDVS_INVALID_ARGUMENT
+    # cdvs_extract only
+    img = np.zeros((64, 64), np.uint8)
+    sz = np.array([(64, 64, 64)], cdvs.IMAGE_DESC_DTYPE)
+    ptrs = (C.c_void_p * 1)(img.ctypes.data)
+    kp = np.zeros(64, cdvs.KEYPOINT_DTYPE)
+    cnt = np.zeros(1, np.int32)
+    st = ctx._L.cdvs_candidates(ctx.handle, 1, C.cast(ptrs, C.c_void_p), sz.ctypes.data, p.ctypes.data,
+                                kp.ctypes.data, 64, cnt.ctypes.data, cdvs.CDVS_ASYNC, None)
+    assert st == cdvs.CDVS_INVALID_ARGUMENT
     # with calls pending, a synchronous call is refused until cdvs_wait
     b.run(cdvs, ctx, p, dev | cdvs.CDVS_ASYNC, stream)
     with pytest.raises(cdvs.CdvsError) as ei:
@@ -128,3 +136,42 @@ def test_async_preconditions(env):
     assert ctx.wait(stream) == cdvs.CDVS_OK
     assert b.run(cdvs, ctx, p, dev, stream) == cdvs.CDVS_OK
     assert ctx.wait(stream) == cdvs.CDVS_OK  # nothing pending
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_async_host_buffers_equal_synchronous_calls(env, pinned):
+    """Host images in, host records out: each call's records reach its own
+    buffers after cdvs_wait, equal to a synchronous call's, while later
+    batches were enqueued behind it."""
+    import torch
+    cdvs, ctx = env
+    stream = torch.cuda.current_stream()
+    batches = [_batch(101, 4), _batch(102, 3, 320, 200), _batch(103, 5), _batch(104, 2, 333, 257)]
+    ref = [ctx.extract(b) for b in batches]
+
+    def host(shape, dtype):
+        t = torch.zeros(shape, dtype=dtype)
+        return t.pin_memory() if pinned else t
+
+    outs = []
+    for b in batches:
+        n = len(b)
+        flat = host((sum(im.size for im in b),), torch.uint8)
+        flat.numpy()[:] = np.concatenate([im.ravel() for im in b])
+        offs = np.cumsum([0] + [im.size for im in b])
+        ptrs = [flat.data_ptr() + int(o) for o in offs[:-1]]
+        sizes = np.array([(im.shape[1], im.shape[0], im.shape[1]) for im in b], cdvs.IMAGE_DESC_DTYPE)
+        cap = n * 1200
+        kp = host((cap * cdvs.KEYPOINT_DTYPE.itemsize,), torch.uint8)
+        desc = host((cap, 128), torch.float32)
+        cnt = host((n,), torch.int32)
+        assert ctx.extract_raw(n, ptrs, sizes, cdvs.params(), kp, desc, cap, cnt, cdvs.CDVS_ASYNC,
+                               stream) == cdvs.CDVS_OK
+        outs.append((flat, kp, desc, cnt))
+    assert ctx.wait(stream) == cdvs.CDVS_OK
+    for (flat, kp, desc, cnt), (rk, rd, rc, _) in zip(outs, ref):
+        c = cnt.numpy()
+        t = int(c.sum())
+        assert np.array_equal(c, rc)
+        assert np.array_equal(kp.numpy()[:t * cdvs.KEYPOINT_DTYPE.itemsize], rk.view(np.uint8).ravel())
+        assert np.array_equal(desc.numpy()[:t], rd)
