@@ -312,8 +312,9 @@ def run_uneven(args, rank, world, local):
     """Uneven batch: 1024 images with sides in 240..1280 and aspect 0.5..2
     (blob count scaled by area), resized on the GPU to larger side 640 (S0)
     and extracted in one call per step; device-resident inputs and outputs,
-    the call's work replayed as one CUDA graph.  FP32 and FP16 level storage,
-    and the same without the graph."""
+    the call's work replayed as one CUDA graph, calls enqueued asynchronously
+    (CDVS_ASYNC).  FP32 and FP16 level storage, and the same without the
+    graph."""
     import multiprocessing as mp
 
     from paper_1705_09776_gb300 import synth
@@ -340,13 +341,15 @@ def run_uneven(args, rank, world, local):
     def timed(p, graph):
         ctx.set_graph(graph)
         for _ in range(args.warmup):
-            ctx.extract_raw(n, ptrs, desc_sizes, p, d_kp, d_desc, cap, d_cnt, flags, stream)
+            ctx.extract_raw(n, ptrs, desc_sizes, p, d_kp, d_desc, cap, d_cnt, flags | cdvs.CDVS_ASYNC, stream)
+        ctx.wait(stream)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
-            ctx.extract_raw(n, ptrs, desc_sizes, p, d_kp, d_desc, cap, d_cnt, flags, stream)
+            ctx.extract_raw(n, ptrs, desc_sizes, p, d_kp, d_desc, cap, d_cnt, flags | cdvs.CDVS_ASYNC, stream)
         e1.record(stream)
+        ctx.wait(stream)
         torch.cuda.synchronize()
         ctx.set_graph(False)
         return e0.elapsed_time(e1) / args.steps, int(d_cnt.sum().item())
