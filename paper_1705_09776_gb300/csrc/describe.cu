@@ -360,25 +360,31 @@ __device__ __forceinline__ void describe_point(const DescribeArgs& a, const Cand
       const float fx0 = floorf(cx), fy0 = floorf(cy), fo0 = floorf(ob);
       const float fx = cx - fx0, fy = cy - fy0, fo = ob - fo0;
       const int x0 = (int)fx0, y0 = (int)fy0, o0 = (int)fo0;
-      // the scaled orientation shares, then one multiply-add per vote
+      // the scaled orientation shares, then one multiply-add per vote (the
+      // vote wxy * a, a already scaled); the 2 x 2 cells as straight-line
+      // code, each vote pair guarded by its cell lying in the 4 x 4 grid
+      // (x0 and y0 are in -1 .. 3)
       const float ws = w * dsc;
       const float a0 = ws * (1.0f - fo), a1 = ws * fo;
-      unsigned* h0 = hd + (o0 & 7);
-      unsigned* h1 = hd + ((o0 + 1) & 7);
-#pragma unroll
-      for (int iy = 0; iy < 2; ++iy) {
-        const int yy = y0 + iy;
-        if (yy < 0 || yy > 3) continue;
-        const float wy = iy ? fy : 1.0f - fy;
-#pragma unroll
-        for (int ix = 0; ix < 2; ++ix) {
-          const int xx = x0 + ix;
-          if (xx < 0 || xx > 3) continue;
-          const float wxy = wy * (ix ? fx : 1.0f - fx);
-          const int cb = (yy * 4 + xx) * 8;
-          vote(h0 + cb, wxy, a0);  // the vote wxy * a, a already scaled
-          vote(h1 + cb, wxy, a1);
-        }
+      const bool x0ok = x0 >= 0, x1ok = x0 <= 2, y0ok = y0 >= 0, y1ok = y0 <= 2;
+      const float wy0 = 1.0f - fy, wx0 = 1.0f - fx;
+      const int cb = (y0 * 4 + x0) * 8;
+      const int i0 = (o0 & 7) + cb, i1 = ((o0 + 1) & 7) + cb;
+      if (y0ok && x0ok) {
+        vote(hd + i0, wy0 * wx0, a0);
+        vote(hd + i1, wy0 * wx0, a1);
+      }
+      if (y0ok && x1ok) {
+        vote(hd + i0 + 8, wy0 * fx, a0);
+        vote(hd + i1 + 8, wy0 * fx, a1);
+      }
+      if (y1ok && x0ok) {
+        vote(hd + i0 + 32, fy * wx0, a0);
+        vote(hd + i1 + 32, fy * wx0, a1);
+      }
+      if (y1ok && x1ok) {
+        vote(hd + i0 + 40, fy * fx, a0);
+        vote(hd + i1 + 40, fy * fx, a1);
       }
     });
     __syncwarp();
