@@ -328,3 +328,16 @@ def test_fp16_storage_error_is_small(ctx, cd):
     ek, ed, _ = O.extract(img, O.params())
     m = PT.match(gk, ek)
     assert np.mean(m >= 0) > 0.9
+    # descriptors of matched records with the same orientation, per octave:
+    # FP16 levels move gradients by a few 1e-2 grey levels, so errors stay far
+    # below those of a misplaced patch (octaves 1 and 2 are stored transposed)
+    for octs in ((0,), (1, 2, 3)):
+        errs = []
+        for i in np.nonzero((m >= 0) & np.isin(gk["octave"], octs))[0]:
+            same = np.nonzero(PT.match(ek, gk[i:i + 1]) == 0)[0]
+            d = [PT.ang(ek["theta"][j], gk["theta"][i]) for j in same]
+            if d and min(d) < 1e-2:
+                errs.append(PT.rel_l2(gd[i], ed[same[int(np.argmin(d))]]))
+        assert len(errs) > 10, (octs, len(errs))
+        assert np.median(errs) < 1e-2 and np.quantile(errs, 0.9) < 5e-2, (octs, np.median(errs),
+                                                                           np.quantile(errs, 0.9))
