@@ -732,6 +732,10 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
   c->cur_set ^= 1;
   StageSet& hset = c->hs();
   if (hset.done && (e = cudaEventSynchronize(hset.done)) != cudaSuccess) return cuda_fail(c, e, "staging set");
+  // records of this set still waiting to go out (an asynchronous call with
+  // host outputs two calls back, followed by one with device outputs) leave
+  // before this call's packing can overwrite them
+  if (c->pend.on && c->pend.set == c->cur_set && (st = flush_readback(c)) != CDVS_OK) return st;
   for (cudaEvent_t* ev : {&hset.done, &hset.in_free, &hset.out_free, &hset.packed})
     if (!*ev && (e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess)
       return cuda_fail(c, e, "staging set");

@@ -175,3 +175,42 @@ def test_async_host_buffers_equal_synchronous_calls(env, pinned):
         assert np.array_equal(c, rc)
         assert np.array_equal(kp.numpy()[:t * cdvs.KEYPOINT_DTYPE.itemsize], rk.view(np.uint8).ravel())
         assert np.array_equal(desc.numpy()[:t], rd)
+
+
+def test_async_mixed_host_and_device_outputs(env):
+    """Host outputs, then device outputs, then host outputs again: the third
+    call reuses the first call's staging set, so the first call's records
+    must leave before the third call packs its own."""
+    import torch
+    cdvs, ctx = env
+    stream = torch.cuda.current_stream()
+    a, b, c = _batch(111, 3), _batch(112, 2, 320, 200), _batch(113, 4)
+    ref = [ctx.extract(x) for x in (a, c)]
+    dev_b = _Dev(cdvs, b)
+    dev_b.run(cdvs, ctx, cdvs.params(), cdvs.CDVS_INPUT_DEVICE | cdvs.CDVS_OUTPUT_DEVICE, stream)
+    torch.cuda.synchronize()
+    ref_b = dev_b.result(cdvs)
+
+    def host_call(imgs):
+        n = len(imgs)
+        flat = torch.from_numpy(np.concatenate([im.ravel() for im in imgs])).pin_memory()
+        offs = np.cumsum([0] + [im.size for im in imgs])
+        sizes = np.array([(im.shape[1], im.shape[0], im.shape[1]) for im in imgs], cdvs.IMAGE_DESC_DTYPE)
+        cap = n * 1200
+        kp = torch.zeros(cap * cdvs.KEYPOINT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+        desc = torch.zeros(cap, 128, dtype=torch.float32).pin_memory()
+        cnt = torch.zeros(n, dtype=torch.int32).pin_memory()
+        ctx.extract_raw(n, [flat.data_ptr() + int(o) for o in offs[:-1]], sizes, cdvs.params(), kp, desc, cap,
+                        cnt, cdvs.CDVS_ASYNC, stream)
+        return flat, kp, desc, cnt
+
+    out_a = host_call(a)
+    dev_b.run(cdvs, ctx, cdvs.params(), cdvs.CDVS_INPUT_DEVICE | cdvs.CDVS_OUTPUT_DEVICE | cdvs.CDVS_ASYNC, stream)
+    out_c = host_call(c)
+    assert ctx.wait(stream) == cdvs.CDVS_OK
+    assert _same(dev_b.result(cdvs), ref_b)
+    for (flat, kp, desc, cnt), (rk, rd, rc, _) in zip((out_a, out_c), ref):
+        t = int(cnt.numpy().sum())
+        assert np.array_equal(cnt.numpy(), rc)
+        assert np.array_equal(kp.numpy()[:t * cdvs.KEYPOINT_DTYPE.itemsize], rk.view(np.uint8).ravel())
+        assert np.array_equal(desc.numpy()[:t], rd)
