@@ -141,6 +141,8 @@ const char *cdvs_last_error(const cdvs_ctx *ctx);
  *                  bins fastest; unit L2 norm
  *   kp_count[i]    records written for image i (host, or device with
  *                  CDVS_OUTPUT_DEVICE)
+ *   flags          CDVS_INPUT_DEVICE, CDVS_OUTPUT_DEVICE, CDVS_ASYNC (return once
+ *                  the batch is enqueued; see cdvs_wait)
  * Returns CDVS_CAPACITY_TRUNCATED if kp_capacity was too small (records are
  * dropped from the end of the batch) or an image had more candidates than the
  * internal queue holds.

@@ -294,7 +294,9 @@ class Context:
         return kp[:tot].copy(), desc[:tot].copy(), cnt, st
 
     def extract_raw(self, n, image_ptrs, sizes, p, kp_out, desc_out, capacity, counts, flags, stream=None):
-        """cdvs_extract with caller-provided pointers (ints) -- no copies here."""
+        """cdvs_extract with caller-provided pointers (ints) -- no copies here.
+        With CDVS_ASYNC in flags the call returns once the batch is enqueued;
+        wait() completes the outstanding calls and returns their status."""
         ptrs = (C.c_void_p * n)(*image_ptrs)
         st = self._L.cdvs_extract(self.handle, n, C.cast(ptrs, C.c_void_p), _ptr(sizes), _ptr(p), _ptr(kp_out),
                                   _ptr(desc_out), capacity, _ptr(counts), flags, _stream_handle(stream))
