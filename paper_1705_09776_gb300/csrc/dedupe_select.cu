@@ -21,17 +21,14 @@ namespace {
 
 constexpr int kSelThreads = 512;
 
-struct SelEntry {
-  float absr, y, x, sigma;
-  int octave, idx;
-};
-
-__device__ __forceinline__ bool ranks_before(const SelEntry& a, const SelEntry& b) {
-  if (a.absr != b.absr) return a.absr > b.absr;
-  if (a.y != b.y) return a.y < b.y;
-  if (a.x != b.x) return a.x < b.x;
-  if (a.sigma != b.sigma) return a.sigma < b.sigma;
-  return a.octave < b.octave;
+// A tie-list entry, as two arrays: the keys (|response|, y, x, sigma in image
+// px) in a float4 and (octave, candidate index) in an int2.
+__device__ __forceinline__ bool ranks_before(const float4& ka, int oa, const float4& kb, int ob) {
+  if (ka.x != kb.x) return ka.x > kb.x;
+  if (ka.y != kb.y) return ka.y < kb.y;
+  if (ka.z != kb.z) return ka.z < kb.z;
+  if (ka.w != kb.w) return ka.w < kb.w;
+  return oa < ob;
 }
 
 // exclusive scan of cnt[0..n) in place (block-wide); returns the total
@@ -209,8 +206,8 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(const __grid_consta
   }
 
   // ---- gather candidates at or above the threshold and sort them
-  SelEntry* list = reinterpret_cast<SelEntry*>(smem4);  // reuses the cell counters
-  int* perm = reinterpret_cast<int*>(list + a.list_cap);
+  float4* key = smem4;  // reuses the cell counters
+  int2* aux = reinterpret_cast<int2*>(key + a.list_cap);
   if (tid == 0) s_misc[3] = 0;
   __syncthreads();
   for (int i = tid; i < n; i += kSelThreads) {
@@ -220,43 +217,34 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(const __grid_consta
     const int pos = atomicAdd(s_misc + 3, 1);
     if (pos >= a.list_cap) continue;
     const float s = (float)(1 << C[i].octave);
-    SelEntry e;
-    e.absr = ar;
-    e.y = C[i].yo * s;
-    e.x = C[i].xo * s;
-    e.sigma = C[i].so * s;
-    e.octave = C[i].octave;
-    e.idx = i;
-    list[pos] = e;
+    key[pos] = make_float4(ar, C[i].yo * s, C[i].xo * s, C[i].so * s);
+    aux[pos] = make_int2(C[i].octave, i);
   }
   __syncthreads();
   const int L = min(s_misc[3], a.list_cap);
   if (tid == 0 && s_misc[3] > a.list_cap) atomicOr(a.status, kStatusSelectOverflow);
   int Pn = 1;
   while (Pn < L) Pn <<= 1;
-  for (int i = tid; i < Pn; i += kSelThreads) {
-    if (i >= L) {
-      SelEntry e;
-      e.absr = -1.0f;
-      e.x = e.y = e.sigma = 0.0f;
-      e.octave = 0x7fffffff;
-      e.idx = -1;
-      list[i] = e;
-    }
-    perm[i] = i;
+  for (int i = L + tid; i < Pn; i += kSelThreads) {  // padding that ranks last
+    key[i] = make_float4(-1.0f, 0.0f, 0.0f, 0.0f);
+    aux[i] = make_int2(0x7fffffff, -1);
   }
   __syncthreads();
+  // bitonic sort of the entries in place
   for (int k = 2; k <= Pn; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
       for (int i = tid; i < Pn; i += kSelThreads) {
         const int l = i ^ j;
         if (l > i) {
-          const int pi = perm[i], pl = perm[l];
+          const float4 ki = key[i], kl = key[l];
+          const int2 ai = aux[i], al = aux[l];
           const bool asc = (i & k) == 0;  // ascending in "rank" order
-          const bool swap = asc ? ranks_before(list[pl], list[pi]) : ranks_before(list[pi], list[pl]);
+          const bool swap = asc ? ranks_before(kl, al.x, ki, ai.x) : ranks_before(ki, ai.x, kl, al.x);
           if (swap) {
-            perm[i] = pl;
-            perm[l] = pi;
+            key[i] = kl;
+            key[l] = ki;
+            aux[i] = al;
+            aux[l] = ai;
           }
         }
       }
@@ -265,24 +253,26 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(const __grid_consta
   }
   const int cnt = min(N, L);
   Cand* out = a.sel + (size_t)img * N;
-  for (int r = tid; r < cnt; r += kSelThreads) out[r] = C[list[perm[r]].idx];
+  for (int r = tid; r < cnt; r += kSelThreads) out[r] = C[aux[r].y];
   if (tid == 0) a.sel_count[img] = cnt;
 }
 
 }  // namespace
 
 // The tie list holds the N selected candidates and any that tie with the
-// N-th: 2N entries (at least 1024, at most kSelectList).  Sized by N, the
-// shared memory of N = 300 (32 KB, the cell counters) lets four CTAs share an
-// SM, so a 256-image batch selects in one wave; a fixed 4096-entry list
-// (115 KB) had allowed one CTA per SM and two waves.
+// N-th: 2N entries (at least 1024, at most kSelectList) of 24 bytes, sorted
+// in place.  Sized by N, the shared memory of N = 300 is the 32 KB of cell
+// counters, and three CTAs share an SM (as many as the registers allow), so a
+// 256-image batch selects in one wave; N = 2000 takes 96 KB, two CTAs per SM.
+// A fixed 4096-entry list with a separate permutation (115 KB) had allowed
+// one CTA per SM.
 cudaError_t launch_select(const SelectArgs& args, int n_images, cudaStream_t s) {
   if (n_images <= 0) return cudaSuccess;
   SelectArgs a = args;
   a.list_cap = 1024;
   while (a.list_cap < 2 * a.N && a.list_cap < kSelectList) a.list_cap <<= 1;
   const size_t smem_cells = sizeof(int) * (kMaxCells + 1);
-  const size_t smem_list = (sizeof(SelEntry) + sizeof(int)) * (size_t)a.list_cap;
+  const size_t smem_list = (sizeof(float4) + sizeof(int2)) * (size_t)a.list_cap;
   const size_t smem = smem_cells > smem_list ? smem_cells : smem_list;
   cudaError_t e = cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
