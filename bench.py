@@ -233,6 +233,32 @@ def run_e2e(ctx, imgs, sizes, p, cap, stream, args, barrier, dist, cdvs, torch):
     return e2e_ms, e2e_records
 
 
+def run_per_image(ctx, cdvs, torch, dptrs, sizes, p, d_kp, d_desc, d_cnt, stream, passes=3):
+    """The batched call against one image per call: the same images, device-
+    resident, one cdvs_extract per image (enqueued asynchronously, so host
+    work overlaps the GPU); images/s over `passes` passes over the batch."""
+    n = len(dptrs)
+    flags = cdvs.CDVS_INPUT_DEVICE | cdvs.CDVS_OUTPUT_DEVICE | cdvs.CDVS_ASYNC
+    cap1 = int(p["max_keypoints"][0]) * int(p["max_orientations"][0])
+
+    def one_pass():
+        for i in range(n):
+            ctx.extract_raw(1, [dptrs[i]], sizes[i:i + 1], p, d_kp, d_desc, cap1, d_cnt[i:i + 1], flags, stream)
+
+    one_pass()
+    ctx.wait(stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(passes):
+        one_pass()
+    e1.record(stream)
+    ctx.wait(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / passes
+    return {"value": n / (ms * 1e-3), "unit": "images/s", "ms_per_batch": ms, "calls_per_batch": n}
+
+
 def record_keys(kp):
     k = np.stack([kp["image"], kp["octave"], kp["x"].view(np.int32), kp["y"].view(np.int32),
                   kp["sigma"].view(np.int32), kp["theta"].view(np.int32)], 1)
@@ -619,6 +645,10 @@ def main():
         e2e_ms, e2e_records = run_e2e(ctx, imgs, sizes, p, cap, stream, args, barrier, dist, cdvs, torch)
     h2d = n * H * W
     d2h = n * 4 + e2e_records * (cdvs.KEYPOINT_DTYPE.itemsize + 128 * 4) + 8
+    try:
+        per_image = run_per_image(ctx, cdvs, torch, dptrs, sizes, p, d_kp, d_desc, d_cnt, stream)
+    except Exception as ex:  # reported, never fatal to the main line
+        per_image = {"error": str(ex)}
     # ---- roofline of the dominant kernel: the octave-0 detection launch (K1)
     peaks = load_peaks()
     flops_o, bytes_o = detect_counts(p)
@@ -654,6 +684,7 @@ def main():
                    "ms_per_step": e2e_ms if e2e_ms == e2e_ms else None,
                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
            "gpu_launches": launches, "roofline": roofline, "clocks": clocks}
+    out["one_image_per_call"] = per_image
     if learned is not None:
         out["learned"] = learned
     if scfv is not None:
