@@ -47,7 +47,7 @@ typedef enum {
 /* flags */
 #define CDVS_INPUT_DEVICE 0x1u   /* image pointers (and point lists) are device memory */
 #define CDVS_OUTPUT_DEVICE 0x2u  /* output buffers are device memory */
-#define CDVS_ASYNC 0x4u          /* cdvs_extract only, with both flags above: see cdvs_wait */
+#define CDVS_ASYNC 0x4u          /* cdvs_extract only: see cdvs_wait */
 
 /* Level storage types (cdvs_params.storage). */
 #define CDVS_STORAGE_FP32 0

@@ -97,3 +97,20 @@ def test_transform_ternary_bit_exact_with_oracle():
     # the stand-in thresholds split every element roughly in thirds on fresh images
     frac = [(q == s).mean() for s in (-1, 0, 1)]
     assert all(0.2 < f < 0.5 for f in frac), frac
+
+
+def test_header_constants_match_the_binding():
+    """Every flag, storage type and size the header defines has the same value
+    in the Python binding."""
+    src = open(os.path.join(ROOT, "include", "cdvs.h")).read()
+    defs = {k: int(v, 0) for k, v in re.findall(r"#define (CDVS_[A-Z0-9_]+) (0x[0-9a-fA-F]+|[0-9]+)u?\b", src)}
+    assert {"CDVS_INPUT_DEVICE", "CDVS_OUTPUT_DEVICE", "CDVS_ASYNC", "CDVS_STORAGE_FP16"} <= set(defs)
+    for k, v in defs.items():
+        py = k if hasattr(cdvs, k) else k[len("CDVS_"):]
+        if hasattr(cdvs, py):
+            assert getattr(cdvs, py) == v, k
+    assert cdvs.PROPOSAL_PARAMS == defs["CDVS_PROPOSAL_PARAMS"]
+    # the status codes of the enum
+    enum = dict((n, int(v)) for n, v in re.findall(r"\b(CDVS_[A-Z_]+) = ([0-9]+)", src))
+    for n, v in enum.items():
+        assert getattr(cdvs, n) == v, n
