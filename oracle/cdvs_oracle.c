@@ -493,17 +493,14 @@ static inline void gradient(const double *G, int W, int H, int u, int v, double 
     *gy = G[(size_t)clampi(v + 1, 0, H - 1) * W + u] - G[(size_t)clampi(v - 1, 0, H - 1) * W + u];
 }
 
-/* Sec. IV-B / Alg. 2 stage A: gradients of the pixels closer than
- * ori_radius * sigma vote, with weight |g| * exp(-d^2 / (2 (1.5 sigma)^2)),
- * into a 36-bin histogram of atan2(gy, gx); every bin that is a local maximum
- * (strictly above both circular neighbours) and above ori_peak_ratio times
- * the highest bin gives an orientation, refined by a parabola through the bin
- * and its neighbours.  Peaks are returned by bin value descending. */
-int oracle_orientations(const double *G, int W, int H, double xo, double yo, double so,
-                        const oracle_params *p, double *thetas, double *hist36) {
+/* Sec. IV-B / Alg. 2 stage A, the histogram: gradients of the pixels closer
+ * than ori_radius * sigma vote, with weight |g| * exp(-d^2 / (2 (w sigma)^2)),
+ * w = ori_weight_sigma, into 36 bins of atan2(gy, gx) (bin b covers angles
+ * [b, b + 1) * 2 pi / 36, hard assignment, no smoothing). */
+void oracle_orientation_hist(const double *G, int W, int H, double xo, double yo, double so,
+                             const oracle_params *p, double *h) {
     const double m = p->margin;
-    double h[36];
-    memset(h, 0, sizeof(h));
+    memset(h, 0, sizeof(double) * 36);
     /* the disc membership (distance < ori_radius * sigma) is a threshold
      * decision too: the bracketing runs move the radius by the margin */
     const double R = p->ori_radius * so * (1.0 + m), R2 = R * R;
@@ -527,9 +524,18 @@ int oracle_orientations(const double *G, int W, int H, double xo, double yo, dou
             h[b] += w;
         }
     }
+}
+
+/* Sec. IV-B / Alg. 2 stage A, the peaks: every bin that is a local maximum
+ * (strictly above both circular neighbours) and above ori_peak_ratio times
+ * the highest bin gives an orientation, refined to the vertex of the parabola
+ * through the bin and its two neighbours (bin centres at b + 1/2).  At most
+ * max_orientations are returned, by bin value descending, ties by bin index
+ * ascending. */
+int oracle_orientation_peaks(const double *h, const oracle_params *p, double *thetas) {
+    const double m = p->margin;
     double mx = 0.0;
     for (int b = 0; b < 36; ++b) mx = h[b] > mx ? h[b] : mx;
-    if (hist36) memcpy(hist36, h, sizeof(h));
     double pv[36], pt[36];
     int pb[36], np = 0;
     for (int b = 0; b < 36; ++b) {
@@ -557,16 +563,26 @@ int oracle_orientations(const double *G, int W, int H, double xo, double yo, dou
     return n;
 }
 
+/* Sec. IV-B / Alg. 2 stage A: the histogram, then its peaks. */
+int oracle_orientations(const double *G, int W, int H, double xo, double yo, double so,
+                        const oracle_params *p, double *thetas, double *hist36) {
+    double h[36];
+    oracle_orientation_hist(G, W, H, xo, yo, so, p, h);
+    if (hist36) memcpy(hist36, h, sizeof(h));
+    return oracle_orientation_peaks(h, p, thetas);
+}
+
 /* ------------------------------------------------ S10: descriptor */
 
-/* Sec. IV-B / Alg. 2 stage B: the pixels closer than desc_radius * sigma are
- * rotated by -theta into a 4 x 4 grid of cells of side cell_side * sigma;
- * each gradient (angle relative to theta) is spread trilinearly over the two
- * nearest cells in x and y and the two nearest of 8 orientation bins, with
- * weight |g| * exp(-(u^2 + v^2) / (2 desc_weight_sigma^2)), (u, v) in cells.
- * The 128 values are L2-normalised, clamped at 0.2 and renormalised. */
-void oracle_descriptor(const double *G, int W, int H, double xo, double yo, double so,
-                       double theta, const oracle_params *p, double *d) {
+/* Sec. IV-B / Alg. 2 stage B, the votes: the pixels closer than
+ * desc_radius * sigma are rotated by -theta into a 4 x 4 grid of cells of
+ * side cell_side * sigma; each gradient (angle relative to theta) is spread
+ * trilinearly over the two nearest cells in x and y and the two nearest of 8
+ * orientation bins, with weight |g| * exp(-(u^2 + v^2) / (2 desc_weight_sigma^2)),
+ * (u, v) in cells.  h gets the 128 unnormalised sums, cells row-major (y, x),
+ * 8 bins fastest. */
+void oracle_descriptor_hist(const double *G, int W, int H, double xo, double yo, double so,
+                            double theta, const oracle_params *p, double *d) {
     memset(d, 0, sizeof(double) * 128);
     /* disc membership (distance < desc_radius * sigma), bracketed like every
      * other threshold decision */
@@ -611,6 +627,13 @@ void oracle_descriptor(const double *G, int W, int H, double xo, double yo, doub
             }
         }
     }
+}
+
+/* Sec. IV-B / Alg. 2 stage B: the votes, then the 128 values L2-normalised,
+ * clamped at 0.2 and renormalised. */
+void oracle_descriptor(const double *G, int W, int H, double xo, double yo, double so,
+                       double theta, const oracle_params *p, double *d) {
+    oracle_descriptor_hist(G, W, H, xo, yo, so, theta, p, d);
     double n2 = 0.0;
     for (int i = 0; i < 128; ++i) n2 += d[i] * d[i];
     if (n2 <= 0.0) return;

@@ -119,6 +119,14 @@ void oracle_dedupe(const oracle_kp *c, int n, const oracle_params *p, uint8_t *k
 int oracle_select(const oracle_kp *c, const uint8_t *keep, int n, const oracle_params *p,
                   int *order);
 
+/* S9 histogram alone: h[36] gets the weighted votes of the disc. */
+void oracle_orientation_hist(const double *G, int W, int H, double xo, double yo, double so,
+                             const oracle_params *p, double *h);
+/* S9 peaks of a 36-bin histogram h: up to max_orientations angles in [0, 2 pi). */
+int oracle_orientation_peaks(const double *h, const oracle_params *p, double *thetas);
+/* S10 votes alone: the 128 unnormalised trilinear sums. */
+void oracle_descriptor_hist(const double *G, int W, int H, double xo, double yo, double so,
+                            double theta, const oracle_params *p, double *d);
 /* S9: orientation histogram (36 bins) and up to max_orientations peaks. */
 int oracle_orientations(const double *G, int W, int H, double xo, double yo, double so,
                         const oracle_params *p, double *thetas, double *hist36);

@@ -80,6 +80,8 @@ def lib():
             "oracle_select": (i32, [P, P, i32, P, P]),
             "oracle_orientations": (i32, [P, i32, i32, f64, f64, f64, P, P, P]),
             "oracle_descriptor": (None, [P, i32, i32, f64, f64, f64, f64, P, P]),
+            "oracle_orientation_peaks": (i32, [P, P, P]),
+            "oracle_descriptor_hist": (None, [P, i32, i32, f64, f64, f64, f64, P, P]),
             "oracle_desc_level": (i32, [P, f64]),
             "oracle_extract": (i32, [P, i32, i32, i32, P, P, P, i32, P]),
             "oracle_candidates": (i32, [P, i32, i32, i32, P, P, i32]),
@@ -240,6 +242,23 @@ def descriptor(G, xo, yo, so, theta, p):
     lib().oracle_descriptor(_p(a), a.shape[1], a.shape[0], float(xo), float(yo), float(so),
                             float(theta), _p(p), _p(d))
     return d
+
+
+def orientation_peaks(hist36, p):
+    """The S9 peak rule alone on a given 36-bin histogram."""
+    h = np.ascontiguousarray(hist36, np.float64).reshape(36)
+    th = np.zeros(36)
+    n = lib().oracle_orientation_peaks(_p(h), _p(p), _p(th))
+    return th[:n].copy()
+
+
+def descriptor_hist(G, xo, yo, so, theta, p):
+    """The S10 votes alone: 128 unnormalised sums, shape (4, 4, 8) = (cy, cx, bin)."""
+    a = np.ascontiguousarray(G, np.float64)
+    d = np.zeros(128)
+    lib().oracle_descriptor_hist(_p(a), a.shape[1], a.shape[0], float(xo), float(yo), float(so),
+                                 float(theta), _p(p), _p(d))
+    return d.reshape(4, 4, 8)
 
 
 def desc_level(p, so):

@@ -422,16 +422,99 @@ def test_orientation_of_a_ramp(P, phi_deg):
 
 
 def test_orientation_peaks_rule(P):
-    """Two ramps in the two halves of a patch: two bins, both returned when the
-    weaker is above 0.8 of the stronger, ordered by value."""
+    """Two ramps in the two halves of a patch give two dominant bins: every
+    local maximum above 0.8 of the highest is returned, by value, and no
+    other bin is."""
     yy, xx = np.mgrid[0:61, 0:61].astype(np.float64)
     G = np.where(yy < 30, 3.0 * xx, 2.7 * yy + 3.0 * 30)   # gradient along x above, along y below
     th, hist = O.orientations(G, 30, 30, 2.0, P)
-    assert th.size >= 1
-    vals = sorted(hist[hist > 0], reverse=True)
-    for t in th:
-        b = int(t * 36 / (2 * math.pi))
-        assert hist[b] > 0.8 * max(hist)
+    l, r = np.roll(hist, 1), np.roll(hist, -1)
+    want = [b for b in range(36) if hist[b] > l[b] and hist[b] > r[b] and hist[b] > 0.8 * hist.max()]
+    want = sorted(want, key=lambda b: (-hist[b], b))[:4]
+    got = [int(t * 36 / (2 * math.pi)) % 36 for t in th]
+    assert got == want and len(got) >= 1
+
+
+@pytest.mark.parametrize("x0", [5.5, 5.83, 5.21, 0.3, 35.9, 17.64])
+def test_orientation_peak_is_the_parabola_vertex(P, x0):
+    """Three bins sampled from an exact parabola y = A - B (x - x0)^2 at the
+    bin centres (bin b is centred at b + 1/2, in bin units): the refined angle
+    is the parabola's own vertex, 2 pi x0 / 36, on either side of the centre
+    and across the wrap at bin 0 / 35."""
+    A, Bc = 10.0, 1.7
+    b = int(math.floor(x0))
+    h = np.zeros(36)
+    for j in (b - 1, b, b + 1):
+        h[j % 36] = A - Bc * ((j + 0.5) - x0) ** 2
+    th = O.orientation_peaks(h, P)
+    assert th.size == 1
+    want = (2 * math.pi * x0 / 36) % (2 * math.pi)
+    assert abs(th[0] - want) < 1e-12, (th[0], want)
+
+
+def test_orientation_peak_ratio_and_order(P):
+    """Sec. IV-B: a bin is an orientation when it is a local maximum above
+    0.8 x the highest bin (strictly); peaks come out by value, at most 4."""
+    def peaks(vals):
+        h = np.zeros(36)
+        for b, v in vals.items():
+            h[b] = v
+        return [int(round(t * 36 / (2 * math.pi) - 0.5)) % 36 for t in O.orientation_peaks(h, P)]
+
+    assert peaks({3: 1.0, 20: 0.85}) == [3, 20]
+    assert peaks({3: 0.85, 20: 1.0}) == [20, 3]        # by value, not by bin
+    assert peaks({3: 1.0, 20: 0.75}) == [3]
+    assert peaks({3: 1.0, 20: 0.8}) == [3]             # strictly above 0.8 x max
+    assert peaks({3: 1.0, 20: 0.8000001}) == [3, 20]
+    assert peaks({3: 1.0, 9: 1.0}) == [3, 9]           # equal values: lower bin first
+    six = {2: 0.95, 8: 0.99, 14: 0.96, 20: 1.0, 26: 0.98, 32: 0.97}
+    assert peaks(six) == [20, 8, 26, 32]               # the 4 largest, by value
+    assert peaks({4: 1.0, 5: 1.0}) == []               # a plateau is not strictly above its neighbour
+    assert peaks({4: 1.0, 5: 0.9}) == [4]              # a shoulder is no peak
+
+
+def _voters(shape, spec):
+    """A patch whose only non-zero central-difference gradients inside the
+    sampling disc are chosen pixels: for a pixel P and an outward unit step
+    e, G = a at P + e gives P the gradient a e and moves the other three
+    pixels that see it (P + 2e, P + e +- e_perp) further out."""
+    G = np.zeros(shape)
+    for (u, v), (ex, ey), a in spec:
+        G[v + ey, u + ex] += a
+    return G
+
+
+def test_orientation_vote_weight_closed_form(P):
+    """Alg. 2 stage A with one gradient sample inside the disc: the bin of its
+    angle gets |g| exp(-d^2 / (2 (1.5 sigma)^2)), every other bin nothing.
+    sigma = 2: disc radius 3.96 x 2 = 7.92 px, the voter at d = 7.7 px
+    (gradient along +x, bin 0) and the others of its bump beyond 8.7 px."""
+    xo, yo, so = 30.3, 30.0, 2.0
+    G = _voters((61, 61), [((38, 30), (1, 0), 1.0)])
+    th, h = O.orientations(G, xo, yo, so, P)
+    want = math.exp(-7.7 ** 2 / (2 * (1.5 * 2.0) ** 2))
+    assert h[0] == pytest.approx(want, rel=1e-12)
+    assert np.count_nonzero(h) == 1
+    assert th.size == 1 and abs(th[0] - 2 * math.pi * 0.5 / 36) < 1e-12
+
+
+@pytest.mark.parametrize("ratio,n_peaks", [(0.85, 2), (0.75, 1), (1 / 0.85, 2), (1 / 0.75, 1)])
+def test_orientation_two_voters_peak_rule(P, ratio, n_peaks):
+    """Two gradient samples at d = 7.7 px (angle 0, bin 0) and d' = 7.3 px
+    (angle pi, bin 18), with magnitudes set so that their weighted votes are
+    in a given ratio: with the weight window exp(-d^2 / (2 (1.5 sigma)^2))
+    the weaker one is an orientation at 0.85 of the stronger and not at 0.75,
+    and the stronger comes first."""
+    xo, yo, so = 30.3, 30.0, 2.0
+    w = lambda d: math.exp(-d * d / 18.0)
+    a2 = ratio * w(7.7) / w(7.3)   # vote(bin 18) / vote(bin 0) = ratio
+    G = _voters((61, 61), [((38, 30), (1, 0), 1.0), ((23, 30), (-1, 0), a2)])
+    th, h = O.orientations(G, xo, yo, so, P)
+    assert np.count_nonzero(h) == 2
+    assert h[18] / h[0] == pytest.approx(ratio, rel=1e-12)
+    bins = [int(round(t * 36 / (2 * math.pi) - 0.5)) % 36 for t in th]
+    strong, weak = (0, 18) if ratio < 1 else (18, 0)
+    assert bins == [strong, weak][:n_peaks]
 
 
 # ------------------------------------------------------- S10 descriptor
@@ -469,6 +552,65 @@ def test_descriptor_of_a_ramp_uses_only_two_orientation_bins(P):
             assert cell[(b0 + 1) % 8] / cell[b0 % 8] == pytest.approx(f / (1 - f), rel=1e-9)
             n_cells += 1
     assert n_cells >= 4
+
+
+def test_descriptor_single_vote_by_hand(P):
+    """Alg. 2 stage B with one gradient sample inside the 6 sigma disc: its
+    vote lands in the cells and bins predicted by hand from cells of side
+    3 sigma centred on the keypoint (cell coordinate u + 1.5), the weight
+    |g| exp(-(u^2 + v^2) / 8) with (u, v) in cells, and the trilinear split.
+
+    sigma = 1.25: disc radius 7.5 px, cell side 3.75 px.  The voter sits 6.75
+    px right of the keypoint (u = 1.8 cells, v = 0) with gradient (1, 0); the
+    rest of its bump lies beyond 7.8 px."""
+    xo, yo, so = 30.25, 30.0, 1.25
+    G = _voters((61, 61), [((37, 30), (1, 0), 1.0)])
+    wgt = math.exp(-(1.8 ** 2) / 8.0)
+    # theta = 0: x cell 1.8 + 1.5 = 3.3 -> cell 3 with 0.7 (cell 4 is outside
+    # the grid); y cell 1.5 -> cells 1 and 2 with 0.5 each; angle 0 -> bin 0
+    h = O.descriptor_hist(G, xo, yo, so, 0.0, P)
+    want = np.zeros((4, 4, 8))
+    want[1, 3, 0] = want[2, 3, 0] = wgt * 0.7 * 0.5
+    assert np.allclose(h, want, rtol=0, atol=1e-13), np.argwhere(h != 0)
+    # theta = pi / 2: the offset rotates by -pi / 2 to (0, -1.8) cells, so y
+    # cell -0.3 -> row 0 with 0.7 (row -1 is outside); x cell 1.5 -> cells 1
+    # and 2 with 0.5; the angle relative to theta is 3 pi / 2 -> bin 6
+    h = O.descriptor_hist(G, xo, yo, so, math.pi / 2, P)
+    want = np.zeros((4, 4, 8))
+    want[0, 1, 6] = want[0, 2, 6] = wgt * 0.7 * 0.5
+    assert np.allclose(h, want, rtol=0, atol=1e-13), np.argwhere(h != 0)
+
+
+def test_descriptor_single_vote_off_axis(P):
+    """An off-axis voter: offset (6, 3) px at sigma = 1.15 (disc 6.9 px, cell
+    side 3.45 px), gradient (2, 0), orientation theta = 0.  Cells: x = 6 / 3.45
+    + 1.5, y = 3 / 3.45 + 1.5; weight 2 exp(-((6^2 + 3^2) / 3.45^2) / 8); the
+    orientation split of angle 0 - theta."""
+    xo, yo, so = 30.0, 30.0, 1.15
+    G = _voters((61, 61), [((36, 33), (1, 0), 2.0)])
+    cx, cy = 6 / 3.45 + 1.5, 3 / 3.45 + 1.5          # 3.2391.., 2.3695..
+    fx, fy = cx - 3, cy - 2
+    wgt = 2.0 * math.exp(-(45 / 3.45 ** 2) / 8.0)
+    h = O.descriptor_hist(G, xo, yo, so, 0.0, P)
+    want = np.zeros((4, 4, 8))
+    want[2, 3, 0] = wgt * (1 - fy) * (1 - fx)
+    want[3, 3, 0] = wgt * fy * (1 - fx)
+    assert np.allclose(h, want, rtol=0, atol=1e-13), np.argwhere(h != 0)
+    # theta = -pi / 8 (i.e. 15 pi / 8): the gradient is at +pi / 8 relative to
+    # theta, half-way between bins 0 and 1 (bin width pi / 4)
+    t = -math.pi / 8
+    h = O.descriptor_hist(G, xo, yo, so, t, P)
+    u = (math.cos(t) * 6 + math.sin(t) * 3) / 3.45
+    v = (-math.sin(t) * 6 + math.cos(t) * 3) / 3.45
+    assert u * u + v * v == pytest.approx(45 / 3.45 ** 2, rel=1e-12)   # rotation keeps the radius
+    cx, cy = u + 1.5, v + 1.5                         # 2.774.., 2.969..
+    assert (math.floor(cx), math.floor(cy)) == (2, 2)
+    fx, fy = cx - 2, cy - 2
+    want = np.zeros((4, 4, 8))
+    for yy, wy in ((2, 1 - fy), (3, fy)):
+        for xx, wx in ((2, 1 - fx), (3, fx)):
+            want[yy, xx, 0] = want[yy, xx, 1] = wgt * wy * wx * 0.5
+    assert np.allclose(h, want, rtol=0, atol=1e-13), np.argwhere(h != 0)
 
 
 # ------------------------------------------------------- S11 transform + ternary
