@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 N_IMAGES, WIDTH, HEIGHT, BASE_SEED = 256, 640, 480, 1
 UNEVEN_SEED = 3
 METRIC = "images/s CDVS keypoints+descriptors @640px (batched/learned vs plain), HBM GB/s"
-SM_COUNT, FP32_LANES_PER_SM, MAX_SM_MHZ = 152, 128, 2070.0
+FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (Blackwell SM: 4 partitions x 32)
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k1_detect_traffic.json")
 
 
@@ -76,6 +76,51 @@ def detect_counts(p, width=None, height=None):
         byts.append((w * h if o == 0 else 4 * w * h) + 4 * levels_written * w * h + decimated)
         w, h = (w + 1) // 2, (h + 1) // 2
     return flops, byts
+
+
+def resize_target(w, h, max_side):
+    """S0 output size: the larger side becomes max_side, the other is scaled and
+    rounded to nearest, ties to even (the library's rule)."""
+    if max_side <= 0 or max(w, h) <= max_side:
+        return w, h
+
+    def rhe(num, den):
+        q, r = divmod(num, den)
+        return q + (1 if 2 * r > den or (2 * r == den and q & 1) else 0)
+    if w >= h:
+        return max_side, max(1, rhe(h * max_side, w))
+    return max(1, rhe(w * max_side, h)), max_side
+
+
+def alu_peak_tflops(torch, local, sm_mhz):
+    """FP32 peak derived from the device: SMs x 128 FMA lanes x 2 flop x the
+    SM clock (the maximum clock nvidia-smi reports)."""
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    return sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12, sms
+
+
+def measure_sgemm_tflops(torch, n=8192, reps=5):
+    """A measured FP32 (non-tensor) throughput: cuBLAS SGEMM n^3 with TF32 off,
+    best of `reps` after a warm-up, CUDA events."""
+    old = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        a = torch.randn(n, n, device="cuda")
+        b = torch.randn(n, n, device="cuda")
+        c = a @ b
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        del a, b, c
+        return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = old
 
 
 class ClockSampler:
@@ -334,22 +379,30 @@ def _gen_uneven(args):
                             n_blobs=max(8, int(round(200 * w * h / (WIDTH * HEIGHT)))))
 
 
-def run_uneven(args, rank, world, local):
-    """Uneven batch: 1024 images with sides in 240..1280 and aspect 0.5..2
-    (blob count scaled by area), resized on the GPU to larger side 640 (S0)
-    and extracted in one call per step; device-resident inputs and outputs,
-    the call's work replayed as one CUDA graph, calls enqueued asynchronously
-    (CDVS_ASYNC).  FP32 and FP16 level storage, and the same without the
-    graph."""
+def gen_uneven(n, seed_offset=0):
     import multiprocessing as mp
 
     from paper_1705_09776_gb300 import synth
-    sizes = synth.uneven_sizes(args.images, base_seed=UNEVEN_SEED + rank)
+    sizes = synth.uneven_sizes(n, base_seed=UNEVEN_SEED + seed_offset)
     with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
         imgs = pool.map(_gen_uneven, [(i, w, h) for i, (w, h) in enumerate(sizes)], chunksize=8)
-    import torch
-    torch.cuda.set_device(local)
-    from paper_1705_09776_gb300 import cdvs
+    return imgs, sizes
+
+
+def k1_roofline(flops, launch_ms, alu_peak, what):
+    return {"kernel": what, "bound": "alu", "achieved": flops / (launch_ms * 1e-3) / 1e12, "peak": alu_peak,
+            "unit": "TFLOP/s", "frac": flops / (launch_ms * 1e-3) / 1e12 / alu_peak,
+            "algorithmic_flops_per_launch": flops, "launch_ms": launch_ms}
+
+
+def uneven_leg(ctx, cdvs, torch, imgs, sizes, args, alu_peak, steps=None):
+    """Uneven batch (config 3): images with sides in 240..1280 and aspect
+    0.5..2 (blob count scaled by area), resized on the GPU to larger side 640
+    (S0) and extracted in one call per step; device-resident inputs and
+    outputs, the call's work replayed as one CUDA graph, calls enqueued
+    asynchronously (CDVS_ASYNC).  FP32 and FP16 level storage, and FP32
+    without the graph."""
+    steps = steps or args.steps
     n = len(imgs)
     flat = np.concatenate([im.ravel() for im in imgs])
     offs = np.cumsum([0] + [im.size for im in imgs])
@@ -357,7 +410,6 @@ def run_uneven(args, rank, world, local):
     ptrs = [d_img.data_ptr() + int(o) for o in offs[:-1]]
     desc_sizes = np.array([(im.shape[1], im.shape[0], im.shape[1]) for im in imgs], cdvs.IMAGE_DESC_DTYPE)
     cap = n * 300 * 4
-    ctx = cdvs.Context(local)
     stream = torch.cuda.current_stream()
     d_kp = torch.zeros(cap * cdvs.KEYPOINT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
     d_desc = torch.zeros(cap, 128, dtype=torch.float32, device="cuda")
@@ -372,41 +424,59 @@ def run_uneven(args, rank, world, local):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             ctx.extract_raw(n, ptrs, desc_sizes, p, d_kp, d_desc, cap, d_cnt, flags | cdvs.CDVS_ASYNC, stream)
         e1.record(stream)
         ctx.wait(stream)
         torch.cuda.synchronize()
         ctx.set_graph(False)
-        return e0.elapsed_time(e1) / args.steps, int(d_cnt.sum().item())
+        return e0.elapsed_time(e1) / steps, int(d_cnt.sum().item())
 
-    sampler = ClockSampler(local)
-    sampler.start()
-    time.sleep(0.3)
     p32 = cdvs.params(max_side=640)
     p16 = cdvs.params(max_side=640, storage=cdvs.CDVS_STORAGE_FP16)
     ms32, rec32 = timed(p32, True)
     ms16, rec16 = timed(p16, True)
     ms_direct, _ = timed(p32, False)
-    clocks = sampler.stop()
-    # stage times from one profiled (direct) call
+    # stage times from profiled (direct) calls
     ctx.profile(True)
     ctx.profile_read(reset=True)
-    ctx.extract_raw(n, ptrs, desc_sizes, p32, d_kp, d_desc, cap, d_cnt, flags, stream)
+    for _ in range(3):
+        ctx.extract_raw(n, ptrs, desc_sizes, p32, d_kp, d_desc, cap, d_cnt, flags, stream)
     torch.cuda.synchronize()
-    prof = ctx.profile_read(reset=True)
+    prof = {k: v[0] / 3 for k, v in ctx.profile_read(reset=True).items()}
     ctx.profile(False)
+    flops0 = sum(detect_counts(p32, *resize_target(w, h, 640))[0][0] for w, h in sizes)
     area = float(sum(w * h for w, h in sizes))
-    out = {"metric": METRIC, "value": n / (ms32 * 1e-3), "unit": "images/s", "n_gpus": 1, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": f"{n}x uneven u8 seeded blob images (sides 240-1280, aspect 0.5-2, blobs by area), "
-                                  "S0 area resize to larger side 640, 4 octaves x 4 LoG scales, N=300",
-                      "mean_input_megapixels": area / n / 1e6, "storage": "fp32", "graph": True,
-                      "l2": "working set > L2", "records_per_step": rec32},
-           "fp16": {"value": n / (ms16 * 1e-3), "ms_per_step": ms16, "records_per_step": rec16},
-           "direct_launches": {"value": n / (ms_direct * 1e-3), "ms_per_step": ms_direct},
-           "stage_ms_per_call": {k: v[0] for k, v in prof.items()}, "clocks": clocks}
+    return {"value": n / (ms32 * 1e-3), "unit": "images/s", "ms_per_step": ms32, "steps": steps,
+            "config": {"workload": f"{n}x uneven u8 seeded blob images (sides 240-1280, aspect 0.5-2, blobs by area), "
+                                   "S0 area resize to larger side 640, 4 octaves x 4 LoG scales, N=300",
+                       "mean_input_megapixels": area / n / 1e6, "storage": "fp32", "graph": True,
+                       "records_per_step": rec32},
+            "fp16": {"value": n / (ms16 * 1e-3), "ms_per_step": ms16, "records_per_step": rec16},
+            "direct_launches": {"value": n / (ms_direct * 1e-3), "ms_per_step": ms_direct},
+            "stage_ms_per_call": prof,
+            "roofline": k1_roofline(flops0, prof["detect_octave0"], alu_peak,
+                                    "detect_kernel, octave-0 launch on the resized images")}
+
+
+def run_uneven(args, rank, world, local):
+    """--workload uneven: the config-3 leg alone, as its own JSON line."""
+    imgs, sizes = gen_uneven(args.images, rank)
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1705_09776_gb300 import cdvs
+    ctx = cdvs.Context(local)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    alu_peak, _ = alu_peak_tflops(torch, local, device_max_mhz())
+    leg = uneven_leg(ctx, cdvs, torch, imgs, sizes, args, alu_peak)
+    clocks = sampler.stop()
+    out = {"metric": METRIC, "value": leg.pop("value"), "unit": "images/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": leg.pop("ms_per_step"), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "clocks": clocks}
+    leg["config"]["l2"] = "working set > L2"
+    out.update(leg)
     print(json.dumps(out), flush=True)
     ctx.close()
 
@@ -421,23 +491,24 @@ def _gen_highres(i):
                             sigma_range=(1.5 * 3.2, 20.0 * 3.2))
 
 
-def run_highres(args, rank, world, local):
-    """High-resolution stress: 2048 x 1536 images (blob count by area, blob
-    sizes x3.2), 6 octaves, up to 2000 points each; plain FP32 against FP16
-    level storage with the learned block proposal, device-resident."""
+def gen_highres(n, offset=0):
     import multiprocessing as mp
     with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
-        imgs = np.stack(pool.map(_gen_highres, range(rank * args.images, (rank + 1) * args.images)))
-    import torch
-    torch.cuda.set_device(local)
-    from paper_1705_09776_gb300 import cdvs
+        return np.stack(pool.map(_gen_highres, range(offset, offset + n)))
+
+
+def highres_leg(ctx, cdvs, torch, imgs, args, alu_peak, steps=None):
+    """High-resolution stress (config 5): 2048 x 1536 images (blob count by
+    area, blob sizes x3.2), 6 octaves, up to 2000 points each; plain FP32
+    against FP16 level storage, and FP16 with the learned block proposal;
+    device-resident."""
+    steps = steps or args.steps
     n, H, W = imgs.shape
     d_img = torch.from_numpy(imgs).cuda()
     ptrs = [d_img.data_ptr() + i * H * W for i in range(n)]
     sizes = np.array([(W, H, W)] * n, cdvs.IMAGE_DESC_DTYPE)
     N = 2000
     cap = n * N * 4
-    ctx = cdvs.Context(local)
     stream = torch.cuda.current_stream()
     d_kp = torch.zeros(cap * cdvs.KEYPOINT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
     d_desc = torch.zeros(cap, 128, dtype=torch.float32, device="cuda")
@@ -455,7 +526,7 @@ def run_highres(args, rank, world, local):
         ctx.profile_read(reset=True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             call(p)
         e1.record(stream)
         torch.cuda.synchronize()
@@ -463,11 +534,8 @@ def run_highres(args, rank, world, local):
         ctx.profile(False)
         tot = int(d_cnt.sum().item())
         kp = d_kp[:tot * cdvs.KEYPOINT_DTYPE.itemsize].cpu().numpy().view(cdvs.KEYPOINT_DTYPE).copy()
-        return e0.elapsed_time(e1) / args.steps, kp, {k: v[0] / args.steps for k, v in prof.items()}
+        return e0.elapsed_time(e1) / steps, kp, {k: v[0] / steps for k, v in prof.items()}
 
-    sampler = ClockSampler(local)
-    sampler.start()
-    time.sleep(0.3)
     p32 = cdvs.params(num_octaves=6, max_keypoints=N)
     ms32, kp32, st32 = timed(p32)
     p16 = cdvs.params(num_octaves=6, max_keypoints=N, storage=cdvs.CDVS_STORAGE_FP16)
@@ -482,23 +550,51 @@ def run_highres(args, rank, world, local):
         base = record_keys(kp16)
         learned = {"value": n / (msl * 1e-3), "ms_per_step": msl, "threshold": thr,
                    "recall_vs_fp16_plain": len(base & record_keys(kpl)) / max(len(base), 1),
-                   "stage_ms_per_step": stl,
-                   "note": "network trained on 640x480 images only"}
-    clocks = sampler.stop()
+                   "stage_ms_per_step": stl}
     flops_o, bytes_o = detect_counts(p32, W, H)
-    out = {"metric": METRIC, "value": n / (ms32 * 1e-3), "unit": "images/s", "n_gpus": 1, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": f"{n}x {W}x{H} u8 seeded blob images (blobs x3.2, count by area), 6 octaves x 4 "
-                                  "LoG scales, N=2000, 128-D float descriptors", "storage": "fp32",
-                      "l2": "working set > L2", "records_per_step": int(len(kp32))},
-           "stage_ms_per_step": st32,
-           "octave0_tflops": flops_o[0] * n / (st32["detect_octave0"] * 1e-3) / 1e12,
-           "fp16": {"value": n / (ms16 * 1e-3), "ms_per_step": ms16, "records_per_step": int(len(kp16)),
-                    "stage_ms_per_step": st16},
-           "fp16_learned": learned, "clocks": clocks}
+    return {"value": n / (ms32 * 1e-3), "unit": "images/s", "ms_per_step": ms32, "steps": steps,
+            "config": {"workload": f"{n}x {W}x{H} u8 seeded blob images (blobs x3.2, count by area), 6 octaves x 4 "
+                                   "LoG scales, N=2000, 128-D float descriptors", "storage": "fp32",
+                       "records_per_step": int(len(kp32))},
+            "stage_ms_per_step": st32,
+            "roofline": k1_roofline(flops_o[0] * n, st32["detect_octave0"], alu_peak,
+                                    "detect_kernel, octave-0 launch (2048x1536)"),
+            "fp16": {"value": n / (ms16 * 1e-3), "ms_per_step": ms16, "records_per_step": int(len(kp16)),
+                     "stage_ms_per_step": st16},
+            "fp16_learned": learned}
+
+
+def run_highres(args, rank, world, local):
+    """--workload highres: the config-5 leg alone, as its own JSON line."""
+    imgs = gen_highres(args.images, rank * args.images)
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1705_09776_gb300 import cdvs
+    ctx = cdvs.Context(local)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    alu_peak, _ = alu_peak_tflops(torch, local, device_max_mhz())
+    leg = highres_leg(ctx, cdvs, torch, imgs, args, alu_peak)
+    clocks = sampler.stop()
+    out = {"metric": METRIC, "value": leg.pop("value"), "unit": "images/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": leg.pop("ms_per_step"), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "clocks": clocks}
+    leg["config"]["l2"] = "working set > L2"
+    out.update(leg)
     print(json.dumps(out), flush=True)
     ctx.close()
+
+
+def device_max_mhz():
+    """The maximum SM clock of GPU 0 as nvidia-smi reports it (the measured
+    peaks file's figure when nvidia-smi is not there)."""
+    try:
+        r = subprocess.run(["nvidia-smi", "-i", os.environ.get("LOCAL_RANK", "0"), "--query-gpu=clocks.max.sm",
+                            "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=20)
+        return float(r.stdout.strip().splitlines()[0])
+    except Exception:
+        return float(load_peaks().get("sm_max_mhz", 2070.0))
 
 
 def run_scfv(ctx, cdvs, torch, d_desc, counts, args):
@@ -545,6 +641,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--images", type=int, default=N_IMAGES, help="images per rank (profiling runs)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal leg")
+    ap.add_argument("--no-legs", action="store_true", help="skip the uneven (config 3) and high-resolution "
+                                                            "(config 5) legs of the default line")
+    ap.add_argument("--uneven-images", type=int, default=1024, help="images of the uneven leg")
+    ap.add_argument("--highres-images", type=int, default=64, help="images of the high-resolution leg")
     ap.add_argument("--workload", default="batch", choices=["batch", "uneven", "highres"],
                     help="batch: 256 x 640x480 (default); uneven: 1024 uneven images resized to 640; "
                          "highres: 512 x 2048x1536, 6 octaves, N=2000")
@@ -565,6 +665,9 @@ def main():
         return run_highres(args, rank, world, local)
 
     imgs = make_batch(args.images, offset=rank * args.images)  # before any CUDA call
+    legs = None
+    if not args.no_legs:
+        legs = (gen_uneven(args.uneven_images, rank), gen_highres(args.highres_images, rank * args.highres_images))
     import torch
     torch.cuda.set_device(local)
     dist = None
@@ -654,13 +757,21 @@ def main():
     flops_o, bytes_o = detect_counts(p)
     o0_ms = prof["detect_octave0"][0] / args.steps
     tflops = flops_o[0] * n / (o0_ms * 1e-3) / 1e12
-    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    sm_max = clocks.get("sm_max_mhz") or device_max_mhz()
+    alu_peak, sms = alu_peak_tflops(torch, local, sm_max)
+    try:
+        sgemm = measure_sgemm_tflops(torch)
+    except Exception:
+        sgemm = None
     gbs = bytes_o[0] * n / (o0_ms * 1e-3) / 1e9
     traffic = load_traffic()
     det_ms = prof["detect"][0] / args.steps
     roofline = {"kernel": "detect_kernel, octave-0 launch (K1: 4 Gaussian levels + LoG + ALP + extremum + refine)",
                 "bound": "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s", "frac": tflops / alu_peak,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived from unit counts and clock)",
+                "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_max:.0f} MHz "
+                               "(SM count and maximum clock queried from the device)",
+                "measured_fp32": {"sgemm_tflops": sgemm, "frac": (tflops / sgemm) if sgemm else None,
+                                  "source": "cuBLAS SGEMM 8192^3 with TF32 off, best of 5 (of measured)"},
                 "traffic": (traffic["dram_bytes_per_image_octave0"] * n if traffic else None),
                 "algorithmic_flops_per_launch": flops_o[0] * n, "algorithmic_bytes_per_launch": bytes_o[0] * n,
                 "launch_ms": o0_ms,
@@ -685,6 +796,16 @@ def main():
                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
            "gpu_launches": launches, "roofline": roofline, "clocks": clocks}
     out["one_image_per_call"] = per_image
+    if legs is not None:
+        (u_imgs, u_sizes), h_imgs = legs
+        try:
+            out["uneven"] = uneven_leg(ctx, cdvs, torch, u_imgs, u_sizes, args, alu_peak)
+        except Exception as ex:  # reported, never fatal to the main line
+            out["uneven"] = {"error": str(ex)}
+        try:
+            out["highres"] = highres_leg(ctx, cdvs, torch, h_imgs, args, alu_peak)
+        except Exception as ex:
+            out["highres"] = {"error": str(ex)}
     if learned is not None:
         out["learned"] = learned
     if scfv is not None:

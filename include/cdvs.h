@@ -191,8 +191,11 @@ cdvs_status cdvs_candidates(cdvs_ctx *ctx, int32_t n_images, const uint8_t *cons
  * cdvs_dedupe_select -- Alg. 1 stage C and the selection of Eq. 5 on given
  * candidates: cand[i * cand_stride + j], j < cand_count[i], are image i's
  * candidates (fields x, y, sigma, response, octave used; octave px positions
- * are x / 2^octave).  Writes the selected points in rank order, packed over
- * the batch, with parent_id = rank.  Host buffers unless the flags say device.
+ * are x / 2^octave; an octave the image does not have is INVALID_ARGUMENT).
+ * Writes the selected points in rank order, packed over the batch, with
+ * parent_id = the candidate's index j.  Any number of candidates tying at the
+ * N-th response is resolved by the total order (|response| desc, y, x,
+ * sigma, octave asc), whatever their order in cand.  Host buffers only.
  */
 cdvs_status cdvs_dedupe_select(cdvs_ctx *ctx, int32_t n_images, const cdvs_image_desc *sizes,
                                const cdvs_keypoint *cand, const int32_t *cand_count,
@@ -277,28 +280,37 @@ cdvs_status cdvs_transform_ternary(const float *desc, int32_t n, const double *t
  * points; about 660 KB) is a fixed array inside the library, so every GPU
  * that loads the library keeps that much device memory until the process
  * exits.  The first call on a device looks the array's device address up
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress); make that first call before any stream capture (a
+ * lookup that fails is not remembered: the next call tries again).
  * All calls share the one array and it keeps the last call's contents: calls
  * whose GPU work overlaps (other streams, other host threads) race and give
  * wrong results -- serialise them.
  *
  *   cand       n_cand candidate records in DEVICE memory (fields x, y, sigma,
- *              response, p_ss, ratio, octave, type used), octave in 0..11
+ *              response, p_ss, ratio, octave, type used); octave is one of
+ *              the image's octaves (0 .. octaves of width x height - 1)
  *   n_cand     0 .. CDVS_NOALLOC_MAX_CANDIDATES; more -> CDVS_UNSUPPORTED_SIZE
  *              (nothing is launched)
  *   width, height  image size (16..32768) the candidates come from
  *   sel_out    DEVICE memory for params->max_keypoints records, written in
  *              rank order with image = 0 and parent_id = index in cand
  *   sel_count  DEVICE int, receives the number of selected points
- * Runs asynchronously on cuda_stream on the current device.  No status word
- * is read back (that would need a synchronisation): the call returns
- * CDVS_OK once the work is queued, or an argument / launch error.
+ *   dev_status DEVICE int or NULL; receives, when the work has run, CDVS_OK,
+ *              CDVS_INVALID_ARGUMENT (a record's octave was not one of the
+ *              image's octaves: that record was left out, the others
+ *              selected), or CDVS_CAPACITY_TRUNCATED (more than 4096
+ *              records identical in response, position, scale and octave
+ *              tie at the N-th rank; not met with real candidates)
+ * Runs asynchronously on cuda_stream on the current device.  The return
+ * value covers the arguments and the launches only (CDVS_OK once the work is
+ * queued); what the GPU finds goes to dev_status, so reading it needs no
+ * synchronisation inside this call.
  */
 #define CDVS_NOALLOC_MAX_CANDIDATES 16384
 cdvs_status cdvs_dedupe_select_noalloc(const cdvs_keypoint *cand, int32_t n_cand, int32_t width,
                                        int32_t height, const cdvs_params *params,
                                        cdvs_keypoint *sel_out, int32_t *sel_count,
-                                       void *cuda_stream);
+                                       int32_t *dev_status, void *cuda_stream);
 
 /* enable = 1: calls of cdvs_extract with both CDVS_INPUT_DEVICE and
  * CDVS_OUTPUT_DEVICE (and profiling off) capture their device work -- input
@@ -410,6 +422,26 @@ cdvs_status cdvs_set_scfv_model(cdvs_ctx *ctx, const cdvs_scfv_model *model);
 cdvs_status cdvs_scfv(cdvs_ctx *ctx, int32_t n_images, const float *desc, const int32_t *counts,
                       int32_t n_select, float *g_mu, float *g_sigma, float *delta, int32_t *order,
                       uint32_t *bits, uint32_t flags, void *cuda_stream);
+
+/* Candidate queue capacity per image (candidates of all octaves before the
+ * cross-octave check).  0 (the default) sizes it from the image: max(4096,
+ * pixels / 16), more than the method finds on any natural image.  When a
+ * synchronous call finds more candidates than its queue holds, it runs again
+ * with room for every one, so results never depend on which candidates
+ * reached the queue first; the context keeps that room for later calls.  An
+ * asynchronous call cannot run again: cdvs_wait reports
+ * CDVS_CAPACITY_TRUNCATED and later calls get twice the room.  Setting the
+ * capacity forgets the room gained so far. */
+cdvs_status cdvs_set_candidate_capacity(cdvs_ctx *ctx, int32_t per_image);
+
+/* ---------------------------------------------------------------------------
+ * Testing hook (not part of the method).  The next `count` device workspace
+ * allocations of any context in the process fail as cudaMalloc does when the
+ * device memory is exhausted: the call that needed them returns
+ * CDVS_OUT_OF_MEMORY and leaves its context usable (the workspace is grown
+ * again by the next call).  count <= 0 turns the injection off.
+ */
+void cdvs_inject_alloc_failures(int32_t count);
 
 #ifdef __cplusplus
 }

@@ -59,7 +59,8 @@ EXPORTED = ["cdvs_params_default", "cdvs_create", "cdvs_destroy", "cdvs_last_err
             "cdvs_candidates", "cdvs_dedupe_select", "cdvs_describe", "cdvs_scale_space",
             "cdvs_rank_host", "cdvs_transform_ternary", "cdvs_profile", "cdvs_profile_read", "cdvs_wait",
             "cdvs_dedupe_select_noalloc", "cdvs_set_proposal", "cdvs_proposal_logits",
-            "cdvs_proposal_train_step", "cdvs_resize", "cdvs_set_graph", "cdvs_set_scfv_model", "cdvs_scfv"]
+            "cdvs_proposal_train_step", "cdvs_resize", "cdvs_set_graph", "cdvs_set_scfv_model", "cdvs_scfv",
+            "cdvs_inject_alloc_failures", "cdvs_set_candidate_capacity"]
 STAGES = ["detect", "select", "describe", "offsets", "pack", "detect_octave0", "proposal"]
 
 
@@ -98,7 +99,7 @@ def load(build_if_missing: bool = True):
         "cdvs_profile": (i32, [P, i32]),
         "cdvs_wait": (i32, [P, P]),
         "cdvs_profile_read": (i32, [P, P, P, i32, i32]),
-        "cdvs_dedupe_select_noalloc": (i32, [P, i32, i32, i32, P, P, P, P]),
+        "cdvs_dedupe_select_noalloc": (i32, [P, i32, i32, i32, P, P, P, P, P]),
         "cdvs_set_proposal": (i32, [P, P, i32]),
         "cdvs_resize": (i32, [P, i32, P, P, i32, P, sz, P, u32, P]),
         "cdvs_set_graph": (i32, [P, i32]),
@@ -106,6 +107,8 @@ def load(build_if_missing: bool = True):
         "cdvs_scfv": (i32, [P, i32, P, P, i32, P, P, P, P, P, u32, P]),
         "cdvs_proposal_logits": (i32, [P, i32, P, P, P, i32, u32, P]),
         "cdvs_proposal_train_step": (i32, [P, P, i32, i32, i32, i32, P, P, P, P, P, P, P, i32, C.c_float, i32, P]),
+        "cdvs_inject_alloc_failures": (None, [i32]),
+        "cdvs_set_candidate_capacity": (i32, [P, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -175,6 +178,10 @@ class Context:
         """cdvs_wait: synchronises the stream of CDVS_ASYNC extractions and
         returns their combined status (raises on errors other than truncation)."""
         return self._check(self._L.cdvs_wait(self.handle, _stream_handle(stream)))
+
+    def set_candidate_capacity(self, per_image: int):
+        """cdvs_set_candidate_capacity: 0 = from the image size."""
+        self._check(self._L.cdvs_set_candidate_capacity(self.handle, int(per_image)))
 
     def set_graph(self, enable: bool):
         """Device-resident extractions through one CUDA graph (cdvs_set_graph)."""
@@ -384,14 +391,23 @@ class Context:
 NOALLOC_MAX_CANDIDATES = 16384
 
 
-def dedupe_select_noalloc(cand_dev, n_cand, width, height, p, sel_out_dev, sel_count_dev, stream=None) -> int:
+def dedupe_select_noalloc(cand_dev, n_cand, width, height, p, sel_out_dev, sel_count_dev, stream=None,
+                          status_dev=None) -> int:
     """cdvs_dedupe_select_noalloc on device buffers (torch tensors or device
     addresses as ints): no memory is allocated by the library.  Returns the
-    status code (asynchronous: outputs are ready once `stream` is)."""
+    call's status code (asynchronous: outputs, and the device status word
+    when given, are ready once `stream` is)."""
     def addr(x):
         return x if isinstance(x, int) or x is None else x.data_ptr()
     return load().cdvs_dedupe_select_noalloc(addr(cand_dev), n_cand, width, height, p.ctypes.data,
-                                             addr(sel_out_dev), addr(sel_count_dev), _stream_handle(stream))
+                                             addr(sel_out_dev), addr(sel_count_dev), addr(status_dev),
+                                             _stream_handle(stream))
+
+
+def inject_alloc_failures(count: int) -> None:
+    """Testing hook: the next `count` workspace allocations fail as if the
+    device were out of memory."""
+    load().cdvs_inject_alloc_failures(int(count))
 
 
 def rank_host(pts: np.ndarray, max_keypoints: int) -> np.ndarray:

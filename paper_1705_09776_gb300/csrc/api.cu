@@ -5,6 +5,7 @@
 //   K3+K10 cross-octave check + selection (one CTA per image)
 //   K5 orientation, packing scan, K6 descriptors
 // Every step of the method runs in the kernels; this file only moves bytes.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -105,6 +106,12 @@ struct cdvs_ctx {
   int n_chunks = 1;                        // of the current call
   int chunk_begin[kMaxInputChunks + 1] = {};
   std::vector<Upload> uploads[kMaxInputChunks];  // empty: inputs already on the device
+  // candidate queue capacity per image: at least this many (grown after a
+  // call whose queue overflowed), and the capacity of the last call
+  int cap_floor = 0;
+  int cap_fixed = 0;  // cdvs_set_candidate_capacity; 0: from the image size
+  int last_cap = 0;
+  bool overflow_rerun = false;  // inside the re-run of an overflowed call
 };
 
 namespace {
@@ -149,6 +156,11 @@ void prof_end(cdvs_ctx* c, int stage, int launches, cudaEvent_t a, cudaStream_t 
   c->recs.push_back(ProfRec{stage, launches, a, b});
 }
 
+// Fault injection for tests of the error paths (cdvs_inject_alloc_failures):
+// the next g_fail_allocs workspace allocations fail as cudaMalloc would when
+// the device is out of memory.
+std::atomic<int> g_fail_allocs{0};
+
 cudaError_t ensure(DevBuf& b, size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (bytes <= b.bytes) return cudaSuccess;
@@ -156,6 +168,8 @@ cudaError_t ensure(DevBuf& b, size_t bytes) {
   b.p = nullptr;
   b.bytes = 0;
   const size_t nb = bytes + bytes / 4;
+  for (int f = g_fail_allocs.load(); f > 0;)
+    if (g_fail_allocs.compare_exchange_weak(f, f - 1)) return cudaErrorMemoryAllocation;
   cudaError_t e = cudaMalloc(&b.p, nb);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -346,9 +360,19 @@ cdvs_status plan_batch(cdvs_ctx* c, int n, const cdvs_image_desc* sizes, const c
   return CDVS_OK;
 }
 
-int cand_capacity(long long max_pixels) {
-  long long cap = std::max(4096LL, (max_pixels / 16 + 1023) & ~1023LL);
+int cand_capacity(long long max_pixels, int fixed, int floor) {
+  long long cap = fixed > 0 ? fixed : std::max(4096LL, (max_pixels / 16 + 1023) & ~1023LL);
+  if (floor > cap) cap = ((long long)floor + 1023) & ~1023LL;
   return (int)std::min(cap, 1LL << 22);
+}
+
+// After a call whose candidate queue overflowed: the queue counters kept
+// counting past the capacity, so the largest count is the capacity that
+// holds every candidate.
+void grow_cap_floor(cdvs_ctx* c, const int* counts, int n) {
+  int mx = 0;
+  for (int i = 0; i < n; ++i) mx = std::max(mx, counts[i]);
+  c->cap_floor = std::max(c->cap_floor, mx);
 }
 
 // Uploads images (if on the host) and the plans; returns the plan of image i
@@ -762,7 +786,8 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
   long long level_elems, max_pixels;
   int max_oct;
   if ((st = plan_batch(c, n, eff.data(), p, level_elems, max_oct, max_pixels)) != CDVS_OK) return st;
-  const int cap = cand_capacity(max_pixels);
+  const int cap = cand_capacity(max_pixels, c->cap_fixed, c->cap_floor);
+  c->last_cap = cap;
   const int N = p.max_keypoints;
   const size_t slots = (size_t)n * N;
   if ((e = ensure(c->levels, (size_t)level_elems * elem_size(p.storage))) != cudaSuccess ||
@@ -858,6 +883,15 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
       return cuda_fail(c, e, "candidate readback");
     int status_bits = h_small[0];
+    if ((status_bits & kStatusCandOverflow) && !c->overflow_rerun) {
+      // a queue overflowed: the call runs again with room for every
+      // candidate, so no candidate is dropped in whatever order they came
+      grow_cap_floor(c, counts.data(), n);
+      c->overflow_rerun = true;
+      st = run(c, mode, n, images, sizes, params, pin, kp_out, desc_out, capacity, kp_count, flags, caller_s);
+      c->overflow_rerun = false;
+      return st;
+    }
     int written = 0;
     std::vector<Cand> tmp;
     for (int i = 0; i < n; ++i) {
@@ -1033,6 +1067,18 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(c, e, "status readback");
   const int status_bits = h_small[0];
   const int total = h_small[1];
+  if ((status_bits & kStatusCandOverflow) && !c->overflow_rerun && mode == kExtract) {
+    // a queue overflowed: the call runs again with room for every candidate,
+    // so the result never depends on which candidates came first
+    std::vector<int> counts(n);
+    if ((e = cudaMemcpy(counts.data(), c->cand_count.p, sizeof(int) * n, cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_fail(c, e, "candidate counts");
+    grow_cap_floor(c, counts.data(), n);
+    c->overflow_rerun = true;
+    st = run(c, mode, n, images, sizes, params, pin, kp_out, desc_out, capacity, kp_count, flags, caller_s);
+    c->overflow_rerun = false;
+    return st;
+  }
   if (!dev_out) {
     if ((e = cudaMemcpyAsync(kp_count, hset.out_count.p, sizeof(int) * n, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (total > 0 && (e = cudaMemcpyAsync(kp_out, hset.out_kp.p, sizeof(cdvs_keypoint) * (size_t)total,
@@ -1193,7 +1239,8 @@ cdvs_status cdvs_dedupe_select(cdvs_ctx* c, int32_t n, const cdvs_image_desc* si
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < cand_count[i]; ++j) {
       const cdvs_keypoint& k = cand[(size_t)i * cand_stride + j];
-      if (k.octave < 0 || k.octave >= kMaxOctaves) return fail(c, CDVS_INVALID_ARGUMENT, "octave out of range");
+      if (k.octave < 0 || k.octave >= c->h_plans[i].n_oct)
+        return fail(c, CDVS_INVALID_ARGUMENT, "candidate octave is not one of the image's octaves");
       const float inv = 1.0f / (float)(1 << k.octave);
       Cand& q = h[(size_t)i * cap + j];
       q.xo = k.x * inv;
@@ -1333,8 +1380,22 @@ cdvs_status cdvs_wait(cdvs_ctx* c, void* cuda_stream) {
       (e = cudaStreamSynchronize(s)) != cudaSuccess)
     return cuda_fail(c, e, "status readback");
   c->async_open = false;
-  return map_status(c, static_cast<int*>(h.p)[0]);
+  const int bits = static_cast<int*>(h.p)[0];
+  // an asynchronous call cannot be run again: its truncation is reported,
+  // and later calls get twice the capacity
+  if (bits & kStatusCandOverflow) c->cap_floor = std::max(c->cap_floor, 2 * c->last_cap);
+  return map_status(c, bits);
 }
+
+cdvs_status cdvs_set_candidate_capacity(cdvs_ctx* c, int32_t per_image) {
+  if (!c) return CDVS_INVALID_ARGUMENT;
+  if (per_image < 0 || per_image > (1 << 22)) return fail(c, CDVS_INVALID_ARGUMENT, "per_image must be in 0..2^22");
+  c->cap_fixed = per_image;
+  c->cap_floor = 0;
+  return CDVS_OK;
+}
+
+void cdvs_inject_alloc_failures(int32_t count) { g_fail_allocs.store(count > 0 ? count : 0); }
 
 cdvs_status cdvs_profile(cdvs_ctx* c, int32_t enable) {
   if (!c) return CDVS_INVALID_ARGUMENT;

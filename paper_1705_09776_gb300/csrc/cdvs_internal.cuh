@@ -31,6 +31,7 @@ constexpr int kStatusCandOverflow = 1;
 constexpr int kStatusSelectOverflow = 2;
 constexpr int kStatusOutTruncated = 4;
 constexpr int kStatusTimeout = 8;        // a bounded device-side wait gave up
+constexpr int kStatusBadInput = 16;      // a caller record was out of range and was left out
 
 // ---------------------------------------------------------------- plans
 // Level (o, k) of an image is stored at level_base + oct[o].level_off +

@@ -13,7 +13,11 @@
 //   3. The N-th largest |response| among the kept candidates is found by a
 //      4-pass radix select on the IEEE bits; the candidates at or above it are
 //      gathered and bitonic-sorted by (|response| desc, y, x, sigma, octave),
-//      a total order, and the first N are written in rank order.
+//      a total order, and the first N are written in rank order.  When more
+//      candidates tie at the N-th |response| than the sort list holds, the
+//      radix select continues over y, x, sigma and octave to find the N-th
+//      entry of the total order itself, and only the entries up to it are
+//      gathered: the result never depends on the queue order.
 #include "cdvs_internal.cuh"
 
 namespace cdvs {
@@ -67,6 +71,74 @@ __device__ int block_exclusive_scan(int* cnt, int n, int* warp_sums) {
   return total;
 }
 
+// Order-preserving 32-bit key of a float (ascending), -0 taken as +0.
+__device__ __forceinline__ unsigned float_key(float f) {
+  const unsigned b = __float_as_uint(f + 0.0f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+// The `remaining`-th largest 32-bit key among the members (member(i, key)
+// returns whether candidate i takes part and sets its key): four passes of 8
+// bits over a shared 256-bucket histogram.  On return `remaining` is how many
+// members with exactly the returned key are still needed (block-uniform).
+template <typename Member>
+__device__ unsigned radix_select_desc(int n, int& remaining, int* s_hist, int* s_misc, Member member) {
+  const int tid = threadIdx.x;
+  unsigned prefix = 0u, mask = 0u;
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    for (int i = tid; i < 256; i += kSelThreads) s_hist[i] = 0;
+    __syncthreads();
+    for (int i = tid; i < n; i += kSelThreads) {
+      unsigned key;
+      if (!member(i, key)) continue;
+      if ((key & mask) == prefix) atomicAdd(s_hist + ((key >> shift) & 255u), 1);
+    }
+    __syncthreads();
+    // the digit d where the count of keys with digits d and above first
+    // reaches `remaining`, scanning down from 255: lane l of warp 0 sums
+    // digits 255 - 8l .. 248 - 8l, a warp scan gives the counts above each
+    // lane's group, and the lane whose group crosses walks its 8 digits
+    if (tid < 32) {
+      const int lane = tid;
+      int c[8], sum = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        c[q] = s_hist[255 - 8 * lane - q];
+        sum += c[q];
+      }
+      int incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      const int excl = incl - sum;
+      if (lane == 31 && incl < remaining) {  // fewer keys than remaining: as a full scan would end
+        s_misc[1] = 0;
+        s_misc[2] = remaining - incl;
+      }
+      if (excl < remaining && remaining <= incl) {
+        int cum = excl;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (cum + c[q] >= remaining) {
+            s_misc[1] = 255 - 8 * lane - q;
+            s_misc[2] = remaining - cum;
+            break;
+          }
+          cum += c[q];
+        }
+      }
+    }
+    __syncthreads();
+    prefix |= (unsigned)s_misc[1] << shift;
+    mask |= 255u << shift;
+    remaining = s_misc[2];
+    __syncthreads();
+  }
+  return prefix;
+}
+
 __global__ void __launch_bounds__(kSelThreads) select_kernel(const __grid_constant__ SelectArgs a) {
   extern __shared__ float4 smem4[];
   __shared__ int warp_sums[33];
@@ -89,15 +161,25 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(const __grid_consta
   int* cell = reinterpret_cast<int*>(smem4);  // ncell + 1 counters -> ends
   for (int i = tid; i <= ncell; i += kSelThreads) cell[i] = 0;
   __syncthreads();
+  // a candidate of an octave the image does not have takes no part (the
+  // callers' records are checked here, not trusted)
+  auto valid = [&](int i) { return C[i].octave >= 0 && C[i].octave < n_oct; };
+  bool bad_input = false;
   for (int i = tid; i < n; i += kSelThreads) {
+    if (!valid(i)) {
+      bad_input = true;
+      continue;
+    }
     const float s = (float)(1 << C[i].octave);
     const int cx = min(max((int)floorf(C[i].xo * s * inv_cs), 0), gx - 1);
     const int cy = min(max((int)floorf(C[i].yo * s * inv_cs), 0), gy - 1);
     atomicAdd(cell + cy * gx + cx, 1);
   }
+  if (bad_input) atomicOr(a.status, kStatusBadInput);
   __syncthreads();
   block_exclusive_scan(cell, ncell, warp_sums);
   for (int i = tid; i < n; i += kSelThreads) {
+    if (!valid(i)) continue;
     const float s = (float)(1 << C[i].octave);
     const int cx = min(max((int)floorf(C[i].xo * s * inv_cs), 0), gx - 1);
     const int cy = min(max((int)floorf(C[i].yo * s * inv_cs), 0), gy - 1);
@@ -109,6 +191,10 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(const __grid_consta
   // ---- 2. cross-octave duplicates
   int kept_local = 0;
   for (int i = tid; i < n; i += kSelThreads) {
+    if (!valid(i)) {
+      keep[i] = 0;
+      continue;
+    }
     const Cand ca = C[i];
     const float sa = (float)(1 << ca.octave);
     const float xa = ca.xo * sa, ya = ca.yo * sa, siga = ca.so * sa;
@@ -149,80 +235,88 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(const __grid_consta
   // non-negative float order like the floats themselves)
   unsigned thr = 0u;
   if (M > N) {
-    unsigned prefix = 0u, mask = 0u;
     int remaining = N;
-    for (int shift = 24; shift >= 0; shift -= 8) {
-      for (int i = tid; i < 256; i += kSelThreads) s_hist[i] = 0;
-      __syncthreads();
-      for (int i = tid; i < n; i += kSelThreads) {
-        if (!keep[i]) continue;
-        const unsigned key = __float_as_uint(fabsf(C[i].resp));
-        if ((key & mask) == prefix) atomicAdd(s_hist + ((key >> shift) & 255u), 1);
-      }
-      __syncthreads();
-      // the digit d where the count of keys with digits d and above first
-      // reaches `remaining`, scanning down from 255: lane l of warp 0 sums
-      // digits 255 - 8l .. 248 - 8l, a warp scan gives the counts above each
-      // lane's group, and the lane whose group crosses walks its 8 digits
-      if (tid < 32) {
-        const int lane = tid;
-        int c[8], sum = 0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          c[q] = s_hist[255 - 8 * lane - q];
-          sum += c[q];
-        }
-        int incl = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int t = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += t;
-        }
-        const int excl = incl - sum;
-        if (lane == 31 && incl < remaining) {  // fewer keys than remaining: as a full scan would end
-          s_misc[1] = 0;
-          s_misc[2] = remaining - incl;
-        }
-        if (excl < remaining && remaining <= incl) {
-          int cum = excl;
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            if (cum + c[q] >= remaining) {
-              s_misc[1] = 255 - 8 * lane - q;
-              s_misc[2] = remaining - cum;
-              break;
-            }
-            cum += c[q];
-          }
-        }
-      }
-      __syncthreads();
-      prefix |= (unsigned)s_misc[1] << shift;
-      mask |= 255u << shift;
-      remaining = s_misc[2];
-      __syncthreads();
-    }
-    thr = prefix;
+    thr = radix_select_desc(n, remaining, s_hist, s_misc, [&](int i, unsigned& key) {
+      key = __float_as_uint(fabsf(C[i].resp));
+      return keep[i] != 0;
+    });
   }
 
   // ---- gather candidates at or above the threshold and sort them
   float4* key = smem4;  // reuses the cell counters
   int2* aux = reinterpret_cast<int2*>(key + a.list_cap);
-  if (tid == 0) s_misc[3] = 0;
-  __syncthreads();
-  for (int i = tid; i < n; i += kSelThreads) {
-    if (!keep[i]) continue;
-    const float ar = fabsf(C[i].resp);
-    if (__float_as_uint(ar) < thr) continue;
-    const int pos = atomicAdd(s_misc + 3, 1);
-    if (pos >= a.list_cap) continue;
+  // tie keys (y, x, sigma, octave) of a candidate, image px; the total order
+  // takes them ascending, so they are selected complemented (largest first)
+  auto tie_key = [&](int i, int k) -> unsigned {
     const float s = (float)(1 << C[i].octave);
-    key[pos] = make_float4(ar, C[i].yo * s, C[i].xo * s, C[i].so * s);
-    aux[pos] = make_int2(C[i].octave, i);
+    if (k == 0) return ~float_key(C[i].yo * s);
+    if (k == 1) return ~float_key(C[i].xo * s);
+    if (k == 2) return ~float_key(C[i].so * s);
+    return ~(unsigned)(C[i].octave + 0x8000);
+  };
+  unsigned tkey[4] = {0u, 0u, 0u, 0u};
+  int n_tie_keys = 0;  // 0: every candidate at thr is gathered
+  int L = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    if (tid == 0) s_misc[3] = 0;
+    __syncthreads();
+    for (int i = tid; i < n; i += kSelThreads) {
+      if (!keep[i]) continue;
+      const float ar = fabsf(C[i].resp);
+      const unsigned ab = __float_as_uint(ar);
+      if (ab < thr) continue;
+      if (ab == thr && n_tie_keys > 0) {
+        // at the threshold: only the ties up to the N-th entry of the total order
+        bool in = true;
+        for (int k = 0; k < 4; ++k) {
+          const unsigned t = tie_key(i, k);
+          if (t != tkey[k]) {
+            in = t > tkey[k];
+            break;
+          }
+        }
+        if (!in) continue;
+      }
+      const int pos = atomicAdd(s_misc + 3, 1);
+      if (pos >= a.list_cap) continue;
+      const float s = (float)(1 << C[i].octave);
+      key[pos] = make_float4(ar, C[i].yo * s, C[i].xo * s, C[i].so * s);
+      aux[pos] = make_int2(C[i].octave, i);
+    }
+    __syncthreads();
+    const int gathered = s_misc[3];
+    __syncthreads();
+    if (gathered <= a.list_cap || pass == 1) {
+      if (tid == 0 && gathered > a.list_cap) atomicOr(a.status, kStatusSelectOverflow);
+      L = min(gathered, a.list_cap);
+      break;
+    }
+    // More candidates tie at the N-th |response| than the list holds: find
+    // the N-th entry of the total order among the ties (radix select on y,
+    // x, sigma, octave in turn), so the list gets exactly the N first ones
+    // whatever the order the candidates were queued in.
+    int above = 0;
+    for (int i = tid; i < n; i += kSelThreads)
+      above += keep[i] && __float_as_uint(fabsf(C[i].resp)) > thr;
+    __syncthreads();
+    if (tid == 0) s_misc[0] = 0;
+    __syncthreads();
+    atomicAdd(s_misc, above);
+    __syncthreads();
+    int remaining = N - s_misc[0];
+    __syncthreads();
+    for (int k = 0; k < 4; ++k) {
+      const int kk = k;
+      tkey[k] = radix_select_desc(n, remaining, s_hist, s_misc, [&](int i, unsigned& t) {
+        if (!keep[i] || __float_as_uint(fabsf(C[i].resp)) != thr) return false;
+        for (int j = 0; j < kk; ++j)
+          if (tie_key(i, j) != tkey[j]) return false;
+        t = tie_key(i, kk);
+        return true;
+      });
+    }
+    n_tie_keys = 4;
   }
-  __syncthreads();
-  const int L = min(s_misc[3], a.list_cap);
-  if (tid == 0 && s_misc[3] > a.list_cap) atomicOr(a.status, kStatusSelectOverflow);
   int Pn = 1;
   while (Pn < L) Pn <<= 1;
   for (int i = L + tid; i < Pn; i += kSelThreads) {  // padding that ranks last

@@ -8,6 +8,11 @@
 // device (cudaGetSymbolAddress, with that device current) and handed to the
 // kernels.  All calls share the array: calls whose work overlaps on the GPU
 // (different streams, or different host threads) race on it.
+//
+// The selection kernel checks the caller's records itself (an octave the
+// image does not have leaves the record out) and resolves any number of ties
+// at the N-th response exactly; what it reports goes to the caller's optional
+// device status word, so no synchronisation is needed to learn it.
 #include <mutex>
 
 #include "cdvs_internal.cuh"
@@ -31,11 +36,12 @@ struct NoAllocScratch {
 
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
-std::once_flag g_once[kMaxDevices];
+std::mutex g_lock[kMaxDevices];
 NoAllocScratch* g_addr[kMaxDevices];
-cudaError_t g_setup_err[kMaxDevices];
 
-// Caller records -> octave-px candidates; clears the counters and status.
+// Caller records -> octave-px candidates; clears the counters and status.  A
+// record whose octave is outside 0 .. n_oct - 1 keeps octave -1, which the
+// selection kernel leaves out (and reports).
 __global__ void noalloc_in_kernel(NoAllocScratch* s, const cdvs_keypoint* cand, int n, int W, int H, int n_oct) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) {
@@ -48,7 +54,8 @@ __global__ void noalloc_in_kernel(NoAllocScratch* s, const cdvs_keypoint* cand, 
   }
   if (i < n) {
     const cdvs_keypoint k = cand[i];
-    const float inv = 1.0f / (float)(1 << k.octave);
+    const bool ok = k.octave >= 0 && k.octave < n_oct;
+    const float inv = ok ? 1.0f / (float)(1 << k.octave) : 0.0f;
     Cand c;
     c.xo = k.x * inv;
     c.yo = k.y * inv;
@@ -56,18 +63,27 @@ __global__ void noalloc_in_kernel(NoAllocScratch* s, const cdvs_keypoint* cand, 
     c.resp = k.response;
     c.pss = k.p_ss;
     c.ratio = k.ratio;
-    c.octave = k.octave;
+    c.octave = ok ? k.octave : -1;
     c.type = k.type;
     c.spare = i;
     s->cand[i] = c;
   }
 }
 
-// Selected points -> caller records (image 0, parent_id = index in the input).
-__global__ void noalloc_out_kernel(const NoAllocScratch* s, cdvs_keypoint* out, int* out_count) {
+// Selected points -> caller records (image 0, parent_id = index in the input),
+// the count, and the call's status code when the caller asked for it.
+__global__ void noalloc_out_kernel(const NoAllocScratch* s, cdvs_keypoint* out, int* out_count, int* out_status) {
   const int n = s->sel_count;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0) *out_count = n;
+  if (i == 0) {
+    *out_count = n;
+    if (out_status) {
+      const int st = s->status;
+      *out_status = (st & kStatusBadInput)          ? CDVS_INVALID_ARGUMENT
+                    : (st & kStatusSelectOverflow) ? CDVS_CAPACITY_TRUNCATED
+                                                   : CDVS_OK;
+    }
+  }
   if (i < n) {
     const Cand& q = s->sel[i];
     const float sc = (float)(1 << q.octave);
@@ -89,16 +105,23 @@ __global__ void noalloc_out_kernel(const NoAllocScratch* s, cdvs_keypoint* out, 
   }
 }
 
-// Device address of the scratch array on the current device, looked up once.
+// Device address of the scratch array on the current device.  Only a
+// successful lookup is kept: a failed one (say, made during a stream
+// capture) is tried again on the next call.
 cudaError_t scratch_address(int device, NoAllocScratch** out) {
   if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::call_once(g_once[device], [device]() {
+  std::lock_guard<std::mutex> lock(g_lock[device]);
+  if (!g_addr[device]) {
     void* p = nullptr;
-    g_setup_err[device] = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return e;
+    }
     g_addr[device] = static_cast<NoAllocScratch*>(p);
-  });
+  }
   *out = g_addr[device];
-  return g_setup_err[device];
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -108,7 +131,8 @@ using namespace cdvs;
 
 extern "C" cdvs_status cdvs_dedupe_select_noalloc(const cdvs_keypoint* cand, int32_t n_cand, int32_t width,
                                                   int32_t height, const cdvs_params* params,
-                                                  cdvs_keypoint* sel_out, int32_t* sel_count, void* cuda_stream) {
+                                                  cdvs_keypoint* sel_out, int32_t* sel_count, int32_t* dev_status,
+                                                  void* cuda_stream) {
   if (!params || !sel_out || !sel_count || n_cand < 0 || (n_cand > 0 && !cand)) return CDVS_INVALID_ARGUMENT;
   if (n_cand > kNoAllocMax) return CDVS_UNSUPPORTED_SIZE;
   if (width < 16 || height < 16 || width > 32768 || height > 32768) return CDVS_UNSUPPORTED_SIZE;
@@ -141,7 +165,7 @@ extern "C" cdvs_status cdvs_dedupe_select_noalloc(const cdvs_keypoint* cand, int
   a.dlog2 = params->dedupe_dlog2;
   a.status = &s->status;
   if (launch_select(a, 1, st) != cudaSuccess) return CDVS_CUDA_ERROR;
-  noalloc_out_kernel<<<(params->max_keypoints + 255) / 256, 256, 0, st>>>(s, sel_out, sel_count);
+  noalloc_out_kernel<<<(params->max_keypoints + 255) / 256, 256, 0, st>>>(s, sel_out, sel_count, dev_status);
   if (cudaGetLastError() != cudaSuccess) return CDVS_CUDA_ERROR;
   return CDVS_OK;
 }

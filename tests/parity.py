@@ -130,5 +130,32 @@ def record_agreement(gk, gd, runs, at_point=None):
     return good, margin, bad
 
 
+def good_pairs(gk, gd, ek, ed):
+    """(i, j) pairs of GPU record i and oracle record j for the same point,
+    with theta within THETA_TOL and a descriptor within DESC_TOL."""
+    out = []
+    m0 = match(gk, ek)
+    for i in range(len(gk)):
+        if m0[i] < 0:
+            continue
+        same_pt = np.nonzero(match(ek, gk[i:i + 1]) == 0)[0]
+        dth = [ang(ek["theta"][j], gk["theta"][i]) for j in same_pt]
+        if dth and min(dth) <= THETA_TOL:
+            j = int(same_pt[int(np.argmin(dth))])
+            if rel_l2(gd[i], ed[j]) <= DESC_TOL:
+                out.append((i, j))
+    return out
+
+
 def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+# Counts that the GPU tests report (printed at the end of the pytest run by
+# tests/conftest.py, so a run's tail shows the good / margin / bad splits and
+# the excluded counts, not only pass or fail).
+REPORT = []
+
+
+def report(name, **counts):
+    REPORT.append((name, counts))

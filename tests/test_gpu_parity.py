@@ -80,6 +80,8 @@ def test_candidates_bracketed_by_oracle(ctx, cd, w, h):
     lo = O.candidates(img, O.params(margin=PT.MARGIN))
     sc = O.candidates(img, O.params(margin=-PT.MARGIN))
     agree, n_dis, n_exc, n = PT.point_agreement(g, ex, lo, sc)
+    PT.report(f"candidates {w}x{h}", oracle=n, gpu=len(g), disagree=n_dis, margin_excluded=n_exc,
+              agreement=round(agree, 5))
     assert agree >= PT.AGREE, (agree, n_dis, n_exc, n)
     m = PT.match(g, ex)
     ok = m >= 0
@@ -138,6 +140,32 @@ def test_dedupe_select_random_sets(ctx):
         assert np.array_equal(sel["parent_id"], order.astype(np.int32)), trial
 
 
+def test_dedupe_select_ties_beyond_the_list(ctx):
+    """More candidates tie at the N-th |response| than the selection's sort
+    list holds (5000 equal responses, N = 2048, a 4096-entry list): the
+    result is still the first N of the total order, exactly as the oracle's,
+    and the same for any order of the input."""
+    from paper_1705_09776_gb300 import cdvs
+    rng = np.random.default_rng(29)
+    n = 5000
+    rec = np.zeros(n, cdvs.KEYPOINT_DTYPE)
+    rec["octave"] = 0                        # one octave: no cross-octave duplicates
+    rec["x"] = rng.integers(1, 639, n) + rng.uniform(-0.5, 0.5, n)
+    rec["y"] = rng.integers(1, 479, n) + rng.uniform(-0.5, 0.5, n)
+    rec["sigma"] = 1.6 * 2 ** rng.uniform(0, 1, n)
+    rec["response"] = rng.choice([-1, 1], n) * 10.0
+    rec["response"][:50] = 20.0               # a few strictly above the tie
+    p = cdvs.params(max_keypoints=2048)
+    order = O.dedupe_select(_oracle_kp_from(rec), O.params(max_keypoints=2048))
+    assert len(order) == 2048
+    sel, cnt, st = ctx.dedupe_select([(480, 640)], [rec], p)
+    assert st == cdvs.CDVS_OK
+    assert np.array_equal(sel["parent_id"], order.astype(np.int32))
+    perm = rng.permutation(n)
+    sel2, _, _ = ctx.dedupe_select([(480, 640)], [rec[perm]], p)
+    assert np.array_equal(perm[sel2["parent_id"]], order)
+
+
 # ------------------------------------------------------------------ S9-S10
 
 @pytest.mark.parametrize("w,h,upright", [(640, 480, 0), (641, 481, 0), (333, 257, 1)])
@@ -155,6 +183,9 @@ def test_describe_on_oracle_points(ctx, cd, w, h, upright):
     sk, sd = O.describe(img, back, O.params(upright=upright, margin=-PT.MARGIN, ori_margin=-PT.MARGIN))
     gk, gd, cnt, st = ctx.describe([img], [rec], cd.params(upright=upright))
     good, margin, bad = PT.record_agreement(gk, gd, [(ok_, od), (lk, ld), (sk, sd)])
+    PT.report(f"describe on oracle points {w}x{h} upright={upright}", oracle=len(ok_), gpu=len(gk), good=good,
+              margin=margin, bad=bad)
+    assert margin <= 0.01 * len(ok_), (good, margin, bad, len(ok_))
     assert bad <= (1 - PT.AGREE) * len(ok_), (good, margin, bad, len(ok_))
     assert good + margin >= PT.AGREE * len(ok_), (good, margin, bad, len(ok_))
 
@@ -175,6 +206,8 @@ def test_extract_end_to_end(ctx, cd, w, h):
 
     gp, ep = points(gk, "parent_id"), points(ek, "parent")
     agree, n_dis, n_exc, n = PT.point_agreement(gp, ep, points(lk, "parent"), points(sk, "parent"))
+    PT.report(f"end-to-end points {w}x{h}", oracle=n, gpu=len(gp), disagree=n_dis, margin_excluded=n_exc,
+              agreement=round(agree, 5))
     assert agree >= PT.AGREE, (agree, n_dis, n_exc, n)
     # orientations and descriptors of matched records: the oracle describes
     # its own selected points exactly and with every threshold moved by 1e-4
@@ -184,7 +217,12 @@ def test_extract_end_to_end(ctx, cd, w, h):
     good, margin, bad = PT.record_agreement(gk, gd, [(ek, ed), od_l, od_s],
                                             at_point=lambda i: O.describe(img, _oracle_kp_from(gk[i:i + 1]),
                                                                           O.params()))
-    assert good > 0.9 * len(ek), (good, margin, bad, len(ek))
+    PT.report(f"end-to-end records {w}x{h}", oracle=len(ek), gpu=len(gk), good=good, margin=margin, bad=bad)
+    # at least 99.5% of the oracle's records are reproduced, at most 1% of
+    # them only as margin cases (a perturbed oracle run, or the oracle at the
+    # GPU's own point, reproduces them), and at most 0.5% are not explained
+    assert good + margin >= PT.AGREE * len(ek), (good, margin, bad, len(ek))
+    assert margin <= 0.01 * len(ek), (good, margin, bad, len(ek))
     assert bad <= (1 - PT.AGREE) * len(ek), (good, margin, bad, len(ek))
 
 
@@ -341,3 +379,53 @@ def test_fp16_storage_error_is_small(ctx, cd):
         assert len(errs) > 10, (octs, len(errs))
         assert np.median(errs) < 1e-2 and np.quantile(errs, 0.9) < 5e-2, (octs, np.median(errs),
                                                                            np.quantile(errs, 0.9))
+
+
+# ------------------------------------------------------------------ failures
+
+def test_allocation_failure_leaves_the_context_usable(cd):
+    """An out-of-memory workspace allocation (injected on the host: the
+    allocation wrapper reports cudaErrorMemoryAllocation) makes the call
+    return CDVS_OUT_OF_MEMORY with a message; the same context then extracts
+    exactly what a fresh one does."""
+    img = _img(333, 257, seed=41)
+    ref = cd.Context(0)
+    rk, rd, rc, _ = ref.extract([img])
+    ref.close()
+    c = cd.Context(0)
+    for n_fail in (1, 3):
+        cd.inject_alloc_failures(n_fail)
+        with pytest.raises(cd.CdvsError) as e:
+            c.extract([img])
+        assert e.value.status == cd.CDVS_OUT_OF_MEMORY
+        assert "workspace" in c.last_error() or "staging" in c.last_error()
+        cd.inject_alloc_failures(0)
+        k, d, cnt, st = c.extract([img])
+        assert st == cd.CDVS_OK
+        assert np.array_equal(k.view(np.uint8), rk.view(np.uint8)) and np.array_equal(d, rd)
+    c.close()
+
+
+def test_candidate_queue_overflow_is_rerun_exactly(cd):
+    """A candidate queue set far smaller than the image's candidates (64 per
+    image) overflows; the call runs again with room for all of them, so its
+    records and candidates equal those of a context with the default room,
+    byte for byte (records) and as a set (candidates, queued in no fixed
+    order)."""
+    imgs = [_img(640, 480, seed=43, i=i) for i in range(3)]
+    ref = cd.Context(0)
+    rk, rd, rc, _ = ref.extract(imgs)
+    rcand, rcc, _ = ref.candidates(imgs)
+    ref.close()
+    c = cd.Context(0)
+    key = lambda r: sorted(zip(r["image"], r["octave"], r["x"], r["y"], r["sigma"]))
+    for call in range(2):
+        c.set_candidate_capacity(64)
+        k, d, cnt, st = c.extract(imgs)
+        assert st == cd.CDVS_OK
+        assert np.array_equal(k.view(np.uint8), rk.view(np.uint8)) and np.array_equal(d, rd)
+        c.set_candidate_capacity(64)
+        cand, cc, st = c.candidates(imgs)
+        assert st == cd.CDVS_OK and np.array_equal(cc, rcc) and key(cand) == key(rcand)
+    PT.report("candidate queue overflow re-run", candidates_per_image=list(map(int, rcc)), capacity=64)
+    c.close()
