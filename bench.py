@@ -178,20 +178,20 @@ def load_peaks():
 
 
 def kernel_sha():
-    """sha256 of K1's sources (the kernel header and its launcher)."""
+    """sha256 of K1's sources (the kernel header and its variant launchers)."""
     h = hashlib.sha256()
-    for f in ("detect_kernel.cuh", "detect.cu"):
+    for f in ("detect_kernel.cuh", "detect.cu", "detect_vb.cu", "detect_vc.cu", "detect_vd.cu"):
         h.update(open(os.path.join(ROOT, "paper_1705_09776_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 
 
-def load_traffic():
-    """DRAM bytes per detection step from the committed ncu summary, when it was
-    taken on the current kernel source."""
+def load_traffic(variant=0):
+    """DRAM bytes per image of the octave-0 detection launch of a K1 variant,
+    from the committed ncu summary, when it was taken on the current sources."""
     try:
         t = json.load(open(TRAFFIC_FILE))
         if t.get("kernel_sha256") == kernel_sha():
-            return t
+            return t["variants"].get(str(variant))
     except Exception:
         pass
     return None
@@ -437,6 +437,12 @@ def uneven_leg(ctx, cdvs, torch, imgs, sizes, args, alu_peak, steps=None):
     ms32, rec32 = timed(p32, True)
     ms16, rec16 = timed(p16, True)
     ms_direct, _ = timed(p32, False)
+    tuning = ctx.detect_tuning()
+    # the same FP32 graph leg with K1's work shape fixed to variant 0 (the
+    # 128 x 32 tile, one 512-thread CTA per SM) instead of the tuned choice
+    ctx.set_detect_variant(0)
+    ms_fixed, _ = timed(p32, True)
+    ctx.set_detect_variant(-1)
     # stage times from profiled (direct) calls
     ctx.profile(True)
     ctx.profile_read(reset=True)
@@ -454,6 +460,8 @@ def uneven_leg(ctx, cdvs, torch, imgs, sizes, args, alu_peak, steps=None):
                        "records_per_step": rec32},
             "fp16": {"value": n / (ms16 * 1e-3), "ms_per_step": ms16, "records_per_step": rec16},
             "direct_launches": {"value": n / (ms_direct * 1e-3), "ms_per_step": ms_direct},
+            "fixed_variant0": {"value": n / (ms_fixed * 1e-3), "ms_per_step": ms_fixed},
+            "detect_tuning": tuning,
             "stage_ms_per_call": prof,
             "roofline": k1_roofline(flops0, prof["detect_octave0"], alu_peak,
                                     "detect_kernel, octave-0 launch on the resized images")}
@@ -540,6 +548,7 @@ def highres_leg(ctx, cdvs, torch, imgs, args, alu_peak, steps=None):
     ms32, kp32, st32 = timed(p32)
     p16 = cdvs.params(num_octaves=6, max_keypoints=N, storage=cdvs.CDVS_STORAGE_FP16)
     ms16, kp16, st16 = timed(p16)
+    tuning = ctx.detect_tuning()
     learned = None
     if os.path.exists(cdvs.PROPOSAL_WEIGHTS):
         theta, thr = cdvs.load_proposal_weights()
@@ -557,6 +566,7 @@ def highres_leg(ctx, cdvs, torch, imgs, args, alu_peak, steps=None):
                                    "LoG scales, N=2000, 128-D float descriptors", "storage": "fp32",
                        "records_per_step": int(len(kp32))},
             "stage_ms_per_step": st32,
+            "detect_tuning": tuning,
             "roofline": k1_roofline(flops_o[0] * n, st32["detect_octave0"], alu_peak,
                                     "detect_kernel, octave-0 launch (2048x1536)"),
             "fp16": {"value": n / (ms16 * 1e-3), "ms_per_step": ms16, "records_per_step": int(len(kp16)),
@@ -644,6 +654,7 @@ def main():
     ap.add_argument("--no-legs", action="store_true", help="skip the uneven (config 3) and high-resolution "
                                                             "(config 5) legs of the default line")
     ap.add_argument("--uneven-images", type=int, default=1024, help="images of the uneven leg")
+    ap.add_argument("--detect-variant", type=int, default=-1, help="K1 work shape: -1 tuned (default), 0..3 fixed")
     ap.add_argument("--highres-images", type=int, default=64, help="images of the high-resolution leg")
     ap.add_argument("--workload", default="batch", choices=["batch", "uneven", "highres"],
                     help="batch: 256 x 640x480 (default); uneven: 1024 uneven images resized to 640; "
@@ -680,6 +691,7 @@ def main():
     p = cdvs.params(storage=cdvs.CDVS_STORAGE_FP16 if args.storage == "fp16" else cdvs.CDVS_STORAGE_FP32)
     cap = n * int(p["max_keypoints"][0]) * int(p["max_orientations"][0])
     ctx = cdvs.Context(local)
+    ctx.set_detect_variant(args.detect_variant)
     stream = torch.cuda.current_stream()
     d_img = torch.from_numpy(imgs).cuda()
     d_kp = torch.zeros(cap * cdvs.KEYPOINT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
@@ -721,6 +733,7 @@ def main():
     prof = ctx.profile_read(reset=True)
     ctx.profile(False)
     clocks = sampler.stop()
+    tuning = ctx.detect_tuning()
     if dist is not None:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -764,9 +777,11 @@ def main():
     except Exception:
         sgemm = None
     gbs = bytes_o[0] * n / (o0_ms * 1e-3) / 1e9
-    traffic = load_traffic()
+    v0 = int(tuning["last_call_variants"][0])
+    traffic = load_traffic(v0)
     det_ms = prof["detect"][0] / args.steps
-    roofline = {"kernel": "detect_kernel, octave-0 launch (K1: 4 Gaussian levels + LoG + ALP + extremum + refine)",
+    roofline = {"kernel": "detect_kernel, octave-0 launch (K1: 4 Gaussian levels + LoG + ALP + extremum + refine), "
+                          f"variant {v0}: {tuning['variants'][v0]}",
                 "bound": "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s", "frac": tflops / alu_peak,
                 "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_max:.0f} MHz "
                                "(SM count and maximum clock queried from the device)",
@@ -794,7 +809,7 @@ def main():
            "e2e": {"value": (n * world / (e2e_ms * 1e-3)) if e2e_ms == e2e_ms else None, "unit": "images/s",
                    "ms_per_step": e2e_ms if e2e_ms == e2e_ms else None,
                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-           "gpu_launches": launches, "roofline": roofline, "clocks": clocks}
+           "gpu_launches": launches, "roofline": roofline, "clocks": clocks, "detect_tuning": tuning}
     out["one_image_per_call"] = per_image
     if legs is not None:
         (u_imgs, u_sizes), h_imgs = legs

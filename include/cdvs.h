@@ -423,6 +423,29 @@ cdvs_status cdvs_scfv(cdvs_ctx *ctx, int32_t n_images, const float *desc, const 
                       int32_t n_select, float *g_mu, float *g_sigma, float *delta, int32_t *order,
                       uint32_t *bits, uint32_t flags, void *cuda_stream);
 
+/* The work shape of interest-point detection (Alg. 1 stages A and B; the
+ * same arithmetic in every shape, so results are identical bit for bit).
+ * Four variants: 0 and 1 tile the octave in 128 x 32 pixel tiles with one
+ * 512-thread CTA per SM, 2 and 3 in 128 x 16 tiles with two 256-thread CTAs
+ * per SM; the y pass of the separable filter takes 6, 12, 4 or 10 rows per
+ * thread.  variant = -1 (the default) tunes them: while a class of octave
+ * launches (the first octave, or the later ones, per storage type and set of
+ * filter radii) has a variant without a time, each call runs one such
+ * variant and times it with CUDA events on its stream (read back by a later
+ * call; first octaves are timed only when the images are on the device, and
+ * such calls do not use the CUDA graph); then every octave takes the variant
+ * whose time per tile times its tile count for the batch is smallest.
+ * variant = 0..3 fixes the shape (the first octave under a block proposal,
+ * and octaves whose filter radii exceed 14 (sigma0 above the default), always
+ * use variant 0). */
+cdvs_status cdvs_set_detect_variant(cdvs_ctx *ctx, int32_t variant);
+
+/* The tuner's state as a JSON object (mode, variant names, per class the
+ * measured microseconds per tile of each variant, and the variants of the
+ * last call's octaves), NUL-terminated into buf (capacity bytes, may be
+ * NULL).  Returns the length of the full text, or -1 for a NULL context. */
+int32_t cdvs_detect_tuning(cdvs_ctx *ctx, char *buf, int32_t capacity);
+
 /* Candidate queue capacity per image (candidates of all octaves before the
  * cross-octave check).  0 (the default) sizes it from the image: max(4096,
  * pixels / 16), more than the method finds on any natural image.  When a

@@ -60,7 +60,8 @@ EXPORTED = ["cdvs_params_default", "cdvs_create", "cdvs_destroy", "cdvs_last_err
             "cdvs_rank_host", "cdvs_transform_ternary", "cdvs_profile", "cdvs_profile_read", "cdvs_wait",
             "cdvs_dedupe_select_noalloc", "cdvs_set_proposal", "cdvs_proposal_logits",
             "cdvs_proposal_train_step", "cdvs_resize", "cdvs_set_graph", "cdvs_set_scfv_model", "cdvs_scfv",
-            "cdvs_inject_alloc_failures", "cdvs_set_candidate_capacity"]
+            "cdvs_inject_alloc_failures", "cdvs_set_candidate_capacity", "cdvs_set_detect_variant",
+            "cdvs_detect_tuning"]
 STAGES = ["detect", "select", "describe", "offsets", "pack", "detect_octave0", "proposal"]
 
 
@@ -109,6 +110,8 @@ def load(build_if_missing: bool = True):
         "cdvs_proposal_train_step": (i32, [P, P, i32, i32, i32, i32, P, P, P, P, P, P, P, i32, C.c_float, i32, P]),
         "cdvs_inject_alloc_failures": (None, [i32]),
         "cdvs_set_candidate_capacity": (i32, [P, i32]),
+        "cdvs_set_detect_variant": (i32, [P, i32]),
+        "cdvs_detect_tuning": (i32, [P, P, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -182,6 +185,18 @@ class Context:
     def set_candidate_capacity(self, per_image: int):
         """cdvs_set_candidate_capacity: 0 = from the image size."""
         self._check(self._L.cdvs_set_candidate_capacity(self.handle, int(per_image)))
+
+    def set_detect_variant(self, variant: int):
+        """cdvs_set_detect_variant: -1 = tuned (default), 0..3 = a fixed work shape."""
+        self._check(self._L.cdvs_set_detect_variant(self.handle, int(variant)))
+
+    def detect_tuning(self) -> dict:
+        """cdvs_detect_tuning as a dict."""
+        import json
+        n = self._L.cdvs_detect_tuning(self.handle, None, 0)
+        buf = C.create_string_buffer(n + 1)
+        self._L.cdvs_detect_tuning(self.handle, buf, n + 1)
+        return json.loads(buf.value.decode())
 
     def set_graph(self, enable: bool):
         """Device-resident extractions through one CUDA graph (cdvs_set_graph)."""

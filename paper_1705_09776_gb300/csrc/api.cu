@@ -5,6 +5,7 @@
 //   K3+K10 cross-octave check + selection (one CTA per image)
 //   K5 orientation, packing scan, K6 descriptors
 // Every step of the method runs in the kernels; this file only moves bytes.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -108,6 +109,24 @@ struct cdvs_ctx {
   std::vector<Upload> uploads[kMaxInputChunks];  // empty: inputs already on the device
   // candidate queue capacity per image: at least this many (grown after a
   // call whose queue overflowed), and the capacity of the last call
+  // K1 work-shape tuner: per class of octave launches (first octave or the
+  // later ones, storage type, level radii) the measured time per tile of
+  // each variant; the variant of every octave of the current call
+  struct TuneClass {
+    int later, storage;
+    int radii[kScales];
+    float ms_per_tile[kDetectVariants];  // < 0: not measured yet
+    int inflight[kDetectVariants];       // measurements enqueued, not read back
+  };
+  struct Measure {
+    int cls, variant;
+    long long tiles;
+    cudaEvent_t a, b;
+  };
+  std::vector<TuneClass> tune;
+  std::vector<Measure> measures;
+  int variant_mode = -1;  // cdvs_set_detect_variant: -1 tuned, else fixed
+  int oct_variant[kMaxOctaves] = {};
   int cap_floor = 0;
   int cap_fixed = 0;  // cdvs_set_candidate_capacity; 0: from the image size
   int last_cap = 0;
@@ -347,17 +366,144 @@ cdvs_status plan_batch(cdvs_ctx* c, int n, const cdvs_image_desc* sizes, const c
     max_oct = std::max(max_oct, no);
     max_pixels = std::max(max_pixels, (long long)d.width * d.height);
   }
+  return CDVS_OK;
+}
+
+// Tiles of octave o of image i with the tile rows of a K1 variant (tiles are
+// 128 wide in every variant).
+long long variant_tiles(const ImgPlan& P, int o, int variant) {
+  if (o >= P.n_oct) return 0;
+  const int ty = detect_variant_rows(variant);
+  return (long long)P.oct[o].tiles_x * ((P.oct[o].H + ty - 1) / ty);
+}
+
+// Per octave, the first tile of every image in the launch's tile order, for
+// the variant that runs the octave (c->oct_variant).
+void build_prefix(cdvs_ctx* c, int n, int max_oct) {
   c->h_prefix.assign((size_t)kMaxOctaves * (n + 1), 0);
   for (int o = 0; o < max_oct; ++o) {
     int* pre = c->h_prefix.data() + (size_t)o * (n + 1);
     pre[0] = 0;
-    for (int i = 0; i < n; ++i) {
-      const ImgPlan& P = c->h_plans[i];
-      const int t = o < P.n_oct ? P.oct[o].tiles_x * P.oct[o].tiles_y : 0;
-      pre[i + 1] = pre[i] + t;
-    }
+    for (int i = 0; i < n; ++i) pre[i + 1] = pre[i] + (int)variant_tiles(c->h_plans[i], o, c->oct_variant[o]);
   }
-  return CDVS_OK;
+}
+
+// ---- the K1 work-shape tuner
+//
+// Every variant computes the same levels and candidates bit for bit, so the
+// tuner measures them on the caller's own calls: while a class of octave
+// launches has an unmeasured variant, each call runs one such variant and
+// times its launches with CUDA events on the call's stream (read back by a
+// later call, without synchronising); once every variant has a time per
+// tile, each octave takes the variant whose time per tile times its tile
+// count for the batch is smallest.  The first octave is measured only on
+// calls whose images are already on the device (its launches wait for
+// uploads otherwise).
+
+int tune_class(cdvs_ctx* c, bool later, int storage, const int* radii) {
+  for (size_t i = 0; i < c->tune.size(); ++i) {
+    const auto& t = c->tune[i];
+    if (t.later == (int)later && t.storage == storage && std::equal(radii, radii + kScales, t.radii)) return (int)i;
+  }
+  cdvs_ctx::TuneClass t;
+  t.later = later;
+  t.storage = storage;
+  std::copy(radii, radii + kScales, t.radii);
+  for (int v = 0; v < kDetectVariants; ++v) {
+    t.ms_per_tile[v] = -1.0f;
+    t.inflight[v] = 0;
+  }
+  c->tune.push_back(t);
+  return (int)c->tune.size() - 1;
+}
+
+// Measurements whose launches have finished become times per tile (the
+// smallest seen per variant).
+void harvest_measures(cdvs_ctx* c) {
+  std::vector<cdvs_ctx::Measure> keep;
+  for (auto& m : c->measures) {
+    const cudaError_t q = cudaEventQuery(m.b);
+    if (q == cudaErrorNotReady) {
+      keep.push_back(m);
+      continue;
+    }
+    float ms = 0.0f;
+    auto& t = c->tune[m.cls];
+    --t.inflight[m.variant];
+    if (q == cudaSuccess && cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess && m.tiles > 0) {
+      const float per = ms / (float)m.tiles;
+      float& cur = t.ms_per_tile[m.variant];
+      cur = cur < 0.0f ? per : std::min(cur, per);
+    }
+    cudaGetLastError();
+    c->pool.push_back(m.a);
+    c->pool.push_back(m.b);
+  }
+  c->measures.swap(keep);
+}
+
+bool class_tuned(const cdvs_ctx::TuneClass& t) {
+  for (int v = 0; v < kDetectVariants; ++v)
+    if (t.ms_per_tile[v] < 0.0f) return false;
+  return true;
+}
+
+// The variant of every octave of this call; the classes this call measures
+// (cls, variant) in `measure` (at most one per class).
+void choose_variants(cdvs_ctx* c, int n, int max_oct, const cdvs_params& p, bool masked0, bool device_inputs,
+                     std::vector<std::pair<int, int>>& measure) {
+  measure.clear();
+  harvest_measures(c);
+  for (int o = 0; o < max_oct; ++o) {
+    int radii[kScales];
+    float taps[kMaxRadius + 1];
+    for (int k = 0; k < kScales; ++k) radii[k] = gauss_taps(tau_of(p, o, k), taps);
+    // radii above 14 (a sigma0 above the default's) and the first octave
+    // under a block proposal run on variant 0 only
+    const bool only0 = (o == 0 && masked0) || *std::max_element(radii, radii + kScales) > 14;
+    if (c->variant_mode >= 0 || only0) {
+      c->oct_variant[o] = only0 ? 0 : c->variant_mode;
+      continue;
+    }
+    const size_t n_classes = c->tune.size();
+    const int cls = tune_class(c, o > 0, p.storage, radii);
+    auto& t = c->tune[cls];
+    if (c->tune.size() > n_classes) {
+      // a new class: load every variant's kernel now, so no timed launch
+      // pays for loading it
+      DetectArgs a;
+      std::memset(&a, 0, sizeof(a));
+      a.octave = o;
+      a.n_images = n;
+      const int maxr = *std::max_element(radii, radii + kScales);
+      for (int u = 0; u < kDetectVariants; ++u) launch_detect(a, 0, maxr, p.storage, c->n_sms, u, nullptr);
+      cudaGetLastError();
+    }
+    int v = -1;
+    for (const auto& m : measure)
+      if (m.first == cls) v = m.second;  // a later octave of a class measured by this call
+    if (v < 0 && !class_tuned(t) && (o > 0 || device_inputs)) {
+      for (int u = 0; u < kDetectVariants && v < 0; ++u)
+        if (t.ms_per_tile[u] < 0.0f && t.inflight[u] == 0) v = u;
+      if (v >= 0) measure.push_back({cls, v});
+    }
+    if (v < 0) {
+      // the measured variant with the least predicted time for this batch
+      double best = 0.0;
+      v = 0;
+      for (int u = 0; u < kDetectVariants; ++u) {
+        if (t.ms_per_tile[u] < 0.0f) continue;
+        long long tiles = 0;
+        for (int i = 0; i < n; ++i) tiles += variant_tiles(c->h_plans[i], o, u);
+        const double cost = (double)tiles * t.ms_per_tile[u];
+        if (best == 0.0 || cost < best) {
+          best = cost;
+          v = u;
+        }
+      }
+    }
+    c->oct_variant[o] = v;
+  }
 }
 
 int cand_capacity(long long max_pixels, int fixed, int floor) {
@@ -457,7 +603,8 @@ cudaError_t issue_upload(cdvs_ctx* c, int k, cudaStream_t s) {
 }
 
 cdvs_status run_detect(cdvs_ctx* c, int n, const cdvs_params& p, int max_oct, int cap, cudaStream_t s,
-                       const uint8_t* tile_mode = nullptr, const uint16_t* block_mask = nullptr) {
+                       const std::vector<std::pair<int, int>>& measure, const uint8_t* tile_mode = nullptr,
+                       const uint16_t* block_mask = nullptr) {
   cudaError_t e;
   DetectArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -476,6 +623,8 @@ cdvs_status run_detect(cdvs_ctx* c, int n, const cdvs_params& p, int max_oct, in
   a.T = p.contrast_T;
   a.edge_lim = (float)(((double)p.edge_r + 1.0) * ((double)p.edge_r + 1.0) / (double)p.edge_r);
   a.offset_max = p.offset_max;
+  cudaEvent_t m_ev[2] = {nullptr, nullptr};
+  int m_idx[2] = {-1, -1};
   for (int o = 0; o < max_oct; ++o) {
     a.octave = o;
     a.write_level0 = o == 0 ? 1 : 0;
@@ -491,6 +640,17 @@ cdvs_status run_detect(cdvs_ctx* c, int n, const cdvs_params& p, int max_oct, in
     // octave 0 runs per input chunk, each launch after its chunk's upload
     const int parts = o == 0 ? c->n_chunks : 1;
     cudaEvent_t ev0 = o == 0 ? prof_begin(c, s) : nullptr;
+    // a tuner measurement starts at the first octave of its group (octave 0
+    // alone, or octaves 1 .. max_oct - 1, which share radii and input type)
+    const int g = o > 0 ? 1 : 0;
+    if (o <= 1)
+      for (size_t j = 0; j < measure.size(); ++j)
+        if (c->tune[measure[j].first].later == g && measure[j].second == c->oct_variant[o] &&
+            (m_ev[g] = take_event(c)) != nullptr) {
+          m_idx[g] = (int)j;
+          cudaEventRecord(m_ev[g], s);
+          break;
+        }
     for (int k = 0; k < parts; ++k) {
       const int i0 = parts > 1 ? c->chunk_begin[k] : 0, i1 = parts > 1 ? c->chunk_begin[k + 1] : n;
       if (o == 0 && (e = issue_upload(c, k, s)) != cudaSuccess) return cuda_fail(c, e, "image upload");
@@ -501,10 +661,25 @@ cdvs_status run_detect(cdvs_ctx* c, int n, const cdvs_params& p, int max_oct, in
       a.tile_prefix = d_prefix + i0;
       a.tile_base = prefix[i0];
       const int n_tiles = prefix[i1] - prefix[i0];
-      if ((e = launch_detect(a, n_tiles, maxr, p.storage, c->n_sms, s)) != cudaSuccess)
+      if (n_tiles > 0 && (e = launch_detect(a, n_tiles, maxr, p.storage, c->n_sms, c->oct_variant[o], s)) != cudaSuccess)
         return cuda_fail(c, e, "detect launch");
     }
     if (o == 0) prof_end(c, 5, parts, ev0, s);
+    // ... and ends after its last octave
+    if (m_ev[g] && o == (g ? max_oct - 1 : 0)) {
+      cudaEvent_t mb = take_event(c);
+      if (mb) {
+        cudaEventRecord(mb, s);
+        long long tiles = 0;
+        for (int q = g; q <= o; ++q) tiles += c->h_prefix[(size_t)q * (n + 1) + n];
+        const auto& m = measure[m_idx[g]];
+        c->measures.push_back(cdvs_ctx::Measure{m.first, m.second, tiles, m_ev[g], mb});
+        ++c->tune[m.first].inflight[m.second];
+      } else {
+        c->pool.push_back(m_ev[g]);
+      }
+      m_ev[g] = nullptr;
+    }
   }
   return CDVS_OK;
 }
@@ -786,6 +961,12 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
   long long level_elems, max_pixels;
   int max_oct;
   if ((st = plan_batch(c, n, eff.data(), p, level_elems, max_oct, max_pixels)) != CDVS_OK) return st;
+  const bool proposal = p.use_proposal && (mode == kExtract || mode == kCandidates);
+  // K1's work shape per octave (measured by this call while a class is being
+  // tuned), then the tile lists of that shape
+  std::vector<std::pair<int, int>> measure;
+  choose_variants(c, n, max_oct, p, proposal, (flags & CDVS_INPUT_DEVICE) || any_resize, measure);
+  build_prefix(c, n, max_oct);
   const int cap = cand_capacity(max_pixels, c->cap_fixed, c->cap_floor);
   c->last_cap = cap;
   const int N = p.max_keypoints;
@@ -810,8 +991,9 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
   // Device-resident extraction can run as one CUDA graph: the stream work
   // below is captured, the cached executable graph is updated in place (or
   // instantiated again when the work changed shape) and launched.
+  // (calls that measure a K1 variant run their launches directly)
   const bool graph = c->graph && mode == kExtract && (flags & CDVS_INPUT_DEVICE) && (flags & CDVS_OUTPUT_DEVICE) &&
-                     !c->prof;
+                     !c->prof && measure.empty();
   struct CaptureGuard {  // ends an abandoned capture on early returns
     cudaStream_t s;
     bool on = false;
@@ -846,7 +1028,6 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
   cudaEvent_t ev = prof_begin(c, s);
   const uint8_t* tile_mode = nullptr;
   const uint16_t* block_mask = nullptr;
-  const bool proposal = p.use_proposal && (mode == kExtract || mode == kCandidates);
   if (proposal || any_resize) {
     // the resize and the network read the whole batch: every upload first
     for (int k = 0; k < c->n_chunks; ++k)
@@ -863,7 +1044,7 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
     tile_mode = static_cast<const uint8_t*>(c->prop_mode.p);
     block_mask = reinterpret_cast<const uint16_t*>(tile_mode + 2 * (size_t)c->h_prefix[n]);
   }
-  if ((st = run_detect(c, n, p, max_oct, cap, s, tile_mode, block_mask)) != CDVS_OK) return st;
+  if ((st = run_detect(c, n, p, max_oct, cap, s, measure, tile_mode, block_mask)) != CDVS_OK) return st;
   prof_end(c, 0, max_oct, ev, s);
   // the staged host images are read no more
   if (!(flags & CDVS_INPUT_DEVICE) && (e = cudaEventRecord(hset.in_free, s)) != cudaSuccess)
@@ -1173,6 +1354,10 @@ void cdvs_destroy(cdvs_ctx* c) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
   }
+  for (const auto& m : c->measures) {
+    cudaEventDestroy(m.a);
+    cudaEventDestroy(m.b);
+  }
   for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
   if (c->copy_stream) {
     cudaStreamSynchronize(c->copy_stream);
@@ -1385,6 +1570,47 @@ cdvs_status cdvs_wait(cdvs_ctx* c, void* cuda_stream) {
   // and later calls get twice the capacity
   if (bits & kStatusCandOverflow) c->cap_floor = std::max(c->cap_floor, 2 * c->last_cap);
   return map_status(c, bits);
+}
+
+cdvs_status cdvs_set_detect_variant(cdvs_ctx* c, int32_t variant) {
+  if (!c) return CDVS_INVALID_ARGUMENT;
+  if (variant < -1 || variant >= kDetectVariants)
+    return fail(c, CDVS_INVALID_ARGUMENT, "variant must be -1 (tuned) or 0..3");
+  c->variant_mode = variant;
+  return CDVS_OK;
+}
+
+int32_t cdvs_detect_tuning(cdvs_ctx* c, char* buf, int32_t capacity) {
+  if (!c) return -1;
+  cudaSetDevice(c->device);
+  harvest_measures(c);
+  std::string j = "{\"mode\": " + std::to_string(c->variant_mode) + ", \"variants\": [";
+  for (int v = 0; v < kDetectVariants; ++v)
+    j += std::string(v ? ", " : "") + "\"" + detect_variant_name(v) + "\"";
+  j += "], \"classes\": [";
+  for (size_t i = 0; i < c->tune.size(); ++i) {
+    const auto& t = c->tune[i];
+    j += std::string(i ? ", " : "") + "{\"octaves\": \"" + (t.later ? "1+" : "0") + "\", \"storage\": \"" +
+         (t.storage == CDVS_STORAGE_FP16 ? "fp16" : "fp32") + "\", \"radii\": [";
+    for (int k = 0; k < kScales; ++k) j += std::string(k ? ", " : "") + std::to_string(t.radii[k]);
+    j += "], \"us_per_tile\": [";
+    for (int v = 0; v < kDetectVariants; ++v) {
+      char num[32];
+      if (t.ms_per_tile[v] < 0.0f) std::snprintf(num, sizeof(num), "null");
+      else std::snprintf(num, sizeof(num), "%.4f", 1e3 * t.ms_per_tile[v]);
+      j += std::string(v ? ", " : "") + num;
+    }
+    j += std::string("], \"tuned\": ") + (class_tuned(t) ? "true" : "false") + "}";
+  }
+  j += "], \"last_call_variants\": [";
+  for (int o = 0; o < kMaxOctaves; ++o) j += std::string(o ? ", " : "") + std::to_string(c->oct_variant[o]);
+  j += "]}";
+  if (buf && capacity > 0) {
+    const size_t m = std::min((size_t)capacity - 1, j.size());
+    std::memcpy(buf, j.data(), m);
+    buf[m] = 0;
+  }
+  return (int32_t)j.size();
 }
 
 cdvs_status cdvs_set_candidate_capacity(cdvs_ctx* c, int32_t per_image) {

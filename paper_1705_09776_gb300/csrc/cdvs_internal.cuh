@@ -151,9 +151,20 @@ struct DescribeArgs {
 
 // launchers (defined in the .cu files)
 size_t detect_smem_bytes(int max_radius);
-cudaError_t launch_detect(const DetectArgs& a, int n_tiles, int max_radius, int storage, int n_sms,
+// K1 variants (work shapes of the same arithmetic; every variant gives the
+// same levels and candidates bit for bit): 0 and 1 tile 128 x 32 with one
+// 512-thread CTA per SM, 2 and 3 tile 128 x 16 with two 256-thread CTAs per
+// SM; they differ in the rows per thread of the y pass.
+constexpr int kDetectVariants = 4;
+int detect_variant_rows(int variant);          // output rows of the variant's tile
+const char* detect_variant_name(int variant);
+cudaError_t launch_detect(const DetectArgs& a, int n_tiles, int max_radius, int storage, int n_sms, int variant,
                           cudaStream_t s);
-cudaError_t launch_detect_masked(const DetectArgs& a, int n_tiles, int max_radius, int storage, int grid,
+cudaError_t launch_detect_a(const DetectArgs& a, int n_tiles, int max_radius, int storage, int n_sms, cudaStream_t s);
+cudaError_t launch_detect_b(const DetectArgs& a, int n_tiles, int max_radius, int storage, int n_sms, cudaStream_t s);
+cudaError_t launch_detect_c(const DetectArgs& a, int n_tiles, int max_radius, int storage, int n_sms, cudaStream_t s);
+cudaError_t launch_detect_d(const DetectArgs& a, int n_tiles, int max_radius, int storage, int n_sms, cudaStream_t s);
+cudaError_t launch_detect_masked(const DetectArgs& a, int n_tiles, int max_radius, int storage, int n_sms,
                                  cudaStream_t s);
 cudaError_t launch_select(const SelectArgs& a, int n_images, cudaStream_t s);
 size_t describe_smem_bytes(int patch_side);

@@ -46,18 +46,34 @@
 namespace cdvs {
 namespace {
 
-constexpr int kRows = kTY + 2 * kHalo;   // 36 rows of G per tile
-constexpr int kRP = kRows / 2;           // 18 row pairs
 constexpr int kGC = kTX + 2 * kHalo;     // 132 columns of G
 constexpr int kLC = kTX + 2;             // 130 columns of L
-constexpr int kSV = 6;                   // rows per thread in the y pass
-constexpr int kSH = 6;                   // columns per thread in the x pass
-constexpr int kLG = 3;                   // row-pair groups in the Laplacian pass
-constexpr int kWarps = kDetThreads / 32;
-static_assert(kRows % kSV == 0 && kSV % 2 == 0, "y-pass strips must tile the row pairs");
-static_assert(kGC % kSH == 0 && kSH % 2 == 0, "x-pass strips must tile the columns");
-static_assert(kRP % kLG == 0, "Laplacian groups must tile the row pairs");
-static_assert((kTX * kTY / 2) % kDetThreads == 0, "extremum loop must be warp-uniform");
+
+// The work shape of a K1 variant: output tile rows TY (the tile is always 128
+// wide), threads per CTA, CTAs per SM the launch bounds ask for, rows per
+// thread in the y pass (SV), columns per thread in the x pass (SH), row-pair
+// groups in the Laplacian (LG), and whether FP32 input is copied straight
+// into the FP32 tile (no staging buffer: the next tile's copies are issued
+// once the last y pass has read the current one).
+template <int TY_, int THREADS_, int MINB_, int SV_, int SH_, int LG_>
+struct Shape {
+  static constexpr int TY = TY_, THREADS = THREADS_, MINB = MINB_, SV = SV_, SH = SH_, LG = LG_;
+  static constexpr int ROWS = TY + 2 * kHalo;  // rows of G per tile
+  static constexpr int RP = ROWS / 2;          // row pairs
+  static constexpr int WARPS = THREADS / 32;
+  static_assert(ROWS % SV == 0 && SV % 2 == 0, "y-pass strips must tile the row pairs");
+  static_assert(kGC % SH == 0 && SH % 2 == 0, "x-pass strips must tile the columns");
+  static_assert(RP % LG == 0, "Laplacian groups must tile the row pairs");
+  static_assert((kTX * TY / 2) % THREADS == 0, "extremum loop must be warp-uniform");
+};
+
+// The variants (index = kernel variant id of the launchers and the tuner):
+// one 512-thread CTA per SM on 128 x 32 tiles (y pass 6 or 12 rows per
+// thread), or two 256-thread CTAs per SM on 128 x 16 tiles (y pass 4 or 10).
+using ShapeA = Shape<32, 512, 1, 6, 6, 3>;
+using ShapeB = Shape<32, 512, 1, 12, 6, 3>;
+using ShapeC = Shape<16, 256, 2, 4, 6, 2>;
+using ShapeD = Shape<16, 256, 2, 10, 6, 2>;
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
@@ -103,7 +119,7 @@ struct TileInfo {
 // rows can be copied in 16-byte pieces when source rows, lengths and
 // destination rows in raw all start on 16-byte boundaries; otherwise they are
 // loaded element by element.
-template <typename InT>
+template <typename S, typename InT>
 __device__ __noinline__ void tile_info(const DetectArgs& a, const int* prefix, int b, int n_tiles, int ic, TileInfo* out) {
   TileInfo t;
   t.valid = b < n_tiles;
@@ -123,7 +139,7 @@ __device__ __noinline__ void tile_info(const DetectArgs& a, const int* prefix, i
   const int k = b - prefix[lo];
   t.img = lo;
   t.tx0 = (k % op.tiles_x) * kTX;
-  t.ty0 = (k / op.tiles_x) * kTY;
+  t.ty0 = (k / op.tiles_x) * S::TY;
   t.W = op.W;
   t.H = op.H;
   t.lpitch = op.lpitch;
@@ -159,17 +175,17 @@ __device__ __noinline__ void tile_info(const DetectArgs& a, const int* prefix, i
 // All threads of the CTA issue the 16-byte copies of every input row of tile
 // t into raw (column c of a raw row is image x = tx0 - cm + c; rows clamp to
 // the image) and commit them as one group.
-template <typename InT>
+template <typename S, typename InT>
 __device__ __forceinline__ void issue_tile_copy(const TileInfo& t, int ic, int rm, InT* raw) {
   constexpr int per = 16 / sizeof(InT);  // elements per piece
   const int cm = (ic - kTX) / 2;
-  const int IR = kRows + 2 * rm;
+  const int IR = S::ROWS + 2 * rm;
   const int y0 = t.ty0 - kHalo - rm;
   const int x0 = t.tx0 - cm;
   const int nc = (t.ce - t.cs) / per;  // pieces per row
   const InT* src = static_cast<const InT*>(t.base) + t.cs;
   InT* dst = raw + (t.cs - x0);
-  for (int i = threadIdx.x; i < IR * nc; i += kDetThreads) {
+  for (int i = threadIdx.x; i < IR * nc; i += S::THREADS) {
     const int row = i / nc, c = i - row * nc;
     const int y = min(max(y0 + row, 0), t.H - 1);
     cp_async16(dst + (size_t)row * ic + c * per, src + (size_t)y * t.pitch + c * per);
@@ -178,14 +194,14 @@ __device__ __forceinline__ void issue_tile_copy(const TileInfo& t, int ic, int r
 }
 
 // raw (copied columns only) -> in (FP32), replicating the edge columns.
-template <typename InT>
+template <typename S, typename InT>
 __device__ __forceinline__ void convert_raw(const InT* raw, const TileInfo& t, int ic, int rm, float* in) {
   const int cm = (ic - kTX) / 2;
-  const int IR = kRows + 2 * rm;
+  const int IR = S::ROWS + 2 * rm;
   const int x0 = t.tx0 - cm;
   const int clo = t.cs - x0, chi = t.ce - 1 - x0;  // first / last copied column
   const int n4 = ic / 4;
-  for (int i = threadIdx.x; i < IR * n4; i += kDetThreads) {
+  for (int i = threadIdx.x; i < IR * n4; i += S::THREADS) {
     const int row = i / n4;
     const int c = (i - row * n4) * 4;
     const InT* src = raw + (size_t)row * ic;
@@ -209,33 +225,53 @@ __device__ __forceinline__ void convert_raw(const InT* raw, const TileInfo& t, i
 
 // Element-by-element input load with clamp-to-edge (tiles whose rows cannot
 // be copied in 16-byte pieces).
-template <typename InT>
+template <typename S, typename InT>
 __device__ __forceinline__ void load_tile_direct(const TileInfo& t, int ic, int rm, float* in) {
   const int cm = (ic - kTX) / 2;
-  const int IR = kRows + 2 * rm;
+  const int IR = S::ROWS + 2 * rm;
   const int y0 = t.ty0 - kHalo - rm, x0 = t.tx0 - cm;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int row = warp; row < IR; row += kWarps) {
+  for (int row = warp; row < IR; row += S::WARPS) {
     const int y = min(max(y0 + row, 0), t.H - 1);
     const InT* src = static_cast<const InT*>(t.base) + (size_t)y * t.pitch;
     for (int c = lane; c < ic; c += 32) in[row * ic + c] = to_f(src[min(max(x0 + c, 0), t.W - 1)]);
   }
 }
 
+// FP32 rows copied straight into `in` (copied columns only): the columns
+// outside the image take the value of the nearest copied one.  Only tiles on
+// the left or right image edge have any.
+template <typename S>
+__device__ __forceinline__ void replicate_in_place(const TileInfo& t, int ic, int rm, float* in) {
+  const int cm = (ic - kTX) / 2;
+  const int IR = S::ROWS + 2 * rm;
+  const int x0 = t.tx0 - cm;
+  const int clo = t.cs - x0, chi = t.ce - 1 - x0;
+  const int nl = clo, nr = ic - 1 - chi, per = nl + nr;
+  if (per == 0) return;
+  for (int i = threadIdx.x; i < IR * per; i += S::THREADS) {
+    const int row = i / per, c = i - row * per;
+    float* r = in + (size_t)row * ic;
+    if (c < nl) r[c] = r[clo];
+    else r[chi + 1 + (c - nl)] = r[chi];
+  }
+}
+
 // ------------------------------------------------ separable filters
-// y pass on column pairs: tmp rows ty0-2 .. ty0+33, columns from
+// y pass on column pairs: tmp rows ty0-2 .. ty0+TY+1, columns from
 // x = tx0 - C (C = 2 + R rounded up to even) to tx0 + 128 + C.
-template <int R, int ic>
+template <typename S, int R, int ic>
 __device__ __forceinline__ void vpass(const float* taps, const float* in, int rm, float* tmp) {
+  constexpr int kSV = S::SV;
   constexpr int C = (2 + R + 1) & ~1;
   constexpr int kPairs = (kTX + 2 * C) / 2;
-  constexpr int kStrips = kRows / kSV;
+  constexpr int kStrips = S::ROWS / kSV;
   constexpr int cm = (ic - kTX) / 2;
   constexpr int col_off = cm - C;  // in-column of tmp column 0
   float2 g[R + 1];
 #pragma unroll
   for (int j = 0; j <= R; ++j) g[j] = f2(taps[j], taps[j]);
-  for (int item = threadIdx.x; item < kPairs * kStrips; item += kDetThreads) {
+  for (int item = threadIdx.x; item < kPairs * kStrips; item += S::THREADS) {
     const int s = item / kPairs;
     const int p = item - s * kPairs;
     const int r0 = s * kSV;
@@ -263,8 +299,9 @@ __device__ __forceinline__ void vpass(const float* taps, const float* in, int rm
 }
 
 // x pass on row pairs: gs[yp][c] (c <-> x = tx0 - 2 + c) from tmp
-template <int R, int ic>
+template <typename S, int R, int ic>
 __device__ __forceinline__ void hpass(const float* taps, const float* tmp, float* gs) {
+  constexpr int kSH = S::SH, kRP = S::RP;
   constexpr int C = (2 + R + 1) & ~1;
   constexpr int kNS = kGC / kSH;
   constexpr int kOff = C - 2 - R;   // tmp column of output column 0's first tap (0 or 1)
@@ -272,7 +309,7 @@ __device__ __forceinline__ void hpass(const float* taps, const float* tmp, float
   float2 g[R + 1];
 #pragma unroll
   for (int j = 0; j <= R; ++j) g[j] = f2(taps[j], taps[j]);
-  for (int item = threadIdx.x; item < kRP * kNS; item += kDetThreads) {
+  for (int item = threadIdx.x; item < kRP * kNS; item += S::THREADS) {
     const int yp = item / kNS;
     const int c0 = (item - yp * kNS) * kSH;
     const float2* t = reinterpret_cast<const float2*>(tmp) + (size_t)yp * ic + c0 + kOff;
@@ -334,13 +371,13 @@ __device__ __forceinline__ void hpass(const float* taps, const float* tmp, float
       break;                                                                                             \
   }
 
-template <int ic>
+template <typename S, int ic>
 __device__ void vpass_dispatch(int R, const float* taps, const float* in, int rm, float* tmp) {
-  CDVS_RADIUS_SWITCH(R, if constexpr (2 + r <= (ic - kTX) / 2) vpass<r, ic>(taps, in, rm, tmp))
+  CDVS_RADIUS_SWITCH(R, if constexpr (2 + r <= (ic - kTX) / 2) vpass<S, r, ic>(taps, in, rm, tmp))
 }
-template <int ic>
+template <typename S, int ic>
 __device__ void hpass_dispatch(int R, const float* taps, const float* tmp, float* gs) {
-  CDVS_RADIUS_SWITCH(R, if constexpr (2 + r <= (ic - kTX) / 2) hpass<r, ic>(taps, tmp, gs))
+  CDVS_RADIUS_SWITCH(R, if constexpr (2 + r <= (ic - kTX) / 2) hpass<S, r, ic>(taps, tmp, gs))
 }
 
 // gs element (row r, col c) of the row-pair layout
@@ -349,21 +386,23 @@ __device__ __forceinline__ float& gat(float* gs, int r, int c) { return gs[((r >
 // Clamp-to-edge for the Laplacian: the column and row just outside the
 // image take the value of the nearest image pixel, so the stencil below
 // needs no border cases (the Laplacian is only used at image pixels).
+template <typename S>
 __device__ __forceinline__ void replicate_borders(float* gs, int W, int H, int tx0, int ty0) {
+  constexpr int kRows = S::ROWS;
   const int cl = 1 - tx0;          // gs column of x = -1 (valid when tx0 == 0)
   const int cr = W - tx0 + kHalo;  // gs column of x = W
   const int rt = 1 - ty0, rb = H - ty0 + kHalo;
   const bool left = tx0 == 0, right = cr < kGC, top = ty0 == 0, bottom = rb < kRows;
   if (!(left || right || top || bottom)) return;  // uniform over the CTA
   if (left || right) {
-    for (int r = threadIdx.x; r < kRows; r += kDetThreads) {
+    for (int r = threadIdx.x; r < kRows; r += S::THREADS) {
       if (left) gat(gs, r, cl) = gat(gs, r, cl + 1);
       if (right) gat(gs, r, cr) = gat(gs, r, cr - 1);
     }
     __syncthreads();
   }
   if (top || bottom) {
-    for (int c = threadIdx.x; c < kGC; c += kDetThreads) {
+    for (int c = threadIdx.x; c < kGC; c += S::THREADS) {
       if (top) gat(gs, rt, c) = gat(gs, rt + 1, c);
       if (bottom) gat(gs, rb, c) = gat(gs, rb - 1, c);
     }
@@ -374,12 +413,14 @@ __device__ __forceinline__ void replicate_borders(float* gs, int W, int H, int t
 // L_{o,k} = s_k^2 * (left + right + up + down - 4 centre) on row pairs; each
 // thread walks one column down kRP / kLG row pairs with a sliding window.
 // (The first and last tile rows of the band get a clamped, unused value.)
+template <typename S>
 __device__ __forceinline__ void laplacian(const float* gs, float s2k, float* L) {
+  constexpr int kRP = S::RP, kLG = S::LG;
   constexpr int kPer = kRP / kLG;
   const float2 s2 = f2(s2k, s2k), m4 = f2(-4.0f, -4.0f);
   const float2* g = reinterpret_cast<const float2*>(gs);
   float2* out = reinterpret_cast<float2*>(L);
-  for (int item = threadIdx.x; item < kLC * kLG; item += kDetThreads) {
+  for (int item = threadIdx.x; item < kLC * kLG; item += S::THREADS) {
     const int grp = item / kLC;
     const int c = item - grp * kLC;  // L column c <-> gs column c + 1
     const int yp0 = grp * kPer;
@@ -410,11 +451,11 @@ __device__ __forceinline__ void store1(__half* d, float v) { *d = __float2half_r
 // Tile interior of G_{o,k} -> level storage.  Each thread takes 2 columns of a
 // row pair (one 16-byte shared load) and writes 2 x 2 values; the row pitch is
 // a multiple of 8 elements, so x + 1 < pitch always holds.
-template <typename StoreT>
+template <typename S, typename StoreT>
 __device__ __forceinline__ void store_level(const float* gs, StoreT* dst, int lpitch, int W, int H, int tx0,
                                             int ty0) {
   constexpr int kQ = kTX / 2;
-  for (int i = threadIdx.x; i < (kTY / 2) * kQ; i += kDetThreads) {
+  for (int i = threadIdx.x; i < (S::TY / 2) * kQ; i += S::THREADS) {
     const int m = i / kQ;            // tile rows 2m, 2m+1 = gs row pair m + 1
     const int c = (i - m * kQ) * 2;  // tile columns c, c+1 = gs columns c+2, c+3
     const int x = tx0 + c, y = ty0 + 2 * m;
@@ -429,11 +470,11 @@ __device__ __forceinline__ void store_level(const float* gs, StoreT* dst, int lp
 // tile, written transposed (to [j][i]) when the next octave is stored in the
 // other orientation.  Consecutive threads write consecutive elements of a
 // stored row either way (16 of a transposed row: 64 bytes).
-template <typename StoreT>
+template <typename S, typename StoreT>
 __device__ __forceinline__ void store_decimated(const float* gs, StoreT* dst, int lpitch1, int W, int H,
                                                 int tx0, int ty0, int dtr) {
-  constexpr int kHX = kTX / 2, kHY = kTY / 2;
-  for (int i = threadIdx.x; i < kHX * kHY; i += kDetThreads) {
+  constexpr int kHX = kTX / 2, kHY = S::TY / 2;
+  for (int i = threadIdx.x; i < kHX * kHY; i += S::THREADS) {
     const int r = dtr ? i % kHY : i / kHX;
     const int c = dtr ? i / kHY : i % kHX;
     const int y = ty0 + 2 * r, x = tx0 + 2 * c;
@@ -502,8 +543,10 @@ __device__ __forceinline__ void cubic_extremum2(const DetectArgs& a, const float
 
 // 8-neighbour test at the centre's t* and refinement (Alg. 1 stage B) for
 // a pixel that passed phase 1 (phase 2).
+template <typename S>
 __device__ __forceinline__ bool refine_pixel(const DetectArgs& a, const float* Ls, int ly, int lx, int bt,
                                              float btv, int x, int y, Found& f) {
+  constexpr int kRP = S::RP;
   // weights of the K samples in p(t*): w_k = sum_i B[i][k] t*^i
   float w[kScales];
 #pragma unroll
@@ -580,35 +623,46 @@ struct TileShared {
   TileInfo info[3];
 };
 
+// Whether a variant copies FP32 input straight into its FP32 tile: the
+// 128 x 16 variants do (their shared memory then fits two CTAs per SM).
+template <typename S, typename InT>
+constexpr bool kDirect = S::TY == 16 && std::is_same<InT, float>::value;
+
 // Masked: the first octave under a block proposal (per-tile modes and block
-// masks); the plain detector compiles without any of it.
-template <typename InT, typename StoreT, int ic, bool Masked>
-__global__ void __launch_bounds__(kDetThreads, 1)
+// masks; 128 x 32 tiles only); the plain detector compiles without any of it.
+template <typename S, typename InT, typename StoreT, int ic, bool Masked>
+__global__ void __launch_bounds__(S::THREADS, S::MINB)
     detect_kernel(const __grid_constant__ DetectArgs a, int rm, int n_tiles) {
+  static_assert(!Masked || S::TY == kTY, "block proposals are laid out on 128 x 32 tiles");
+  constexpr bool Direct = kDirect<S, InT>;
+  constexpr int kRows = S::ROWS, kRP = S::RP, kWarps = S::WARPS, kThreads = S::THREADS;
   extern __shared__ float4 smem4[];
   __shared__ TileShared sh;
   const int IR = kRows + 2 * rm;
-  const size_t raw_floats = ((size_t)IR * ic * sizeof(InT) + 15) / 16 * 4;
+  const size_t raw_floats = Direct ? 0 : ((size_t)IR * ic * sizeof(InT) + 15) / 16 * 4;
   InT* raw = reinterpret_cast<InT*>(smem4);
   float* in = reinterpret_cast<float*>(smem4) + raw_floats;
   float* tmp = in + (size_t)IR * ic;
   float* gs = tmp + kRows * ic;
   float* Ls = gs + kRows * kGC;
   int* prefix = reinterpret_cast<int*>(Ls + kScales * kRows * kLC);
+  // where the next tile's rows land: the staging buffer, or (FP32 input of
+  // the direct variants) the FP32 tile itself
+  InT* land = Direct ? reinterpret_cast<InT*>(in) : raw;
   const int o = a.octave;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-  for (int i = threadIdx.x; i <= a.n_images; i += kDetThreads) prefix[i] = a.tile_prefix[i] - a.tile_base;
+  for (int i = threadIdx.x; i <= a.n_images; i += kThreads) prefix[i] = a.tile_prefix[i] - a.tile_base;
   __syncthreads();
 
   int b = blockIdx.x;
   if (b >= n_tiles) return;
   if (threadIdx.x == 0) {
-    tile_info<InT>(a, prefix, b, n_tiles, ic, &sh.info[0]);
-    tile_info<InT>(a, prefix, b + gridDim.x, n_tiles, ic, &sh.info[1]);
+    tile_info<S, InT>(a, prefix, b, n_tiles, ic, &sh.info[0]);
+    tile_info<S, InT>(a, prefix, b + gridDim.x, n_tiles, ic, &sh.info[1]);
   }
   __syncthreads();
-  if (sh.info[0].bulk) issue_tile_copy<InT>(sh.info[0], ic, rm, raw);
+  if (sh.info[0].bulk) issue_tile_copy<S, InT>(sh.info[0], ic, rm, land);
 
   for (int slot = 0; b < n_tiles; b += gridDim.x, slot = slot == 2 ? 0 : slot + 1) {
     const TileInfo& cur = sh.info[slot];
@@ -618,15 +672,18 @@ __global__ void __launch_bounds__(kDetThreads, 1)
     if (cur.bulk) {  // uniform
       cp_async_wait_all();
       __syncthreads();
-      convert_raw<InT>(raw, cur, ic, rm, in);
+      if constexpr (Direct) replicate_in_place<S>(cur, ic, rm, in);
+      else convert_raw<S, InT>(raw, cur, ic, rm, in);
     } else {
-      load_tile_direct<InT>(cur, ic, rm, in);
+      load_tile_direct<S, InT>(cur, ic, rm, in);
     }
     if (threadIdx.x == 0) sh.n_pending = 0;
     __syncthreads();
     // ---- next tile's input on its way while this one is processed (raw is
-    // free: every thread is past convert_raw)
-    if (nxt.bulk) issue_tile_copy<InT>(nxt, ic, rm, raw);
+    // free: every thread is past convert_raw); the direct variants wait for
+    // the last y pass to be done with `in`
+    if constexpr (!Direct)
+      if (nxt.bulk) issue_tile_copy<S, InT>(nxt, ic, rm, raw);
 
     const int W = cur.W, H = cur.H, lpitch = cur.lpitch, tx0 = cur.tx0, ty0 = cur.ty0, img = cur.img;
     const long long dec_off = cur.dec_off;
@@ -642,43 +699,51 @@ __global__ void __launch_bounds__(kDetThreads, 1)
 
     // ---- levels: the y pass of level k+1 shares a phase with the stores and
     // the Laplacian of level k
-    vpass_dispatch<ic>(a.radius[k0], a.taps[k0], in, rm, tmp);
+    vpass_dispatch<S, ic>(a.radius[k0], a.taps[k0], in, rm, tmp);
     __syncthreads();
-    hpass_dispatch<ic>(a.radius[k0], a.taps[k0], tmp, gs);
+    if constexpr (Direct)
+      if (k0 == kScales - 1 && nxt.bulk) issue_tile_copy<S, InT>(nxt, ic, rm, land);
+    hpass_dispatch<S, ic>(a.radius[k0], a.taps[k0], tmp, gs);
     __syncthreads();
     for (int k = k0; k < kScales; ++k) {
-      replicate_borders(gs, W, H, tx0, ty0);
-      if (k > 0 || a.write_level0) store_level<StoreT>(gs, lev + k * lstride, lpitch, W, H, tx0, ty0);
+      replicate_borders<S>(gs, W, H, tx0, ty0);
+      if (k > 0 || a.write_level0) store_level<S, StoreT>(gs, lev + k * lstride, lpitch, W, H, tx0, ty0);
       if (k == kScales - 1 && dec_off >= 0)
-        store_decimated<StoreT>(gs, reinterpret_cast<StoreT*>(a.levels) + dec_off, dec_pitch, W, H, tx0, ty0,
-                                cur.dec_tr);
-      if (!Masked || mode == kModeDetect) laplacian(gs, a.s2[k], Ls + (size_t)k * kRP * kLC * 2);
-      if (k + 1 < kScales) vpass_dispatch<ic>(a.radius[k + 1], a.taps[k + 1], in, rm, tmp);
+        store_decimated<S, StoreT>(gs, reinterpret_cast<StoreT*>(a.levels) + dec_off, dec_pitch, W, H, tx0, ty0,
+                                   cur.dec_tr);
+      if (!Masked || mode == kModeDetect) laplacian<S>(gs, a.s2[k], Ls + (size_t)k * kRP * kLC * 2);
+      if (k + 1 < kScales) vpass_dispatch<S, ic>(a.radius[k + 1], a.taps[k + 1], in, rm, tmp);
       __syncthreads();
       if (k + 1 < kScales) {
-        hpass_dispatch<ic>(a.radius[k + 1], a.taps[k + 1], tmp, gs);
+        // after the last y pass `in` is free: the direct variants start the
+        // next tile's copies into it now
+        if constexpr (Direct)
+          if (k + 1 == kScales - 1 && nxt.bulk) issue_tile_copy<S, InT>(nxt, ic, rm, land);
+        hpass_dispatch<S, ic>(a.radius[k + 1], a.taps[k + 1], tmp, gs);
         __syncthreads();
       }
     }
 
     if (Masked && mode != kModeDetect) {
-      if (warp == kWarps - 1 && lane == 0) tile_info<InT>(a, prefix, b + 2 * gridDim.x, n_tiles, ic, after);
+      if (warp == kWarps - 1 && lane == 0) tile_info<S, InT>(a, prefix, b + 2 * gridDim.x, n_tiles, ic, after);
       __syncthreads();  // gs and `in` are rewritten by the next tile
       continue;
     }
 
     // ---- phase 1, per pixel pair (tile rows 2m, 2m+1 are L row pair m + 1):
     // cubic coefficients of Eq. 3 on packed pairs, then the admissible
-    // extremum in scale; survivors are compacted into `in` and `tmp`
-    Pending* pend = reinterpret_cast<Pending*>(in);
-    constexpr int kIt = (kTX * kTY / 2) / kDetThreads;
+    // extremum in scale; survivors are compacted into shared memory that the
+    // level passes are done with (`in`, or for the direct variants, whose
+    // `in` is receiving the next tile, `tmp` and `gs`)
+    Pending* pend = reinterpret_cast<Pending*>(Direct ? tmp : in);
+    constexpr int kIt = (kTX * S::TY / 2) / kThreads;
     int bt[kIt][2];
     float tb[kIt][2];
     // all pixel pairs of the thread first (independent work in flight), then
     // the compaction
 #pragma unroll
     for (int it = 0; it < kIt; ++it) {
-      const int idx = it * kDetThreads + threadIdx.x;
+      const int idx = it * kThreads + threadIdx.x;
       const int m = idx / kTX, lx = idx - (idx / kTX) * kTX;
       float2 Lk[kScales];
 #pragma unroll
@@ -699,7 +764,7 @@ __global__ void __launch_bounds__(kDetThreads, 1)
     }
 #pragma unroll
     for (int it = 0; it < kIt; ++it) {
-      const int idx = it * kDetThreads + threadIdx.x;
+      const int idx = it * kThreads + threadIdx.x;
       const int m = idx / kTX, lx = idx - (idx / kTX) * kTX;
       const unsigned m0 = __ballot_sync(0xffffffffu, bt[it][0] != 0);
       const unsigned m1 = __ballot_sync(0xffffffffu, bt[it][1] != 0);
@@ -729,15 +794,15 @@ __global__ void __launch_bounds__(kDetThreads, 1)
     // matter: the selection orders candidates by a total order of their own.
     // Meanwhile the last warp's lane 0 looks up the tile after next.
     const int np = sh.n_pending;
-    if (warp == kWarps - 1 && lane == 0) tile_info<InT>(a, prefix, b + 2 * gridDim.x, n_tiles, ic, after);
-    for (int i0 = warp * 32; i0 < np; i0 += kDetThreads) {
+    if (warp == kWarps - 1 && lane == 0) tile_info<S, InT>(a, prefix, b + 2 * gridDim.x, n_tiles, ic, after);
+    for (int i0 = warp * 32; i0 < np; i0 += kThreads) {
       const int i = i0 + lane;
       Found f;
       bool found = false;
       if (i < np) {
         const Pending e = pend[i];
         const int ly = e.code >> 16, lx = (e.code >> 1) & 0x7fff;
-        found = refine_pixel(a, Ls, ly, lx, (e.code & 1) ? 1 : -1, e.t, tx0 + lx, ty0 + ly, f);
+        found = refine_pixel<S>(a, Ls, ly, lx, (e.code & 1) ? 1 : -1, e.t, tx0 + lx, ty0 + ly, f);
       }
       const unsigned msk = __ballot_sync(0xffffffffu, found);
       if (msk == 0) continue;
@@ -764,8 +829,8 @@ __global__ void __launch_bounds__(kDetThreads, 1)
         }
       }
     }
-    // the pending list lives in `in`, rewritten by the next tile; the tile
-    // after next is described in `after`
+    // the pending list lives in `in` (or `tmp`), rewritten by the next tile;
+    // the tile after next is described in `after`
     __syncthreads();
   }
   cp_async_wait_all();  // nothing may still be landing in shared memory at exit
@@ -776,27 +841,63 @@ __global__ void __launch_bounds__(kDetThreads, 1)
 // The input tile pitch: 128 + 2 Cm columns for radii up to 14 and up to 24.
 static int tile_pitch(int max_radius) { return max_radius <= 14 ? 160 : 184; }
 
+template <typename S>
 static size_t detect_smem(int max_radius, int in_size, int n_images) {
   const int ic = tile_pitch(max_radius);
-  const size_t rows = (size_t)(kRows + 2 * max_radius);
-  const size_t raw = (rows * ic * in_size + 15) / 16 * 16;
-  return raw + sizeof(float) * (rows * ic + (size_t)kRows * ic + (size_t)kRows * kGC +
-                                (size_t)kScales * kRows * kLC) +
+  const size_t rows = (size_t)(S::ROWS + 2 * max_radius);
+  const bool direct = S::TY == 16 && in_size == 4;
+  const size_t raw = direct ? 0 : (rows * ic * in_size + 15) / 16 * 16;
+  return raw + sizeof(float) * (rows * ic + (size_t)S::ROWS * ic + (size_t)S::ROWS * kGC +
+                                (size_t)kScales * S::ROWS * kLC) +
          sizeof(int) * (size_t)(n_images + 1);
 }
 
-// the launch of one variant (shared memory attribute, grid of persistent CTAs)
-#define CDVS_LAUNCH(IN, ST, IC, M)                                                                                  \
-  do {                                                                                                              \
-    const size_t smem = detect_smem(max_radius, sizeof(IN), a.n_images);                                           \
-    e = cudaFuncSetAttribute(detect_kernel<IN, ST, IC, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-    if (e != cudaSuccess) return e;                                                                                 \
-    detect_kernel<IN, ST, IC, M><<<grid, kDetThreads, smem, s>>>(a, max_radius, n_tiles);                           \
-  } while (0)
-#define CDVS_LAUNCH_IC(IN, ST, M)                                   \
-  do {                                                              \
-    if (tile_pitch(max_radius) == 160) CDVS_LAUNCH(IN, ST, 160, M); \
-    else CDVS_LAUNCH(IN, ST, 184, M);                               \
-  } while (0)
+// The launch of one variant: shared memory attribute, and a grid of
+// persistent CTAs, as many per SM as fit (at most the tile count).
+template <typename S, typename IN, typename ST, int IC, bool M>
+static cudaError_t launch_variant(const DetectArgs& a, int n_tiles, int max_radius, int n_sms, cudaStream_t s) {
+  const size_t smem = detect_smem<S>(max_radius, sizeof(IN), a.n_images);
+  auto kern = detect_kernel<S, IN, ST, IC, M>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess || n_tiles <= 0) return e;  // no tiles: only the kernel's attributes are set up
+  int per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, S::THREADS, smem)) != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int grid = n_tiles < n_sms * per_sm ? n_tiles : n_sms * per_sm;
+  kern<<<grid, S::THREADS, smem, s>>>(a, max_radius, n_tiles);
+  return cudaGetLastError();
+}
+
+// One variant for the input / storage types of an octave and the tile pitch
+// of its radii (radii above 14, from a larger sigma0 than the default, only
+// in variant A).
+template <typename S, bool M>
+static cudaError_t launch_typed(const DetectArgs& a, int n_tiles, int max_radius, int storage, int n_sms,
+                                cudaStream_t s) {
+  constexpr bool kWide = std::is_same<S, ShapeA>::value;
+  const bool wide = tile_pitch(max_radius) != 160;
+  if constexpr (kWide) {
+    if (wide) {
+      if (storage == CDVS_STORAGE_FP16) {
+        if (a.octave == 0) return launch_variant<S, uint8_t, __half, 184, M>(a, n_tiles, max_radius, n_sms, s);
+        if constexpr (M) return cudaErrorInvalidValue;
+        else return launch_variant<S, __half, __half, 184, M>(a, n_tiles, max_radius, n_sms, s);
+      }
+      if (a.octave == 0) return launch_variant<S, uint8_t, float, 184, M>(a, n_tiles, max_radius, n_sms, s);
+      if constexpr (M) return cudaErrorInvalidValue;
+      else return launch_variant<S, float, float, 184, M>(a, n_tiles, max_radius, n_sms, s);
+    }
+  } else {
+    if (wide) return cudaErrorInvalidValue;
+  }
+  if (storage == CDVS_STORAGE_FP16) {
+    if (a.octave == 0) return launch_variant<S, uint8_t, __half, 160, M>(a, n_tiles, max_radius, n_sms, s);
+    if constexpr (M) return cudaErrorInvalidValue;
+    else return launch_variant<S, __half, __half, 160, M>(a, n_tiles, max_radius, n_sms, s);
+  }
+  if (a.octave == 0) return launch_variant<S, uint8_t, float, 160, M>(a, n_tiles, max_radius, n_sms, s);
+  if constexpr (M) return cudaErrorInvalidValue;
+  else return launch_variant<S, float, float, 160, M>(a, n_tiles, max_radius, n_sms, s);
+}
 
 }  // namespace cdvs

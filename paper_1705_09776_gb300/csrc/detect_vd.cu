@@ -1,0 +1,11 @@
+// detect_vd.cu -- K1 launches of variant D: two 256-thread CTAs per SM on 128 x 16 tiles, y pass 10 rows per thread.
+// The kernel is in detect_kernel.cuh.
+#include "detect_kernel.cuh"
+
+namespace cdvs {
+
+cudaError_t launch_detect_d(const DetectArgs& a, int n_tiles, int max_radius, int storage, int n_sms, cudaStream_t s) {
+  return launch_typed<ShapeD, false>(a, n_tiles, max_radius, storage, n_sms, s);
+}
+
+}  // namespace cdvs

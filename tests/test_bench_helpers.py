@@ -38,19 +38,20 @@ def test_detect_counts_octave0_by_hand():
 
 
 def test_traffic_record_is_keyed_on_the_kernel_source(tmp_path, monkeypatch):
-    rec = {"dram_bytes_per_image_octave0": 4.6e6, "kernel_sha256": bench.kernel_sha()}
+    rec = {"variants": {"2": {"dram_bytes_per_image_octave0": 4.6e6}}, "kernel_sha256": bench.kernel_sha()}
     f = tmp_path / "traffic.json"
     f.write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "TRAFFIC_FILE", str(f))
-    assert bench.load_traffic()["dram_bytes_per_image_octave0"] == 4.6e6
+    assert bench.load_traffic(2)["dram_bytes_per_image_octave0"] == 4.6e6
+    assert bench.load_traffic(1) is None
     rec["kernel_sha256"] = "0" * 64  # taken on another kernel: no traffic figure
     f.write_text(json.dumps(rec))
-    assert bench.load_traffic() is None
+    assert bench.load_traffic(2) is None
 
 
 def test_committed_traffic_record_matches_the_sources():
-    """The committed ncu figure was taken on the K1 sources in the tree."""
-    assert bench.load_traffic() is not None
+    """The committed ncu figures were taken on the K1 sources in the tree."""
+    assert all(bench.load_traffic(v) is not None for v in range(4))
 
 
 def test_tile_modes_rule():

@@ -162,3 +162,87 @@ def test_highres_full_size_runs_and_is_deterministic(env):
     assert (a[2] <= 2000 * p["max_orientations"][0]).all() and (a[2] > 1000).all()
     assert np.array_equal(a[0].view(np.uint8), b[0].view(np.uint8)) and np.array_equal(a[1], b[1])
     assert len(np.unique(a[0][a[0]["image"] == 0]["parent_id"])) <= 2000
+
+
+# ------------------------------------------------------------------ K1 work shapes
+
+def _variant_run(ctx, cd, imgs, p):
+    out = []
+    for v in range(4):
+        ctx.set_detect_variant(v)
+        k, d, c, st = ctx.extract(imgs, p)
+        assert st == cd.CDVS_OK
+        lv = ctx.scale_space(imgs[0], p)
+        cand, cc, _ = ctx.candidates(imgs, p)
+        out.append((k, d, c, lv, cand))
+    ctx.set_detect_variant(-1)
+    return out
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_detect_variants_are_bit_identical(storage):
+    """K1's four work shapes (128 x 32 tiles with one 512-thread CTA per SM,
+    128 x 16 tiles with two 256-thread CTAs per SM, two y-pass splits each)
+    compute the same arithmetic: levels, candidate sets, records and
+    descriptors are identical bit for bit, on ragged sizes and on an image
+    whose later octaves are stored transposed."""
+    from paper_1705_09776_gb300 import cdvs as cd
+    ctx = cd.Context(0)
+    p = cd.params(storage=cd.CDVS_STORAGE_FP16 if storage == "fp16" else cd.CDVS_STORAGE_FP32)
+    imgs = [synth.blob_image(synth.image_seed(51, i), w, h, n_blobs=max(4, w * h // 1500))
+            for i, (w, h) in enumerate([(640, 480), (641, 481), (97, 75), (300, 700), (16, 16), (1000, 37)])]
+    runs = _variant_run(ctx, cd, imgs, p)
+    key = lambda r: sorted(zip(r["image"], r["octave"], r["x"].view(np.int32), r["y"].view(np.int32),
+                               r["sigma"].view(np.int32), r["response"].view(np.int32)))
+    k0, d0, c0, lv0, cand0 = runs[0]
+    assert len(k0) > 100
+    for v, (k, d, c, lv, cand) in enumerate(runs[1:], 1):
+        assert np.array_equal(c, c0), v
+        assert np.array_equal(k.view(np.uint8), k0.view(np.uint8)), v
+        assert np.array_equal(d, d0), v
+        for o in range(len(lv0)):
+            for j in range(4):
+                assert np.array_equal(lv[o][j], lv0[o][j]), (v, o, j)
+        assert key(cand) == key(cand0), v
+    ctx.close()
+
+
+def test_detect_tuner_measures_every_variant_and_keeps_results():
+    """With the default (tuned) work shape, device-resident calls measure
+    each variant of each octave class once, then choose; every call's records
+    equal the fixed shape's byte for byte."""
+    import torch
+    from paper_1705_09776_gb300 import cdvs as cd
+    imgs = np.stack([synth.blob_image(synth.image_seed(52, i)) for i in range(8)])
+    n, H, W = imgs.shape
+    ref = cd.Context(0)
+    ref.set_detect_variant(0)
+    rk, rd, rc, _ = ref.extract(list(imgs))
+    ref.close()
+    ctx = cd.Context(0)
+    dev = torch.from_numpy(imgs).cuda()
+    cap = n * 300 * 4
+    kp = torch.zeros(cap * cd.KEYPOINT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    desc = torch.zeros(cap, 128, dtype=torch.float32, device="cuda")
+    cnt = torch.zeros(n, dtype=torch.int32, device="cuda")
+    sizes = np.array([(W, H, W)] * n, cd.IMAGE_DESC_DTYPE)
+    ptrs = [dev.data_ptr() + i * H * W for i in range(n)]
+    used = set()
+    for call in range(12):
+        st = ctx.extract_raw(n, ptrs, sizes, cd.params(), kp, desc, cap, cnt,
+                             cd.CDVS_INPUT_DEVICE | cd.CDVS_OUTPUT_DEVICE, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        assert st == cd.CDVS_OK
+        tot = int(cnt.sum().item())
+        assert np.array_equal(cnt.cpu().numpy(), rc)
+        assert np.array_equal(kp.cpu().numpy()[:tot * cd.KEYPOINT_DTYPE.itemsize], rk.view(np.uint8))
+        assert np.array_equal(desc.cpu().numpy()[:tot], rd)
+        info = ctx.detect_tuning()
+        used.add(tuple(info["last_call_variants"][:4]))
+    info = ctx.detect_tuning()
+    assert info["mode"] == -1 and len(info["classes"]) == 2
+    for cl in info["classes"]:
+        assert cl["tuned"], info
+        assert all(t is not None and t > 0 for t in cl["us_per_tile"]), info
+    assert len(used) >= 4          # every variant ran
+    ctx.close()
