@@ -632,7 +632,9 @@ cdvs_status run_detect(cdvs_ctx* c, int n, const cdvs_params& p, int max_oct, in
     a.block_mask = o == 0 ? block_mask : nullptr;
     int maxr = 0;
     for (int k = 0; k < kScales; ++k) {
-      a.radius[k] = gauss_taps(tau_of(p, o, k), a.taps[k]);
+      float t1[kMaxRadius + 1];
+      a.radius[k] = gauss_taps(tau_of(p, o, k), t1);
+      for (int j = 0; j <= std::max(a.radius[k], 0); ++j) a.taps[k][j] = make_float2(t1[j], t1[j]);
       maxr = std::max(maxr, a.radius[k]);
     }
     const int* prefix = c->h_prefix.data() + (size_t)o * (n + 1);

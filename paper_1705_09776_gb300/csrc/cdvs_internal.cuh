@@ -78,7 +78,8 @@ struct DetectArgs {
   int cand_cap;
   int* status;
   int radius[kScales];
-  float taps[kScales][kMaxRadius + 1];   // one side of each symmetric level filter
+  float2 taps[kScales][kMaxRadius + 1];  // one side of each symmetric level filter, each tap as a pair
+                                         // {g, g} (the operand of a packed FP32 multiply-add)
   float s2[kScales];                     // s_k^2: LoG scale normalisation
   float B[4][kScales];                   // cubic fit in t = sigma - tc: a_i = sum_k B[i][k] L_k
   float tc;                              // centre of the fitting variable

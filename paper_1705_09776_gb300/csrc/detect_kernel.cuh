@@ -261,7 +261,7 @@ __device__ __forceinline__ void replicate_in_place(const TileInfo& t, int ic, in
 // y pass on column pairs: tmp rows ty0-2 .. ty0+TY+1, columns from
 // x = tx0 - C (C = 2 + R rounded up to even) to tx0 + 128 + C.
 template <typename S, int R, int ic>
-__device__ __forceinline__ void vpass(const float* taps, const float* in, int rm, float* tmp) {
+__device__ __forceinline__ void vpass(const float2* taps, const float* in, int rm, float* tmp) {
   constexpr int kSV = S::SV;
   constexpr int C = (2 + R + 1) & ~1;
   constexpr int kPairs = (kTX + 2 * C) / 2;
@@ -270,7 +270,7 @@ __device__ __forceinline__ void vpass(const float* taps, const float* in, int rm
   constexpr int col_off = cm - C;  // in-column of tmp column 0
   float2 g[R + 1];
 #pragma unroll
-  for (int j = 0; j <= R; ++j) g[j] = f2(taps[j], taps[j]);
+  for (int j = 0; j <= R; ++j) g[j] = taps[j];
   for (int item = threadIdx.x; item < kPairs * kStrips; item += S::THREADS) {
     const int s = item / kPairs;
     const int p = item - s * kPairs;
@@ -300,7 +300,7 @@ __device__ __forceinline__ void vpass(const float* taps, const float* in, int rm
 
 // x pass on row pairs: gs[yp][c] (c <-> x = tx0 - 2 + c) from tmp
 template <typename S, int R, int ic>
-__device__ __forceinline__ void hpass(const float* taps, const float* tmp, float* gs) {
+__device__ __forceinline__ void hpass(const float2* taps, const float* tmp, float* gs) {
   constexpr int kSH = S::SH, kRP = S::RP;
   constexpr int C = (2 + R + 1) & ~1;
   constexpr int kNS = kGC / kSH;
@@ -308,7 +308,7 @@ __device__ __forceinline__ void hpass(const float* taps, const float* tmp, float
   constexpr int kIn = kSH + 2 * R;  // even
   float2 g[R + 1];
 #pragma unroll
-  for (int j = 0; j <= R; ++j) g[j] = f2(taps[j], taps[j]);
+  for (int j = 0; j <= R; ++j) g[j] = taps[j];
   for (int item = threadIdx.x; item < kRP * kNS; item += S::THREADS) {
     const int yp = item / kNS;
     const int c0 = (item - yp * kNS) * kSH;
@@ -372,11 +372,11 @@ __device__ __forceinline__ void hpass(const float* taps, const float* tmp, float
   }
 
 template <typename S, int ic>
-__device__ void vpass_dispatch(int R, const float* taps, const float* in, int rm, float* tmp) {
+__device__ void vpass_dispatch(int R, const float2* taps, const float* in, int rm, float* tmp) {
   CDVS_RADIUS_SWITCH(R, if constexpr (2 + r <= (ic - kTX) / 2) vpass<S, r, ic>(taps, in, rm, tmp))
 }
 template <typename S, int ic>
-__device__ void hpass_dispatch(int R, const float* taps, const float* tmp, float* gs) {
+__device__ void hpass_dispatch(int R, const float2* taps, const float* tmp, float* gs) {
   CDVS_RADIUS_SWITCH(R, if constexpr (2 + r <= (ic - kTX) / 2) hpass<S, r, ic>(taps, tmp, gs))
 }
 
@@ -628,6 +628,131 @@ struct TileShared {
 template <typename S, typename InT>
 constexpr bool kDirect = S::TY == 16 && std::is_same<InT, float>::value;
 
+// Whether a variant runs a tile's detection (phases 1 and 2) during the
+// next tile's first level passes: the 128 x 32 variants do.  The scale test
+// and the refinement then share phases with the next tile's input staging
+// and first y pass, so their latency-bound work overlaps the filters'
+// multiply-adds, and a tile costs two block barriers fewer.  The tile's L
+// levels stay in shared memory until the next tile's first Laplacian
+// overwrites them; the survivors list has a region of its own (so the
+// 184-column tiles of radii above 14, whose shared memory is full, do not).
+template <typename S, int ic>
+constexpr bool kDefer = S::TY == 32 && ic == 160;
+
+// What the detection of a tile needs to know about it.
+struct DetTile {
+  int tx0, ty0, W, H, img, tr;
+  unsigned bmask;
+};
+
+// ---- phase 1, per pixel pair (tile rows 2m, 2m+1 are L row pair m + 1):
+// cubic coefficients of Eq. 3 on packed pairs, then the admissible extremum
+// in scale; survivors are compacted into `pend` (count in *n_pending).
+template <typename S, bool Masked>
+__device__ __forceinline__ void detect_phase1(const DetectArgs& a, const float* Ls, const DetTile& t,
+                                              Pending* pend, int* n_pending) {
+  constexpr int kRP = S::RP, kThreads = S::THREADS;
+  constexpr int kIt = (kTX * S::TY / 2) / kThreads;
+  const int lane = threadIdx.x & 31;
+  int bt[kIt][2];
+  float tb[kIt][2];
+  // all pixel pairs of the thread first (independent work in flight), then
+  // the compaction
+#pragma unroll
+  for (int it = 0; it < kIt; ++it) {
+    const int idx = it * kThreads + threadIdx.x;
+    const int m = idx / kTX, lx = idx - (idx / kTX) * kTX;
+    float2 Lk[kScales];
+#pragma unroll
+    for (int k = 0; k < kScales; ++k) Lk[k] = reinterpret_cast<const float2*>(Ls)[(k * kRP + m + 1) * kLC + lx + 1];
+    float2 al2[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float2 s = f2(0.0f, 0.0f);
+#pragma unroll
+      for (int k = 0; k < kScales; ++k) s = fma2(f2(a.B[i][k], a.B[i][k]), Lk[k], s);
+      al2[i] = s;
+    }
+    const int x = t.tx0 + lx, y0 = t.ty0 + 2 * m;
+    // rows 2m, 2m + 1 lie in block row m / 8; a proposal may rule the block out
+    const bool inx =
+        x >= 1 && x < t.W - 1 && (!Masked || ((t.bmask >> ((m >> 3) * (kTX / 16) + (lx >> 4))) & 1u));
+    cubic_extremum2(a, al2, inx && y0 >= 1 && y0 < t.H - 1, inx && y0 + 1 < t.H - 1, bt[it], tb[it]);
+  }
+#pragma unroll
+  for (int it = 0; it < kIt; ++it) {
+    const int idx = it * kThreads + threadIdx.x;
+    const int m = idx / kTX, lx = idx - (idx / kTX) * kTX;
+    const unsigned m0 = __ballot_sync(0xffffffffu, bt[it][0] != 0);
+    const unsigned m1 = __ballot_sync(0xffffffffu, bt[it][1] != 0);
+    if (m0 | m1) {
+      int base = 0;
+      if (lane == 0) base = atomicAdd(n_pending, __popc(m0) + __popc(m1));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      const unsigned below = (1u << lane) - 1u;
+      if (bt[it][0] != 0) {
+        Pending e;
+        e.code = ((2 * m) << 16) | (lx << 1) | (bt[it][0] > 0 ? 1 : 0);
+        e.t = tb[it][0];
+        pend[base + __popc(m0 & below)] = e;
+      }
+      if (bt[it][1] != 0) {
+        Pending e;
+        e.code = ((2 * m + 1) << 16) | (lx << 1) | (bt[it][1] > 0 ? 1 : 0);
+        e.t = tb[it][1];
+        pend[base + __popc(m0) + __popc(m1 & below)] = e;
+      }
+    }
+  }
+}
+
+// ---- phase 2: neighbour test and refinement of the np survivors, densely;
+// one queue reservation per warp and round.  The queue order does not
+// matter: the selection orders candidates by a total order of its own.
+template <typename S>
+__device__ __forceinline__ void detect_phase2(const DetectArgs& a, const float* Ls, const DetTile& t,
+                                              const Pending* pend, int np) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i0 = warp * 32; i0 < np; i0 += S::THREADS) {
+    const int i = i0 + lane;
+    Found f;
+    bool found = false;
+    if (i < np) {
+      const Pending e = pend[i];
+      const int ly = e.code >> 16, lx = (e.code >> 1) & 0x7fff;
+      found = refine_pixel<S>(a, Ls, ly, lx, (e.code & 1) ? 1 : -1, e.t, t.tx0 + lx, t.ty0 + ly, f);
+    }
+    const unsigned msk = __ballot_sync(0xffffffffu, found);
+    if (msk == 0) continue;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(a.cand_count + t.img, __popc(msk));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (found) {
+      const int pos = base + __popc(msk & ((1u << lane) - 1u));
+      if (pos < a.cand_cap) {
+        Cand c;
+        const bool tr = t.tr;  // image frame
+        c.xo = tr ? f.yo : f.xo;
+        c.yo = tr ? f.xo : f.yo;
+        c.so = f.so;
+        c.resp = f.resp;
+        c.pss = f.pss;
+        c.ratio = f.ratio;
+        c.octave = (short)a.octave;
+        c.type = (short)f.type;
+        c.spare = 0;
+        a.cands[(size_t)t.img * a.cand_cap + pos] = c;
+      } else {
+        atomicOr(a.status, kStatusCandOverflow);
+      }
+    }
+  }
+}
+
+// Shared memory of the survivors list when it has a region of its own.
+template <typename S, int ic>
+constexpr size_t kPendBytes = kDefer<S, ic> ? sizeof(Pending) * kTX * S::TY : 0;
+
 // Masked: the first octave under a block proposal (per-tile modes and block
 // masks; 128 x 32 tiles only); the plain detector compiles without any of it.
 template <typename S, typename InT, typename StoreT, int ic, bool Masked>
@@ -635,6 +760,7 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB)
     detect_kernel(const __grid_constant__ DetectArgs a, int rm, int n_tiles) {
   static_assert(!Masked || S::TY == kTY, "block proposals are laid out on 128 x 32 tiles");
   constexpr bool Direct = kDirect<S, InT>;
+  constexpr bool Defer = kDefer<S, ic>;
   constexpr int kRows = S::ROWS, kRP = S::RP, kWarps = S::WARPS, kThreads = S::THREADS;
   extern __shared__ float4 smem4[];
   __shared__ TileShared sh;
@@ -645,14 +771,18 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB)
   float* tmp = in + (size_t)IR * ic;
   float* gs = tmp + kRows * ic;
   float* Ls = gs + kRows * kGC;
-  int* prefix = reinterpret_cast<int*>(Ls + kScales * kRows * kLC);
+  float* pend_region = Ls + kScales * kRows * kLC;
+  int* prefix = reinterpret_cast<int*>(pend_region + kPendBytes<S, ic> / sizeof(float));
+  // the survivors list: its own region (deferred detection), or `in` -- for
+  // the direct variants, whose `in` is receiving the next tile, `tmp` and `gs`
+  Pending* pend = reinterpret_cast<Pending*>(Defer ? pend_region : (Direct ? tmp : in));
   // where the next tile's rows land: the staging buffer, or (FP32 input of
   // the direct variants) the FP32 tile itself
   InT* land = Direct ? reinterpret_cast<InT*>(in) : raw;
-  const int o = a.octave;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
   for (int i = threadIdx.x; i <= a.n_images; i += kThreads) prefix[i] = a.tile_prefix[i] - a.tile_base;
+  if (threadIdx.x == 0) sh.n_pending = 0;
   __syncthreads();
 
   int b = blockIdx.x;
@@ -664,11 +794,17 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB)
   __syncthreads();
   if (sh.info[0].bulk) issue_tile_copy<S, InT>(sh.info[0], ic, rm, land);
 
+  DetTile prev;        // the tile whose detection is deferred to this one
+  bool prev_det = false;
+  prev.tx0 = prev.ty0 = prev.W = prev.H = prev.img = prev.tr = 0;
+  prev.bmask = 0u;
+
   for (int slot = 0; b < n_tiles; b += gridDim.x, slot = slot == 2 ? 0 : slot + 1) {
     const TileInfo& cur = sh.info[slot];
     const TileInfo& nxt = sh.info[slot == 2 ? 0 : slot + 1];
     TileInfo* after = &sh.info[slot == 0 ? 2 : slot - 1];
-    // ---- this tile's input into `in`
+    // ---- this tile's input into `in`, and (deferred) the scale test of
+    // the previous tile
     if (cur.bulk) {  // uniform
       cp_async_wait_all();
       __syncthreads();
@@ -677,7 +813,11 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB)
     } else {
       load_tile_direct<S, InT>(cur, ic, rm, in);
     }
-    if (threadIdx.x == 0) sh.n_pending = 0;
+    if constexpr (Defer) {
+      if (prev_det) detect_phase1<S, Masked>(a, Ls, prev, pend, &sh.n_pending);
+    } else {
+      if (threadIdx.x == 0) sh.n_pending = 0;
+    }
     __syncthreads();
     // ---- next tile's input on its way while this one is processed (raw is
     // free: every thread is past convert_raw); the direct variants wait for
@@ -685,7 +825,7 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB)
     if constexpr (!Direct)
       if (nxt.bulk) issue_tile_copy<S, InT>(nxt, ic, rm, raw);
 
-    const int W = cur.W, H = cur.H, lpitch = cur.lpitch, tx0 = cur.tx0, ty0 = cur.ty0, img = cur.img;
+    const int W = cur.W, H = cur.H, lpitch = cur.lpitch, tx0 = cur.tx0, ty0 = cur.ty0;
     const long long dec_off = cur.dec_off;
     const int dec_pitch = cur.dec_pitch;
     StoreT* lev = reinterpret_cast<StoreT*>(a.levels) + cur.level_off;
@@ -698,9 +838,15 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB)
     const int k0 = Masked && mode == kModeLevel3 ? kScales - 1 : 0;
 
     // ---- levels: the y pass of level k+1 shares a phase with the stores and
-    // the Laplacian of level k
+    // the Laplacian of level k; (deferred) the previous tile's refinement
+    // shares the first y pass's phase -- its L levels are overwritten only by
+    // this tile's first Laplacian
     vpass_dispatch<S, ic>(a.radius[k0], a.taps[k0], in, rm, tmp);
+    if constexpr (Defer)
+      if (prev_det) detect_phase2<S>(a, Ls, prev, pend, sh.n_pending);
     __syncthreads();
+    if constexpr (Defer)
+      if (threadIdx.x == 0) sh.n_pending = 0;  // read by the refinement above, rewritten by the next scale test
     if constexpr (Direct)
       if (k0 == kScales - 1 && nxt.bulk) issue_tile_copy<S, InT>(nxt, ic, rm, land);
     hpass_dispatch<S, ic>(a.radius[k0], a.taps[k0], tmp, gs);
@@ -713,6 +859,9 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB)
                                    cur.dec_tr);
       if (!Masked || mode == kModeDetect) laplacian<S>(gs, a.s2[k], Ls + (size_t)k * kRP * kLC * 2);
       if (k + 1 < kScales) vpass_dispatch<S, ic>(a.radius[k + 1], a.taps[k + 1], in, rm, tmp);
+      // the tile after next is looked up by one lane while the others filter
+      if (k == k0 && warp == kWarps - 1 && lane == 0)
+        tile_info<S, InT>(a, prefix, b + 2 * gridDim.x, n_tiles, ic, after);
       __syncthreads();
       if (k + 1 < kScales) {
         // after the last y pass `in` is free: the direct variants start the
@@ -724,114 +873,36 @@ __global__ void __launch_bounds__(S::THREADS, S::MINB)
       }
     }
 
-    if (Masked && mode != kModeDetect) {
-      if (warp == kWarps - 1 && lane == 0) tile_info<S, InT>(a, prefix, b + 2 * gridDim.x, n_tiles, ic, after);
-      __syncthreads();  // gs and `in` are rewritten by the next tile
-      continue;
-    }
-
-    // ---- phase 1, per pixel pair (tile rows 2m, 2m+1 are L row pair m + 1):
-    // cubic coefficients of Eq. 3 on packed pairs, then the admissible
-    // extremum in scale; survivors are compacted into shared memory that the
-    // level passes are done with (`in`, or for the direct variants, whose
-    // `in` is receiving the next tile, `tmp` and `gs`)
-    Pending* pend = reinterpret_cast<Pending*>(Direct ? tmp : in);
-    constexpr int kIt = (kTX * S::TY / 2) / kThreads;
-    int bt[kIt][2];
-    float tb[kIt][2];
-    // all pixel pairs of the thread first (independent work in flight), then
-    // the compaction
-#pragma unroll
-    for (int it = 0; it < kIt; ++it) {
-      const int idx = it * kThreads + threadIdx.x;
-      const int m = idx / kTX, lx = idx - (idx / kTX) * kTX;
-      float2 Lk[kScales];
-#pragma unroll
-      for (int k = 0; k < kScales; ++k)
-        Lk[k] = reinterpret_cast<const float2*>(Ls)[(k * kRP + m + 1) * kLC + lx + 1];
-      float2 al2[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        float2 s = f2(0.0f, 0.0f);
-#pragma unroll
-        for (int k = 0; k < kScales; ++k) s = fma2(f2(a.B[i][k], a.B[i][k]), Lk[k], s);
-        al2[i] = s;
+    DetTile t;
+    t.tx0 = tx0;
+    t.ty0 = ty0;
+    t.W = W;
+    t.H = H;
+    t.img = cur.img;
+    t.tr = cur.tr;
+    t.bmask = bmask;
+    const bool det = !Masked || mode == kModeDetect;
+    if constexpr (Defer) {
+      // the scale test and refinement of this tile run with the next one
+      prev = t;
+      prev_det = det;
+    } else {
+      if (det) {
+        detect_phase1<S, Masked>(a, Ls, t, pend, &sh.n_pending);
+        __syncthreads();
+        detect_phase2<S>(a, Ls, t, pend, sh.n_pending);
       }
-      const int x = tx0 + lx, y0 = ty0 + 2 * m;
-      // rows 2m, 2m + 1 lie in block row m / 8; a proposal may rule the block out
-      const bool inx = x >= 1 && x < W - 1 && (!Masked || ((bmask >> ((m >> 3) * (kTX / 16) + (lx >> 4))) & 1u));
-      cubic_extremum2(a, al2, inx && y0 >= 1 && y0 < H - 1, inx && y0 + 1 < H - 1, bt[it], tb[it]);
+      // the pending list lives in `in` (or `tmp`), rewritten by the next tile
+      __syncthreads();
     }
-#pragma unroll
-    for (int it = 0; it < kIt; ++it) {
-      const int idx = it * kThreads + threadIdx.x;
-      const int m = idx / kTX, lx = idx - (idx / kTX) * kTX;
-      const unsigned m0 = __ballot_sync(0xffffffffu, bt[it][0] != 0);
-      const unsigned m1 = __ballot_sync(0xffffffffu, bt[it][1] != 0);
-      if (m0 | m1) {
-        int base = 0;
-        if (lane == 0) base = atomicAdd(&sh.n_pending, __popc(m0) + __popc(m1));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        const unsigned below = (1u << lane) - 1u;
-        if (bt[it][0] != 0) {
-          Pending e;
-          e.code = ((2 * m) << 16) | (lx << 1) | (bt[it][0] > 0 ? 1 : 0);
-          e.t = tb[it][0];
-          pend[base + __popc(m0 & below)] = e;
-        }
-        if (bt[it][1] != 0) {
-          Pending e;
-          e.code = ((2 * m + 1) << 16) | (lx << 1) | (bt[it][1] > 0 ? 1 : 0);
-          e.t = tb[it][1];
-          pend[base + __popc(m0) + __popc(m1 & below)] = e;
-        }
-      }
+  }
+  if constexpr (Defer) {
+    // the last tile's detection
+    if (prev_det) {
+      detect_phase1<S, Masked>(a, Ls, prev, pend, &sh.n_pending);
+      __syncthreads();
+      detect_phase2<S>(a, Ls, prev, pend, sh.n_pending);
     }
-    __syncthreads();
-
-    // ---- phase 2: neighbour test and refinement of the survivors, densely;
-    // one queue reservation per warp and round.  The queue order does not
-    // matter: the selection orders candidates by a total order of their own.
-    // Meanwhile the last warp's lane 0 looks up the tile after next.
-    const int np = sh.n_pending;
-    if (warp == kWarps - 1 && lane == 0) tile_info<S, InT>(a, prefix, b + 2 * gridDim.x, n_tiles, ic, after);
-    for (int i0 = warp * 32; i0 < np; i0 += kThreads) {
-      const int i = i0 + lane;
-      Found f;
-      bool found = false;
-      if (i < np) {
-        const Pending e = pend[i];
-        const int ly = e.code >> 16, lx = (e.code >> 1) & 0x7fff;
-        found = refine_pixel<S>(a, Ls, ly, lx, (e.code & 1) ? 1 : -1, e.t, tx0 + lx, ty0 + ly, f);
-      }
-      const unsigned msk = __ballot_sync(0xffffffffu, found);
-      if (msk == 0) continue;
-      int base = 0;
-      if (lane == 0) base = atomicAdd(a.cand_count + img, __popc(msk));
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (found) {
-        const int pos = base + __popc(msk & ((1u << lane) - 1u));
-        if (pos < a.cand_cap) {
-          Cand c;
-          const bool tr = cur.tr;  // image frame
-          c.xo = tr ? f.yo : f.xo;
-          c.yo = tr ? f.xo : f.yo;
-          c.so = f.so;
-          c.resp = f.resp;
-          c.pss = f.pss;
-          c.ratio = f.ratio;
-          c.octave = (short)o;
-          c.type = (short)f.type;
-          c.spare = 0;
-          a.cands[(size_t)img * a.cand_cap + pos] = c;
-        } else {
-          atomicOr(a.status, kStatusCandOverflow);
-        }
-      }
-    }
-    // the pending list lives in `in` (or `tmp`), rewritten by the next tile;
-    // the tile after next is described in `after`
-    __syncthreads();
   }
   cp_async_wait_all();  // nothing may still be landing in shared memory at exit
 }
@@ -844,12 +915,13 @@ static int tile_pitch(int max_radius) { return max_radius <= 14 ? 160 : 184; }
 template <typename S>
 static size_t detect_smem(int max_radius, int in_size, int n_images) {
   const int ic = tile_pitch(max_radius);
+  const size_t pend = ic == 160 ? kPendBytes<S, 160> : kPendBytes<S, 184>;
   const size_t rows = (size_t)(S::ROWS + 2 * max_radius);
   const bool direct = S::TY == 16 && in_size == 4;
   const size_t raw = direct ? 0 : (rows * ic * in_size + 15) / 16 * 16;
   return raw + sizeof(float) * (rows * ic + (size_t)S::ROWS * ic + (size_t)S::ROWS * kGC +
                                 (size_t)kScales * S::ROWS * kLC) +
-         sizeof(int) * (size_t)(n_images + 1);
+         pend + sizeof(int) * (size_t)(n_images + 1);
 }
 
 // The launch of one variant: shared memory attribute, and a grid of
