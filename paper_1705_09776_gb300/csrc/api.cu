@@ -1654,6 +1654,16 @@ cdvs_status cdvs_set_scfv_model(cdvs_ctx* c, const cdvs_scfv_model* m) {
     d[kScfvOffLw + i] = (float)(std::log(w) - 0.5 * logdet);
     d[kScfvOffNmu + i] = (float)(1.0 / std::sqrt(w));
     d[kScfvOffNsig + i] = (float)(1.0 / std::sqrt(2.0 * w));
+    // Eq. 10's matrix form: -1/2 sum_k (y_k - mu_k)^2 / v_k
+    //   = sum_k y_k^2 (-1/(2 v_k)) + sum_k y_k (mu_k / v_k) - 1/2 sum_k mu_k^2 / v_k
+    double cq = 0.0;
+    for (int k = 0; k < kScfvDim; ++k) {
+      const double v = m->variances[i * kScfvDim + k], mu = m->means[i * kScfvDim + k];
+      d[kScfvOffW + kScfvWIndex(k, i)] = (float)(-0.5 / v);
+      d[kScfvOffW + kScfvWIndex(kScfvDim + k, i)] = (float)(mu / v);
+      cq += mu * mu / v;
+    }
+    d[kScfvOffC + i] = (float)(std::log(w) - 0.5 * logdet - 0.5 * cq);
   }
   cudaError_t e;
   if ((e = cudaSetDevice(c->device)) != cudaSuccess || (e = ensure(c->scfv_model, sizeof(float) * d.size())) != cudaSuccess ||

@@ -228,9 +228,21 @@ cudaError_t launch_resize(const ResizeJob* d_jobs, int n_jobs, int max_rows, cud
 constexpr int kScfvComp = 512, kScfvDim = 32;
 // the device model, derived on the host: P transposed [128][32], the PCA
 // mean, mu [512][32], 1/s [512][32], log w_i - 1/2 sum_k log(2 pi v_ik),
-// 1/sqrt(w_i), 1/sqrt(2 w_i)
+// 1/sqrt(w_i), 1/sqrt(2 w_i); then the matrix form of the log-likelihood
+// (Eq. 10): W [64][512] with rows k < 32 = -1/(2 v_ik) (the y_k^2 terms) and
+// rows 32 + k = mu_ik / v_ik (the y_k terms), stored in the register order
+// of the tensor-core B fragments (kScfvWIndex), and the constant
+// c_i = log w_i - 1/2 sum_k log(2 pi v_ik) - 1/2 sum_k mu_ik^2 / v_ik
 constexpr int kScfvOffPcaT = 0, kScfvOffMean = 4096, kScfvOffMu = 4224, kScfvOffIsd = 20608, kScfvOffLw = 36992,
-              kScfvOffNmu = 37504, kScfvOffNsig = 38016, kScfvModelFloats = 38528;
+              kScfvOffNmu = 37504, kScfvOffNsig = 38016, kScfvOffW = 38528, kScfvOffC = 71296,
+              kScfvModelFloats = 71808;
+// Position of W[k][i] in the fragment order: warp w = i / 64 of the
+// posterior kernel, k-step s = k / 8, n-tile j = (i % 64) / 8, lane
+// 4 (i % 8) + (k % 4), element (k % 8) / 4.
+inline int kScfvWIndex(int k, int i) {
+  const int w = i / 64, j = (i % 64) / 8, g = i % 8, s = k / 8, t = k % 4, e = (k % 8) / 4;
+  return ((((w * 8 + s) * 8 + j) * 32 + (4 * g + t)) * 2) + e;
+}
 cudaError_t launch_scfv(const float* desc, int n_rec, const int* rec_off, int n_images, const float* model,
                         int n_select, float* Y, float* Q, float* g_mu, float* g_sig, float* delta, int* order,
                         uint32_t* bits, int n_sms, cudaStream_t s);

@@ -10,10 +10,19 @@
 //   delta(i)   = population std of the 32 entries of g_mu(i)            Eq. 8
 //
 // then the components ranked by delta (descending, ties to the lower index)
-// and the sign bits of g_mu for the first n_select of them.  Every sum runs
-// in FP32 in a fixed order: the posterior is a softmax over 512 components of
-// distances of ~32 terms, too sensitive for TF32 or BF16 operands, and the
-// whole aggregation is ~30 MFLOP per image, so the FP32 pipes suffice.
+// and the sign bits of g_mu for the first n_select of them.
+//
+// The two contractions run on the tensor cores, as the paper's matrix form
+// has them (Eq. 10, 12, 14):
+//   * the log-likelihoods of a tile of records against all 512 components,
+//     L = [y^2 | y] W + c, with W = [-1/(2v); mu/v] (64 x 512);
+//   * per image, S = Gamma^T [1 | y | y^2] (512 x 65), from which
+//     g_mu = (S_y - mu S_1) / s and g_sigma = (S_yy - 2 mu S_y + mu^2 S_1) / v - S_1.
+// Both use mma.sync m16n8k8 with TF32 operands split in two (x = hi + lo,
+// hi and lo both TF32) and three products per term (hi hi + hi lo + lo hi),
+// accumulated in FP32: about 21 significant bits per product, so the
+// softmax, which needs the log-likelihood to ~1e-5 absolute, stays within
+// FP32-level error.  The softmax and every reduction run in a fixed order.
 #include <algorithm>
 
 #include "cdvs_internal.cuh"
@@ -23,145 +32,318 @@ namespace {
 
 constexpr int kComp = kScfvComp, kDim = kScfvDim, kIn = 128;
 
-// K_a: y = P (x - m), one warp per record, lane j = output dimension j.
-__global__ void __launch_bounds__(256) scfv_pca_kernel(const float* desc, int n_rec, const float* model,
-                                                       float* Y) {
-  __shared__ float pt[kIn * kDim];  // P transposed: [k][j]
+// ---- split-TF32 tensor-core products
+
+// x = hi + lo with hi, lo both representable in TF32 (round to nearest).
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));
+  const float r = x - __uint_as_float(hi);
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(r));
+}
+
+// D = A B + D for one 16 x 8 x 8 block (A row-major 16 x 8, B 8 x 8).
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+               "{%0,%1,%2,%3};"
+               : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+               : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// hi*hi + hi*lo + lo*hi, the small products first
+__device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4],
+                                     const uint32_t (&bh)[2], const uint32_t (&bl)[2]) {
+  mma_tf32(d, al, bh);
+  mma_tf32(d, ah, bl);
+  mma_tf32(d, ah, bh);
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// K_a + K_b: projection and posteriors.  Persistent CTAs of 8 warps; a tile
+// is 64 records (four 16-row tensor-core tiles).
+//   1. y = (x - m) P^T on the tensor cores: the tile's descriptors minus the
+//      PCA mean (FP32) times P^T (staged once per CTA, split into TF32
+//      hi / lo); warp w computes the 16 x 8 output blocks (w / 2, 2 (w % 2))
+//      and (w / 2, 2 (w % 2) + 1).  y goes to shared memory and to Y.
+//   2. the log-likelihoods L = [y^2 | y] W + c: warp w owns components
+//      64w .. 64w + 63 (eight 8-column tiles) for all four row tiles; W is
+//      staged once per CTA in fragment order.
+//   3. per record the softmax over the 512 components, in a fixed order.
+// The fragment layouts of m16n8k8: lane = 4 g + t; A element
+// (g + 8 (q & 1), t + 4 (q >> 1)) in register q; B elements (t, g) and
+// (t + 4, g); C elements (g, 2t), (g, 2t + 1), (g + 8, 2t), (g + 8, 2t + 1).
+constexpr int kPostTile = 64, kPostThreads = 256, kYPitch = 36, kXPitch = 132;
+constexpr float kLog2e = 1.4426950408889634f;
+
+// dynamic shared memory of K_b (floats): W | P^T hi, lo in fragment order |
+// the descriptor tile
+constexpr int kPostSmemFloats = 2 * kDim * kComp + 2 * kIn * kDim + kPostTile * kXPitch;
+
+__global__ void __launch_bounds__(kPostThreads, 1) scfv_post_kernel(const float* desc, int n_rec,
+                                                                    const float* model, float* Y, float* Q) {
+  extern __shared__ float4 w4[];
+  float* const Ws = reinterpret_cast<float*>(w4);
+  uint32_t* const Ph = reinterpret_cast<uint32_t*>(Ws + 2 * kDim * kComp);  // [16 k-steps][4 n-tiles][32 lanes][2]
+  uint32_t* const Pl = Ph + kIn * kDim;
+  float* const xs = reinterpret_cast<float*>(Pl + kIn * kDim);               // [64][kXPitch]
+  __shared__ float ys[kPostTile][kYPitch];
+  __shared__ float cs[kComp];
   __shared__ float mean[kIn];
-  for (int i = threadIdx.x; i < kIn * kDim; i += blockDim.x) pt[i] = model[kScfvOffPcaT + i];
-  for (int i = threadIdx.x; i < kIn; i += blockDim.x) mean[i] = model[kScfvOffMean + i];
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int warps = (gridDim.x * blockDim.x) >> 5;
-  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n_rec; r += warps) {
-    const float4 x4 = reinterpret_cast<const float4*>(desc + (size_t)r * kIn)[lane];
-    const float x[4] = {x4.x - mean[4 * lane], x4.y - mean[4 * lane + 1], x4.z - mean[4 * lane + 2],
-                        x4.w - mean[4 * lane + 3]};
-    float acc = 0.0f;
-    for (int q = 0; q < 32; ++q)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc = fmaf(__shfl_sync(0xffffffffu, x[c], q), pt[(4 * q + c) * kDim + lane], acc);
-    Y[(size_t)r * kDim + lane] = acc;
+  __shared__ float red[kPostThreads / 32][kPostTile];
+  __shared__ float tmax[kPostTile], tinv[kPostTile];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
+  for (int i = tid; i < 2 * kDim * kComp / 4; i += kPostThreads)
+    w4[i] = reinterpret_cast<const float4*>(model + kScfvOffW)[i];
+  // P^T (model: pt[k][j], k = input dimension, j = output dimension) in B
+  // fragment order for k-step s, n-tile j8: (k = 8s + t (+4), j = 8 j8 + g)
+  for (int i = tid; i < kIn * kDim; i += kPostThreads) {
+    const int e = i & 1, ln = (i >> 1) & 31, j8 = (i >> 6) & 3, ks = i >> 8;
+    const int k = 8 * ks + (ln & 3) + 4 * e, j = 8 * j8 + (ln >> 2);
+    split_tf32(model[kScfvOffPcaT + k * kDim + j], Ph[i], Pl[i]);
   }
-}
-
-// K_b: posteriors of 32 records at a time; thread i = component i.
-constexpr int kPostRec = 32;
-__global__ void __launch_bounds__(kComp, 1) scfv_post_kernel(const float* Y, int n_rec, const float* model,
-                                                             float* Q) {
-  __shared__ __align__(16) float ys[kPostRec][kDim];
-  __shared__ float red[kComp / 32][kPostRec];
-  __shared__ float tot[kPostRec];
-  const int i = threadIdx.x, lane = i & 31, warp = i >> 5;
-  float mu[kDim], isd[kDim];
-#pragma unroll
-  for (int k = 0; k < kDim; ++k) {
-    mu[k] = model[kScfvOffMu + i * kDim + k];
-    isd[k] = model[kScfvOffIsd + i * kDim + k];
-  }
-  const float lw = model[kScfvOffLw + i];
-  for (int r0 = blockIdx.x * kPostRec; r0 < n_rec; r0 += gridDim.x * kPostRec) {
-    __syncthreads();
-    for (int e = i; e < kPostRec * kDim; e += kComp) {
-      const int r = e / kDim;
-      ys[r][e - r * kDim] = r0 + r < n_rec ? Y[(size_t)(r0 + r) * kDim + e - r * kDim] : 0.0f;
-    }
-    __syncthreads();
-    float l[kPostRec];
-#pragma unroll
-    for (int r = 0; r < kPostRec; ++r) {
-      float d2 = 0.0f;
-#pragma unroll
-      for (int k = 0; k < kDim; k += 4) {
-        const float4 y = *reinterpret_cast<const float4*>(&ys[r][k]);
-        const float d0 = (y.x - mu[k]) * isd[k], d1 = (y.y - mu[k + 1]) * isd[k + 1];
-        const float d2_ = (y.z - mu[k + 2]) * isd[k + 2], d3 = (y.w - mu[k + 3]) * isd[k + 3];
-        d2 = fmaf(d0, d0, d2);
-        d2 = fmaf(d1, d1, d2);
-        d2 = fmaf(d2_, d2_, d2);
-        d2 = fmaf(d3, d3, d2);
+  for (int i = tid; i < kComp; i += kPostThreads) cs[i] = model[kScfvOffC + i];
+  for (int i = tid; i < kIn; i += kPostThreads) mean[i] = model[kScfvOffMean + i];
+  const float2* wf = reinterpret_cast<const float2*>(w4) + warp * 8 * 8 * 32;
+  for (int r0 = blockIdx.x * kPostTile; r0 < n_rec; r0 += gridDim.x * kPostTile) {
+    __syncthreads();  // model staged; the previous tile is done with xs, ys, red, tmax, tinv
+    for (int e = tid; e < kPostTile * kIn / 4; e += kPostThreads) {
+      const int r = e / (kIn / 4), c4 = e - r * (kIn / 4);
+      float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      if (r0 + r < n_rec) {
+        v = reinterpret_cast<const float4*>(desc + (size_t)(r0 + r) * kIn)[c4];
+        v.x -= mean[4 * c4];
+        v.y -= mean[4 * c4 + 1];
+        v.z -= mean[4 * c4 + 2];
+        v.w -= mean[4 * c4 + 3];
       }
-      l[r] = fmaf(-0.5f, d2, lw);
+      *reinterpret_cast<float4*>(xs + r * kXPitch + 4 * c4) = v;
     }
-    // per record: max over the 512 components, then the sum of exponentials
+    __syncthreads();
+    {  // 1. projection: blocks (mt, nt) and (mt, nt + 1) of the 64 x 32 output
+      const int mt = warp >> 1, nt0 = 2 * (warp & 1);
+      float pa[2][4] = {{0.0f, 0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f, 0.0f}};
+#pragma unroll 4
+      for (int ks = 0; ks < kIn / 8; ++ks) {
+        uint32_t ah[4], al[4];
 #pragma unroll
-    for (int r = 0; r < kPostRec; ++r) {
-      float v = l[r];
-      for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-      if (lane == 0) red[warp][r] = v;
-    }
-    __syncthreads();
-    if (i < kPostRec) {
-      float v = red[0][i];
-      for (int w = 1; w < kComp / 32; ++w) v = fmaxf(v, red[w][i]);
-      tot[i] = v;
-    }
-    __syncthreads();
+        for (int q = 0; q < 4; ++q)
+          split_tf32(xs[(16 * mt + g + 8 * (q & 1)) * kXPitch + 8 * ks + t + 4 * (q >> 1)], ah[q], al[q]);
 #pragma unroll
-    for (int r = 0; r < kPostRec; ++r) {
-      l[r] = expf(l[r] - tot[r]);
-      float v = l[r];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) red[warp][r] = v;
+        for (int u = 0; u < 2; ++u) {
+          const int f = ((ks * 4 + nt0 + u) * 32 + lane) * 2;
+          const uint32_t bh[2] = {Ph[f], Ph[f + 1]}, bl[2] = {Pl[f], Pl[f + 1]};
+          mma3(pa[u], ah, al, bh, bl);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int r = 16 * mt + g, c = 8 * (nt0 + u) + 2 * t;
+        ys[r][c] = pa[u][0];
+        ys[r][c + 1] = pa[u][1];
+        ys[r + 8][c] = pa[u][2];
+        ys[r + 8][c + 1] = pa[u][3];
+      }
     }
     __syncthreads();
-    if (i < kPostRec) {
+    for (int e = tid; e < kPostTile * kDim; e += kPostThreads) {
+      const int r = e / kDim, k = e - r * kDim;
+      if (r0 + r < n_rec) Y[(size_t)(r0 + r) * kDim + k] = ys[r][k];
+    }
+    // 2. log-likelihoods
+    float acc[4][8][4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[m][j][q] = 0.0f;
+#pragma unroll 1
+    for (int s = 0; s < 8; ++s) {
+      // A = [y^2 | y]: k-steps 0..3 take the squares of dimensions 8s..8s+7,
+      // k-steps 4..7 the dimensions themselves
+      uint32_t ah[4][4], al[4][4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float y = ys[16 * m + g + 8 * (q & 1)][8 * (s & 3) + t + 4 * (q >> 1)];
+          split_tf32(s < 4 ? y * y : y, ah[m][q], al[m][q]);
+        }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float2 w = wf[(s * 8 + j) * 32 + lane];
+        uint32_t bh[2], bl[2];
+        split_tf32(w.x, bh[0], bl[0]);
+        split_tf32(w.y, bh[1], bl[1]);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) mma3(acc[m][j], ah[m], al[m], bh, bl);
+      }
+    }
+    // 3. softmax per record: records 16m + g + 8h of this lane (h = q >> 1),
+    // components 64 warp + 8j + 2t + (q & 1)
+    float mx[4][2];
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float v = -3.0e38f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            float& l = acc[m][j][2 * h + e];
+            l += cs[64 * warp + 8 * j + 2 * t + e];
+            v = fmaxf(v, l);
+          }
+        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 1));
+        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 2));
+        mx[m][h] = v;
+      }
+    if (t == 0)
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) red[warp][16 * m + g + 8 * h] = mx[m][h];
+    __syncthreads();
+    if (tid < kPostTile) {
+      float v = red[0][tid];
+      for (int w = 1; w < kPostThreads / 32; ++w) v = fmaxf(v, red[w][tid]);
+      tmax[tid] = v;
+    }
+    __syncthreads();
+    float sm[4][2];
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float mref = tmax[16 * m + g + 8 * h] * kLog2e;
+        float v = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            float& l = acc[m][j][2 * h + e];
+            l = ex2_approx(fmaf(l, kLog2e, -mref));
+            v += l;
+          }
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        sm[m][h] = v;
+      }
+    __syncthreads();  // every max read before red is rewritten
+    if (t == 0)
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) red[warp][16 * m + g + 8 * h] = sm[m][h];
+    __syncthreads();
+    if (tid < kPostTile) {
       float v = 0.0f;
-      for (int w = 0; w < kComp / 32; ++w) v += red[w][i];
-      tot[i] = 1.0f / v;
+      for (int w = 0; w < kPostThreads / 32; ++w) v += red[w][tid];
+      tinv[tid] = 1.0f / v;
     }
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < kPostRec; ++r)
-      if (r0 + r < n_rec) Q[(size_t)(r0 + r) * kComp + i] = l[r] * tot[r];
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = 16 * m + g + 8 * h;
+        if (r0 + r >= n_rec) continue;
+        const float inv = tinv[r];
+        float2* out = reinterpret_cast<float2*>(Q + (size_t)(r0 + r) * kComp + 64 * warp + 2 * t);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) out[4 * j] = make_float2(acc[m][j][2 * h] * inv, acc[m][j][2 * h + 1] * inv);
+      }
   }
 }
 
-// K_c: Fisher gradients.  CTA = 32 components of one image; thread = one
-// component and two dimensions.  Chunks of kGradRec records' posteriors (of
-// those components) and projections are staged in shared memory with
-// coalesced loads; every thread then sums its terms in record order.
-constexpr int kGradComp = 32, kGradRec = 64, kGradThreads = 512;
-__global__ void __launch_bounds__(kGradThreads) scfv_grad_kernel(const float* Y, const float* Q,
-                                                                 const int* rec_off, const float* model,
-                                                                 float* g_mu, float* g_sig) {
-  __shared__ float qs[kGradRec][kGradComp];
-  __shared__ float2 ys[kGradRec][kDim / 2];
-  const int b = blockIdx.y, i0 = blockIdx.x * kGradComp;
-  const int il = threadIdx.x >> 4, kp = threadIdx.x & 15;  // component i0 + il, dimensions 2 kp, 2 kp + 1
-  const int i = i0 + il;
-  const float2 mu = make_float2(model[kScfvOffMu + i * kDim + 2 * kp], model[kScfvOffMu + i * kDim + 2 * kp + 1]);
-  const float2 isd = make_float2(model[kScfvOffIsd + i * kDim + 2 * kp], model[kScfvOffIsd + i * kDim + 2 * kp + 1]);
+// K_c: Fisher gradients as per-image products S = Gamma^T [1 | y | y^2]
+// (512 x 65, padded to 72 columns).  CTA = 128 components of one image,
+// warp w = components 16w .. 16w + 15 of them (one 16-row tile), all nine
+// 8-column tiles; the image's records go through in chunks of 32 (four
+// 8-deep k-steps), staged in shared memory (the [1 | y | y^2] chunk already
+// split into TF32 hi / lo, once for all warps).  Then the gradients from S.
+constexpr int kGradBlock = 128, kGradChunk = 32, kGradThreads = 256, kZCols = 72, kQPitch = 136, kSPitch = 73;
+constexpr int kGradSmemFloats = kGradChunk * (kQPitch + 2 * kZCols) + kGradBlock * kSPitch;
+
+__global__ void __launch_bounds__(kGradThreads) scfv_grad_kernel(const float* Y, const float* Q, const int* rec_off,
+                                                                 const float* model, float* g_mu, float* g_sig) {
+  extern __shared__ float4 gsm4[];
+  float* const base = reinterpret_cast<float*>(gsm4);
+  float (*qs)[kQPitch] = reinterpret_cast<float (*)[kQPitch]>(base);
+  uint32_t (*zh)[kZCols] = reinterpret_cast<uint32_t (*)[kZCols]>(base + kGradChunk * kQPitch);
+  uint32_t (*zl)[kZCols] = reinterpret_cast<uint32_t (*)[kZCols]>(base + kGradChunk * (kQPitch + kZCols));
+  float (*S)[kSPitch] = reinterpret_cast<float (*)[kSPitch]>(base + kGradChunk * (kQPitch + 2 * kZCols));
+  const int b = blockIdx.y, i0 = blockIdx.x * kGradBlock;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
   const int t0 = rec_off[b], t1 = rec_off[b + 1];
-  float a1x = 0.0f, a1y = 0.0f, a2x = 0.0f, a2y = 0.0f;
-  for (int c0 = t0; c0 < t1; c0 += kGradRec) {
-    const int nr = min(kGradRec, t1 - c0);
+  float acc[kZCols / 8][4];
+#pragma unroll
+  for (int j = 0; j < kZCols / 8; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[j][q] = 0.0f;
+  for (int c0 = t0; c0 < t1; c0 += kGradChunk) {
+    const int nr = min(kGradChunk, t1 - c0);
     __syncthreads();
-    for (int e = threadIdx.x; e < kGradRec * kGradComp; e += kGradThreads) {
-      const int r = e / kGradComp, c = e - r * kGradComp;
-      qs[r][c] = r < nr ? Q[(size_t)(c0 + r) * kComp + i0 + c] : 0.0f;
+    for (int e = tid; e < kGradChunk * kGradBlock / 4; e += kGradThreads) {
+      const int r = e / (kGradBlock / 4), c4 = e - r * (kGradBlock / 4);
+      const float4 v = r < nr ? reinterpret_cast<const float4*>(Q + (size_t)(c0 + r) * kComp + i0)[c4]
+                              : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      *reinterpret_cast<float4*>(&qs[r][4 * c4]) = v;
     }
-    for (int e = threadIdx.x; e < kGradRec * (kDim / 2); e += kGradThreads) {
-      const int r = e / (kDim / 2), c = e - r * (kDim / 2);
-      ys[r][c] = r < nr ? reinterpret_cast<const float2*>(Y + (size_t)(c0 + r) * kDim)[c] : make_float2(0.f, 0.f);
+    for (int e = tid; e < kGradChunk * kZCols; e += kGradThreads) {
+      const int r = e / kZCols, c = e - r * kZCols;
+      float z = 0.0f;
+      if (r < nr) {
+        if (c == 0) z = 1.0f;
+        else if (c <= kDim) z = Y[(size_t)(c0 + r) * kDim + c - 1];
+        else if (c <= 2 * kDim) {
+          const float y = Y[(size_t)(c0 + r) * kDim + c - 1 - kDim];
+          z = y * y;
+        }
+      }
+      split_tf32(z, zh[r][c], zl[r][c]);
     }
     __syncthreads();
-    for (int r = 0; r < nr; ++r) {
-      const float g = qs[r][il];
-      const float2 y = ys[r][kp];
-      const float dx = (y.x - mu.x) * isd.x, dy = (y.y - mu.y) * isd.y;
-      a1x = fmaf(g, dx, a1x);
-      a1y = fmaf(g, dy, a1y);
-      a2x = fmaf(g, fmaf(dx, dx, -1.0f), a2x);
-      a2y = fmaf(g, fmaf(dy, dy, -1.0f), a2y);
+#pragma unroll
+    for (int s = 0; s < kGradChunk / 8; ++s) {
+      // A = Gamma^T: rows = this warp's 16 components, columns = 8 records
+      uint32_t ah[4], al[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        split_tf32(qs[8 * s + t + 4 * (q >> 1)][16 * warp + g + 8 * (q & 1)], ah[q], al[q]);
+#pragma unroll
+      for (int j = 0; j < kZCols / 8; ++j) {
+        const uint32_t bh[2] = {zh[8 * s + t][8 * j + g], zh[8 * s + t + 4][8 * j + g]};
+        const uint32_t bl[2] = {zl[8 * s + t][8 * j + g], zl[8 * s + t + 4][8 * j + g]};
+        mma3(acc[j], ah, al, bh, bl);
+      }
     }
   }
+  // S rows = components of this CTA, columns = [1 | y | y^2 | pad]
+#pragma unroll
+  for (int j = 0; j < kZCols / 8; ++j) {
+    S[16 * warp + g][8 * j + 2 * t] = acc[j][0];
+    S[16 * warp + g][8 * j + 2 * t + 1] = acc[j][1];
+    S[16 * warp + g + 8][8 * j + 2 * t] = acc[j][2];
+    S[16 * warp + g + 8][8 * j + 2 * t + 1] = acc[j][3];
+  }
+  __syncthreads();
   const int K = t1 - t0;
   const float inv = K > 0 ? 1.0f / (float)K : 0.0f;
-  const float nm = inv * model[kScfvOffNmu + i], ns = inv * model[kScfvOffNsig + i];
-  const size_t o = ((size_t)b * kComp + i) * kDim + 2 * kp;
-  reinterpret_cast<float2*>(g_mu + o)[0] = make_float2(a1x * nm, a1y * nm);
-  reinterpret_cast<float2*>(g_sig + o)[0] = make_float2(a2x * ns, a2y * ns);
+  for (int e = tid; e < kGradBlock * kDim; e += kGradThreads) {
+    const int il = e / kDim, k = e - il * kDim, i = i0 + il;
+    const float s0 = S[il][0], s1 = S[il][1 + k], s2 = S[il][1 + kDim + k];
+    const float mu = model[kScfvOffMu + i * kDim + k], isd = model[kScfvOffIsd + i * kDim + k];
+    const float nm = inv * model[kScfvOffNmu + i], ns = inv * model[kScfvOffNsig + i];
+    const size_t o = ((size_t)b * kComp + i) * kDim + k;
+    g_mu[o] = nm * isd * fmaf(-mu, s0, s1);
+    g_sig[o] = ns * fmaf(isd * isd, fmaf(mu, fmaf(mu, s0, -2.0f * s1), s2), -s0);
+  }
 }
 
 // K_d: delta, ranks and sign bits; one CTA per image, thread i = component i.
@@ -208,11 +390,17 @@ cudaError_t launch_scfv(const float* desc, int n_rec, const int* rec_off, int n_
                         uint32_t* bits, int n_sms, cudaStream_t s) {
   if (n_images <= 0) return cudaSuccess;
   if (n_rec > 0) {
-    scfv_pca_kernel<<<std::max(1, std::min((n_rec + 7) / 8, n_sms * 8)), 256, 0, s>>>(desc, n_rec, model, Y);
-    scfv_post_kernel<<<std::max(1, std::min((n_rec + kPostRec - 1) / kPostRec, n_sms)), kComp, 0, s>>>(Y, n_rec,
-                                                                                                   model, Q);
+    const int pbytes = (int)(sizeof(float) * kPostSmemFloats);
+    cudaError_t e = cudaFuncSetAttribute(scfv_post_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pbytes);
+    if (e != cudaSuccess) return e;
+    scfv_post_kernel<<<std::max(1, std::min((n_rec + kPostTile - 1) / kPostTile, n_sms)), kPostThreads, pbytes, s>>>(
+        desc, n_rec, model, Y, Q);
   }
-  scfv_grad_kernel<<<dim3(kComp / kGradComp, n_images), kGradThreads, 0, s>>>(Y, Q, rec_off, model, g_mu, g_sig);
+  const int gbytes = (int)(sizeof(float) * kGradSmemFloats);
+  cudaError_t e = cudaFuncSetAttribute(scfv_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, gbytes);
+  if (e != cudaSuccess) return e;
+  scfv_grad_kernel<<<dim3(kComp / kGradBlock, n_images), kGradThreads, gbytes, s>>>(Y, Q, rec_off, model, g_mu,
+                                                                                     g_sig);
   scfv_rank_kernel<<<n_images, kComp, 0, s>>>(g_mu, n_select, delta, order, bits);
   return cudaGetLastError();
 }

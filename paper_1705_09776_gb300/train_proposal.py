@@ -6,7 +6,11 @@ Labels come from the plain detector: a 16x16 block is positive when a
 first-octave record of cdvs_extract (after the cross-octave check and the
 selection, Sec. III-B) lies in it.  The images are the seeded synthetic
 blob images (seeds 1000000 + i for training, 3000000 + i for choosing the
-threshold).  Training runs the library's own forward, backward and Adam
+threshold).  A fraction of them (--zoom) carries the statistics of the
+high-resolution workload at 640 x 480: the blobs 3.2 times larger and as
+many per pixel as in a 2048 x 1536 image (200 / 10.24 of them), so one
+network serves both scales; the threshold must keep the records of both
+kinds of validation image.  Training runs the library's own forward, backward and Adam
 kernels (cdvs_proposal_train_step, BF16 as in inference).  The threshold is
 the largest of a fixed list whose masked extraction keeps at least
 `--keep` of the plain detector's records on the validation images.  The
@@ -23,21 +27,30 @@ import numpy as np
 from . import synth
 
 TRAIN_BASE, VAL_BASE = 1_000_000, 3_000_000
+ZOOM_TRAIN_BASE, ZOOM_VAL_BASE = 5_000_000, 6_000_000
+ZOOM = 3.2   # blob scale of the 2048 x 1536 workload against the 640 x 480 one
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_OUT = os.path.join(HERE, "proposal_weights.npz")
 THRESHOLDS = (0.5, 0.4, 0.3, 0.2, 0.15, 0.1, 0.07, 0.05, 0.03, 0.02, 0.01)
 
 
 def _gen(args):
-    base, i = args
+    base, i, zoom = args
+    if zoom:
+        # a 640 x 480 window of the high-resolution workload: blobs ZOOM times
+        # larger, as many per pixel as there
+        return synth.blob_image(synth.image_seed(base, i), n_blobs=int(round(200 / (ZOOM * ZOOM))),
+                                sigma_range=(1.5 * ZOOM, 20.0 * ZOOM))
     return synth.blob_image(synth.image_seed(base, i))
 
 
-def make_images(base: int, n: int, procs: int) -> np.ndarray:
+def make_images(base: int, n: int, procs: int, zoom: bool = False) -> np.ndarray:
     """Seeded images, generated in a spawn pool (call before CUDA starts)."""
     import multiprocessing as mp
+    if n == 0:
+        return np.zeros((0, 480, 640), np.uint8)
     with mp.get_context("spawn").Pool(procs) as pool:
-        return np.stack(pool.map(_gen, [(base, i) for i in range(n)], chunksize=16))
+        return np.stack(pool.map(_gen, [(base, i, zoom) for i in range(n)], chunksize=16))
 
 
 def block_labels(records, n_images: int, height: int, width: int) -> np.ndarray:
@@ -89,12 +102,18 @@ def main(argv=None):
     ap.add_argument("--epochs", type=int, default=3)
     ap.add_argument("--lr", type=float, default=3e-3)
     ap.add_argument("--keep", type=float, default=0.995)
+    ap.add_argument("--zoom", type=float, default=0.25,
+                    help="fraction of training and validation images with the high-resolution statistics")
     ap.add_argument("--procs", type=int, default=os.cpu_count() or 1)
     ap.add_argument("--out", default=DEFAULT_OUT)
     a = ap.parse_args(argv)
     t0 = time.time()
-    train = make_images(TRAIN_BASE, a.train, a.procs)
-    val = make_images(VAL_BASE, a.val, a.procs)
+    nz, nzv = int(round(a.train * a.zoom)), int(round(a.val * a.zoom))
+    train = np.concatenate([make_images(TRAIN_BASE, a.train - nz, a.procs),
+                            make_images(ZOOM_TRAIN_BASE, nz, a.procs, zoom=True)])
+    vals = [make_images(VAL_BASE, a.val - nzv, a.procs)]
+    if nzv:
+        vals.append(make_images(ZOOM_VAL_BASE, nzv, a.procs, zoom=True))
     t_gen = time.time() - t0
 
     import torch
@@ -134,24 +153,24 @@ def main(argv=None):
     t_train = time.time() - t1
     th = theta.cpu().numpy()
 
-    # threshold: the largest whose masked extraction keeps `keep` of the records
+    # threshold: the largest whose masked extraction keeps `keep` of the
+    # records of every kind of validation image
     ctx.set_proposal(th)
-    vrec, _ = extract_batches(ctx, cdvs, val, plain)
-    vkeys = record_keys(vrec)
+    vkeys = [record_keys(extract_batches(ctx, cdvs, v, plain)[0]) for v in vals]
     chosen, table = None, []
     for t in THRESHOLDS:
-        mrec, _ = extract_batches(ctx, cdvs, val, cdvs.params(use_proposal=1, proposal_threshold=t))
-        r = recall(vkeys, mrec)
-        table.append((t, r))
-        print(f"threshold {t}: recall {r:.5f}", flush=True)
-        if r >= a.keep:
+        rs = [recall(k, extract_batches(ctx, cdvs, v, cdvs.params(use_proposal=1, proposal_threshold=t))[0])
+              for k, v in zip(vkeys, vals)]
+        table.append([t] + rs)
+        print(f"threshold {t}: recall " + ", ".join(f"{r:.5f}" for r in rs), flush=True)
+        if min(rs) >= a.keep:
             chosen = t
             break
     if chosen is None:
         chosen = THRESHOLDS[-1]
     np.savez(a.out, theta=th, threshold=np.float32(chosen), loss_history=np.array(hist, np.float64),
              recall_table=np.array(table, np.float64),
-             config=np.array([a.train, a.val, a.batch, a.epochs, a.lr, a.keep], np.float64),
+             config=np.array([a.train, a.val, a.batch, a.epochs, a.lr, a.keep, a.zoom], np.float64),
              seconds=np.array([t_gen, t_train], np.float64))
     print(f"wrote {a.out}: threshold {chosen}, gen {t_gen:.1f} s, train {t_train:.1f} s", flush=True)
 
