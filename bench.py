@@ -369,7 +369,8 @@ def run_learned(ctx, imgs, step_with, p_plain, args, cdvs, torch, plain_kp):
             "first_octave_tiles": {"detect": int(counts[2]), "levels_only": int(counts[1]),
                                    "level3_only": int(counts[0])},
             "stage_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
-            "weights": "paper_1705_09776_gb300/proposal_weights.npz (train_proposal.py; images of seeds 1e6+i)"}
+            "weights": "paper_1705_09776_gb300/proposal_weights.npz (train_proposal.py; images of seeds 1e6+i and, "
+                       "with the high-resolution statistics, 5e6+i)"}
 
 
 def _gen_uneven(args):
@@ -551,7 +552,7 @@ def highres_leg(ctx, cdvs, torch, imgs, args, alu_peak, steps=None):
     tuning = ctx.detect_tuning()
     learned = None
     if os.path.exists(cdvs.PROPOSAL_WEIGHTS):
-        theta, thr = cdvs.load_proposal_weights()
+        theta, thr = cdvs.load_proposal_weights(highres=True)
         ctx.set_proposal(theta)
         pl = cdvs.params(num_octaves=6, max_keypoints=N, storage=cdvs.CDVS_STORAGE_FP16, use_proposal=1,
                          proposal_threshold=thr)

@@ -50,10 +50,13 @@ PROPOSAL_PARAMS = 4817
 PROPOSAL_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "proposal_weights.npz")
 
 
-def load_proposal_weights(path=None):
-    """(theta, threshold) of a trained block proposal (train_proposal.py)."""
+def load_proposal_weights(path=None, highres=False):
+    """(theta, threshold) of a trained block proposal (train_proposal.py): the
+    threshold chosen on 640 x 480 images, or with highres=True the one chosen
+    on images with the high-resolution workload's statistics."""
     d = np.load(path or PROPOSAL_WEIGHTS)
-    return d["theta"].astype(np.float32), float(d["threshold"])
+    key = "threshold_zoom" if highres and "threshold_zoom" in d else "threshold"
+    return d["theta"].astype(np.float32), float(d[key])
 
 EXPORTED = ["cdvs_params_default", "cdvs_create", "cdvs_destroy", "cdvs_last_error", "cdvs_extract",
             "cdvs_candidates", "cdvs_dedupe_select", "cdvs_describe", "cdvs_scale_space",

@@ -9,12 +9,14 @@ blob images (seeds 1000000 + i for training, 3000000 + i for choosing the
 threshold).  A fraction of them (--zoom) carries the statistics of the
 high-resolution workload at 640 x 480: the blobs 3.2 times larger and as
 many per pixel as in a 2048 x 1536 image (200 / 10.24 of them), so one
-network serves both scales; the threshold must keep the records of both
-kinds of validation image.  Training runs the library's own forward, backward and Adam
-kernels (cdvs_proposal_train_step, BF16 as in inference).  The threshold is
-the largest of a fixed list whose masked extraction keeps at least
-`--keep` of the plain detector's records on the validation images.  The
-output .npz holds `theta` (FP32), `threshold` and the training record.
+network serves both scales.  Training runs the library's own forward,
+backward and Adam kernels (cdvs_proposal_train_step, BF16 as in
+inference).  Each kind of validation image gets its own threshold: the
+largest of a fixed list whose masked extraction keeps at least `--keep` of
+the plain detector's records on those images.  The
+output .npz holds `theta` (FP32), `threshold` (640 x 480 images),
+`threshold_zoom` (images with the high-resolution statistics) and the
+training record.
 """
 from __future__ import annotations
 
@@ -153,26 +155,29 @@ def main(argv=None):
     t_train = time.time() - t1
     th = theta.cpu().numpy()
 
-    # threshold: the largest whose masked extraction keeps `keep` of the
-    # records of every kind of validation image
+    # thresholds: per kind of validation image, the largest whose masked
+    # extraction keeps `keep` of the plain detector's records
     ctx.set_proposal(th)
     vkeys = [record_keys(extract_batches(ctx, cdvs, v, plain)[0]) for v in vals]
-    chosen, table = None, []
+    chosen = [None] * len(vals)
+    table = []
     for t in THRESHOLDS:
         rs = [recall(k, extract_batches(ctx, cdvs, v, cdvs.params(use_proposal=1, proposal_threshold=t))[0])
               for k, v in zip(vkeys, vals)]
         table.append([t] + rs)
         print(f"threshold {t}: recall " + ", ".join(f"{r:.5f}" for r in rs), flush=True)
-        if min(rs) >= a.keep:
-            chosen = t
+        for j, r in enumerate(rs):
+            if chosen[j] is None and r >= a.keep:
+                chosen[j] = t
+        if all(c is not None for c in chosen):
             break
-    if chosen is None:
-        chosen = THRESHOLDS[-1]
-    np.savez(a.out, theta=th, threshold=np.float32(chosen), loss_history=np.array(hist, np.float64),
+    chosen = [THRESHOLDS[-1] if c is None else c for c in chosen]
+    np.savez(a.out, theta=th, threshold=np.float32(chosen[0]),
+             threshold_zoom=np.float32(chosen[-1]), loss_history=np.array(hist, np.float64),
              recall_table=np.array(table, np.float64),
              config=np.array([a.train, a.val, a.batch, a.epochs, a.lr, a.keep, a.zoom], np.float64),
              seconds=np.array([t_gen, t_train], np.float64))
-    print(f"wrote {a.out}: threshold {chosen}, gen {t_gen:.1f} s, train {t_train:.1f} s", flush=True)
+    print(f"wrote {a.out}: thresholds {chosen}, gen {t_gen:.1f} s, train {t_train:.1f} s", flush=True)
 
 
 if __name__ == "__main__":

@@ -220,3 +220,27 @@ def test_entry_point_argument_errors(env):
         ctx.extract(img, cdvs.params(use_proposal=1, proposal_threshold=1.5))
     assert e.value.status == cdvs.CDVS_INVALID_ARGUMENT
     ctx.close()
+
+
+def test_trained_proposal_recall_at_high_resolution(env):
+    """The same network on held-out 2048 x 1536 images of the high-resolution
+    workload (blobs x3.2, 6 octaves, N = 2000, FP16 levels), at the threshold
+    chosen on images with those statistics: the masked extraction keeps >= 99%
+    of the plain extraction's records, bit-exact."""
+    cdvs, ctx, torch = env
+    theta, thr = cdvs.load_proposal_weights(highres=True)
+    k = 2048 * 1536 / (640 * 480)
+    imgs = [synth.blob_image(synth.image_seed(7, i), 2048, 1536, n_blobs=int(round(200 * k)),
+                             sigma_range=(1.5 * 3.2, 20.0 * 3.2)) for i in range(2)]
+    p = dict(num_octaves=6, max_keypoints=2000, storage=cdvs.CDVS_STORAGE_FP16)
+    plain, _, _, _ = ctx.extract(imgs, cdvs.params(**p))
+    ctx.set_proposal(theta)
+    masked, _, _, _ = ctx.extract(imgs, cdvs.params(use_proposal=1, proposal_threshold=thr, **p))
+
+    def keys(r):
+        return set(map(tuple, np.stack([r["image"], r["octave"], r["x"].view(np.int32), r["y"].view(np.int32),
+                                        r["sigma"].view(np.int32), r["theta"].view(np.int32)], 1).tolist()))
+    recall = len(keys(plain) & keys(masked)) / len(keys(plain))
+    import parity as PT
+    PT.report("proposal recall 2048x1536", threshold=thr, records=len(plain), recall=round(recall, 5))
+    assert recall >= 0.99, recall
