@@ -396,7 +396,10 @@ cdvs_status cdvs_proposal_train_step(cdvs_ctx *ctx, const uint8_t *images, int32
  * for the 512 components, the components ranked by delta (descending, ties to
  * the lower index), and bit k of the word of each of the first n_select
  * ranked components set when g_mu(i)_k > 0.  An image with no descriptor
- * gives zero gradients.  All arithmetic is FP32.
+ * gives zero gradients.  The two contractions (Eq. 10, and Eq. 12/14's
+ * Gamma^T [1 | y | y^2]) run on the tensor cores with operands split in two
+ * halves and three products per term (about 21 significant bits per
+ * product, FP32 accumulation); everything else is FP32.
  * ------------------------------------------------------------------------- */
 #define CDVS_SCFV_COMPONENTS 512
 #define CDVS_SCFV_DIM 32
@@ -409,7 +412,11 @@ typedef struct {
     const float *variances;  /* 512 x 32, positive (diagonal) */
 } cdvs_scfv_model;
 
-/* Copies a model (host memory) into the context. */
+/* Copies a model (host memory) into the context.  INVALID_ARGUMENT unless the
+ * weights and variances are positive, the PCA mean has norm <= 2 and every
+ * PCA row norm <= 64 (an orthonormal PCA has norm 1; the bound keeps the
+ * projections of unit descriptors within the range of the gradient
+ * products' FP16 halves). */
 cdvs_status cdvs_set_scfv_model(cdvs_ctx *ctx, const cdvs_scfv_model *model);
 
 /* SCFV of a batch.  desc: the records' descriptors packed over the batch as

@@ -1636,6 +1636,17 @@ cdvs_status cdvs_set_scfv_model(cdvs_ctx* c, const cdvs_scfv_model* m) {
   if (!m || !m->pca_mean || !m->pca || !m->weights || !m->means || !m->variances)
     return fail(c, CDVS_INVALID_ARGUMENT, "NULL model array");
   std::vector<float> d(kScfvModelFloats);
+  // the gradient products take [1 | y | y^2] in FP16 halves: bounded PCA
+  // rows (orthonormal ones have norm 1) and mean keep |y| <= 2 * 64 for unit
+  // descriptors, so y^2 stays far inside FP16's range
+  double mean2 = 0.0;
+  for (int k = 0; k < 128; ++k) mean2 += (double)m->pca_mean[k] * m->pca_mean[k];
+  if (!(mean2 <= 4.0)) return fail(c, CDVS_INVALID_ARGUMENT, "the PCA mean must have norm <= 2");
+  for (int j = 0; j < kScfvDim; ++j) {
+    double r2 = 0.0;
+    for (int k = 0; k < 128; ++k) r2 += (double)m->pca[j * 128 + k] * m->pca[j * 128 + k];
+    if (!(r2 <= 64.0 * 64.0)) return fail(c, CDVS_INVALID_ARGUMENT, "PCA rows must have norm <= 64");
+  }
   for (int k = 0; k < 128; ++k) {
     d[kScfvOffMean + k] = m->pca_mean[k];
     for (int j = 0; j < kScfvDim; ++j) d[kScfvOffPcaT + k * kScfvDim + j] = m->pca[j * 128 + k];

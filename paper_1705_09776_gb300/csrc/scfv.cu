@@ -18,11 +18,14 @@
 //     L = [y^2 | y] W + c, with W = [-1/(2v); mu/v] (64 x 512);
 //   * per image, S = Gamma^T [1 | y | y^2] (512 x 65), from which
 //     g_mu = (S_y - mu S_1) / s and g_sigma = (S_yy - 2 mu S_y + mu^2 S_1) / v - S_1.
-// Both use mma.sync m16n8k8 with TF32 operands split in two (x = hi + lo,
-// hi and lo both TF32) and three products per term (hi hi + hi lo + lo hi),
-// accumulated in FP32: about 21 significant bits per product, so the
-// softmax, which needs the log-likelihood to ~1e-5 absolute, stays within
-// FP32-level error.  The softmax and every reduction run in a fixed order.
+// Both split their operands in two (x = hi + lo) and take three products per
+// term (hi hi + hi lo + lo hi), accumulated in FP32: about 21 significant
+// bits per product, so the softmax, which needs the log-likelihood to ~1e-5
+// absolute, stays within FP32-level error.  The log-likelihoods use TF32
+// halves (mma.sync m16n8k8: the model's 1/v can be large, and TF32 keeps
+// FP32's range); the gradient products use FP16 halves (m16n8k16, twice the
+// rate; every operand there is bounded).  The softmax and every reduction
+// run in a fixed order.
 #include <algorithm>
 
 #include "cdvs_internal.cuh"
@@ -262,87 +265,165 @@ __global__ void __launch_bounds__(kPostThreads, 1) scfv_post_kernel(const float*
 }
 
 // K_c: Fisher gradients as per-image products S = Gamma^T [1 | y | y^2]
-// (512 x 65, padded to 72 columns).  CTA = 128 components of one image,
-// warp w = components 16w .. 16w + 15 of them (one 16-row tile), all nine
-// 8-column tiles; the image's records go through in chunks of 32 (four
-// 8-deep k-steps), staged in shared memory (the [1 | y | y^2] chunk already
-// split into TF32 hi / lo, once for all warps).  Then the gradients from S.
-constexpr int kGradBlock = 128, kGradChunk = 32, kGradThreads = 256, kZCols = 72, kQPitch = 136, kSPitch = 73;
-constexpr int kGradSmemFloats = kGradChunk * (kQPitch + 2 * kZCols) + kGradBlock * kSPitch;
+// (512 x 65, padded to 72 columns), one CTA per image: warp w owns
+// components 32w .. 32w + 31 (two 16-row tiles) and all nine 8-column tiles.
+// The image's records go through in chunks of 32 (two 16-deep k-steps); the
+// chunk's posteriors arrive by asynchronous copies, double-buffered, while
+// the previous chunk is multiplied.  Operands are split into FP16 hi / lo
+// (x = hi + lo, 22 significant bits; posteriors lie in [0, 1] and
+// [1 | y | y^2] within +-4 for the projections of unit descriptors on the
+// orthonormal PCA rows, far inside FP16's range) and multiplied by
+// mma.sync m16n8k16 with FP32 accumulation, three products per term.  The
+// [1 | y | y^2] chunk is split once, into shared memory, for all warps.
+// Fragment layouts of m16n8k16 (f16): lane = 4 g + t; A register q holds
+// row g + 8 (q & 1), columns 2t + 8 (q >> 1) + {0, 1}; B register q holds
+// rows 2t + 8 q + {0, 1}, column g; C as for m16n8k8.
+constexpr int kGradChunk = 32, kGradThreads = 512, kZCols = 72, kQPitch = kComp + 8, kSPitch = 73;
+// dynamic shared memory (32-bit words): two posterior chunks | Z hi, lo as
+// record pairs | (after the loop) S for 256 components at a time
+constexpr int kGradQWords = kGradChunk * kQPitch;
+constexpr int kGradZWords = (kGradChunk / 2) * kZCols;
+constexpr int kGradSmemWords = 2 * kGradQWords + 2 * kGradZWords;
+static_assert(256 * kSPitch <= 2 * kGradQWords, "S of 256 components fits the posterior buffers");
 
-__global__ void __launch_bounds__(kGradThreads) scfv_grad_kernel(const float* Y, const float* Q, const int* rec_off,
-                                                                 const float* model, float* g_mu, float* g_sig) {
+__device__ __forceinline__ void split_h2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+  const __half2 h = __floats2half2_rn(x0, x1);
+  const float2 f = __half22float2(h);
+  const __half2 l = __floats2half2_rn(x0 - f.x, x1 - f.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+__device__ __forceinline__ void mma_f16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+               "{%0,%1,%2,%3};"
+               : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+               : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<unsigned>(__cvta_generic_to_shared(dst))),
+               "l"(src)
+               : "memory");
+}
+
+// Posteriors of records c0 .. c0 + nr - 1 (nr <= 32) into a chunk buffer;
+// the rows past nr are zeroed.
+__device__ __forceinline__ void load_q_chunk(const float* Q, int c0, int nr, float* qs) {
+  for (int e = threadIdx.x; e < kGradChunk * kComp / 4; e += kGradThreads) {
+    const int r = e / (kComp / 4), c4 = e - r * (kComp / 4);
+    float* dst = qs + r * kQPitch + 4 * c4;
+    if (r < nr) cp_async16(dst, Q + (size_t)(c0 + r) * kComp + 4 * c4);
+    else *reinterpret_cast<float4*>(dst) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kGradThreads, 1) scfv_grad_kernel(const float* Y, const float* Q, const int* rec_off,
+                                                                    const float* model, float* g_mu, float* g_sig) {
   extern __shared__ float4 gsm4[];
-  float* const base = reinterpret_cast<float*>(gsm4);
-  float (*qs)[kQPitch] = reinterpret_cast<float (*)[kQPitch]>(base);
-  uint32_t (*zh)[kZCols] = reinterpret_cast<uint32_t (*)[kZCols]>(base + kGradChunk * kQPitch);
-  uint32_t (*zl)[kZCols] = reinterpret_cast<uint32_t (*)[kZCols]>(base + kGradChunk * (kQPitch + kZCols));
-  float (*S)[kSPitch] = reinterpret_cast<float (*)[kSPitch]>(base + kGradChunk * (kQPitch + 2 * kZCols));
-  const int b = blockIdx.y, i0 = blockIdx.x * kGradBlock;
+  float* const qbuf = reinterpret_cast<float*>(gsm4);                       // 2 x [32][kQPitch]
+  uint32_t* const zh = reinterpret_cast<uint32_t*>(qbuf + 2 * kGradQWords);  // [16 record pairs][72]
+  uint32_t* const zl = zh + kGradZWords;
+  const int b = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
   const int t0 = rec_off[b], t1 = rec_off[b + 1];
-  float acc[kZCols / 8][4];
+  float acc[2][kZCols / 8][4];
 #pragma unroll
-  for (int j = 0; j < kZCols / 8; ++j)
+  for (int m = 0; m < 2; ++m)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[j][q] = 0.0f;
-  for (int c0 = t0; c0 < t1; c0 += kGradChunk) {
+    for (int j = 0; j < kZCols / 8; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[m][j][q] = 0.0f;
+  if (t0 < t1) load_q_chunk(Q, t0, min(kGradChunk, t1 - t0), qbuf);
+  for (int c0 = t0, buf = 0; c0 < t1; c0 += kGradChunk, buf ^= 1) {
     const int nr = min(kGradChunk, t1 - c0);
-    __syncthreads();
-    for (int e = tid; e < kGradChunk * kGradBlock / 4; e += kGradThreads) {
-      const int r = e / (kGradBlock / 4), c4 = e - r * (kGradBlock / 4);
-      const float4 v = r < nr ? reinterpret_cast<const float4*>(Q + (size_t)(c0 + r) * kComp + i0)[c4]
-                              : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-      *reinterpret_cast<float4*>(&qs[r][4 * c4]) = v;
-    }
-    for (int e = tid; e < kGradChunk * kZCols; e += kGradThreads) {
-      const int r = e / kZCols, c = e - r * kZCols;
-      float z = 0.0f;
-      if (r < nr) {
-        if (c == 0) z = 1.0f;
-        else if (c <= kDim) z = Y[(size_t)(c0 + r) * kDim + c - 1];
-        else if (c <= 2 * kDim) {
-          const float y = Y[(size_t)(c0 + r) * kDim + c - 1 - kDim];
-          z = y * y;
+    // [1 | y | y^2] of the chunk, split, as record pairs (every warp is past
+    // the previous chunk's products: the barrier at the end of the loop)
+    for (int e = tid; e < kGradZWords; e += kGradThreads) {
+      const int rp = e / kZCols, c = e - rp * kZCols;
+      float z[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = 2 * rp + h;
+        z[h] = 0.0f;
+        if (r < nr) {
+          if (c == 0) z[h] = 1.0f;
+          else if (c <= kDim) z[h] = Y[(size_t)(c0 + r) * kDim + c - 1];
+          else if (c <= 2 * kDim) {
+            const float y = Y[(size_t)(c0 + r) * kDim + c - 1 - kDim];
+            z[h] = y * y;
+          }
         }
       }
-      split_tf32(z, zh[r][c], zl[r][c]);
+      split_h2(z[0], z[1], zh[e], zl[e]);
+    }
+    // the next chunk's posteriors on their way; this chunk's have landed
+    if (c0 + kGradChunk < t1) {
+      load_q_chunk(Q, c0 + kGradChunk, min(kGradChunk, t1 - c0 - kGradChunk), qbuf + (buf ^ 1) * kGradQWords);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
     __syncthreads();
+    const float* qs = qbuf + buf * kGradQWords;
 #pragma unroll
-    for (int s = 0; s < kGradChunk / 8; ++s) {
-      // A = Gamma^T: rows = this warp's 16 components, columns = 8 records
-      uint32_t ah[4], al[4];
+    for (int s = 0; s < kGradChunk / 16; ++s) {
+      // A = Gamma^T: rows = components 32 warp + 16 m .., columns = records 16 s ..
+      uint32_t ah[2][4], al[2][4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        split_tf32(qs[8 * s + t + 4 * (q >> 1)][16 * warp + g + 8 * (q & 1)], ah[q], al[q]);
+      for (int m = 0; m < 2; ++m)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int c = 32 * warp + 16 * m + g + 8 * (q & 1);
+          const int r = 16 * s + 2 * t + 8 * (q >> 1);
+          split_h2(qs[r * kQPitch + c], qs[(r + 1) * kQPitch + c], ah[m][q], al[m][q]);
+        }
 #pragma unroll
       for (int j = 0; j < kZCols / 8; ++j) {
-        const uint32_t bh[2] = {zh[8 * s + t][8 * j + g], zh[8 * s + t + 4][8 * j + g]};
-        const uint32_t bl[2] = {zl[8 * s + t][8 * j + g], zl[8 * s + t + 4][8 * j + g]};
-        mma3(acc[j], ah, al, bh, bl);
+        const int rp = 8 * s + t, col = 8 * j + g;
+        const uint32_t bh[2] = {zh[rp * kZCols + col], zh[(rp + 4) * kZCols + col]};
+        const uint32_t bl[2] = {zl[rp * kZCols + col], zl[(rp + 4) * kZCols + col]};
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+          mma_f16(acc[m][j], al[m], bh);
+          mma_f16(acc[m][j], ah[m], bl);
+          mma_f16(acc[m][j], ah[m], bh);
+        }
       }
     }
+    __syncthreads();  // the chunk's buffers are rewritten next
   }
-  // S rows = components of this CTA, columns = [1 | y | y^2 | pad]
-#pragma unroll
-  for (int j = 0; j < kZCols / 8; ++j) {
-    S[16 * warp + g][8 * j + 2 * t] = acc[j][0];
-    S[16 * warp + g][8 * j + 2 * t + 1] = acc[j][1];
-    S[16 * warp + g + 8][8 * j + 2 * t] = acc[j][2];
-    S[16 * warp + g + 8][8 * j + 2 * t + 1] = acc[j][3];
-  }
-  __syncthreads();
+  // S rows = components, columns = [1 | y | y^2 | pad], 256 components at a
+  // time in the posterior buffers, then the gradients
   const int K = t1 - t0;
   const float inv = K > 0 ? 1.0f / (float)K : 0.0f;
-  for (int e = tid; e < kGradBlock * kDim; e += kGradThreads) {
-    const int il = e / kDim, k = e - il * kDim, i = i0 + il;
-    const float s0 = S[il][0], s1 = S[il][1 + k], s2 = S[il][1 + kDim + k];
-    const float mu = model[kScfvOffMu + i * kDim + k], isd = model[kScfvOffIsd + i * kDim + k];
-    const float nm = inv * model[kScfvOffNmu + i], ns = inv * model[kScfvOffNsig + i];
-    const size_t o = ((size_t)b * kComp + i) * kDim + k;
-    g_mu[o] = nm * isd * fmaf(-mu, s0, s1);
-    g_sig[o] = ns * fmaf(isd * isd, fmaf(mu, fmaf(mu, s0, -2.0f * s1), s2), -s0);
+  float* const S = qbuf;
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    if ((warp >> 3) == half) {
+      const int rl = 32 * (warp & 7);
+#pragma unroll
+      for (int m = 0; m < 2; ++m)
+#pragma unroll
+        for (int j = 0; j < kZCols / 8; ++j) {
+          S[(rl + 16 * m + g) * kSPitch + 8 * j + 2 * t] = acc[m][j][0];
+          S[(rl + 16 * m + g) * kSPitch + 8 * j + 2 * t + 1] = acc[m][j][1];
+          S[(rl + 16 * m + g + 8) * kSPitch + 8 * j + 2 * t] = acc[m][j][2];
+          S[(rl + 16 * m + g + 8) * kSPitch + 8 * j + 2 * t + 1] = acc[m][j][3];
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < 256 * kDim; e += kGradThreads) {
+      const int il = e / kDim, k = e - il * kDim, i = 256 * half + il;
+      const float s0 = S[il * kSPitch], s1 = S[il * kSPitch + 1 + k], s2 = S[il * kSPitch + 1 + kDim + k];
+      const float mu = model[kScfvOffMu + i * kDim + k], isd = model[kScfvOffIsd + i * kDim + k];
+      const float nm = inv * model[kScfvOffNmu + i], ns = inv * model[kScfvOffNsig + i];
+      const size_t o = ((size_t)b * kComp + i) * kDim + k;
+      g_mu[o] = nm * isd * fmaf(-mu, s0, s1);
+      g_sig[o] = ns * fmaf(isd * isd, fmaf(mu, fmaf(mu, s0, -2.0f * s1), s2), -s0);
+    }
+    __syncthreads();
   }
 }
 
@@ -396,11 +477,10 @@ cudaError_t launch_scfv(const float* desc, int n_rec, const int* rec_off, int n_
     scfv_post_kernel<<<std::max(1, std::min((n_rec + kPostTile - 1) / kPostTile, n_sms)), kPostThreads, pbytes, s>>>(
         desc, n_rec, model, Y, Q);
   }
-  const int gbytes = (int)(sizeof(float) * kGradSmemFloats);
+  const int gbytes = (int)(sizeof(float) * kGradSmemWords);
   cudaError_t e = cudaFuncSetAttribute(scfv_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, gbytes);
   if (e != cudaSuccess) return e;
-  scfv_grad_kernel<<<dim3(kComp / kGradBlock, n_images), kGradThreads, gbytes, s>>>(Y, Q, rec_off, model, g_mu,
-                                                                                     g_sig);
+  scfv_grad_kernel<<<n_images, kGradThreads, gbytes, s>>>(Y, Q, rec_off, model, g_mu, g_sig);
   scfv_rank_kernel<<<n_images, kComp, 0, s>>>(g_mu, n_select, delta, order, bits);
   return cudaGetLastError();
 }
