@@ -277,7 +277,7 @@ cdvs_status cdvs_transform_ternary(const float *desc, int32_t n, const double *t
  * serialise the capture).
  *
  * Its scratch (converted candidates, cell order, check flags, selected
- * points; about 660 KB) is a fixed array inside the library, so every GPU
+ * points; about 930 KB) is a fixed array inside the library, so every GPU
  * that loads the library keeps that much device memory until the process
  * exits.  The first call on a device looks the array's device address up
  * (cudaGetSymbolAddress); make that first call before any stream capture (a

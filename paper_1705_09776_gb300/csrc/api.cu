@@ -74,7 +74,7 @@ struct cdvs_ctx {
   int device = 0;
   int n_sms = 0;
   std::string err;
-  DevBuf levels, cands, cand_count, order, keep, sel, sel_count, ori_theta, ori_count, rec_off,
+  DevBuf levels, cands, cand_count, order, keep, skey, soct, sel, sel_count, ori_theta, ori_count, rec_off,
       rec_total, plans, tile_prefix, status, input, dump, stage_kp, stage_desc;
   // learned block proposal: parameters, per-call image table, logits, tile modes, training workspace
   DevBuf prop_theta, prop_imgs, prop_logits, prop_mode, prop_ws;
@@ -978,6 +978,8 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
       (e = ensure(c->cand_count, sizeof(int) * n)) != cudaSuccess ||
       (e = ensure(c->order, sizeof(int) * (size_t)n * cap)) != cudaSuccess ||
       (e = ensure(c->keep, (size_t)n * cap)) != cudaSuccess ||
+      (e = ensure(c->skey, sizeof(float4) * (size_t)n * cap)) != cudaSuccess ||
+      (e = ensure(c->soct, (size_t)n * cap)) != cudaSuccess ||
       (e = ensure(c->sel, sizeof(Cand) * slots)) != cudaSuccess ||
       (e = ensure(c->sel_count, sizeof(int) * n)) != cudaSuccess ||
       (e = ensure(c->ori_theta, sizeof(float) * slots * kMaxOri)) != cudaSuccess ||
@@ -1121,6 +1123,8 @@ cdvs_status run(cdvs_ctx* c, Mode mode, int n, const uint8_t* const* images, con
     a.cand_cap = cap;
     a.order = static_cast<int*>(c->order.p);
     a.keep = static_cast<unsigned char*>(c->keep.p);
+    a.skey = static_cast<float4*>(c->skey.p);
+    a.soct = static_cast<unsigned char*>(c->soct.p);
     a.sel = static_cast<Cand*>(c->sel.p);
     a.sel_count = static_cast<int*>(c->sel_count.p);
     a.N = N;
@@ -1328,7 +1332,7 @@ cdvs_status cdvs_create(cdvs_ctx** out, int device, size_t workspace_bytes_hint)
 void cdvs_destroy(cdvs_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
-  DevBuf* bufs[] = {&c->levels,  &c->cands,   &c->cand_count, &c->order,   &c->keep,
+  DevBuf* bufs[] = {&c->levels,  &c->cands,   &c->cand_count, &c->order,   &c->keep, &c->skey, &c->soct,
                     &c->sel,     &c->sel_count, &c->ori_theta, &c->ori_count, &c->rec_off,
                     &c->rec_total, &c->plans,
                     &c->tile_prefix, &c->status, &c->input, &c->dump, &c->stage_kp, &c->stage_desc,
@@ -1443,6 +1447,7 @@ cdvs_status cdvs_dedupe_select(cdvs_ctx* c, int32_t n, const cdvs_image_desc* si
   if ((e = ensure(c->cands, sizeof(Cand) * h.size())) != cudaSuccess ||
       (e = ensure(c->cand_count, sizeof(int) * n)) != cudaSuccess ||
       (e = ensure(c->order, sizeof(int) * h.size())) != cudaSuccess || (e = ensure(c->keep, h.size())) != cudaSuccess ||
+      (e = ensure(c->skey, sizeof(float4) * h.size())) != cudaSuccess || (e = ensure(c->soct, h.size())) != cudaSuccess ||
       (e = ensure(c->sel, sizeof(Cand) * (size_t)n * N)) != cudaSuccess ||
       (e = ensure(c->sel_count, sizeof(int) * n)) != cudaSuccess ||
       (e = ensure(c->status, sizeof(int) * 4)) != cudaSuccess ||
@@ -1464,6 +1469,8 @@ cdvs_status cdvs_dedupe_select(cdvs_ctx* c, int32_t n, const cdvs_image_desc* si
   a.cand_cap = cap;
   a.order = static_cast<int*>(c->order.p);
   a.keep = static_cast<unsigned char*>(c->keep.p);
+  a.skey = static_cast<float4*>(c->skey.p);
+  a.soct = static_cast<unsigned char*>(c->soct.p);
   a.sel = static_cast<Cand*>(c->sel.p);
   a.sel_count = static_cast<int*>(c->sel_count.p);
   a.N = N;

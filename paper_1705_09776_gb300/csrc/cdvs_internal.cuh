@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "../../include/cdvs.h"
 
 namespace cdvs {
@@ -104,8 +106,10 @@ struct SelectArgs {
   const Cand* cands;
   const int* cand_count;
   int cand_cap;
-  int* order;              // scratch n_images x cand_cap
+  int* order;              // scratch n_images x cand_cap: candidate index at each cell-sorted position
   unsigned char* keep;     // scratch n_images x cand_cap
+  float4* skey;            // scratch n_images x cand_cap: cell-sorted (x, y, sigma in image px, |response|)
+  unsigned char* soct;     // scratch n_images x cand_cap: cell-sorted octaves
   Cand* sel;               // n_images x N
   int* sel_count;
   int N;
@@ -149,6 +153,47 @@ struct DescribeArgs {
   int* base_out;
   int last_group;               // 1: the scan also writes the batch total and the truncation bit
 };
+
+// Host-side launch set-up of one kernel, per device: the largest dynamic
+// shared memory it was allowed so far and its occupancy at the last size
+// asked.  cudaFuncSetAttribute and the occupancy query cost microseconds of
+// host time each, which a call of one small image would pay at every launch;
+// here they run once per kernel, device and size.
+struct LaunchCache {
+  static constexpr int kDevices = 16;
+  std::mutex m;
+  int smem_set[kDevices] = {};
+  int occ_for[kDevices] = {};  // shared memory + 1 of the cached occupancy (0: none)
+  int occ[kDevices] = {};
+};
+
+// Allows `smem` bytes of dynamic shared memory for `func` on the current
+// device and, when per_sm is given, returns how many CTAs of `threads`
+// threads fit on an SM.
+template <typename F>
+cudaError_t prepare_launch(F* func, LaunchCache& c, int smem, int threads, int* per_sm) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= LaunchCache::kDevices) {
+    if ((e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+    return per_sm ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, func, threads, smem) : cudaSuccess;
+  }
+  std::lock_guard<std::mutex> lock(c.m);
+  if (smem > c.smem_set[dev]) {
+    if ((e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+    c.smem_set[dev] = smem;
+  }
+  if (per_sm) {
+    if (c.occ_for[dev] != smem + 1) {
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ[dev], func, threads, smem)) != cudaSuccess)
+        return e;
+      c.occ_for[dev] = smem + 1;
+    }
+    *per_sm = c.occ[dev];
+  }
+  return cudaSuccess;
+}
 
 // launchers (defined in the .cu files)
 size_t detect_smem_bytes(int max_radius);

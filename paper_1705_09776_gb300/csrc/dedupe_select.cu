@@ -152,6 +152,8 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(const __grid_consta
   const Cand* C = a.cands + (size_t)img * a.cand_cap;
   int* order = a.order + (size_t)img * a.cand_cap;
   unsigned char* keep = a.keep + (size_t)img * a.cand_cap;
+  float4* skey = a.skey + (size_t)img * a.cand_cap;
+  unsigned char* soct = a.soct + (size_t)img * a.cand_cap;
 
   // ---- 1. cells of side cs (image px), cs >= 2^(n_oct-1)
   int cs = 1 << max(n_oct - 1, 0);
@@ -185,20 +187,24 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(const __grid_consta
     const int cy = min(max((int)floorf(C[i].yo * s * inv_cs), 0), gy - 1);
     const int pos = atomicAdd(cell + cy * gx + cx, 1);  // after this, cell[c] = end of cell c
     order[pos] = i;
+    // the compact copy the check reads, in cell order (the same products as
+    // the check would form from the record)
+    skey[pos] = make_float4(C[i].xo * s, C[i].yo * s, C[i].so * s, fabsf(C[i].resp));
+    soct[pos] = (unsigned char)C[i].octave;
   }
   __syncthreads();
 
-  // ---- 2. cross-octave duplicates
+  // ---- 2. cross-octave duplicates, walked in cell order: neighbouring lanes
+  // take neighbouring candidates, so they read the same runs of the sorted
+  // copy (cached lines), and no read depends on another
+  for (int i = tid; i < n; i += kSelThreads)
+    if (!valid(i)) keep[i] = 0;
+  const int nv = cell[ncell - 1];  // candidates that took part in the sort
   int kept_local = 0;
-  for (int i = tid; i < n; i += kSelThreads) {
-    if (!valid(i)) {
-      keep[i] = 0;
-      continue;
-    }
-    const Cand ca = C[i];
-    const float sa = (float)(1 << ca.octave);
-    const float xa = ca.xo * sa, ya = ca.yo * sa, siga = ca.so * sa;
-    const float ra = fabsf(ca.resp);
+  for (int p = tid; p < nv; p += kSelThreads) {
+    const float4 ka = skey[p];
+    const int oa = soct[p];
+    const float xa = ka.x, ya = ka.y, siga = ka.z, ra = ka.w;
     const int cx = min(max((int)floorf(xa * inv_cs), 0), gx - 1);
     const int cy = min(max((int)floorf(ya * inv_cs), 0), gy - 1);
     bool k = true;
@@ -207,21 +213,21 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(const __grid_consta
         const int c = yy * gx + xx;
         const int beg = c == 0 ? 0 : cell[c - 1], end = cell[c];
         for (int j = beg; j < end; ++j) {
-          const Cand cb = C[order[j]];
-          const int d = ca.octave - cb.octave;
+          const int ob = soct[j];
+          const int d = oa - ob;
           if (d != 1 && d != -1) continue;
-          const float win = (float)(1 << max(ca.octave, (int)cb.octave));
-          const float sb = (float)(1 << cb.octave);
-          if (!(fabsf(xa - cb.xo * sb) <= win && fabsf(ya - cb.yo * sb) <= win)) continue;
-          if (!(fabsf(log2f(siga / (cb.so * sb))) <= a.dlog2)) continue;
-          const float rb = fabsf(cb.resp);
-          if (rb > ra || (rb == ra && cb.octave < ca.octave)) {
+          const float4 kb = skey[j];
+          const float win = (float)(1 << max(oa, ob));
+          if (!(fabsf(xa - kb.x) <= win && fabsf(ya - kb.y) <= win)) continue;
+          if (!(fabsf(log2f(siga / kb.z)) <= a.dlog2)) continue;
+          const float rb = kb.w;
+          if (rb > ra || (rb == ra && ob < oa)) {
             k = false;
             break;
           }
         }
       }
-    keep[i] = k ? 1 : 0;
+    keep[order[p]] = k ? 1 : 0;
     kept_local += k ? 1 : 0;
   }
   if (tid == 0) s_misc[0] = 0;
@@ -368,8 +374,8 @@ cudaError_t launch_select(const SelectArgs& args, int n_images, cudaStream_t s) 
   const size_t smem_cells = sizeof(int) * (kMaxCells + 1);
   const size_t smem_list = (sizeof(float4) + sizeof(int2)) * (size_t)a.list_cap;
   const size_t smem = smem_cells > smem_list ? smem_cells : smem_list;
-  cudaError_t e = cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  static LaunchCache cache;
+  cudaError_t e = prepare_launch(select_kernel, cache, (int)smem, kSelThreads, nullptr);
   if (e != cudaSuccess) return e;
   select_kernel<<<n_images, kSelThreads, smem, s>>>(a);
   return cudaGetLastError();

@@ -653,18 +653,17 @@ cudaError_t launch_describe(const DescribeArgs& a, int storage, int n_sms, cudaS
   const int slots = (a.img_end - a.img_begin) * a.N;
   if (slots <= 0) return cudaSuccess;
   const size_t smem = describe_smem_bytes(a.patch_side);
-  auto go = [&](auto kernel) -> cudaError_t {
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+  static LaunchCache cache32, cache16;
+  auto go = [&](auto kernel, LaunchCache& cache) -> cudaError_t {
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kFWarps * 32, smem);
+    cudaError_t e = prepare_launch(kernel, cache, (int)smem, kFWarps * 32, &per_sm);
     if (e != cudaSuccess) return e;
     const int need = (slots + kFWarps - 1) / kFWarps;
     const int grid = std::max(1, std::min(need, std::max(per_sm, 1) * n_sms));
     kernel<<<grid, kFWarps * 32, smem, s>>>(a);
     return cudaGetLastError();
   };
-  return storage == CDVS_STORAGE_FP16 ? go(describe_kernel<__half>) : go(describe_kernel<float>);
+  return storage == CDVS_STORAGE_FP16 ? go(describe_kernel<__half>, cache16) : go(describe_kernel<float>, cache32);
 }
 
 // The packing scratch (rec_off) holds local_off (n_images * N ints), then

@@ -930,10 +930,10 @@ template <typename S, typename IN, typename ST, int IC, bool M>
 static cudaError_t launch_variant(const DetectArgs& a, int n_tiles, int max_radius, int n_sms, cudaStream_t s) {
   const size_t smem = detect_smem<S>(max_radius, sizeof(IN), a.n_images);
   auto kern = detect_kernel<S, IN, ST, IC, M>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess || n_tiles <= 0) return e;  // no tiles: only the kernel's attributes are set up
+  static LaunchCache cache;
   int per_sm = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, S::THREADS, smem)) != cudaSuccess) return e;
+  cudaError_t e = prepare_launch(kern, cache, (int)smem, S::THREADS, &per_sm);
+  if (e != cudaSuccess || n_tiles <= 0) return e;  // no tiles: only the kernel's set-up
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int grid = n_tiles < n_sms * per_sm ? n_tiles : n_sms * per_sm;
   kern<<<grid, S::THREADS, smem, s>>>(a, max_radius, n_tiles);

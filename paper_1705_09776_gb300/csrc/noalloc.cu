@@ -25,7 +25,9 @@ constexpr int kMaxDevices = 64;
 
 struct NoAllocScratch {
   Cand cand[kNoAllocMax];            // the caller's candidates in octave px
+  float4 skey[kNoAllocMax];          // cell-sorted compact copies for the cross-octave check
   int order[kNoAllocMax];            // cell-sorted candidate indices
+  unsigned char soct[kNoAllocMax];   // cell-sorted octaves
   unsigned char keep[kNoAllocMax];   // cross-octave check result
   Cand sel[kMaxSelect];              // selected points in rank order
   ImgPlan plan;                      // size and octave count of the image
@@ -159,6 +161,8 @@ extern "C" cdvs_status cdvs_dedupe_select_noalloc(const cdvs_keypoint* cand, int
   a.cand_cap = kNoAllocMax;
   a.order = s->order;
   a.keep = s->keep;
+  a.skey = s->skey;
+  a.soct = s->soct;
   a.sel = s->sel;
   a.sel_count = &s->sel_count;
   a.N = params->max_keypoints;

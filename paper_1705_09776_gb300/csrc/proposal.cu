@@ -610,8 +610,8 @@ void pack_proposal_fragments(const float* theta, uint32_t* frag) {
 cudaError_t launch_proposal_infer(const PropImage* d_imgs, int n_images, int max_th, int max_tw, const float* theta,
                                   const uint32_t* frag, float* logits, cudaStream_t s) {
   if (n_images <= 0) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(proposal_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kInfSmem);
+  static LaunchCache cache;
+  cudaError_t e = prepare_launch(proposal_infer_kernel, cache, (int)kInfSmem, kInfThreads, nullptr);
   if (e != cudaSuccess) return e;
   dim3 grid((max_tw + kRBX - 1) / kRBX, (max_th + kRBY - 1) / kRBY, n_images);
   proposal_infer_kernel<<<grid, kInfThreads, kInfSmem, s>>>(d_imgs, theta, reinterpret_cast<const uint2*>(frag),

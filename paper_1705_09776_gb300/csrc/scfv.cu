@@ -472,13 +472,15 @@ cudaError_t launch_scfv(const float* desc, int n_rec, const int* rec_off, int n_
   if (n_images <= 0) return cudaSuccess;
   if (n_rec > 0) {
     const int pbytes = (int)(sizeof(float) * kPostSmemFloats);
-    cudaError_t e = cudaFuncSetAttribute(scfv_post_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pbytes);
+    static LaunchCache post_cache;
+    cudaError_t e = prepare_launch(scfv_post_kernel, post_cache, pbytes, kPostThreads, nullptr);
     if (e != cudaSuccess) return e;
     scfv_post_kernel<<<std::max(1, std::min((n_rec + kPostTile - 1) / kPostTile, n_sms)), kPostThreads, pbytes, s>>>(
         desc, n_rec, model, Y, Q);
   }
   const int gbytes = (int)(sizeof(float) * kGradSmemWords);
-  cudaError_t e = cudaFuncSetAttribute(scfv_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, gbytes);
+  static LaunchCache grad_cache;
+  cudaError_t e = prepare_launch(scfv_grad_kernel, grad_cache, gbytes, kGradThreads, nullptr);
   if (e != cudaSuccess) return e;
   scfv_grad_kernel<<<n_images, kGradThreads, gbytes, s>>>(Y, Q, rec_off, model, g_mu, g_sig);
   scfv_rank_kernel<<<n_images, kComp, 0, s>>>(g_mu, n_select, delta, order, bits);
