@@ -70,6 +70,14 @@ __device__ __forceinline__ float warp_sum(float v) {
 // vote is rounded by adding 1.5 * 2^23 in FP32 (exact for values below 2^22)
 // and reading the mantissa.
 constexpr int kFWarps = 8;
+// Descriptor bins: cell (y0, x0) and orientation o at y0 * kCellRow + x0 * 8 + o.
+// A cell row takes 36 words, not 32.  Lane l's run of disc pixels starts about
+// one disc row below lane l-1's, so at any step a warp's lanes lie on a line
+// across the disc, in several cell rows; with 32-word rows the same cell
+// column and orientation of every cell row would share a bank.
+constexpr int kCellRow = 36;
+constexpr int kHdWords = 4 * kCellRow;
+__device__ __forceinline__ int hd_index(int b) { return b + (b >> 5) * (kCellRow - 32); }
 constexpr float kPi = 3.14159265358979f;
 constexpr float kHalfPi = 1.57079632679490f;
 constexpr float kLog2e = 1.44269504088896f;
@@ -339,7 +347,7 @@ __device__ __forceinline__ void describe_point(const DescribeArgs& a, const Cand
   for (int j = 0; j < n_ori; ++j) {
     const float theta = thetas[j];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) hd[lane + 32 * q] = 0u;
+    for (int q = 0; q < 4; ++q) hd[hd_index(lane + 32 * q)] = 0u;
     __syncwarp();
     float st, ct;
     sincosf(theta, &st, &ct);
@@ -368,7 +376,7 @@ __device__ __forceinline__ void describe_point(const DescribeArgs& a, const Cand
       const float a0 = ws * (1.0f - fo), a1 = ws * fo;
       const bool x0ok = x0 >= 0, x1ok = x0 <= 2, y0ok = y0 >= 0, y1ok = y0 <= 2;
       const float wy0 = 1.0f - fy, wx0 = 1.0f - fx;
-      const int cb = (y0 * 4 + x0) * 8;
+      const int cb = y0 * kCellRow + x0 * 8;
       const int i0 = (o0 & 7) + cb, i1 = ((o0 + 1) & 7) + cb;
       if (y0ok && x0ok) {
         vote(hd + i0, wy0 * wx0, a0);
@@ -379,18 +387,18 @@ __device__ __forceinline__ void describe_point(const DescribeArgs& a, const Cand
         vote(hd + i1 + 8, wy0 * fx, a1);
       }
       if (y1ok && x0ok) {
-        vote(hd + i0 + 32, fy * wx0, a0);
-        vote(hd + i1 + 32, fy * wx0, a1);
+        vote(hd + i0 + kCellRow, fy * wx0, a0);
+        vote(hd + i1 + kCellRow, fy * wx0, a1);
       }
       if (y1ok && x1ok) {
-        vote(hd + i0 + 40, fy * fx, a0);
-        vote(hd + i1 + 40, fy * fx, a1);
+        vote(hd + i0 + kCellRow + 8, fy * fx, a0);
+        vote(hd + i1 + kCellRow + 8, fy * fx, a1);
       }
     });
     __syncwarp();
     float v[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = (float)hd[lane + 32 * q] / dsc;
+    for (int q = 0; q < 4; ++q) v[q] = (float)hd[hd_index(lane + 32 * q)] / dsc;
     float n2 = warp_sum(v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
     if (n2 > 0.0f) {
       const float inv = 1.0f / sqrtf(n2);
@@ -487,11 +495,11 @@ __global__ void __launch_bounds__(kFWarps * 32, 3) describe_kernel(const __grid_
   const int P = a.patch_side;
   float* patch = reinterpret_cast<float*>(smem4) + (size_t)warp * P * P;
   unsigned* hist = reinterpret_cast<unsigned*>(reinterpret_cast<float*>(smem4) + (size_t)kFWarps * P * P) +
-                   warp * (36 + 128 + kMaxOri + 3 * P);
+                   warp * (36 + kHdWords + kMaxOri + 3 * P);
   unsigned* ho = hist;        // 36 orientation bins
-  unsigned* hd = hist + 36;   // 128 descriptor bins
-  float* thetas = reinterpret_cast<float*>(hist + 36 + 128);  // the point's orientations
-  int* ru = reinterpret_cast<int*>(hist + 36 + 128 + kMaxOri);  // disc row tables, P rows each
+  unsigned* hd = hist + 36;   // 128 descriptor bins (at hd_index)
+  float* thetas = reinterpret_cast<float*>(hist + 36 + kHdWords);  // the point's orientations
+  int* ru = reinterpret_cast<int*>(hist + 36 + kHdWords + kMaxOri);  // disc row tables, P rows each
   int* rn = ru + P;
   int* rp = rn + P;
   const int S0 = a.img_begin * a.N, S1 = a.img_end * a.N;
@@ -644,7 +652,7 @@ __global__ void levels_to_f32_kernel(const StoreT* src, int Wi, int Hi, int tr, 
 
 size_t describe_smem_bytes(int patch_side) {
   return (size_t)kFWarps * ((size_t)patch_side * patch_side * sizeof(float) +
-                            (36 + 128 + kMaxOri + 3 * (size_t)patch_side) * sizeof(unsigned));
+                            (36 + kHdWords + kMaxOri + 3 * (size_t)patch_side) * sizeof(unsigned));
 }
 
 // Persistent grid: as many CTAs as fit on the SMs at once (never more than
