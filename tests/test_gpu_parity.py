@@ -3,7 +3,8 @@
 Inputs are the seeded synthetic images (paper_1705_09776_gb300.synth) at
 sizes the oracle finishes in seconds: several tiles and ragged tails (97x75,
 641x481, 333x257), the 640x480 workload image, the smallest supported size,
-and a portrait 300x700 whose second octave is stored transposed.  Tolerances
+the widest (32768x16) and a tall 16x4096 image, and a portrait 300x700 whose
+second octave is stored transposed.  Tolerances
 are those of tests/parity.py.
 """
 import math
@@ -18,7 +19,9 @@ import parity as PT
 
 pytestmark = pytest.mark.gpu
 
-SIZES = [(640, 480), (97, 75), (641, 481), (333, 257), (16, 16)]
+# the last two: the widest image the ABI takes (32768 columns, 256 tiles in a
+# row, the smallest height) and a tall one (16 columns, less than one tile)
+SIZES = [(640, 480), (97, 75), (641, 481), (333, 257), (16, 16), (32768, 16), (16, 4096)]
 # octaves past the first are stored transposed when that takes fewer tiles:
 # octaves 1-2 of 640 x 480 and 641 x 481 and octave 1 of this portrait size are
 TRANSPOSED = [(300, 700)]
@@ -71,7 +74,7 @@ def test_scale_space_levels(ctx, w, h):
 
 # ------------------------------------------------------------------ S2-S5
 
-@pytest.mark.parametrize("w,h", SIZES[:4] + TRANSPOSED)
+@pytest.mark.parametrize("w,h", SIZES[:4] + SIZES[5:] + TRANSPOSED)
 def test_candidates_bracketed_by_oracle(ctx, cd, w, h):
     img = _img(w, h, seed=2)
     g, cnt, st = ctx.candidates([img])
@@ -192,7 +195,7 @@ def test_describe_on_oracle_points(ctx, cd, w, h, upright):
 
 # ------------------------------------------------------------------ S1-S10
 
-@pytest.mark.parametrize("w,h", [(640, 480), (641, 481), (333, 257)])
+@pytest.mark.parametrize("w,h", [(640, 480), (641, 481), (333, 257), (32768, 16), (16, 4096)])
 def test_extract_end_to_end(ctx, cd, w, h):
     img = _img(w, h, seed=5)
     gk, gd, cnt, st = ctx.extract([img])
