@@ -398,8 +398,12 @@ cdvs_status cdvs_proposal_train_step(cdvs_ctx *ctx, const uint8_t *images, int32
  * ranked components set when g_mu(i)_k > 0.  An image with no descriptor
  * gives zero gradients.  The two contractions (Eq. 10, and Eq. 12/14's
  * Gamma^T [1 | y | y^2]) run on the tensor cores with operands split in two
- * halves and three products per term (about 21 significant bits per
- * product, FP32 accumulation); everything else is FP32.
+ * FP16 halves and three products per term (about 22 significant bits per
+ * product, FP32 accumulation; each component's column of Eq. 10's matrix is
+ * scaled by a power of two into FP16's range, exactly undone); everything
+ * else is FP32.  Should the tensor cores not complete a tile's products
+ * within a bounded wait, that tile's posteriors, and so the gradients of
+ * its images, come out NaN.
  * ------------------------------------------------------------------------- */
 #define CDVS_SCFV_COMPONENTS 512
 #define CDVS_SCFV_DIM 32
@@ -413,10 +417,10 @@ typedef struct {
 } cdvs_scfv_model;
 
 /* Copies a model (host memory) into the context.  INVALID_ARGUMENT unless the
- * weights and variances are positive, the PCA mean has norm <= 2 and every
+ * weights and variances are positive, the PCA mean has norm <= 2, every
  * PCA row norm <= 64 (an orthonormal PCA has norm 1; the bound keeps the
- * projections of unit descriptors within the range of the gradient
- * products' FP16 halves). */
+ * projections of unit descriptors within the range of the FP16 halves) and
+ * the derived log-likelihood terms 1/v and mu/v are finite. */
 cdvs_status cdvs_set_scfv_model(cdvs_ctx *ctx, const cdvs_scfv_model *model);
 
 /* SCFV of a batch.  desc: the records' descriptors packed over the batch as

@@ -1643,6 +1643,7 @@ cdvs_status cdvs_set_scfv_model(cdvs_ctx* c, const cdvs_scfv_model* m) {
   if (!m || !m->pca_mean || !m->pca || !m->weights || !m->means || !m->variances)
     return fail(c, CDVS_INVALID_ARGUMENT, "NULL model array");
   std::vector<float> d(kScfvModelFloats);
+  std::vector<__half> bh(2 * kScfvWHalfWords), bl(2 * kScfvWHalfWords);  // the B operand's halves
   // the gradient products take [1 | y | y^2] in FP16 halves: bounded PCA
   // rows (orthonormal ones have norm 1) and mean keep |y| <= 2 * 64 for unit
   // descriptors, so y^2 stays far inside FP16's range
@@ -1674,14 +1675,48 @@ cdvs_status cdvs_set_scfv_model(cdvs_ctx* c, const cdvs_scfv_model* m) {
     d[kScfvOffNsig + i] = (float)(1.0 / std::sqrt(2.0 * w));
     // Eq. 10's matrix form: -1/2 sum_k (y_k - mu_k)^2 / v_k
     //   = sum_k y_k^2 (-1/(2 v_k)) + sum_k y_k (mu_k / v_k) - 1/2 sum_k mu_k^2 / v_k
-    double cq = 0.0;
+    double cq = 0.0, col[2 * kScfvDim], big = 0.0;
     for (int k = 0; k < kScfvDim; ++k) {
       const double v = m->variances[i * kScfvDim + k], mu = m->means[i * kScfvDim + k];
-      d[kScfvOffW + kScfvWIndex(k, i)] = (float)(-0.5 / v);
-      d[kScfvOffW + kScfvWIndex(kScfvDim + k, i)] = (float)(mu / v);
+      col[k] = -0.5 / v;
+      col[kScfvDim + k] = mu / v;
       cq += mu * mu / v;
     }
+    for (double x : col) big = std::max(big, std::fabs(x));
+    if (!std::isfinite(big) || !std::isfinite(cq)) return fail(c, CDVS_INVALID_ARGUMENT, "GMM parameters overflow");
+    // column i scaled by a power of two, largest |entry| <= 2^14, then split
+    // into FP16 halves (the lo half carries the next 11 bits)
+    const int ex = big > 0.0 ? 14 - (int)std::ceil(std::log2(big)) : 0;
+    for (int k = 0; k < 2 * kScfvDim; ++k) {
+      const double x = std::ldexp(col[k], ex);
+      const __half h = __float2half_rn((float)x);
+      bh[kScfvTcBIndex(i, k)] = h;
+      bl[kScfvTcBIndex(i, k)] = __float2half_rn((float)(x - (double)__half2float(h)));
+    }
+    d[kScfvOffInvE + i] = (float)std::ldexp(1.0, -ex);
     d[kScfvOffC + i] = (float)(std::log(w) - 0.5 * logdet - 0.5 * cq);
+  }
+  std::memcpy(d.data() + kScfvOffW, bh.data(), sizeof(__half) * bh.size());
+  std::memcpy(d.data() + kScfvOffW + kScfvWHalfWords, bl.data(), sizeof(__half) * bl.size());
+  // P^T as FP16 hi / lo B fragments of the projection (|P| <= 64 by the row
+  // norm check above)
+  {
+    uint32_t* pf = reinterpret_cast<uint32_t*>(d.data() + kScfvOffPf);
+    for (int st = 0; st < 128 / 16; ++st)
+      for (int j8 = 0; j8 < kScfvDim / 8; ++j8)
+        for (int lane = 0; lane < 32; ++lane)
+          for (int q = 0; q < 2; ++q) {
+            const int g = lane / 4, t = lane % 4, k0 = 16 * st + 2 * t + 8 * q, j = 8 * j8 + g;
+            __half hi[2], lo[2];
+            for (int e = 0; e < 2; ++e) {
+              const float x = m->pca[j * 128 + k0 + e];
+              hi[e] = __float2half_rn(x);
+              lo[e] = __float2half_rn(x - __half2float(hi[e]));
+            }
+            const int idx = kScfvPfIndex(st, j8, lane, q);
+            std::memcpy(pf + idx, hi, 4);
+            std::memcpy(pf + 2048 + idx, lo, 4);
+          }
   }
   cudaError_t e;
   if ((e = cudaSetDevice(c->device)) != cudaSuccess || (e = ensure(c->scfv_model, sizeof(float) * d.size())) != cudaSuccess ||

@@ -274,20 +274,26 @@ constexpr int kScfvComp = 512, kScfvDim = 32;
 // the device model, derived on the host: P transposed [128][32], the PCA
 // mean, mu [512][32], 1/s [512][32], log w_i - 1/2 sum_k log(2 pi v_ik),
 // 1/sqrt(w_i), 1/sqrt(2 w_i); then the matrix form of the log-likelihood
-// (Eq. 10): W [64][512] with rows k < 32 = -1/(2 v_ik) (the y_k^2 terms) and
-// rows 32 + k = mu_ik / v_ik (the y_k terms), stored in the register order
-// of the tensor-core B fragments (kScfvWIndex), and the constant
-// c_i = log w_i - 1/2 sum_k log(2 pi v_ik) - 1/2 sum_k mu_ik^2 / v_ik
+// (Eq. 10), W [64][512] with rows k < 32 = -1/(2 v_ik) (the y_k^2 terms) and
+// rows 32 + k = mu_ik / v_ik (the y_k terms), as the tcgen05 B operand: per
+// component i, column i of W times a power of two e_i (largest |entry| at most
+// 2^14), split into FP16 hi and lo halves, each half [512][64] in the
+// no-swizzle K-major core-matrix order (kScfvTcBIndex, in halves); the
+// constant c_i = log w_i - 1/2 sum_k log(2 pi v_ik) - 1/2 sum_k mu_ik^2 / v_ik;
+// 1 / e_i; and P transposed as FP16 hi / lo B fragments of mma.sync
+// m16n8k16 (kScfvPfIndex, half2 words).
 constexpr int kScfvOffPcaT = 0, kScfvOffMean = 4096, kScfvOffMu = 4224, kScfvOffIsd = 20608, kScfvOffLw = 36992,
               kScfvOffNmu = 37504, kScfvOffNsig = 38016, kScfvOffW = 38528, kScfvOffC = 71296,
-              kScfvModelFloats = 71808;
-// Position of W[k][i] in the fragment order: warp w = i / 64 of the
-// posterior kernel, k-step s = k / 8, n-tile j = (i % 64) / 8, lane
-// 4 (i % 8) + (k % 4), element (k % 8) / 4.
-inline int kScfvWIndex(int k, int i) {
-  const int w = i / 64, j = (i % 64) / 8, g = i % 8, s = k / 8, t = k % 4, e = (k % 8) / 4;
-  return ((((w * 8 + s) * 8 + j) * 32 + (4 * g + t)) * 2) + e;
-}
+              kScfvOffInvE = 71808, kScfvOffPf = 72320, kScfvModelFloats = 76416;
+constexpr int kScfvWHalfWords = 16384;  // one FP16 half of the B operand, in 32-bit words
+// Position (in halves) of B element (component i, row k of W) in one half:
+// 8 x 8 core matrices of 128 contiguous bytes, adjacent along k at 128
+// bytes, along i at 1024 bytes.
+inline int kScfvTcBIndex(int i, int k) { return (i / 8) * 512 + (k / 8) * 64 + (i % 8) * 8 + (k % 8); }
+// Position (in half2 words) of the projection fragment holding P^T rows
+// (input dimensions) 2t + 8q, 2t + 8q + 1 of k-step s and output column
+// 8 j8 + g (lane 4 g + t); the lo halves follow 2048 words later.
+inline int kScfvPfIndex(int s, int j8, int lane, int q) { return ((s * 4 + j8) * 32 + lane) * 2 + q; }
 cudaError_t launch_scfv(const float* desc, int n_rec, const int* rec_off, int n_images, const float* model,
                         int n_select, float* Y, float* Q, float* g_mu, float* g_sig, float* delta, int* order,
                         uint32_t* bits, int n_sms, cudaStream_t s);

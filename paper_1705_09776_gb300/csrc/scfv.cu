@@ -15,17 +15,18 @@
 // The two contractions run on the tensor cores, as the paper's matrix form
 // has them (Eq. 10, 12, 14):
 //   * the log-likelihoods of a tile of records against all 512 components,
-//     L = [y^2 | y] W + c, with W = [-1/(2v); mu/v] (64 x 512);
+//     L = [y^2 | y] W + c, with W = [-1/(2v); mu/v] (64 x 512), on tcgen05
+//     with the accumulators in tensor memory;
 //   * per image, S = Gamma^T [1 | y | y^2] (512 x 65), from which
-//     g_mu = (S_y - mu S_1) / s and g_sigma = (S_yy - 2 mu S_y + mu^2 S_1) / v - S_1.
-// Both split their operands in two (x = hi + lo) and take three products per
-// term (hi hi + hi lo + lo hi), accumulated in FP32: about 21 significant
-// bits per product, so the softmax, which needs the log-likelihood to ~1e-5
-// absolute, stays within FP32-level error.  The log-likelihoods use TF32
-// halves (mma.sync m16n8k8: the model's 1/v can be large, and TF32 keeps
-// FP32's range); the gradient products use FP16 halves (m16n8k16, twice the
-// rate; every operand there is bounded).  The softmax and every reduction
-// run in a fixed order.
+//     g_mu = (S_y - mu S_1) / s and g_sigma = (S_yy - 2 mu S_y + mu^2 S_1) / v - S_1,
+//     on mma.sync.
+// Both split their operands into two FP16 halves (x = hi + lo) and take
+// three products per term (hi hi + hi lo + lo hi), accumulated in FP32:
+// about 22 significant bits per product, so the softmax, which needs the
+// log-likelihood to ~1e-5 absolute, stays within FP32-level error.  The
+// model's 1/v can be large, so each component's column of W is scaled by a
+// power of two into FP16's range on the host and the scale is undone, exactly,
+// on the accumulator.  The softmax and every reduction run in a fixed order.
 #include <algorithm>
 
 #include "cdvs_internal.cuh"
@@ -35,29 +36,23 @@ namespace {
 
 constexpr int kComp = kScfvComp, kDim = kScfvDim, kIn = 128;
 
-// ---- split-TF32 tensor-core products
+// ---- FP16-split tensor-core products
 
-// x = hi + lo with hi, lo both representable in TF32 (round to nearest).
-__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));
-  const float r = x - __uint_as_float(hi);
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(r));
+// (x0, x1) = hi + lo, both halves FP16 pairs (round to nearest)
+__device__ __forceinline__ void split_h2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+  const __half2 h = __floats2half2_rn(x0, x1);
+  const float2 f = __half22float2(h);
+  const __half2 l = __floats2half2_rn(x0 - f.x, x1 - f.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-// D = A B + D for one 16 x 8 x 8 block (A row-major 16 x 8, B 8 x 8).
-__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+// D = A B + D for one 16 x 8 x 16 block (mma.sync m16n8k16, FP16 in, FP32 accumulate)
+__device__ __forceinline__ void mma_f16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
                "{%0,%1,%2,%3};"
                : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
                : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-// hi*hi + hi*lo + lo*hi, the small products first
-__device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4],
-                                     const uint32_t (&bh)[2], const uint32_t (&bl)[2]) {
-  mma_tf32(d, al, bh);
-  mma_tf32(d, ah, bl);
-  mma_tf32(d, ah, bh);
 }
 
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -66,201 +61,262 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
-// K_a + K_b: projection and posteriors.  Persistent CTAs of 8 warps; a tile
-// is 64 records (four 16-row tensor-core tiles).
-//   1. y = (x - m) P^T on the tensor cores: the tile's descriptors minus the
-//      PCA mean (FP32) times P^T (staged once per CTA, split into TF32
-//      hi / lo); warp w computes the 16 x 8 output blocks (w / 2, 2 (w % 2))
-//      and (w / 2, 2 (w % 2) + 1).  y goes to shared memory and to Y.
-//   2. the log-likelihoods L = [y^2 | y] W + c: warp w owns components
-//      64w .. 64w + 63 (eight 8-column tiles) for all four row tiles; W is
-//      staged once per CTA in fragment order.
-//   3. per record the softmax over the 512 components, in a fixed order.
-// The fragment layouts of m16n8k8: lane = 4 g + t; A element
-// (g + 8 (q & 1), t + 4 (q >> 1)) in register q; B elements (t, g) and
-// (t + 4, g); C elements (g, 2t), (g, 2t + 1), (g + 8, 2t), (g + 8, 2t + 1).
-constexpr int kPostTile = 64, kPostThreads = 256, kYPitch = 36, kXPitch = 132;
-constexpr float kLog2e = 1.4426950408889634f;
+// ---- tcgen05: shared-memory matrix descriptors, tensor memory, mbarrier
 
-// dynamic shared memory of K_b (floats): W | P^T hi, lo in fragment order |
-// the descriptor tile
-constexpr int kPostSmemFloats = 2 * kDim * kComp + 2 * kIn * kDim + kPostTile * kXPitch;
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// No-swizzle K-major operand at shared address `a`: 8 x 16-byte core
+// matrices, adjacent along K at `lbo` bytes, along M / N at `sbo` bytes.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t a, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((a >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version (fixed 0b001); base offset 0, no swizzle
+  return d;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Waits (at most 2^20 polls) for phase `parity` of the mbarrier; false when
+// it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (int it = 0; it < (1 << 20) && !done; ++it) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+  }
+  return done != 0;
+}
+
+// 32 consecutive accumulator columns of this warp's 32 lanes (one record per
+// lane), read as FP32
+__device__ __forceinline__ void tmem_ld32(uint32_t addr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int e = 0; e < 32; ++e) v[e] = __uint_as_float(r[e]);
+}
+
+// K_a + K_b: projection and posteriors, persistent CTAs of 8 warps (one per
+// SM: the log-likelihoods of a tile fill the SM's 512 tensor-memory
+// columns); a tile is 128 records.
+//   1. y = (x - m) P^T: warp w takes records 16w .. 16w + 15 and all 32
+//      outputs, FP16 hi / lo operands on mma.sync m16n8k16, three products
+//      per term.  y goes to shared memory and to Y.
+//   2. The log-likelihoods L = [y^2 | y] W + c on tcgen05: A = [y^2 | y]
+//      (128 x 64) split into FP16 halves in shared memory, B = the model's
+//      column-scaled W in FP16 halves (staged once per CTA), three products
+//      (lo hi, hi lo, hi hi) per half of the 512 components (M = 128,
+//      N = 256, K = 16 each), issued by one thread, accumulated in FP32 in
+//      tensor memory; one commit to an mbarrier.
+//   3. Per record the softmax over the 512 components, read back with
+//      tcgen05.ld: warp w reads lanes 32 (w % 4) .. (its records) and
+//      components 256 (w / 4) .. ; l = acc / e_i + c_i, then the maximum, the
+//      sum of exp(l - max) and the posteriors, three passes over the
+//      accumulators, each half's partial results combined in a fixed order.
+// A tile whose products do not complete within the bounded wait gets NaN
+// posteriors.
+// Fragment layouts of m16n8k16 (f16): lane = 4 g + t; A register q holds
+// row g + 8 (q & 1), columns 2t + 8 (q >> 1) + {0, 1}; B register q holds
+// rows 2t + 8 q + {0, 1}, column g; C elements (g, 2t), (g, 2t + 1),
+// (g + 8, 2t), (g + 8, 2t + 1).
+constexpr int kPostTile = 128, kPostThreads = 256, kYPitch = 36;
+constexpr int kTcSbo = (2 * kDim / 8) * 128;          // 1024: bytes between 8-row groups of A and B
+constexpr int kTcABytes = kPostTile / 8 * kTcSbo;     // 16 KB per half
+constexpr int kTcBBytes = kComp / 8 * kTcSbo;         // 64 KB per half
+constexpr int kPfWords = 2048;                        // projection fragments per half
+// kind::f16 instruction descriptor: FP32 accumulator, FP16 A and B, both K-major, N = 256, M = 128
+constexpr uint32_t kTcIdesc = (1u << 4) | ((uint32_t)(256 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+constexpr int kTmemCols = 512;
+constexpr float kLog2e = 1.4426950408889634f;
+// dynamic shared memory: B hi | B lo | A hi | A lo | projection fragments hi, lo
+constexpr int kPostSmemBytes = 2 * kTcBBytes + 2 * kTcABytes + 2 * kPfWords * 4;
+static_assert(kScfvWHalfWords * 4 == kTcBBytes, "the model's B halves are the staged ones");
 
 __global__ void __launch_bounds__(kPostThreads, 1) scfv_post_kernel(const float* desc, int n_rec,
                                                                     const float* model, float* Y, float* Q) {
-  extern __shared__ float4 w4[];
-  float* const Ws = reinterpret_cast<float*>(w4);
-  uint32_t* const Ph = reinterpret_cast<uint32_t*>(Ws + 2 * kDim * kComp);  // [16 k-steps][4 n-tiles][32 lanes][2]
-  uint32_t* const Pl = Ph + kIn * kDim;
-  float* const xs = reinterpret_cast<float*>(Pl + kIn * kDim);               // [64][kXPitch]
+  extern __shared__ __align__(128) unsigned char smb[];
+  unsigned char* const Bs = smb;                                 // B hi, then B lo
+  unsigned char* const As = smb + 2 * kTcBBytes;                 // A hi, then A lo
+  uint32_t* const Pf = reinterpret_cast<uint32_t*>(As + 2 * kTcABytes);
   __shared__ float ys[kPostTile][kYPitch];
-  __shared__ float cs[kComp];
-  __shared__ float mean[kIn];
-  __shared__ float red[kPostThreads / 32][kPostTile];
-  __shared__ float tmax[kPostTile], tinv[kPostTile];
+  __shared__ float cs[kComp], inve[kComp], mean[kIn];
+  __shared__ float redm[2][kPostTile], reds[2][kPostTile];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
-  for (int i = tid; i < 2 * kDim * kComp / 4; i += kPostThreads)
-    w4[i] = reinterpret_cast<const float4*>(model + kScfvOffW)[i];
-  // P^T (model: pt[k][j], k = input dimension, j = output dimension) in B
-  // fragment order for k-step s, n-tile j8: (k = 8s + t (+4), j = 8 j8 + g)
-  for (int i = tid; i < kIn * kDim; i += kPostThreads) {
-    const int e = i & 1, ln = (i >> 1) & 31, j8 = (i >> 6) & 3, ks = i >> 8;
-    const int k = 8 * ks + (ln & 3) + 4 * e, j = 8 * j8 + (ln >> 2);
-    split_tf32(model[kScfvOffPcaT + k * kDim + j], Ph[i], Pl[i]);
+  if (blockIdx.x * kPostTile >= n_rec) return;
+  for (int i = tid; i < 2 * kTcBBytes / 16; i += kPostThreads)
+    reinterpret_cast<uint4*>(Bs)[i] = reinterpret_cast<const uint4*>(model + kScfvOffW)[i];
+  for (int i = tid; i < 2 * kPfWords; i += kPostThreads) Pf[i] = reinterpret_cast<const uint32_t*>(model + kScfvOffPf)[i];
+  for (int i = tid; i < kComp; i += kPostThreads) {
+    cs[i] = model[kScfvOffC + i];
+    inve[i] = model[kScfvOffInvE + i];
   }
-  for (int i = tid; i < kComp; i += kPostThreads) cs[i] = model[kScfvOffC + i];
   for (int i = tid; i < kIn; i += kPostThreads) mean[i] = model[kScfvOffMean + i];
-  const float2* wf = reinterpret_cast<const float2*>(w4) + warp * 8 * 8 * 32;
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // B is read by the tensor cores
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  uint32_t phase = 0;
   for (int r0 = blockIdx.x * kPostTile; r0 < n_rec; r0 += gridDim.x * kPostTile) {
-    __syncthreads();  // model staged; the previous tile is done with xs, ys, red, tmax, tinv
-    for (int e = tid; e < kPostTile * kIn / 4; e += kPostThreads) {
-      const int r = e / (kIn / 4), c4 = e - r * (kIn / 4);
-      float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-      if (r0 + r < n_rec) {
-        v = reinterpret_cast<const float4*>(desc + (size_t)(r0 + r) * kIn)[c4];
-        v.x -= mean[4 * c4];
-        v.y -= mean[4 * c4 + 1];
-        v.z -= mean[4 * c4 + 2];
-        v.w -= mean[4 * c4 + 3];
-      }
-      *reinterpret_cast<float4*>(xs + r * kXPitch + 4 * c4) = v;
-    }
-    __syncthreads();
-    {  // 1. projection: blocks (mt, nt) and (mt, nt + 1) of the 64 x 32 output
-      const int mt = warp >> 1, nt0 = 2 * (warp & 1);
-      float pa[2][4] = {{0.0f, 0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f, 0.0f}};
-#pragma unroll 4
-      for (int ks = 0; ks < kIn / 8; ++ks) {
+    {  // 1. projection
+      float pa[4][4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) pa[j][0] = pa[j][1] = pa[j][2] = pa[j][3] = 0.0f;
+      // rows past the last record repeat it (finite values, never stored)
+      const float* xa = desc + (size_t)min(r0 + 16 * warp + g, n_rec - 1) * kIn;
+      const float* xb = desc + (size_t)min(r0 + 16 * warp + g + 8, n_rec - 1) * kIn;
+#pragma unroll 2
+      for (int s = 0; s < kIn / 16; ++s) {
         uint32_t ah[4], al[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          split_tf32(xs[(16 * mt + g + 8 * (q & 1)) * kXPitch + 8 * ks + t + 4 * (q >> 1)], ah[q], al[q]);
+        for (int q = 0; q < 4; ++q) {
+          const int c = 16 * s + 2 * t + 8 * (q >> 1);
+          const float2 v = *reinterpret_cast<const float2*>(((q & 1) ? xb : xa) + c);
+          split_h2(v.x - mean[c], v.y - mean[c + 1], ah[q], al[q]);
+        }
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int f = ((ks * 4 + nt0 + u) * 32 + lane) * 2;
-          const uint32_t bh[2] = {Ph[f], Ph[f + 1]}, bl[2] = {Pl[f], Pl[f + 1]};
-          mma3(pa[u], ah, al, bh, bl);
+        for (int j = 0; j < 4; ++j) {
+          const int f = ((s * 4 + j) * 32 + lane) * 2;
+          const uint32_t bh[2] = {Pf[f], Pf[f + 1]}, bl[2] = {Pf[kPfWords + f], Pf[kPfWords + f + 1]};
+          mma_f16(pa[j], al, bh);
+          mma_f16(pa[j], ah, bl);
+          mma_f16(pa[j], ah, bh);
         }
       }
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int r = 16 * mt + g, c = 8 * (nt0 + u) + 2 * t;
-        ys[r][c] = pa[u][0];
-        ys[r][c + 1] = pa[u][1];
-        ys[r + 8][c] = pa[u][2];
-        ys[r + 8][c + 1] = pa[u][3];
+      for (int j = 0; j < 4; ++j) {
+        const int r = 16 * warp + g, c = 8 * j + 2 * t;
+        ys[r][c] = pa[j][0];
+        ys[r][c + 1] = pa[j][1];
+        ys[r + 8][c] = pa[j][2];
+        ys[r + 8][c + 1] = pa[j][3];
       }
     }
-    __syncthreads();
+    __syncthreads();  // ys complete; the previous tile's accumulator reads are done (fenced)
     for (int e = tid; e < kPostTile * kDim; e += kPostThreads) {
       const int r = e / kDim, k = e - r * kDim;
       if (r0 + r < n_rec) Y[(size_t)(r0 + r) * kDim + k] = ys[r][k];
     }
-    // 2. log-likelihoods
-    float acc[4][8][4];
+    // A = [y^2 | y] in FP16 halves: 8-element pieces (record r, columns 8 kc ..)
+    for (int e = tid; e < kPostTile * 8; e += kPostThreads) {
+      const int r = e & (kPostTile - 1), kc = e / kPostTile;
+      uint32_t hi[4], lo[4];
 #pragma unroll
-    for (int m = 0; m < 4; ++m)
-#pragma unroll
-      for (int j = 0; j < 8; ++j)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[m][j][q] = 0.0f;
-#pragma unroll 1
-    for (int s = 0; s < 8; ++s) {
-      // A = [y^2 | y]: k-steps 0..3 take the squares of dimensions 8s..8s+7,
-      // k-steps 4..7 the dimensions themselves
-      uint32_t ah[4][4], al[4][4];
-#pragma unroll
-      for (int m = 0; m < 4; ++m)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float y = ys[16 * m + g + 8 * (q & 1)][8 * (s & 3) + t + 4 * (q >> 1)];
-          split_tf32(s < 4 ? y * y : y, ah[m][q], al[m][q]);
+      for (int u = 0; u < 4; ++u) {
+        float y0 = ys[r][8 * (kc & 3) + 2 * u], y1 = ys[r][8 * (kc & 3) + 2 * u + 1];
+        if (kc < 4) {
+          y0 *= y0;
+          y1 *= y1;
         }
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const float2 w = wf[(s * 8 + j) * 32 + lane];
-        uint32_t bh[2], bl[2];
-        split_tf32(w.x, bh[0], bl[0]);
-        split_tf32(w.y, bh[1], bl[1]);
-#pragma unroll
-        for (int m = 0; m < 4; ++m) mma3(acc[m][j], ah[m], al[m], bh, bl);
+        split_h2(y0, y1, hi[u], lo[u]);
       }
+      const int off = (r >> 3) * kTcSbo + kc * 128 + (r & 7) * 16;
+      *reinterpret_cast<uint4*>(As + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<uint4*>(As + kTcABytes + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
-    // 3. softmax per record: records 16m + g + 8h of this lane (h = q >> 1),
-    // components 64 warp + 8j + 2t + (q & 1)
-    float mx[4][2];
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    // 2. the products, one thread
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t a0 = smem_addr(As), b0 = smem_addr(Bs);
 #pragma unroll
-    for (int m = 0; m < 4; ++m)
+      for (int h = 0; h < 2; ++h)
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        float v = -3.0e38f;
+        for (int p = 0; p < 3; ++p) {  // lo hi, hi lo, hi hi
+          const uint32_t ap = a0 + (p == 0 ? kTcABytes : 0), bp = b0 + (p == 1 ? kTcBBytes : 0) + h * 32 * kTcSbo;
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            float& l = acc[m][j][2 * h + e];
-            l += cs[64 * warp + 8 * j + 2 * t + e];
-            v = fmaxf(v, l);
+          for (int ks = 0; ks < 2 * kDim / 16; ++ks) {
+            const uint64_t da = tc_desc(ap + ks * 256, 128, kTcSbo), db = tc_desc(bp + ks * 256, 128, kTcSbo);
+            const uint32_t acc = (p | ks) ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem + (uint32_t)(256 * h)),
+                "l"(da), "l"(db), "r"(kTcIdesc), "r"(acc));
           }
-        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 1));
-        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 2));
-        mx[m][h] = v;
-      }
-    if (t == 0)
-#pragma unroll
-      for (int m = 0; m < 4; ++m)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) red[warp][16 * m + g + 8 * h] = mx[m][h];
-    __syncthreads();
-    if (tid < kPostTile) {
-      float v = red[0][tid];
-      for (int w = 1; w < kPostThreads / 32; ++w) v = fmaxf(v, red[w][tid]);
-      tmax[tid] = v;
+        }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_addr(&mbar))
+                   : "memory");
     }
-    __syncthreads();
-    float sm[4][2];
+    // 3. softmax
+    const bool ok = mbar_wait(&mbar, phase);
+    phase ^= 1u;
+    tc_fence_after();
+    const int quad = warp & 3, half = warp >> 2, r = 32 * quad + lane, n0 = 256 * half;
+    const uint32_t taddr = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)n0;
+    float mx = -3.0e38f;
+#pragma unroll 1
+    for (int c = 0; c < 8; ++c) {
+      float v[32];
+      tmem_ld32(taddr + 32 * c, v);
 #pragma unroll
-    for (int m = 0; m < 4; ++m)
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const float mref = tmax[16 * m + g + 8 * h] * kLog2e;
-        float v = 0.0f;
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            float& l = acc[m][j][2 * h + e];
-            l = ex2_approx(fmaf(l, kLog2e, -mref));
-            v += l;
-          }
-        v += __shfl_xor_sync(0xffffffffu, v, 1);
-        v += __shfl_xor_sync(0xffffffffu, v, 2);
-        sm[m][h] = v;
-      }
-    __syncthreads();  // every max read before red is rewritten
-    if (t == 0)
-#pragma unroll
-      for (int m = 0; m < 4; ++m)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) red[warp][16 * m + g + 8 * h] = sm[m][h];
-    __syncthreads();
-    if (tid < kPostTile) {
-      float v = 0.0f;
-      for (int w = 0; w < kPostThreads / 32; ++w) v += red[w][tid];
-      tinv[tid] = 1.0f / v;
+      for (int e = 0; e < 32; ++e) mx = fmaxf(mx, fmaf(v[e], inve[n0 + 32 * c + e], cs[n0 + 32 * c + e]));
     }
+    redm[half][r] = mx;
     __syncthreads();
+    const float mref = fmaxf(redm[0][r], redm[1][r]) * kLog2e;
+    float sum = 0.0f;
+#pragma unroll 1
+    for (int c = 0; c < 8; ++c) {
+      float v[32];
+      tmem_ld32(taddr + 32 * c, v);
 #pragma unroll
-    for (int m = 0; m < 4; ++m)
+      for (int e = 0; e < 32; ++e)
+        sum += ex2_approx(fmaf(fmaf(v[e], inve[n0 + 32 * c + e], cs[n0 + 32 * c + e]), kLog2e, -mref));
+    }
+    reds[half][r] = sum;
+    __syncthreads();
+    const float inv = ok ? 1.0f / (reds[0][r] + reds[1][r]) : __int_as_float(0x7fc00000);
+    // every lane reads (the loads are warp-collective); lanes past the last
+    // record store nothing
+    const bool live = r0 + r < n_rec;
+    float4* out = reinterpret_cast<float4*>(Q + (size_t)min(r0 + r, n_rec - 1) * kComp + n0);
+#pragma unroll 1
+    for (int c = 0; c < 8; ++c) {
+      float v[32];
+      tmem_ld32(taddr + 32 * c, v);
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int r = 16 * m + g + 8 * h;
-        if (r0 + r >= n_rec) continue;
-        const float inv = tinv[r];
-        float2* out = reinterpret_cast<float2*>(Q + (size_t)(r0 + r) * kComp + 64 * warp + 2 * t);
+      for (int e = 0; e < 32; e += 4) {
+        float o[4];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) out[4 * j] = make_float2(acc[m][j][2 * h] * inv, acc[m][j][2 * h + 1] * inv);
+        for (int u = 0; u < 4; ++u)
+          o[u] = ex2_approx(fmaf(fmaf(v[e + u], inve[n0 + 32 * c + e + u], cs[n0 + 32 * c + e + u]), kLog2e, -mref)) *
+                 inv;
+        if (live) out[(32 * c + e) / 4] = make_float4(o[0], o[1], o[2], o[3]);
       }
+    }
+    tc_fence_before();  // these reads precede the next tile's products
+  }
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
   }
 }
 
@@ -286,20 +342,7 @@ constexpr int kGradZWords = (kGradChunk / 2) * kZCols;
 constexpr int kGradSmemWords = 2 * kGradQWords + 2 * kGradZWords;
 static_assert(256 * kSPitch <= 2 * kGradQWords, "S of 256 components fits the posterior buffers");
 
-__device__ __forceinline__ void split_h2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
-  const __half2 h = __floats2half2_rn(x0, x1);
-  const float2 f = __half22float2(h);
-  const __half2 l = __floats2half2_rn(x0 - f.x, x1 - f.y);
-  hi = *reinterpret_cast<const uint32_t*>(&h);
-  lo = *reinterpret_cast<const uint32_t*>(&l);
-}
 
-__device__ __forceinline__ void mma_f16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-               "{%0,%1,%2,%3};"
-               : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-               : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<unsigned>(__cvta_generic_to_shared(dst))),
@@ -471,7 +514,7 @@ cudaError_t launch_scfv(const float* desc, int n_rec, const int* rec_off, int n_
                         uint32_t* bits, int n_sms, cudaStream_t s) {
   if (n_images <= 0) return cudaSuccess;
   if (n_rec > 0) {
-    const int pbytes = (int)(sizeof(float) * kPostSmemFloats);
+    const int pbytes = kPostSmemBytes;
     static LaunchCache post_cache;
     cudaError_t e = prepare_launch(scfv_post_kernel, post_cache, pbytes, kPostThreads, nullptr);
     if (e != cudaSuccess) return e;
