@@ -55,6 +55,13 @@ __device__ __forceinline__ void mma_f16(float (&d)[4], const uint32_t (&a)[4], c
                : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+// 16-byte asynchronous copy global -> shared (both 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<unsigned>(__cvta_generic_to_shared(dst))),
+               "l"(src)
+               : "memory");
+}
+
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -113,9 +120,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t addr, float (&v)[32]) {
 // K_a + K_b: projection and posteriors, persistent CTAs of 8 warps (one per
 // SM: the log-likelihoods of a tile fill the SM's 512 tensor-memory
 // columns); a tile is 128 records.
-//   1. y = (x - m) P^T: warp w takes records 16w .. 16w + 15 and all 32
-//      outputs, FP16 hi / lo operands on mma.sync m16n8k16, three products
-//      per term.  y goes to shared memory and to Y.
+//   1. y = (x - m) P^T: warp w takes records 16 (w % 8) .. + 15 and the
+//      outputs of its kProjTiles 8-column tiles, FP16 hi / lo operands on
+//      mma.sync m16n8k16, three products per term.  y goes to shared memory
+//      and to Y.
 //   2. The log-likelihoods L = [y^2 | y] W + c on tcgen05: A = [y^2 | y]
 //      (128 x 64) split into FP16 halves in shared memory, B = the model's
 //      column-scaled W in FP16 halves (staged once per CTA), three products
@@ -124,9 +132,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t addr, float (&v)[32]) {
 //      tensor memory; one commit to an mbarrier.
 //   3. Per record the softmax over the 512 components, read back with
 //      tcgen05.ld: warp w reads lanes 32 (w % 4) .. (its records) and
-//      components 256 (w / 4) .. ; l = acc / e_i + c_i, then the maximum, the
-//      sum of exp(l - max) and the posteriors, three passes over the
-//      accumulators, each half's partial results combined in a fixed order.
+//      components kPartCols (w / 4) .. ; l = acc / e_i + c_i; a running maximum
+//      and sum of exponentials, then the posteriors: two passes over the
+//      accumulators, the four parts of a record combined in a fixed order.
 // A tile whose products do not complete within the bounded wait gets NaN
 // posteriors.
 // Fragment layouts of m16n8k16 (f16): lane = 4 g + t; A register q holds
@@ -134,6 +142,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t addr, float (&v)[32]) {
 // rows 2t + 8 q + {0, 1}, column g; C elements (g, 2t), (g, 2t + 1),
 // (g + 8, 2t), (g + 8, 2t + 1).
 constexpr int kPostTile = 128, kPostThreads = 256, kYPitch = 36;
+constexpr int kPostWarps = kPostThreads / 32;
+constexpr int kPostParts = kPostWarps / 4;          // column parts of a record in the softmax
+constexpr int kPartCols = kComp / kPostParts;
+constexpr int kProjTiles = 4 / (kPostWarps / 8);    // projection n-tiles per warp
+static_assert(kPostWarps == 8 || kPostWarps == 16, "8 or 16 warps");
 constexpr int kTcSbo = (2 * kDim / 8) * 128;          // 1024: bytes between 8-row groups of A and B
 constexpr int kTcABytes = kPostTile / 8 * kTcSbo;     // 16 KB per half
 constexpr int kTcBBytes = kComp / 8 * kTcSbo;         // 64 KB per half
@@ -153,15 +166,20 @@ __global__ void __launch_bounds__(kPostThreads, 1) scfv_post_kernel(const float*
   unsigned char* const As = smb + 2 * kTcBBytes;                 // A hi, then A lo
   uint32_t* const Pf = reinterpret_cast<uint32_t*>(As + 2 * kTcABytes);
   __shared__ float ys[kPostTile][kYPitch];
-  __shared__ float cs[kComp], inve[kComp], mean[kIn];
-  __shared__ float redm[2][kPostTile], reds[2][kPostTile];
+  __shared__ __align__(16) float cs[kComp];
+  __shared__ __align__(16) float inve[kComp];
+  __shared__ float mean[kIn];
+  __shared__ float redm[kPostParts][kPostTile], reds[kPostParts][kPostTile];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
   if (blockIdx.x * kPostTile >= n_rec) return;
+  // the model's operands, 16-byte asynchronous copies all in flight at once
   for (int i = tid; i < 2 * kTcBBytes / 16; i += kPostThreads)
-    reinterpret_cast<uint4*>(Bs)[i] = reinterpret_cast<const uint4*>(model + kScfvOffW)[i];
-  for (int i = tid; i < 2 * kPfWords; i += kPostThreads) Pf[i] = reinterpret_cast<const uint32_t*>(model + kScfvOffPf)[i];
+    cp_async16(Bs + 16 * i, reinterpret_cast<const unsigned char*>(model + kScfvOffW) + 16 * i);
+  for (int i = tid; i < 2 * kPfWords / 4; i += kPostThreads)
+    cp_async16(Pf + 4 * i, reinterpret_cast<const uint32_t*>(model + kScfvOffPf) + 4 * i);
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
   for (int i = tid; i < kComp; i += kPostThreads) {
     cs[i] = model[kScfvOffC + i];
     inve[i] = model[kScfvOffInvE + i];
@@ -183,34 +201,45 @@ __global__ void __launch_bounds__(kPostThreads, 1) scfv_post_kernel(const float*
   const uint32_t tmem = tmem_base;
   uint32_t phase = 0;
   for (int r0 = blockIdx.x * kPostTile; r0 < n_rec; r0 += gridDim.x * kPostTile) {
-    {  // 1. projection
-      float pa[4][4];
+    {  // 1. projection: warp w takes records 16 (w % 8) .. + 15 and kProjTiles 8-column output tiles
+      const int rw = 16 * (warp & 7), j0 = kProjTiles * (warp >> 3);
+      float pa[kProjTiles][4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) pa[j][0] = pa[j][1] = pa[j][2] = pa[j][3] = 0.0f;
+      for (int j = 0; j < kProjTiles; ++j) pa[j][0] = pa[j][1] = pa[j][2] = pa[j][3] = 0.0f;
       // rows past the last record repeat it (finite values, never stored)
-      const float* xa = desc + (size_t)min(r0 + 16 * warp + g, n_rec - 1) * kIn;
-      const float* xb = desc + (size_t)min(r0 + 16 * warp + g + 8, n_rec - 1) * kIn;
-#pragma unroll 2
-      for (int s = 0; s < kIn / 16; ++s) {
-        uint32_t ah[4], al[4];
+      const float* xa = desc + (size_t)min(r0 + rw + g, n_rec - 1) * kIn;
+      const float* xb = desc + (size_t)min(r0 + rw + g + 8, n_rec - 1) * kIn;
+      // the loads of four k-steps are issued before any of them is used
+#pragma unroll 1
+      for (int s0 = 0; s0 < kIn / 16; s0 += 4) {
+        float2 v[4][4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int c = 16 * s + 2 * t + 8 * (q >> 1);
-          const float2 v = *reinterpret_cast<const float2*>(((q & 1) ? xb : xa) + c);
-          split_h2(v.x - mean[c], v.y - mean[c + 1], ah[q], al[q]);
-        }
+        for (int sb = 0; sb < 4; ++sb)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int f = ((s * 4 + j) * 32 + lane) * 2;
-          const uint32_t bh[2] = {Pf[f], Pf[f + 1]}, bl[2] = {Pf[kPfWords + f], Pf[kPfWords + f + 1]};
-          mma_f16(pa[j], al, bh);
-          mma_f16(pa[j], ah, bl);
-          mma_f16(pa[j], ah, bh);
+          for (int q = 0; q < 4; ++q)
+            v[sb][q] = __ldg(reinterpret_cast<const float2*>(((q & 1) ? xb : xa) + 16 * (s0 + sb) + 2 * t + 8 * (q >> 1)));
+#pragma unroll
+        for (int sb = 0; sb < 4; ++sb) {
+          const int s = s0 + sb;
+          uint32_t ah[4], al[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int c = 16 * s + 2 * t + 8 * (q >> 1);
+            split_h2(v[sb][q].x - mean[c], v[sb][q].y - mean[c + 1], ah[q], al[q]);
+          }
+#pragma unroll
+          for (int j = 0; j < kProjTiles; ++j) {
+            const int f = ((s * 4 + j0 + j) * 32 + lane) * 2;
+            const uint32_t bh[2] = {Pf[f], Pf[f + 1]}, bl[2] = {Pf[kPfWords + f], Pf[kPfWords + f + 1]};
+            mma_f16(pa[j], al, bh);
+            mma_f16(pa[j], ah, bl);
+            mma_f16(pa[j], ah, bh);
+          }
         }
       }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int r = 16 * warp + g, c = 8 * j + 2 * t;
+      for (int j = 0; j < kProjTiles; ++j) {
+        const int r = rw + g, c = 8 * (j0 + j) + 2 * t;
         ys[r][c] = pa[j][0];
         ys[r][c + 1] = pa[j][1];
         ys[r + 8][c] = pa[j][2];
@@ -264,51 +293,67 @@ __global__ void __launch_bounds__(kPostThreads, 1) scfv_post_kernel(const float*
                        smem_addr(&mbar))
                    : "memory");
     }
-    // 3. softmax
+    // 3. softmax: warp w reads the lanes of quadrant w % 4 (its records) and
+    // components kPartCols (w / 4) .., in 32-column pieces.  Pass 1
+    // keeps a running maximum m and sum of exp(l - m), rescaled once per
+    // piece; the four parts of a record combine in a fixed order.
     const bool ok = mbar_wait(&mbar, phase);
     phase ^= 1u;
     tc_fence_after();
-    const int quad = warp & 3, half = warp >> 2, r = 32 * quad + lane, n0 = 256 * half;
+    const int quad = warp & 3, part = warp >> 2, r = 32 * quad + lane, n0 = kPartCols * part;
     const uint32_t taddr = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)n0;
-    float mx = -3.0e38f;
+    float m = -3.0e38f, sum = 0.0f;
 #pragma unroll 1
-    for (int c = 0; c < 8; ++c) {
+    for (int c = 0; c < kPartCols / 32; ++c) {
       float v[32];
       tmem_ld32(taddr + 32 * c, v);
+      float cm = -3.0e38f;
 #pragma unroll
-      for (int e = 0; e < 32; ++e) mx = fmaxf(mx, fmaf(v[e], inve[n0 + 32 * c + e], cs[n0 + 32 * c + e]));
-    }
-    redm[half][r] = mx;
-    __syncthreads();
-    const float mref = fmaxf(redm[0][r], redm[1][r]) * kLog2e;
-    float sum = 0.0f;
-#pragma unroll 1
-    for (int c = 0; c < 8; ++c) {
-      float v[32];
-      tmem_ld32(taddr + 32 * c, v);
+      for (int e = 0; e < 32; e += 4) {
+        const float4 iv = *reinterpret_cast<const float4*>(inve + n0 + 32 * c + e);
+        const float4 cv = *reinterpret_cast<const float4*>(cs + n0 + 32 * c + e);
+        v[e] = fmaf(v[e], iv.x, cv.x);
+        v[e + 1] = fmaf(v[e + 1], iv.y, cv.y);
+        v[e + 2] = fmaf(v[e + 2], iv.z, cv.z);
+        v[e + 3] = fmaf(v[e + 3], iv.w, cv.w);
+        cm = fmaxf(fmaxf(cm, fmaxf(v[e], v[e + 1])), fmaxf(v[e + 2], v[e + 3]));
+      }
+      const float mn = fmaxf(m, cm), mref = mn * kLog2e;
+      float ps = 0.0f;
 #pragma unroll
-      for (int e = 0; e < 32; ++e)
-        sum += ex2_approx(fmaf(fmaf(v[e], inve[n0 + 32 * c + e], cs[n0 + 32 * c + e]), kLog2e, -mref));
+      for (int e = 0; e < 32; ++e) ps += ex2_approx(fmaf(v[e], kLog2e, -mref));
+      sum = fmaf(sum, ex2_approx((m - mn) * kLog2e), ps);
+      m = mn;
     }
-    reds[half][r] = sum;
+    redm[part][r] = m;
+    reds[part][r] = sum;
     __syncthreads();
-    const float inv = ok ? 1.0f / (reds[0][r] + reds[1][r]) : __int_as_float(0x7fc00000);
+    float M = redm[0][r];
+#pragma unroll
+    for (int p = 1; p < kPostParts; ++p) M = fmaxf(M, redm[p][r]);
+    float S = 0.0f;
+#pragma unroll
+    for (int p = 0; p < kPostParts; ++p) S = fmaf(reds[p][r], ex2_approx((redm[p][r] - M) * kLog2e), S);
+    const float inv = ok ? 1.0f / S : __int_as_float(0x7fc00000);
+    const float mref = M * kLog2e;
     // every lane reads (the loads are warp-collective); lanes past the last
     // record store nothing
     const bool live = r0 + r < n_rec;
     float4* out = reinterpret_cast<float4*>(Q + (size_t)min(r0 + r, n_rec - 1) * kComp + n0);
 #pragma unroll 1
-    for (int c = 0; c < 8; ++c) {
+    for (int c = 0; c < kPartCols / 32; ++c) {
       float v[32];
       tmem_ld32(taddr + 32 * c, v);
 #pragma unroll
       for (int e = 0; e < 32; e += 4) {
-        float o[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          o[u] = ex2_approx(fmaf(fmaf(v[e + u], inve[n0 + 32 * c + e + u], cs[n0 + 32 * c + e + u]), kLog2e, -mref)) *
-                 inv;
-        if (live) out[(32 * c + e) / 4] = make_float4(o[0], o[1], o[2], o[3]);
+        const float4 iv = *reinterpret_cast<const float4*>(inve + n0 + 32 * c + e);
+        const float4 cv = *reinterpret_cast<const float4*>(cs + n0 + 32 * c + e);
+        float4 o;
+        o.x = ex2_approx(fmaf(fmaf(v[e], iv.x, cv.x), kLog2e, -mref)) * inv;
+        o.y = ex2_approx(fmaf(fmaf(v[e + 1], iv.y, cv.y), kLog2e, -mref)) * inv;
+        o.z = ex2_approx(fmaf(fmaf(v[e + 2], iv.z, cv.z), kLog2e, -mref)) * inv;
+        o.w = ex2_approx(fmaf(fmaf(v[e + 3], iv.w, cv.w), kLog2e, -mref)) * inv;
+        if (live) out[(32 * c + e) / 4] = o;
       }
     }
     tc_fence_before();  // these reads precede the next tile's products
@@ -341,14 +386,6 @@ constexpr int kGradQWords = kGradChunk * kQPitch;
 constexpr int kGradZWords = (kGradChunk / 2) * kZCols;
 constexpr int kGradSmemWords = 2 * kGradQWords + 2 * kGradZWords;
 static_assert(256 * kSPitch <= 2 * kGradQWords, "S of 256 components fits the posterior buffers");
-
-
-
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<unsigned>(__cvta_generic_to_shared(dst))),
-               "l"(src)
-               : "memory");
-}
 
 // Posteriors of records c0 .. c0 + nr - 1 (nr <= 32) into a chunk buffer;
 // the rows past nr are zeroed.
