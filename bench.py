@@ -777,6 +777,10 @@ def main():
         sgemm = measure_sgemm_tflops(torch)
     except Exception:
         sgemm = None
+    try:
+        ffma2 = ctx.probe_fp32_rate()
+    except Exception:
+        ffma2 = None
     gbs = bytes_o[0] * n / (o0_ms * 1e-3) / 1e9
     v0 = int(tuning["last_call_variants"][0])
     traffic = load_traffic(v0)
@@ -788,6 +792,9 @@ def main():
                                "(SM count and maximum clock queried from the device)",
                 "measured_fp32": {"sgemm_tflops": sgemm, "frac": (tflops / sgemm) if sgemm else None,
                                   "source": "cuBLAS SGEMM 8192^3 with TF32 off, best of 5 (of measured)"},
+                "measured_ffma2": {"tflops": ffma2, "frac": (tflops / ffma2) if ffma2 else None,
+                                   "source": "cdvs_probe_fp32_rate: fma.rn.f32x2 register loop on every SM "
+                                             "(of measured)"},
                 "traffic": (traffic["dram_bytes_per_image_octave0"] * n if traffic else None),
                 "algorithmic_flops_per_launch": flops_o[0] * n, "algorithmic_bytes_per_launch": bytes_o[0] * n,
                 "launch_ms": o0_ms,

@@ -469,6 +469,16 @@ int32_t cdvs_detect_tuning(cdvs_ctx *ctx, char *buf, int32_t capacity);
 cdvs_status cdvs_set_candidate_capacity(cdvs_ctx *ctx, int32_t per_image);
 
 /* ---------------------------------------------------------------------------
+ * Measurement helper (not part of the method).  Measures the rate of packed
+ * FP32 multiply-adds (fma.rn.f32x2, the instruction of interest-point
+ * detection's filters and fit) on the context's GPU: a register-only loop on
+ * every SM, timed with CUDA events, ~10 ms.  *tflops counts two flops per
+ * multiply-add.  Blocks the calling thread; uses a stream of its own.
+ * INVALID_ARGUMENT for a NULL argument; CUDA_ERROR if a launch fails.
+ */
+cdvs_status cdvs_probe_fp32_rate(cdvs_ctx *ctx, double *tflops);
+
+/* ---------------------------------------------------------------------------
  * Testing hook (not part of the method).  The next `count` device workspace
  * allocations of any context in the process fail as cudaMalloc does when the
  * device memory is exhausted: the call that needed them returns

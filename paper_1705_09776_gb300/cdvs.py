@@ -64,7 +64,7 @@ EXPORTED = ["cdvs_params_default", "cdvs_create", "cdvs_destroy", "cdvs_last_err
             "cdvs_dedupe_select_noalloc", "cdvs_set_proposal", "cdvs_proposal_logits",
             "cdvs_proposal_train_step", "cdvs_resize", "cdvs_set_graph", "cdvs_set_scfv_model", "cdvs_scfv",
             "cdvs_inject_alloc_failures", "cdvs_set_candidate_capacity", "cdvs_set_detect_variant",
-            "cdvs_detect_tuning"]
+            "cdvs_detect_tuning", "cdvs_probe_fp32_rate"]
 STAGES = ["detect", "select", "describe", "offsets", "pack", "detect_octave0", "proposal"]
 
 
@@ -115,6 +115,7 @@ def load(build_if_missing: bool = True):
         "cdvs_set_candidate_capacity": (i32, [P, i32]),
         "cdvs_set_detect_variant": (i32, [P, i32]),
         "cdvs_detect_tuning": (i32, [P, P, i32]),
+        "cdvs_probe_fp32_rate": (i32, [P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -200,6 +201,12 @@ class Context:
         buf = C.create_string_buffer(n + 1)
         self._L.cdvs_detect_tuning(self.handle, buf, n + 1)
         return json.loads(buf.value.decode())
+
+    def probe_fp32_rate(self) -> float:
+        """cdvs_probe_fp32_rate: the measured packed-FP32 FMA rate, TFLOP/s."""
+        v = C.c_double(0.0)
+        self._check(self._L.cdvs_probe_fp32_rate(self.handle, C.byref(v)))
+        return float(v.value)
 
     def set_graph(self, enable: bool):
         """Device-resident extractions through one CUDA graph (cdvs_set_graph)."""

@@ -1798,6 +1798,14 @@ cdvs_status cdvs_scfv(cdvs_ctx* c, int32_t n, const float* desc, const int32_t* 
   return CDVS_OK;
 }
 
+cdvs_status cdvs_probe_fp32_rate(cdvs_ctx* c, double* tflops) {
+  if (!c || !tflops) return CDVS_INVALID_ARGUMENT;
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e == cudaSuccess) e = probe_ffma2(c->n_sms, tflops);
+  if (e != cudaSuccess) return cuda_fail(c, e, "FP32 rate probe");
+  return CDVS_OK;
+}
+
 cdvs_status cdvs_set_graph(cdvs_ctx* c, int32_t enable) {
   if (!c || (enable != 0 && enable != 1)) return CDVS_INVALID_ARGUMENT;
   if (c->async_open) return fail(c, CDVS_INVALID_ARGUMENT, "asynchronous extractions are pending: call cdvs_wait first");

@@ -294,6 +294,8 @@ inline int kScfvTcBIndex(int i, int k) { return (i / 8) * 512 + (k / 8) * 64 + (
 // (input dimensions) 2t + 8q, 2t + 8q + 1 of k-step s and output column
 // 8 j8 + g (lane 4 g + t); the lo halves follow 2048 words later.
 inline int kScfvPfIndex(int s, int j8, int lane, int q) { return ((s * 4 + j8) * 32 + lane) * 2 + q; }
+// The measured packed-FP32 FMA rate of the current device (probe.cu).
+cudaError_t probe_ffma2(int n_sms, double* tflops);
 cudaError_t launch_scfv(const float* desc, int n_rec, const int* rec_off, int n_images, const float* model,
                         int n_select, float* Y, float* Q, float* g_mu, float* g_sig, float* delta, int* order,
                         uint32_t* bits, int n_sms, cudaStream_t s);

@@ -2,7 +2,8 @@
 with the oracle-derived stand-in model (tests/golden/scfv_model.npz).
 
 Inputs are the GPU's own descriptors of seeded images (the aggregation is
-compared, not the descriptors), plus an empty image.  Tolerances: g_mu and
+compared, not the descriptors), plus an empty image, and record counts
+around the 128-record tiles of the log-likelihood products.  Tolerances: g_mu and
 g_sigma relative L2 per image <= 1e-4, delta <= 1e-4 relative; ranks and
 sign bits are compared where the FP64 values decide them with a margin
 (adjacent deltas apart by more than 1e-4 relative, |g| above 1e-4 of the
@@ -83,3 +84,33 @@ def test_scfv_device_buffers_equal_host(env):
     for a, b in zip(h[:4], outs[:4]):
         assert np.array_equal(a, b.cpu().numpy())
     assert np.array_equal(h[4], outs[4].cpu().numpy().view(np.uint32))
+
+
+def _check_image(got_mu, got_sig, got_delta, X, model):
+    rm, rs, rd = S.fisher(X, model)
+    for got, ref in ((got_mu, rm), (got_sig, rs)):
+        assert np.linalg.norm(got - ref) <= 1e-4 * np.linalg.norm(ref)
+    np.testing.assert_allclose(got_delta, rd, rtol=1e-4, atol=1e-7 * rd.max())
+
+
+def test_scfv_ragged_counts_match_oracle(env):
+    """Record counts around the 128-record tiles of the log-likelihood
+    products: images of 1, 127, 128, 129 and 0 records, the rest in a last
+    image, so tiles span image boundaries and the last tile is partial; then
+    a whole batch smaller than one tile (5 records) and a single record."""
+    cdvs, ctx, model = env
+    imgs = [synth.blob_image(synth.image_seed(83, i)) for i in range(2)]
+    kp, desc, cnt, _ = ctx.extract(imgs)
+    total = int(cnt.sum())
+    assert total > 1 + 127 + 128 + 129 + 10
+    for counts in ([1, 127, 128, 129, 0, total - 385], [5], [1]):
+        counts = np.array(counts, np.int32)
+        n = int(counts.sum())
+        g_mu, g_sig, delta, order, bits = ctx.scfv(desc[:n], counts, 16)
+        off = np.concatenate([[0], np.cumsum(counts)])
+        for b in range(len(counts)):
+            X = desc[off[b]:off[b + 1]].astype(np.float64)
+            if len(X) == 0:
+                assert not g_mu[b].any() and not g_sig[b].any()
+                continue
+            _check_image(g_mu[b], g_sig[b], delta[b], X, model)
