@@ -401,9 +401,9 @@ cdvs_status cdvs_proposal_train_step(cdvs_ctx *ctx, const uint8_t *images, int32
  * FP16 halves and three products per term (about 22 significant bits per
  * product, FP32 accumulation; each component's column of Eq. 10's matrix is
  * scaled by a power of two into FP16's range, exactly undone); everything
- * else is FP32.  Should the tensor cores not complete a tile's products
- * within a bounded wait, that tile's posteriors, and so the gradients of
- * its images, come out NaN.
+ * else is FP32.  Should the tensor cores not complete the products within a
+ * bounded wait (0.2 s), every gradient of the call comes out NaN and a
+ * synchronous call returns CDVS_DEVICE_TIMEOUT; the context stays usable.
  * ------------------------------------------------------------------------- */
 #define CDVS_SCFV_COMPONENTS 512
 #define CDVS_SCFV_DIM 32
@@ -486,6 +486,13 @@ cdvs_status cdvs_probe_fp32_rate(cdvs_ctx *ctx, double *tflops);
  * again by the next call).  count <= 0 turns the injection off.
  */
 void cdvs_inject_alloc_failures(int32_t count);
+
+/* Testing hook (not part of the method).  The next `count` cdvs_scfv calls of
+ * any context leave the tensor-core products of the log-likelihoods
+ * unissued, so the posterior kernel's bounded wait (0.2 s) runs out with
+ * nothing in flight: the call reports DEVICE_TIMEOUT (synchronous calls) and its
+ * gradients are NaN; the context stays usable.  count <= 0 turns it off. */
+void cdvs_inject_scfv_wait_timeouts(int32_t count);
 
 #ifdef __cplusplus
 }

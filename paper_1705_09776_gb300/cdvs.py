@@ -64,7 +64,7 @@ EXPORTED = ["cdvs_params_default", "cdvs_create", "cdvs_destroy", "cdvs_last_err
             "cdvs_dedupe_select_noalloc", "cdvs_set_proposal", "cdvs_proposal_logits",
             "cdvs_proposal_train_step", "cdvs_resize", "cdvs_set_graph", "cdvs_set_scfv_model", "cdvs_scfv",
             "cdvs_inject_alloc_failures", "cdvs_set_candidate_capacity", "cdvs_set_detect_variant",
-            "cdvs_detect_tuning", "cdvs_probe_fp32_rate"]
+            "cdvs_detect_tuning", "cdvs_probe_fp32_rate", "cdvs_inject_scfv_wait_timeouts"]
 STAGES = ["detect", "select", "describe", "offsets", "pack", "detect_octave0", "proposal"]
 
 
@@ -116,6 +116,7 @@ def load(build_if_missing: bool = True):
         "cdvs_set_detect_variant": (i32, [P, i32]),
         "cdvs_detect_tuning": (i32, [P, P, i32]),
         "cdvs_probe_fp32_rate": (i32, [P, P]),
+        "cdvs_inject_scfv_wait_timeouts": (None, [i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -433,6 +434,12 @@ def inject_alloc_failures(count: int) -> None:
     """Testing hook: the next `count` workspace allocations fail as if the
     device were out of memory."""
     load().cdvs_inject_alloc_failures(int(count))
+
+
+def inject_scfv_wait_timeouts(count: int) -> None:
+    """Testing hook: the next `count` SCFV calls leave their tensor-core
+    products unissued, so the bounded wait in the posterior kernel runs out."""
+    load().cdvs_inject_scfv_wait_timeouts(int(count))
 
 
 def rank_host(pts: np.ndarray, max_keypoints: int) -> np.ndarray:

@@ -179,6 +179,9 @@ void prof_end(cdvs_ctx* c, int stage, int launches, cudaEvent_t a, cudaStream_t 
 // the next g_fail_allocs workspace allocations fail as cudaMalloc would when
 // the device is out of memory.
 std::atomic<int> g_fail_allocs{0};
+// the next g_skip_products cdvs_scfv calls leave their tensor-core products
+// unissued, so the posterior kernel's bounded wait runs out (a testing hook)
+std::atomic<int> g_skip_products{0};
 
 cudaError_t ensure(DevBuf& b, size_t bytes) {
   if (bytes == 0) bytes = 16;
@@ -1632,6 +1635,8 @@ cdvs_status cdvs_set_candidate_capacity(cdvs_ctx* c, int32_t per_image) {
 
 void cdvs_inject_alloc_failures(int32_t count) { g_fail_allocs.store(count > 0 ? count : 0); }
 
+void cdvs_inject_scfv_wait_timeouts(int32_t count) { g_skip_products.store(count > 0 ? count : 0); }
+
 cdvs_status cdvs_profile(cdvs_ctx* c, int32_t enable) {
   if (!c) return CDVS_INVALID_ARGUMENT;
   c->prof = enable != 0;
@@ -1735,7 +1740,7 @@ cdvs_status cdvs_scfv(cdvs_ctx* c, int32_t n, const float* desc, const int32_t* 
     return fail(c, CDVS_INVALID_ARGUMENT, "n_images in 0..4096 and n_select in 0..512 required");
   if (n == 0) return CDVS_OK;
   if (!counts || (n_select > 0 && !bits)) return fail(c, CDVS_INVALID_ARGUMENT, "NULL counts or bits");
-  std::vector<int> off(n + 1, 0);
+  std::vector<int> off(n + 2, 0);  // record offsets, then the device status word (0)
   for (int i = 0; i < n; ++i) {
     if (counts[i] < 0) return fail(c, CDVS_INVALID_ARGUMENT, "negative count");
     off[i + 1] = off[i] + counts[i];
@@ -1755,7 +1760,7 @@ cdvs_status cdvs_scfv(cdvs_ctx* c, int32_t n, const float* desc, const int32_t* 
   if ((e = ensure(c->scfv_y, sizeof(float) * std::max<size_t>(n_rec, 1) * kScfvDim)) != cudaSuccess ||
       (e = ensure(c->scfv_q, sizeof(float) * std::max<size_t>(n_rec, 1) * kScfvComp)) != cudaSuccess ||
       (e = ensure(c->scfv_out, sizeof(float) * out_floats)) != cudaSuccess ||
-      (e = ensure(c->scfv_off, sizeof(int) * (n + 1))) != cudaSuccess ||
+      (e = ensure(c->scfv_off, sizeof(int) * (n + 2))) != cudaSuccess ||
       (!dev_in && n_rec > 0 && (e = ensure(c->scfv_desc, sizeof(float) * 128 * (size_t)n_rec)) != cudaSuccess))
     return cuda_fail(c, e, "SCFV workspace");
   float* sc = static_cast<float*>(c->scfv_out.p);
@@ -1776,11 +1781,18 @@ cdvs_status cdvs_scfv(cdvs_ctx* c, int32_t n, const float* desc, const int32_t* 
       return cuda_fail(c, e, "descriptor upload");
     d_desc = static_cast<const float*>(c->scfv_desc.p);
   }
-  if ((e = cudaMemcpyAsync(c->scfv_off.p, off.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+  int* d_status = static_cast<int*>(c->scfv_off.p) + n + 1;
+  int skip = 0;  // the testing hook: leave one call's tensor-core products unissued
+  for (int f = g_skip_products.load(); f > 0;)
+    if (g_skip_products.compare_exchange_weak(f, f - 1)) {
+      skip = 1;
+      break;
+    }
+  if ((e = cudaMemcpyAsync(c->scfv_off.p, off.data(), sizeof(int) * (n + 2), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = launch_scfv(d_desc, n_rec, static_cast<const int*>(c->scfv_off.p), n,
                        static_cast<const float*>(c->scfv_model.p), n_select, static_cast<float*>(c->scfv_y.p),
-                       static_cast<float*>(c->scfv_q.p), o_mu, o_sig, o_delta, o_order, o_bits, c->n_sms, s)) !=
-          cudaSuccess)
+                       static_cast<float*>(c->scfv_q.p), o_mu, o_sig, o_delta, o_order, o_bits, d_status, skip,
+                       c->n_sms, s)) != cudaSuccess)
     return cuda_fail(c, e, "SCFV launch");
   if (!dev_out) {
     struct Out {
@@ -1794,7 +1806,14 @@ cdvs_status cdvs_scfv(cdvs_ctx* c, int32_t n, const float* desc, const int32_t* 
       if (o.h && o.bytes && (e = cudaMemcpyAsync(o.h, o.d, o.bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return cuda_fail(c, e, "SCFV readback");
   }
-  if ((!dev_in || !dev_out) && (e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(c, e, "SCFV");
+  if (!dev_in || !dev_out) {
+    int st = 0;
+    if ((e = cudaMemcpyAsync(&st, d_status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+      return cuda_fail(c, e, "SCFV");
+    if (st & kStatusTimeout)
+      return fail(c, CDVS_DEVICE_TIMEOUT, "SCFV: the tensor-core products did not complete within the bounded wait");
+  }
   return CDVS_OK;
 }
 

@@ -298,6 +298,6 @@ inline int kScfvPfIndex(int s, int j8, int lane, int q) { return ((s * 4 + j8) *
 cudaError_t probe_ffma2(int n_sms, double* tflops);
 cudaError_t launch_scfv(const float* desc, int n_rec, const int* rec_off, int n_images, const float* model,
                         int n_select, float* Y, float* Q, float* g_mu, float* g_sig, float* delta, int* order,
-                        uint32_t* bits, int n_sms, cudaStream_t s);
+                        uint32_t* bits, int* status, int skip_products, int n_sms, cudaStream_t s);
 
 }  // namespace cdvs

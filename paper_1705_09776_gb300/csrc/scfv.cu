@@ -85,19 +85,27 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t a, uint32_t lbo, uint32_t s
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Waits (at most 2^20 polls) for phase `parity` of the mbarrier; false when
-// it gave up.
+// Waits for phase `parity` of the mbarrier to complete: at most 2^22 polls
+// and 0.2 s (the global nanosecond timer); false when it gave up.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t done = 0;
-  for (int it = 0; it < (1 << 20) && !done; ++it) {
+  const uint64_t t0 = global_ns();
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t done = 0;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(done)
         : "r"(smem_addr(bar)), "r"(parity)
         : "memory");
+    if (done) return true;
+    if (global_ns() - t0 > 200000000ull) return false;
   }
-  return done != 0;
+  return false;
 }
 
 // 32 consecutive accumulator columns of this warp's 32 lanes (one record per
@@ -135,8 +143,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t addr, float (&v)[32]) {
 //      components kPartCols (w / 4) .. ; l = acc / e_i + c_i; a running maximum
 //      and sum of exponentials, then the posteriors: two passes over the
 //      accumulators, the four parts of a record combined in a fixed order.
-// A tile whose products do not complete within the bounded wait gets NaN
-// posteriors.
+// Should a tile's products not complete within the bounded wait, the CTA
+// sets kStatusTimeout in *status, stops, waits (bounded again) for the
+// products still in flight and frees its tensor memory; the gradient kernel
+// then writes NaN gradients.  skip_products (a testing hook) leaves the
+// products unissued, so that the wait runs out with nothing in flight.
 // Fragment layouts of m16n8k16 (f16): lane = 4 g + t; A register q holds
 // row g + 8 (q & 1), columns 2t + 8 (q >> 1) + {0, 1}; B register q holds
 // rows 2t + 8 q + {0, 1}, column g; C elements (g, 2t), (g, 2t + 1),
@@ -160,7 +171,8 @@ constexpr int kPostSmemBytes = 2 * kTcBBytes + 2 * kTcABytes + 2 * kPfWords * 4;
 static_assert(kScfvWHalfWords * 4 == kTcBBytes, "the model's B halves are the staged ones");
 
 __global__ void __launch_bounds__(kPostThreads, 1) scfv_post_kernel(const float* desc, int n_rec,
-                                                                    const float* model, float* Y, float* Q) {
+                                                                    const float* model, float* Y, float* Q,
+                                                                    int* status, int skip_products) {
   extern __shared__ __align__(128) unsigned char smb[];
   unsigned char* const Bs = smb;                                 // B hi, then B lo
   unsigned char* const As = smb + 2 * kTcBBytes;                 // A hi, then A lo
@@ -200,6 +212,7 @@ __global__ void __launch_bounds__(kPostThreads, 1) scfv_post_kernel(const float*
   tc_fence_after();
   const uint32_t tmem = tmem_base;
   uint32_t phase = 0;
+  bool inflight = false;  // products of an abandoned tile may still be running
   for (int r0 = blockIdx.x * kPostTile; r0 < n_rec; r0 += gridDim.x * kPostTile) {
     {  // 1. projection: warp w takes records 16 (w % 8) .. + 15 and kProjTiles 8-column output tiles
       const int rw = 16 * (warp & 7), j0 = kProjTiles * (warp >> 3);
@@ -271,7 +284,7 @@ __global__ void __launch_bounds__(kPostThreads, 1) scfv_post_kernel(const float*
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     // 2. the products, one thread
-    if (tid == 0) {
+    if (tid == 0 && !skip_products) {
       tc_fence_after();
       const uint32_t a0 = smem_addr(As), b0 = smem_addr(Bs);
 #pragma unroll
@@ -298,6 +311,11 @@ __global__ void __launch_bounds__(kPostThreads, 1) scfv_post_kernel(const float*
     // keeps a running maximum m and sum of exp(l - m), rescaled once per
     // piece; the four parts of a record combine in a fixed order.
     const bool ok = mbar_wait(&mbar, phase);
+    if (__syncthreads_or(!ok)) {  // uniform: any thread that gave up stops the CTA
+      if (tid == 0) atomicOr(status, kStatusTimeout);
+      inflight = !skip_products;
+      break;
+    }
     phase ^= 1u;
     tc_fence_after();
     const int quad = warp & 3, part = warp >> 2, r = 32 * quad + lane, n0 = kPartCols * part;
@@ -334,7 +352,7 @@ __global__ void __launch_bounds__(kPostThreads, 1) scfv_post_kernel(const float*
     float S = 0.0f;
 #pragma unroll
     for (int p = 0; p < kPostParts; ++p) S = fmaf(reds[p][r], ex2_approx((redm[p][r] - M) * kLog2e), S);
-    const float inv = ok ? 1.0f / S : __int_as_float(0x7fc00000);
+    const float inv = 1.0f / S;
     const float mref = M * kLog2e;
     // every lane reads (the loads are warp-collective); lanes past the last
     // record store nothing
@@ -358,6 +376,8 @@ __global__ void __launch_bounds__(kPostThreads, 1) scfv_post_kernel(const float*
     }
     tc_fence_before();  // these reads precede the next tile's products
   }
+  // the abandoned tile's products finish (bounded) before their tensor memory is freed
+  if (inflight) mbar_wait(&mbar, phase);
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
@@ -400,13 +420,22 @@ __device__ __forceinline__ void load_q_chunk(const float* Q, int c0, int nr, flo
 }
 
 __global__ void __launch_bounds__(kGradThreads, 1) scfv_grad_kernel(const float* Y, const float* Q, const int* rec_off,
-                                                                    const float* model, float* g_mu, float* g_sig) {
+                                                                    const float* model, float* g_mu, float* g_sig,
+                                                                    const int* status) {
   extern __shared__ float4 gsm4[];
   float* const qbuf = reinterpret_cast<float*>(gsm4);                       // 2 x [32][kQPitch]
   uint32_t* const zh = reinterpret_cast<uint32_t*>(qbuf + 2 * kGradQWords);  // [16 record pairs][72]
   uint32_t* const zl = zh + kGradZWords;
   const int b = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
+  if (*status & kStatusTimeout) {  // the posteriors are incomplete: NaN gradients
+    const float nan = __int_as_float(0x7fc00000);
+    for (int e = tid; e < kComp * kDim; e += kGradThreads) {
+      g_mu[(size_t)b * kComp * kDim + e] = nan;
+      g_sig[(size_t)b * kComp * kDim + e] = nan;
+    }
+    return;
+  }
   const int t0 = rec_off[b], t1 = rec_off[b + 1];
   float acc[2][kZCols / 8][4];
 #pragma unroll
@@ -548,7 +577,7 @@ __global__ void __launch_bounds__(kComp) scfv_rank_kernel(const float* g_mu, int
 
 cudaError_t launch_scfv(const float* desc, int n_rec, const int* rec_off, int n_images, const float* model,
                         int n_select, float* Y, float* Q, float* g_mu, float* g_sig, float* delta, int* order,
-                        uint32_t* bits, int n_sms, cudaStream_t s) {
+                        uint32_t* bits, int* status, int skip_products, int n_sms, cudaStream_t s) {
   if (n_images <= 0) return cudaSuccess;
   if (n_rec > 0) {
     const int pbytes = kPostSmemBytes;
@@ -556,13 +585,13 @@ cudaError_t launch_scfv(const float* desc, int n_rec, const int* rec_off, int n_
     cudaError_t e = prepare_launch(scfv_post_kernel, post_cache, pbytes, kPostThreads, nullptr);
     if (e != cudaSuccess) return e;
     scfv_post_kernel<<<std::max(1, std::min((n_rec + kPostTile - 1) / kPostTile, n_sms)), kPostThreads, pbytes, s>>>(
-        desc, n_rec, model, Y, Q);
+        desc, n_rec, model, Y, Q, status, skip_products);
   }
   const int gbytes = (int)(sizeof(float) * kGradSmemWords);
   static LaunchCache grad_cache;
   cudaError_t e = prepare_launch(scfv_grad_kernel, grad_cache, gbytes, kGradThreads, nullptr);
   if (e != cudaSuccess) return e;
-  scfv_grad_kernel<<<n_images, kGradThreads, gbytes, s>>>(Y, Q, rec_off, model, g_mu, g_sig);
+  scfv_grad_kernel<<<n_images, kGradThreads, gbytes, s>>>(Y, Q, rec_off, model, g_mu, g_sig, status);
   scfv_rank_kernel<<<n_images, kComp, 0, s>>>(g_mu, n_select, delta, order, bits);
   return cudaGetLastError();
 }

@@ -114,3 +114,27 @@ def test_scfv_ragged_counts_match_oracle(env):
                 assert not g_mu[b].any() and not g_sig[b].any()
                 continue
             _check_image(g_mu[b], g_sig[b], delta[b], X, model)
+
+
+def test_scfv_bounded_wait_reports_and_context_recovers(env):
+    """The posterior kernel's wait on the tensor-core products is bounded:
+    with the products left unissued (the testing hook; nothing faults and
+    nothing is in flight) the wait runs out after 0.2 s, the synchronous call
+    reports CUDA_ERROR and the gradients it computed are NaN; the next call
+    on the same context matches the oracle again."""
+    cdvs, ctx, model = env
+    imgs = [synth.blob_image(synth.image_seed(84, i)) for i in range(2)]
+    kp, desc, cnt, _ = ctx.extract(imgs)
+    d = np.ascontiguousarray(desc, np.float32)
+    c = np.ascontiguousarray(cnt, np.int32)
+    g_mu = np.zeros((len(c), 512, 32), np.float32)
+    g_sig = np.zeros_like(g_mu)
+    cdvs.inject_scfv_wait_timeouts(1)
+    st = ctx._L.cdvs_scfv(ctx.handle, len(c), d.ctypes.data, c.ctypes.data, 0, g_mu.ctypes.data, g_sig.ctypes.data,
+                          None, None, None, 0, None)
+    assert st == cdvs.CDVS_DEVICE_TIMEOUT
+    assert np.isnan(g_mu).all() and np.isnan(g_sig).all()
+    g_mu2, g_sig2, delta2, _, _ = ctx.scfv(desc, cnt, 16)
+    off = np.concatenate([[0], np.cumsum(cnt)])
+    for b in range(len(cnt)):
+        _check_image(g_mu2[b], g_sig2[b], delta2[b], desc[off[b]:off[b + 1]].astype(np.float64), model)
