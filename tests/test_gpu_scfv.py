@@ -120,7 +120,7 @@ def test_scfv_bounded_wait_reports_and_context_recovers(env):
     """The posterior kernel's wait on the tensor-core products is bounded:
     with the products left unissued (the testing hook; nothing faults and
     nothing is in flight) the wait runs out after 0.2 s, the synchronous call
-    reports CUDA_ERROR and the gradients it computed are NaN; the next call
+    reports DEVICE_TIMEOUT and the gradients it computed are NaN; the next call
     on the same context matches the oracle again."""
     cdvs, ctx, model = env
     imgs = [synth.blob_image(synth.image_seed(84, i)) for i in range(2)]
