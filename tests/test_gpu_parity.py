@@ -200,6 +200,13 @@ def test_extract_end_to_end(ctx, cd, w, h):
     img = _img(w, h, seed=5)
     gk, gd, cnt, st = ctx.extract([img])
     assert st == cd.CDVS_OK
+    _check_end_to_end(img, gk, gd, f"{w}x{h}")
+
+
+def _check_end_to_end(img, gk, gd, label):
+    """The GPU's records and descriptors of one image against the oracle's:
+    points by agreement with margin runs, records by the bracketing of
+    parity.py."""
     ek, ed, _ = O.extract(img, O.params())
     lk, _, _ = O.extract(img, O.params(margin=PT.MARGIN))
     sk, _, _ = O.extract(img, O.params(margin=-PT.MARGIN))
@@ -209,7 +216,7 @@ def test_extract_end_to_end(ctx, cd, w, h):
 
     gp, ep = points(gk, "parent_id"), points(ek, "parent")
     agree, n_dis, n_exc, n = PT.point_agreement(gp, ep, points(lk, "parent"), points(sk, "parent"))
-    PT.report(f"end-to-end points {w}x{h}", oracle=n, gpu=len(gp), disagree=n_dis, margin_excluded=n_exc,
+    PT.report(f"end-to-end points {label}", oracle=n, gpu=len(gp), disagree=n_dis, margin_excluded=n_exc,
               agreement=round(agree, 5))
     assert agree >= PT.AGREE, (agree, n_dis, n_exc, n)
     # orientations and descriptors of matched records: the oracle describes
@@ -220,13 +227,45 @@ def test_extract_end_to_end(ctx, cd, w, h):
     good, margin, bad = PT.record_agreement(gk, gd, [(ek, ed), od_l, od_s],
                                             at_point=lambda i: O.describe(img, _oracle_kp_from(gk[i:i + 1]),
                                                                           O.params()))
-    PT.report(f"end-to-end records {w}x{h}", oracle=len(ek), gpu=len(gk), good=good, margin=margin, bad=bad)
+    PT.report(f"end-to-end records {label}", oracle=len(ek), gpu=len(gk), good=good, margin=margin, bad=bad)
     # at least 99.5% of the oracle's records are reproduced, at most 1% of
     # them only as margin cases (a perturbed oracle run, or the oracle at the
     # GPU's own point, reproduces them), and at most 0.5% are not explained
     assert good + margin >= PT.AGREE * len(ek), (good, margin, bad, len(ek))
     assert margin <= 0.01 * len(ek), (good, margin, bad, len(ek))
     assert bad <= (1 - PT.AGREE) * len(ek), (good, margin, bad, len(ek))
+
+
+def test_bench_workload_sampled_images_match_oracle(ctx, cd):
+    """The benchmark's own workload at full size (256 x 640x480, seeded as
+    bench.py seeds it) in the launch configuration bench.py times: device
+    buffers, CDVS_ASYNC calls, one cdvs_wait.  Four sampled images (the first,
+    two in the middle, the last) against the oracle, as end to end above."""
+    import torch
+
+    import bench
+    imgs = bench.make_batch(256)
+    n, H, W = imgs.shape
+    p = cd.params()
+    cap = n * int(p["max_keypoints"][0]) * int(p["max_orientations"][0])
+    d_img = torch.from_numpy(imgs).cuda()
+    d_kp = torch.zeros(cap * cd.KEYPOINT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    d_desc = torch.zeros(cap, 128, dtype=torch.float32, device="cuda")
+    d_cnt = torch.zeros(n, dtype=torch.int32, device="cuda")
+    sizes = np.array([(W, H, W)] * n, cd.IMAGE_DESC_DTYPE)
+    dptrs = [d_img.data_ptr() + i * H * W for i in range(n)]
+    flags = cd.CDVS_INPUT_DEVICE | cd.CDVS_OUTPUT_DEVICE | cd.CDVS_ASYNC
+    stream = torch.cuda.current_stream()
+    for _ in range(3):  # as the bench's steps: the later calls run with the tuner's state of the earlier
+        ctx.extract_raw(n, dptrs, sizes, p, d_kp, d_desc, cap, d_cnt, flags, stream)
+    assert ctx.wait(stream) == cd.CDVS_OK
+    cnt = d_cnt.cpu().numpy()
+    tot = int(cnt.sum())
+    kp = d_kp[:tot * cd.KEYPOINT_DTYPE.itemsize].cpu().numpy().view(cd.KEYPOINT_DTYPE)
+    desc = d_desc[:tot].cpu().numpy()
+    off = np.concatenate([[0], np.cumsum(cnt)])
+    for i in (0, 85, 170, 255):
+        _check_end_to_end(imgs[i], kp[off[i]:off[i + 1]], desc[off[i]:off[i + 1]], f"bench batch image {i}")
 
 
 # ------------------------------------------------------------------ batches
