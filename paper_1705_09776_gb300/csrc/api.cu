@@ -79,7 +79,7 @@ struct cdvs_ctx {
   // learned block proposal: parameters, per-call image table, logits, tile modes, training workspace
   DevBuf prop_theta, prop_imgs, prop_logits, prop_mode, prop_ws;
   DevBuf resized, resize_jobs;  // S0: resized images and their job table
-  DevBuf scfv_model, scfv_desc, scfv_y, scfv_q, scfv_out, scfv_off;  // SCFV model and scratch
+  DevBuf scfv_model, scfv_desc, scfv_q, scfv_out, scfv_off;  // SCFV model and scratch (scfv_q: the gradient operands)
   DevBuf out_counters;  // per output group: slot claims, scan CTAs done, first record (+1)
   bool scfv_set = false;
   // the per-call staging sets (StageSet) and the CUDA graph that
@@ -1340,7 +1340,7 @@ void cdvs_destroy(cdvs_ctx* c) {
                     &c->rec_total, &c->plans,
                     &c->tile_prefix, &c->status, &c->input, &c->dump, &c->stage_kp, &c->stage_desc,
                     &c->prop_theta, &c->prop_imgs, &c->prop_logits, &c->prop_mode, &c->prop_ws,
-                    &c->resized, &c->resize_jobs, &c->scfv_model, &c->scfv_desc, &c->scfv_y, &c->scfv_q,
+                    &c->resized, &c->resize_jobs, &c->scfv_model, &c->scfv_desc, &c->scfv_q,
                     &c->scfv_out, &c->scfv_off, &c->out_counters};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
@@ -1757,8 +1757,7 @@ cdvs_status cdvs_scfv(cdvs_ctx* c, int32_t n, const float* desc, const int32_t* 
   // scratch: projected descriptors, posteriors, and the outputs the caller
   // does not take (or takes on the host)
   const size_t out_floats = (size_t)n * (2 * per + kScfvComp) + (size_t)n * kScfvComp + (size_t)n * kScfvComp;
-  if ((e = ensure(c->scfv_y, sizeof(float) * std::max<size_t>(n_rec, 1) * kScfvDim)) != cudaSuccess ||
-      (e = ensure(c->scfv_q, sizeof(float) * std::max<size_t>(n_rec, 1) * kScfvComp)) != cudaSuccess ||
+  if ((e = ensure(c->scfv_q, std::max<size_t>(scfv_ops_bytes(n_rec), 16))) != cudaSuccess ||
       (e = ensure(c->scfv_out, sizeof(float) * out_floats)) != cudaSuccess ||
       (e = ensure(c->scfv_off, sizeof(int) * (n + 2))) != cudaSuccess ||
       (!dev_in && n_rec > 0 && (e = ensure(c->scfv_desc, sizeof(float) * 128 * (size_t)n_rec)) != cudaSuccess))
@@ -1790,8 +1789,8 @@ cdvs_status cdvs_scfv(cdvs_ctx* c, int32_t n, const float* desc, const int32_t* 
     }
   if ((e = cudaMemcpyAsync(c->scfv_off.p, off.data(), sizeof(int) * (n + 2), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = launch_scfv(d_desc, n_rec, static_cast<const int*>(c->scfv_off.p), n,
-                       static_cast<const float*>(c->scfv_model.p), n_select, static_cast<float*>(c->scfv_y.p),
-                       static_cast<float*>(c->scfv_q.p), o_mu, o_sig, o_delta, o_order, o_bits, d_status, skip,
+                       static_cast<const float*>(c->scfv_model.p), n_select, c->scfv_q.p, o_mu, o_sig, o_delta,
+                       o_order, o_bits, d_status, skip,
                        c->n_sms, s)) != cudaSuccess)
     return cuda_fail(c, e, "SCFV launch");
   if (!dev_out) {

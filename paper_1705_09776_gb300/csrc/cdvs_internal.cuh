@@ -296,8 +296,11 @@ inline int kScfvTcBIndex(int i, int k) { return (i / 8) * 512 + (k / 8) * 64 + (
 inline int kScfvPfIndex(int s, int j8, int lane, int q) { return ((s * 4 + j8) * 32 + lane) * 2 + q; }
 // The measured packed-FP32 FMA rate of the current device (probe.cu).
 cudaError_t probe_ffma2(int n_sms, double* tflops);
+// The bytes of the operands the posterior kernel writes for the gradient
+// products (32-record chunks of the batch).
+size_t scfv_ops_bytes(int n_rec);
 cudaError_t launch_scfv(const float* desc, int n_rec, const int* rec_off, int n_images, const float* model,
-                        int n_select, float* Y, float* Q, float* g_mu, float* g_sig, float* delta, int* order,
+                        int n_select, void* ops, float* g_mu, float* g_sig, float* delta, int* order,
                         uint32_t* bits, int* status, int skip_products, int n_sms, cudaStream_t s);
 
 }  // namespace cdvs

@@ -19,7 +19,9 @@
 //     with the accumulators in tensor memory;
 //   * per image, S = Gamma^T [1 | y | y^2] (512 x 65), from which
 //     g_mu = (S_y - mu S_1) / s and g_sigma = (S_yy - 2 mu S_y + mu^2 S_1) / v - S_1,
-//     on mma.sync.
+//     also on tcgen05, its operands written ready by the posterior kernel.
+// (The PCA projection, 1/8 of Eq. 10's products, runs on mma.sync inside the
+// posterior kernel, whose shared memory holds no room for its operands.)
 // Both split their operands into two FP16 halves (x = hi + lo) and take
 // three products per term (hi hi + hi lo + lo hi), accumulated in FP32:
 // about 22 significant bits per product, so the softmax, which needs the
@@ -152,7 +154,23 @@ __device__ __forceinline__ void tmem_ld32(uint32_t addr, float (&v)[32]) {
 // row g + 8 (q & 1), columns 2t + 8 (q >> 1) + {0, 1}; B register q holds
 // rows 2t + 8 q + {0, 1}, column g; C elements (g, 2t), (g, 2t + 1),
 // (g + 8, 2t), (g + 8, 2t + 1).
+// The posterior kernel's output is the gradient products' operands, laid
+// out as the gradient kernel stages them: per chunk of 32 consecutive
+// records of the batch (kChunkBytes, 16-byte aligned),
+//   Gamma^T hi | Gamma^T lo   MN-major: element (component m, record k) at
+//                             (k / 8) 8 KB + (m / 8) 128 + (k % 8) 16 + (m % 8) 2
+//   Z hi | Z lo               K-major, Z = [1 | y | y^2 | 0] (80 columns):
+//                             element (column n, record k) at
+//                             (n / 8) 512 + (k / 8) 128 + (n % 8) 16 + (k % 8) 2
+// in FP16 halves (x = hi + lo).  Records past the batch's last are zero.
+constexpr int kChunk = 32, kZCols = 80;
+constexpr int kGKst = kComp / 8 * 128;                   // 8 KB: Gamma^T bytes between 8-record groups
+constexpr int kGBytes = kChunk / 8 * kGKst;              // 32 KB per half
+constexpr int kZSbo = kChunk / 8 * 128;                  // 512: Z bytes between 8-column groups
+constexpr int kZBytes = kZCols / 8 * kZSbo;              // 5 KB per half
+constexpr int kChunkBytes = 2 * kGBytes + 2 * kZBytes;   // 75776
 constexpr int kPostTile = 128, kPostThreads = 256, kYPitch = 36;
+static_assert(kPostTile % kChunk == 0, "posterior tiles hold whole chunks");
 constexpr int kPostWarps = kPostThreads / 32;
 constexpr int kPostParts = kPostWarps / 4;          // column parts of a record in the softmax
 constexpr int kPartCols = kComp / kPostParts;
@@ -171,7 +189,7 @@ constexpr int kPostSmemBytes = 2 * kTcBBytes + 2 * kTcABytes + 2 * kPfWords * 4;
 static_assert(kScfvWHalfWords * 4 == kTcBBytes, "the model's B halves are the staged ones");
 
 __global__ void __launch_bounds__(kPostThreads, 1) scfv_post_kernel(const float* desc, int n_rec,
-                                                                    const float* model, float* Y, float* Q,
+                                                                    const float* model, unsigned char* ops,
                                                                     int* status, int skip_products) {
   extern __shared__ __align__(128) unsigned char smb[];
   unsigned char* const Bs = smb;                                 // B hi, then B lo
@@ -260,9 +278,34 @@ __global__ void __launch_bounds__(kPostThreads, 1) scfv_post_kernel(const float*
       }
     }
     __syncthreads();  // ys complete; the previous tile's accumulator reads are done (fenced)
-    for (int e = tid; e < kPostTile * kDim; e += kPostThreads) {
-      const int r = e / kDim, k = e - r * kDim;
-      if (r0 + r < n_rec) Y[(size_t)(r0 + r) * kDim + k] = ys[r][k];
+    // Z = [1 | y | y^2 | 0] of the tile's chunks: a 16-byte row per (column
+    // n, 8 records) and half; records past the last are zero
+    const int n_chunks = (n_rec + kChunk - 1) / kChunk;
+    for (int e = tid; e < (kPostTile / 8) * kZCols; e += kPostThreads) {
+      const int n = e % kZCols, rg = e / kZCols;  // rg: 8-record group of the tile
+      const int C = (r0 + 8 * rg) / kChunk;
+      if (C >= n_chunks) continue;
+      uint32_t hi[4], lo[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        float z[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int rl = 8 * rg + 2 * u + h;
+          float x = 0.0f;
+          if (r0 + rl < n_rec) {
+            if (n == 0) x = 1.0f;
+            else if (n <= kDim) x = ys[rl][n - 1];
+            else if (n <= 2 * kDim) x = ys[rl][n - 1 - kDim] * ys[rl][n - 1 - kDim];
+          }
+          z[h] = x;
+        }
+        split_h2(z[0], z[1], hi[u], lo[u]);
+      }
+      unsigned char* zb = ops + (size_t)C * kChunkBytes + 2 * kGBytes;
+      const int off = (n >> 3) * kZSbo + (((r0 + 8 * rg) % kChunk) >> 3) * 128 + (n & 7) * 16;
+      *reinterpret_cast<uint4*>(zb + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<uint4*>(zb + kZBytes + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
     // A = [y^2 | y] in FP16 halves: 8-element pieces (record r, columns 8 kc ..)
     for (int e = tid; e < kPostTile * 8; e += kPostThreads) {
@@ -354,24 +397,33 @@ __global__ void __launch_bounds__(kPostThreads, 1) scfv_post_kernel(const float*
     for (int p = 0; p < kPostParts; ++p) S = fmaf(reds[p][r], ex2_approx((redm[p][r] - M) * kLog2e), S);
     const float inv = 1.0f / S;
     const float mref = M * kLog2e;
-    // every lane reads (the loads are warp-collective); lanes past the last
-    // record store nothing
+    // every lane reads (the loads are warp-collective).  A lane's record k of
+    // chunk C: 8 components at a time into 16-byte rows of Gamma^T hi / lo;
+    // records past the last are written as zero up to the chunk's end.
     const bool live = r0 + r < n_rec;
-    float4* out = reinterpret_cast<float4*>(Q + (size_t)min(r0 + r, n_rec - 1) * kComp + n0);
+    const bool in_chunks = r0 + r < kChunk * ((n_rec + kChunk - 1) / kChunk);
+    unsigned char* const gb = ops + (size_t)((r0 + r) / kChunk) * kChunkBytes +
+                              (((r0 + r) % kChunk) >> 3) * kGKst + ((r0 + r) & 7) * 16;
 #pragma unroll 1
     for (int c = 0; c < kPartCols / 32; ++c) {
       float v[32];
       tmem_ld32(taddr + 32 * c, v);
 #pragma unroll
-      for (int e = 0; e < 32; e += 4) {
-        const float4 iv = *reinterpret_cast<const float4*>(inve + n0 + 32 * c + e);
-        const float4 cv = *reinterpret_cast<const float4*>(cs + n0 + 32 * c + e);
-        float4 o;
-        o.x = ex2_approx(fmaf(fmaf(v[e], iv.x, cv.x), kLog2e, -mref)) * inv;
-        o.y = ex2_approx(fmaf(fmaf(v[e + 1], iv.y, cv.y), kLog2e, -mref)) * inv;
-        o.z = ex2_approx(fmaf(fmaf(v[e + 2], iv.z, cv.z), kLog2e, -mref)) * inv;
-        o.w = ex2_approx(fmaf(fmaf(v[e + 3], iv.w, cv.w), kLog2e, -mref)) * inv;
-        if (live) out[(32 * c + e) / 4] = o;
+      for (int e = 0; e < 32; e += 8) {
+        float o[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          o[u] = live ? ex2_approx(fmaf(fmaf(v[e + u], inve[n0 + 32 * c + e + u], cs[n0 + 32 * c + e + u]), kLog2e,
+                                        -mref)) * inv
+                      : 0.0f;
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) split_h2(o[2 * u], o[2 * u + 1], hi[u], lo[u]);
+        const int m = n0 + 32 * c + e;  // 8-component group
+        if (in_chunks) {
+          *reinterpret_cast<uint4*>(gb + (m >> 3) * 128) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+          *reinterpret_cast<uint4*>(gb + kGBytes + (m >> 3) * 128) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        }
       }
     }
     tc_fence_before();  // these reads precede the next tile's products
@@ -386,153 +438,205 @@ __global__ void __launch_bounds__(kPostThreads, 1) scfv_post_kernel(const float*
 }
 
 // K_c: Fisher gradients as per-image products S = Gamma^T [1 | y | y^2]
-// (512 x 65, padded to 72 columns), one CTA per image: warp w owns
-// components 32w .. 32w + 31 (two 16-row tiles) and all nine 8-column tiles.
-// The image's records go through in chunks of 32 (two 16-deep k-steps); the
-// chunk's posteriors arrive by asynchronous copies, double-buffered, while
-// the previous chunk is multiplied.  Operands are split into FP16 hi / lo
-// (x = hi + lo, 22 significant bits; posteriors lie in [0, 1] and
-// [1 | y | y^2] within +-4 for the projections of unit descriptors on the
-// orthonormal PCA rows, far inside FP16's range) and multiplied by
-// mma.sync m16n8k16 with FP32 accumulation, three products per term.  The
-// [1 | y | y^2] chunk is split once, into shared memory, for all warps.
-// Fragment layouts of m16n8k16 (f16): lane = 4 g + t; A register q holds
-// row g + 8 (q & 1), columns 2t + 8 (q >> 1) + {0, 1}; B register q holds
-// rows 2t + 8 q + {0, 1}, column g; C as for m16n8k8.
-constexpr int kGradChunk = 32, kGradThreads = 512, kZCols = 72, kQPitch = kComp + 8, kSPitch = 73;
-// dynamic shared memory (32-bit words): two posterior chunks | Z hi, lo as
-// record pairs | (after the loop) S for 256 components at a time
-constexpr int kGradQWords = kGradChunk * kQPitch;
-constexpr int kGradZWords = (kGradChunk / 2) * kZCols;
-constexpr int kGradSmemWords = 2 * kGradQWords + 2 * kGradZWords;
-static_assert(256 * kSPitch <= 2 * kGradQWords, "S of 256 components fits the posterior buffers");
+// (512 x 65, padded to 80 columns) on tcgen05, one CTA of 16 warps per image;
+// g_mu = (S_y - mu S_1) / s and g_sigma = (S_yy - 2 mu S_y + mu^2 S_1) / v - S_1.
+// The operands come ready from the posterior kernel, chunk by chunk (32
+// records of the batch, kChunkBytes): one bulk asynchronous copy stages a
+// chunk into one of two operand buffers, completing on that buffer's
+// mbarrier.  In the image's first and last chunk the records of the
+// neighbouring images keep their posteriors but get zero rows of Z, so they
+// add nothing.  Per chunk one thread issues 24 products (four 128-component
+// blocks x two k-steps x lo hi, hi lo, hi hi; M = 128, N = 80, K = 16) into
+// 4 x 80 tensor-memory columns, accumulated over the image's chunks; once a
+// chunk's products complete, its buffer takes the chunk two ahead.  Then
+// warp w reads the accumulators of component block w / 4, lanes of quadrant
+// w % 4: thread = component, its 65 sums in registers, and writes its row
+// of g_mu and g_sigma.  Every wait is bounded.
+constexpr int kGradThreads = 512;
+// kind::f16: FP32 accumulator, FP16 A (MN-major) and B (K-major), N = 80, M = 128
+constexpr uint32_t kGradIdesc =
+    (1u << 4) | (1u << 15) | ((uint32_t)(kZCols >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+constexpr int kGradSmemBytes = 2 * kChunkBytes;
 
-// Posteriors of records c0 .. c0 + nr - 1 (nr <= 32) into a chunk buffer;
-// the rows past nr are zeroed.
-__device__ __forceinline__ void load_q_chunk(const float* Q, int c0, int nr, float* qs) {
-  for (int e = threadIdx.x; e < kGradChunk * kComp / 4; e += kGradThreads) {
-    const int r = e / (kComp / 4), c4 = e - r * (kComp / 4);
-    float* dst = qs + r * kQPitch + 4 * c4;
-    if (r < nr) cp_async16(dst, Q + (size_t)(c0 + r) * kComp + 4 * c4);
-    else *reinterpret_cast<float4*>(dst) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  }
-  asm volatile("cp.async.commit_group;" ::: "memory");
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, int bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
 }
 
-__global__ void __launch_bounds__(kGradThreads, 1) scfv_grad_kernel(const float* Y, const float* Q, const int* rec_off,
+// One thread: the 24 products of the chunk in buffer `buf`, then a commit to
+// `bar`.  da0 / db0 describe buffer 0's Gamma^T hi and Z hi; every other
+// operand differs in its start address only (the low field, 16-byte units;
+// shared addresses stay below 256 KB, so the sum never carries out).
+__device__ __forceinline__ void grad_issue(uint32_t tmem, uint64_t da0, uint64_t db0, int buf, bool first,
+                                           uint64_t* bar) {
+  tc_fence_after();
+  const uint64_t b16 = (uint64_t)(buf * kChunkBytes) >> 4;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {  // lo hi, hi lo, hi hi
+#pragma unroll
+      for (int ks = 0; ks < kChunk / 16; ++ks) {
+        const uint64_t da = da0 + b16 + (uint64_t)(((p == 0 ? kGBytes : 0) + j * 2048 + ks * 2 * kGKst) >> 4);
+        const uint64_t db = db0 + b16 + (uint64_t)(((p == 1 ? kZBytes : 0) + ks * 256) >> 4);
+        const uint32_t acc = (first && p == 0 && ks == 0) ? 0u : 1u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem + (uint32_t)(kZCols * j)),
+            "l"(da), "l"(db), "r"(kGradIdesc), "r"(acc));
+      }
+    }
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+               : "memory");
+}
+
+__global__ void __launch_bounds__(kGradThreads, 1) scfv_grad_kernel(const unsigned char* ops, const int* rec_off,
                                                                     const float* model, float* g_mu, float* g_sig,
-                                                                    const int* status) {
-  extern __shared__ float4 gsm4[];
-  float* const qbuf = reinterpret_cast<float*>(gsm4);                       // 2 x [32][kQPitch]
-  uint32_t* const zh = reinterpret_cast<uint32_t*>(qbuf + 2 * kGradQWords);  // [16 record pairs][72]
-  uint32_t* const zl = zh + kGradZWords;
+                                                                    int* status) {
+  extern __shared__ __align__(128) unsigned char gsm[];
+  __shared__ __align__(8) uint64_t bars[4];  // copies into buffer 0, 1; products from buffer 0, 1
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
   const int b = blockIdx.x;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
-  if (*status & kStatusTimeout) {  // the posteriors are incomplete: NaN gradients
-    const float nan = __int_as_float(0x7fc00000);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float nan = __int_as_float(0x7fc00000);
+  const int t0 = rec_off[b], t1 = rec_off[b + 1];
+  if ((*status & kStatusTimeout) || t1 <= t0) {
+    // incomplete posteriors: NaN; no descriptor: zero gradients
+    const float v = t1 <= t0 && !(*status & kStatusTimeout) ? 0.0f : nan;
+    for (int e = tid; e < kComp * kDim; e += kGradThreads) {
+      g_mu[(size_t)b * kComp * kDim + e] = v;
+      g_sig[(size_t)b * kComp * kDim + e] = v;
+    }
+    return;
+  }
+  const int C0 = t0 / kChunk, n_ch = (t1 - 1) / kChunk - C0 + 1;
+  if (tid == 0) {
+    for (int q = 0; q < 4; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bars[q])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_flag = 0;
+    for (int q = 0; q < 2 && q < n_ch; ++q)  // chunks 0 and 1 on their way
+      bulk_copy(gsm + q * kChunkBytes, ops + (size_t)(C0 + q) * kChunkBytes, kChunkBytes, &bars[q]);
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  const uint64_t da0 = tc_desc(smem_addr(gsm), kGKst, 128);               // MN-major: K stride, M stride
+  const uint64_t db0 = tc_desc(smem_addr(gsm + 2 * kGBytes), 128, kZSbo);  // K-major
+  uint32_t cph[2] = {0u, 0u};  // parity of each buffer's next copy completion
+  uint32_t mph[2] = {0u, 0u};  // (thread 0) parity of each buffer's next product completion
+  bool copy_out[2] = {n_ch > 0, n_ch > 1};  // (thread 0) copies issued, not yet seen complete by all
+  bool failed = false;
+  int last_issued = -1;  // the last chunk whose products were issued
+  for (int c = 0; c < n_ch; ++c) {
+    const int s = c & 1;
+    unsigned char* const buf = gsm + s * kChunkBytes;
+    const bool ok = mbar_wait(&bars[s], cph[s]);  // chunk c staged
+    if (__syncthreads_or(!ok || abort_flag)) {
+      failed = true;
+      break;
+    }
+    cph[s] ^= 1u;
+    copy_out[s] = false;
+    // records of the chunk outside the image: zero Z rows (both halves)
+    const int g0 = (C0 + c) * kChunk;
+    const int lo = max(t0 - g0, 0), hi = min(t1 - g0, kChunk);
+    if (lo > 0 || hi < kChunk) {
+      for (int e = tid; e < kChunk * kZCols; e += kGradThreads) {
+        const int k = e / kZCols, n = e - k * kZCols;
+        if (k >= lo && k < hi) continue;
+        const int off = 2 * kGBytes + (n >> 3) * kZSbo + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
+        *reinterpret_cast<__half*>(buf + off) = __float2half_rn(0.0f);
+        *reinterpret_cast<__half*>(buf + kZBytes + off) = __float2half_rn(0.0f);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // read by the tensor cores
+      __syncthreads();
+    }
+    last_issued = c;
+    if (tid == 0) {
+      grad_issue(tmem, da0, db0, s, c == 0, &bars[2 + s]);
+      if (c + 2 < n_ch) {  // this buffer takes chunk c + 2 once the products have read it
+        if (mbar_wait(&bars[2 + s], mph[s])) {
+          mph[s] ^= 1u;
+          bulk_copy(buf, ops + (size_t)(C0 + c + 2) * kChunkBytes, kChunkBytes, &bars[s]);
+          copy_out[s] = true;
+        } else {
+          abort_flag = 1;
+        }
+      }
+    }
+  }
+  // every product complete before the accumulators are read or freed: the
+  // last issued chunk's commit covers all earlier products.  Its buffer's
+  // barrier completes once per chunk of that parity, so the wait is for
+  // phase last_issued / 2; the earlier phases are complete (the chunk was
+  // staged only after them), so the parity is unambiguous.
+  if (last_issued >= 0 && !mbar_wait(&bars[2 + (last_issued & 1)], (uint32_t)((last_issued >> 1) & 1)))
+    failed = true;
+  // (thread 0) copies still in flight land before the kernel ends
+  if (tid == 0)
+    for (int q = 0; q < 2; ++q)
+      if (copy_out[q] && !mbar_wait(&bars[q], cph[q])) failed = true;
+  failed = __syncthreads_or(failed);
+  tc_fence_after();
+  if (failed) {
+    if (tid == 0) atomicOr(status, kStatusTimeout);
     for (int e = tid; e < kComp * kDim; e += kGradThreads) {
       g_mu[(size_t)b * kComp * kDim + e] = nan;
       g_sig[(size_t)b * kComp * kDim + e] = nan;
     }
-    return;
-  }
-  const int t0 = rec_off[b], t1 = rec_off[b + 1];
-  float acc[2][kZCols / 8][4];
+  } else {
+    // thread = component i: S_1, S_y, S_yy from its accumulator lane
+    const int j = warp >> 2, quad = warp & 3, i = 128 * j + 32 * quad + lane;
+    const uint32_t taddr = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(kZCols * j);
+    float sa[32], sb[32], s0;
+    {
+      float v[32];
+      tmem_ld32(taddr, v);  // columns 0 .. 31: S_1, S_y[0 .. 30]
+      s0 = v[0];
 #pragma unroll
-  for (int m = 0; m < 2; ++m)
+      for (int k = 0; k < 31; ++k) sa[k] = v[k + 1];
+      tmem_ld32(taddr + 32, v);  // columns 32 .. 63: S_y[31], S_yy[0 .. 30]
+      sa[31] = v[0];
 #pragma unroll
-    for (int j = 0; j < kZCols / 8; ++j)
+      for (int k = 0; k < 31; ++k) sb[k] = v[k + 1];
+      tmem_ld32(taddr + 64, v);  // columns 64 ..: S_yy[31]
+      sb[31] = v[0];
+    }
+    const float inv = 1.0f / (float)(t1 - t0);
+    const float nm = inv * model[kScfvOffNmu + i], ns = inv * model[kScfvOffNsig + i];
+    const float* mu = model + kScfvOffMu + (size_t)i * kDim;
+    const float* isd = model + kScfvOffIsd + (size_t)i * kDim;
+    float4* om = reinterpret_cast<float4*>(g_mu + ((size_t)b * kComp + i) * kDim);
+    float4* os = reinterpret_cast<float4*>(g_sig + ((size_t)b * kComp + i) * kDim);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[m][j][q] = 0.0f;
-  if (t0 < t1) load_q_chunk(Q, t0, min(kGradChunk, t1 - t0), qbuf);
-  for (int c0 = t0, buf = 0; c0 < t1; c0 += kGradChunk, buf ^= 1) {
-    const int nr = min(kGradChunk, t1 - c0);
-    // [1 | y | y^2] of the chunk, split, as record pairs (every warp is past
-    // the previous chunk's products: the barrier at the end of the loop)
-    for (int e = tid; e < kGradZWords; e += kGradThreads) {
-      const int rp = e / kZCols, c = e - rp * kZCols;
-      float z[2];
+    for (int k4 = 0; k4 < kDim / 4; ++k4) {
+      float gm[4], gs[4];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int r = 2 * rp + h;
-        z[h] = 0.0f;
-        if (r < nr) {
-          if (c == 0) z[h] = 1.0f;
-          else if (c <= kDim) z[h] = Y[(size_t)(c0 + r) * kDim + c - 1];
-          else if (c <= 2 * kDim) {
-            const float y = Y[(size_t)(c0 + r) * kDim + c - 1 - kDim];
-            z[h] = y * y;
-          }
-        }
+      for (int u = 0; u < 4; ++u) {
+        const int k = 4 * k4 + u;
+        const float m = __ldg(mu + k), d = __ldg(isd + k);
+        gm[u] = nm * d * fmaf(-m, s0, sa[k]);
+        gs[u] = ns * fmaf(d * d, fmaf(m, fmaf(m, s0, -2.0f * sa[k]), sb[k]), -s0);
       }
-      split_h2(z[0], z[1], zh[e], zl[e]);
+      om[k4] = make_float4(gm[0], gm[1], gm[2], gm[3]);
+      os[k4] = make_float4(gs[0], gs[1], gs[2], gs[3]);
     }
-    // the next chunk's posteriors on their way; this chunk's have landed
-    if (c0 + kGradChunk < t1) {
-      load_q_chunk(Q, c0 + kGradChunk, min(kGradChunk, t1 - c0 - kGradChunk), qbuf + (buf ^ 1) * kGradQWords);
-      asm volatile("cp.async.wait_group 1;" ::: "memory");
-    } else {
-      asm volatile("cp.async.wait_group 0;" ::: "memory");
-    }
-    __syncthreads();
-    const float* qs = qbuf + buf * kGradQWords;
-#pragma unroll
-    for (int s = 0; s < kGradChunk / 16; ++s) {
-      // A = Gamma^T: rows = components 32 warp + 16 m .., columns = records 16 s ..
-      uint32_t ah[2][4], al[2][4];
-#pragma unroll
-      for (int m = 0; m < 2; ++m)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int c = 32 * warp + 16 * m + g + 8 * (q & 1);
-          const int r = 16 * s + 2 * t + 8 * (q >> 1);
-          split_h2(qs[r * kQPitch + c], qs[(r + 1) * kQPitch + c], ah[m][q], al[m][q]);
-        }
-#pragma unroll
-      for (int j = 0; j < kZCols / 8; ++j) {
-        const int rp = 8 * s + t, col = 8 * j + g;
-        const uint32_t bh[2] = {zh[rp * kZCols + col], zh[(rp + 4) * kZCols + col]};
-        const uint32_t bl[2] = {zl[rp * kZCols + col], zl[(rp + 4) * kZCols + col]};
-#pragma unroll
-        for (int m = 0; m < 2; ++m) {
-          mma_f16(acc[m][j], al[m], bh);
-          mma_f16(acc[m][j], ah[m], bl);
-          mma_f16(acc[m][j], ah[m], bh);
-        }
-      }
-    }
-    __syncthreads();  // the chunk's buffers are rewritten next
   }
-  // S rows = components, columns = [1 | y | y^2 | pad], 256 components at a
-  // time in the posterior buffers, then the gradients
-  const int K = t1 - t0;
-  const float inv = K > 0 ? 1.0f / (float)K : 0.0f;
-  float* const S = qbuf;
-#pragma unroll
-  for (int half = 0; half < 2; ++half) {
-    if ((warp >> 3) == half) {
-      const int rl = 32 * (warp & 7);
-#pragma unroll
-      for (int m = 0; m < 2; ++m)
-#pragma unroll
-        for (int j = 0; j < kZCols / 8; ++j) {
-          S[(rl + 16 * m + g) * kSPitch + 8 * j + 2 * t] = acc[m][j][0];
-          S[(rl + 16 * m + g) * kSPitch + 8 * j + 2 * t + 1] = acc[m][j][1];
-          S[(rl + 16 * m + g + 8) * kSPitch + 8 * j + 2 * t] = acc[m][j][2];
-          S[(rl + 16 * m + g + 8) * kSPitch + 8 * j + 2 * t + 1] = acc[m][j][3];
-        }
-    }
-    __syncthreads();
-    for (int e = tid; e < 256 * kDim; e += kGradThreads) {
-      const int il = e / kDim, k = e - il * kDim, i = 256 * half + il;
-      const float s0 = S[il * kSPitch], s1 = S[il * kSPitch + 1 + k], s2 = S[il * kSPitch + 1 + kDim + k];
-      const float mu = model[kScfvOffMu + i * kDim + k], isd = model[kScfvOffIsd + i * kDim + k];
-      const float nm = inv * model[kScfvOffNmu + i], ns = inv * model[kScfvOffNsig + i];
-      const size_t o = ((size_t)b * kComp + i) * kDim + k;
-      g_mu[o] = nm * isd * fmaf(-mu, s0, s1);
-      g_sig[o] = ns * fmaf(isd * isd, fmaf(mu, fmaf(mu, s0, -2.0f * s1), s2), -s0);
-    }
-    __syncthreads();
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
   }
 }
 
@@ -575,8 +679,10 @@ __global__ void __launch_bounds__(kComp) scfv_rank_kernel(const float* g_mu, int
 
 }  // namespace
 
+size_t scfv_ops_bytes(int n_rec) { return (size_t)((n_rec + kChunk - 1) / kChunk) * kChunkBytes; }
+
 cudaError_t launch_scfv(const float* desc, int n_rec, const int* rec_off, int n_images, const float* model,
-                        int n_select, float* Y, float* Q, float* g_mu, float* g_sig, float* delta, int* order,
+                        int n_select, void* ops, float* g_mu, float* g_sig, float* delta, int* order,
                         uint32_t* bits, int* status, int skip_products, int n_sms, cudaStream_t s) {
   if (n_images <= 0) return cudaSuccess;
   if (n_rec > 0) {
@@ -585,13 +691,14 @@ cudaError_t launch_scfv(const float* desc, int n_rec, const int* rec_off, int n_
     cudaError_t e = prepare_launch(scfv_post_kernel, post_cache, pbytes, kPostThreads, nullptr);
     if (e != cudaSuccess) return e;
     scfv_post_kernel<<<std::max(1, std::min((n_rec + kPostTile - 1) / kPostTile, n_sms)), kPostThreads, pbytes, s>>>(
-        desc, n_rec, model, Y, Q, status, skip_products);
+        desc, n_rec, model, static_cast<unsigned char*>(ops), status, skip_products);
   }
-  const int gbytes = (int)(sizeof(float) * kGradSmemWords);
+  const int gbytes = kGradSmemBytes;
   static LaunchCache grad_cache;
   cudaError_t e = prepare_launch(scfv_grad_kernel, grad_cache, gbytes, kGradThreads, nullptr);
   if (e != cudaSuccess) return e;
-  scfv_grad_kernel<<<n_images, kGradThreads, gbytes, s>>>(Y, Q, rec_off, model, g_mu, g_sig, status);
+  scfv_grad_kernel<<<n_images, kGradThreads, gbytes, s>>>(static_cast<const unsigned char*>(ops), rec_off, model,
+                                                          g_mu, g_sig, status);
   scfv_rank_kernel<<<n_images, kComp, 0, s>>>(g_mu, n_select, delta, order, bits);
   return cudaGetLastError();
 }
