@@ -614,22 +614,37 @@ __global__ void __launch_bounds__(kGradThreads, 1) scfv_grad_kernel(const unsign
     }
     const float inv = 1.0f / (float)(t1 - t0);
     const float nm = inv * model[kScfvOffNmu + i], ns = inv * model[kScfvOffNsig + i];
-    const float* mu = model + kScfvOffMu + (size_t)i * kDim;
-    const float* isd = model + kScfvOffIsd + (size_t)i * kDim;
-    float4* om = reinterpret_cast<float4*>(g_mu + ((size_t)b * kComp + i) * kDim);
-    float4* os = reinterpret_cast<float4*>(g_sig + ((size_t)b * kComp + i) * kDim);
+    // the component's mu and 1/s rows (128-byte aligned) as 16-byte loads
+    const float4* mu4 = reinterpret_cast<const float4*>(model + kScfvOffMu + (size_t)i * kDim);
+    const float4* isd4 = reinterpret_cast<const float4*>(model + kScfvOffIsd + (size_t)i * kDim);
+    // rows of g_mu and g_sigma into the (now idle) operand buffers, 36-float
+    // pitch, then out by coalesced 16-byte stores
+    constexpr int kRowP = 36;
+    float4* om = reinterpret_cast<float4*>(reinterpret_cast<float*>(gsm) + (size_t)i * kRowP);
+    float4* os = reinterpret_cast<float4*>(reinterpret_cast<float*>(gsm) + (size_t)(kComp + i) * kRowP);
 #pragma unroll
     for (int k4 = 0; k4 < kDim / 4; ++k4) {
+      const float4 m4 = __ldg(mu4 + k4), d4 = __ldg(isd4 + k4);
+      const float mv[4] = {m4.x, m4.y, m4.z, m4.w}, dv[4] = {d4.x, d4.y, d4.z, d4.w};
       float gm[4], gs[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int k = 4 * k4 + u;
-        const float m = __ldg(mu + k), d = __ldg(isd + k);
+        const float m = mv[u], d = dv[u];
         gm[u] = nm * d * fmaf(-m, s0, sa[k]);
         gs[u] = ns * fmaf(d * d, fmaf(m, fmaf(m, s0, -2.0f * sa[k]), sb[k]), -s0);
       }
       om[k4] = make_float4(gm[0], gm[1], gm[2], gm[3]);
       os[k4] = make_float4(gs[0], gs[1], gs[2], gs[3]);
+    }
+    __syncthreads();
+    const float4* sm4 = reinterpret_cast<const float4*>(gsm);
+    float4* gm4 = reinterpret_cast<float4*>(g_mu + (size_t)b * kComp * kDim);
+    float4* gs4 = reinterpret_cast<float4*>(g_sig + (size_t)b * kComp * kDim);
+    for (int e = tid; e < kComp * kDim / 4; e += kGradThreads) {
+      const int row = e / (kDim / 4), c4 = e - row * (kDim / 4);
+      gm4[e] = sm4[row * (kRowP / 4) + c4];
+      gs4[e] = sm4[(kComp + row) * (kRowP / 4) + c4];
     }
   }
   tc_fence_before();
