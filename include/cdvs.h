@@ -401,8 +401,9 @@ cdvs_status cdvs_proposal_train_step(cdvs_ctx *ctx, const uint8_t *images, int32
  * FP16 halves and three products per term (about 22 significant bits per
  * product, FP32 accumulation; each component's column of Eq. 10's matrix is
  * scaled by a power of two into FP16's range, exactly undone); everything
- * else is FP32.  Should the tensor cores not complete the products within a
- * bounded wait (0.2 s), every gradient of the call comes out NaN and a
+ * else is FP32.  Should the tensor cores or the copies feeding them not
+ * complete within a bounded wait (0.2 s), the affected gradients come out
+ * NaN (every image's, when the log-likelihood products time out) and a
  * synchronous call returns CDVS_DEVICE_TIMEOUT; the context stays usable.
  * ------------------------------------------------------------------------- */
 #define CDVS_SCFV_COMPONENTS 512
