@@ -311,7 +311,27 @@ constexpr int kInP = 160;                                  // input row pitch (b
 constexpr int kInfThreads = 256;
 static_assert(kInX + 15 <= kInP, "input rows hold the region after 16-byte alignment");
 constexpr int kA2Tiles = (kA2X * kA2Y + 15) / 16;          // 39 row tiles of conv2
-constexpr size_t kInfSmem = (size_t)kInY * kInP + (size_t)kA1X * kA1Y * kC * 2 + (size_t)kA2X * kA2Y * kC * 2;
+// Shared-memory layout of the activations: one position holds 16 BF16
+// channels in two 16-byte chunks (channels 0-7, 8-15), chunk index 2 p + half.
+// Both buffers permute chunks within each 128-byte line (8 chunks) by an XOR
+// swizzle so that the 8 rows of every ldmatrix matrix fall in 8 different
+// bank groups:
+//  * A1 (row pitch 69 positions): conv2 reads positions two apart, so chunk
+//    bits 0-1 are XORed with bits 3-4;
+//  * A2 (row pitch 36 positions, 34 used): conv3 reads two runs of 4
+//    positions one row apart, so chunk bit 0 is XORed with bit 3.
+// Each buffer is a whole number of lines, so a swizzled chunk stays inside it.
+constexpr int kA2P = 36;                                   // A2 row pitch in shared memory (positions)
+constexpr size_t kLine = 128;
+constexpr size_t kInBytes = ((size_t)kInY * kInP + kLine - 1) / kLine * kLine;
+constexpr size_t kA1Bytes = ((size_t)kA1X * kA1Y * kC * 2 + kLine - 1) / kLine * kLine;
+constexpr size_t kA2Bytes = ((size_t)kA2P * kA2Y * kC * 2 + kLine - 1) / kLine * kLine;
+constexpr size_t kInfSmem = kInBytes + kA1Bytes + kA2Bytes;
+// two CTAs per SM: 228 KB per SM, each CTA also holds under 1 KB of static
+// arrays and the 1 KB the hardware reserves
+static_assert(2 * (kInfSmem + 1024 + 1024) <= 228 * 1024, "two CTAs per SM");
+__device__ __forceinline__ int a1_chunk(int c) { return c ^ ((c >> 3) & 3); }
+__device__ __forceinline__ int a2_chunk(int c) { return c ^ ((c >> 3) & 1); }
 
 __device__ __forceinline__ void ldmatrix_x4(unsigned (&r)[4], const void* p) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
@@ -347,8 +367,8 @@ __global__ void __launch_bounds__(kInfThreads, 2) proposal_infer_kernel(const Pr
                                                                         const uint2* frag, float* logits) {
   extern __shared__ float4 smem4[];
   uint8_t* in_s = reinterpret_cast<uint8_t*>(smem4);
-  __nv_bfloat16* a1_s = reinterpret_cast<__nv_bfloat16*>(in_s + (size_t)kInY * kInP);
-  __nv_bfloat16* a2_s = a1_s + (size_t)kA1X * kA1Y * kC;
+  __nv_bfloat16* a1_s = reinterpret_cast<__nv_bfloat16*>(in_s + kInBytes);
+  __nv_bfloat16* a2_s = reinterpret_cast<__nv_bfloat16*>(in_s + kInBytes + kA1Bytes);
   __shared__ float w1[kC * 9], b1[kC], b2[kC], b3[kC], wh[kC];
   const PropImage im = imgs[blockIdx.z];
   const int bx0 = blockIdx.x * kRBX, by0 = blockIdx.y * kRBY;  // first block of the CTA
@@ -391,33 +411,61 @@ __global__ void __launch_bounds__(kInfThreads, 2) proposal_infer_kernel(const Pr
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
-  // conv1 on the FP32 pipes: A1 positions of the region, zero outside A1
-  for (int p = threadIdx.x; p < kA1X * kA1Y; p += kInfThreads) {
-    const int r = p / kA1X, c = p - r * kA1X;
-    const int gy = ya1 + r, gx = xa1 + c;
-    uint4* dst = reinterpret_cast<uint4*>(a1_s + (size_t)p * kC);
-    if (gy < 0 || gy >= im.H1 || gx < 0 || gx >= im.W1) {
-      dst[0] = make_uint4(0, 0, 0, 0);
-      dst[1] = make_uint4(0, 0, 0, 0);
-      continue;
-    }
-    float xv[9];
+  // conv1 on the tensor cores: row tiles of 16 A1 positions (row-major over
+  // the 69 x 37 region) times the 9 taps (K padded to 16 with zeros) -> 16
+  // channels, mma.sync m16n8k16 BF16 -> FP32.  The inputs (u8 - 128) / 64
+  // are exact in BF16 and the weights are BF16-rounded, so every product is
+  // exact; A1 is zero outside the layer.  Fragments (lane = 4 g + t): A
+  // register q holds position g + 8 (q & 1), taps 2t + 8 (q >> 1) + {0, 1};
+  // B register q holds taps 2t + 8q + {0, 1}, channel 8h + g; C holds
+  // positions g, g + 8 and channels 8h + 2t + {0, 1}.
+  {
+    const int g = lane >> 2, t = lane & 3;
+    unsigned bw1[2][2];  // [n-tile h][register q]
 #pragma unroll
-    for (int k = 0; k < 9; ++k)
-      xv[k] = ((float)in_s[(2 * r + k / 3) * kInP + sh + 2 * c + k % 3] - 128.0f) * (1.0f / 64.0f);
-    unsigned pk[8];
+    for (int h = 0; h < 2; ++h)
 #pragma unroll
-    for (int co = 0; co < kC; co += 2) {
-      float s0 = b1[co], s1 = b1[co + 1];
-#pragma unroll
-      for (int k = 0; k < 9; ++k) {
-        s0 = fmaf(w1[co * 9 + k], xv[k], s0);
-        s1 = fmaf(w1[(co + 1) * 9 + k], xv[k], s1);
+      for (int q = 0; q < 2; ++q) {
+        const int k0 = 2 * t + 8 * q, co = 8 * h + g;
+        const float w0 = k0 < 9 ? w1[co * 9 + k0] : 0.0f, wv = k0 + 1 < 9 ? w1[co * 9 + k0 + 1] : 0.0f;
+        bw1[h][q] = pack_bf16(w0, wv);
       }
-      pk[co / 2] = pack_bf16(fmaxf(s0, 0.0f), fmaxf(s1, 0.0f));
+    constexpr int kA1N = kA1X * kA1Y, kA1Tiles = (kA1N + 15) / 16;
+    for (int tile = warp; tile < kA1Tiles; tile += kInfThreads / 32) {
+      int pr[2], rr1[2], cc1[2];
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        pr[hh] = 16 * tile + g + 8 * hh;
+        const int pc = min(pr[hh], kA1N - 1);  // past the region: a valid position, not stored
+        rr1[hh] = pc / kA1X;
+        cc1[hh] = pc - rr1[hh] * kA1X;
+      }
+      auto x = [&](int hh, int k) {  // input of tap k for position hh (k < 9)
+        return ((float)in_s[(2 * rr1[hh] + k / 3) * kInP + sh + 2 * cc1[hh] + k % 3] - 128.0f) * (1.0f / 64.0f);
+      };
+      unsigned a[4];
+      a[0] = pack_bf16(x(0, 2 * t), x(0, 2 * t + 1));
+      a[1] = pack_bf16(x(1, 2 * t), x(1, 2 * t + 1));
+      a[2] = t == 0 ? pack_bf16(x(0, 8), 0.0f) : 0u;
+      a[3] = t == 0 ? pack_bf16(x(1, 8), 0.0f) : 0u;
+      float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+      mma_bf16(acc[0], a, bw1[0][0], bw1[0][1]);
+      mma_bf16(acc[1], a, bw1[1][0], bw1[1][1]);
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int p = pr[hh];
+        if (p >= kA1N) continue;
+        const int gy = ya1 + rr1[hh], gx = xa1 + cc1[hh];
+        const bool ok = gy >= 0 && gy < im.H1 && gx >= 0 && gx < im.W1;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int co = 8 * h + 2 * t;
+          const float v0 = ok ? fmaxf(acc[h][2 * hh] + b1[co], 0.0f) : 0.0f;
+          const float v1 = ok ? fmaxf(acc[h][2 * hh + 1] + b1[co + 1], 0.0f) : 0.0f;
+          reinterpret_cast<unsigned*>(a1_s)[4 * a1_chunk(2 * p + h) + t] = pack_bf16(v0, v1);
+        }
+      }
     }
-    dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-    dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
   }
   __syncthreads();
   const int q = lane & 3, rr = lane >> 2;
@@ -430,12 +478,12 @@ __global__ void __launch_bounds__(kInfThreads, 2) proposal_infer_kernel(const Pr
       // this lane's ldmatrix row: position 16 t + lane % 16 (clamped), k half lane / 16
       const int pr = min(16 * t + (lane & 15), kA2X * kA2Y - 1);
       const int r2 = pr / kA2X, c2 = pr - (pr / kA2X) * kA2X;
-      const __nv_bfloat16* base = a1_s + ((size_t)(2 * r2) * kA1X + 2 * c2) * kC + 8 * (lane >> 4);
+      const int c0 = 2 * ((2 * r2) * kA1X + 2 * c2) + (lane >> 4);  // chunk of tap 0
       float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
         unsigned a[4];
-        ldmatrix_x4(a, base + ((size_t)(k / 3) * kA1X + k % 3) * kC);
+        ldmatrix_x4(a, a1_s + 8 * a1_chunk(c0 + 2 * ((k / 3) * kA1X + k % 3)));
         mma_bf16(acc[0], a, bw[k][0][0], bw[k][0][1]);
         mma_bf16(acc[1], a, bw[k][1][0], bw[k][1][1]);
       }
@@ -446,13 +494,13 @@ __global__ void __launch_bounds__(kInfThreads, 2) proposal_infer_kernel(const Pr
         const int r2o = p / kA2X, c2o = p - (p / kA2X) * kA2X;
         const int gy = ya2 + r2o, gx = xa2 + c2o;
         const bool ok = gy >= 0 && gy < im.H2 && gx >= 0 && gx < im.W2;
-        unsigned* dst = reinterpret_cast<unsigned*>(a2_s + (size_t)p * kC);
+        const int ps = r2o * kA2P + c2o;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int co = 8 * h + 2 * q;
           const float v0 = ok ? fmaxf(acc[h][2 * half] + b2[co], 0.0f) : 0.0f;
           const float v1 = ok ? fmaxf(acc[h][2 * half + 1] + b2[co + 1], 0.0f) : 0.0f;
-          dst[co / 2] = pack_bf16(v0, v1);
+          reinterpret_cast<unsigned*>(a2_s)[4 * a2_chunk(2 * ps + h) + q] = pack_bf16(v0, v1);
         }
       }
     }
@@ -469,12 +517,12 @@ __global__ void __launch_bounds__(kInfThreads, 2) proposal_infer_kernel(const Pr
       if (ty >= im.Th || tx >= im.Tw) continue;  // warp-uniform
       const int i = lane & 15;
       const int r3 = 4 * cy + i / 4, c3 = 4 * cx + i % 4;
-      const __nv_bfloat16* base = a2_s + ((size_t)r3 * kA2X + c3) * kC + 8 * (lane >> 4);
+      const int c0 = 2 * (r3 * kA2P + c3) + (lane >> 4);  // chunk of tap 0
       float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
         unsigned a[4];
-        ldmatrix_x4(a, base + ((size_t)(k / 3) * kA2X + k % 3) * kC);
+        ldmatrix_x4(a, a2_s + 8 * a2_chunk(c0 + 2 * ((k / 3) * kA2P + k % 3)));
         mma_bf16(acc[0], a, bw[k][0][0], bw[k][0][1]);
         mma_bf16(acc[1], a, bw[k][1][0], bw[k][1][1]);
       }
