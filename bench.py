@@ -338,25 +338,35 @@ def tile_modes(logits, zt, H, W, reach):
 def run_learned(ctx, imgs, step_with, p_plain, args, cdvs, torch, plain_kp):
     """The same batch with the learned block proposal masking first-octave
     detection: throughput, keypoint recall against the plain detector (exact
-    record identity), and how the first-octave tiles were treated."""
+    record identity), and how the first-octave tiles were treated.  Also the
+    mechanism's floor on this batch: the same step with a network that
+    proposes no block (every first-octave tile takes its cheapest mode, the
+    network still runs at full cost)."""
     theta, thr = cdvs.load_proposal_weights()
-    ctx.set_proposal(theta)
     p = cdvs.params(storage=int(p_plain["storage"][0]), use_proposal=1, proposal_threshold=thr)
-    for _ in range(args.warmup):
-        step_with(p)
-    torch.cuda.synchronize()
-    ctx.profile(True)
-    ctx.profile_read(reset=True)
     stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        kp, cnt = step_with(p)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    prof = ctx.profile_read(reset=True)
-    ctx.profile(False)
+
+    def timed(weights):
+        ctx.set_proposal(weights)
+        for _ in range(args.warmup):
+            step_with(p)
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        ctx.profile_read(reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            kp, _ = step_with(p)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = ctx.profile_read(reset=True)
+        ctx.profile(False)
+        return e0.elapsed_time(e1) / args.steps, prof, kp
+
+    none = np.zeros_like(theta)
+    none[-1] = -20.0  # head bias only: every logit is -20
+    ms_none, prof_none, _ = timed(none)
+    ms, prof, kp = timed(theta)
     learned_kp = kp()
     plain = record_keys(plain_kp)
     recall = len(plain & record_keys(learned_kp)) / max(len(plain), 1)
@@ -369,6 +379,8 @@ def run_learned(ctx, imgs, step_with, p_plain, args, cdvs, torch, plain_kp):
             "first_octave_tiles": {"detect": int(counts[2]), "levels_only": int(counts[1]),
                                    "level3_only": int(counts[0])},
             "stage_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+            "no_block_proposed": {"ms_per_step": ms_none,
+                                  "stage_ms_per_step": {k: v[0] / args.steps for k, v in prof_none.items()}},
             "weights": "paper_1705_09776_gb300/proposal_weights.npz (train_proposal.py; images of seeds 1e6+i and, "
                        "with the high-resolution statistics, 5e6+i)"}
 
@@ -830,6 +842,13 @@ def main():
         except Exception as ex:
             out["highres"] = {"error": str(ex)}
     if learned is not None:
+        # break-even: the share of first-octave tiles a mask must take out of
+        # detection (to their cheapest mode) for the saving to pay for the
+        # network and the tile-mode passes
+        st_none = learned["no_block_proposed"]["stage_ms_per_step"]
+        net_ms = st_none.get("proposal", float("nan"))
+        saving = o0_ms - st_none.get("detect_octave0", float("nan"))
+        learned["break_even_skipped_tile_share"] = net_ms / saving if saving > 0 else None
         out["learned"] = learned
     if scfv is not None:
         out["scfv"] = scfv
