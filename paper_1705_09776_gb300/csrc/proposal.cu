@@ -349,6 +349,13 @@ __device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // .x = lo (low half)
   return *reinterpret_cast<const unsigned*>(&v);
 }
+// relu, round to BF16 and pack in one instruction (the first source goes to
+// the upper half)
+__device__ __forceinline__ unsigned pack_relu_bf16(float lo, float hi) {
+  unsigned r;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
 
 // B fragments of one 16 -> 16 layer for this lane, prepacked by the host
 // (pack_proposal_fragments): one coalesced 8-byte load per tap and half.
@@ -430,6 +437,12 @@ __global__ void __launch_bounds__(kInfThreads, 2) proposal_infer_kernel(const Pr
         const float w0 = k0 < 9 ? w1[co * 9 + k0] : 0.0f, wv = k0 + 1 < 9 ? w1[co * 9 + k0 + 1] : 0.0f;
         bw1[h][q] = pack_bf16(w0, wv);
       }
+    float bias[2][2];  // this lane's output channels 8 h + 2 t + {0, 1}
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      bias[h][0] = b1[8 * h + 2 * t];
+      bias[h][1] = b1[8 * h + 2 * t + 1];
+    }
     constexpr int kA1N = kA1X * kA1Y, kA1Tiles = (kA1N + 15) / 16;
     for (int tile = warp; tile < kA1Tiles; tile += kInfThreads / 32) {
       int pr[2], rr1[2], cc1[2];
@@ -448,7 +461,9 @@ __global__ void __launch_bounds__(kInfThreads, 2) proposal_infer_kernel(const Pr
       a[1] = pack_bf16(x(1, 2 * t), x(1, 2 * t + 1));
       a[2] = t == 0 ? pack_bf16(x(0, 8), 0.0f) : 0u;
       a[3] = t == 0 ? pack_bf16(x(1, 8), 0.0f) : 0u;
-      float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+      // accumulators start at the bias
+      float acc[2][4] = {{bias[0][0], bias[0][1], bias[0][0], bias[0][1]},
+                         {bias[1][0], bias[1][1], bias[1][0], bias[1][1]}};
       mma_bf16(acc[0], a, bw1[0][0], bw1[0][1]);
       mma_bf16(acc[1], a, bw1[1][0], bw1[1][1]);
 #pragma unroll
@@ -459,10 +474,8 @@ __global__ void __launch_bounds__(kInfThreads, 2) proposal_infer_kernel(const Pr
         const bool ok = gy >= 0 && gy < im.H1 && gx >= 0 && gx < im.W1;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const int co = 8 * h + 2 * t;
-          const float v0 = ok ? fmaxf(acc[h][2 * hh] + b1[co], 0.0f) : 0.0f;
-          const float v1 = ok ? fmaxf(acc[h][2 * hh + 1] + b1[co + 1], 0.0f) : 0.0f;
-          reinterpret_cast<unsigned*>(a1_s)[4 * a1_chunk(2 * p + h) + t] = pack_bf16(v0, v1);
+          const unsigned v = pack_relu_bf16(acc[h][2 * hh], acc[h][2 * hh + 1]);
+          reinterpret_cast<unsigned*>(a1_s)[4 * a1_chunk(2 * p + h) + t] = ok ? v : 0u;
         }
       }
     }
@@ -474,12 +487,20 @@ __global__ void __launch_bounds__(kInfThreads, 2) proposal_infer_kernel(const Pr
   {
     unsigned bw[9][2][2];
     load_bfrag(frag, 0, lane, bw);
+    float bias[2][2];  // this lane's output channels 8 h + 2 q + {0, 1}
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      bias[h][0] = b2[8 * h + 2 * q];
+      bias[h][1] = b2[8 * h + 2 * q + 1];
+    }
     for (int t = warp; t < kA2Tiles; t += kInfThreads / 32) {
       // this lane's ldmatrix row: position 16 t + lane % 16 (clamped), k half lane / 16
       const int pr = min(16 * t + (lane & 15), kA2X * kA2Y - 1);
       const int r2 = pr / kA2X, c2 = pr - (pr / kA2X) * kA2X;
       const int c0 = 2 * ((2 * r2) * kA1X + 2 * c2) + (lane >> 4);  // chunk of tap 0
-      float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+      // accumulators start at the bias
+      float acc[2][4] = {{bias[0][0], bias[0][1], bias[0][0], bias[0][1]},
+                         {bias[1][0], bias[1][1], bias[1][0], bias[1][1]}};
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
         unsigned a[4];
@@ -497,10 +518,8 @@ __global__ void __launch_bounds__(kInfThreads, 2) proposal_infer_kernel(const Pr
         const int ps = r2o * kA2P + c2o;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const int co = 8 * h + 2 * q;
-          const float v0 = ok ? fmaxf(acc[h][2 * half] + b2[co], 0.0f) : 0.0f;
-          const float v1 = ok ? fmaxf(acc[h][2 * half + 1] + b2[co + 1], 0.0f) : 0.0f;
-          reinterpret_cast<unsigned*>(a2_s)[4 * a2_chunk(2 * ps + h) + q] = pack_bf16(v0, v1);
+          const unsigned v = pack_relu_bf16(acc[h][2 * half], acc[h][2 * half + 1]);
+          reinterpret_cast<unsigned*>(a2_s)[4 * a2_chunk(2 * ps + h) + q] = ok ? v : 0u;
         }
       }
     }
