@@ -335,6 +335,16 @@ def tile_modes(logits, zt, H, W, reach):
     return counts
 
 
+def break_even_share(network_ms, octave0_plain_ms, octave0_none_ms):
+    """The share of first-octave tiles a mask must take out of detection (to
+    their cheapest mode) for the saving to pay for the network and its
+    tile-mode passes: network time / (plain octave 0 - octave 0 with no block
+    proposed), assuming the saving grows in proportion to the tiles skipped.
+    None when masking saves nothing."""
+    saving = octave0_plain_ms - octave0_none_ms
+    return network_ms / saving if saving > 0 else None
+
+
 def run_learned(ctx, imgs, step_with, p_plain, args, cdvs, torch, plain_kp):
     """The same batch with the learned block proposal masking first-octave
     detection: throughput, keypoint recall against the plain detector (exact
@@ -842,13 +852,9 @@ def main():
         except Exception as ex:
             out["highres"] = {"error": str(ex)}
     if learned is not None:
-        # break-even: the share of first-octave tiles a mask must take out of
-        # detection (to their cheapest mode) for the saving to pay for the
-        # network and the tile-mode passes
         st_none = learned["no_block_proposed"]["stage_ms_per_step"]
-        net_ms = st_none.get("proposal", float("nan"))
-        saving = o0_ms - st_none.get("detect_octave0", float("nan"))
-        learned["break_even_skipped_tile_share"] = net_ms / saving if saving > 0 else None
+        learned["break_even_skipped_tile_share"] = break_even_share(
+            st_none.get("proposal", float("nan")), o0_ms, st_none.get("detect_octave0", float("nan")))
         out["learned"] = learned
     if scfv is not None:
         out["scfv"] = scfv

@@ -70,3 +70,14 @@ def test_tile_modes_rule():
     assert bench.tile_modes([logits], 0.0, H, W, reach=0.0).tolist() == [2, 0, 2]
     logits[1, 7] = 10.0                 # block (1, 7) lies within one block of all four tiles
     assert bench.tile_modes([logits], 0.0, H, W, reach=0.0).tolist() == [0, 0, 4]
+
+
+def test_break_even_share_by_hand():
+    # network 0.5 ms; masking every tile saves 1.86 - 0.69 = 1.17 ms
+    assert abs(bench.break_even_share(0.5, 1.86, 0.69) - 0.5 / 1.17) < 1e-12
+    # a network as costly as the whole saving breaks even only at every tile
+    assert abs(bench.break_even_share(1.0, 2.0, 1.0) - 1.0) < 1e-12
+    # no saving (or a slower masked octave): never pays
+    assert bench.break_even_share(0.5, 1.0, 1.0) is None
+    assert bench.break_even_share(0.5, 1.0, 1.2) is None
+    assert bench.break_even_share(0.5, float("nan"), 0.7) is None
