@@ -1,4 +1,5 @@
-"""Pins of the SCFV oracle (CPU): the joint log-likelihood against scipy's
+"""Pins of the SCFV oracle (CPU): the PCA projection on its basis rows, the
+joint log-likelihood against scipy's
 multivariate normal, both Fisher gradients against finite differences of the
 GMM log-likelihood, a one-component model against its closed form, the
 paper's matrix form of the distance (Eq. 10) against the direct sum with V
@@ -28,6 +29,20 @@ def _loglik(X, m):
     l = S.log_joint(Y, m["weights"], m["means"], m["variances"])
     mx = l.max(axis=1, keepdims=True)
     return float((mx[:, 0] + np.log(np.exp(l - mx).sum(axis=1))).sum())
+
+
+def test_pca_projects_onto_the_basis_rows():
+    """The projection is onto the rows of the orthonormal basis after the mean
+    is taken off: mean + 2.5 P[j] maps to 2.5 e_j, the mean itself to 0, and a
+    vector orthogonal to every row to 0."""
+    m = _small_model(8)
+    P, mean = m["pca"], m["pca_mean"]
+    for j in range(4):
+        np.testing.assert_allclose(S.pca((mean + 2.5 * P[j])[None], mean, P)[0], 2.5 * np.eye(4)[j], atol=1e-12)
+    np.testing.assert_allclose(S.pca(mean[None], mean, P), 0.0, atol=1e-12)
+    v = np.random.default_rng(9).normal(size=10)
+    v -= P.T @ (P @ v)                      # remove the basis components
+    np.testing.assert_allclose(S.pca((mean + v)[None], mean, P), 0.0, atol=1e-12)
 
 
 def test_log_joint_matches_scipy():
