@@ -92,3 +92,53 @@ def test_block_labels():
     y = PO.block_labels([(0.0, 0.0), (15.4, 2.0), (15.6, 2.0), (639.0, 479.0)], 480, 640)
     assert y.shape == (30, 40) and y.sum() == 3
     assert y[0, 0] == 1 and y[0, 1] == 1 and y[29, 39] == 1
+
+
+def test_forward_by_hand_on_constant_images():
+    """The whole forward pass worked by hand.  Channel 0 only: centre taps of
+    1 in all three layers (the centre tap reads the input at (s y, s x)), one
+    extra corner tap of 2^-9 in conv2, head weight 1, head bias 0.25.  On a
+    constant 64 x 64 image the block (1, 1) is interior at every layer, so
+    x = (u - 128) / 64, A1 = relu(x), z2 = A1 (1 + 2^-9), A3 = relu(A2) and the
+    logit is A3 + 0.25.  In BF16 mode A2 is rounded: 1 + 2^-9 lies below half
+    a BF16 ulp above 1 (2^-8), so it rounds to 1."""
+    p = {name: np.zeros(shp) for name, shp in PO.SHAPES}
+    p["W1"][0, 0, 1, 1] = 1.0
+    p["W2"][0, 0, 1, 1] = 1.0
+    p["W2"][0, 0, 0, 0] = 2.0 ** -9
+    p["W3"][0, 0, 1, 1] = 1.0
+    p["Wh"][0] = 1.0
+    p["bh"][0] = 0.25
+    theta = PO.pack(p)
+    cases = [(192, 1.25, 1.25 + 2.0 ** -9),          # x = 1
+             (160, 0.75, 0.75 + 2.0 ** -10),         # x = 0.5
+             (100, 0.25, 0.25)]                      # x < 0: every activation is 0
+    for u, want_bf16, want_fp64 in cases:
+        img = np.full((64, 64), u, np.uint8)
+        z16, _ = PO.forward(img, theta, bf16=True)
+        z64, _ = PO.forward(img, theta, bf16=False)
+        assert z16.shape == (4, 4)
+        assert z16[1, 1] == want_bf16, (u, z16[1, 1])
+        assert z64[1, 1] == want_fp64, (u, z64[1, 1])
+
+
+def test_forward_rounds_the_weights_and_a1_to_bf16():
+    """Channel 0 only: W1 centre 1 and corner 2^-9, W2 centre 1, W3 centre
+    1 + 2^-9, head weight 1.  On a constant image of 192 (x = 1) an interior
+    z1 is 1 + 2^-9, which BF16 rounds to 1 (below half an ulp above 1), and
+    so is W3's centre; A3 is not rounded.  So the logit of the interior block
+    is 1 in BF16 mode and (1 + 2^-9)^2 in FP64, and A1 is 1 in BF16 mode."""
+    p = {name: np.zeros(shp) for name, shp in PO.SHAPES}
+    p["W1"][0, 0, 1, 1] = 1.0
+    p["W1"][0, 0, 0, 0] = 2.0 ** -9
+    p["W2"][0, 0, 1, 1] = 1.0
+    p["W3"][0, 0, 1, 1] = 1.0 + 2.0 ** -9
+    p["Wh"][0] = 1.0
+    theta = PO.pack(p)
+    img = np.full((64, 64), 192, np.uint8)
+    z16, c16 = PO.forward(img, theta, bf16=True)
+    z64, c64 = PO.forward(img, theta, bf16=False)
+    assert c16["a1"][0, 10, 10] == 1.0
+    assert c64["a1"][0, 10, 10] == 1.0 + 2.0 ** -9
+    assert z16[1, 1] == 1.0
+    assert z64[1, 1] == (1.0 + 2.0 ** -9) ** 2
