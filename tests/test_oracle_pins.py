@@ -643,3 +643,113 @@ def test_ternary_values_and_thresholds():
     q = O.ternary(v, lo, hi)
     assert set(np.unique(q)).issubset({-1, 0, 1})
     assert np.array_equal(q, np.where(v < -0.3, -1, np.where(v > 0.3, 1, 0)))
+
+
+def test_extremum_tie_goes_to_the_smaller_sigma(P):
+    """Sec. III-A with two qualifying roots of equal |p|: p(s) = 32 ((s - 2.5)^3
+    - 0.75 (s - 2.5)) has p' = 96 (s - 2)(s - 3), p(2) = 8 (a maximum) and
+    p(3) = -8 (a minimum), all exact in binary.  Both lie in [1.6, 3.2] and
+    reach the contrast 4, so the tie rule decides: the smaller sigma."""
+    a = np.array([-440.0, 576.0, -240.0, 32.0])
+    assert O.alp_extremum(a, P) == (1, 2.0, 8.0)
+    assert O.alp_extremum(-a, P) == (-1, 2.0, -8.0)   # the mirrored cubic: a minimum at 2
+
+
+def test_descriptor_level_is_the_nearest_in_log_scale(P):
+    """Alg. 2 reads the Gaussian level nearest to sigma in log scale: level k
+    of s_k = sigma0 2^(k/3), so t = 3 log2(sigma/sigma0) rounds to the
+    nearest integer, clamped to 0..3."""
+    for t, k in [(-0.7, 0), (0.0, 0), (0.4, 0), (0.6, 1), (1.4, 1), (1.6, 2), (2.6, 3), (3.0, 3), (3.8, 3)]:
+        assert O.desc_level(P, 1.6 * 2.0 ** (t / 3.0)) == k, t
+
+
+@pytest.mark.parametrize("radius,inside", [(4.0, False), (4.0 + 1e-9, True)])
+def test_orientation_disc_is_open(radius, inside):
+    """Sec. IV-B takes the pixels closer than the radius: a voter at distance
+    exactly 4 px (sigma = 1, radius 4 sigma) votes nothing, one just inside the
+    radius votes |g| exp(-d^2 / (2 (1.5 sigma)^2)) into bin 0.  The voter's bump
+    pixels lie 5 px or more away."""
+    p = O.params(ori_radius=radius)
+    G = _voters((41, 41), [((24, 20), (1, 0), 1.0)])
+    th, h = O.orientations(G, 20.0, 20.0, 1.0, p)
+    if inside:
+        assert h[0] == pytest.approx(math.exp(-16.0 / (2 * 1.5 ** 2)), rel=1e-12)
+        assert np.count_nonzero(h) == 1
+    else:
+        assert not h.any() and th.size == 0
+
+
+def test_descriptor_clamp_level(P):
+    """Alg. 2 stage B normalises the 128 sums, clamps at 0.2 and normalises
+    again.  With n = h / |h| and d the descriptor, every entry with n > 0.2
+    takes the same value max(d), and every other entry keeps its ratio to the
+    clamped ones: d_i / max(d) = n_i / 0.2.  That fixes the clamp level from
+    the two outputs without redoing the normalisation."""
+    img = synth.blob_image(synth.image_seed(23, 0), 96, 96, n_blobs=6).astype(np.float64)
+    G = O.filter_separable(img, O.gaussian_taps(2.0))
+    for xo, yo, so, theta in [(48.3, 47.6, 2.2, 0.4), (40.0, 55.5, 3.0, 2.0)]:
+        h = O.descriptor_hist(G, xo, yo, so, theta, P).ravel()
+        d = O.descriptor(G, xo, yo, so, theta, P)
+        n = h / np.linalg.norm(h)
+        big = n > 0.2
+        assert big.any() and (~big & (n > 0)).any()
+        assert np.allclose(d[big], d.max(), rtol=1e-13, atol=0)
+        np.testing.assert_allclose(d[~big] / d.max(), n[~big] / 0.2, rtol=1e-12, atol=1e-15)
+        assert abs(np.linalg.norm(d) - 1.0) < 1e-12
+
+
+def test_ternary_thresholds_are_strict():
+    """Sec. III-C: an element is -1 below its lower threshold and +1 above its
+    upper one; an element equal to either threshold is 0."""
+    lo, hi = np.full(128, -0.25), np.full(128, 0.5)
+    v = np.zeros(128)
+    v[:4] = [-0.25, 0.5, -0.2500001, 0.5000001]
+    q = O.ternary(v, lo, hi)
+    assert q[:4].tolist() == [0, 0, -1, 1] and not q[4:].any()
+
+
+def test_octave_needs_three_pixels_per_side(P):
+    """Alg. 1 builds octaves while both sides are at least 3 px (the 3 x 3
+    neighbour test needs an interior pixel); each octave is ceil(side / 2) of
+    the previous one."""
+    assert O.octave_dims(10, 5, P) == [(10, 5), (5, 3)]          # next would be 3 x 2
+    assert O.octave_dims(3, 3, P) == [(3, 3)]
+    assert O.octave_dims(2, 40, P) == []
+    assert O.octave_dims(40, 40, P) == [(40, 40), (20, 20), (10, 10), (5, 5)]
+
+
+def test_contrast_and_scale_range_are_inclusive():
+    """Sec. III-A: a root counts when |p| >= T and sigma lies in the closed
+    range [s_0, s_3].  p(s) = 2 s^3 - 21 s^2 + 60 s + a0 has p' = 6 (s - 2)(s - 5)
+    (roots exact in binary), a maximum at 2 and p(2) = a0 + 52."""
+    P = O.params()
+    assert O.alp_extremum(np.array([-48.0, 60.0, -21.0, 2.0]), P) == (1, 2.0, 4.0)   # |p| = T = 4
+    assert O.alp_extremum(np.array([-48.5, 60.0, -21.0, 2.0]), P)[0] == 0           # |p| = 3.5 < T
+    P2 = O.params(sigma0=2.0)                                                        # range [2, 4]
+    assert O.alp_extremum(np.array([-44.0, 60.0, -21.0, 2.0]), P2) == (1, 2.0, 8.0)  # root at s_0
+    P3 = O.params(sigma0=2.0000001)
+    assert O.alp_extremum(np.array([-44.0, 60.0, -21.0, 2.0]), P3)[0] == 0           # just outside
+
+
+def test_refine_offset_limit_is_inclusive(P):
+    """Alg. 1 stage B keeps a point whose offset is at most offset_max (0.5):
+    q with left 0, centre 8, right 8, top and bottom 0 gives g = (4, 0),
+    H = diag(-8, -16), delta = (0.5, 0), p-hat = 8 + 0.5 * 4 * 0.5 = 9 and
+    tr^2 / det = 576 / 128 = 4.5, all exact.  A right value of 8.5 moves the
+    offset to 4.25 / 7.5 > 0.5 and drops it."""
+    q = np.array([[0.0, 0.0, 0.0], [0.0, 8.0, 8.0], [0.0, 0.0, 0.0]])
+    ok, out = O.refine(q, P)
+    assert ok == 1 and out.tolist() == [0.5, 0.0, 9.0, 4.5]
+    q[1, 2] = 8.5
+    assert O.refine(q, P)[0] == 0
+
+
+@pytest.mark.parametrize("radius,inside", [(4.0, False), (4.0 + 1e-9, True)])
+def test_descriptor_disc_is_open(radius, inside):
+    """Alg. 2 stage B samples the pixels closer than desc_radius * sigma: a
+    voter at exactly 4 px (sigma = 1, radius 4) votes nothing; just inside it
+    votes.  Its bump pixels lie 5 px or more away."""
+    p = O.params(desc_radius=radius)
+    G = _voters((41, 41), [((24, 20), (1, 0), 1.0)])
+    h = O.descriptor_hist(G, 20.0, 20.0, 1.0, 0.0, p)
+    assert bool(h.any()) == inside
