@@ -1,0 +1,375 @@
+"""Plants one plausible slip at a time into a copy of an oracle and checks that
+the oracle's pins fail with it.  CPU only, run by hand:
+
+    python tests/plant_slips.py [c|proposal|scfv|resize ...] [--only NAME ...]
+
+A slip is one exact text replacement in the oracle's source.  The C oracle's
+copy is built with gcc into a temporary folder and loaded, in a child
+process, in place of the real library; a numpy oracle's copy is loaded, in a
+child process, in place of the real module.  The child runs the oracle's pin
+file and the slip counts as caught when a pin fails.
+
+Prints CAUGHT or SURVIVED per slip and exits 1 when a slip survives that is
+not listed in EXPECTED_SURVIVORS (each with the reason it cannot be caught).
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import subprocess
+import sys
+import tempfile
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# Slips no pin can catch, and why.
+EXPECTED_SURVIVORS = {
+    # The 3 x 3 neighbour test's strictness differs only on exact ties of the
+    # fitted response between neighbours, which filtered images do not give;
+    # near-ties are decided by the bracketing runs (margin = +-1e-4).
+    ("c", "nbr_nonstrict"),
+    # Equivalent: a square image takes the other branch to the same size.
+    ("resize", "ge_to_gt"),
+    # Equivalent: an image whose larger side equals the limit is "resized" to
+    # its own size, which copies it.
+    ("resize", "no_resize_equal"),
+}
+
+
+def _run_child(code: str) -> bool:
+    """True when the child's pytest run failed (the slip was caught)."""
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=1800)
+    return r.returncode != 0
+
+
+def check_c(slips, tmpd):
+    src = open(os.path.join(ROOT, "oracle", "cdvs_oracle.c")).read()
+    for name, old, new in slips:
+        if src.count(old) != 1:
+            raise SystemExit(f"c/{name}: the text to replace occurs {src.count(old)} times")
+        cpath = os.path.join(tmpd, f"{name}.c")
+        lib = os.path.join(tmpd, f"{name}.so")
+        with open(cpath, "w") as f:
+            f.write(src.replace(old, new))
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                               "-I", os.path.join(ROOT, "oracle"), cpath, "-o", lib, "-lm"])
+        code = ("import sys; sys.path.insert(0, '.'); import oracle.oracle as O; "
+                f"O.LIB_PATH = {lib!r}; O.build = lambda force=False: {lib!r}; import pytest; "
+                "sys.exit(pytest.main(['-q', '-x', '-p', 'no:cacheprovider', 'tests/test_oracle_pins.py']))")
+        yield name, _run_child(code)
+
+
+def check_py(module: str, test_file: str, slips, tmpd):
+    path = os.path.join(ROOT, "oracle", f"{module}.py")
+    src = open(path).read()
+    for name, old, new in slips:
+        if src.count(old) != 1:
+            raise SystemExit(f"{module}/{name}: the text to replace occurs {src.count(old)} times")
+        mpath = os.path.join(tmpd, f"{module}_{name}.py")
+        with open(mpath, "w") as f:
+            f.write(src.replace(old, new))
+        code = ("import sys, types; sys.path.insert(0, '.'); import oracle; "
+                f"m = types.ModuleType('oracle.{module}'); m.__file__ = {path!r}; "
+                f"exec(compile(open({mpath!r}).read(), {path!r}, 'exec'), m.__dict__); "
+                f"sys.modules['oracle.{module}'] = m; oracle.{module} = m; import pytest; "
+                f"sys.exit(pytest.main(['-q', '-x', '-p', 'no:cacheprovider', {test_file!r}]))")
+        yield name, _run_child(code)
+
+
+# ---- slips of the C oracle (S1-S11): name, text, replacement
+C_SLIPS = [
+    ('scale_den',
+     '(double)k / (double)(p->scales_per_octave - 1)',
+     '(double)k / (double)(p->scales_per_octave)'),
+    ('tau_base_swap',
+     '(o == 0) ? p->sigma_in : p->sigma0',
+     '(o == 0) ? p->sigma0 : p->sigma_in'),
+    ('taps_3sigma',
+     '(int)ceil(4.0 * tau)',
+     '(int)ceil(3.0 * tau)'),
+    ('decimate_odd',
+     'top[(size_t)(2 * y) * Wo[o - 1] + 2 * x]',
+     'top[(size_t)(2 * y + 1) * Wo[o - 1] + 2 * x + 1]'),
+    ('lap_no_s2',
+     'L[(size_t)y * W + x] = s * s * (',
+     'L[(size_t)y * W + x] = s * ('),
+    ('lap_sign',
+     '(l + r + u + d - 4.0 * c)',
+     '(4.0 * c - l - r - u - d)'),
+    ('ext_type_flip',
+     'int t = pdd < 0.0 ? +1 : -1;',
+     'int t = pdd < 0.0 ? -1 : +1;'),
+    ('ext_tie_larger_s',
+     '(fabs(v) == fabs(best_v) && s < best_s)',
+     '(fabs(v) == fabs(best_v) && s > best_s)'),
+    ('ext_first_wins',
+     'if (best_t == 0 || fabs(v) > fabs(best_v) ||',
+     'if (best_t == 0 || fabs(v) < fabs(best_v) ||'),
+    ('ref_hxy_sign',
+     '0.25 * (q[8] - q[6] - q[2] + q[0])',
+     '0.25 * (q[8] - q[6] + q[2] - q[0])'),
+    ('ref_dx_sign',
+     'double dx = -(hyy * gx - hxy * gy) / det;',
+     'double dx = (hyy * gx - hxy * gy) / det;'),
+    ('ref_resp_full',
+     'q[4] + 0.5 * (gx * dx + gy * dy)',
+     'q[4] + (gx * dx + gy * dy)'),
+    ('edge_lim_no_div',
+     '(p->edge_r + 1.0) * (p->edge_r + 1.0) / p->edge_r',
+     '(p->edge_r + 1.0) * (p->edge_r + 1.0)'),
+    ('nbr_nonstrict',
+     't > 0 ? !(pn < v + m * fabs(v)) : !(pn > v - m * fabs(v))',
+     't > 0 ? !(pn <= v + m * fabs(v)) : !(pn >= v - m * fabs(v))'),
+    ('kp_scale_oct',
+     'const double scale = ldexp(1.0, o);',
+     'const double scale = ldexp(1.0, o + 1);'),
+    ('dd_window_half',
+     'double win = ldexp(1.0, oc) * (1.0 - m);',
+     'double win = ldexp(1.0, oc - 1) * (1.0 - m);'),
+    ('dd_keep_lower',
+     'if (rb > ra * (1.0 + m) ||',
+     'if (rb < ra * (1.0 - m) ||'),
+    ('dd_tie_finer',
+     '(m == 0.0 && rb == ra && c[b].octave < c[a].octave)',
+     '(m == 0.0 && rb == ra && c[b].octave > c[a].octave)'),
+    ('sel_y_desc',
+     'if (a->y != b->y) return a->y < b->y ? -1 : 1;',
+     'if (a->y != b->y) return a->y < b->y ? 1 : -1;'),
+    ('sel_x_before_y',
+     'if (a->y != b->y) return a->y < b->y ? -1 : 1;\n    if (a->x != b->x) return a->x < b->x ? -1 : 1;',
+     'if (a->x != b->x) return a->x < b->x ? -1 : 1;\n    if (a->y != b->y) return a->y < b->y ? -1 : 1;'),
+    ('desc_level_floor',
+     '(int)lround((double)(K - 1) * log2(so / p->sigma0))',
+     '(int)floor((double)(K - 1) * log2(so / p->sigma0))'),
+    ('grad_gy_sign',
+     '*gy = G[(size_t)clampi(v + 1, 0, H - 1) * W + u] - G[(size_t)clampi(v - 1, 0, H - 1) * W + u];',
+     '*gy = G[(size_t)clampi(v - 1, 0, H - 1) * W + u] - G[(size_t)clampi(v + 1, 0, H - 1) * W + u];'),
+    ('ori_disc_le',
+     'if (!(d2 < R2)) continue;',
+     'if (!(d2 <= R2)) continue;'),
+    ('ori_w_no_half',
+     'exp(-d2 / (2.0 * sw * sw))',
+     'exp(-d2 / (sw * sw))'),
+    ('ori_peak_ge',
+     'if (!(c > l && c > r)) continue;',
+     'if (!(c >= l && c >= r)) continue;'),
+    ('ori_parab_sign',
+     'double off = 0.5 * (l - r) / (l - 2.0 * c + r);',
+     'double off = 0.5 * (r - l) / (l - 2.0 * c + r);'),
+    ('ori_centre_no_half',
+     '((double)b + 0.5 + off) / 36.0',
+     '((double)b + off) / 36.0'),
+    ('desc_rot_sign',
+     'double xr = (ct * du + st * dv) / cs;\n            double yr = (-st * du + ct * dv) / cs;',
+     'double xr = (ct * du - st * dv) / cs;\n            double yr = (st * du + ct * dv) / cs;'),
+    ('desc_rel_plus',
+     'double rel = atan2(gy, gx) - theta;',
+     'double rel = atan2(gy, gx) + theta;'),
+    ('desc_cell_offset_2',
+     'double cx = xr + 1.5, cy = yr + 1.5;',
+     'double cx = xr + 2.0, cy = yr + 2.0;'),
+    ('desc_xy_swap',
+     'd[(yy * 4 + xx) * 8 + oo]',
+     'd[(xx * 4 + yy) * 8 + oo]'),
+    ('desc_clamp_03',
+     'if (d[i] > 0.2) d[i] = 0.2;',
+     'if (d[i] > 0.3) d[i] = 0.3;'),
+    ('desc_no_renorm',
+     '    inv = 1.0 / sqrt(n2);\n    for (int i = 0; i < 128; ++i) d[i] *= inv;\n}',
+     '    inv = 1.0;\n    for (int i = 0; i < 128; ++i) d[i] *= inv;\n}'),
+    ('oct_floor_half',
+     'w = (w + 1) / 2; /* ceil(W/2): decimation keeps the even coordinates */',
+     'w = w / 2;'),
+    ('oct_min_size',
+     'if (w < 3 || h < 3) break;',
+     'if (w < 2 || h < 2) break;'),
+    ('desc_disc_le',
+     'if (!(du * du + dv * dv < R2)) continue;',
+     'if (!(du * du + dv * dv <= R2)) continue;'),
+    ('tr_a_v2',
+     'v[2] = (h[0] - h[1]) / 2.0;\n    v[3] = (h[2] - h[3]) / 2.0;',
+     'v[2] = (h[1] - h[0]) / 2.0;\n    v[3] = (h[2] - h[3]) / 2.0;'),
+    ('tr_b_v7_div4',
+     'v[7] = ((h[0] + h[1] + h[2] + h[3]) - (h[4] + h[5] + h[6] + h[7])) / 8.0;',
+     'v[7] = ((h[0] + h[1] + h[2] + h[3]) - (h[4] + h[5] + h[6] + h[7])) / 4.0;'),
+    ('tr_checker_swap',
+     'if (((cx + cy) & 1) == 0) transform_set_a',
+     'if (((cx + cy) & 1) == 1) transform_set_a'),
+    ('tern_le',
+     'q[j] = (int8_t)(v[j] < t_lo[j] ? -1 : (v[j] > t_hi[j] ? 1 : 0));',
+     'q[j] = (int8_t)(v[j] <= t_lo[j] ? -1 : (v[j] >= t_hi[j] ? 1 : 0));'),
+    ('dd_dlog_no_abs',
+     'if (!(fabs(log2(c[a].sigma / c[b].sigma)) <= p->dedupe_dlog2 * (1.0 - m))) continue;',
+     'if (!(log2(c[a].sigma / c[b].sigma) <= p->dedupe_dlog2 * (1.0 - m))) continue;'),
+    ('sel_no_cap',
+     'int N = m < p->max_keypoints ? m : p->max_keypoints;',
+     'int N = m;'),
+    ('ori_max_ori',
+     'int n = np < p->max_orientations ? np : p->max_orientations;',
+     'int n = np;'),
+    ('ori_bin_round',
+     'double fl = floor(f);',
+     'double fl = floor(f + 0.5);'),
+    ('contrast_strict',
+     'if (!(fabs(v) >= T)) continue;',
+     'if (!(fabs(v) > T)) continue;'),
+    ('offset_lt',
+     'if (!(fabs(dx) <= omax && fabs(dy) <= omax)) return 0;',
+     'if (!(fabs(dx) < omax && fabs(dy) < omax)) return 0;'),
+    ('sigma_range_open',
+     'if (!(s >= lo && s <= hi)) continue;',
+     'if (!(s > lo && s < hi)) continue;'),
+]
+
+# ---- slips of the proposal-network oracle
+PROPOSAL_SLIPS = [
+    ('no_bf16_a1',
+     'a1 = rnd(np.maximum(z1, 0.0))',
+     'a1 = np.maximum(z1, 0.0)'),
+    ('w_not_rounded',
+     'w1, w2, w3, wh = rnd(p["W1"]), rnd(p["W2"]), rnd(p["W3"]), rnd(p["Wh"])',
+     'w1, w2, w3, wh = p["W1"], p["W2"], p["W3"], p["Wh"]'),
+    ('conv1_stride1',
+     'z1 = conv3x3(x, w1, p["b1"], 2)',
+     'z1 = conv3x3(x, w1, p["b1"], 1)'),
+    ('pool_cells_2',
+     'cell = a3[:, 4 * ty:min(4 * ty + 4, H2), 4 * tx:min(4 * tx + 4, W2)]',
+     'cell = a3[:, 2 * ty:min(2 * ty + 2, H2), 2 * tx:min(2 * tx + 2, W2)]'),
+    ('b2_dropped',
+     'z2 = conv3x3(a1, w2, p["b2"], 2)',
+     'z2 = conv3x3(a1, w2, 0 * p["b2"], 2)'),
+    ('bce_no_log1p',
+     '+ np.log1p(np.exp(-np.abs(z)))',
+     '+ 0.0'),
+    ('input_shift_127',
+     '(np.asarray(img, np.float64) - 128.0) / 64.0',
+     '(np.asarray(img, np.float64) - 127.0) / 64.0'),
+    ('no_relu_a3',
+     'a3 = np.maximum(z3, 0.0)',
+     'a3 = z3'),
+    ('pool_sum_over_16',
+     'cell.mean(axis=(1, 2)) if cell.size else 0.0',
+     'cell.sum(axis=(1, 2)) / 16.0 if cell.size else 0.0'),
+    ('head_bias_sign',
+     '+ p["bh"][0]',
+     '- p["bh"][0]'),
+    ('no_bf16_a2',
+     'a2 = rnd(np.maximum(z2, 0.0))',
+     'a2 = np.maximum(z2, 0.0)'),
+    ('conv3_stride2',
+     'z3 = conv3x3(a2, w3, p["b3"], 1)',
+     'z3 = conv3x3(a2, w3, p["b3"], 2)'),
+    ('bce_sign',
+     '- y * z +',
+     '+ y * z +'),
+    ('blocks_of_8',
+     'th, tw = -(-H // 16), -(-W // 16)',
+     'th, tw = -(-H // 8), -(-W // 8)'),
+]
+
+# ---- slips of the SCFV oracle
+SCFV_SLIPS = [
+    ('bits_ge',
+     'if g_mu[i, k] > 0:',
+     'if g_mu[i, k] >= 0:'),
+    ('bits_reversed',
+     'word |= 1 << k',
+     'word |= 1 << (31 - k)'),
+    ('pca_plus_mean',
+     '(np.asarray(X, np.float64) - np.asarray(mean, np.float64))',
+     '(np.asarray(X, np.float64) + np.asarray(mean, np.float64))'),
+    ('logjoint_no_logw',
+     'l[:, i] = math.log(w[i]) - 0.5',
+     'l[:, i] = 0.0 - 0.5'),
+    ('logjoint_no_norm',
+     '+ np.log(2 * math.pi * var[i]).sum())',
+     '+ 0.0)'),
+    ('gmu_w_not_sqrt',
+     '/ (K * math.sqrt(w[i]))',
+     '/ (K * w[i])'),
+    ('gsig_no_sqrt2',
+     '/ (K * math.sqrt(2.0 * w[i]))',
+     '/ (K * math.sqrt(w[i]))'),
+    ('gsig_minus_half',
+     '(d * d - 1.0)',
+     '(d * d - 0.5)'),
+    ('d_over_var',
+     'd = (Y - means[i]) / sd[i]',
+     'd = (Y - means[i]) / var[i]'),
+    ('delta_no_center',
+     '((g_mu - g_mu.mean(axis=1, keepdims=True)) ** 2)',
+     '(g_mu ** 2)'),
+    ('ranking_ties_high',
+     'key=lambda i: (-delta[i], i)',
+     'key=lambda i: (-delta[i], -i)'),
+    ('ranking_ascending',
+     'key=lambda i: (-delta[i], i)',
+     'key=lambda i: (delta[i], i)'),
+]
+
+# ---- slips of the S0 resize oracle
+RESIZE_SLIPS = [
+    ('round_half_up',
+     'if 2 * r > den or (2 * r == den and q % 2 == 1):',
+     'if 2 * r >= den:'),
+    ('round_floor',
+     '    if 2 * r > den or (2 * r == den and q % 2 == 1):\n        q += 1\n',
+     ''),
+    ('size_floor',
+     'return max_side, max(1, round_half_even_div(height * max_side, width))',
+     'return max_side, max(1, (height * max_side) // width)'),
+    ('size_swap',
+     'return max(1, round_half_even_div(width * max_side, height)), max_side',
+     'return max_side, max(1, round_half_even_div(width * max_side, height))'),
+    ('ge_to_gt',
+     'if width >= height:',
+     'if width > height:'),
+    ('xs_off_by_one',
+     'xs = range((x2 * W) // W2, min(-(-((x2 + 1) * W) // W2), W))',
+     'xs = range((x2 * W) // W2, min(-(-((x2 + 1) * W) // W2), W - 1))'),
+    ('overlap_swapped',
+     'return max(0, min((o + 1) * n_in, (i + 1) * n_out) - max(o * n_in, i * n_out))',
+     'return max(0, min((o + 1) * n_out, (i + 1) * n_in) - max(o * n_out, i * n_in))'),
+    ('no_resize_equal',
+     'if max_side <= 0 or max(width, height) <= max_side:',
+     'if max_side <= 0 or max(width, height) < max_side:'),
+]
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("oracles", nargs="*", help="c, proposal, scfv and/or resize (default: all four)")
+    ap.add_argument("--only", nargs="*", default=None, help="slip names to run (default: all)")
+    args = ap.parse_args()
+    args.oracles = args.oracles or ["c", "proposal", "scfv", "resize"]
+    for o in args.oracles:
+        if o not in ("c", "proposal", "scfv", "resize"):
+            ap.error(f"unknown oracle {o!r}")
+
+    def pick(slips):
+        return [s for s in slips if args.only is None or s[0] in args.only]
+
+    unexpected = []
+    with tempfile.TemporaryDirectory(prefix="slips_") as tmpd:
+        for oracle in args.oracles:
+            if oracle == "c":
+                runs = check_c(pick(C_SLIPS), tmpd)
+            elif oracle == "proposal":
+                runs = check_py("proposal_oracle", "tests/test_proposal_oracle.py", pick(PROPOSAL_SLIPS), tmpd)
+            elif oracle == "scfv":
+                runs = check_py("scfv_oracle", "tests/test_scfv_oracle.py", pick(SCFV_SLIPS), tmpd)
+            else:
+                runs = check_py("resize_oracle", "tests/test_resize_oracle.py", pick(RESIZE_SLIPS), tmpd)
+            for name, caught in runs:
+                expected = (oracle, name) in EXPECTED_SURVIVORS
+                tag = "CAUGHT" if caught else ("SURVIVED (expected)" if expected else "SURVIVED")
+                print(f"{oracle:9s} {name:22s} {tag}", flush=True)
+                if not caught and not expected:
+                    unexpected.append(f"{oracle}/{name}")
+    if unexpected:
+        print("unexpected survivors:", " ".join(unexpected))
+        sys.exit(1)
+
+
+if __name__ == "__main__":
+    main()
