@@ -28,6 +28,9 @@ EXPECTED_SURVIVORS = {
     # fitted response between neighbours, which filtered images do not give;
     # near-ties are decided by the bracketing runs (margin = +-1e-4).
     ("c", "nbr_nonstrict"),
+    # Equivalent: with det H = 0 the edge ratio tr^2 / det is infinite (or NaN),
+    # so the next test rejects the point anyway.
+    ("c", "ref_det_ge"),
     # Equivalent: a square image takes the other branch to the same size.
     ("resize", "ge_to_gt"),
     # Equivalent: an image whose larger side equals the limit is "resized" to
@@ -219,6 +222,48 @@ C_SLIPS = [
     ('sigma_range_open',
      'if (!(s >= lo && s <= hi)) continue;',
      'if (!(s > lo && s < hi)) continue;'),
+    ('dd_any_octaves',
+     'if (d != 1 && d != -1) continue;',
+     'if (d == 0) continue;'),
+    ('ref_det_ge',
+     'if (!(det > 0.0)) return 0;',
+     'if (!(det >= 0.0)) return 0;'),
+    ('sel_resp_asc',
+     'if (ra != rb) return ra > rb ? -1 : 1;',
+     'if (ra != rb) return ra < rb ? -1 : 1;'),
+    ('sel_sigma_desc',
+     'if (a->sigma != b->sigma) return a->sigma < b->sigma ? -1 : 1;',
+     'if (a->sigma != b->sigma) return a->sigma < b->sigma ? 1 : -1;'),
+    ('sel_oct_desc',
+     'if (a->octave != b->octave) return a->octave < b->octave ? -1 : 1;',
+     'if (a->octave != b->octave) return a->octave < b->octave ? 1 : -1;'),
+    ('peak_ratio_ge',
+     'if (!(c > p->ori_peak_ratio * mx * (1.0 - m))) continue;',
+     'if (!(c >= p->ori_peak_ratio * mx * (1.0 - m))) continue;'),
+    ('peaks_tie_bin_desc',
+     '(pv[j] == pv[j - 1] && pb[j] < pb[j - 1])',
+     '(pv[j] == pv[j - 1] && pb[j] > pb[j - 1])'),
+    ('taps_no_norm',
+     'for (int i = 0; i < 2 * r + 1; ++i) taps[i] /= sum;',
+     ''),
+    ('base_from_level2',
+     'const double *top = levels + off - (size_t)Wo[o - 1] * Ho[o - 1];',
+     'const double *top = levels + off - 2 * (size_t)Wo[o - 1] * Ho[o - 1];'),
+    ('kp_no_offset',
+     'k.xo = x + r[0];',
+     'k.xo = x;'),
+    ('p_ss_factor',
+     'k.p_ss = 6.0 * a[3] * ss + 2.0 * a[2];',
+     'k.p_ss = 3.0 * a[3] * ss + 2.0 * a[2];'),
+    ('tr_a_v6_half',
+     'v[6] = ((h[0] + h[4]) - (h[2] + h[6])) / 4.0;',
+     'v[6] = ((h[0] + h[4]) - (h[2] + h[6])) / 2.0;'),
+    ('ori_margin_dir',
+     'if (p->ori_margin > 0.0 && frac > 1.0 - p->ori_margin) b += 1;',
+     'if (p->ori_margin > 0.0 && frac > 1.0 - p->ori_margin) b -= 1;'),
+    ('desc_w_sigma',
+     'const double ws2 = 2.0 * p->desc_weight_sigma * p->desc_weight_sigma;',
+     'const double ws2 = p->desc_weight_sigma * p->desc_weight_sigma;'),
 ]
 
 # ---- slips of the proposal-network oracle

@@ -300,7 +300,7 @@ def test_dedupe_rules(P):
         _kp(100, 100, 3.2, -20, 0), _kp(101, 99, 3.3, -25, 1),     # pair: second wins
         _kp(200, 50, 3.0, 30, 0), _kp(202, 52, 3.0, 30, 1),         # tie at the window edge: finer wins
         _kp(300, 300, 3.0, 10, 0), _kp(300, 300, 3.0, 50, 0),       # same octave: never duplicates
-        _kp(400, 100, 3.0, 10, 0), _kp(400, 100, 12.0, 50, 2),      # octaves 0 and 2: not adjacent
+        _kp(400, 100, 3.0, 10, 0), _kp(400, 100, 3.0, 50, 2),       # octaves 0 and 2, same place and scale: not adjacent
         _kp(500, 100, 3.0, 10, 0), _kp(500, 100, 3.0 * 2 ** (1 / 3) * 1.001, 50, 1),  # outside sigma window
         _kp(600, 100, 6.0, 10, 1), _kp(604, 100, 6.0, 50, 2),       # |dx| = 4 = 2^2 inclusive -> dup
         _kp(50, 400, 6.0, 10, 1), _kp(54.01, 400, 6.0, 50, 2),      # just outside the box
@@ -753,3 +753,52 @@ def test_descriptor_disc_is_open(radius, inside):
     G = _voters((41, 41), [((24, 20), (1, 0), 1.0)])
     h = O.descriptor_hist(G, 20.0, 20.0, 1.0, 0.0, p)
     assert bool(h.any()) == inside
+
+
+def test_selection_ties_by_sigma_then_octave():
+    """Eq. 5's order is total: |response| descending, then y, x, sigma and
+    octave ascending.  Five records equal in |response|, y and x (one of them
+    negative) sort by sigma, then by octave."""
+    c = np.concatenate([_kp(10, 10, 3.0, 5, 1), _kp(10, 10, 2.0, -5, 1), _kp(10, 10, 2.0, 5, 0),
+                        _kp(10, 10, 2.0, 5, 2), _kp(10, 10, 2.5, 5, 0)])
+    P = O.params()
+    keep = np.ones(c.size, np.uint8)
+    order = np.zeros(c.size, np.int32)
+    n = O.lib().oracle_select(O._p(c), O._p(keep), c.size, O._p(P), O._p(order))
+    assert order[:n].tolist() == [2, 1, 3, 4, 0]
+
+
+@pytest.mark.parametrize("ori_margin,bin_", [(0.0, 35), (1e-3, 0), (-1e-3, 35)])
+def test_orientation_bin_bracketing_direction(ori_margin, bin_):
+    """The bracketing runs move a vote within ori_margin (a fraction of a bin)
+    of a bin edge across that edge.  One voter at d = 7.7 px (sigma = 2) with
+    gradient (1, -1e-4): angle -1e-4 rad, 5.7e-4 of a bin below the edge of
+    bin 0, so it lands in bin 35, and in bin 0 once ori_margin = 1e-3 moves it
+    up; a negative margin moves only votes just above an edge.  Its tilt
+    leaves one other pixel of weight 1e-4 in bin 0."""
+    p = O.params(ori_margin=ori_margin)
+    G = _voters((61, 61), [((38, 30), (1, 0), 1.0), ((38, 30), (0, -1), 1e-4)])
+    _, h = O.orientations(G, 30.3, 30.0, 2.0, p)
+    w = math.sqrt(1 + 1e-8) * math.exp(-7.7 ** 2 / (2 * (1.5 * 2.0) ** 2))
+    assert h[bin_] == pytest.approx(w, rel=1e-3)
+    others = np.delete(h, [bin_, 0])
+    assert not others.any()
+
+
+def test_p_ss_is_the_cubics_second_derivative(P):
+    """p_ss of a record is d2p/dsigma2 of its pixel's ALP cubic at sigma*, and
+    sigma* is a root of dp/dsigma.  The cubic is rebuilt from the separately
+    pinned steps: levels, scale-normalised Laplacians and the ALP fit."""
+    img = synth.blob_image(synth.image_seed(24, 0), 120, 90, n_blobs=12)
+    levels = O.scale_space(img, P)
+    beta = O.alp_matrix(P)
+    L = [O.laplacian(levels[0][k], O.scale(P, k)) for k in range(4)]
+    c = O.candidates(img, P)
+    c = c[c["octave"] == 0]
+    assert c.size >= 5
+    for k in c:
+        x, y = int(round(k["xo"])), int(round(k["yo"]))
+        a = O.alp_fit(beta, np.array([Lk[y, x] for Lk in L]))
+        s = k["so"]
+        assert abs(3 * a[3] * s * s + 2 * a[2] * s + a[1]) <= 1e-9 * (abs(a[1]) + abs(a[2] * s) + abs(a[3] * s * s))
+        assert k["p_ss"] == pytest.approx(6 * a[3] * s + 2 * a[2], rel=1e-12, abs=1e-12)
