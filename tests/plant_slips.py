@@ -31,6 +31,12 @@ EXPECTED_SURVIVORS = {
     # Equivalent: with det H = 0 the edge ratio tr^2 / det is infinite (or NaN),
     # so the next test rejects the point anyway.
     ("c", "ref_det_ge"),
+    # Equivalent: an exact double root of dp/dsigma (D = 0) has p'' = 0 exactly
+    # there, which the next test rejects.
+    ("c", "D_lt"),
+    # Equivalent: with D > 0 the two roots are distinct and p'' is not 0 at
+    # either; in the near-quadratic branch p'' is 2 a2 + O(a3), and a2 != 0.
+    ("c", "pdd_zero_kept"),
     # Equivalent: a square image takes the other branch to the same size.
     ("resize", "ge_to_gt"),
     # Equivalent: an image whose larger side equals the limit is "resized" to
@@ -264,6 +270,36 @@ C_SLIPS = [
     ('desc_w_sigma',
      'const double ws2 = 2.0 * p->desc_weight_sigma * p->desc_weight_sigma;',
      'const double ws2 = p->desc_weight_sigma * p->desc_weight_sigma;'),
+    ('describe_level0',
+     'const double *G = levels + oracle_level_offset(W, H, p, o, k);',
+     'const double *G = levels + oracle_level_offset(W, H, p, o, 0);'),
+    ('extract_unordered',
+     'for (int i = 0; i < N; ++i) sel[i] = cand[order[i]];',
+     'for (int i = 0; i < N; ++i) sel[i] = cand[i];'),
+    ('quad_root_sign',
+     'if (B != 0.0) roots[nr++] = -C / B;',
+     'if (B != 0.0) roots[nr++] = C / B;'),
+    ('detect_border_2',
+     'for (int y = 1; y < H - 1; ++y)',
+     'for (int y = 2; y < H - 1; ++y)'),
+    ('filter_zero_pad',
+     'for (int q = -r; q <= r; ++q) acc += in[(size_t)clampi(i + q, 0, H - 1) * W + j] * taps[q + r];',
+     'for (int q = -r; q <= r; ++q) if (i + q >= 0 && i + q < H) acc += in[(size_t)(i + q) * W + j] * taps[q + r];'),
+    ('lap_zero_left',
+     'double l = G[(size_t)y * W + clampi(x - 1, 0, W - 1)];',
+     'double l = x > 0 ? G[(size_t)y * W + x - 1] : 0.0;'),
+    ('D_lt',
+     'if (D <= 0.0) return 0;',
+     'if (D < 0.0) return 0;'),
+    ('pdd_zero_kept',
+     'if (pdd == 0.0) continue;',
+     ''),
+    ('ref_gy_sign',
+     'double gy = 0.5 * (q[7] - q[1]);',
+     'double gy = 0.5 * (q[1] - q[7]);'),
+    ('ref_hyy_wrong',
+     'double hyy = q[7] - 2.0 * q[4] + q[1];',
+     'double hyy = q[7] - 2.0 * q[4] + q[3];'),
 ]
 
 # ---- slips of the proposal-network oracle

@@ -802,3 +802,47 @@ def test_p_ss_is_the_cubics_second_derivative(P):
         s = k["so"]
         assert abs(3 * a[3] * s * s + 2 * a[2] * s + a[1]) <= 1e-9 * (abs(a[1]) + abs(a[2] * s) + abs(a[3] * s * s))
         assert k["p_ss"] == pytest.approx(6 * a[3] * s + 2 * a[2], rel=1e-12, abs=1e-12)
+
+
+def test_laplacian_clamps_to_the_edge():
+    """Alg. 1's 5-point Laplacian reads the edge pixel again outside the level.
+    On G = x + 5 (20 x 30): at x = 0 the left sample is G(0) = 5, so the sum
+    is 5 + 6 + 5 + 5 - 4 * 5 = 1; at x = 29 the right sample is G(29), giving
+    -1; interior columns give 0.  Scaled by s^2 = 4."""
+    y, x = np.mgrid[0:20, 0:30].astype(np.float64)
+    L = O.laplacian(x + 5.0, 2.0)
+    assert np.all(L[:, 0] == 4.0) and np.all(L[:, -1] == -4.0) and np.all(L[:, 1:-1] == 0.0)
+    L = O.laplacian(y + 5.0, 2.0)
+    assert np.all(L[0, :] == 4.0) and np.all(L[-1, :] == -4.0) and np.all(L[1:-1, :] == 0.0)
+
+
+def test_detection_covers_every_interior_pixel(P):
+    """Alg. 1's 3 x 3 test runs at every pixel that has all eight neighbours:
+    bright 3 x 3 dots centred on rows 1 and 62 and columns 1 and 78 of a flat
+    64 x 80 image give extrema on those rows and columns of the first octave
+    (a refined position stays within 0.5 px of its pixel)."""
+    img = np.full((64, 80), 100, np.uint8)
+    for x, y in [(40, 1), (40, 62), (1, 30), (78, 30)]:
+        img[y - 1:y + 2, x - 1:x + 2] = 200
+    c = O.candidates(img, P)
+    c = c[c["octave"] == 0]
+    ys, xs = np.rint(c["yo"]).astype(int), np.rint(c["xo"]).astype(int)
+    assert ys.min() == 1 and ys.max() == 62 and xs.min() == 1 and xs.max() == 78
+
+
+def test_describe_reads_the_nearest_level(P):
+    """Alg. 2 describes a point on the Gaussian level of its octave nearest to
+    its scale: the pipeline's descriptors equal the stage run by hand on level
+    desc_level(sigma) of that octave, for points of levels 0 to 3 in octaves 0
+    and 1."""
+    img = synth.blob_image(synth.image_seed(25, 0), 96, 80, n_blobs=10)
+    levels = O.scale_space(img, P)
+    pts = np.concatenate([_kp(40.3, 37.6, 1.6 * 2 ** (t / 3) * 2 ** o, 9.0, o)
+                          for o in (0, 1) for t in (0.0, 1.1, 1.9, 3.0)])
+    kp, d = O.describe(img, pts, O.params(upright=1))
+    assert len(kp) == len(pts)
+    for r, dr in zip(kp, d):
+        k = O.desc_level(P, r["so"])
+        want = O.descriptor(levels[r["octave"]][k], r["xo"], r["yo"], r["so"], 0.0, P)
+        np.testing.assert_array_equal(dr, want)
+    assert sorted({O.desc_level(P, r["so"]) for r in kp}) == [0, 1, 2, 3]
