@@ -346,6 +346,30 @@ PROPOSAL_SLIPS = [
     ('blocks_of_8',
      'th, tw = -(-H // 16), -(-W // 16)',
      'th, tw = -(-H // 8), -(-W // 8)'),
+    ('bw_sigmoid_sign',
+     'dz = (1.0 / (1.0 + np.exp(-z)) - y) / n_blocks',
+     'dz = (y - 1.0 / (1.0 + np.exp(-z))) / n_blocks'),
+    ('bw_no_relu_mask_2',
+     'dz2 = da2 * (c["z2"] > 0)',
+     'dz2 = da2'),
+    ('bw_pool_div_16',
+     'da3[:, ys, xs] = dP[:, ty, tx][:, None, None] / n',
+     'da3[:, ys, xs] = dP[:, ty, tx][:, None, None] / 16'),
+    ('bw_dw_transposed',
+     'dw[:, :, ky, kx] = np.einsum("ohw,chw->oc", dz, pad[sl])',
+     'dw[:, :, ky, kx] = np.einsum("ohw,chw->co", dz, pad[sl])'),
+    ('bw_da_w_transposed',
+     'dpad[sl] += np.einsum("oc,ohw->chw", w[:, :, ky, kx], dz)',
+     'dpad[sl] += np.einsum("co,ohw->chw", w[:, :, ky, kx], dz)'),
+    ('bw_bh_mean',
+     'g["bh"] += dz.sum()',
+     'g["bh"] += dz.mean()'),
+    ('bw_per_image_mean',
+     'dz = (1.0 / (1.0 + np.exp(-z)) - y) / n_blocks',
+     'dz = (1.0 / (1.0 + np.exp(-z)) - y) / len(imgs)'),
+    ('labels_floor',
+     'bx = min(max(int(np.floor(x + 0.5)) // 16, 0), tw - 1)',
+     'bx = min(max(int(np.floor(x)) // 16, 0), tw - 1)'),
 ]
 
 # ---- slips of the SCFV oracle
