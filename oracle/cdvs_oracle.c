@@ -415,6 +415,20 @@ int oracle_detect_octave(const double *levels_o, int W, int H, int o, const orac
     return found;
 }
 
+/* Stages S2-S5 on one octave's given levels (K planes of W x H, level k at
+ * k W H), with its candidates copied to out (at most cap).  Returns their
+ * count.  A test entry point: it lets a test build levels whose responses tie
+ * exactly, which filtered images do not give. */
+int oracle_detect_levels(const double *levels_o, int W, int H, int o, const oracle_params *p,
+                         oracle_kp *out, int cap) {
+    oracle_kp *buf = NULL;
+    int n = 0, bcap = 0;
+    oracle_detect_octave(levels_o, W, H, o, p, &buf, &n, &bcap);
+    for (int i = 0; i < n && i < cap; ++i) out[i] = buf[i];
+    free(buf);
+    return n;
+}
+
 /* ------------------------------------------------ S7: cross-octave check */
 
 /* Alg. 1 stage C: candidates of adjacent octaves that are close in (x, y,

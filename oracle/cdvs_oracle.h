@@ -112,6 +112,11 @@ int oracle_refine(const double q[9], const oracle_params *p, double out[4]);
 int oracle_detect_octave(const double *levels_o, int W, int H, int o, const oracle_params *p,
                          oracle_kp **buf, int *n, int *cap);
 
+/* S2-S5 on given levels of one octave, candidates copied to out (at most
+ * cap); returns their number (a test entry point). */
+int oracle_detect_levels(const double *levels_o, int W, int H, int o, const oracle_params *p,
+                         oracle_kp *out, int cap);
+
 /* S7: keep[i] = 0 for candidates removed by the cross-octave check. */
 void oracle_dedupe(const oracle_kp *c, int n, const oracle_params *p, uint8_t *keep);
 

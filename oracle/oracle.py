@@ -76,6 +76,7 @@ def lib():
             "oracle_cubic": (f64, [P, f64]),
             "oracle_alp_extremum": (i32, [P, P, P, P]),
             "oracle_refine": (i32, [P, P, P]),
+            "oracle_detect_levels": (i32, [P, i32, i32, i32, P, P, i32]),
             "oracle_dedupe": (None, [P, i32, P, P]),
             "oracle_select": (i32, [P, P, i32, P, P]),
             "oracle_orientations": (i32, [P, i32, i32, f64, f64, f64, P, P, P]),
@@ -211,6 +212,15 @@ def refine(q3x3, p):
     out = np.zeros(4)
     ok = lib().oracle_refine(_p(q), _p(p), _p(out))
     return ok, out
+
+
+def detect_levels(levels: np.ndarray, octave: int, p, cap: int = 100000) -> np.ndarray:
+    """S2-S5 on given levels of one octave: levels (K, H, W) float64."""
+    a = np.ascontiguousarray(levels, np.float64)
+    out = np.zeros(cap, KP_DTYPE)
+    n = lib().oracle_detect_levels(_p(a), a.shape[2], a.shape[1], int(octave), _p(p), _p(out), cap)
+    assert n <= cap
+    return out[:n].copy()
 
 
 def dedupe(cands: np.ndarray, p) -> np.ndarray:

@@ -24,10 +24,6 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 # Slips no pin can catch, and why.
 EXPECTED_SURVIVORS = {
-    # The 3 x 3 neighbour test's strictness differs only on exact ties of the
-    # fitted response between neighbours, which filtered images do not give;
-    # near-ties are decided by the bracketing runs (margin = +-1e-4).
-    ("c", "nbr_nonstrict"),
     # Equivalent: with det H = 0 the edge ratio tr^2 / det is infinite (or NaN),
     # so the next test rejects the point anyway.
     ("c", "ref_det_ge"),

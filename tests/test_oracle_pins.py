@@ -846,3 +846,23 @@ def test_describe_reads_the_nearest_level(P):
         want = O.descriptor(levels[r["octave"]][k], r["xo"], r["yo"], r["so"], 0.0, P)
         np.testing.assert_array_equal(dr, want)
     assert sorted({O.desc_level(P, r["so"]) for r in kp}) == [0, 1, 2, 3]
+
+
+@pytest.mark.parametrize("right,n_points", [(1.0, 0), (1.25, 1)])
+def test_neighbour_test_is_strict(P, right, n_points):
+    """Alg. 1's 3 x 3 test wants the centre strictly beyond all 8 neighbours.
+    Levels G_k = c_k B, B a horizontal domino (1 and `right` at (9, 8) and
+    (10, 8)), c_k = w_k / s_k^2 with w = 100 (1, 3, 3, 1): every response is
+    B's Laplacian times one cubic in sigma with a maximum inside the octave.
+    With equal pixels the two responses tie exactly (the same operations on
+    the same values), so neither is a minimum and nothing is found; the ring
+    around them ties too.  With 1.25 on the right, that pixel is a strict
+    minimum and is found."""
+    B = np.zeros((16, 20))
+    B[8, 9], B[8, 10] = 1.0, right
+    w = 100.0 * np.array([1.0, 3.0, 3.0, 1.0])
+    levels = np.stack([w[k] / O.scale(P, k) ** 2 * B for k in range(4)])
+    c = O.detect_levels(levels, 0, P)
+    assert len(c) == n_points
+    if n_points:
+        assert c[0]["type"] == -1 and abs(c[0]["xo"] - 10) <= 0.5 and c[0]["yo"] == 8.0
