@@ -430,7 +430,12 @@ cdvs_status cdvs_set_scfv_model(cdvs_ctx *ctx, const cdvs_scfv_model *model);
  * Outputs per image (any may be NULL): g_mu and g_sigma [512][32], delta
  * [512], order [512] (component of each rank), bits [n_select] (0 <= n_select
  * <= 512).  flags: CDVS_INPUT_DEVICE (desc on the device), CDVS_OUTPUT_DEVICE
- * (outputs on the device).  Synchronous unless both flags are set. */
+ * (outputs on the device).  Synchronous unless both flags are set.  An
+ * asynchronous call returns before its kernels finish and does not read the
+ * device status back: a bounded wait that gave up shows only as NaN in g_mu,
+ * g_sigma and delta of the affected images, whose order and bits then carry
+ * no meaning.  A caller that needs the status as a return value makes a
+ * synchronous call. */
 cdvs_status cdvs_scfv(cdvs_ctx *ctx, int32_t n_images, const float *desc, const int32_t *counts,
                       int32_t n_select, float *g_mu, float *g_sigma, float *delta, int32_t *order,
                       uint32_t *bits, uint32_t flags, void *cuda_stream);
