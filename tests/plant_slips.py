@@ -1,7 +1,8 @@
-"""Plants one plausible slip at a time into a copy of an oracle and checks that
-the oracle's pins fail with it.  CPU only, run by hand:
+"""Plants one plausible slip at a time into a copy of an oracle (or of the
+parity gate, tests/parity.py) and checks that its pins fail with it.  CPU
+only, run by hand:
 
-    python tests/plant_slips.py [c|proposal|scfv|resize ...] [--only NAME ...]
+    python tests/plant_slips.py [c|proposal|scfv|resize|parity ...] [--only NAME ...]
 
 A slip is one exact text replacement in the oracle's source.  The C oracle's
 copy is built with gcc into a temporary folder and loaded, in a child
@@ -64,20 +65,25 @@ def check_c(slips, tmpd):
         yield name, _run_child(code)
 
 
-def check_py(module: str, test_file: str, slips, tmpd):
-    path = os.path.join(ROOT, "oracle", f"{module}.py")
+def check_py(module: str, test_file: str, slips, tmpd, path=None):
+    """Slips in a Python module: oracle/<module>.py, or the module at `path`
+    imported under the name `module`."""
+    path = path or os.path.join(ROOT, "oracle", f"{module}.py")
     src = open(path).read()
     for name, old, new in slips:
         if src.count(old) != 1:
             raise SystemExit(f"{module}/{name}: the text to replace occurs {src.count(old)} times")
-        mpath = os.path.join(tmpd, f"{module}_{name}.py")
+        mpath = os.path.join(tmpd, f"{module.replace('.', '_')}_{name}.py")
         with open(mpath, "w") as f:
             f.write(src.replace(old, new))
-        code = ("import sys, types; sys.path.insert(0, '.'); import oracle; "
-                f"m = types.ModuleType('oracle.{module}'); m.__file__ = {path!r}; "
+        parent = module.rsplit(".", 1)[0] if "." in module else None
+        code = ("import sys, types; sys.path.insert(0, '.'); sys.path.insert(0, 'tests'); "
+                + (f"import {parent}; " if parent else "")
+                + f"m = types.ModuleType({module!r}); m.__file__ = {path!r}; "
                 f"exec(compile(open({mpath!r}).read(), {path!r}, 'exec'), m.__dict__); "
-                f"sys.modules['oracle.{module}'] = m; oracle.{module} = m; import pytest; "
-                f"sys.exit(pytest.main(['-q', '-x', '-p', 'no:cacheprovider', {test_file!r}]))")
+                f"sys.modules[{module!r}] = m; "
+                + (f"{parent}.{module.rsplit('.', 1)[1]} = m; " if parent else "")
+                + f"import pytest; sys.exit(pytest.main(['-q', '-x', '-p', 'no:cacheprovider', {test_file!r}]))")
         yield name, _run_child(code)
 
 
@@ -437,14 +443,57 @@ RESIZE_SLIPS = [
 ]
 
 
+# ---- slips of the parity gate (tests/parity.py), checked by tests/test_parity_helpers.py
+PARITY_SLIPS = [
+    ('window_1px',
+     '(np.abs(bx - ax[i]) < 0.5) & (np.abs(by - ay[i]) < 0.5)',
+     '(np.abs(bx - ax[i]) < 1.0) & (np.abs(by - ay[i]) < 1.0)'),
+    ('dlog_wide',
+     '(np.abs(np.log(bsg / asg[i])) < 0.01)',
+     '(np.abs(np.log(bsg / asg[i])) < 0.1)'),
+    ('no_octave_test',
+     '(b["octave"] == a["octave"][i]) & ',
+     ''),
+    ('dup_record_margin',
+     'bad += 1  # a duplicate of oracle records already paired',
+     'margin += 1  # a duplicate of oracle records already paired'),
+    ('dup_points_ignored',
+     '(extra & ~extra_margin).sum() + dup.sum())',
+     '(extra & ~extra_margin).sum())'),
+    ('extra_always_margin',
+     'extra_margin = extra & g_in_loose',
+     'extra_margin = extra'),
+    ('miss_margin_or',
+     'miss_margin = miss & ~(e_in_loose & e_in_strict)',
+     'miss_margin = miss & ~(e_in_loose | e_in_strict)'),
+    ('theta_tol_10x',
+     'if ang(ek["theta"][j], gk["theta"][i]) <= THETA_TOL and rel_l2(gd[i], ed[j]) <= DESC_TOL])',
+     'if ang(ek["theta"][j], gk["theta"][i]) <= 10 * THETA_TOL and rel_l2(gd[i], ed[j]) <= DESC_TOL])'),
+    ('desc_tol_10x',
+     'if ang(ek["theta"][j], gk["theta"][i]) <= THETA_TOL and rel_l2(gd[i], ed[j]) <= DESC_TOL])',
+     'if ang(ek["theta"][j], gk["theta"][i]) <= THETA_TOL and rel_l2(gd[i], ed[j]) <= 10 * DESC_TOL])'),
+    ('ang_no_wrap',
+     'return min(d, 2 * np.pi - d)',
+     'return d'),
+    ('greedy_matching',
+     'if k not in seen_left:',
+     'if False:'),
+    ('perturbed_runs_ignored',
+     '                hit = True\n',
+     '                hit = False\n'),
+    ('at_point_ignored',
+     'if not hit and at_point is not None:',
+     'if False:'),
+]
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("oracles", nargs="*", help="c, proposal, scfv and/or resize (default: all four)")
+    ap.add_argument("oracles", nargs="*", help="c, proposal, scfv, resize and/or parity (default: all five)")
     ap.add_argument("--only", nargs="*", default=None, help="slip names to run (default: all)")
     args = ap.parse_args()
-    args.oracles = args.oracles or ["c", "proposal", "scfv", "resize"]
+    args.oracles = args.oracles or ["c", "proposal", "scfv", "resize", "parity"]
     for o in args.oracles:
-        if o not in ("c", "proposal", "scfv", "resize"):
+        if o not in ("c", "proposal", "scfv", "resize", "parity"):
             ap.error(f"unknown oracle {o!r}")
 
     def pick(slips):
@@ -456,11 +505,17 @@ def main():
             if oracle == "c":
                 runs = check_c(pick(C_SLIPS), tmpd)
             elif oracle == "proposal":
-                runs = check_py("proposal_oracle", "tests/test_proposal_oracle.py", pick(PROPOSAL_SLIPS), tmpd)
+                runs = check_py("oracle.proposal_oracle", "tests/test_proposal_oracle.py", pick(PROPOSAL_SLIPS), tmpd,
+                                os.path.join(ROOT, "oracle", "proposal_oracle.py"))
             elif oracle == "scfv":
-                runs = check_py("scfv_oracle", "tests/test_scfv_oracle.py", pick(SCFV_SLIPS), tmpd)
+                runs = check_py("oracle.scfv_oracle", "tests/test_scfv_oracle.py", pick(SCFV_SLIPS), tmpd,
+                                os.path.join(ROOT, "oracle", "scfv_oracle.py"))
+            elif oracle == "resize":
+                runs = check_py("oracle.resize_oracle", "tests/test_resize_oracle.py", pick(RESIZE_SLIPS), tmpd,
+                                os.path.join(ROOT, "oracle", "resize_oracle.py"))
             else:
-                runs = check_py("resize_oracle", "tests/test_resize_oracle.py", pick(RESIZE_SLIPS), tmpd)
+                runs = check_py("parity", "tests/test_parity_helpers.py", pick(PARITY_SLIPS), tmpd,
+                                os.path.join(ROOT, "tests", "parity.py"))
             for name, caught in runs:
                 expected = (oracle, name) in EXPECTED_SURVIVORS
                 tag = "CAUGHT" if caught else ("SURVIVED (expected)" if expected else "SURVIVED")

@@ -69,7 +69,8 @@ def test_point_window_and_octave():
     pts = ORACLE[[0]]
     near = _recs([(10.49, 9.51, 2.0 * np.exp(0.0099), 0, 0.0)])
     assert PT.point_agreement(near, pts, pts, pts)[1:] == (0, 0, 1)
-    for far in [(10.51, 10, 2.0, 0, 0.0), (10, 10, 2.0 * np.exp(0.0101), 0, 0.0), (10, 10, 2.0, 1, 0.0)]:
+    # (20, 20, 4.0) in octave 1 has the octave coordinates (10, 10, 2.0) of the oracle's point
+    for far in [(10.51, 10, 2.0, 0, 0.0), (10, 10, 2.0 * np.exp(0.0101), 0, 0.0), (20, 20, 4.0, 1, 0.0)]:
         assert PT.point_agreement(_recs([far]), pts, pts, pts)[1] == 2   # extra and missing
 
 
@@ -82,10 +83,14 @@ def test_orientation_and_descriptor_tolerances():
     gk["theta"][0] += 0.2 * PT.THETA_TOL
     gd[1] += 0.2 * PT.DESC_TOL / np.sqrt(128)
     assert PT.record_agreement(gk, gd, runs) == (3, 0, 2)
-    # theta wraps at 2 pi
-    gk, gd = ORACLE.copy(), DESC.copy()
-    gk["theta"][4] = ORACLE["theta"][4] - 2 * np.pi
-    assert PT.record_agreement(gk, gd, runs) == (5, 0, 0)
+    # theta wraps at 2 pi: 5e-5 and 2 pi - 3e-5 are 8e-5 apart
+    ek = ORACLE.copy()
+    ek["theta"][4] = 5e-5
+    gk, gd = ek.copy(), DESC.copy()
+    gk["theta"][4] = 2 * np.pi - 3e-5
+    assert PT.record_agreement(gk, gd, [(ek, DESC)] * 3) == (5, 0, 0)
+    gk["theta"][4] = 2 * np.pi - 6e-5
+    assert PT.record_agreement(gk, gd, [(ek, DESC)] * 3) == (4, 0, 1)
 
 
 def test_a_record_only_a_perturbed_run_explains_is_a_margin_case():
