@@ -114,3 +114,17 @@ def test_header_constants_match_the_binding():
     enum = dict((n, int(v)) for n, v in re.findall(r"\b(CDVS_[A-Z_]+) = ([0-9]+)", src))
     for n, v in enum.items():
         assert getattr(cdvs, n) == v, n
+
+
+def test_names_the_readme_examples_use_exist():
+    """The README's examples call these parameters, functions and methods."""
+    p = cdvs.params(max_keypoints=2000, num_octaves=6, storage=cdvs.CDVS_STORAGE_FP16, max_side=640,
+                    use_proposal=1, proposal_threshold=0.1)
+    assert int(p["max_keypoints"][0]) == 2000 and int(p["max_side"][0]) == 640
+    for name in ("rank_host", "transform_ternary", "load_proposal_weights", "CDVS_ASYNC"):
+        assert hasattr(cdvs, name), name
+    for name in ("extract", "extract_raw", "wait", "set_graph", "candidates", "dedupe_select", "describe",
+                 "set_scfv_model", "scfv", "set_proposal"):
+        assert callable(getattr(cdvs.Context, name)), name
+    theta, thr = cdvs.load_proposal_weights()
+    assert 0.0 < thr < 1.0 and theta.ndim == 1
