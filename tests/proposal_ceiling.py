@@ -1,6 +1,6 @@
 """What a perfect block proposal would skip (CPU, run by hand):
 
-    python tests/proposal_ceiling.py [n_images]
+    python tests/proposal_ceiling.py [n_images] [n_workloads]
 
 For 640 x 480 blob images of several densities and noise levels, the blocks
 holding a first-octave record of the FP64 oracle's extraction (the records a
@@ -28,10 +28,11 @@ WORKLOADS = [(200, 4.0), (60, 4.0), (20, 4.0), (20, 1.0), (6, 1.0)]   # (blobs, 
 
 def main():
     n_images = int(sys.argv[1]) if len(sys.argv) > 1 else 8
+    workloads = WORKLOADS[:int(sys.argv[2])] if len(sys.argv) > 2 else WORKLOADS
     p = cdvs.params()
     reach = max(float(p["desc_radius"][0]), float(p["ori_radius"][0])) * 2 * float(p["sigma0"][0]) * 1.001 + 2
     P = O.params()
-    for n_blobs, noise in WORKLOADS:
+    for n_blobs, noise in workloads:
         counts = np.zeros(3, np.int64)
         for i in range(n_images):
             img = synth.blob_image(synth.image_seed(900 + n_blobs, i), n_blobs=n_blobs, noise_std=noise)
