@@ -27,7 +27,8 @@ N_IMAGES = 48
 N_COMP, DIM = 512, 32
 
 
-def main():
+def compute():
+    """The model's arrays, as written to scfv_model.npz (without the source note)."""
     imgs = [synth.blob_image(synth.image_seed(SEED, i)) for i in range(N_IMAGES)]
     kp, d, counts = O.extract_batch(imgs, O.params(), cap=2048)
     X = np.concatenate([d[b, :counts[b]] for b in range(N_IMAGES)])
@@ -41,12 +42,16 @@ def main():
     means = Y[perm]
     var = np.tile(Y.var(axis=0) / 4.0, (N_COMP, 1))
     w = np.full(N_COMP, 1.0 / N_COMP)
+    return dict(pca_mean=mean.astype(np.float32), pca=P.astype(np.float32), weights=w.astype(np.float32),
+                means=means.astype(np.float32), variances=var.astype(np.float32)), len(X)
+
+
+def main():
+    model, n = compute()
     out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "scfv_model.npz")
-    np.savez(out, pca_mean=mean.astype(np.float32), pca=P.astype(np.float32), weights=w.astype(np.float32),
-             means=means.astype(np.float32), variances=var.astype(np.float32),
-             source=np.array(f"oracle descriptors of {N_IMAGES} seeded 640x480 images, seed 0x{SEED:X}, "
-                             f"{len(X)} records"))
-    print("wrote", out, "from", len(X), "descriptors")
+    np.savez(out, **model, source=np.array(f"oracle descriptors of {N_IMAGES} seeded 640x480 images, "
+                                           f"seed 0x{SEED:X}, {n} records"))
+    print("wrote", out, "from", n, "descriptors")
 
 
 if __name__ == "__main__":

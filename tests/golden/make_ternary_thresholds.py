@@ -22,7 +22,8 @@ SEED = 0xCA11B
 N_IMAGES = 100
 
 
-def main():
+def compute():
+    """The thresholds as written to ternary_thresholds.json."""
     p = O.params()
     imgs = [synth.blob_image(synth.image_seed(SEED, i)) for i in range(N_IMAGES)]
     kp, d, counts = O.extract_batch(imgs, p, cap=2048)
@@ -33,11 +34,15 @@ def main():
     V = np.array(V)
     lo = np.quantile(V, 1.0 / 3.0, axis=0)
     hi = np.quantile(V, 2.0 / 3.0, axis=0)
-    out = {"source": "oracle descriptors of %d seeded 640x480 images, base seed 0x%X" % (N_IMAGES, SEED),
-           "n_descriptors": int(V.shape[0]), "t_lo": lo.tolist(), "t_hi": hi.tolist()}
+    return {"source": "oracle descriptors of %d seeded 640x480 images, base seed 0x%X" % (N_IMAGES, SEED),
+            "n_descriptors": int(V.shape[0]), "t_lo": lo.tolist(), "t_hi": hi.tolist()}
+
+
+def main():
+    out = compute()
     with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "ternary_thresholds.json"), "w") as f:
         json.dump(out, f, indent=1)
-    print("wrote thresholds from", V.shape[0], "descriptors")
+    print("wrote thresholds from", out["n_descriptors"], "descriptors")
 
 
 if __name__ == "__main__":
