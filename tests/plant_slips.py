@@ -372,6 +372,15 @@ PROPOSAL_SLIPS = [
     ('labels_floor',
      'bx = min(max(int(np.floor(x + 0.5)) // 16, 0), tw - 1)',
      'bx = min(max(int(np.floor(x)) // 16, 0), tw - 1)'),
+    ('layout_w2_w3_swapped',
+     'SHAPES = [("W1", (C, 1, 3, 3)), ("b1", (C,)), ("W2", (C, C, 3, 3)), ("b2", (C,)),\n          ("W3", (C, C, 3, 3)), ("b3", (C,)), ("Wh", (C,)), ("bh", (1,))]',
+     'SHAPES = [("W1", (C, 1, 3, 3)), ("b1", (C,)), ("W3", (C, C, 3, 3)), ("b2", (C,)),\n          ("W2", (C, C, 3, 3)), ("b3", (C,)), ("Wh", (C,)), ("bh", (1,))]'),
+    ('bf16_ties_away',
+     'b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000',
+     'b = (b + 0x8000) & 0xFFFF0000'),
+    ('bf16_truncate',
+     'b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000',
+     'b = b & 0xFFFF0000'),
 ]
 
 # ---- slips of the SCFV oracle

@@ -142,3 +142,17 @@ def test_forward_rounds_the_weights_and_a1_to_bf16():
     assert c64["a1"][0, 10, 10] == 1.0 + 2.0 ** -9
     assert z16[1, 1] == 1.0
     assert z64[1, 1] == (1.0 + 2.0 ** -9) ** 2
+
+
+def test_flat_parameter_layout():
+    """The flat parameter vector the GPU also reads: W1 (144), b1 (16), W2
+    (2304), b2 (16), W3 (2304), b3 (16), Wh (16), bh (1) in that order, 4817
+    values, each weight tensor row-major over [co][ci][ky][kx]."""
+    assert PO.N_PARAMS == 4817
+    p = PO.unpack(np.arange(4817, dtype=np.float64))
+    starts = {"W1": 0, "b1": 144, "W2": 160, "b2": 2464, "W3": 2480, "b3": 4784, "Wh": 4800, "bh": 4816}
+    for name, first in starts.items():
+        assert p[name].ravel()[0] == first, name
+    assert p["W2"][1, 2, 0, 1] == 160 + ((1 * 16 + 2) * 3 + 0) * 3 + 1
+    assert p["W1"][3, 0, 2, 1] == (3 * 3 + 2) * 3 + 1
+    np.testing.assert_array_equal(PO.pack(p), np.arange(4817))
